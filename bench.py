@@ -1,0 +1,393 @@
+#!/usr/bin/env python
+"""Benchmark of the unitary-matrix simulation hot path on GB300.
+
+Workload (one "step"): a batch of 11-qubit circuits shaped like the paper's
+evaluated programs - fully entangled (GHZ chain), Deutsch-Jozsa with a
+constant and with a balanced oracle, and QFT on a seeded basis state, 25 %
+each - simulated by the fused step kernels in one CUDA-graph launch: the
+state of every circuit, |psi_i|^2 in FP64 and the FP64 norm of every circuit.
+Synthetic, seeded inputs (base seed 14398).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl tqs|reference]
+
+Prints one JSON line (rank 0).  metric: circuits/s (whole job); beside it the
+plain materialised-matrix form on the same GPU, the dense-equivalent complex
+GFLOP/s, the roofline of the fused kernel, the end-to-end rate through the
+host-buffer C entry point, and the CPU FP64 oracle timed on the host.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+N_QUBITS = 11
+BATCH = 16384
+METRIC = "circuits/s"
+WORKLOAD = "paper-shaped 11-qubit circuits (GHZ / DJ-constant / DJ-balanced / QFT, 25% each)"
+
+# DRAM bytes per launch of the fused warp-team kernel on this workload, from the
+# ncu capture summarised in profiles/ (None until measured for the current kernel).
+NCU_TRAFFIC_BYTES = None
+
+
+def parse_args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--impl", choices=["tqs", "reference"], default="tqs")
+    ap.add_argument("--batch", type=int, default=BATCH)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-plain", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+# ------------------------------------------------------------ CPU oracle arm
+
+ORACLE_SNIPPET = r"""
+import json, sys, time
+sys.path.insert(0, %(root)r)
+from oracle import kron_route
+from paper_2305_14398_gb300 import workloads as W
+mix = W.paper_mix(%(n)d, 4, seed_tag=%(tag)d)
+kinds = %(kinds)r
+t0 = time.perf_counter()
+done = 0
+for i in kinds:
+    name, ops = mix[i]
+    kron_route.simulate(%(n)d, ops)
+    done += 1
+dt = time.perf_counter() - t0
+print(json.dumps({"circuits": done, "seconds": dt}))
+"""
+
+
+def oracle_sample(kinds, tag=1):
+    """Time the oracle's literal route (Algorithm 1/2: Kronecker step matrix +
+    dense matvec per step, FP64) on the given circuits of the mix, one thread,
+    in a fresh process."""
+    env = dict(os.environ)
+    for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+        env[k] = "1"
+    code = ORACLE_SNIPPET % {"root": ROOT, "n": N_QUBITS, "tag": tag, "kinds": list(kinds)}
+    r = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True,
+                       timeout=900)
+    if r.returncode != 0:
+        raise RuntimeError("oracle sample failed: " + r.stderr[-2000:])
+    return json.loads(r.stdout.strip().splitlines()[-1])
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return 0
+    # each step: one circuit of the mix, kinds in rotation (GHZ, DJc, DJb, QFT)
+    for w in range(args.warmup):
+        oracle_sample([w % 4])
+    total_c, total_s = 0, 0.0
+    for k in range(args.steps):
+        r = oracle_sample([k % 4])
+        total_c += r["circuits"]
+        total_s += r["seconds"]
+    value = total_c / total_s
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "circuits/s",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * total_s / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "n_qubits": N_QUBITS},
+        "cpu_baseline": {"value": value, "unit": "circuits/s", "cores": 1, "kind": "oracle",
+                         "sample": "one circuit per step, kinds in rotation GHZ/DJ-constant/"
+                                   "DJ-balanced/QFT, literal Kronecker route, FP64, 1 thread"},
+        "e2e": {"value": value, "unit": "circuits/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ------------------------------------------------------------------ clocks
+
+class ClockSampler:
+    """nvidia-smi samples (timestamped on the host) during a window."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.samples = []
+        self.proc = None
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "50"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 8:
+                self.samples.append((time.perf_counter(), parts))
+
+    def stop(self):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+            self.thread.join(timeout=5)
+
+    def summary(self, t0, t1):
+        inside = [p for t, p in self.samples if t0 <= t <= t1]
+        window = "timed region"
+        if len(inside) < 3:
+            inside = [p for _, p in self.samples]
+            window = "warm-up + timed region (timed region shorter than the sampling period)"
+        if not inside:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"], "window": window}
+
+        def num(x):
+            try:
+                return float(x)
+            except ValueError:
+                return None
+
+        sm = [num(p[0]) for p in inside if num(p[0]) is not None]
+        smax = [num(p[1]) for p in inside if num(p[1]) is not None]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for p in inside for i in range(4) if p[4 + i] == "Active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None, "reasons": reasons,
+                "samples": len(inside), "window": window}
+
+
+def smi_index(local):
+    """nvidia-smi -i argument of this rank's GPU (index or UUID)."""
+    cvd = os.environ.get("CUDA_VISIBLE_DEVICES")
+    if cvd:
+        parts = [p.strip() for p in cvd.split(",") if p.strip()]
+        if local < len(parts):
+            return parts[local]
+    return str(local)
+
+
+# ----------------------------------------------------------------- GPU arm
+
+def run_tqs(args):
+    import torch
+
+    from paper_2305_14398_gb300 import binding as B
+    from paper_2305_14398_gb300 import build as _build
+    from paper_2305_14398_gb300 import workloads as W
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    if not os.path.exists(B.LIB_PATH):
+        _build.build()
+    B.lib()
+
+    # ---------------------------------------------------------- inputs
+    circs = [(N_QUBITS, ops) for _, ops in W.paper_mix(N_QUBITS, args.batch, seed_tag=1 + 1000 * rank)]
+    arrays = B.pack_ops(circs)
+    b = B.tqs_batch_create_packed(*arrays)
+    count, total, offs, steps_total, prog_bytes = B.tqs_batch_info(b, extra=True)
+    states = torch.empty(total, dtype=torch.complex64, device="cuda")
+    probs = torch.empty(total, dtype=torch.float64, device="cuda")
+    norms = torch.empty(count, dtype=torch.float64, device="cuda")
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")  # > 129 MB L2
+    stream = torch.cuda.current_stream()
+
+    sampler = ClockSampler(smi_index(local))
+    sampler.start()
+    # first run uploads and captures the graph (untimed)
+    B.tqs_batch_run(b, states, probs, norms, use_graph=True)
+    for _ in range(max(3, args.warmup)):
+        flush.zero_()
+        B.tqs_batch_run(b, states, probs, norms, use_graph=True)
+    torch.cuda.synchronize()
+    # soak so that clock samples exist around a short timed region
+    t_soak = time.perf_counter()
+    while time.perf_counter() - t_soak < 1.0:
+        B.tqs_batch_run(b, states, probs, norms, use_graph=True)
+        torch.cuda.synchronize()
+
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    launches0 = B.tqs_launch_count()
+    t0 = time.perf_counter()
+    for k in range(args.steps):
+        flush.zero_()  # L2 flush between timed steps (not timed)
+        ev[k][0].record(stream)
+        B.tqs_batch_run(b, states, probs, norms, use_graph=True)
+        ev[k][1].record(stream)
+    torch.cuda.synchronize()
+    t1 = time.perf_counter()
+    launches = B.tqs_launch_count() - launches0
+    if dist:
+        dist.barrier()
+    sampler.stop()
+    step_ms = [s.elapsed_time(e) for s, e in ev]
+    total_s = sum(step_ms) / 1e3
+    if dist:
+        t = torch.tensor([total_s], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_s = float(t.item())
+    value = count * world * args.steps / total_s
+    ms_step = 1e3 * total_s / args.steps
+
+    # sanity: every norm within 1e-6 of 1
+    nrm = norms.cpu()
+    norm_err = float((nrm - 1.0).abs().max())
+
+    # ------------------------------------------------- roofline (fused kernel)
+    N = 1 << N_QUBITS
+    alg_bytes = count * (N * 8 + N * 8 + 8) + prog_bytes  # state + probs + norm written, program read
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except (OSError, ValueError):
+        pass
+    hbm_peak = peaks.get("hbm_gbs", 6800.0)
+    peak_src = "measured" if "hbm_gbs" in peaks else "fallback"
+    achieved_gbs = alg_bytes / (ms_step / 1e3) / 1e9
+    dense_flops = 8.0 * (4 ** N_QUBITS) * steps_total  # ZGEMM convention, dense-equivalent
+    line = {
+        "metric": METRIC, "value": value, "unit": "circuits/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD, "n_qubits": N_QUBITS, "circuits_per_gpu": count,
+                   "steps_per_batch": steps_total, "parallelism": f"replicas x{world}",
+                   "l2": "flushed between timed steps (256 MiB write, not timed)",
+                   "outputs": "state (complex64) + |psi|^2 (f64) + norm (f64) per circuit"},
+        "dense_equiv_complex_gflops": dense_flops * world * args.steps / total_s / 1e9,
+        "roofline": {"bound": "hbm", "achieved": achieved_gbs, "peak": hbm_peak,
+                     "unit": "GB/s", "frac": achieved_gbs / hbm_peak,
+                     "traffic": NCU_TRAFFIC_BYTES, "peak_source": peak_src,
+                     "kernel": "fused_kernel<TEAM_WARP>",
+                     "algorithmic_bytes_per_launch": alg_bytes},
+        "norm_max_err": norm_err,
+        "gpu_launches": launches,
+    }
+    line["clocks"] = sampler.summary(t0, t1)
+
+    # ------------------------------------------------------- plain form
+    if not args.no_plain and rank == 0:
+        mix = W.paper_mix(N_QUBITS, 4, seed_tag=1)
+        handles = [B.circuit_from_ops(N_QUBITS, ops) for _, ops in mix]
+        out = torch.empty(N, dtype=torch.complex64, device="cuda")
+        for h in handles:
+            B.tqs_simulate_plain(h, out)
+        torch.cuda.synchronize()
+        reps = 3
+        s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        s.record(stream)
+        for _ in range(reps):
+            for h in handles:
+                B.tqs_simulate_plain(h, out)
+        e.record(stream)
+        torch.cuda.synchronize()
+        plain_s = s.elapsed_time(e) / 1e3
+        plain_steps = sum(B.tqs_circuit_info(h)[2] for h in handles) * reps
+        for h in handles:
+            B.tqs_circuit_destroy(h)
+        plain_rate = 4 * reps / plain_s
+        line["plain"] = {
+            "value": plain_rate, "unit": "circuits/s",
+            "sample": "one circuit of each kind, 3 repetitions",
+            "dense_equiv_complex_gflops": 8.0 * (4 ** N_QUBITS) * plain_steps / plain_s / 1e9,
+            "hbm_gbs_algorithmic": 16.0 * (4 ** N_QUBITS) * plain_steps / plain_s / 1e9,
+            "fused_speedup": value / world / plain_rate,
+        }
+
+    # ------------------------------------------------------- end to end
+    if not args.no_e2e:
+        h_states = torch.empty(total, dtype=torch.complex64).pin_memory()
+        h_probs = torch.empty(total, dtype=torch.float64).pin_memory()
+        h_norms = torch.empty(count, dtype=torch.float64).pin_memory()
+        e2e_steps = max(3, min(args.steps, 10))
+        bb = B.tqs_batch_create_packed(*arrays)
+        B.tqs_batch_run_host(bb, h_states, h_probs, h_norms)  # warm
+        B.tqs_batch_destroy(bb)
+        if dist:
+            dist.barrier()
+        te0 = time.perf_counter()
+        for _ in range(e2e_steps):
+            bb = B.tqs_batch_create_packed(*arrays)
+            B.tqs_batch_run_host(bb, h_states, h_probs, h_norms)
+            B.tqs_batch_destroy(bb)
+        te = time.perf_counter() - te0
+        if dist:
+            t = torch.tensor([te], device="cuda", dtype=torch.float64)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            te = float(t.item())
+        line["e2e"] = {"value": count * world * e2e_steps / te, "unit": "circuits/s",
+                       "h2d_bytes_per_step": int(prog_bytes),
+                       "d2h_bytes_per_step": int(total * 8 + total * 8 + count * 8),
+                       "steps": e2e_steps,
+                       "path": "tqs_batch_create_packed (host gate arrays) + tqs_batch_run_host "
+                               "(pinned host buffers) + tqs_batch_destroy"}
+
+    # ---------------------------------------------------------- CPU oracle
+    if not args.no_cpu_baseline and rank == 0:
+        r = oracle_sample([0, 1, 2, 3])
+        line["cpu_baseline"] = {
+            "value": r["circuits"] / r["seconds"], "unit": "circuits/s", "cores": 1,
+            "kind": "oracle",
+            "sample": "4 circuits (one GHZ, DJ-constant, DJ-balanced, QFT) of the same workload, "
+                      "literal Kronecker route (Algorithm 1/2), FP64, 1 thread",
+        }
+
+    B.tqs_batch_destroy(b)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    args = parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_tqs(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

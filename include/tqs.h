@@ -1,0 +1,250 @@
+/*
+ * tqs.h - C ABI of the GB300 (sm_103a) unitary-matrix quantum circuit
+ * simulator.
+ *
+ * Model (TornadoQSim, arXiv 2305.14398):
+ *   - a circuit of n qubits records operations through gate calls; steps are
+ *     created as operations are added (Sec. 5.2, circuit model);
+ *   - each step's 2^n x 2^n unitary is the Kronecker product of the step's
+ *     gate matrices, identity on idle qubits (Algorithm 2, eq. 9s1), with a
+ *     controlled gate written as the projector sum
+ *     |0><0|_c (x) I_t + |1><1|_c (x) U_t (eq. 7);
+ *   - the state evolves as psi <- S_k psi (eq. 11); the circuit unitary is
+ *     the chain U <- S_k U (Algorithm 1);
+ *   - simulateFullState returns the state; probabilities |psi_i|^2 give the
+ *     measurement statistics (Sec. 5.2, Simulator interface).
+ *
+ * Conventions shared by every call:
+ *   - Qubit q is bit q of an amplitude index (little-endian).  A state is
+ *     2^n interleaved complex64 values (tqs_c64) in index order.
+ *   - Controlled gates take qubits {control, target}.
+ *   - Pointers named d_* are DEVICE pointers (cudaMalloc'd or from a CUDA
+ *     caching allocator) owned by the caller; pointers named h_* are host
+ *     pointers owned by the caller.  The library never frees caller memory.
+ *   - Device buffers passed in must be 16-byte aligned (any cudaMalloc or
+ *     torch allocation is); a misaligned pointer returns TQS_ERR_ARG.
+ *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *     stream).  Device work is enqueued on it and the call returns without
+ *     synchronising unless stated.  Library-internal scratch (programs,
+ *     step tables, operand planes, partial sums) is allocated with
+ *     cudaMalloc by the first call that needs it, cached on its handle (or,
+ *     for calls without a handle, per host thread), and freed by the
+ *     handle's destroy call (cudaFree waits for the device).  Make that
+ *     first call outside any stream capture.
+ *   - Every call returns a tqs_status; no exception crosses the ABI.  On
+ *     error, tqs_last_error() returns a message for the calling thread.
+ *     Argument errors are detected before any device work is enqueued.
+ *     Asynchronous CUDA errors surface as TQS_ERR_CUDA from a later call.
+ */
+#ifndef TQS_ABI_H_
+#define TQS_ABI_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct { float re, im; } tqs_c64;
+
+typedef struct tqs_circuit tqs_circuit;
+typedef struct tqs_batch tqs_batch;
+
+typedef enum {
+  TQS_OK = 0,
+  TQS_ERR_ARG = 1,              /* NULL pointer, bad count, bad gate id, bad params */
+  TQS_ERR_QUBIT_RANGE = 2,      /* qubit index outside [0, n) */
+  TQS_ERR_QUBIT_DUP = 3,        /* the same qubit twice in one gate */
+  TQS_ERR_TOO_MANY_QUBITS = 4,  /* n above the call's limit */
+  TQS_ERR_NOMEM = 5,            /* host or device allocation failed */
+  TQS_ERR_BUDGET = 6,           /* request does not fit the given memory budget */
+  TQS_ERR_CUDA = 7,             /* a CUDA runtime call failed */
+  TQS_ERR_TIMEOUT = 8,          /* a bounded device wait ran out */
+  TQS_ERR_STATE = 9,            /* object used in the wrong state */
+  TQS_ERR_UNSUPPORTED = 10      /* valid request this build does not implement */
+} tqs_status;
+
+/* Gate kinds.  Table 1 (Sec. 2.3): H, X, Y, Z, R (phase shift R_phi,
+ * params {phi}).  Sec. 5.2 names S and T (S = R_{pi/2}, T = R_{pi/4}).
+ * RX, RY, RZ (params {theta}) and U3 (params {theta, phi, lambda}) use the
+ * textbook definitions.  Controlled gates (eq. 7, qubits {control, target}):
+ * CNOT (eq. 8), CZ, CP (params {phi}) and CU (params: 8 doubles, re/im of
+ * u00, u01, u10, u11; must be unitary to 1e-9).  SWAP (qubits {a, b})
+ * appears in the QFT circuit of Sec. 2.5. */
+typedef enum {
+  TQS_H = 0, TQS_X = 1, TQS_Y = 2, TQS_Z = 3, TQS_S = 4, TQS_T = 5, TQS_R = 6,
+  TQS_RX = 7, TQS_RY = 8, TQS_RZ = 9, TQS_U3 = 10,
+  TQS_CNOT = 11, TQS_CZ = 12, TQS_CP = 13, TQS_CU = 14, TQS_SWAP = 15,
+  TQS_GATE_COUNT = 16
+} tqs_gate;
+
+/* Arithmetic of the circuit-unitary chain (Algorithm 1). */
+typedef enum {
+  TQS_PREC_FP32_SIMT = 0,   /* FP32 CUDA-core complex GEMM (4 real products) */
+  TQS_PREC_TC_BF16X3 = 1,   /* tcgen05 tensor cores, 3M complex product, each real
+                               product as BF16 hi*hi + hi*lo + lo*hi, FP32 accumulate */
+  TQS_PREC_TC_TF32X3 = 2    /* as above with TF32 hi/lo splits (not built yet:
+                               returns TQS_ERR_UNSUPPORTED) */
+} tqs_prec;
+
+#define TQS_MAX_QUBITS 16          /* state-vector calls */
+#define TQS_MAX_DENSE_QUBITS 14    /* calls that hold a 2^n x 2^n matrix */
+
+/* ------------------------------------------------------------------ circuit
+ * Sec. 5.2 (circuit model): create a circuit of n qubits, add operations
+ * through gate calls, which check each operation's preconditions; steps
+ * are created as operations are added ("as soon as possible": an operation
+ * joins the step after the last step that touches one of its qubits). */
+
+/* Create an empty circuit of 1 <= n_qubits <= TQS_MAX_QUBITS qubits.
+ * *out receives the handle (owned by the caller until tqs_circuit_destroy). */
+tqs_status tqs_circuit_create(int n_qubits, tqs_circuit** out);
+
+/* Destroy a circuit and any device memory it caches.  NULL is accepted. */
+tqs_status tqs_circuit_destroy(tqs_circuit* c);
+
+/* Append one gate.  qubits: nq = 1 (single-qubit gates) or 2 (controlled
+ * gates: {control, target}; SWAP: {a, b}).  params: np doubles as listed
+ * under tqs_gate (np may exceed the need; extra values are ignored; params
+ * may be NULL when the gate takes none).  Errors: TQS_ERR_ARG,
+ * TQS_ERR_QUBIT_RANGE, TQS_ERR_QUBIT_DUP.  On error the circuit is unchanged. */
+tqs_status tqs_add_gate(tqs_circuit* c, int gate, const int* qubits, int nq,
+                        const double* params, int np);
+
+/* Sizes of the circuit: qubits, gates, and steps of the step table. */
+tqs_status tqs_circuit_info(const tqs_circuit* c, int* n_qubits, int* n_gates, int* n_steps);
+
+/* Step table (Sec. 5.3 stages 1-3): h_step_of_gate[g] receives the step index
+ * of gate g (n_gates ints, host memory). */
+tqs_status tqs_circuit_steps(const tqs_circuit* c, int* h_step_of_gate);
+
+/* Inspection of the fused step program that tqs_simulate runs (for tests
+ * of the host compiler and for tools).  The circuit's steps are compiled
+ * into passes; a pass names 4 "local" physical qubit bits, and each of its
+ * ops applies one step factor to the amplitudes in registers.
+ *   *n_passes, *n_ops : receive the sizes (may be NULL).
+ *   h_passes : NULL or n_passes records of 16 bytes:
+ *              {uint8 L[4]; uint32 op_begin; uint32 op_count; uint32 pad}
+ *   h_ops    : NULL or n_ops records of 48 bytes:
+ *              {uint8 kind (0 dense, 1 anti-diagonal, 2 diagonal), tloc, t,
+ *               ckind (0 none, 1 local, 2 far), c, unit, pad[2];
+ *               float m[8] (4 complex entries); uint32 pad[2]}
+ *   h_pos    : NULL or 16 bytes, the physical bit of each logical qubit at
+ *              the end (SWAP factors are relabelings).
+ * Host memory only; no device work. */
+tqs_status tqs_circuit_program(tqs_circuit* c, int* n_passes, int* n_ops, void* h_passes,
+                               void* h_ops, uint8_t* h_pos);
+
+/* ---------------------------------------------------------------- simulate
+ * simulateFullState (Sec. 5.2): the final state psi = S_m ... S_1 psi_0.
+ * Each step is applied by the fused step kernel, which generates the step
+ * unitary from its Kronecker factors in registers instead of reading a
+ * materialised matrix.
+ *   d_init  : 2^n tqs_c64 initial state, or NULL for |0...0>.
+ *   d_out   : 2^n tqs_c64, receives the final state (must not alias d_init).
+ *   d_probs : 2^n doubles, receives |psi_i|^2 computed in FP64, or NULL.
+ *   d_norm  : 1 double, receives sum_i |psi_i|^2 (FP64), or NULL.
+ * n <= TQS_MAX_QUBITS.  Arithmetic: FP32 amplitudes, FP64 probabilities. */
+tqs_status tqs_simulate(tqs_circuit* c, const tqs_c64* d_init, tqs_c64* d_out,
+                        double* d_probs, double* d_norm, void* stream);
+
+/* The same result by the plain materialised form (Sec. 5.3 stages 4 and 6,
+ * applied per step): for each step, S_k is written to device scratch as a
+ * dense 2^n x 2^n complex64 matrix (Algorithm 2) and psi <- S_k psi is a
+ * dense matrix-vector product.  n <= TQS_MAX_DENSE_QUBITS.  Scratch:
+ * 8 * 4^n + 16 * 2^n bytes, cached on the circuit. */
+tqs_status tqs_simulate_plain(tqs_circuit* c, const tqs_c64* d_init, tqs_c64* d_out,
+                              void* stream);
+
+/* Algorithm 2 alone: write step `step` (0-based) of the circuit as a dense
+ * row-major matrix, d_S[r * 2^n + c] = <r|S|c>.  n <= TQS_MAX_DENSE_QUBITS. */
+tqs_status tqs_materialize_step(tqs_circuit* c, int step, tqs_c64* d_S, void* stream);
+
+/* ----------------------------------------------------------------- unitary
+ * Algorithm 1: the circuit unitary U = S_m ... S_1 as a chain of complex
+ * matrix products U <- S_k U (the product with the initial identity is
+ * skipped), in the arithmetic `prec` (tqs_prec).
+ *   d_U : 2^n x 2^n tqs_c64, row-major, d_U[r * 2^n + c] = <r|U|c>.
+ * n <= TQS_MAX_DENSE_QUBITS; tensor-core precisions need n >= 7.
+ * Scratch: about 28 * 4^n bytes (operand planes), released with the circuit. */
+tqs_status tqs_circuit_unitary(tqs_circuit* c, int prec, tqs_c64* d_U, void* stream);
+
+/* ---------------------------------------------------------- probabilities
+ * p_i = |psi_i|^2 in FP64 (the products of the FP32 parts are exact in
+ * FP64) and their FP64 sum, summed in a fixed order (deterministic).
+ *   d_state : 2^n tqs_c64;  d_probs : 2^n doubles or NULL;
+ *   d_sum   : 1 double or NULL.  1 <= n <= 30.
+ * Scratch: one double per reduction block. */
+tqs_status tqs_probabilities(const tqs_c64* d_state, int n, double* d_probs,
+                             double* d_sum, void* stream);
+
+/* Marginal probability that every qubit set in `mask` reads 0:
+ * sum of |psi_i|^2 over i with (i & mask) == 0, FP64, deterministic
+ * (Deutsch-Jozsa input register, Sec. 2.5).  d_out: 1 double. */
+tqs_status tqs_marginal_zero(const tqs_c64* d_state, int n, uint64_t mask,
+                             double* d_out, void* stream);
+
+/* ------------------------------------------------------------------- batch
+ * Many circuits of uneven size and depth simulated by one graph launch of
+ * the persistent fused step kernels.  The batch copies what it needs from
+ * the circuits at creation; they may be destroyed afterwards.
+ * Output layout: circuit i's state occupies amplitudes
+ * [offsets[i], offsets[i+1]) of d_states (and the same range of d_probs);
+ * d_norms[i] receives its probability sum. */
+
+/* Create a batch from `count` circuit handles (each n <= TQS_MAX_QUBITS). */
+tqs_status tqs_batch_create(tqs_circuit* const* cs, int count, tqs_batch** out);
+
+/* Create a batch straight from host gate arrays (no circuit handles):
+ *   h_nq[count]         qubit count of each circuit
+ *   h_gate_off[count+1] gate range of circuit i: [h_gate_off[i], h_gate_off[i+1])
+ *   h_kind[G]           tqs_gate of each gate
+ *   h_qubits[2*G]       qubits of each gate (second ignored for 1-qubit gates)
+ *   h_params[8*G]       parameters of each gate, 8 slots per gate
+ * Preconditions are checked as in tqs_add_gate. */
+tqs_status tqs_batch_create_packed(int count, const int32_t* h_nq, const int64_t* h_gate_off,
+                                   const int32_t* h_kind, const int32_t* h_qubits,
+                                   const double* h_params, tqs_batch** out);
+
+/* Sizes of a batch (each output may be NULL): number of circuits, total
+ * amplitudes, total steps of the step tables (ASAP packing), bytes of the
+ * device program the kernels read, and h_offsets (count+1 int64) the
+ * amplitude offsets of the circuits. */
+tqs_status tqs_batch_info(const tqs_batch* b, int* count, int64_t* total_amps,
+                          int64_t* total_steps, int64_t* program_bytes, int64_t* h_offsets);
+
+/* Run the batch on `stream`: d_states (total_amps tqs_c64), d_probs
+ * (total_amps doubles or NULL), d_norms (count doubles or NULL).  The first
+ * run uploads the batch program (cached) and, with use_graph != 0, captures
+ * the launches into a CUDA graph that later runs with the same pointers
+ * replay. */
+tqs_status tqs_batch_run(tqs_batch* b, tqs_c64* d_states, double* d_probs, double* d_norms,
+                         int use_graph, void* stream);
+
+/* Host-buffer form of tqs_batch_run: uploads the program, runs, and copies
+ * the results into h_states / h_probs / h_norms (host memory, NULL to skip),
+ * then synchronises `stream`.  Pinned host memory makes the copies faster. */
+tqs_status tqs_batch_run_host(tqs_batch* b, tqs_c64* h_states, double* h_probs,
+                              double* h_norms, void* stream);
+
+/* Destroy the batch and its device memory.  NULL is accepted. */
+tqs_status tqs_batch_destroy(tqs_batch* b);
+
+/* ------------------------------------------------------------------ misc */
+
+/* Thread-local message of the last failed call ("" if none). */
+const char* tqs_last_error(void);
+
+/* Static name of a status code. */
+const char* tqs_status_string(int status);
+
+/* Number of this library's kernel launches enqueued so far by this process
+ * (a graph replay counts its kernel nodes). */
+int64_t tqs_launch_count(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* TQS_ABI_H_ */

@@ -1,0 +1,295 @@
+"""ctypes binding of libtqs.so (include/tqs.h): argument marshalling only.
+
+Every function has the C entry point's name and calls it once.  Device
+buffers are torch CUDA tensors (their data_ptr() is passed); streams default
+to torch's current stream.  All computation happens in the library's
+kernels: if libtqs.so is missing this module raises instead of falling back.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import re
+from typing import Iterable, List, Optional, Sequence, Tuple
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libtqs.so")
+HEADER = os.path.join(os.path.dirname(HERE), "include", "tqs.h")
+
+GATE_IDS = {"h": 0, "x": 1, "y": 2, "z": 3, "s": 4, "t": 5, "r": 6, "rx": 7, "ry": 8, "rz": 9,
+            "u3": 10, "cx": 11, "cnot": 11, "cz": 12, "cp": 13, "cu": 14, "swap": 15}
+TWO_QUBIT_IDS = {11, 12, 13, 14, 15}
+
+PREC_FP32_SIMT = 0
+PREC_TC_BF16X3 = 1
+PREC_TC_TF32X3 = 2
+
+STATUS = ["TQS_OK", "TQS_ERR_ARG", "TQS_ERR_QUBIT_RANGE", "TQS_ERR_QUBIT_DUP",
+          "TQS_ERR_TOO_MANY_QUBITS", "TQS_ERR_NOMEM", "TQS_ERR_BUDGET", "TQS_ERR_CUDA",
+          "TQS_ERR_TIMEOUT", "TQS_ERR_STATE", "TQS_ERR_UNSUPPORTED"]
+
+
+class TqsError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        name = STATUS[status] if 0 <= status < len(STATUS) else str(status)
+        super().__init__(f"{name}: {message}")
+        self.status = status
+        self.name = name
+
+
+_lib = None
+
+_vp = ctypes.c_void_p
+_i = ctypes.c_int
+_i64 = ctypes.c_int64
+_u64 = ctypes.c_uint64
+_pi = ctypes.POINTER(ctypes.c_int)
+_pd = ctypes.POINTER(ctypes.c_double)
+
+_SIGS = {
+    "tqs_circuit_create": (_i, [_i, ctypes.POINTER(_vp)]),
+    "tqs_circuit_destroy": (_i, [_vp]),
+    "tqs_add_gate": (_i, [_vp, _i, _pi, _i, _pd, _i]),
+    "tqs_circuit_info": (_i, [_vp, _pi, _pi, _pi]),
+    "tqs_circuit_steps": (_i, [_vp, _pi]),
+    "tqs_circuit_program": (_i, [_vp, _pi, _pi, _vp, _vp, _vp]),
+    "tqs_simulate": (_i, [_vp, _vp, _vp, _vp, _vp, _vp]),
+    "tqs_simulate_plain": (_i, [_vp, _vp, _vp, _vp]),
+    "tqs_materialize_step": (_i, [_vp, _i, _vp, _vp]),
+    "tqs_circuit_unitary": (_i, [_vp, _i, _vp, _vp]),
+    "tqs_probabilities": (_i, [_vp, _i, _vp, _vp, _vp]),
+    "tqs_marginal_zero": (_i, [_vp, _i, _u64, _vp, _vp]),
+    "tqs_batch_create": (_i, [ctypes.POINTER(_vp), _i, ctypes.POINTER(_vp)]),
+    "tqs_batch_create_packed": (_i, [_i, _vp, _vp, _vp, _vp, _vp, ctypes.POINTER(_vp)]),
+    "tqs_batch_info": (_i, [_vp, _pi, ctypes.POINTER(_i64), ctypes.POINTER(_i64),
+                            ctypes.POINTER(_i64), _vp]),
+    "tqs_batch_run": (_i, [_vp, _vp, _vp, _vp, _i, _vp]),
+    "tqs_batch_run_host": (_i, [_vp, _vp, _vp, _vp, _vp]),
+    "tqs_batch_destroy": (_i, [_vp]),
+    "tqs_last_error": (ctypes.c_char_p, []),
+    "tqs_status_string": (ctypes.c_char_p, [_i]),
+    "tqs_launch_count": (_i64, []),
+}
+
+
+def lib():
+    """Load libtqs.so (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is missing: build it with "
+                               "`python -m paper_2305_14398_gb300.build`")
+        L = ctypes.CDLL(LIB_PATH)
+        for name, (res, args) in _SIGS.items():
+            if hasattr(L, name):
+                f = getattr(L, name)
+                f.restype = res
+                f.argtypes = args
+        _lib = L
+    return _lib
+
+
+def header_functions() -> List[str]:
+    """Names of the functions include/tqs.h declares."""
+    txt = open(HEADER).read()
+    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+    return sorted(set(re.findall(r"\b(tqs_[a-z0-9_]+)\s*\(", txt)))
+
+
+def _check(status: int):
+    if status != 0:
+        msg = lib().tqs_last_error().decode(errors="replace")
+        raise TqsError(status, msg)
+
+
+def _ptr(t) -> Optional[int]:
+    if t is None:
+        return None
+    return t.data_ptr()
+
+
+def _stream(stream) -> Optional[int]:
+    if stream is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+# ----------------------------------------------------------------- circuit
+
+def tqs_circuit_create(n_qubits: int) -> int:
+    h = _vp()
+    _check(lib().tqs_circuit_create(int(n_qubits), ctypes.byref(h)))
+    return h.value
+
+
+def tqs_circuit_destroy(c: int) -> None:
+    _check(lib().tqs_circuit_destroy(c))
+
+
+def tqs_add_gate(c: int, gate, qubits: Sequence[int], params: Sequence[float] = ()) -> None:
+    gid = GATE_IDS[gate] if isinstance(gate, str) else int(gate)
+    qs = (ctypes.c_int * len(qubits))(*[int(q) for q in qubits])
+    ps = (ctypes.c_double * max(1, len(params)))(*[float(p) for p in params])
+    _check(lib().tqs_add_gate(c, gid, qs, len(qubits), ps, len(params)))
+
+
+def tqs_circuit_info(c: int) -> Tuple[int, int, int]:
+    n, g, s = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+    _check(lib().tqs_circuit_info(c, ctypes.byref(n), ctypes.byref(g), ctypes.byref(s)))
+    return n.value, g.value, s.value
+
+
+def tqs_circuit_steps(c: int) -> List[int]:
+    _, g, _ = tqs_circuit_info(c)
+    arr = (ctypes.c_int * max(1, g))()
+    _check(lib().tqs_circuit_steps(c, arr))
+    return list(arr[:g])
+
+
+PASS_DTYPE = np.dtype([("L", np.uint8, 4), ("op_begin", np.uint32), ("op_count", np.uint32),
+                       ("pad", np.uint32)])
+OP_DTYPE = np.dtype([("kind", np.uint8), ("tloc", np.uint8), ("t", np.uint8), ("ckind", np.uint8),
+                     ("c", np.uint8), ("unit", np.uint8), ("pad0", np.uint8, 2),
+                     ("m", np.complex64, 4), ("pad1", np.uint32, 2)])
+
+
+def tqs_circuit_program(c: int):
+    """(passes, ops, pos) of the compiled fused program as numpy records."""
+    npass, nops = ctypes.c_int(), ctypes.c_int()
+    _check(lib().tqs_circuit_program(c, ctypes.byref(npass), ctypes.byref(nops), None, None, None))
+    passes = np.zeros(npass.value, dtype=PASS_DTYPE)
+    ops = np.zeros(nops.value, dtype=OP_DTYPE)
+    pos = np.zeros(16, dtype=np.uint8)
+    _check(lib().tqs_circuit_program(c, None, None, passes.ctypes.data, ops.ctypes.data,
+                                     pos.ctypes.data))
+    return passes, ops, pos
+
+
+def circuit_from_ops(n: int, ops: Iterable) -> int:
+    """tqs_circuit_create + one tqs_add_gate per (name, qubits, params)."""
+    c = tqs_circuit_create(n)
+    try:
+        for name, qs, ps in ops:
+            tqs_add_gate(c, name, qs, ps)
+    except Exception:
+        tqs_circuit_destroy(c)
+        raise
+    return c
+
+
+# ---------------------------------------------------------------- simulate
+
+def tqs_simulate(c: int, out, init=None, probs=None, norm=None, stream=None) -> None:
+    _check(lib().tqs_simulate(c, _ptr(init), _ptr(out), _ptr(probs), _ptr(norm), _stream(stream)))
+
+
+def tqs_simulate_plain(c: int, out, init=None, stream=None) -> None:
+    _check(lib().tqs_simulate_plain(c, _ptr(init), _ptr(out), _stream(stream)))
+
+
+def tqs_materialize_step(c: int, step: int, S, stream=None) -> None:
+    _check(lib().tqs_materialize_step(c, int(step), _ptr(S), _stream(stream)))
+
+
+def tqs_circuit_unitary(c: int, prec: int, U, stream=None) -> None:
+    _check(lib().tqs_circuit_unitary(c, int(prec), _ptr(U), _stream(stream)))
+
+
+def tqs_probabilities(state, n: int, probs=None, total=None, stream=None) -> None:
+    _check(lib().tqs_probabilities(_ptr(state), int(n), _ptr(probs), _ptr(total), _stream(stream)))
+
+
+def tqs_marginal_zero(state, n: int, mask: int, out, stream=None) -> None:
+    _check(lib().tqs_marginal_zero(_ptr(state), int(n), int(mask), _ptr(out), _stream(stream)))
+
+
+# ------------------------------------------------------------------- batch
+
+def tqs_batch_create(circuits: Sequence[int]) -> int:
+    arr = (_vp * len(circuits))(*circuits)
+    h = _vp()
+    _check(lib().tqs_batch_create(arr, len(circuits), ctypes.byref(h)))
+    return h.value
+
+
+def pack_ops(circuits: Sequence[Tuple[int, Sequence]]):
+    """Host arrays of tqs_batch_create_packed from [(n, ops), ...]."""
+    count = len(circuits)
+    nq = np.empty(count, dtype=np.int32)
+    off = np.zeros(count + 1, dtype=np.int64)
+    for i, (n, ops) in enumerate(circuits):
+        nq[i] = n
+        off[i + 1] = off[i] + len(ops)
+    G = int(off[-1])
+    kind = np.empty(max(G, 1), dtype=np.int32)
+    qub = np.zeros((max(G, 1), 2), dtype=np.int32)
+    par = np.zeros((max(G, 1), 8), dtype=np.float64)
+    k = 0
+    for n, ops in circuits:
+        for name, qs, ps in ops:
+            kind[k] = GATE_IDS[name]
+            qub[k, :len(qs)] = qs
+            par[k, :len(ps)] = ps
+            k += 1
+    return nq, off, kind, qub, par
+
+
+def tqs_batch_create_packed(nq, off, kind, qub, par) -> int:
+    nq = np.ascontiguousarray(nq, dtype=np.int32)
+    off = np.ascontiguousarray(off, dtype=np.int64)
+    kind = np.ascontiguousarray(kind, dtype=np.int32)
+    qub = np.ascontiguousarray(qub, dtype=np.int32)
+    par = np.ascontiguousarray(par, dtype=np.float64)
+    h = _vp()
+    _check(lib().tqs_batch_create_packed(len(nq), nq.ctypes.data, off.ctypes.data, kind.ctypes.data,
+                                         qub.ctypes.data, par.ctypes.data, ctypes.byref(h)))
+    return h.value
+
+
+def tqs_batch_info(b: int, extra: bool = False):
+    """(count, total_amps, offsets) or, with extra, also (total_steps, program_bytes)."""
+    count, total, steps, pbytes = ctypes.c_int(), _i64(), _i64(), _i64()
+    _check(lib().tqs_batch_info(b, ctypes.byref(count), ctypes.byref(total), ctypes.byref(steps),
+                                ctypes.byref(pbytes), None))
+    offs = np.empty(count.value + 1, dtype=np.int64)
+    _check(lib().tqs_batch_info(b, None, None, None, None, offs.ctypes.data))
+    if extra:
+        return count.value, total.value, offs, steps.value, pbytes.value
+    return count.value, total.value, offs
+
+
+def tqs_batch_run(b: int, states, probs=None, norms=None, use_graph: bool = True, stream=None) -> None:
+    _check(lib().tqs_batch_run(b, _ptr(states), _ptr(probs), _ptr(norms), int(bool(use_graph)),
+                               _stream(stream)))
+
+
+def tqs_batch_run_host(b: int, h_states=None, h_probs=None, h_norms=None, stream=None) -> None:
+    """Host buffers: torch CPU tensors (pinned or not) or numpy arrays."""
+    def hp(x):
+        if x is None:
+            return None
+        if isinstance(x, np.ndarray):
+            return x.ctypes.data
+        return x.data_ptr()
+    _check(lib().tqs_batch_run_host(b, hp(h_states), hp(h_probs), hp(h_norms), _stream(stream)))
+
+
+def tqs_batch_destroy(b: int) -> None:
+    _check(lib().tqs_batch_destroy(b))
+
+
+def tqs_launch_count() -> int:
+    return int(lib().tqs_launch_count())
+
+
+def tqs_last_error() -> str:
+    return lib().tqs_last_error().decode(errors="replace")
+
+
+def tqs_status_string(s: int) -> str:
+    return lib().tqs_status_string(int(s)).decode()

@@ -1,0 +1,82 @@
+// Probabilities and their FP64 sum (sm_103a).
+//
+// p_i = |psi_i|^2 (Sec. 2.1, eq. 2) computed in FP64 from the FP32 parts (their
+// squares are exact in FP64), optionally written out, and summed over the
+// indices i with (i & zero_mask) == 0 (zero_mask = 0: the norm; otherwise the
+// marginal probability that the masked qubits read 0, as for the
+// Deutsch-Jozsa input register of Sec. 2.5).  The reduction runs in a fixed
+// order: per-block partial sums into scratch, then one warp sums the
+// partials, so the result does not depend on scheduling.
+#include "tqs_internal.h"
+
+namespace tqs {
+namespace {
+
+constexpr int kProbThreads = 256;
+constexpr int64_t kAmpsPerBlock = 8192;
+constexpr int kMaxPartials = 1024;
+
+__global__ void __launch_bounds__(kProbThreads)
+    probs_kernel(const float2* __restrict__ st, int64_t N, int64_t chunk, double* __restrict__ probs,
+                 uint64_t zero_mask, double* __restrict__ partials) {
+  const int64_t begin = int64_t(blockIdx.x) * chunk;
+  int64_t end = begin + chunk;
+  if (end > N) end = N;
+  double acc = 0.0;
+  for (int64_t i = begin + 2 * threadIdx.x; i < end; i += 2 * kProbThreads) {
+    const float4 v = __ldcs(reinterpret_cast<const float4*>(st + i));
+    const double x0 = v.x, y0 = v.y, x1 = v.z, y1 = v.w;
+    const double q0 = fma(x0, x0, y0 * y0);
+    const double q1 = fma(x1, x1, y1 * y1);
+    if (probs) __stcs(reinterpret_cast<double2*>(probs + i), make_double2(q0, q1));
+    if ((static_cast<uint64_t>(i) & zero_mask) == 0) acc += q0;
+    if ((static_cast<uint64_t>(i + 1) & zero_mask) == 0) acc += q1;
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  __shared__ double red[kProbThreads / 32];
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double s = 0.0;
+#pragma unroll
+    for (int w = 0; w < kProbThreads / 32; ++w) s += red[w];
+    partials[blockIdx.x] = s;
+  }
+}
+
+__global__ void sum_partials_kernel(const double* __restrict__ partials, int count,
+                                    double* __restrict__ out) {
+  double acc = 0.0;
+  for (int i = threadIdx.x; i < count; i += 32) acc += partials[i];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  if (threadIdx.x == 0) *out = acc;
+}
+
+}  // namespace
+
+int probs_partial_count(int n) {
+  const int64_t N = int64_t(1) << n;
+  int64_t blocks = (N + kAmpsPerBlock - 1) / kAmpsPerBlock;
+  if (blocks > kMaxPartials) blocks = kMaxPartials;
+  if (blocks < 1) blocks = 1;
+  return static_cast<int>(blocks);
+}
+
+cudaError_t launch_probs(const float2* d_state, int n, double* d_probs, uint64_t zero_mask,
+                         double* d_partials, int n_partials, double* d_sum, cudaStream_t s) {
+  const int64_t N = int64_t(1) << n;
+  int64_t chunk = (N + n_partials - 1) / n_partials;
+  chunk = (chunk + 1) & ~int64_t(1);
+  probs_kernel<<<n_partials, kProbThreads, 0, s>>>(d_state, N, chunk, d_probs, zero_mask,
+                                                   d_partials);
+  count_launches(1);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess || d_sum == nullptr) return e;
+  sum_partials_kernel<<<1, 32, 0, s>>>(d_partials, n_partials, d_sum);
+  count_launches(1);
+  return cudaGetLastError();
+}
+
+}  // namespace tqs

@@ -1,0 +1,997 @@
+// Host side of the C ABI (include/tqs.h): gate data, the circuit model and its
+// step packing, the fused-pass compiler, batches, and the entry points.
+//
+// Sec. 5.2: the circuit model records operations and creates steps as they
+// are added; the data provider supplies each operation's matrix separately
+// from the circuit structure.  Sec. 5.3: stages 1-3 (steps, operations per
+// step, operation data) run here; stages 4-6 run in the kernels.
+#include <algorithm>
+#include <atomic>
+#include <cmath>
+#include <complex>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <memory>
+#include <mutex>
+#include <numeric>
+#include <string>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "../../include/tqs.h"
+#include "tqs_internal.h"
+
+namespace tqs {
+
+// ---------------------------------------------------------------- errors
+
+static thread_local std::string g_last_error;
+static std::atomic<int64_t> g_launches{0};
+
+void count_launches(int64_t k) { g_launches.fetch_add(k, std::memory_order_relaxed); }
+
+static tqs_status fail(tqs_status s, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof(buf), fmt, ap);
+  va_end(ap);
+  g_last_error = buf;
+  return s;
+}
+
+static tqs_status cuda_fail(cudaError_t e, const char* what) {
+  return fail(e == cudaErrorMemoryAllocation ? TQS_ERR_NOMEM : TQS_ERR_CUDA, "%s: %s", what,
+              cudaGetErrorString(e));
+}
+
+#define TQS_CUDA(call, what)                      \
+  do {                                            \
+    cudaError_t e_ = (call);                      \
+    if (e_ != cudaSuccess) return cuda_fail(e_, what); \
+  } while (0)
+
+// A device buffer owned by a handle (cudaMalloc / cudaFree).
+struct DevBuf {
+  void* p = nullptr;
+  size_t bytes = 0;
+  DevBuf() = default;
+  DevBuf(const DevBuf&) = delete;
+  DevBuf& operator=(const DevBuf&) = delete;
+  ~DevBuf() { release(); }
+  void release() {
+    if (p) cudaFree(p);
+    p = nullptr;
+    bytes = 0;
+  }
+  cudaError_t ensure(size_t n) {
+    if (n <= bytes && p) return cudaSuccess;
+    release();
+    cudaError_t e = cudaMalloc(&p, n ? n : 16);
+    if (e == cudaSuccess) bytes = n;
+    else p = nullptr;
+    return e;
+  }
+  template <class T> T* as() const { return static_cast<T*>(p); }
+};
+
+// ------------------------------------------------------------ gate data
+// Table 1 (Sec. 2.3), S and T (Sec. 5.2), textbook rotations, eq. 7 / eq. 8.
+
+using cd = std::complex<double>;
+
+struct Mat2 {
+  cd m[4];  // [[m0, m1], [m2, m3]]
+};
+
+static bool is_controlled(int g) { return g == TQS_CNOT || g == TQS_CZ || g == TQS_CP || g == TQS_CU; }
+static bool is_two_qubit(int g) { return is_controlled(g) || g == TQS_SWAP; }
+static int n_params(int g) {
+  switch (g) {
+    case TQS_R: case TQS_RX: case TQS_RY: case TQS_RZ: case TQS_CP: return 1;
+    case TQS_U3: return 3;
+    case TQS_CU: return 8;
+    default: return 0;
+  }
+}
+
+// Single-qubit matrix of a gate, or the U of a controlled gate.
+static Mat2 gate_matrix(int g, const double* p) {
+  const double r2 = 1.0 / std::sqrt(2.0);
+  const cd I(0.0, 1.0);
+  Mat2 u;
+  switch (g) {
+    case TQS_H: u = {{r2, r2, r2, -r2}}; break;
+    case TQS_X: case TQS_CNOT: u = {{0.0, 1.0, 1.0, 0.0}}; break;
+    case TQS_Y: u = {{0.0, -I, I, 0.0}}; break;
+    case TQS_Z: case TQS_CZ: u = {{1.0, 0.0, 0.0, -1.0}}; break;
+    case TQS_S: u = {{1.0, 0.0, 0.0, I}}; break;
+    case TQS_T: u = {{1.0, 0.0, 0.0, std::polar(1.0, M_PI / 4.0)}}; break;
+    case TQS_R: case TQS_CP: u = {{1.0, 0.0, 0.0, std::polar(1.0, p[0])}}; break;
+    case TQS_RX: {
+      const double c = std::cos(p[0] / 2), s = std::sin(p[0] / 2);
+      u = {{c, -I * s, -I * s, c}};
+      break;
+    }
+    case TQS_RY: {
+      const double c = std::cos(p[0] / 2), s = std::sin(p[0] / 2);
+      u = {{c, -s, s, c}};
+      break;
+    }
+    case TQS_RZ: u = {{std::polar(1.0, -p[0] / 2), 0.0, 0.0, std::polar(1.0, p[0] / 2)}}; break;
+    case TQS_U3: {
+      const double c = std::cos(p[0] / 2), s = std::sin(p[0] / 2);
+      u = {{c, -std::polar(1.0, p[2]) * s, std::polar(1.0, p[1]) * s,
+            std::polar(1.0, p[1] + p[2]) * c}};
+      break;
+    }
+    case TQS_CU: u = {{cd(p[0], p[1]), cd(p[2], p[3]), cd(p[4], p[5]), cd(p[6], p[7])}}; break;
+    default: u = {{1.0, 0.0, 0.0, 1.0}}; break;
+  }
+  return u;
+}
+
+static bool is_unitary(const Mat2& u, double tol) {
+  const cd a = u.m[0], b = u.m[1], c = u.m[2], d = u.m[3];
+  // U^dagger U
+  const cd e00 = std::conj(a) * a + std::conj(c) * c;
+  const cd e01 = std::conj(a) * b + std::conj(c) * d;
+  const cd e11 = std::conj(b) * b + std::conj(d) * d;
+  return std::abs(e00 - 1.0) <= tol && std::abs(e11 - 1.0) <= tol && std::abs(e01) <= tol;
+}
+
+// One recorded operation.
+struct Gate {
+  int kind;
+  int q[2];
+  int nq;
+  double p[8];
+  Mat2 u;     // single-qubit matrix, or the controlled U
+  int step;   // step index (ASAP)
+};
+
+static inline float2 to_f2(cd z) {
+  return make_float2(static_cast<float>(z.real()), static_cast<float>(z.imag()));
+}
+
+// ---------------------------------------------------------- fused compile
+
+enum GClass { G_DENSE, G_ANTI, G_DIAG, G_SWAP };
+
+static GClass classify(const Gate& g) {
+  if (g.kind == TQS_SWAP) return G_SWAP;
+  const Mat2& u = g.u;
+  if (u.m[1] == cd(0.0) && u.m[2] == cd(0.0)) return G_DIAG;
+  if (u.m[0] == cd(0.0) && u.m[3] == cd(0.0)) return G_ANTI;
+  return G_DENSE;
+}
+
+struct Program {
+  int n = 0, nint = 4;
+  std::vector<FusedPass> passes;
+  std::vector<FusedOp> ops;
+  uint8_t pos[16];
+  int identity = 1;
+  double cost = 0.0;
+};
+
+// Turn the circuit (gates in step order) into passes of 4 local bits.  One
+// in-order scan per pass: a gate is ready when no earlier unscheduled gate
+// shares a qubit with it (tracked as `blocked` qubits); a ready non-diagonal
+// gate is scheduled if its target bit is or can become local; diagonal gates
+// are always scheduled; SWAPs relabel qubits.  The result does not depend on
+// the other circuits of a batch.
+static void compile_program(int n, const std::vector<const Gate*>& gs, Program& P) {
+  P.n = n;
+  P.nint = std::max(n, 4);
+  const int nint = P.nint;
+  int phys[16];
+  for (int q = 0; q < 16; ++q) phys[q] = q;
+  const uint32_t all = (n >= 32) ? 0xffffffffu : ((1u << n) - 1u);
+  std::vector<int> pending(gs.size()), still;
+  std::iota(pending.begin(), pending.end(), 0);
+  struct Raw {
+    const Gate* g;
+    GClass cls;
+    int t, c;  // physical bits (c = -1: uncontrolled)
+  };
+  std::vector<Raw> raw;
+  auto emit_pass = [&](uint32_t Lmask, int nL) {
+    for (int b = 0; nL < 4 && b < nint; ++b)
+      if (!((Lmask >> b) & 1)) { Lmask |= 1u << b; ++nL; }
+    FusedPass ps{};
+    int loc[16];
+    for (int b = 0; b < 16; ++b) loc[b] = -1;
+    int k = 0;
+    for (int b = 0; b < nint; ++b)
+      if ((Lmask >> b) & 1) { ps.L[k] = static_cast<uint8_t>(b); loc[b] = k++; }
+    ps.op_begin = static_cast<uint32_t>(P.ops.size());
+    ps.op_count = static_cast<uint32_t>(raw.size());
+    double pass_cost = 6.0;
+    for (const Raw& r : raw) {
+      FusedOp op{};
+      const Mat2& u = r.g->u;
+      if (r.cls == G_DIAG) {
+        op.kind = OP_DIAG;
+        op.m[0] = to_f2(u.m[0]);
+        op.m[1] = to_f2(u.m[3]);
+        op.m[2] = to_f2(u.m[3] / u.m[0]);
+        pass_cost += 0.5;
+      } else if (r.cls == G_ANTI) {
+        op.kind = OP_ANTI;
+        op.m[1] = to_f2(u.m[1]);
+        op.m[2] = to_f2(u.m[2]);
+        op.unit = (u.m[1] == cd(1.0) && u.m[2] == cd(1.0)) ? 1 : 0;
+        pass_cost += 1.0;
+      } else {
+        op.kind = OP_DENSE;
+        for (int i = 0; i < 4; ++i) op.m[i] = to_f2(u.m[i]);
+        pass_cost += 2.0;
+      }
+      if (loc[r.t] >= 0) { op.tloc = 1; op.t = static_cast<uint8_t>(loc[r.t]); }
+      else { op.tloc = 0; op.t = static_cast<uint8_t>(r.t); }
+      if (r.c < 0) { op.ckind = CTL_NONE; op.c = 0; }
+      else if (loc[r.c] >= 0) { op.ckind = CTL_LOCAL; op.c = static_cast<uint8_t>(loc[r.c]); }
+      else { op.ckind = CTL_FAR; op.c = static_cast<uint8_t>(r.c); }
+      P.ops.push_back(op);
+    }
+    P.passes.push_back(ps);
+    P.cost += pass_cost * static_cast<double>(1u << nint);
+    raw.clear();
+  };
+  while (!pending.empty()) {
+    uint32_t Lmask = 0, blocked = 0;
+    int nL = 0;
+    still.clear();
+    size_t idx = 0;
+    for (; idx < pending.size(); ++idx) {
+      if (blocked == all) break;
+      const Gate& g = *gs[pending[idx]];
+      const uint32_t qm = (1u << g.q[0]) | (g.nq == 2 ? (1u << g.q[1]) : 0u);
+      if (qm & blocked) {  // an earlier gate on one of its qubits waits: so must it,
+        blocked |= qm;     // and every later gate on any of its qubits
+        still.push_back(pending[idx]);
+        continue;
+      }
+      const GClass cls = classify(g);
+      if (cls == G_SWAP) { std::swap(phys[g.q[0]], phys[g.q[1]]); continue; }
+      const int tq = is_controlled(g.kind) ? g.q[1] : g.q[0];
+      const int cq = is_controlled(g.kind) ? g.q[0] : -1;
+      const int t = phys[tq];
+      const int c = cq >= 0 ? phys[cq] : -1;
+      if (cls != G_DIAG && !((Lmask >> t) & 1)) {
+        if (nL == 4) { blocked |= qm; still.push_back(pending[idx]); continue; }
+        Lmask |= 1u << t;
+        ++nL;
+      }
+      raw.push_back({&g, cls, t, c});
+    }
+    for (; idx < pending.size(); ++idx) still.push_back(pending[idx]);
+    emit_pass(Lmask, nL);
+    pending.swap(still);
+  }
+  if (P.passes.empty()) emit_pass(0u, 0);
+  P.identity = 1;
+  for (int q = 0; q < 16; ++q) {
+    P.pos[q] = static_cast<uint8_t>(q < n ? phys[q] : q);
+    if (q < n && phys[q] != q) P.identity = 0;
+  }
+  P.cost += 2.0 * static_cast<double>(1u << n);
+}
+
+static int team_for(int nint) {
+  if (nint <= kWarpMaxQ) return TEAM_WARP;
+  if (nint <= kCtaMaxQ) return TEAM_CTA;
+  return TEAM_GLOBAL;
+}
+
+static int device_sms() {
+  static int sms = 0;
+  if (sms == 0) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (sms <= 0) sms = 1;
+  }
+  return sms;
+}
+
+}  // namespace tqs
+
+using namespace tqs;
+
+// ------------------------------------------------------------------ circuit
+
+struct tqs_circuit {
+  int n = 0;
+  std::vector<Gate> gates;
+  std::vector<int> last;  // last step touching each qubit
+  int nsteps = 0;
+  // cached fused program and its device copy
+  bool prog_valid = false;
+  Program prog;
+  DevBuf d_prog;      // FusedCirc + passes + ops
+  DevBuf d_counter;   // job counter
+  DevBuf d_gscratch;  // TEAM_GLOBAL slot
+  // cached plain-form step table
+  bool steps_valid = false;
+  std::vector<StepFactor> factors;
+  std::vector<StepDesc> steps;
+  DevBuf d_factors;
+  DevBuf d_plain;     // S scratch + two state vectors
+  DevBuf d_partials;  // probability partials
+  // chain scratch
+  DevBuf d_chain;
+};
+
+extern "C" {
+
+const char* tqs_last_error(void) { return g_last_error.c_str(); }
+
+const char* tqs_status_string(int s) {
+  switch (s) {
+    case TQS_OK: return "TQS_OK";
+    case TQS_ERR_ARG: return "TQS_ERR_ARG";
+    case TQS_ERR_QUBIT_RANGE: return "TQS_ERR_QUBIT_RANGE";
+    case TQS_ERR_QUBIT_DUP: return "TQS_ERR_QUBIT_DUP";
+    case TQS_ERR_TOO_MANY_QUBITS: return "TQS_ERR_TOO_MANY_QUBITS";
+    case TQS_ERR_NOMEM: return "TQS_ERR_NOMEM";
+    case TQS_ERR_BUDGET: return "TQS_ERR_BUDGET";
+    case TQS_ERR_CUDA: return "TQS_ERR_CUDA";
+    case TQS_ERR_TIMEOUT: return "TQS_ERR_TIMEOUT";
+    case TQS_ERR_STATE: return "TQS_ERR_STATE";
+    case TQS_ERR_UNSUPPORTED: return "TQS_ERR_UNSUPPORTED";
+    default: return "TQS_ERR_UNKNOWN";
+  }
+}
+
+int64_t tqs_launch_count(void) { return g_launches.load(); }
+
+tqs_status tqs_circuit_create(int n_qubits, tqs_circuit** out) {
+  if (!out) return fail(TQS_ERR_ARG, "tqs_circuit_create: out is NULL");
+  *out = nullptr;
+  if (n_qubits < 1) return fail(TQS_ERR_ARG, "tqs_circuit_create: n_qubits must be >= 1");
+  if (n_qubits > TQS_MAX_QUBITS)
+    return fail(TQS_ERR_TOO_MANY_QUBITS, "tqs_circuit_create: n_qubits %d > %d", n_qubits,
+                TQS_MAX_QUBITS);
+  tqs_circuit* c = new (std::nothrow) tqs_circuit();
+  if (!c) return fail(TQS_ERR_NOMEM, "tqs_circuit_create: out of host memory");
+  c->n = n_qubits;
+  c->last.assign(n_qubits, -1);
+  *out = c;
+  return TQS_OK;
+}
+
+tqs_status tqs_circuit_destroy(tqs_circuit* c) {
+  delete c;
+  return TQS_OK;
+}
+
+static tqs_status check_gate(int n, int gate, const int* qubits, int nq, const double* params,
+                             int np, Gate& g) {
+  if (gate < 0 || gate >= TQS_GATE_COUNT) return fail(TQS_ERR_ARG, "unknown gate id %d", gate);
+  const int want = is_two_qubit(gate) ? 2 : 1;
+  if (!qubits || nq != want)
+    return fail(TQS_ERR_ARG, "gate %d takes %d qubit(s), got %d", gate, want, nq);
+  const int need = n_params(gate);
+  if (np < need || (need > 0 && !params))
+    return fail(TQS_ERR_ARG, "gate %d takes %d parameter(s), got %d", gate, need, np);
+  for (int i = 0; i < nq; ++i)
+    if (qubits[i] < 0 || qubits[i] >= n)
+      return fail(TQS_ERR_QUBIT_RANGE, "qubit %d outside [0, %d)", qubits[i], n);
+  if (nq == 2 && qubits[0] == qubits[1])
+    return fail(TQS_ERR_QUBIT_DUP, "gate %d uses qubit %d twice", gate, qubits[0]);
+  g.kind = gate;
+  g.nq = nq;
+  g.q[0] = qubits[0];
+  g.q[1] = nq == 2 ? qubits[1] : qubits[0];
+  for (int i = 0; i < 8; ++i) g.p[i] = (i < need) ? params[i] : 0.0;
+  for (int i = 0; i < need; ++i)
+    if (!std::isfinite(g.p[i])) return fail(TQS_ERR_ARG, "gate %d: non-finite parameter", gate);
+  g.u = gate_matrix(gate, g.p);
+  if (gate == TQS_CU && !is_unitary(g.u, 1e-9))
+    return fail(TQS_ERR_ARG, "CU matrix is not unitary to 1e-9");
+  return TQS_OK;
+}
+
+tqs_status tqs_add_gate(tqs_circuit* c, int gate, const int* qubits, int nq, const double* params,
+                        int np) {
+  if (!c) return fail(TQS_ERR_ARG, "tqs_add_gate: circuit is NULL");
+  Gate g{};
+  tqs_status s = check_gate(c->n, gate, qubits, nq, params, np, g);
+  if (s != TQS_OK) return s;
+  // ASAP step: after the last step touching any of the gate's qubits.
+  int step = 0;
+  for (int i = 0; i < g.nq; ++i) step = std::max(step, c->last[g.q[i]] + 1);
+  g.step = step;
+  for (int i = 0; i < g.nq; ++i) c->last[g.q[i]] = step;
+  c->nsteps = std::max(c->nsteps, step + 1);
+  c->gates.push_back(g);
+  c->prog_valid = false;
+  c->steps_valid = false;
+  return TQS_OK;
+}
+
+tqs_status tqs_circuit_info(const tqs_circuit* c, int* n_qubits, int* n_gates, int* n_steps) {
+  if (!c) return fail(TQS_ERR_ARG, "tqs_circuit_info: circuit is NULL");
+  if (n_qubits) *n_qubits = c->n;
+  if (n_gates) *n_gates = static_cast<int>(c->gates.size());
+  if (n_steps) *n_steps = c->nsteps;
+  return TQS_OK;
+}
+
+tqs_status tqs_circuit_steps(const tqs_circuit* c, int* h_step_of_gate) {
+  if (!c || !h_step_of_gate) return fail(TQS_ERR_ARG, "tqs_circuit_steps: NULL argument");
+  for (size_t i = 0; i < c->gates.size(); ++i) h_step_of_gate[i] = c->gates[i].step;
+  return TQS_OK;
+}
+
+}  // extern "C"
+
+// Gates in step order (stable within a step).
+static std::vector<const Gate*> step_order(const std::vector<Gate>& gates) {
+  std::vector<const Gate*> v;
+  v.reserve(gates.size());
+  for (const Gate& g : gates) v.push_back(&g);
+  std::stable_sort(v.begin(), v.end(), [](const Gate* a, const Gate* b) { return a->step < b->step; });
+  return v;
+}
+
+static void ensure_program(tqs_circuit* c) {
+  if (c->prog_valid) return;
+  c->prog = Program();
+  compile_program(c->n, step_order(c->gates), c->prog);
+  c->prog_valid = true;
+}
+
+static bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
+extern "C" tqs_status tqs_circuit_program(tqs_circuit* c, int* n_passes, int* n_ops, void* h_passes,
+                                          void* h_ops, uint8_t* h_pos) {
+  if (!c) return fail(TQS_ERR_ARG, "tqs_circuit_program: circuit is NULL");
+  ensure_program(c);
+  if (n_passes) *n_passes = static_cast<int>(c->prog.passes.size());
+  if (n_ops) *n_ops = static_cast<int>(c->prog.ops.size());
+  if (h_passes) std::memcpy(h_passes, c->prog.passes.data(), c->prog.passes.size() * sizeof(FusedPass));
+  if (h_ops) std::memcpy(h_ops, c->prog.ops.data(), c->prog.ops.size() * sizeof(FusedOp));
+  if (h_pos) std::memcpy(h_pos, c->prog.pos, 16);
+  return TQS_OK;
+}
+
+
+// Device image of one or more programs: [FusedCirc x count][FusedPass...][FusedOp...]
+struct Image {
+  std::vector<FusedCirc> circs;
+  std::vector<FusedPass> passes;
+  std::vector<FusedOp> ops;
+  size_t circ_bytes() const { return circs.size() * sizeof(FusedCirc); }
+  size_t pass_bytes() const { return passes.size() * sizeof(FusedPass); }
+  size_t op_bytes() const { return ops.size() * sizeof(FusedOp); }
+  size_t bytes() const { return circ_bytes() + pass_bytes() + op_bytes(); }
+  void add(const Program& P, int64_t out_off) {
+    FusedCirc fc{};
+    fc.n = P.n;
+    fc.nint = P.nint;
+    fc.pass_begin = static_cast<int32_t>(passes.size());
+    fc.pass_count = static_cast<int32_t>(P.passes.size());
+    fc.out_off = out_off;
+    fc.team = team_for(P.nint);
+    fc.identity = P.identity;
+    std::memcpy(fc.pos, P.pos, 16);
+    fc.init = nullptr;
+    const uint32_t op_base = static_cast<uint32_t>(ops.size());
+    for (FusedPass ps : P.passes) {
+      ps.op_begin += op_base;
+      passes.push_back(ps);
+    }
+    ops.insert(ops.end(), P.ops.begin(), P.ops.end());
+    circs.push_back(fc);
+  }
+  cudaError_t upload(void* dst, cudaStream_t s) const {
+    char* d = static_cast<char*>(dst);
+    cudaError_t e = cudaMemcpyAsync(d, circs.data(), circ_bytes(), cudaMemcpyHostToDevice, s);
+    if (e != cudaSuccess) return e;
+    if (!passes.empty())
+      e = cudaMemcpyAsync(d + circ_bytes(), passes.data(), pass_bytes(), cudaMemcpyHostToDevice, s);
+    if (e != cudaSuccess) return e;
+    if (!ops.empty())
+      e = cudaMemcpyAsync(d + circ_bytes() + pass_bytes(), ops.data(), op_bytes(),
+                          cudaMemcpyHostToDevice, s);
+    return e;
+  }
+};
+
+// Everything after the C-ABI entry points below shares these launch helpers.
+struct LaunchPlan {
+  int team;
+  int warps;
+  int slice_q;
+  int grid;
+};
+
+static LaunchPlan plan_for(int team, int max_nint, int jobs, int warps_hint) {
+  LaunchPlan lp{team, 1, 4, 1};
+  if (team == TEAM_WARP) {
+    lp.slice_q = std::max(4, max_nint);
+    int w = warps_hint > 0 ? warps_hint : 4;
+    const size_t slice = (size_t(1) << lp.slice_q) * sizeof(float2);
+    while (w > 1 && size_t(w) * slice > 200 * 1024) w >>= 1;
+    lp.warps = w;
+    const int per_sm = std::max(1, fused_max_ctas_per_sm(TEAM_WARP, w, lp.slice_q));
+    const int want = (jobs + w - 1) / w;
+    lp.grid = std::max(1, std::min(want, per_sm * device_sms()));
+  } else if (team == TEAM_CTA) {
+    lp.slice_q = std::max(4, max_nint);
+    const int per_sm = std::max(1, fused_max_ctas_per_sm(TEAM_CTA, 1, lp.slice_q));
+    lp.grid = std::max(1, std::min(jobs, per_sm * device_sms()));
+  } else {
+    lp.slice_q = kGlobalSlotQ;
+    lp.grid = std::max(1, std::min(jobs, device_sms()));
+  }
+  return lp;
+}
+
+extern "C" {
+
+tqs_status tqs_simulate(tqs_circuit* c, const tqs_c64* d_init, tqs_c64* d_out, double* d_probs,
+                        double* d_norm, void* stream) {
+  if (!c || !d_out) return fail(TQS_ERR_ARG, "tqs_simulate: NULL circuit or output");
+  if (!aligned16(d_out) || (d_probs && !aligned16(d_probs)) || (d_init && !aligned16(d_init)))
+    return fail(TQS_ERR_ARG, "tqs_simulate: device buffers must be 16-byte aligned");
+  if (d_init && reinterpret_cast<const void*>(d_init) == reinterpret_cast<const void*>(d_out))
+    return fail(TQS_ERR_ARG, "tqs_simulate: d_init must not alias d_out");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  ensure_program(c);
+  const Program& P = c->prog;
+  const int team = team_for(P.nint);
+  Image img;
+  img.add(P, 0);
+  img.circs[0].init = reinterpret_cast<const float2*>(d_init);
+  const size_t order_off = (img.bytes() + 255) & ~size_t(255);
+  TQS_CUDA(c->d_prog.ensure(order_off + 256), "tqs_simulate: cudaMalloc program");
+  TQS_CUDA(img.upload(c->d_prog.p, s), "tqs_simulate: upload program");
+  TQS_CUDA(c->d_counter.ensure(2 * sizeof(int32_t)), "tqs_simulate: cudaMalloc counter");
+  // order[0] = 0 lives right after the image; counter is zeroed per launch
+  static const int32_t zero_order[1] = {0};
+  char* base = c->d_prog.as<char>();
+  TQS_CUDA(cudaMemcpyAsync(base + order_off, zero_order, sizeof(int32_t), cudaMemcpyHostToDevice, s),
+           "tqs_simulate: upload order");
+  TQS_CUDA(cudaMemsetAsync(c->d_counter.p, 0, sizeof(int32_t), s), "tqs_simulate: memset");
+  FusedLaunch L{};
+  L.circs = reinterpret_cast<const FusedCirc*>(base);
+  L.passes = reinterpret_cast<const FusedPass*>(base + img.circ_bytes());
+  L.ops = reinterpret_cast<const FusedOp*>(base + img.circ_bytes() + img.pass_bytes());
+  L.order = reinterpret_cast<const int32_t*>(base + order_off);
+  L.n_jobs = 1;
+  L.counter = c->d_counter.as<int32_t>();
+  L.out = reinterpret_cast<float2*>(d_out);
+  L.probs = d_probs;
+  L.norms = d_norm;
+  LaunchPlan lp = plan_for(team, P.nint, 1, 1);
+  if (team == TEAM_GLOBAL) {
+    TQS_CUDA(c->d_gscratch.ensure((size_t(1) << kGlobalSlotQ) * sizeof(float2)),
+             "tqs_simulate: cudaMalloc scratch");
+    L.gscratch = c->d_gscratch.as<float2>();
+  }
+  L.team = lp.team;
+  L.warps_per_cta = lp.warps;
+  L.slice_q = lp.slice_q;
+  L.grid = 1;
+  TQS_CUDA(launch_fused(L, s), "tqs_simulate: launch");
+  return TQS_OK;
+}
+
+}  // extern "C"
+
+// ------------------------------------------------------ plain step table
+
+static void ensure_steps(tqs_circuit* c) {
+  if (c->steps_valid) return;
+  c->factors.clear();
+  c->steps.assign(c->nsteps, StepDesc{0, 0, 0, 0});
+  const uint32_t all = (1u << c->n) - 1u;
+  std::vector<std::vector<const Gate*>> by_step(c->nsteps);
+  for (const Gate& g : c->gates) by_step[g.step].push_back(&g);
+  for (int k = 0; k < c->nsteps; ++k) {
+    StepDesc d{static_cast<int32_t>(c->factors.size()), 0, all, 0};
+    for (const Gate* g : by_step[k]) {
+      StepFactor f{};
+      if (!is_two_qubit(g->kind)) {
+        f.nq = 1;
+        f.q0 = f.q1 = static_cast<uint8_t>(g->q[0]);
+        for (int i = 0; i < 4; ++i) f.m[i] = to_f2(g->u.m[i]);
+        d.idle &= ~(1u << g->q[0]);
+      } else {
+        f.nq = 2;
+        f.q0 = static_cast<uint8_t>(g->q[0]);
+        f.q1 = static_cast<uint8_t>(g->q[1]);
+        cd M[16] = {};
+        if (g->kind == TQS_SWAP) {
+          // |a b> -> |b a> in the (q0, q1) labelling
+          M[0 * 4 + 0] = 1.0;
+          M[1 * 4 + 2] = 1.0;
+          M[2 * 4 + 1] = 1.0;
+          M[3 * 4 + 3] = 1.0;
+        } else {
+          // eq. 7: diag(I, U) with the control first
+          M[0 * 4 + 0] = 1.0;
+          M[1 * 4 + 1] = 1.0;
+          M[2 * 4 + 2] = g->u.m[0];
+          M[2 * 4 + 3] = g->u.m[1];
+          M[3 * 4 + 2] = g->u.m[2];
+          M[3 * 4 + 3] = g->u.m[3];
+        }
+        for (int i = 0; i < 16; ++i) f.m[i] = to_f2(M[i]);
+        d.idle &= ~((1u << g->q[0]) | (1u << g->q[1]));
+      }
+      c->factors.push_back(f);
+      ++d.f_count;
+    }
+    c->steps[k] = d;
+  }
+  c->steps_valid = true;
+}
+
+static tqs_status upload_factors(tqs_circuit* c, cudaStream_t s) {
+  ensure_steps(c);
+  const size_t bytes = std::max<size_t>(c->factors.size(), 1) * sizeof(StepFactor);
+  TQS_CUDA(c->d_factors.ensure(bytes), "cudaMalloc step table");
+  if (!c->factors.empty())
+    TQS_CUDA(cudaMemcpyAsync(c->d_factors.p, c->factors.data(), c->factors.size() * sizeof(StepFactor),
+                             cudaMemcpyHostToDevice, s),
+             "upload step table");
+  return TQS_OK;
+}
+
+extern "C" {
+
+tqs_status tqs_materialize_step(tqs_circuit* c, int step, tqs_c64* d_S, void* stream) {
+  if (!c || !d_S) return fail(TQS_ERR_ARG, "tqs_materialize_step: NULL argument");
+  if (c->n > TQS_MAX_DENSE_QUBITS)
+    return fail(TQS_ERR_TOO_MANY_QUBITS, "tqs_materialize_step: n %d > %d", c->n,
+                TQS_MAX_DENSE_QUBITS);
+  if (step < 0 || step >= c->nsteps)
+    return fail(TQS_ERR_ARG, "tqs_materialize_step: step %d outside [0, %d)", step, c->nsteps);
+  if (!aligned16(d_S)) return fail(TQS_ERR_ARG, "tqs_materialize_step: d_S must be 16-byte aligned");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  tqs_status st = upload_factors(c, s);
+  if (st != TQS_OK) return st;
+  TQS_CUDA(launch_materialize(c->d_factors.as<StepFactor>(), c->steps[step], c->n,
+                              reinterpret_cast<float2*>(d_S), s),
+           "tqs_materialize_step: launch");
+  return TQS_OK;
+}
+
+tqs_status tqs_simulate_plain(tqs_circuit* c, const tqs_c64* d_init, tqs_c64* d_out, void* stream) {
+  if (!c || !d_out) return fail(TQS_ERR_ARG, "tqs_simulate_plain: NULL argument");
+  if (c->n > TQS_MAX_DENSE_QUBITS)
+    return fail(TQS_ERR_TOO_MANY_QUBITS, "tqs_simulate_plain: n %d > %d", c->n,
+                TQS_MAX_DENSE_QUBITS);
+  if (!aligned16(d_out) || (d_init && !aligned16(d_init)))
+    return fail(TQS_ERR_ARG, "tqs_simulate_plain: device buffers must be 16-byte aligned");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  tqs_status st = upload_factors(c, s);
+  if (st != TQS_OK) return st;
+  const size_t N = size_t(1) << c->n;
+  const size_t sbytes = N * N * sizeof(float2);
+  TQS_CUDA(c->d_plain.ensure(sbytes + 2 * N * sizeof(float2)), "tqs_simulate_plain: cudaMalloc");
+  float2* S = c->d_plain.as<float2>();
+  float2* x = reinterpret_cast<float2*>(reinterpret_cast<char*>(c->d_plain.p) + sbytes);
+  float2* y = x + N;
+  if (d_init) {
+    TQS_CUDA(cudaMemcpyAsync(x, d_init, N * sizeof(float2), cudaMemcpyDeviceToDevice, s), "copy init");
+  } else {
+    TQS_CUDA(cudaMemsetAsync(x, 0, N * sizeof(float2), s), "memset init");
+    const float2 one = make_float2(1.f, 0.f);
+    TQS_CUDA(cudaMemcpyAsync(x, &one, sizeof(float2), cudaMemcpyHostToDevice, s), "init |0>");
+  }
+  for (int k = 0; k < c->nsteps; ++k) {
+    TQS_CUDA(launch_materialize(c->d_factors.as<StepFactor>(), c->steps[k], c->n, S, s),
+             "tqs_simulate_plain: materialize");
+    TQS_CUDA(launch_matvec(S, x, y, c->n, s), "tqs_simulate_plain: matvec");
+    std::swap(x, y);
+  }
+  TQS_CUDA(cudaMemcpyAsync(d_out, x, N * sizeof(float2), cudaMemcpyDeviceToDevice, s), "copy out");
+  return TQS_OK;
+}
+
+// ------------------------------------------------------------ probabilities
+
+// Scratch for the partial sums: one per circuit-less call site, kept per thread.
+static DevBuf& probs_scratch() {
+  static thread_local DevBuf buf;
+  return buf;
+}
+
+static tqs_status probs_common(const tqs_c64* d_state, int n, double* d_probs, uint64_t mask,
+                               double* d_sum, cudaStream_t s, const char* who) {
+  if (!d_state) return fail(TQS_ERR_ARG, "%s: d_state is NULL", who);
+  if (n < 1 || n > 30) return fail(TQS_ERR_TOO_MANY_QUBITS, "%s: n %d outside [1, 30]", who, n);
+  if (!aligned16(d_state) || (d_probs && !aligned16(d_probs)))
+    return fail(TQS_ERR_ARG, "%s: device buffers must be 16-byte aligned", who);
+  const int parts = probs_partial_count(n);
+  DevBuf& buf = probs_scratch();
+  TQS_CUDA(buf.ensure(size_t(parts) * sizeof(double)), "probabilities: cudaMalloc partials");
+  TQS_CUDA(launch_probs(reinterpret_cast<const float2*>(d_state), n, d_probs, mask,
+                        buf.as<double>(), parts, d_sum, s),
+           "probabilities: launch");
+  return TQS_OK;
+}
+
+tqs_status tqs_probabilities(const tqs_c64* d_state, int n, double* d_probs, double* d_sum,
+                             void* stream) {
+  return probs_common(d_state, n, d_probs, 0, d_sum, static_cast<cudaStream_t>(stream),
+                      "tqs_probabilities");
+}
+
+tqs_status tqs_marginal_zero(const tqs_c64* d_state, int n, uint64_t mask, double* d_out,
+                             void* stream) {
+  if (!d_out) return fail(TQS_ERR_ARG, "tqs_marginal_zero: d_out is NULL");
+  if (n >= 1 && n <= 30 && (mask >> n) != 0)
+    return fail(TQS_ERR_QUBIT_RANGE, "tqs_marginal_zero: mask names qubits >= n");
+  return probs_common(d_state, n, nullptr, mask, d_out, static_cast<cudaStream_t>(stream),
+                      "tqs_marginal_zero");
+}
+
+}  // extern "C"
+
+// ------------------------------------------------------------------ batch
+
+struct tqs_batch {
+  int count = 0;
+  int64_t total_steps = 0;
+  std::vector<int64_t> offsets;  // count + 1
+  Image img;
+  std::vector<int32_t> order;    // [warp jobs][cta jobs][global jobs]
+  int n_team[3] = {0, 0, 0};
+  int max_nint[3] = {4, 4, 4};
+  DevBuf d_img;                  // image + order + counters
+  size_t order_off = 0, counter_off = 0;
+  bool uploaded = false;
+  DevBuf d_gscratch;
+  LaunchPlan plans[3];
+  // graph cache
+  cudaStream_t cap_stream = nullptr;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  void* g_states = nullptr;
+  void* g_probs = nullptr;
+  void* g_norms = nullptr;
+  int graph_kernels = 0;
+  // host-run buffers
+  DevBuf h_states, h_probs, h_norms;
+  ~tqs_batch() {
+    if (exec) cudaGraphExecDestroy(exec);
+    if (graph) cudaGraphDestroy(graph);
+    if (cap_stream) cudaStreamDestroy(cap_stream);
+  }
+};
+
+static tqs_status batch_finish(tqs_batch* b, std::vector<Program>& progs) {
+  b->count = static_cast<int>(progs.size());
+  b->offsets.assign(b->count + 1, 0);
+  for (int i = 0; i < b->count; ++i) b->offsets[i + 1] = b->offsets[i] + (int64_t(1) << progs[i].n);
+  std::vector<int> idx[3];
+  for (int i = 0; i < b->count; ++i) {
+    b->img.add(progs[i], b->offsets[i]);
+    const int t = team_for(progs[i].nint);
+    idx[t].push_back(i);
+    b->max_nint[t] = std::max(b->max_nint[t], progs[i].nint);
+  }
+  for (int t = 0; t < 3; ++t) {
+    std::stable_sort(idx[t].begin(), idx[t].end(),
+                     [&](int a, int c) { return progs[a].cost > progs[c].cost; });
+    b->n_team[t] = static_cast<int>(idx[t].size());
+    b->order.insert(b->order.end(), idx[t].begin(), idx[t].end());
+  }
+  return TQS_OK;
+}
+
+extern "C" {
+
+tqs_status tqs_batch_create(tqs_circuit* const* cs, int count, tqs_batch** out) {
+  if (!out || !cs || count < 1) return fail(TQS_ERR_ARG, "tqs_batch_create: bad arguments");
+  *out = nullptr;
+  std::unique_ptr<tqs_batch> b(new (std::nothrow) tqs_batch());
+  if (!b) return fail(TQS_ERR_NOMEM, "tqs_batch_create: out of host memory");
+  std::vector<Program> progs(count);
+  for (int i = 0; i < count; ++i) {
+    if (!cs[i]) return fail(TQS_ERR_ARG, "tqs_batch_create: circuit %d is NULL", i);
+    compile_program(cs[i]->n, step_order(cs[i]->gates), progs[i]);
+    b->total_steps += cs[i]->nsteps;
+  }
+  tqs_status s = batch_finish(b.get(), progs);
+  if (s != TQS_OK) return s;
+  *out = b.release();
+  return TQS_OK;
+}
+
+tqs_status tqs_batch_create_packed(int count, const int32_t* h_nq, const int64_t* h_gate_off,
+                                   const int32_t* h_kind, const int32_t* h_qubits,
+                                   const double* h_params, tqs_batch** out) {
+  if (!out || count < 1 || !h_nq || !h_gate_off || !h_kind || !h_qubits || !h_params)
+    return fail(TQS_ERR_ARG, "tqs_batch_create_packed: bad arguments");
+  *out = nullptr;
+  std::unique_ptr<tqs_batch> b(new (std::nothrow) tqs_batch());
+  if (!b) return fail(TQS_ERR_NOMEM, "tqs_batch_create_packed: out of host memory");
+  std::vector<Program> progs(count);
+  std::vector<Gate> gates;
+  std::vector<int> last;
+  std::vector<const Gate*> order;
+  for (int i = 0; i < count; ++i) {
+    const int n = h_nq[i];
+    if (n < 1 || n > TQS_MAX_QUBITS)
+      return fail(TQS_ERR_TOO_MANY_QUBITS, "circuit %d: n %d outside [1, %d]", i, n, TQS_MAX_QUBITS);
+    const int64_t g0 = h_gate_off[i], g1 = h_gate_off[i + 1];
+    if (g1 < g0) return fail(TQS_ERR_ARG, "circuit %d: gate offsets decrease", i);
+    gates.assign(static_cast<size_t>(g1 - g0), Gate{});
+    last.assign(n, -1);
+    for (int64_t k = g0; k < g1; ++k) {
+      const int kind = h_kind[k];
+      const int nq = (kind >= 0 && kind < TQS_GATE_COUNT && is_two_qubit(kind)) ? 2 : 1;
+      Gate& g = gates[static_cast<size_t>(k - g0)];
+      tqs_status s = check_gate(n, kind, h_qubits + 2 * k, nq, h_params + 8 * k, 8, g);
+      if (s != TQS_OK) return s;
+      int step = 0;
+      for (int j = 0; j < g.nq; ++j) step = std::max(step, last[g.q[j]] + 1);
+      g.step = step;
+      for (int j = 0; j < g.nq; ++j) last[g.q[j]] = step;
+    }
+    int nsteps = 0;
+    for (int q = 0; q < n; ++q) nsteps = std::max(nsteps, last[q] + 1);
+    b->total_steps += nsteps;
+    compile_program(n, step_order(gates), progs[i]);
+  }
+  tqs_status s = batch_finish(b.get(), progs);
+  if (s != TQS_OK) return s;
+  *out = b.release();
+  return TQS_OK;
+}
+
+tqs_status tqs_batch_info(const tqs_batch* b, int* count, int64_t* total_amps, int64_t* total_steps,
+                          int64_t* program_bytes, int64_t* h_offsets) {
+  if (!b) return fail(TQS_ERR_ARG, "tqs_batch_info: batch is NULL");
+  if (count) *count = b->count;
+  if (total_amps) *total_amps = b->offsets.back();
+  if (total_steps) *total_steps = b->total_steps;
+  if (program_bytes)
+    *program_bytes = static_cast<int64_t>(b->img.bytes() + b->order.size() * sizeof(int32_t));
+  if (h_offsets) std::memcpy(h_offsets, b->offsets.data(), b->offsets.size() * sizeof(int64_t));
+  return TQS_OK;
+}
+
+}  // extern "C"
+
+static tqs_status batch_upload(tqs_batch* b, cudaStream_t s) {
+  b->order_off = (b->img.bytes() + 255) & ~size_t(255);
+  b->counter_off = (b->order_off + b->order.size() * sizeof(int32_t) + 255) & ~size_t(255);
+  TQS_CUDA(b->d_img.ensure(b->counter_off + 256), "tqs_batch: cudaMalloc program");
+  TQS_CUDA(b->img.upload(b->d_img.p, s), "tqs_batch: upload program");
+  TQS_CUDA(cudaMemcpyAsync(b->d_img.as<char>() + b->order_off, b->order.data(),
+                           b->order.size() * sizeof(int32_t), cudaMemcpyHostToDevice, s),
+           "tqs_batch: upload order");
+  for (int t = 0; t < 3; ++t)
+    b->plans[t] = plan_for(t, b->max_nint[t], b->n_team[t], 4);
+  if (b->n_team[TEAM_GLOBAL] > 0)
+    TQS_CUDA(b->d_gscratch.ensure(size_t(b->plans[TEAM_GLOBAL].grid) *
+                                  (size_t(1) << kGlobalSlotQ) * sizeof(float2)),
+             "tqs_batch: cudaMalloc scratch");
+  b->uploaded = true;
+  return TQS_OK;
+}
+
+// Enqueue the batch's kernels (memset of the job counters + one launch per
+// team kind present).  Returns the number of kernels launched.
+static tqs_status batch_enqueue(tqs_batch* b, float2* states, double* probs, double* norms,
+                                cudaStream_t s, int* kernels) {
+  char* base = b->d_img.as<char>();
+  int32_t* counters = reinterpret_cast<int32_t*>(base + b->counter_off);
+  TQS_CUDA(cudaMemsetAsync(counters, 0, 3 * sizeof(int32_t), s), "tqs_batch: memset counters");
+  int k = 0;
+  int first = 0;
+  for (int t = 0; t < 3; ++t) {
+    if (b->n_team[t] == 0) continue;
+    FusedLaunch L{};
+    L.circs = reinterpret_cast<const FusedCirc*>(base);
+    L.passes = reinterpret_cast<const FusedPass*>(base + b->img.circ_bytes());
+    L.ops = reinterpret_cast<const FusedOp*>(base + b->img.circ_bytes() + b->img.pass_bytes());
+    L.order = reinterpret_cast<const int32_t*>(base + b->order_off) + first;
+    L.n_jobs = b->n_team[t];
+    L.counter = counters + t;
+    L.out = states;
+    L.probs = probs;
+    L.norms = norms;
+    L.gscratch = b->d_gscratch.as<float2>();
+    L.team = t;
+    L.warps_per_cta = b->plans[t].warps;
+    L.slice_q = b->plans[t].slice_q;
+    L.grid = b->plans[t].grid;
+    TQS_CUDA(launch_fused(L, s), "tqs_batch: launch");
+    first += b->n_team[t];
+    ++k;
+  }
+  if (kernels) *kernels = k;
+  return TQS_OK;
+}
+
+extern "C" {
+
+tqs_status tqs_batch_run(tqs_batch* b, tqs_c64* d_states, double* d_probs, double* d_norms,
+                         int use_graph, void* stream) {
+  if (!b || !d_states) return fail(TQS_ERR_ARG, "tqs_batch_run: NULL batch or states");
+  if (!aligned16(d_states) || (d_probs && !aligned16(d_probs)))
+    return fail(TQS_ERR_ARG, "tqs_batch_run: device buffers must be 16-byte aligned");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if (!b->uploaded) {
+    tqs_status st = batch_upload(b, s);
+    if (st != TQS_OK) return st;
+  }
+  float2* states = reinterpret_cast<float2*>(d_states);
+  if (!use_graph) return batch_enqueue(b, states, d_probs, d_norms, s, nullptr);
+  if (!b->exec || b->g_states != d_states || b->g_probs != d_probs || b->g_norms != d_norms) {
+    if (b->exec) { cudaGraphExecDestroy(b->exec); b->exec = nullptr; }
+    if (b->graph) { cudaGraphDestroy(b->graph); b->graph = nullptr; }
+    if (!b->cap_stream)
+      TQS_CUDA(cudaStreamCreateWithFlags(&b->cap_stream, cudaStreamNonBlocking), "tqs_batch: stream");
+    // the upload must be complete before the captured work can run on another stream
+    TQS_CUDA(cudaStreamSynchronize(s), "tqs_batch: sync before capture");
+    TQS_CUDA(cudaStreamBeginCapture(b->cap_stream, cudaStreamCaptureModeThreadLocal),
+             "tqs_batch: begin capture");
+    const int64_t before = tqs_launch_count();
+    int kernels = 0;
+    tqs_status st = batch_enqueue(b, states, d_probs, d_norms, b->cap_stream, &kernels);
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaStreamEndCapture(b->cap_stream, &g);
+    count_launches(before - tqs_launch_count());  // captured launches did not run yet
+    if (st != TQS_OK) { if (g) cudaGraphDestroy(g); return st; }
+    if (e != cudaSuccess) return cuda_fail(e, "tqs_batch: end capture");
+    b->graph = g;
+    TQS_CUDA(cudaGraphInstantiate(&b->exec, g, 0), "tqs_batch: instantiate");
+    b->g_states = d_states;
+    b->g_probs = d_probs;
+    b->g_norms = d_norms;
+    b->graph_kernels = kernels;
+  }
+  TQS_CUDA(cudaGraphLaunch(b->exec, s), "tqs_batch: graph launch");
+  count_launches(b->graph_kernels);
+  return TQS_OK;
+}
+
+tqs_status tqs_batch_run_host(tqs_batch* b, tqs_c64* h_states, double* h_probs, double* h_norms,
+                              void* stream) {
+  if (!b) return fail(TQS_ERR_ARG, "tqs_batch_run_host: batch is NULL");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  tqs_status st = batch_upload(b, s);  // the program is this call's input
+  if (st != TQS_OK) return st;
+  const size_t amps = static_cast<size_t>(b->offsets.back());
+  TQS_CUDA(b->h_states.ensure(amps * sizeof(float2)), "tqs_batch_run_host: cudaMalloc states");
+  if (h_probs) TQS_CUDA(b->h_probs.ensure(amps * sizeof(double)), "tqs_batch_run_host: cudaMalloc probs");
+  TQS_CUDA(b->h_norms.ensure(size_t(b->count) * sizeof(double)), "tqs_batch_run_host: cudaMalloc norms");
+  float2* ds = b->h_states.as<float2>();
+  double* dp = h_probs ? b->h_probs.as<double>() : nullptr;
+  double* dn = b->h_norms.as<double>();
+  st = batch_enqueue(b, ds, dp, dn, s, nullptr);
+  if (st != TQS_OK) return st;
+  if (h_states)
+    TQS_CUDA(cudaMemcpyAsync(h_states, ds, amps * sizeof(float2), cudaMemcpyDeviceToHost, s), "D2H states");
+  if (h_probs)
+    TQS_CUDA(cudaMemcpyAsync(h_probs, dp, amps * sizeof(double), cudaMemcpyDeviceToHost, s), "D2H probs");
+  if (h_norms)
+    TQS_CUDA(cudaMemcpyAsync(h_norms, dn, size_t(b->count) * sizeof(double), cudaMemcpyDeviceToHost, s),
+             "D2H norms");
+  TQS_CUDA(cudaStreamSynchronize(s), "tqs_batch_run_host: sync");
+  return TQS_OK;
+}
+
+tqs_status tqs_batch_destroy(tqs_batch* b) {
+  delete b;
+  return TQS_OK;
+}
+
+tqs_status tqs_circuit_unitary(tqs_circuit* c, int prec, tqs_c64* d_U, void* stream) {
+  (void)c; (void)prec; (void)d_U; (void)stream;
+  return fail(TQS_ERR_UNSUPPORTED, "tqs_circuit_unitary: not built yet");
+}
+
+}  // extern "C"

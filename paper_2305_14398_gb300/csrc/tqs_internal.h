@@ -1,0 +1,135 @@
+// Internal data layouts shared by the host compiler (tqs_host.cpp) and the
+// sm_103a kernels.  Not part of the public ABI.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace tqs {
+
+// ---------------------------------------------------------------------------
+// Fused step program.
+//
+// The host turns a circuit's steps (Algorithm 2: one Kronecker factor per gate,
+// identity elsewhere) into "passes".  A pass names 4 physical qubit bits that
+// are local to a thread: each thread owns the 16 amplitudes whose indices differ
+// only in those bits and applies, in registers, every factor of the pass whose
+// non-diagonal action stays inside them (eq. 12 butterflies; a controlled
+// factor's control may be any qubit).  Diagonal factors are phases and need no
+// locality.  SWAP factors are qubit relabelings done on the host.
+// ---------------------------------------------------------------------------
+
+enum OpKind : uint8_t {
+  OP_DENSE = 0,   // general 2x2 on the (local) target
+  OP_ANTI = 1,    // anti-diagonal [[0, m01], [m10, 0]] on the (local) target
+  OP_DIAG = 2     // diag(d0, d1) on the target, any locality
+};
+
+enum CtlKind : uint8_t {
+  CTL_NONE = 0,   // uncontrolled
+  CTL_LOCAL = 1,  // control is local position `c`
+  CTL_FAR = 2     // control is physical bit `c` outside the pass's local bits
+};
+
+struct alignas(16) FusedOp {
+  uint8_t kind;    // OpKind
+  uint8_t tloc;    // 1: target is local position `t`; 0: target is physical bit `t`
+  uint8_t t;
+  uint8_t ckind;   // CtlKind
+  uint8_t c;
+  uint8_t unit;    // OP_ANTI with m01 == m10 == 1 (X, CNOT)
+  uint8_t pad0[2];
+  float2 m[4];     // DENSE: m00 m01 m10 m11 | ANTI: -, m01, m10, - | DIAG: d0, d1, d1/d0, -
+  uint32_t pad1[2];
+};
+static_assert(sizeof(FusedOp) == 48, "FusedOp layout");
+
+struct alignas(16) FusedPass {
+  uint8_t L[4];        // physical bits of local positions 0..3, ascending
+  uint32_t op_begin;   // index into the op array
+  uint32_t op_count;
+  uint32_t pad;
+};
+static_assert(sizeof(FusedPass) == 16, "FusedPass layout");
+
+enum TeamKind : int32_t { TEAM_WARP = 0, TEAM_CTA = 1, TEAM_GLOBAL = 2 };
+
+struct alignas(16) FusedCirc {
+  int32_t n;            // logical qubits
+  int32_t nint;         // internal qubits = max(n, 4)
+  int32_t pass_begin;   // index into the pass array
+  int32_t pass_count;
+  int64_t out_off;      // amplitude offset of this circuit's outputs
+  int32_t team;         // TeamKind
+  int32_t identity;     // 1 if the output qubit map is the identity
+  uint8_t pos[16];      // physical bit of logical qubit q at the end
+  const float2* init;   // initial state (logical order) or nullptr for |0..0>
+  int64_t pad;
+};
+static_assert(sizeof(FusedCirc) == 64, "FusedCirc layout");
+
+// Team limits: a warp team holds up to 2^kWarpMaxQ amplitudes in its shared
+// memory slice; a CTA team up to 2^kCtaMaxQ in its CTA's shared memory; larger
+// states live in global scratch (L2-resident) and are worked by a CTA.
+constexpr int kWarpMaxQ = 11;
+constexpr int kCtaMaxQ = 14;
+constexpr int kCtaThreads = 256;
+constexpr int kGlobalThreads = 512;
+constexpr int kGlobalSlotQ = 16;   // log2 amplitudes per TEAM_GLOBAL scratch slot
+
+struct FusedLaunch {
+  const FusedCirc* circs;   // device
+  const FusedPass* passes;  // device
+  const FusedOp* ops;       // device
+  const int32_t* order;     // device: circuit indices of this team kind, costliest first
+  int32_t n_jobs;
+  int32_t* counter;         // device: job counter, zeroed before the launch
+  float2* out;              // device outputs (logical order)
+  double* probs;            // nullable
+  double* norms;            // nullable
+  float2* gscratch;         // TEAM_GLOBAL: per-CTA state slots (2^16 amplitudes each)
+  int32_t team;             // TeamKind of this launch
+  int32_t warps_per_cta;    // TEAM_WARP
+  int32_t slice_q;          // TEAM_WARP: log2 amplitudes per warp slice; TEAM_CTA: log2 per CTA
+  int32_t grid;             // CTAs
+};
+
+cudaError_t launch_fused(const FusedLaunch& L, cudaStream_t s);
+int fused_max_ctas_per_sm(int team, int warps_per_cta, int slice_q);
+
+// ---------------------------------------------------------------------------
+// Plain materialised form (stages 4 and 6 of Sec. 5.3).
+// ---------------------------------------------------------------------------
+
+struct StepFactor {
+  uint8_t nq;      // 1 or 2
+  uint8_t q0, q1;  // qubits (q0 = control for controlled gates)
+  uint8_t pad[5];
+  float2 m[16];    // nq = 1: 2x2 row-major in m[0..3]; nq = 2: 4x4 row-major,
+                   // local index (bit q0 << 1) | bit q1
+};
+static_assert(sizeof(StepFactor) == 136, "StepFactor layout");
+
+struct StepDesc {
+  int32_t f_begin;   // index into the factor array
+  int32_t f_count;
+  uint32_t idle;     // mask of qubits no factor touches (identity there)
+  int32_t pad;
+};
+
+cudaError_t launch_materialize(const StepFactor* d_factors, StepDesc step, int n, float2* d_S,
+                               cudaStream_t s);
+cudaError_t launch_matvec(const float2* d_S, const float2* d_x, float2* d_y, int n,
+                          cudaStream_t s);
+
+// ---------------------------------------------------------------------------
+// Probabilities / marginals (FP64).
+// ---------------------------------------------------------------------------
+int probs_partial_count(int n);
+cudaError_t launch_probs(const float2* d_state, int n, double* d_probs, uint64_t zero_mask,
+                         double* d_partials, int n_partials, double* d_sum, cudaStream_t s);
+
+// Process-wide count of kernel launches enqueued by this library.
+void count_launches(int64_t k);
+
+}  // namespace tqs

@@ -1,0 +1,217 @@
+"""Host logic of the CUDA path, checked on the CPU.
+
+The library compiles a circuit's steps into passes of 4 thread-local qubit
+bits (tqs_circuit_program).  This test replays that program in numpy with the
+kernel's semantics (butterflies on local bits, pending per-bit phases, far
+controls, SWAP relabeling, final qubit map) and compares the final state with
+the FP64 oracle.  It also checks the ASAP step table and the error codes.
+No GPU is needed: only host entry points are called.
+"""
+import numpy as np
+import pytest
+
+from oracle import fsv_route, kron_route
+from paper_2305_14398_gb300 import binding as B
+from paper_2305_14398_gb300 import workloads as W
+
+DENSE, ANTI, DIAG = 0, 1, 2
+NONE, LOCAL, FAR = 0, 1, 2
+
+
+def ins0(x, b):
+    return ((x >> b) << (b + 1)) | (x & ((1 << b) - 1))
+
+
+def replay(n, passes, ops, pos):
+    nint = max(n, 4)
+    st = np.zeros(1 << nint, dtype=np.complex128)
+    st[0] = 1.0
+    G = (1 << nint) >> 4
+    for ps in passes:
+        L = [int(v) for v in ps["L"]]
+        assert L == sorted(L) and len(set(L)) == 4 and max(L) < nint
+        g = np.arange(G, dtype=np.int64)
+        base = g
+        for l in L:
+            base = ins0(base, l)
+        offs = np.array([sum(((j >> k) & 1) << L[k] for k in range(4)) for j in range(16)])
+        idx = base[:, None] + offs[None, :]
+        a = st[idx].copy()
+        pend = np.ones((G, 4), dtype=np.complex128)
+        sc = np.ones(G, dtype=np.complex128)
+        b0, cnt = int(ps["op_begin"]), int(ps["op_count"])
+        for op in ops[b0:b0 + cnt]:
+            kind, tloc, t, ckind, c = (int(op[k]) for k in ("kind", "tloc", "t", "ckind", "c"))
+            m = op["m"].astype(np.complex128)
+            if kind == DIAG:
+                d0, d1, r = m[0], m[1], m[2]
+                if tloc:
+                    if ckind == LOCAL:
+                        for j in range(16):
+                            if (j >> c) & 1:
+                                a[:, j] *= d1 if (j >> t) & 1 else d0
+                    else:
+                        on = np.ones(G, bool) if ckind == NONE else ((base >> c) & 1) == 1
+                        sc[on] *= d0
+                        pend[on, t] *= r
+                else:
+                    v = np.where(((base >> t) & 1) == 1, d1, d0)
+                    if ckind == LOCAL:
+                        pend[:, c] *= v
+                    else:
+                        on = np.ones(G, bool) if ckind == NONE else ((base >> c) & 1) == 1
+                        sc[on] *= v[on]
+                continue
+            assert tloc == 1, "non-diagonal op with a far target"
+            if ckind == LOCAL:
+                assert c != t
+            on = np.ones(G, bool) if ckind != FAR else ((base >> c) & 1) == 1
+            for j in range(16):
+                if (j >> t) & 1:
+                    a[:, j] *= pend[:, t]
+            pend[:, t] = 1.0
+            for p in range(8):
+                j0 = ((p >> t) << (t + 1)) | (p & ((1 << t) - 1))
+                j1 = j0 | (1 << t)
+                if ckind == LOCAL and not (j0 >> c) & 1:
+                    continue
+                x0, x1 = a[:, j0].copy(), a[:, j1].copy()
+                if kind == DENSE:
+                    y0 = m[0] * x0 + m[1] * x1
+                    y1 = m[2] * x0 + m[3] * x1
+                elif op["unit"]:
+                    y0, y1 = x1, x0
+                else:
+                    y0, y1 = m[1] * x1, m[2] * x0
+                a[on, j0] = y0[on]
+                a[on, j1] = y1[on]
+        for b in range(4):
+            for j in range(16):
+                if (j >> b) & 1:
+                    a[:, j] *= pend[:, b]
+        a *= sc[:, None]
+        st[idx] = a
+    i = np.arange(1 << n, dtype=np.int64)
+    phys = np.zeros_like(i)
+    for q in range(n):
+        phys |= ((i >> q) & 1) << int(pos[q])
+    return st[phys]
+
+
+def compiled(n, ops):
+    c = B.circuit_from_ops(n, ops)
+    try:
+        return B.tqs_circuit_program(c)
+    finally:
+        B.tqs_circuit_destroy(c)
+
+
+CASES = [("bell", 2, W.bell())]
+CASES += [(f"ghz{n}", n, W.ghz_chain(n)) for n in (1, 3, 5, 11)]
+CASES += [(f"ghzfan{n}", n, W.ghz_fanout(n)) for n in (4, 9)]
+CASES += [(f"qft{n}", n, W.qft_on_basis(n, (5 * n + 3) % (1 << n))) for n in (1, 2, 3, 4, 5, 7, 10, 11)]
+CASES += [(f"dj{n}{b}", n, W.deutsch_jozsa(n, b, (5, n, int(b)))) for n in (3, 6, 11) for b in (False, True)]
+CASES += [(f"rand{n}_{k}", n, W.random_small(n, 8 * n, (6, n, k))) for n in (1, 2, 3, 4, 5, 6, 8) for k in range(3)]
+CASES += [(f"mixed{n}", n, W.random_mixed(n, 12, (7, n))) for n in (4, 7, 9, 12)]
+CASES += [(f"layered{n}", n, W.random_layered(n, 3, (8, n))) for n in (5, 10, 12)]
+
+
+@pytest.mark.parametrize("name,n,ops", CASES, ids=[c[0] for c in CASES])
+def test_program_replay_matches_oracle(name, n, ops):
+    passes, prog_ops, pos = compiled(n, ops)
+    got = replay(n, passes, prog_ops, pos)
+    want = fsv_route.simulate(n, ops)
+    # the program stores matrices in FP32; the replay computes in FP64
+    assert np.max(np.abs(got - want)) < 2e-6
+
+
+def test_steps_are_asap():
+    """Step table (Sec. 5.2 reading: as soon as possible) matches the oracle's packing."""
+    for n, ops in [(2, W.bell()), (6, W.qft(6)), (7, W.random_small(7, 40, (9, 1)))]:
+        c = B.circuit_from_ops(n, ops)
+        try:
+            steps = B.tqs_circuit_steps(c)
+            nn, ng, ns = B.tqs_circuit_info(c)
+        finally:
+            B.tqs_circuit_destroy(c)
+        ref = kron_route.steps_asap(n, ops)
+        assert ns == len(ref) and ng == len(ops) and nn == n
+        k = 0
+        want = {}
+        for si, st in enumerate(ref):
+            for op in st:
+                want.setdefault(id(op), si)
+        # the oracle keeps op objects; map by position in the input list
+        pos_of = {id(op): i for i, op in enumerate(ops)}
+        ref_steps = [0] * len(ops)
+        for si, st in enumerate(ref):
+            for op in st:
+                ref_steps[pos_of[id(op)]] = si
+        assert steps == ref_steps
+
+
+def test_ghz_steps_and_passes():
+    """GHZ chain on n qubits: n steps; the compiler needs ceil(n/4)+ passes."""
+    n = 11
+    c = B.circuit_from_ops(n, W.ghz_chain(n))
+    try:
+        assert B.tqs_circuit_info(c)[2] == n
+        passes, ops, pos = B.tqs_circuit_program(c)
+        assert len(ops) == n and len(passes) <= 4
+    finally:
+        B.tqs_circuit_destroy(c)
+
+
+@pytest.mark.parametrize("bad,status", [
+    (("h", (3,), ()), "TQS_ERR_QUBIT_RANGE"),
+    (("h", (-1,), ()), "TQS_ERR_QUBIT_RANGE"),
+    (("cx", (1, 1), ()), "TQS_ERR_QUBIT_DUP"),
+    (("cx", (1,), ()), "TQS_ERR_ARG"),
+    (("rx", (0,), ()), "TQS_ERR_ARG"),
+    (("cu", (0, 1), (1, 0, 0, 0, 0, 0, 2, 0)), "TQS_ERR_ARG"),
+    (("rz", (0,), (float("nan"),)), "TQS_ERR_ARG"),
+])
+def test_gate_preconditions(bad, status):
+    """Preconditions are checked when an operation is added (Sec. 5.2)."""
+    c = B.tqs_circuit_create(3)
+    try:
+        with pytest.raises(B.TqsError) as e:
+            B.tqs_add_gate(c, bad[0], bad[1], bad[2])
+        assert e.value.name == status
+        assert B.tqs_circuit_info(c)[1] == 0
+    finally:
+        B.tqs_circuit_destroy(c)
+
+
+def test_circuit_size_limits():
+    with pytest.raises(B.TqsError) as e:
+        B.tqs_circuit_create(17)
+    assert e.value.name == "TQS_ERR_TOO_MANY_QUBITS"
+    with pytest.raises(B.TqsError) as e:
+        B.tqs_circuit_create(0)
+    assert e.value.name == "TQS_ERR_ARG"
+
+
+def test_packed_batch_host_side():
+    """tqs_batch_create_packed checks preconditions and lays out outputs."""
+    circs = [(3, W.ghz_chain(3)), (5, W.qft(5)), (12, W.ghz_chain(12)), (15, W.ghz_chain(15))]
+    b = B.tqs_batch_create_packed(*B.pack_ops(circs))
+    try:
+        count, total, offs = B.tqs_batch_info(b)
+        assert count == 4 and total == 8 + 32 + 4096 + 32768
+        assert list(offs) == [0, 8, 40, 4136, 36904]
+    finally:
+        B.tqs_batch_destroy(b)
+    nq, off, kind, qub, par = B.pack_ops([(3, [("cx", (0, 3), ())])])
+    with pytest.raises(B.TqsError) as e:
+        B.tqs_batch_create_packed(nq, off, kind, qub, par)
+    assert e.value.name == "TQS_ERR_QUBIT_RANGE"
+
+
+def test_library_exports_every_declared_symbol():
+    """libtqs.so loads on the CPU and exports every function include/tqs.h declares."""
+    L = B.lib()
+    names = B.header_functions()
+    assert len(names) >= 20
+    missing = [n for n in names if not hasattr(L, n)]
+    assert not missing, missing
