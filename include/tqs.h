@@ -125,16 +125,20 @@ tqs_status tqs_circuit_steps(const tqs_circuit* c, int* h_step_of_gate);
  * ops applies one step factor to the amplitudes in registers.
  *   *n_passes, *n_ops : receive the sizes (may be NULL).
  *   h_passes : NULL or n_passes records of 16 bytes:
- *              {uint8 L[4]; uint32 op_begin; uint32 op_count; uint32 pad}
- *   h_ops    : NULL or n_ops records of 48 bytes:
- *              {uint8 kind (0 dense, 1 anti-diagonal, 2 diagonal), tloc, t,
- *               ckind (0 none, 1 local, 2 far), c, unit, pad[2];
- *               float m[8] (4 complex entries); uint32 pad[2]}
+ *              {uint8 L[4]; uint32 op_begin; uint32 op_count; float scale}
+ *              (scale: exact power of two applied at the end of the pass)
+ *   h_ops    : NULL or n_ops records of 80 bytes:
+ *              {uint8 kind (0 dense, 1 anti-diagonal, 2 diagonal,
+ *               3 Hadamard without its 2^-1/2), tloc, t,
+ *               ckind (0 none, 1 local, 2 far), c, unit, pad[2]; uint32 pad[2];
+ *               float m[8] (4 complex entries); float lo[8] (their FP32
+ *               rounding residues, dense ops)}
  *   h_pos    : NULL or 16 bytes, the physical bit of each logical qubit at
  *              the end (SWAP factors are relabelings).
+ *   h_out_scale : NULL or 1 float, the factor applied to the output state.
  * Host memory only; no device work. */
 tqs_status tqs_circuit_program(tqs_circuit* c, int* n_passes, int* n_ops, void* h_passes,
-                               void* h_ops, uint8_t* h_pos);
+                               void* h_ops, uint8_t* h_pos, float* h_out_scale);
 
 /* ---------------------------------------------------------------- simulate
  * simulateFullState (Sec. 5.2): the final state psi = S_m ... S_1 psi_0.

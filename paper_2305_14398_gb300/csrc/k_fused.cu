@@ -22,19 +22,6 @@ __device__ __forceinline__ float2 cmul(float2 a, float2 b) {
   return make_float2(fmaf(a.x, b.x, -a.y * b.y), fmaf(a.x, b.y, a.y * b.x));
 }
 
-// a * x + b * y
-__device__ __forceinline__ float2 cmac2(float2 a, float2 x, float2 b, float2 y) {
-  float re = a.x * x.x;
-  re = fmaf(-a.y, x.y, re);
-  re = fmaf(b.x, y.x, re);
-  re = fmaf(-b.y, y.y, re);
-  float im = a.x * x.y;
-  im = fmaf(a.y, x.x, im);
-  im = fmaf(b.x, y.y, im);
-  im = fmaf(b.y, y.x, im);
-  return make_float2(re, im);
-}
-
 // Shared-memory slot of amplitude i: XOR the low 4 bits with bits 4..7 so that
 // the 16-amplitude groups of a warp spread over the banks for any choice of
 // local bits.  A bijection on every aligned block of 256 amplitudes.
@@ -45,20 +32,60 @@ __device__ __forceinline__ int ins0(int x, int b) {
   return ((x >> b) << (b + 1)) | (x & ((1 << b) - 1));
 }
 
+// (ah + al) * x + (bh + bl) * y for coefficients split into FP32 hi + lo
+// parts: the small lo products first, then the hi products, so that the
+// coefficient rounding of a single FP32 matrix adds no bias to the norm.
+__device__ __forceinline__ float2 cmac2_hl(float2 ah, float2 al, float2 x, float2 bh, float2 bl,
+                                           float2 y) {
+  float re = al.x * x.x;
+  re = fmaf(-al.y, x.y, re);
+  re = fmaf(bl.x, y.x, re);
+  re = fmaf(-bl.y, y.y, re);
+  re = fmaf(ah.x, x.x, re);
+  re = fmaf(-ah.y, x.y, re);
+  re = fmaf(bh.x, y.x, re);
+  re = fmaf(-bh.y, y.y, re);
+  float im = al.x * x.y;
+  im = fmaf(al.y, x.x, im);
+  im = fmaf(bl.x, y.y, im);
+  im = fmaf(bl.y, y.x, im);
+  im = fmaf(ah.x, x.y, im);
+  im = fmaf(ah.y, x.x, im);
+  im = fmaf(bh.x, y.y, im);
+  im = fmaf(bh.y, y.x, im);
+  return make_float2(re, im);
+}
+
 // ------------------------------------------------------------ butterflies
 // T: local position of the target; C: local position of the control or -1.
 
+struct Coef {
+  float2 h[4], l[4];
+};
+
 template <int T, int C>
-__device__ __forceinline__ void dense_t(float2 (&a)[16], float2 m00, float2 m01, float2 m10,
-                                        float2 m11) {
+__device__ __forceinline__ void dense_t(float2 (&a)[16], const Coef& m) {
 #pragma unroll
   for (int p = 0; p < 8; ++p) {
     const int j0 = ((p >> T) << (T + 1)) | (p & ((1 << T) - 1));
     const int j1 = j0 | (1 << T);
     if (C >= 0 && !((j0 >> C) & 1)) continue;
     const float2 x0 = a[j0], x1 = a[j1];
-    a[j0] = cmac2(m00, x0, m01, x1);
-    a[j1] = cmac2(m10, x0, m11, x1);
+    a[j0] = cmac2_hl(m.h[0], m.l[0], x0, m.h[1], m.l[1], x1);
+    a[j1] = cmac2_hl(m.h[2], m.l[2], x0, m.h[3], m.l[3], x1);
+  }
+}
+
+// Hadamard butterfly without its 2^-1/2 (restored by the pass scale).
+template <int T>
+__device__ __forceinline__ void h_t(float2 (&a)[16]) {
+#pragma unroll
+  for (int p = 0; p < 8; ++p) {
+    const int j0 = ((p >> T) << (T + 1)) | (p & ((1 << T) - 1));
+    const int j1 = j0 | (1 << T);
+    const float2 x0 = a[j0], x1 = a[j1];
+    a[j0] = make_float2(x0.x + x1.x, x0.y + x1.y);
+    a[j1] = make_float2(x0.x - x1.x, x0.y - x1.y);
   }
 }
 
@@ -161,9 +188,10 @@ __device__ __forceinline__ float2 f2(unsigned x, unsigned y) {
   return make_float2(__uint_as_float(x), __uint_as_float(y));
 }
 
-// Apply the ops of one pass to the 16 amplitudes of one group.
+// Apply the ops of one pass to the 16 amplitudes of one group, then the
+// pass's exact power-of-two scale.
 __device__ __forceinline__ void run_ops(float2 (&a)[16], const FusedOp* __restrict__ ops,
-                                        uint32_t count, int base) {
+                                        uint32_t count, int base, float scale) {
   Pending pd;
   pd.p0 = pd.p1 = pd.p2 = pd.p3 = make_float2(1.f, 0.f);
   pd.dirty = 0;
@@ -172,16 +200,27 @@ __device__ __forceinline__ void run_ops(float2 (&a)[16], const FusedOp* __restri
   for (uint32_t k = 0; k < count; ++k) {
     const uint4* rec = reinterpret_cast<const uint4*>(ops + k);
     const uint4 q0 = __ldg(rec);
-    const uint4 q1 = __ldg(rec + 1);
     const int kind = q0.x & 0xff;
     const int tloc = (q0.x >> 8) & 0xff;
     const int t = (q0.x >> 16) & 0xff;
     const int ckind = q0.x >> 24;
     const int c = q0.y & 0xff;
     const int unit = (q0.y >> 8) & 0xff;
-    const float2 m0 = f2(q0.z, q0.w);
-    const float2 m1 = f2(q1.x, q1.y);
-    const float2 m2 = f2(q1.z, q1.w);
+    if (kind == OP_H) {
+      pend_flush(a, pd, t);
+      switch (t) {
+        case 0: h_t<0>(a); break;
+        case 1: h_t<1>(a); break;
+        case 2: h_t<2>(a); break;
+        default: h_t<3>(a); break;
+      }
+      continue;
+    }
+    const uint4 q1 = __ldg(rec + 1);
+    const uint4 q2 = __ldg(rec + 2);
+    const float2 m0 = f2(q1.x, q1.y);
+    const float2 m1 = f2(q1.z, q1.w);
+    const float2 m2 = f2(q2.x, q2.y);
     if (kind == OP_DIAG) {
       // d0 = m0, d1 = m1, ratio d1/d0 = m2
       if (tloc) {
@@ -208,9 +247,18 @@ __device__ __forceinline__ void run_ops(float2 (&a)[16], const FusedOp* __restri
     pend_flush(a, pd, t);
     const int sel = t * 5 + (ckind == CTL_LOCAL ? c : -1) + 1;
     if (kind == OP_DENSE) {
-      const uint4 q2 = __ldg(rec + 2);
-      const float2 m3 = f2(q2.x, q2.y);
-      TQS_DISPATCH_TC(dense_t, (a, m0, m1, m2, m3));
+      const uint4 q3 = __ldg(rec + 3);
+      const uint4 q4 = __ldg(rec + 4);
+      Coef m;
+      m.h[0] = m0;
+      m.h[1] = m1;
+      m.h[2] = m2;
+      m.h[3] = f2(q2.z, q2.w);
+      m.l[0] = f2(q3.x, q3.y);
+      m.l[1] = f2(q3.z, q3.w);
+      m.l[2] = f2(q4.x, q4.y);
+      m.l[3] = f2(q4.z, q4.w);
+      TQS_DISPATCH_TC(dense_t, (a, m));
     } else if (unit) {
       TQS_DISPATCH_TC(swap_t, (a));
     } else {
@@ -222,8 +270,13 @@ __device__ __forceinline__ void run_ops(float2 (&a)[16], const FusedOp* __restri
   pend_flush(a, pd, 2);
   pend_flush(a, pd, 3);
   if (sc_set) {
+    sc.x *= scale;  // exact: scale is a power of two
+    sc.y *= scale;
 #pragma unroll
     for (int j = 0; j < 16; ++j) a[j] = cmul(a[j], sc);
+  } else if (scale != 1.0f) {
+#pragma unroll
+    for (int j = 0; j < 16; ++j) a[j] = make_float2(a[j].x * scale, a[j].y * scale);
   }
 }
 
@@ -257,6 +310,7 @@ __device__ void run_circuit(const FusedLaunch& L, int ci, float2* st, int rank, 
               l3 = pr.x >> 24;
     const FusedOp* ops = L.ops + pr.y;
     const uint32_t count = pr.z;
+    const float scale = __uint_as_float(pr.w);
     const bool gen = (p == 0) && (init == nullptr);
     const int b0 = 1 << l0, b1 = 1 << l1, b2 = 1 << l2, b3 = 1 << l3;
     for (int g = rank; g < G; g += size) {
@@ -271,7 +325,7 @@ __device__ void run_circuit(const FusedLaunch& L, int ci, float2* st, int rank, 
         else
           a[j] = st[swz(off)];
       }
-      run_ops(a, ops, count, base);
+      run_ops(a, ops, count, base, scale);
 #pragma unroll
       for (int j = 0; j < 16; ++j) {
         const int off = base + ((j & 1) ? b0 : 0) + ((j & 2) ? b1 : 0) + ((j & 4) ? b2 : 0) +
@@ -288,6 +342,7 @@ __device__ void run_circuit(const FusedLaunch& L, int ci, float2* st, int rank, 
   const unsigned pw[4] = {posw.x, posw.y, posw.z, posw.w};
   float2* out = L.out + cd.out_off;
   double* probs = L.probs ? L.probs + cd.out_off : nullptr;
+  const float oscale = cd.out_scale;
   double acc = 0.0;
   for (int i = rank * 2; i < N; i += size * 2) {
     int p0 = i, p1 = i + 1;
@@ -303,8 +358,12 @@ __device__ void run_circuit(const FusedLaunch& L, int ci, float2* st, int rank, 
         }
       }
     }
-    const float2 v0 = st[swz(p0)];
-    const float2 v1 = st[swz(p1)];
+    float2 v0 = st[swz(p0)];
+    float2 v1 = st[swz(p1)];
+    if (oscale != 1.0f) {
+      v0 = make_float2(v0.x * oscale, v0.y * oscale);
+      v1 = make_float2(v1.x * oscale, v1.y * oscale);
+    }
     *reinterpret_cast<float4*>(out + i) = make_float4(v0.x, v0.y, v1.x, v1.y);
     // |psi|^2 in FP64: the squares of the FP32 parts are exact in FP64.
     const double x0 = v0.x, y0 = v0.y, x1 = v1.x, y1 = v1.y;

@@ -160,12 +160,25 @@ static inline float2 to_f2(cd z) {
 
 enum GClass { G_DENSE, G_ANTI, G_DIAG, G_SWAP };
 
-static GClass classify(const Gate& g) {
-  if (g.kind == TQS_SWAP) return G_SWAP;
-  const Mat2& u = g.u;
+static GClass classify_mat(const Mat2& u) {
   if (u.m[1] == cd(0.0) && u.m[2] == cd(0.0)) return G_DIAG;
   if (u.m[0] == cd(0.0) && u.m[3] == cd(0.0)) return G_ANTI;
   return G_DENSE;
+}
+
+static GClass classify(const Gate& g) {
+  if (g.kind == TQS_SWAP) return G_SWAP;
+  return classify_mat(g.u);
+}
+
+// a * b (apply b, then a)
+static Mat2 mat_mul(const Mat2& a, const Mat2& b) {
+  Mat2 r;
+  r.m[0] = a.m[0] * b.m[0] + a.m[1] * b.m[2];
+  r.m[1] = a.m[0] * b.m[1] + a.m[1] * b.m[3];
+  r.m[2] = a.m[2] * b.m[0] + a.m[3] * b.m[2];
+  r.m[3] = a.m[2] * b.m[1] + a.m[3] * b.m[3];
+  return r;
 }
 
 struct Program {
@@ -174,15 +187,23 @@ struct Program {
   std::vector<FusedOp> ops;
   uint8_t pos[16];
   int identity = 1;
+  float out_scale = 1.0f;
   double cost = 0.0;
 };
+
+// At most this many unscaled Hadamard butterflies per pass (bounds the growth
+// of the unscaled amplitudes to 2^kMaxHPerPass before the pass rescale).
+constexpr int kMaxHPerPass = 48;
 
 // Turn the circuit (gates in step order) into passes of 4 local bits.  One
 // in-order scan per pass: a gate is ready when no earlier unscheduled gate
 // shares a qubit with it (tracked as `blocked` qubits); a ready non-diagonal
 // gate is scheduled if its target bit is or can become local; diagonal gates
-// are always scheduled; SWAPs relabel qubits.  The result does not depend on
-// the other circuits of a batch.
+// are always scheduled; SWAPs relabel qubits.  Within a pass, consecutive
+// uncontrolled single-qubit factors on the same qubit are multiplied in FP64
+// (the mixed-product property of the Kronecker product: consecutive steps'
+// factors on one qubit compose).  The result does not depend on the other
+// circuits of a batch.
 static void compile_program(int n, const std::vector<const Gate*>& gs, Program& P) {
   P.n = n;
   P.nint = std::max(n, 4);
@@ -193,11 +214,35 @@ static void compile_program(int n, const std::vector<const Gate*>& gs, Program& 
   std::vector<int> pending(gs.size()), still;
   std::iota(pending.begin(), pending.end(), 0);
   struct Raw {
-    const Gate* g;
+    Mat2 u;
     GClass cls;
-    int t, c;  // physical bits (c = -1: uncontrolled)
+    bool is_h;    // unfused uncontrolled Hadamard
+    bool single;  // uncontrolled single-qubit factor
+    int t, c;     // physical bits (c = -1: uncontrolled)
   };
   std::vector<Raw> raw;
+  int last_touch[16];
+  int h_in_pass = 0;
+  int h_carry = 0;  // Hadamard factors 2^-1/2 not yet applied
+  auto push_raw = [&](const Gate& g, GClass cls, int t, int c) {
+    const bool single = (c < 0);
+    if (single) {
+      const int last = last_touch[t];
+      if (last >= 0 && raw[last].single && raw[last].t == t) {
+        Raw& r = raw[last];
+        if (r.is_h) --h_in_pass;
+        r.u = mat_mul(g.u, r.u);
+        r.is_h = false;
+        r.cls = classify_mat(r.u);
+        return;
+      }
+    }
+    const bool is_h = single && g.kind == TQS_H && h_in_pass < kMaxHPerPass;
+    if (is_h) ++h_in_pass;
+    raw.push_back({g.u, cls, is_h, single, t, c});
+    last_touch[t] = static_cast<int>(raw.size()) - 1;
+    if (c >= 0) last_touch[c] = static_cast<int>(raw.size()) - 1;
+  };
   auto emit_pass = [&](uint32_t Lmask, int nL) {
     for (int b = 0; nL < 4 && b < nint; ++b)
       if (!((Lmask >> b) & 1)) { Lmask |= 1u << b; ++nL; }
@@ -210,10 +255,15 @@ static void compile_program(int n, const std::vector<const Gate*>& gs, Program& 
     ps.op_begin = static_cast<uint32_t>(P.ops.size());
     ps.op_count = static_cast<uint32_t>(raw.size());
     double pass_cost = 6.0;
+    int h_count = 0;
     for (const Raw& r : raw) {
       FusedOp op{};
-      const Mat2& u = r.g->u;
-      if (r.cls == G_DIAG) {
+      const Mat2& u = r.u;
+      if (r.is_h) {
+        op.kind = OP_H;
+        ++h_count;
+        pass_cost += 0.5;
+      } else if (r.cls == G_DIAG) {
         op.kind = OP_DIAG;
         op.m[0] = to_f2(u.m[0]);
         op.m[1] = to_f2(u.m[3]);
@@ -227,8 +277,12 @@ static void compile_program(int n, const std::vector<const Gate*>& gs, Program& 
         pass_cost += 1.0;
       } else {
         op.kind = OP_DENSE;
-        for (int i = 0; i < 4; ++i) op.m[i] = to_f2(u.m[i]);
-        pass_cost += 2.0;
+        for (int i = 0; i < 4; ++i) {
+          op.m[i] = to_f2(u.m[i]);
+          const cd hi(op.m[i].x, op.m[i].y);
+          op.lo[i] = to_f2(u.m[i] - hi);
+        }
+        pass_cost += 3.0;
       }
       if (loc[r.t] >= 0) { op.tloc = 1; op.t = static_cast<uint8_t>(loc[r.t]); }
       else { op.tloc = 0; op.t = static_cast<uint8_t>(r.t); }
@@ -237,13 +291,19 @@ static void compile_program(int n, const std::vector<const Gate*>& gs, Program& 
       else { op.ckind = CTL_FAR; op.c = static_cast<uint8_t>(r.c); }
       P.ops.push_back(op);
     }
+    // exact power-of-two rescale for this pass's unscaled Hadamards
+    const int tot = h_carry + h_count;
+    ps.scale = std::ldexp(1.0f, -(tot / 2));
+    h_carry = tot % 2;
     P.passes.push_back(ps);
     P.cost += pass_cost * static_cast<double>(1u << nint);
     raw.clear();
+    h_in_pass = 0;
   };
   while (!pending.empty()) {
     uint32_t Lmask = 0, blocked = 0;
     int nL = 0;
+    for (int b = 0; b < 16; ++b) last_touch[b] = -1;
     still.clear();
     size_t idx = 0;
     for (; idx < pending.size(); ++idx) {
@@ -266,13 +326,14 @@ static void compile_program(int n, const std::vector<const Gate*>& gs, Program& 
         Lmask |= 1u << t;
         ++nL;
       }
-      raw.push_back({&g, cls, t, c});
+      push_raw(g, cls, t, c);
     }
     for (; idx < pending.size(); ++idx) still.push_back(pending[idx]);
     emit_pass(Lmask, nL);
     pending.swap(still);
   }
   if (P.passes.empty()) emit_pass(0u, 0);
+  P.out_scale = h_carry ? static_cast<float>(1.0 / std::sqrt(2.0)) : 1.0f;
   P.identity = 1;
   for (int q = 0; q < 16; ++q) {
     P.pos[q] = static_cast<uint8_t>(q < n ? phys[q] : q);
@@ -448,7 +509,7 @@ static void ensure_program(tqs_circuit* c) {
 
 static bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
 extern "C" tqs_status tqs_circuit_program(tqs_circuit* c, int* n_passes, int* n_ops, void* h_passes,
-                                          void* h_ops, uint8_t* h_pos) {
+                                          void* h_ops, uint8_t* h_pos, float* h_out_scale) {
   if (!c) return fail(TQS_ERR_ARG, "tqs_circuit_program: circuit is NULL");
   ensure_program(c);
   if (n_passes) *n_passes = static_cast<int>(c->prog.passes.size());
@@ -456,6 +517,7 @@ extern "C" tqs_status tqs_circuit_program(tqs_circuit* c, int* n_passes, int* n_
   if (h_passes) std::memcpy(h_passes, c->prog.passes.data(), c->prog.passes.size() * sizeof(FusedPass));
   if (h_ops) std::memcpy(h_ops, c->prog.ops.data(), c->prog.ops.size() * sizeof(FusedOp));
   if (h_pos) std::memcpy(h_pos, c->prog.pos, 16);
+  if (h_out_scale) *h_out_scale = c->prog.out_scale;
   return TQS_OK;
 }
 
@@ -480,6 +542,7 @@ struct Image {
     fc.identity = P.identity;
     std::memcpy(fc.pos, P.pos, 16);
     fc.init = nullptr;
+    fc.out_scale = P.out_scale;
     const uint32_t op_base = static_cast<uint32_t>(ops.size());
     for (FusedPass ps : P.passes) {
       ps.op_begin += op_base;

@@ -20,9 +20,11 @@ namespace tqs {
 // ---------------------------------------------------------------------------
 
 enum OpKind : uint8_t {
-  OP_DENSE = 0,   // general 2x2 on the (local) target
+  OP_DENSE = 0,   // general 2x2 on the (local) target, coefficients as hi + lo
   OP_ANTI = 1,    // anti-diagonal [[0, m01], [m10, 0]] on the (local) target
-  OP_DIAG = 2     // diag(d0, d1) on the target, any locality
+  OP_DIAG = 2,    // diag(d0, d1) on the target, any locality
+  OP_H = 3        // uncontrolled Hadamard without its 2^-1/2: (x0 + x1, x0 - x1);
+                  // the pass scale restores the factor exactly
 };
 
 enum CtlKind : uint8_t {
@@ -39,16 +41,17 @@ struct alignas(16) FusedOp {
   uint8_t c;
   uint8_t unit;    // OP_ANTI with m01 == m10 == 1 (X, CNOT)
   uint8_t pad0[2];
-  float2 m[4];     // DENSE: m00 m01 m10 m11 | ANTI: -, m01, m10, - | DIAG: d0, d1, d1/d0, -
   uint32_t pad1[2];
+  float2 m[4];     // DENSE: m00 m01 m10 m11 | ANTI: -, m01, m10, - | DIAG: d0, d1, d1/d0, -
+  float2 lo[4];    // DENSE: m - m_fp32 rounded to FP32 (the FP64 matrix is m + lo)
 };
-static_assert(sizeof(FusedOp) == 48, "FusedOp layout");
+static_assert(sizeof(FusedOp) == 80, "FusedOp layout");
 
 struct alignas(16) FusedPass {
   uint8_t L[4];        // physical bits of local positions 0..3, ascending
   uint32_t op_begin;   // index into the op array
   uint32_t op_count;
-  uint32_t pad;
+  float scale;         // exact power of two applied to every amplitude at the pass end
 };
 static_assert(sizeof(FusedPass) == 16, "FusedPass layout");
 
@@ -64,7 +67,8 @@ struct alignas(16) FusedCirc {
   int32_t identity;     // 1 if the output qubit map is the identity
   uint8_t pos[16];      // physical bit of logical qubit q at the end
   const float2* init;   // initial state (logical order) or nullptr for |0..0>
-  int64_t pad;
+  float out_scale;      // 1, or 2^-1/2 when an odd Hadamard factor is left over
+  int32_t pad;
 };
 static_assert(sizeof(FusedCirc) == 64, "FusedCirc layout");
 

@@ -14,7 +14,7 @@ from oracle import fsv_route, kron_route
 from paper_2305_14398_gb300 import binding as B
 from paper_2305_14398_gb300 import workloads as W
 
-DENSE, ANTI, DIAG = 0, 1, 2
+DENSE, ANTI, DIAG, HAD = 0, 1, 2, 3
 NONE, LOCAL, FAR = 0, 1, 2
 
 
@@ -22,7 +22,7 @@ def ins0(x, b):
     return ((x >> b) << (b + 1)) | (x & ((1 << b) - 1))
 
 
-def replay(n, passes, ops, pos):
+def replay(n, passes, ops, pos, out_scale=1.0):
     nint = max(n, 4)
     st = np.zeros(1 << nint, dtype=np.complex128)
     st[0] = 1.0
@@ -42,7 +42,11 @@ def replay(n, passes, ops, pos):
         b0, cnt = int(ps["op_begin"]), int(ps["op_count"])
         for op in ops[b0:b0 + cnt]:
             kind, tloc, t, ckind, c = (int(op[k]) for k in ("kind", "tloc", "t", "ckind", "c"))
-            m = op["m"].astype(np.complex128)
+            m = op["m"].astype(np.complex128) + (op["lo"].astype(np.complex128) if kind == DENSE else 0)
+            if kind == HAD:
+                assert tloc == 1 and ckind == NONE
+                m = np.array([1, 1, 1, -1], dtype=np.complex128)
+                kind = DENSE
             if kind == DIAG:
                 d0, d1, r = m[0], m[1], m[2]
                 if tloc:
@@ -89,13 +93,13 @@ def replay(n, passes, ops, pos):
             for j in range(16):
                 if (j >> b) & 1:
                     a[:, j] *= pend[:, b]
-        a *= sc[:, None]
+        a *= sc[:, None] * float(ps["scale"])
         st[idx] = a
     i = np.arange(1 << n, dtype=np.int64)
     phys = np.zeros_like(i)
     for q in range(n):
         phys |= ((i >> q) & 1) << int(pos[q])
-    return st[phys]
+    return st[phys] * out_scale
 
 
 def compiled(n, ops):
@@ -118,8 +122,8 @@ CASES += [(f"layered{n}", n, W.random_layered(n, 3, (8, n))) for n in (5, 10, 12
 
 @pytest.mark.parametrize("name,n,ops", CASES, ids=[c[0] for c in CASES])
 def test_program_replay_matches_oracle(name, n, ops):
-    passes, prog_ops, pos = compiled(n, ops)
-    got = replay(n, passes, prog_ops, pos)
+    passes, prog_ops, pos, osc = compiled(n, ops)
+    got = replay(n, passes, prog_ops, pos, osc)
     want = fsv_route.simulate(n, ops)
     # the program stores matrices in FP32; the replay computes in FP64
     assert np.max(np.abs(got - want)) < 2e-6
@@ -156,8 +160,9 @@ def test_ghz_steps_and_passes():
     c = B.circuit_from_ops(n, W.ghz_chain(n))
     try:
         assert B.tqs_circuit_info(c)[2] == n
-        passes, ops, pos = B.tqs_circuit_program(c)
+        passes, ops, pos, osc = B.tqs_circuit_program(c)
         assert len(ops) == n and len(passes) <= 4
+        assert ops[0]["kind"] == HAD and osc == np.float32(2 ** -0.5)
     finally:
         B.tqs_circuit_destroy(c)
 
