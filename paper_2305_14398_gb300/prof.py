@@ -1,0 +1,45 @@
+"""Small driver for ncu captures of the fused step kernels.
+
+    python -m paper_2305_14398_gb300.prof COUNT {mix|batch} REPS
+
+mix:   COUNT paper-shaped 11-qubit circuits (GHZ / DJ-constant / DJ-balanced /
+       QFT, 25 % each); batch: the first COUNT circuits of the random batched
+       workload (n = 4..14, depth 5..40).  Runs tqs_batch_run REPS times
+       without a graph, then once more timed with CUDA events.
+"""
+import sys
+
+import torch
+
+from . import binding as B
+from . import workloads as W
+
+
+def main(argv):
+    count = int(argv[1]) if len(argv) > 1 else 2048
+    kind = argv[2] if len(argv) > 2 else "mix"
+    reps = int(argv[3]) if len(argv) > 3 else 4
+    if kind == "mix":
+        circs = [(11, ops) for _, ops in W.paper_mix(11, count)]
+    else:
+        circs = W.batch_circuits(count, 3)
+    b = B.tqs_batch_create_packed(*B.pack_ops(circs))
+    c, total, _ = B.tqs_batch_info(b)
+    st = torch.empty(total, dtype=torch.complex64, device="cuda")
+    pr = torch.empty(total, dtype=torch.float64, device="cuda")
+    nm = torch.empty(c, dtype=torch.float64, device="cuda")
+    for _ in range(reps):
+        B.tqs_batch_run(b, st, pr, nm, use_graph=False)
+    torch.cuda.synchronize()
+    s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    s.record()
+    B.tqs_batch_run(b, st, pr, nm, use_graph=False)
+    e.record()
+    torch.cuda.synchronize()
+    print(kind, count, "ms %.4f" % s.elapsed_time(e),
+          "norm err %.2e" % float((nm - 1).abs().max()))
+    B.tqs_batch_destroy(b)
+
+
+if __name__ == "__main__":
+    main(sys.argv)
