@@ -183,6 +183,27 @@ tqs_status tqs_circuit_unitary(tqs_circuit* c, int prec, tqs_c64* d_U, void* str
 tqs_status tqs_probabilities(const tqs_c64* d_state, int n, double* d_probs,
                              double* d_sum, void* stream);
 
+/* Allocation-free form of tqs_probabilities, for callers that cannot call
+ * cudaMalloc: for example a host framework that hands out all device memory
+ * from its own pre-sized pool and forbids any other allocation, or a
+ * latency-critical loop that cannot afford cudaMalloc/cudaFree, which may
+ * synchronise the device.  The paper has no counterpart; it is a deployment
+ * convenience.  Same arguments, results and determinism as tqs_probabilities.
+ *   - Scratch: the per-block partial sums live in one fixed device array of
+ *     1024 doubles (8 KiB) that every GPU loading the library holds until the
+ *     process exits.  1 <= n <= 30 (at most 1024 partial sums); larger n
+ *     returns TQS_ERR_TOO_MANY_QUBITS.
+ *   - The first call on each device looks up the array's device address
+ *     (cudaGetSymbolAddress) with that device current and caches it; make
+ *     that first call before any stream capture.  No call allocates or frees
+ *     device memory.
+ *   - Every call on a GPU shares that GPU's copy of the array.  Each call
+ *     overwrites all the partial sums it reads, so nothing carries over
+ *     between calls, but calls that overlap on the same GPU (for example on
+ *     two streams) race on it: serialise them. */
+tqs_status tqs_probabilities_noalloc(const tqs_c64* d_state, int n, double* d_probs,
+                                     double* d_sum, void* stream);
+
 /* Marginal probability that every qubit set in `mask` reads 0:
  * sum of |psi_i|^2 over i with (i & mask) == 0, FP64, deterministic
  * (Deutsch-Jozsa input register, Sec. 2.5).  d_out: 1 double. */

@@ -61,6 +61,7 @@ _SIGS = {
     "tqs_circuit_unitary": (_i, [_vp, _i, _vp, _vp]),
     "tqs_probabilities": (_i, [_vp, _i, _vp, _vp, _vp]),
     "tqs_marginal_zero": (_i, [_vp, _i, _u64, _vp, _vp]),
+    "tqs_probabilities_noalloc": (_i, [_vp, _i, _vp, _vp, _vp]),
     "tqs_batch_create": (_i, [ctypes.POINTER(_vp), _i, ctypes.POINTER(_vp)]),
     "tqs_batch_create_packed": (_i, [_i, _vp, _vp, _vp, _vp, _vp, ctypes.POINTER(_vp)]),
     "tqs_batch_info": (_i, [_vp, _pi, ctypes.POINTER(_i64), ctypes.POINTER(_i64),
@@ -204,6 +205,11 @@ def tqs_circuit_unitary(c: int, prec: int, U, stream=None) -> None:
 
 def tqs_probabilities(state, n: int, probs=None, total=None, stream=None) -> None:
     _check(lib().tqs_probabilities(_ptr(state), int(n), _ptr(probs), _ptr(total), _stream(stream)))
+
+
+def tqs_probabilities_noalloc(state, n: int, probs=None, total=None, stream=None) -> None:
+    _check(lib().tqs_probabilities_noalloc(_ptr(state), int(n), _ptr(probs), _ptr(total),
+                                           _stream(stream)))
 
 
 def tqs_marginal_zero(state, n: int, mask: int, out, stream=None) -> None:

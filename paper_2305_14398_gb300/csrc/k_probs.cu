@@ -7,6 +7,9 @@
 // Deutsch-Jozsa input register of Sec. 2.5).  The reduction runs in a fixed
 // order: per-block partial sums into scratch, then one warp sums the
 // partials, so the result does not depend on scheduling.
+#include <mutex>
+
+#include "../../include/tqs.h"
 #include "tqs_internal.h"
 
 namespace tqs {
@@ -79,4 +82,72 @@ cudaError_t launch_probs(const float2* d_state, int n, double* d_probs, uint64_t
   return cudaGetLastError();
 }
 
+// ---------------------------------------------------------------------------
+// Allocation-free variant (tqs_probabilities_noalloc).
+//
+// Its per-block partial sums live in this fixed array, loaded with the library
+// and kept by every GPU that loads it until the process exits.  Host code may
+// not use the array's name as a device address: the address is looked up with
+// cudaGetSymbolAddress once per device, with that device current, and cached.
+// Each call overwrites all the partials it reads, so nothing needs clearing
+// between calls; calls that overlap on the GPU share the array and race.
+// ---------------------------------------------------------------------------
+constexpr int kStaticPartials = kMaxPartials;  // 1024 doubles = 8 KiB
+static __device__ __align__(256) double g_static_partials[kStaticPartials];
+
+namespace {
+constexpr int kMaxDevices = 64;
+std::mutex g_static_mu;
+double* g_static_ptr[kMaxDevices] = {};
+}  // namespace
+
 }  // namespace tqs
+
+extern "C" tqs_status tqs_probabilities_noalloc(const tqs_c64* d_state, int n, double* d_probs,
+                                                double* d_sum, void* stream) {
+  using namespace tqs;
+  if (!d_state) {
+    set_last_error("tqs_probabilities_noalloc: d_state is NULL");
+    return TQS_ERR_ARG;
+  }
+  if (n < 1 || n > 30) {
+    set_last_error("tqs_probabilities_noalloc: n must be in [1, 30]");
+    return TQS_ERR_TOO_MANY_QUBITS;
+  }
+  if ((reinterpret_cast<uintptr_t>(d_state) & 15u) || (reinterpret_cast<uintptr_t>(d_probs) & 15u)) {
+    set_last_error("tqs_probabilities_noalloc: device buffers must be 16-byte aligned");
+    return TQS_ERR_ARG;
+  }
+  const int parts = probs_partial_count(n);
+  if (parts > kStaticPartials) {
+    set_last_error("tqs_probabilities_noalloc: needs more partial sums than the fixed 1024");
+    return TQS_ERR_TOO_MANY_QUBITS;
+  }
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess || dev < 0 || dev >= kMaxDevices) {
+    set_last_error("tqs_probabilities_noalloc: no usable current device");
+    return TQS_ERR_CUDA;
+  }
+  double* partials = nullptr;
+  {
+    std::lock_guard<std::mutex> lock(g_static_mu);
+    if (!g_static_ptr[dev]) {
+      void* ptr = nullptr;
+      e = cudaGetSymbolAddress(&ptr, g_static_partials);
+      if (e != cudaSuccess || ptr == nullptr) {
+        set_last_error("tqs_probabilities_noalloc: cudaGetSymbolAddress failed");
+        return TQS_ERR_CUDA;
+      }
+      g_static_ptr[dev] = static_cast<double*>(ptr);
+    }
+    partials = g_static_ptr[dev];
+  }
+  e = launch_probs(reinterpret_cast<const float2*>(d_state), n, d_probs, 0, partials, parts, d_sum,
+                   static_cast<cudaStream_t>(stream));
+  if (e != cudaSuccess) {
+    set_last_error("tqs_probabilities_noalloc: kernel launch failed");
+    return TQS_ERR_CUDA;
+  }
+  return TQS_OK;
+}

@@ -32,6 +32,8 @@ static std::atomic<int64_t> g_launches{0};
 
 void count_launches(int64_t k) { g_launches.fetch_add(k, std::memory_order_relaxed); }
 
+void set_last_error(const char* msg) { g_last_error = msg; }
+
 static tqs_status fail(tqs_status s, const char* fmt, ...) {
   char buf[512];
   va_list ap;

@@ -136,4 +136,7 @@ cudaError_t launch_probs(const float2* d_state, int n, double* d_probs, uint64_t
 // Process-wide count of kernel launches enqueued by this library.
 void count_launches(int64_t k);
 
+// Record the calling thread's last error message (read by tqs_last_error).
+void set_last_error(const char* msg);
+
 }  // namespace tqs
