@@ -128,11 +128,13 @@ tqs_status tqs_circuit_steps(const tqs_circuit* c, int* h_step_of_gate);
  *              {uint8 L[4]; uint32 op_begin; uint32 op_count; float scale}
  *              (scale: exact power of two applied at the end of the pass)
  *   h_ops    : NULL or n_ops records of 80 bytes:
- *              {uint8 kind (0 dense, 1 anti-diagonal, 2 diagonal,
- *               3 Hadamard without its 2^-1/2), tloc, t,
- *               ckind (0 none, 1 local, 2 far), c, unit, pad[2]; uint32 pad[2];
- *               float m[8] (4 complex entries); float lo[8] (their FP32
- *               rounding residues, dense ops)}
+ *              {uint8 code (0-3 Hadamard without its 2^-1/2, 4-7 exchange
+ *               (X, CNOT), 8-11 anti-diagonal, 12-15 dense, each + the local
+ *               target position; 16 diagonal), tloc, t, ckind (0 none,
+ *               1 local, 2 far), c (diagonal ops: target / control), fbit
+ *               (far control bit, 255 none), uint16 act (active-pair mask);
+ *               uint32 pad[2]; float m[8] (4 complex entries); float lo[8]
+ *               (their FP32 rounding residues, dense ops)}
  *   h_pos    : NULL or 16 bytes, the physical bit of each logical qubit at
  *              the end (SWAP factors are relabelings).
  *   h_out_scale : NULL or 1 float, the factor applied to the output state.

@@ -15,7 +15,7 @@ from typing import Iterable, List, Optional, Sequence, Tuple
 import numpy as np
 
 HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(HERE, "libtqs.so")
+LIB_PATH = os.environ.get("TQS_LIB") or os.path.join(HERE, "libtqs.so")
 HEADER = os.path.join(os.path.dirname(HERE), "include", "tqs.h")
 
 GATE_IDS = {"h": 0, "x": 1, "y": 2, "z": 3, "s": 4, "t": 5, "r": 6, "rx": 7, "ry": 8, "rz": 9,
@@ -154,8 +154,8 @@ def tqs_circuit_steps(c: int) -> List[int]:
 
 PASS_DTYPE = np.dtype([("L", np.uint8, 4), ("op_begin", np.uint32), ("op_count", np.uint32),
                        ("scale", np.float32)])
-OP_DTYPE = np.dtype([("kind", np.uint8), ("tloc", np.uint8), ("t", np.uint8), ("ckind", np.uint8),
-                     ("c", np.uint8), ("unit", np.uint8), ("pad0", np.uint8, 2),
+OP_DTYPE = np.dtype([("code", np.uint8), ("tloc", np.uint8), ("t", np.uint8), ("ckind", np.uint8),
+                     ("c", np.uint8), ("fbit", np.uint8), ("act", np.uint16),
                      ("pad1", np.uint32, 2), ("m", np.complex64, 4), ("lo", np.complex64, 4)])
 
 

@@ -13,6 +13,7 @@
 // Teams: one warp per circuit (n <= 11), one CTA per circuit (n <= 14), or one
 // CTA on global scratch (n <= 16).  Warps/CTAs pull circuits from an atomic
 // job counter (costliest first), so one persistent launch runs a whole batch.
+#include "exact_sq.h"
 #include "tqs_internal.h"
 
 namespace tqs {
@@ -57,22 +58,54 @@ __device__ __forceinline__ float2 cmac2_hl(float2 ah, float2 al, float2 x, float
 }
 
 // ------------------------------------------------------------ butterflies
-// T: local position of the target; C: local position of the control or -1.
+// T: local position of the target.  `act` is a 16-bit mask over the local
+// amplitude index: the op acts on the pairs whose j0 bit is set in it (all
+// ones when uncontrolled, the control-bit-1 half for a local control).
 
 struct Coef {
   float2 h[4], l[4];
 };
 
-template <int T, int C>
-__device__ __forceinline__ void dense_t(float2 (&a)[16], const Coef& m) {
+__device__ __forceinline__ float2 sel(bool on, float2 y, float2 x) {
+  return make_float2(on ? y.x : x.x, on ? y.y : x.y);
+}
+
+template <int T>
+__device__ __forceinline__ void dense_t(float2 (&a)[16], const Coef& m, unsigned act) {
 #pragma unroll
   for (int p = 0; p < 8; ++p) {
     const int j0 = ((p >> T) << (T + 1)) | (p & ((1 << T) - 1));
     const int j1 = j0 | (1 << T);
-    if (C >= 0 && !((j0 >> C) & 1)) continue;
+    const bool on = (act >> j0) & 1;
     const float2 x0 = a[j0], x1 = a[j1];
-    a[j0] = cmac2_hl(m.h[0], m.l[0], x0, m.h[1], m.l[1], x1);
-    a[j1] = cmac2_hl(m.h[2], m.l[2], x0, m.h[3], m.l[3], x1);
+    a[j0] = sel(on, cmac2_hl(m.h[0], m.l[0], x0, m.h[1], m.l[1], x1), x0);
+    a[j1] = sel(on, cmac2_hl(m.h[2], m.l[2], x0, m.h[3], m.l[3], x1), x1);
+  }
+}
+
+template <int T>
+__device__ __forceinline__ void anti_t(float2 (&a)[16], float2 m01, float2 m10, unsigned act) {
+#pragma unroll
+  for (int p = 0; p < 8; ++p) {
+    const int j0 = ((p >> T) << (T + 1)) | (p & ((1 << T) - 1));
+    const int j1 = j0 | (1 << T);
+    const bool on = (act >> j0) & 1;
+    const float2 x0 = a[j0], x1 = a[j1];
+    a[j0] = sel(on, cmul(m01, x1), x0);
+    a[j1] = sel(on, cmul(m10, x0), x1);
+  }
+}
+
+template <int T>
+__device__ __forceinline__ void swap_t(float2 (&a)[16], unsigned act) {
+#pragma unroll
+  for (int p = 0; p < 8; ++p) {
+    const int j0 = ((p >> T) << (T + 1)) | (p & ((1 << T) - 1));
+    const int j1 = j0 | (1 << T);
+    const bool on = (act >> j0) & 1;
+    const float2 x0 = a[j0], x1 = a[j1];
+    a[j0] = sel(on, x1, x0);
+    a[j1] = sel(on, x0, x1);
   }
 }
 
@@ -89,42 +122,6 @@ __device__ __forceinline__ void h_t(float2 (&a)[16]) {
   }
 }
 
-template <int T, int C>
-__device__ __forceinline__ void anti_t(float2 (&a)[16], float2 m01, float2 m10) {
-#pragma unroll
-  for (int p = 0; p < 8; ++p) {
-    const int j0 = ((p >> T) << (T + 1)) | (p & ((1 << T) - 1));
-    const int j1 = j0 | (1 << T);
-    if (C >= 0 && !((j0 >> C) & 1)) continue;
-    const float2 x0 = a[j0], x1 = a[j1];
-    a[j0] = cmul(m01, x1);
-    a[j1] = cmul(m10, x0);
-  }
-}
-
-template <int T, int C>
-__device__ __forceinline__ void swap_t(float2 (&a)[16]) {
-#pragma unroll
-  for (int p = 0; p < 8; ++p) {
-    const int j0 = ((p >> T) << (T + 1)) | (p & ((1 << T) - 1));
-    const int j1 = j0 | (1 << T);
-    if (C >= 0 && !((j0 >> C) & 1)) continue;
-    const float2 x0 = a[j0];
-    a[j0] = a[j1];
-    a[j1] = x0;
-  }
-}
-
-// Controlled diagonal with both qubits local.
-template <int T, int C>
-__device__ __forceinline__ void diag_t(float2 (&a)[16], float2 d0, float2 d1) {
-#pragma unroll
-  for (int j = 0; j < 16; ++j) {
-    if (C >= 0 && !((j >> C) & 1)) continue;
-    a[j] = cmul(a[j], ((j >> T) & 1) ? d1 : d0);
-  }
-}
-
 template <int B>
 __device__ __forceinline__ void scale_bit(float2 (&a)[16], float2 ph) {
 #pragma unroll
@@ -132,29 +129,23 @@ __device__ __forceinline__ void scale_bit(float2 (&a)[16], float2 ph) {
     if ((j >> B) & 1) a[j] = cmul(a[j], ph);
 }
 
-#define TQS_DISPATCH_TC(FN, ARGS)   \
-  switch (sel) {                    \
-    case 0: FN<0, -1> ARGS; break;  \
-    case 2: FN<0, 1> ARGS; break;   \
-    case 3: FN<0, 2> ARGS; break;   \
-    case 4: FN<0, 3> ARGS; break;   \
-    case 5: FN<1, -1> ARGS; break;  \
-    case 6: FN<1, 0> ARGS; break;   \
-    case 8: FN<1, 2> ARGS; break;   \
-    case 9: FN<1, 3> ARGS; break;   \
-    case 10: FN<2, -1> ARGS; break; \
-    case 11: FN<2, 0> ARGS; break;  \
-    case 12: FN<2, 1> ARGS; break;  \
-    case 14: FN<2, 3> ARGS; break;  \
-    case 15: FN<3, -1> ARGS; break; \
-    case 16: FN<3, 0> ARGS; break;  \
-    case 17: FN<3, 1> ARGS; break;  \
-    case 18: FN<3, 2> ARGS; break;  \
-    default: break;                 \
+// 16-bit masks of the local indices j whose bit b is set.
+__device__ __forceinline__ unsigned bit_mask(int b) {
+  return b == 0 ? 0xAAAAu : b == 1 ? 0xCCCCu : b == 2 ? 0xF0F0u : 0xFF00u;
+}
+
+// Controlled diagonal with both qubits local: amplitudes with the control bit
+// set are multiplied by d0 (target 0) or d1 (target 1).
+__device__ __forceinline__ void diag_local(float2 (&a)[16], int t, int c, float2 d0, float2 d1) {
+  const unsigned cm = bit_mask(c), tm = bit_mask(t);
+#pragma unroll
+  for (int j = 0; j < 16; ++j) {
+    if ((cm >> j) & 1) a[j] = cmul(a[j], ((tm >> j) & 1) ? d1 : d0);
   }
+}
 
 // Pending per-bit phases: a diagonal factor that depends on one local bit is
-// folded into ph[b] (applied to the amplitudes with local bit b = 1) and only
+// folded into p_b (applied to the amplitudes with local bit b = 1) and only
 // multiplied in before a non-diagonal factor on bit b, or at the end of the
 // pass.  Factors that depend on far bits only fold into the scalar `sc`.
 struct Pending {
@@ -189,7 +180,8 @@ __device__ __forceinline__ float2 f2(unsigned x, unsigned y) {
 }
 
 // Apply the ops of one pass to the 16 amplitudes of one group, then the
-// pass's exact power-of-two scale.
+// pass's exact power-of-two scale.  One jump per op on its dispatch code; the
+// next op's header is fetched while the current one runs.
 __device__ __forceinline__ void run_ops(float2 (&a)[16], const FusedOp* __restrict__ ops,
                                         uint32_t count, int base, float scale) {
   Pending pd;
@@ -197,72 +189,93 @@ __device__ __forceinline__ void run_ops(float2 (&a)[16], const FusedOp* __restri
   pd.dirty = 0;
   float2 sc = make_float2(1.f, 0.f);
   bool sc_set = false;
+  uint4 next = count ? __ldg(reinterpret_cast<const uint4*>(ops)) : make_uint4(0, 0, 0, 0);
   for (uint32_t k = 0; k < count; ++k) {
     const uint4* rec = reinterpret_cast<const uint4*>(ops + k);
-    const uint4 q0 = __ldg(rec);
-    const int kind = q0.x & 0xff;
+    const uint4 q0 = next;
+    if (k + 1 < count) next = __ldg(reinterpret_cast<const uint4*>(ops + k + 1));
+    const int code = q0.x & 0xff;
+    if (code < OPC_DIAG) {
+      const int fbit = q0.y >> 8 & 0xff;
+      if (fbit != 0xff && !((base >> fbit) & 1)) continue;  // far control is 0 here
+      const int t = code & 3;
+      const unsigned act = q0.y >> 16;
+      pend_flush(a, pd, t);
+      switch (code) {
+        case OPC_H + 0: h_t<0>(a); break;
+        case OPC_H + 1: h_t<1>(a); break;
+        case OPC_H + 2: h_t<2>(a); break;
+        case OPC_H + 3: h_t<3>(a); break;
+        case OPC_SWAP + 0: swap_t<0>(a, act); break;
+        case OPC_SWAP + 1: swap_t<1>(a, act); break;
+        case OPC_SWAP + 2: swap_t<2>(a, act); break;
+        case OPC_SWAP + 3: swap_t<3>(a, act); break;
+        case OPC_ANTI + 0:
+        case OPC_ANTI + 1:
+        case OPC_ANTI + 2:
+        case OPC_ANTI + 3: {
+          const uint4 q1 = __ldg(rec + 1);
+          const uint4 q2 = __ldg(rec + 2);
+          const float2 m01 = f2(q1.z, q1.w), m10 = f2(q2.x, q2.y);
+          switch (t) {
+            case 0: anti_t<0>(a, m01, m10, act); break;
+            case 1: anti_t<1>(a, m01, m10, act); break;
+            case 2: anti_t<2>(a, m01, m10, act); break;
+            default: anti_t<3>(a, m01, m10, act); break;
+          }
+          break;
+        }
+        default: {
+          const uint4 q1 = __ldg(rec + 1);
+          const uint4 q2 = __ldg(rec + 2);
+          const uint4 q3 = __ldg(rec + 3);
+          const uint4 q4 = __ldg(rec + 4);
+          Coef m;
+          m.h[0] = f2(q1.x, q1.y);
+          m.h[1] = f2(q1.z, q1.w);
+          m.h[2] = f2(q2.x, q2.y);
+          m.h[3] = f2(q2.z, q2.w);
+          m.l[0] = f2(q3.x, q3.y);
+          m.l[1] = f2(q3.z, q3.w);
+          m.l[2] = f2(q4.x, q4.y);
+          m.l[3] = f2(q4.z, q4.w);
+          switch (t) {
+            case 0: dense_t<0>(a, m, act); break;
+            case 1: dense_t<1>(a, m, act); break;
+            case 2: dense_t<2>(a, m, act); break;
+            default: dense_t<3>(a, m, act); break;
+          }
+          break;
+        }
+      }
+      continue;
+    }
+    // diagonal: d0 = m0, d1 = m1, ratio d1/d0 = m2
     const int tloc = (q0.x >> 8) & 0xff;
     const int t = (q0.x >> 16) & 0xff;
     const int ckind = q0.x >> 24;
     const int c = q0.y & 0xff;
-    const int unit = (q0.y >> 8) & 0xff;
-    if (kind == OP_H) {
-      pend_flush(a, pd, t);
-      switch (t) {
-        case 0: h_t<0>(a); break;
-        case 1: h_t<1>(a); break;
-        case 2: h_t<2>(a); break;
-        default: h_t<3>(a); break;
-      }
-      continue;
-    }
     const uint4 q1 = __ldg(rec + 1);
     const uint4 q2 = __ldg(rec + 2);
     const float2 m0 = f2(q1.x, q1.y);
     const float2 m1 = f2(q1.z, q1.w);
     const float2 m2 = f2(q2.x, q2.y);
-    if (kind == OP_DIAG) {
-      // d0 = m0, d1 = m1, ratio d1/d0 = m2
-      if (tloc) {
-        if (ckind == CTL_LOCAL) {
-          const int sel = t * 5 + c + 1;
-          TQS_DISPATCH_TC(diag_t, (a, m0, m1));
-        } else if (ckind == CTL_NONE || ((base >> c) & 1)) {
-          sc = cmul(sc, m0);
-          sc_set = true;
-          pend_mul(pd, t, m2);
-        }
-      } else {
-        const float2 v = ((base >> t) & 1) ? m1 : m0;
-        if (ckind == CTL_LOCAL) {
-          pend_mul(pd, c, v);
-        } else if (ckind == CTL_NONE || ((base >> c) & 1)) {
-          sc = cmul(sc, v);
-          sc_set = true;
-        }
+    if (tloc) {
+      if (ckind == CTL_LOCAL) {
+        diag_local(a, t, c, m0, m1);
+      } else if (ckind == CTL_NONE || ((base >> c) & 1)) {
+        sc = cmul(sc, m0);
+        sc_set = true;
+        pend_mul(pd, t, m2);
       }
-      continue;
-    }
-    if (ckind == CTL_FAR && !((base >> c) & 1)) continue;
-    pend_flush(a, pd, t);
-    const int sel = t * 5 + (ckind == CTL_LOCAL ? c : -1) + 1;
-    if (kind == OP_DENSE) {
-      const uint4 q3 = __ldg(rec + 3);
-      const uint4 q4 = __ldg(rec + 4);
-      Coef m;
-      m.h[0] = m0;
-      m.h[1] = m1;
-      m.h[2] = m2;
-      m.h[3] = f2(q2.z, q2.w);
-      m.l[0] = f2(q3.x, q3.y);
-      m.l[1] = f2(q3.z, q3.w);
-      m.l[2] = f2(q4.x, q4.y);
-      m.l[3] = f2(q4.z, q4.w);
-      TQS_DISPATCH_TC(dense_t, (a, m));
-    } else if (unit) {
-      TQS_DISPATCH_TC(swap_t, (a));
     } else {
-      TQS_DISPATCH_TC(anti_t, (a, m1, m2));
+      const float2 v = ((base >> t) & 1) ? m1 : m0;
+      if (ckind == CTL_LOCAL) {
+        pend_mul(pd, c, v);
+      } else if (ckind == CTL_NONE || ((base >> c) & 1)) {
+        sc = cmul(sc, v);
+        sc_set = true;
+      }
     }
   }
   pend_flush(a, pd, 0);
@@ -280,6 +293,42 @@ __device__ __forceinline__ void run_ops(float2 (&a)[16], const FusedOp* __restri
   }
 }
 
+// Compensated (Kahan) FP32 accumulation of |v|^2 for the per-circuit norm:
+// the per-thread partial sums are exact to a few FP32 ulps and are combined
+// across threads in FP64.
+__device__ __forceinline__ void kahan_add(float p, float& sum, float& comp) {
+  const float y = p - comp;
+  const float t = sum + y;
+  comp = (t - sum) - y;
+  sum = t;
+}
+
+// |v|^2 correctly rounded to FP64: the two squares are exact FP64 values built
+// with integer operations; one FP64 add rounds their sum.
+__device__ __forceinline__ double prob_f64(float2 v) {
+  const double a = __longlong_as_double(
+      static_cast<long long>(sq_f32_as_f64_bits(__float_as_uint(v.x))));
+  const double b = __longlong_as_double(
+      static_cast<long long>(sq_f32_as_f64_bits(__float_as_uint(v.y))));
+  return __dadd_rn(a, b);
+}
+
+// P(v): the physical index of logical index v, the XOR of 2^pos[q] over the
+// set bits q of v (the output map is a bit permutation, linear over XOR).
+struct PosMap {
+  unsigned long long lo, hi;  // pos[0..7], pos[8..15] as bytes
+};
+
+// P(v): physical index of logical index v, the XOR of 2^pos[q] over the set
+// bits q of v (the final qubit map is a bit permutation, linear over XOR).
+__device__ __forceinline__ int pfwd_bit(int q, const PosMap& pm) {
+  return 1 << static_cast<int>(((q < 8 ? pm.lo : pm.hi) >> ((q & 7) * 8)) & 0xff);
+}
+__device__ __forceinline__ int pfwd_of(int v, const PosMap& pm, int n) {
+  int r = 0;
+  for (int q = 0; q < n; ++q) if ((v >> q) & 1) r |= pfwd_bit(q, pm);
+  return r;
+}
 template <int TEAM>
 __device__ __forceinline__ void team_sync() {
   if (TEAM == TEAM_WARP)
@@ -296,83 +345,77 @@ __device__ void run_circuit(const FusedLaunch& L, int ci, float2* st, int rank, 
   const int n = cd.n;
   const int G = 1 << (nint - 4);
   const float2* init = cd.init;
-
   if (init != nullptr) {
     const int NI = 1 << nint, N = 1 << n;
     for (int i = rank; i < NI; i += size)
       st[swz(i)] = (i < N) ? init[i] : make_float2(0.f, 0.f);
     team_sync<TEAM>();
   }
-
   for (int p = 0; p < cd.pass_count; ++p) {
     const uint4 pr = __ldg(reinterpret_cast<const uint4*>(L.passes + cd.pass_begin + p));
-    const int l0 = pr.x & 0xff, l1 = (pr.x >> 8) & 0xff, l2 = (pr.x >> 16) & 0xff,
-              l3 = pr.x >> 24;
+    const int l0 = pr.x & 0xff, l1 = (pr.x >> 8) & 0xff, l2 = (pr.x >> 16) & 0xff, l3 = pr.x >> 24;
     const FusedOp* ops = L.ops + pr.y;
     const uint32_t count = pr.z;
     const float scale = __uint_as_float(pr.w);
     const bool gen = (p == 0) && (init == nullptr);
+    const int w0 = swz(1 << l0), w1 = swz(1 << l1), w2 = swz(1 << l2), w3 = swz(1 << l3);
     const int b0 = 1 << l0, b1 = 1 << l1, b2 = 1 << l2, b3 = 1 << l3;
     for (int g = rank; g < G; g += size) {
-      int base = ins0(ins0(ins0(ins0(g, l0), l1), l2), l3);
+      const int base = ins0(ins0(ins0(ins0(g, l0), l1), l2), l3);
+      const int sb = swz(base);
       float2 a[16];
 #pragma unroll
       for (int j = 0; j < 16; ++j) {
-        const int off = base + ((j & 1) ? b0 : 0) + ((j & 2) ? b1 : 0) + ((j & 4) ? b2 : 0) +
-                        ((j & 8) ? b3 : 0);
-        if (gen)
+        if (gen) {
+          const int off = base | ((j & 1) ? b0 : 0) | ((j & 2) ? b1 : 0) | ((j & 4) ? b2 : 0) | ((j & 8) ? b3 : 0);
           a[j] = make_float2(off == 0 ? 1.f : 0.f, 0.f);
-        else
-          a[j] = st[swz(off)];
+        } else {
+          a[j] = st[sb ^ ((j & 1) ? w0 : 0) ^ ((j & 2) ? w1 : 0) ^ ((j & 4) ? w2 : 0) ^ ((j & 8) ? w3 : 0)];
+        }
       }
       run_ops(a, ops, count, base, scale);
 #pragma unroll
-      for (int j = 0; j < 16; ++j) {
-        const int off = base + ((j & 1) ? b0 : 0) + ((j & 2) ? b1 : 0) + ((j & 4) ? b2 : 0) +
-                        ((j & 8) ? b3 : 0);
-        st[swz(off)] = a[j];
-      }
+      for (int j = 0; j < 16; ++j)
+        st[sb ^ ((j & 1) ? w0 : 0) ^ ((j & 2) ? w1 : 0) ^ ((j & 4) ? w2 : 0) ^ ((j & 8) ? w3 : 0)] = a[j];
     }
     team_sync<TEAM>();
   }
-
-  // Output: logical index i holds the amplitude at physical index P(i).
+  // Output: logical index i holds the amplitude at physical index P(i).  A
+  // thread writes i = 2 rank + 2 size k (two amplitudes, one 16-byte store);
+  // k runs in Gray-code order so P(i) changes by one XOR per iteration.
   const int N = 1 << n;
-  const uint4 posw = *reinterpret_cast<const uint4*>(cd.pos);
-  const unsigned pw[4] = {posw.x, posw.y, posw.z, posw.w};
+  PosMap pw;
+  { const ulonglong2 pv = *reinterpret_cast<const ulonglong2*>(cd.pos); pw.lo = pv.x; pw.hi = pv.y; }
   float2* out = L.out + cd.out_off;
   double* probs = L.probs ? L.probs + cd.out_off : nullptr;
   const float oscale = cd.out_scale;
-  double acc = 0.0;
-  for (int i = rank * 2; i < N; i += size * 2) {
-    int p0 = i, p1 = i + 1;
-    if (!cd.identity) {
-      p0 = 0;
-      p1 = 0;
-#pragma unroll
-      for (int q = 0; q < 16; ++q) {
-        if (q < n) {
-          const int b = (pw[q >> 2] >> ((q & 3) * 8)) & 0xff;
-          p0 |= ((i >> q) & 1) << b;
-          p1 |= (((i + 1) >> q) & 1) << b;
-        }
+  const int sh = 31 - __clz(2 * size);
+  const int i0 = 2 * rank;
+  float nsum = 0.f, ncomp = 0.f;
+  if (i0 < N) {
+    const int p_lo = cd.identity ? i0 : pfwd_of(i0, pw, n);
+    const int p_one = cd.identity ? 1 : pfwd_bit(0, pw);
+    int p_hi = 0;
+    const int iters = (N + 2 * size - 1) >> sh;
+    for (int k = 0; k < iters; ++k) {
+      if (k > 0) {
+        const int q = sh + (__ffs(k) - 1);
+        p_hi ^= cd.identity ? (1 << q) : pfwd_bit(q, pw);
       }
+      const int gk = k ^ (k >> 1);
+      const int i = i0 + (gk << sh);
+      const int p0 = p_lo ^ p_hi;
+      float2 v0 = st[swz(p0)];
+      float2 v1 = st[swz(p0 ^ p_one)];
+      if (oscale != 1.0f) { v0 = make_float2(v0.x * oscale, v0.y * oscale); v1 = make_float2(v1.x * oscale, v1.y * oscale); }
+      *reinterpret_cast<float4*>(out + i) = make_float4(v0.x, v0.y, v1.x, v1.y);
+      if (probs) *reinterpret_cast<double2*>(probs + i) = make_double2(prob_f64(v0), prob_f64(v1));
+      kahan_add(fmaf(v0.x, v0.x, v0.y * v0.y), nsum, ncomp);
+      kahan_add(fmaf(v1.x, v1.x, v1.y * v1.y), nsum, ncomp);
     }
-    float2 v0 = st[swz(p0)];
-    float2 v1 = st[swz(p1)];
-    if (oscale != 1.0f) {
-      v0 = make_float2(v0.x * oscale, v0.y * oscale);
-      v1 = make_float2(v1.x * oscale, v1.y * oscale);
-    }
-    *reinterpret_cast<float4*>(out + i) = make_float4(v0.x, v0.y, v1.x, v1.y);
-    // |psi|^2 in FP64: the squares of the FP32 parts are exact in FP64.
-    const double x0 = v0.x, y0 = v0.y, x1 = v1.x, y1 = v1.y;
-    const double q0 = fma(x0, x0, y0 * y0);
-    const double q1 = fma(x1, x1, y1 * y1);
-    if (probs) *reinterpret_cast<double2*>(probs + i) = make_double2(q0, q1);
-    acc += q0 + q1;
   }
-  // Fixed-order reduction (deterministic).
+  // Fixed-order reduction (deterministic): per-thread compensated FP32 -> FP64.
+  double acc = static_cast<double>(nsum) - static_cast<double>(ncomp);
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
   if (TEAM == TEAM_WARP) {
@@ -381,11 +424,7 @@ __device__ void run_circuit(const FusedLaunch& L, int ci, float2* st, int rank, 
     const int warp = rank >> 5, lane = rank & 31;
     if (lane == 0) s_red[warp] = acc;
     __syncthreads();
-    if (rank == 0) {
-      double s = 0.0;
-      for (int w = 0; w < (size >> 5); ++w) s += s_red[w];
-      if (L.norms) L.norms[ci] = s;
-    }
+    if (rank == 0) { double s = 0.0; for (int w = 0; w < (size >> 5); ++w) s += s_red[w]; if (L.norms) L.norms[ci] = s; }
   }
   team_sync<TEAM>();
 }

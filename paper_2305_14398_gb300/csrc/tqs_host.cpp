@@ -245,8 +245,9 @@ static void compile_program(int n, const std::vector<const Gate*>& gs, Program& 
     last_touch[t] = static_cast<int>(raw.size()) - 1;
     if (c >= 0) last_touch[c] = static_cast<int>(raw.size()) - 1;
   };
-  auto emit_pass = [&](uint32_t Lmask, int nL) {
-    for (int b = 0; nL < 4 && b < nint; ++b)
+  auto emit_pass = [&](uint32_t Lmask, int nL, bool last) {
+    (void)last;
+    for (int b = 0; nL < 4 && b < nint; ++b)  // padding: the lowest free bits
       if (!((Lmask >> b) & 1)) { Lmask |= 1u << b; ++nL; }
     FusedPass ps{};
     int loc[16];
@@ -258,39 +259,52 @@ static void compile_program(int n, const std::vector<const Gate*>& gs, Program& 
     ps.op_count = static_cast<uint32_t>(raw.size());
     double pass_cost = 6.0;
     int h_count = 0;
+    static const uint16_t kBitMask[4] = {0xAAAA, 0xCCCC, 0xF0F0, 0xFF00};
     for (const Raw& r : raw) {
       FusedOp op{};
       const Mat2& u = r.u;
-      if (r.is_h) {
-        op.kind = OP_H;
-        ++h_count;
-        pass_cost += 0.5;
-      } else if (r.cls == G_DIAG) {
-        op.kind = OP_DIAG;
+      op.fbit = 0xFF;
+      op.act = 0xFFFF;
+      if (r.cls != G_DIAG || r.is_h) {
+        // non-diagonal: the target is local
+        const int tl = loc[r.t];
+        op.t = static_cast<uint8_t>(tl);
+        op.tloc = 1;
+        if (r.c >= 0) {
+          if (loc[r.c] >= 0) op.act = kBitMask[loc[r.c]];
+          else op.fbit = static_cast<uint8_t>(r.c);
+        }
+        if (r.is_h) {
+          op.code = static_cast<uint8_t>(OPC_H + tl);
+          ++h_count;
+          pass_cost += 0.5;
+        } else if (r.cls == G_ANTI) {
+          const bool unit = (u.m[1] == cd(1.0) && u.m[2] == cd(1.0));
+          op.code = static_cast<uint8_t>((unit ? OPC_SWAP : OPC_ANTI) + tl);
+          op.m[1] = to_f2(u.m[1]);
+          op.m[2] = to_f2(u.m[2]);
+          pass_cost += unit ? 0.5 : 1.0;
+        } else {
+          op.code = static_cast<uint8_t>(OPC_DENSE + tl);
+          for (int i = 0; i < 4; ++i) {
+            op.m[i] = to_f2(u.m[i]);
+            const cd hi(op.m[i].x, op.m[i].y);
+            op.lo[i] = to_f2(u.m[i] - hi);
+          }
+          pass_cost += 3.0;
+        }
+      } else {
+        op.code = OPC_DIAG;
         op.m[0] = to_f2(u.m[0]);
         op.m[1] = to_f2(u.m[3]);
         op.m[2] = to_f2(u.m[3] / u.m[0]);
         pass_cost += 0.5;
-      } else if (r.cls == G_ANTI) {
-        op.kind = OP_ANTI;
-        op.m[1] = to_f2(u.m[1]);
-        op.m[2] = to_f2(u.m[2]);
-        op.unit = (u.m[1] == cd(1.0) && u.m[2] == cd(1.0)) ? 1 : 0;
-        pass_cost += 1.0;
-      } else {
-        op.kind = OP_DENSE;
-        for (int i = 0; i < 4; ++i) {
-          op.m[i] = to_f2(u.m[i]);
-          const cd hi(op.m[i].x, op.m[i].y);
-          op.lo[i] = to_f2(u.m[i] - hi);
-        }
-        pass_cost += 3.0;
+        if (loc[r.t] >= 0) { op.tloc = 1; op.t = static_cast<uint8_t>(loc[r.t]); }
+        else { op.tloc = 0; op.t = static_cast<uint8_t>(r.t); }
+        if (r.c < 0) { op.ckind = CTL_NONE; op.c = 0; }
+        else if (loc[r.c] >= 0) { op.ckind = CTL_LOCAL; op.c = static_cast<uint8_t>(loc[r.c]); }
+        else { op.ckind = CTL_FAR; op.c = static_cast<uint8_t>(r.c); }
       }
-      if (loc[r.t] >= 0) { op.tloc = 1; op.t = static_cast<uint8_t>(loc[r.t]); }
-      else { op.tloc = 0; op.t = static_cast<uint8_t>(r.t); }
-      if (r.c < 0) { op.ckind = CTL_NONE; op.c = 0; }
-      else if (loc[r.c] >= 0) { op.ckind = CTL_LOCAL; op.c = static_cast<uint8_t>(loc[r.c]); }
-      else { op.ckind = CTL_FAR; op.c = static_cast<uint8_t>(r.c); }
       P.ops.push_back(op);
     }
     // exact power-of-two rescale for this pass's unscaled Hadamards
@@ -331,10 +345,10 @@ static void compile_program(int n, const std::vector<const Gate*>& gs, Program& 
       push_raw(g, cls, t, c);
     }
     for (; idx < pending.size(); ++idx) still.push_back(pending[idx]);
-    emit_pass(Lmask, nL);
+    emit_pass(Lmask, nL, still.empty());
     pending.swap(still);
   }
-  if (P.passes.empty()) emit_pass(0u, 0);
+  if (P.passes.empty()) emit_pass(0u, 0, true);
   P.out_scale = h_carry ? static_cast<float>(1.0 / std::sqrt(2.0)) : 1.0f;
   P.identity = 1;
   for (int q = 0; q < 16; ++q) {

@@ -19,12 +19,22 @@ namespace tqs {
 // locality.  SWAP factors are qubit relabelings done on the host.
 // ---------------------------------------------------------------------------
 
-enum OpKind : uint8_t {
-  OP_DENSE = 0,   // general 2x2 on the (local) target, coefficients as hi + lo
-  OP_ANTI = 1,    // anti-diagonal [[0, m01], [m10, 0]] on the (local) target
-  OP_DIAG = 2,    // diag(d0, d1) on the target, any locality
-  OP_H = 3        // uncontrolled Hadamard without its 2^-1/2: (x0 + x1, x0 - x1);
-                  // the pass scale restores the factor exactly
+// Dispatch code of an op (one jump per op in the kernel):
+//   OPC_H + t      uncontrolled Hadamard without its 2^-1/2 on local position t:
+//                  (x0 + x1, x0 - x1); the pass scale restores the factor exactly
+//   OPC_SWAP + t   anti-diagonal with unit entries (X, CNOT): exchange the pair
+//   OPC_ANTI + t   anti-diagonal [[0, m01], [m10, 0]]
+//   OPC_DENSE + t  general 2x2, coefficients as FP32 hi + lo
+//   OPC_DIAG       diag(d0, d1) on a target of any locality (fields tloc, t, ckind, c)
+// Non-diagonal ops act on the pairs whose low index j0 has its bit set in `act`
+// (all ones, or the control-bit-1 half for a local control), and only in the
+// groups whose base has physical bit `fbit` set (0xFF: no far control).
+enum OpCode : uint8_t {
+  OPC_H = 0,
+  OPC_SWAP = 4,
+  OPC_ANTI = 8,
+  OPC_DENSE = 12,
+  OPC_DIAG = 16
 };
 
 enum CtlKind : uint8_t {
@@ -34,13 +44,13 @@ enum CtlKind : uint8_t {
 };
 
 struct alignas(16) FusedOp {
-  uint8_t kind;    // OpKind
-  uint8_t tloc;    // 1: target is local position `t`; 0: target is physical bit `t`
+  uint8_t code;    // OpCode (+ local target position for non-diagonal ops)
+  uint8_t tloc;    // OPC_DIAG: 1 if the target is local position `t`, else physical bit `t`
   uint8_t t;
-  uint8_t ckind;   // CtlKind
+  uint8_t ckind;   // OPC_DIAG: CtlKind of the control `c`
   uint8_t c;
-  uint8_t unit;    // OP_ANTI with m01 == m10 == 1 (X, CNOT)
-  uint8_t pad0[2];
+  uint8_t fbit;    // non-diagonal: physical bit of a far control, 0xFF if none
+  uint16_t act;    // non-diagonal: active-pair mask over the 16 local indices
   uint32_t pad1[2];
   float2 m[4];     // DENSE: m00 m01 m10 m11 | ANTI: -, m01, m10, - | DIAG: d0, d1, d1/d0, -
   float2 lo[4];    // DENSE: m - m_fp32 rounded to FP32 (the FP64 matrix is m + lo)

@@ -14,7 +14,7 @@ from oracle import fsv_route, kron_route
 from paper_2305_14398_gb300 import binding as B
 from paper_2305_14398_gb300 import workloads as W
 
-DENSE, ANTI, DIAG, HAD = 0, 1, 2, 3
+OPC_H, OPC_SWAP, OPC_ANTI, OPC_DENSE, OPC_DIAG = 0, 4, 8, 12, 16
 NONE, LOCAL, FAR = 0, 1, 2
 
 
@@ -41,13 +41,10 @@ def replay(n, passes, ops, pos, out_scale=1.0):
         sc = np.ones(G, dtype=np.complex128)
         b0, cnt = int(ps["op_begin"]), int(ps["op_count"])
         for op in ops[b0:b0 + cnt]:
-            kind, tloc, t, ckind, c = (int(op[k]) for k in ("kind", "tloc", "t", "ckind", "c"))
-            m = op["m"].astype(np.complex128) + (op["lo"].astype(np.complex128) if kind == DENSE else 0)
-            if kind == HAD:
-                assert tloc == 1 and ckind == NONE
-                m = np.array([1, 1, 1, -1], dtype=np.complex128)
-                kind = DENSE
-            if kind == DIAG:
+            code = int(op["code"])
+            m = op["m"].astype(np.complex128)
+            if code == OPC_DIAG:
+                tloc, t, ckind, c = (int(op[k]) for k in ("tloc", "t", "ckind", "c"))
                 d0, d1, r = m[0], m[1], m[2]
                 if tloc:
                     if ckind == LOCAL:
@@ -66,10 +63,17 @@ def replay(n, passes, ops, pos, out_scale=1.0):
                         on = np.ones(G, bool) if ckind == NONE else ((base >> c) & 1) == 1
                         sc[on] *= v[on]
                 continue
-            assert tloc == 1, "non-diagonal op with a far target"
-            if ckind == LOCAL:
-                assert c != t
-            on = np.ones(G, bool) if ckind != FAR else ((base >> c) & 1) == 1
+            assert code < OPC_DIAG
+            t = code & 3
+            assert int(op["t"]) == t and int(op["tloc"]) == 1
+            kind = code & ~3
+            if kind == OPC_DENSE:
+                m = m + op["lo"].astype(np.complex128)
+            elif kind == OPC_H:
+                assert int(op["fbit"]) == 255 and int(op["act"]) == 0xFFFF
+                m = np.array([1, 1, 1, -1], dtype=np.complex128)
+            fbit, act = int(op["fbit"]), int(op["act"])
+            on = np.ones(G, bool) if fbit == 255 else ((base >> fbit) & 1) == 1
             for j in range(16):
                 if (j >> t) & 1:
                     a[:, j] *= pend[:, t]
@@ -77,13 +81,13 @@ def replay(n, passes, ops, pos, out_scale=1.0):
             for p in range(8):
                 j0 = ((p >> t) << (t + 1)) | (p & ((1 << t) - 1))
                 j1 = j0 | (1 << t)
-                if ckind == LOCAL and not (j0 >> c) & 1:
+                if not (act >> j0) & 1:
                     continue
                 x0, x1 = a[:, j0].copy(), a[:, j1].copy()
-                if kind == DENSE:
+                if kind in (OPC_DENSE, OPC_H):
                     y0 = m[0] * x0 + m[1] * x1
                     y1 = m[2] * x0 + m[3] * x1
-                elif op["unit"]:
+                elif kind == OPC_SWAP:
                     y0, y1 = x1, x0
                 else:
                     y0, y1 = m[1] * x1, m[2] * x0
@@ -162,7 +166,7 @@ def test_ghz_steps_and_passes():
         assert B.tqs_circuit_info(c)[2] == n
         passes, ops, pos, osc = B.tqs_circuit_program(c)
         assert len(ops) == n and len(passes) <= 4
-        assert ops[0]["kind"] == HAD and osc == np.float32(2 ** -0.5)
+        assert ops[0]["code"] == OPC_H and osc == np.float32(2 ** -0.5)
     finally:
         B.tqs_circuit_destroy(c)
 
