@@ -50,6 +50,7 @@ def parse_args():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-chain", action="store_true")
     return ap.parse_args()
 
 
@@ -364,6 +365,10 @@ def run_tqs(args):
                        "path": "tqs_batch_create_packed (host gate arrays) + tqs_batch_run_host "
                                "(pinned host buffers) + tqs_batch_destroy"}
 
+    # ------------------------------------------- circuit-unitary chain (a5)
+    if not args.no_chain and rank == 0:
+        line["chain"] = bench_chain(B, W, torch, peaks)
+
     # ---------------------------------------------------------- CPU oracle
     if not args.no_cpu_baseline and rank == 0:
         r = oracle_sample([0, 1, 2, 3])
@@ -380,6 +385,51 @@ def run_tqs(args):
     if dist:
         dist.destroy_process_group()
     return 0
+
+
+def bench_chain(B, W, torch, peaks):
+    """Algorithm 1 on the random layered circuits (20 layers, 40 steps) at
+    n = 12, 13, 14: tensor-core BF16x3 chain (and FP32 SIMT at n = 12), with the
+    error of sampled columns against the FP64 oracle at n = 12."""
+    import numpy as np
+    from oracle import fsv_route
+
+    peak = peaks.get("bf16_tflops", 1927.5)
+    out = {"workload": "random layered: 20 x (U3 on every qubit + CNOTs on n/2 seeded pairs), "
+                       "40 steps, U = S_40 ... S_1",
+           "tensor_peak_tflops": peak, "peak_source": "measured bf16 burst"}
+    for n, prec, reps in [(12, B.PREC_TC_BF16X3, 3), (12, B.PREC_FP32_SIMT, 1),
+                          (13, B.PREC_TC_BF16X3, 2), (14, B.PREC_TC_BF16X3, 1)]:
+        ops = W.random_layered(n, 20, (2, n))
+        c = B.circuit_from_ops(n, ops)
+        U = torch.empty((1 << n, 1 << n), dtype=torch.complex64, device="cuda")
+        B.tqs_circuit_unitary(c, prec, U)
+        torch.cuda.synchronize()
+        s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        s.record()
+        for _ in range(reps):
+            B.tqs_circuit_unitary(c, prec, U)
+        e.record()
+        torch.cuda.synchronize()
+        sec = s.elapsed_time(e) / 1e3 / reps
+        N = 1 << n
+        gemms = B.tqs_circuit_info(c)[2] - 1
+        key = f"n{n}_{'tc_bf16x3' if prec == B.PREC_TC_BF16X3 else 'fp32_simt'}"
+        rec = {"ms": 1e3 * sec, "gemms": gemms,
+               "useful_complex_gflops": 8.0 * N ** 3 * gemms / sec / 1e9}
+        if prec == B.PREC_TC_BF16X3:
+            issued = 18.0 * N ** 3 * gemms / sec / 1e12  # 3 real GEMMs x 3 split products
+            rec["issued_tensor_tflops"] = issued
+            rec["tensor_frac"] = issued / peak
+        if n == 12:
+            cols = [0, 1, 777, 2048, 4095]
+            got = U[:, cols].cpu().numpy().astype(np.complex128)
+            rec["max_abs_err_vs_oracle"] = float(np.max(np.abs(got - fsv_route.unitary_columns(n, ops, cols))))
+        out[key] = rec
+        B.tqs_circuit_destroy(c)
+        del U
+        torch.cuda.empty_cache()
+    return out
 
 
 def main():

@@ -173,7 +173,10 @@ tqs_status tqs_materialize_step(tqs_circuit* c, int step, tqs_c64* d_S, void* st
  * skipped), in the arithmetic `prec` (tqs_prec).
  *   d_U : 2^n x 2^n tqs_c64, row-major, d_U[r * 2^n + c] = <r|U|c>.
  * n <= TQS_MAX_DENSE_QUBITS; tensor-core precisions need n >= 7.
- * Scratch: about 28 * 4^n bytes (operand planes), released with the circuit. */
+ * Scratch (cached on the circuit): 36 * 4^n bytes for TQS_PREC_TC_BF16X3
+ * (three matrices of six BF16 planes), 24 * 4^n for TQS_PREC_FP32_SIMT.
+ * The tensor-core form synchronises `stream` before returning and returns
+ * TQS_ERR_TIMEOUT if one of its bounded device waits ran out. */
 tqs_status tqs_circuit_unitary(tqs_circuit* c, int prec, tqs_c64* d_U, void* stream);
 
 /* ---------------------------------------------------------- probabilities

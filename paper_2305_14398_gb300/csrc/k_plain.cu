@@ -2,38 +2,17 @@
 // written out as a dense matrix) and stage 6 applied per step (eq. 11, dense
 // matrix-vector product).  This is the baseline the fused kernel is measured
 // against; both kernels stream the 2^n x 2^n complex64 matrix through HBM.
+#include "step_entry.h"
 #include "tqs_internal.h"
 
 namespace tqs {
 namespace {
 
-__device__ __forceinline__ float2 cmul(float2 a, float2 b) {
-  return make_float2(fmaf(a.x, b.x, -a.y * b.y), fmaf(a.x, b.y, a.y * b.x));
-}
-
 // S[r][c] = prod_f M_f[bits_f(r)][bits_f(c)] when r and c agree on every idle
-// qubit (identity factors), else 0.  Factors are staged in shared memory.
+// qubit (identity factors), else 0 (step_entry.h).  Factors are staged in
+// shared memory.
 constexpr int kMatThreads = 256;
 constexpr int kMaxFactors = 16;
-
-__device__ __forceinline__ float2 entry(const StepFactor* fs, int nf, uint32_t idle, uint32_t r,
-                                        uint32_t c) {
-  if ((r ^ c) & idle) return make_float2(0.f, 0.f);
-  float2 v = make_float2(1.f, 0.f);
-  for (int k = 0; k < nf; ++k) {
-    const StepFactor& f = fs[k];
-    int idx;
-    if (f.nq == 1) {
-      idx = ((r >> f.q0) & 1) * 2 + ((c >> f.q0) & 1);
-    } else {
-      const int rr = (((r >> f.q0) & 1) << 1) | ((r >> f.q1) & 1);
-      const int cc = (((c >> f.q0) & 1) << 1) | ((c >> f.q1) & 1);
-      idx = rr * 4 + cc;
-    }
-    v = cmul(v, f.m[idx]);
-  }
-  return v;
-}
 
 __global__ void __launch_bounds__(kMatThreads)
     materialize_kernel(const StepFactor* __restrict__ factors, int nf, uint32_t idle, int n,
@@ -49,8 +28,8 @@ __global__ void __launch_bounds__(kMatThreads)
     const int64_t flat = e << 1;
     const uint32_t r = static_cast<uint32_t>(flat >> n);
     const uint32_t c = static_cast<uint32_t>(flat & (N - 1));
-    const float2 v0 = entry(fs, nf, idle, r, c);
-    const float2 v1 = entry(fs, nf, idle, r, c + 1);
+    const float2 v0 = step_entry(fs, nf, idle, r, c);
+    const float2 v1 = step_entry(fs, nf, idle, r, c + 1);
     __stcs(reinterpret_cast<float4*>(S + flat), make_float4(v0.x, v0.y, v1.x, v1.y));
   }
 }

@@ -401,6 +401,7 @@ struct tqs_circuit {
   DevBuf d_partials;  // probability partials
   // chain scratch
   DevBuf d_chain;
+  DevBuf d_err;
 };
 
 extern "C" {
@@ -1069,8 +1070,46 @@ tqs_status tqs_batch_destroy(tqs_batch* b) {
 }
 
 tqs_status tqs_circuit_unitary(tqs_circuit* c, int prec, tqs_c64* d_U, void* stream) {
-  (void)c; (void)prec; (void)d_U; (void)stream;
-  return fail(TQS_ERR_UNSUPPORTED, "tqs_circuit_unitary: not built yet");
+  if (!c || !d_U) return fail(TQS_ERR_ARG, "tqs_circuit_unitary: NULL argument");
+  if (!aligned16(d_U)) return fail(TQS_ERR_ARG, "tqs_circuit_unitary: d_U must be 16-byte aligned");
+  if (c->n > TQS_MAX_DENSE_QUBITS)
+    return fail(TQS_ERR_TOO_MANY_QUBITS, "tqs_circuit_unitary: n %d > %d", c->n, TQS_MAX_DENSE_QUBITS);
+  if (prec == TQS_PREC_TC_TF32X3)
+    return fail(TQS_ERR_UNSUPPORTED, "tqs_circuit_unitary: TF32x3 is not built");
+  if (prec != TQS_PREC_FP32_SIMT && prec != TQS_PREC_TC_BF16X3)
+    return fail(TQS_ERR_ARG, "tqs_circuit_unitary: unknown precision %d", prec);
+  if (prec == TQS_PREC_TC_BF16X3 && c->n < 7)
+    return fail(TQS_ERR_ARG, "tqs_circuit_unitary: the tensor-core chain needs n >= 7");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  tqs_status st = upload_factors(c, s);
+  if (st != TQS_OK) return st;
+  float2* U = reinterpret_cast<float2*>(d_U);
+  if (c->nsteps <= 1) {
+    // Algorithm 1 with at most one step: U = S_1 (or the identity).
+    StepDesc d = c->nsteps == 1 ? c->steps[0] : StepDesc{0, 0, (1u << c->n) - 1u, 0};
+    TQS_CUDA(launch_materialize(c->d_factors.as<StepFactor>(), d, c->n, U, s),
+             "tqs_circuit_unitary: materialize");
+    return TQS_OK;
+  }
+  if (prec == TQS_PREC_FP32_SIMT) {
+    TQS_CUDA(c->d_chain.ensure(chain_simt_scratch_bytes(c->n)), "tqs_circuit_unitary: cudaMalloc");
+    TQS_CUDA(chain_simt(c->d_factors.as<StepFactor>(), c->steps.data(), c->nsteps, c->n, U,
+                        c->d_chain.p, s),
+             "tqs_circuit_unitary: SIMT chain");
+    return TQS_OK;
+  }
+  TQS_CUDA(c->d_chain.ensure(chain_tc_scratch_bytes(c->n)), "tqs_circuit_unitary: cudaMalloc");
+  TQS_CUDA(c->d_err.ensure(sizeof(int)), "tqs_circuit_unitary: cudaMalloc");
+  TQS_CUDA(cudaMemsetAsync(c->d_err.p, 0, sizeof(int), s), "tqs_circuit_unitary: memset");
+  TQS_CUDA(chain_tc(c->d_factors.as<StepFactor>(), c->steps.data(), c->nsteps, c->n, U,
+                    c->d_chain.p, c->d_err.as<int>(), s),
+           "tqs_circuit_unitary: tensor-core chain");
+  int err = 0;
+  TQS_CUDA(cudaMemcpyAsync(&err, c->d_err.p, sizeof(int), cudaMemcpyDeviceToHost, s),
+           "tqs_circuit_unitary: read status");
+  TQS_CUDA(cudaStreamSynchronize(s), "tqs_circuit_unitary: sync");
+  if (err) return fail(TQS_ERR_TIMEOUT, "tqs_circuit_unitary: a device wait ran out");
+  return TQS_OK;
 }
 
 }  // extern "C"
