@@ -51,6 +51,7 @@ def parse_args():
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-chain", action="store_true")
+    ap.add_argument("--no-serving", action="store_true")
     return ap.parse_args()
 
 
@@ -204,6 +205,7 @@ def smi_index(local):
 # ----------------------------------------------------------------- GPU arm
 
 def run_tqs(args):
+    import numpy as np
     import torch
 
     from paper_2305_14398_gb300 import binding as B
@@ -368,6 +370,20 @@ def run_tqs(args):
     # ------------------------------------------- circuit-unitary chain (a5)
     if not args.no_chain and rank == 0:
         line["chain"] = bench_chain(B, W, torch, peaks)
+
+    # ----------------------------------------------------- serving loop (a8)
+    if not args.no_serving and rank == 0:
+        from paper_2305_14398_gb300 import serve
+        reqs = W.serving_requests(20000, 2000.0)
+        r = serve.replay(reqs, budget_bytes=120 * 10 ** 9, max_inflight=4, max_batch=256)
+        line["serving"] = {
+            "workload": "20000 simulate requests, Poisson 2000 req/s (seeded), n ~ U{6..16}, "
+                        "25% each GHZ / Deutsch-Jozsa / QFT / random mixed; HBM budget 120 GB; "
+                        "continuous batching, 4 batches in flight",
+            "p50_ms": r["p50_ms"], "p99_ms": r["p99_ms"], "mean_ms": r["mean_ms"],
+            "max_ms": r["max_ms"], "completed_rps": r["throughput_rps"], "wall_s": r["wall_s"],
+            "norm_max_err": float(np.max(np.abs(r["norms"] - 1.0))),
+            "peak_device_bytes": r["stats"]["peak_bytes"]}
 
     # ---------------------------------------------------------- CPU oracle
     if not args.no_cpu_baseline and rank == 0:

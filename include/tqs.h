@@ -261,6 +261,59 @@ tqs_status tqs_batch_run_host(tqs_batch* b, tqs_c64* h_states, double* h_probs,
 /* Destroy the batch and its device memory.  NULL is accepted. */
 tqs_status tqs_batch_destroy(tqs_batch* b);
 
+/* ------------------------------------------------------------------ server
+ * Continuous batching of simulate requests (simulateFullState of Sec. 5.2
+ * served to many callers; the serving loop itself has no counterpart in the
+ * paper).  The server owns no thread: the caller submits requests as they
+ * arrive and calls tqs_server_poll often.  Each poll
+ *   1. reaps batches whose device work has finished (CUDA events), moves
+ *      their results to host memory and releases their device bytes from
+ *      the budget, reporting the finished tags;
+ *   2. admits queued requests in arrival order while their device bytes
+ *      (program, state, norm, and for n >= 15 a 512 KiB work slot) fit the
+ *      budget, and launches each admitted group as one batch of the
+ *      persistent fused step kernels on a free stream, so that requests that
+ *      arrive while others run start as soon as a stream and memory are free,
+ *      and up to max_inflight batches overlap on the device.
+ * A request's result is bitwise the one tqs_simulate gives for the same
+ * circuit: batching never changes the arithmetic. */
+
+typedef struct tqs_server tqs_server;
+
+/* hbm_budget_bytes: device bytes that in-flight batches may hold at once;
+ * max_inflight: concurrent batches (streams), 1..64; max_batch: requests per
+ * batch.  Device memory is taken stream-ordered (cudaMallocAsync) per batch
+ * and returned when the batch's work is done. */
+tqs_status tqs_server_create(size_t hbm_budget_bytes, int max_inflight, int max_batch,
+                             tqs_server** out);
+
+/* Queue one request: a circuit of n_qubits given by host gate arrays in the
+ * layout of tqs_batch_create_packed (kind[n_gates], qubits[2*n_gates],
+ * params[8*n_gates]).  `tag` names the result (must not name an untaken
+ * result).  Preconditions are checked as in tqs_add_gate; a request that
+ * alone exceeds the budget returns TQS_ERR_BUDGET. */
+tqs_status tqs_server_submit_packed(tqs_server* s, int64_t tag, int n_qubits, int n_gates,
+                                    const int32_t* h_kind, const int32_t* h_qubits,
+                                    const double* h_params);
+
+/* Reap finished batches, admit and launch queued requests (non-blocking).
+ * h_done_tags[max_done] receives the tags finished since the last poll and
+ * *n_done their number; a finished batch with more requests than the free
+ * room is reported by a later poll. */
+tqs_status tqs_server_poll(tqs_server* s, int64_t* h_done_tags, int max_done, int* n_done);
+
+/* Copy a finished request's state (2^n tqs_c64, host, or NULL) and FP64 norm
+ * (host, or NULL) and forget it.  TQS_ERR_STATE if `tag` is not finished. */
+tqs_status tqs_server_take(tqs_server* s, int64_t tag, tqs_c64* h_state, double* h_norm);
+
+/* Counters (each may be NULL): queued requests, requests in flight, requests
+ * finished so far, device bytes held now and at most so far. */
+tqs_status tqs_server_stats(const tqs_server* s, int64_t* queued, int64_t* inflight,
+                            int64_t* done, int64_t* bytes_in_use, int64_t* peak_bytes);
+
+/* Wait for in-flight work, then free everything.  NULL is accepted. */
+tqs_status tqs_server_destroy(tqs_server* s);
+
 /* ------------------------------------------------------------------ misc */
 
 /* Thread-local message of the last failed call ("" if none). */

@@ -69,6 +69,13 @@ _SIGS = {
     "tqs_batch_run": (_i, [_vp, _vp, _vp, _vp, _i, _vp]),
     "tqs_batch_run_host": (_i, [_vp, _vp, _vp, _vp, _vp]),
     "tqs_batch_destroy": (_i, [_vp]),
+    "tqs_server_create": (_i, [ctypes.c_size_t, _i, _i, ctypes.POINTER(_vp)]),
+    "tqs_server_submit_packed": (_i, [_vp, _i64, _i, _i, _vp, _vp, _vp]),
+    "tqs_server_poll": (_i, [_vp, _vp, _i, _pi]),
+    "tqs_server_take": (_i, [_vp, _i64, _vp, _vp]),
+    "tqs_server_stats": (_i, [_vp, ctypes.POINTER(_i64), ctypes.POINTER(_i64),
+                              ctypes.POINTER(_i64), ctypes.POINTER(_i64), ctypes.POINTER(_i64)]),
+    "tqs_server_destroy": (_i, [_vp]),
     "tqs_last_error": (ctypes.c_char_p, []),
     "tqs_status_string": (ctypes.c_char_p, [_i]),
     "tqs_launch_count": (_i64, []),
@@ -301,3 +308,59 @@ def tqs_last_error() -> str:
 
 def tqs_status_string(s: int) -> str:
     return lib().tqs_status_string(int(s)).decode()
+
+
+# ------------------------------------------------------------------ server
+
+def tqs_server_create(hbm_budget_bytes: int, max_inflight: int = 4, max_batch: int = 256) -> int:
+    h = _vp()
+    _check(lib().tqs_server_create(int(hbm_budget_bytes), int(max_inflight), int(max_batch),
+                                   ctypes.byref(h)))
+    return h.value
+
+
+def pack_request(ops):
+    """(kind, qubits, params) host arrays of one request."""
+    g = max(len(ops), 1)
+    kind = np.zeros(g, dtype=np.int32)
+    qub = np.zeros((g, 2), dtype=np.int32)
+    par = np.zeros((g, 8), dtype=np.float64)
+    for k, (name, qs, ps) in enumerate(ops):
+        kind[k] = GATE_IDS[name]
+        qub[k, :len(qs)] = qs
+        par[k, :len(ps)] = ps
+    return kind, qub, par, len(ops)
+
+
+def tqs_server_submit_packed(sv: int, tag: int, n_qubits: int, packed) -> None:
+    kind, qub, par, n_gates = packed
+    _check(lib().tqs_server_submit_packed(sv, int(tag), int(n_qubits), int(n_gates),
+                                          kind.ctypes.data, qub.ctypes.data, par.ctypes.data))
+
+
+def tqs_server_poll(sv: int, max_done: int = 4096) -> np.ndarray:
+    buf = np.empty(max_done, dtype=np.int64)
+    nd = ctypes.c_int()
+    _check(lib().tqs_server_poll(sv, buf.ctypes.data, int(max_done), ctypes.byref(nd)))
+    return buf[:nd.value].copy()
+
+
+def tqs_server_take(sv: int, tag: int, n_qubits=None):
+    """(state or None, norm) of a finished request."""
+    norm = ctypes.c_double()
+    if n_qubits is None:
+        _check(lib().tqs_server_take(sv, int(tag), None, ctypes.byref(norm)))
+        return None, norm.value
+    st = np.empty(1 << n_qubits, dtype=np.complex64)
+    _check(lib().tqs_server_take(sv, int(tag), st.ctypes.data, ctypes.byref(norm)))
+    return st, norm.value
+
+
+def tqs_server_stats(sv: int) -> dict:
+    v = [_i64() for _ in range(5)]
+    _check(lib().tqs_server_stats(sv, *[ctypes.byref(x) for x in v]))
+    return dict(zip(("queued", "inflight", "done", "bytes_in_use", "peak_bytes"), [x.value for x in v]))
+
+
+def tqs_server_destroy(sv: int) -> None:
+    _check(lib().tqs_server_destroy(sv))

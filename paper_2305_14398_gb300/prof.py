@@ -2,6 +2,8 @@
 
     python -m paper_2305_14398_gb300.prof COUNT {mix|batch} REPS
 
+chain: the 40-step random layered circuit-unitary chain at n = COUNT
+       (tensor-core BF16x3);
 mix:   COUNT paper-shaped 11-qubit circuits (GHZ / DJ-constant / DJ-balanced /
        QFT, 25 % each); batch: the first COUNT circuits of the random batched
        workload (n = 4..14, depth 5..40).  Runs tqs_batch_run REPS times
@@ -15,10 +17,28 @@ from . import binding as B
 from . import workloads as W
 
 
+def chain(n, reps):
+    ops = W.random_layered(n, 20, (2, n))
+    c = B.circuit_from_ops(n, ops)
+    U = torch.empty((1 << n, 1 << n), dtype=torch.complex64, device="cuda")
+    for _ in range(reps):
+        B.tqs_circuit_unitary(c, B.PREC_TC_BF16X3, U)
+    torch.cuda.synchronize()
+    s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    s.record()
+    B.tqs_circuit_unitary(c, B.PREC_TC_BF16X3, U)
+    e.record()
+    torch.cuda.synchronize()
+    print("chain", n, "ms %.3f" % s.elapsed_time(e))
+    B.tqs_circuit_destroy(c)
+
+
 def main(argv):
     count = int(argv[1]) if len(argv) > 1 else 2048
     kind = argv[2] if len(argv) > 2 else "mix"
     reps = int(argv[3]) if len(argv) > 3 else 4
+    if kind == "chain":
+        return chain(count, reps)
     if kind == "mix":
         circs = [(11, ops) for _, ops in W.paper_mix(11, count)]
     else:

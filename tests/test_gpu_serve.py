@@ -1,0 +1,70 @@
+"""The serving loop (continuous batching, tqs_server_*) on the GPU.
+
+* every request of a mixed stream finishes; its norm is within 1e-6 of 1 for
+  n <= 14 (the stated range) and within 3e-6 for the deeper n = 15, 16 states;
+* sampled results match the FP64 oracle (1e-5) and are bitwise the result of
+  the same circuit simulated alone (tqs_simulate): batching does not change them;
+* a small HBM budget forces queueing: every request still finishes and the
+  device bytes held never exceed the budget.
+"""
+import numpy as np
+import pytest
+
+from oracle import fsv_route
+from paper_2305_14398_gb300 import binding as B
+from paper_2305_14398_gb300 import serve
+from paper_2305_14398_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    B.lib()
+
+
+def check_norms(reqs, norms):
+    ns = np.array([q[2] for q in reqs])
+    err = np.abs(norms - 1.0)
+    assert np.max(err[ns <= 14], initial=0.0) <= 1e-6
+    assert np.max(err[ns > 14], initial=0.0) <= 3e-6
+
+
+def alone(n, ops):
+    c = B.circuit_from_ops(n, ops)
+    try:
+        out = torch.empty(1 << n, dtype=torch.complex64, device="cuda")
+        norm = torch.empty(1, dtype=torch.float64, device="cuda")
+        B.tqs_simulate(c, out, norm=norm)
+        torch.cuda.synchronize()
+        return out.cpu().numpy(), float(norm.cpu()[0])
+    finally:
+        B.tqs_circuit_destroy(c)
+
+
+def test_serving_mixed_stream_alone_equals_mix():
+    reqs = W.serving_requests(300, rate_hz=20000.0, seed_tag=41)
+    r = serve.replay(reqs, budget_bytes=8 << 30, max_inflight=4, max_batch=64, keep_states=True)
+    assert np.all(np.isfinite(r["latency_s"]))
+    check_norms(reqs, r["norms"])
+    for i in range(0, len(reqs), 23):
+        _, _, n, ops = reqs[i]
+        st, nm = alone(n, ops)
+        assert np.array_equal(st.view(np.uint32), r["states"][i].view(np.uint32)), (i, n)
+        assert nm == r["norms"][i]
+        if n <= 14:
+            assert np.max(np.abs(r["states"][i].astype(np.complex128) - fsv_route.simulate(n, ops))) <= 1e-5
+
+
+def test_serving_small_budget_forces_queueing():
+    reqs = W.serving_requests(150, rate_hz=50000.0, n_lo=12, n_hi=16, seed_tag=42)
+    budget = 64 << 20
+    r = serve.replay(reqs, budget_bytes=budget, max_inflight=3, max_batch=32)
+    assert np.all(np.isfinite(r["latency_s"]))
+    check_norms(reqs, r["norms"])
+    assert r["stats"]["peak_bytes"] <= budget
+    assert r["stats"]["done"] == len(reqs)
+    assert r["stats"]["bytes_in_use"] == 0

@@ -224,3 +224,29 @@ def test_library_exports_every_declared_symbol():
     assert len(names) >= 20
     missing = [n for n in names if not hasattr(L, n)]
     assert not missing, missing
+
+
+def test_server_host_side():
+    """Server request validation and budget admission, on the host only."""
+    sv = B.tqs_server_create(1 << 30, 2, 16)
+    try:
+        B.tqs_server_submit_packed(sv, 0, 5, B.pack_request(W.ghz_chain(5)))
+        B.tqs_server_submit_packed(sv, 1, 16, B.pack_request(W.qft(16)))
+        assert B.tqs_server_stats(sv)["queued"] == 2
+        with pytest.raises(B.TqsError) as e:
+            B.tqs_server_submit_packed(sv, 2, 3, B.pack_request([("cx", (0, 3), ())]))
+        assert e.value.name == "TQS_ERR_QUBIT_RANGE"
+        with pytest.raises(B.TqsError) as e:
+            B.tqs_server_take(sv, 0)
+        assert e.value.name == "TQS_ERR_STATE"
+    finally:
+        B.tqs_server_destroy(sv)
+    small = B.tqs_server_create(1 << 16, 1, 4)
+    try:
+        with pytest.raises(B.TqsError) as e:
+            B.tqs_server_submit_packed(small, 0, 14, B.pack_request(W.ghz_chain(14)))
+        assert e.value.name == "TQS_ERR_BUDGET"
+    finally:
+        B.tqs_server_destroy(small)
+    with pytest.raises(B.TqsError):
+        B.tqs_server_create(0, 1, 1)
