@@ -224,6 +224,8 @@ def run_tqs(args):
 
     # ---------------------------------------------------------- inputs
     circs = [(N_QUBITS, ops) for _, ops in W.paper_mix(N_QUBITS, args.batch, seed_tag=1 + 1000 * rank)]
+    from paper_2305_14398_gb300 import autotune
+    tuned = autotune.tune_warps_per_cta(circs, sample=4096)
     arrays = B.pack_ops(circs)
     b = B.tqs_batch_create_packed(*arrays)
     count, total, offs, steps_total, prog_bytes = B.tqs_batch_info(b, extra=True)
@@ -298,7 +300,9 @@ def run_tqs(args):
         "config": {"workload": WORKLOAD, "n_qubits": N_QUBITS, "circuits_per_gpu": count,
                    "steps_per_batch": steps_total, "parallelism": f"replicas x{world}",
                    "l2": "flushed between timed steps (256 MiB write, not timed)",
-                   "outputs": "state (complex64) + |psi|^2 (f64) + norm (f64) per circuit"},
+                   "outputs": "state (complex64) + |psi|^2 (f64) + norm (f64) per circuit",
+                   "launch": {"warps_per_cta": tuned["warps"], "autotune_ms": tuned["timings_ms"],
+                              "autotune_source": tuned["source"]}},
         "dense_equiv_complex_gflops": dense_flops * world * args.steps / total_s / 1e9,
         "roofline": {"bound": "hbm", "achieved": achieved_gbs, "peak": hbm_peak,
                      "unit": "GB/s", "frac": achieved_gbs / hbm_peak,

@@ -314,6 +314,24 @@ tqs_status tqs_server_stats(const tqs_server* s, int64_t* queued, int64_t* infli
 /* Wait for in-flight work, then free everything.  NULL is accepted. */
 tqs_status tqs_server_destroy(tqs_server* s);
 
+/* ----------------------------------------------------------------- options
+ * Launch options read when a batch (or a single simulate) plans its launches.
+ * TQS_OPT_WARPS_PER_CTA, key = log2 of the amplitudes of a warp's shared
+ * memory slice (4..11), value = warps per CTA of the warp-team kernel (1..16;
+ * default 4; capped so that a CTA's slices fit 200 KiB).  Options change launch
+ * shapes only, never a result bit (a circuit always runs on one warp). */
+#define TQS_OPT_WARPS_PER_CTA 1
+
+tqs_status tqs_set_option(int option, int key, int64_t value);
+tqs_status tqs_get_option(int option, int key, int64_t* value);
+
+/* Self-test of the bounded device waits (no counterpart in the paper): one
+ * thread waits on an mbarrier that nothing completes, gives up after
+ * `wait_cycles` SM cycles (1 .. 2^31), records the time-out in a device status
+ * word and returns.  Returns TQS_ERR_TIMEOUT when the wait ran out (the
+ * expected result), synchronising `stream`; the context stays usable. */
+tqs_status tqs_selftest_wait_timeout(int64_t wait_cycles, void* stream);
+
 /* ------------------------------------------------------------------ misc */
 
 /* Thread-local message of the last failed call ("" if none). */

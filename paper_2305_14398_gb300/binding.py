@@ -76,6 +76,9 @@ _SIGS = {
     "tqs_server_stats": (_i, [_vp, ctypes.POINTER(_i64), ctypes.POINTER(_i64),
                               ctypes.POINTER(_i64), ctypes.POINTER(_i64), ctypes.POINTER(_i64)]),
     "tqs_server_destroy": (_i, [_vp]),
+    "tqs_set_option": (_i, [_i, _i, _i64]),
+    "tqs_get_option": (_i, [_i, _i, ctypes.POINTER(_i64)]),
+    "tqs_selftest_wait_timeout": (_i, [_i64, _vp]),
     "tqs_last_error": (ctypes.c_char_p, []),
     "tqs_status_string": (ctypes.c_char_p, [_i]),
     "tqs_launch_count": (_i64, []),
@@ -364,3 +367,22 @@ def tqs_server_stats(sv: int) -> dict:
 
 def tqs_server_destroy(sv: int) -> None:
     _check(lib().tqs_server_destroy(sv))
+
+
+# ----------------------------------------------------------------- options
+
+OPT_WARPS_PER_CTA = 1
+
+
+def tqs_set_option(option: int, key: int, value: int) -> None:
+    _check(lib().tqs_set_option(int(option), int(key), int(value)))
+
+
+def tqs_get_option(option: int, key: int) -> int:
+    v = _i64()
+    _check(lib().tqs_get_option(int(option), int(key), ctypes.byref(v)))
+    return v.value
+
+
+def tqs_selftest_wait_timeout(wait_cycles: int, stream=None) -> None:
+    _check(lib().tqs_selftest_wait_timeout(int(wait_cycles), _stream(stream)))

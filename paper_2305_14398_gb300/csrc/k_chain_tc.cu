@@ -323,7 +323,28 @@ cudaError_t launch_gen(const StepFactor* d_factors, const StepDesc& st, int n, i
   return cudaGetLastError();
 }
 
+__global__ void wait_selftest_kernel(int* status, long long wait_cycles) {
+  __shared__ uint64_t bar;
+  mbar_init(smem_u32(&bar), 1);
+  fence_barrier_init();
+  const uint32_t b = smem_u32(&bar);
+  if (mbar_try_wait(b, 0)) return;  // nothing arrives: never taken
+  const long long t0 = clock64();
+  while (!mbar_try_wait(b, 0)) {
+    if (clock64() - t0 > wait_cycles) {
+      atomicExch(status, 1);
+      return;
+    }
+  }
+}
+
 }  // namespace
+
+cudaError_t launch_wait_selftest(int* status, long long wait_cycles, cudaStream_t s) {
+  wait_selftest_kernel<<<1, 1, 0, s>>>(status, wait_cycles);
+  count_launches(1);
+  return cudaGetLastError();
+}
 
 size_t chain_tc_scratch_bytes(int n) {
   const size_t N = size_t(1) << n;

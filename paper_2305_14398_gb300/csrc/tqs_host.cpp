@@ -592,11 +592,14 @@ struct LaunchPlan {
   int grid;
 };
 
+// TQS_OPT_WARPS_PER_CTA table, indexed by the warp slice's log2 amplitudes.
+static std::atomic<int> g_warps_for_q[16] = {4, 4, 4, 4, 4, 4, 4, 4, 4, 4, 4, 4, 4, 4, 4, 4};
+
 static LaunchPlan plan_for(int team, int max_nint, int jobs, int warps_hint) {
   LaunchPlan lp{team, 1, 4, 1};
   if (team == TEAM_WARP) {
     lp.slice_q = std::max(4, max_nint);
-    int w = warps_hint > 0 ? warps_hint : 4;
+    int w = warps_hint > 0 ? warps_hint : g_warps_for_q[lp.slice_q].load();
     const size_t slice = (size_t(1) << lp.slice_q) * sizeof(float2);
     while (w > 1 && size_t(w) * slice > 200 * 1024) w >>= 1;
     lp.warps = w;
@@ -954,7 +957,7 @@ static tqs_status batch_upload(tqs_batch* b, cudaStream_t s) {
                            b->order.size() * sizeof(int32_t), cudaMemcpyHostToDevice, s),
            "tqs_batch: upload order");
   for (int t = 0; t < 3; ++t)
-    b->plans[t] = plan_for(t, b->max_nint[t], b->n_team[t], 4);
+    b->plans[t] = plan_for(t, b->max_nint[t], b->n_team[t], 0);
   if (b->n_team[TEAM_GLOBAL] > 0)
     TQS_CUDA(b->d_gscratch.ensure(size_t(b->plans[TEAM_GLOBAL].grid) *
                                   (size_t(1) << kGlobalSlotQ) * sizeof(float2)),
@@ -1222,7 +1225,7 @@ static tqs_status server_launch(tqs_server* sv, SrvSlot& sl) {
   }
   const size_t amps = static_cast<size_t>(sl.offsets.back());
   LaunchPlan plans[3];
-  for (int t = 0; t < 3; ++t) plans[t] = plan_for(t, max_nint[t], n_team[t], 4);
+  for (int t = 0; t < 3; ++t) plans[t] = plan_for(t, max_nint[t], n_team[t], 0);
   const size_t order_off = (img.bytes() + 255) & ~size_t(255);
   const size_t counter_off = (order_off + order.size() * sizeof(int32_t) + 255) & ~size_t(255);
   const size_t states_off = counter_off + 256;
@@ -1429,6 +1432,45 @@ tqs_status tqs_server_stats(const tqs_server* sv, int64_t* queued, int64_t* infl
 
 tqs_status tqs_server_destroy(tqs_server* sv) {
   delete sv;
+  return TQS_OK;
+}
+
+}  // extern "C"
+
+extern "C" {
+
+tqs_status tqs_set_option(int option, int key, int64_t value) {
+  if (option == TQS_OPT_WARPS_PER_CTA) {
+    if (key < 4 || key > kWarpMaxQ) return fail(TQS_ERR_ARG, "tqs_set_option: key %d outside [4, %d]", key, kWarpMaxQ);
+    if (value < 1 || value > 16) return fail(TQS_ERR_ARG, "tqs_set_option: warps %lld outside [1, 16]", static_cast<long long>(value));
+    g_warps_for_q[key].store(static_cast<int>(value));
+    return TQS_OK;
+  }
+  return fail(TQS_ERR_ARG, "tqs_set_option: unknown option %d", option);
+}
+
+tqs_status tqs_get_option(int option, int key, int64_t* value) {
+  if (!value) return fail(TQS_ERR_ARG, "tqs_get_option: value is NULL");
+  if (option == TQS_OPT_WARPS_PER_CTA) {
+    if (key < 4 || key > kWarpMaxQ) return fail(TQS_ERR_ARG, "tqs_get_option: key %d outside [4, %d]", key, kWarpMaxQ);
+    *value = g_warps_for_q[key].load();
+    return TQS_OK;
+  }
+  return fail(TQS_ERR_ARG, "tqs_get_option: unknown option %d", option);
+}
+
+tqs_status tqs_selftest_wait_timeout(int64_t wait_cycles, void* stream) {
+  if (wait_cycles < 1 || wait_cycles > (int64_t(1) << 31))
+    return fail(TQS_ERR_ARG, "tqs_selftest_wait_timeout: wait_cycles outside [1, 2^31]");
+  static thread_local DevBuf status;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  TQS_CUDA(status.ensure(sizeof(int)), "tqs_selftest_wait_timeout: cudaMalloc");
+  TQS_CUDA(cudaMemsetAsync(status.p, 0, sizeof(int), s), "tqs_selftest_wait_timeout: memset");
+  TQS_CUDA(launch_wait_selftest(status.as<int>(), wait_cycles, s), "tqs_selftest_wait_timeout: launch");
+  int h = 0;
+  TQS_CUDA(cudaMemcpyAsync(&h, status.p, sizeof(int), cudaMemcpyDeviceToHost, s), "read status");
+  TQS_CUDA(cudaStreamSynchronize(s), "tqs_selftest_wait_timeout: sync");
+  if (h) return fail(TQS_ERR_TIMEOUT, "tqs_selftest_wait_timeout: the wait ran out (expected)");
   return TQS_OK;
 }
 

@@ -156,6 +156,10 @@ cudaError_t launch_probs(const float2* d_state, int n, double* d_probs, uint64_t
 // Process-wide count of kernel launches enqueued by this library.
 void count_launches(int64_t k);
 
+// One thread waits on an mbarrier nothing completes, for at most wait_cycles;
+// on time-out it sets *status = 1 and returns.
+cudaError_t launch_wait_selftest(int* status, long long wait_cycles, cudaStream_t s);
+
 // Record the calling thread's last error message (read by tqs_last_error).
 void set_last_error(const char* msg);
 

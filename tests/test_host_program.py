@@ -250,3 +250,17 @@ def test_server_host_side():
         B.tqs_server_destroy(small)
     with pytest.raises(B.TqsError):
         B.tqs_server_create(0, 1, 1)
+
+
+def test_launch_options():
+    old = B.tqs_get_option(B.OPT_WARPS_PER_CTA, 11)
+    try:
+        B.tqs_set_option(B.OPT_WARPS_PER_CTA, 11, 8)
+        assert B.tqs_get_option(B.OPT_WARPS_PER_CTA, 11) == 8
+        for bad in [(11, 0), (11, 17), (3, 4), (12, 4)]:
+            with pytest.raises(B.TqsError):
+                B.tqs_set_option(B.OPT_WARPS_PER_CTA, *bad)
+        with pytest.raises(B.TqsError):
+            B.tqs_set_option(99, 11, 4)
+    finally:
+        B.tqs_set_option(B.OPT_WARPS_PER_CTA, 11, old)
