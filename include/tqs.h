@@ -128,19 +128,27 @@ tqs_status tqs_circuit_steps(const tqs_circuit* c, int* h_step_of_gate);
  *              {uint8 L[4]; uint32 op_begin; uint32 op_count; float scale}
  *              (scale: exact power of two applied at the end of the pass)
  *   h_ops    : NULL or n_ops records of 80 bytes:
- *              {uint8 code (0-3 Hadamard without its 2^-1/2, 4-7 exchange
- *               (X, CNOT), 8-11 anti-diagonal, 12-15 dense, each + the local
- *               target position; 16 diagonal), tloc, t, ckind (0 none,
- *               1 local, 2 far), c (diagonal ops: target / control), fbit
- *               (far control bit, 255 none), uint16 act (active-pair mask);
+ *              {uint8 code, t, c, tbit, d0one, fbit; uint16 act;
  *               uint32 pad[2]; float m[8] (4 complex entries); float lo[8]
- *               (their FP32 rounding residues, dense ops)}
+ *               (their FP32 rounding residues, dense ops)}.  code: 0-3
+ *               Hadamard without its 2^-1/2, 4-7 X, 8-11 X under a far
+ *               control, 12-27 X under a local control (12 + 4 t + c), 28-31
+ *               anti-diagonal, 32-35 dense, 36-39 controlled dense, each + the
+ *               local target position t; diagonal: 40-43 local target, 44-47
+ *               local target + far control, 48-51 far target + local control
+ *               c, 52 far target, 53 both local (fields t, c).  fbit: far
+ *               control bit (255 none); tbit: far target bit; act: active-pair
+ *               mask over the 16 local indices; d0one: d0 == 1 exactly.
  *   h_pos    : NULL or 16 bytes, the physical bit of each logical qubit at
  *              the end (SWAP factors are relabelings).
  *   h_out_scale : NULL or 1 float, the factor applied to the output state.
+ *   h_gen_index : NULL or 1 int, the basis state the program starts from
+ *              (leading X gates on untouched qubits are folded into it; the
+ *              program for a given input state folds nothing).
  * Host memory only; no device work. */
 tqs_status tqs_circuit_program(tqs_circuit* c, int* n_passes, int* n_ops, void* h_passes,
-                               void* h_ops, uint8_t* h_pos, float* h_out_scale);
+                               void* h_ops, uint8_t* h_pos, float* h_out_scale,
+                               int* h_gen_index);
 
 /* ---------------------------------------------------------------- simulate
  * simulateFullState (Sec. 5.2): the final state psi = S_m ... S_1 psi_0.

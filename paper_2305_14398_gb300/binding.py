@@ -54,7 +54,8 @@ _SIGS = {
     "tqs_add_gate": (_i, [_vp, _i, _pi, _i, _pd, _i]),
     "tqs_circuit_info": (_i, [_vp, _pi, _pi, _pi]),
     "tqs_circuit_steps": (_i, [_vp, _pi]),
-    "tqs_circuit_program": (_i, [_vp, _pi, _pi, _vp, _vp, _vp, ctypes.POINTER(ctypes.c_float)]),
+    "tqs_circuit_program": (_i, [_vp, _pi, _pi, _vp, _vp, _vp, ctypes.POINTER(ctypes.c_float),
+                                 _pi]),
     "tqs_simulate": (_i, [_vp, _vp, _vp, _vp, _vp, _vp]),
     "tqs_simulate_plain": (_i, [_vp, _vp, _vp, _vp]),
     "tqs_materialize_step": (_i, [_vp, _i, _vp, _vp]),
@@ -164,23 +165,24 @@ def tqs_circuit_steps(c: int) -> List[int]:
 
 PASS_DTYPE = np.dtype([("L", np.uint8, 4), ("op_begin", np.uint32), ("op_count", np.uint32),
                        ("scale", np.float32)])
-OP_DTYPE = np.dtype([("code", np.uint8), ("tloc", np.uint8), ("t", np.uint8), ("ckind", np.uint8),
-                     ("c", np.uint8), ("fbit", np.uint8), ("act", np.uint16),
+OP_DTYPE = np.dtype([("code", np.uint8), ("t", np.uint8), ("c", np.uint8), ("tbit", np.uint8),
+                     ("d0one", np.uint8), ("fbit", np.uint8), ("act", np.uint16),
                      ("pad1", np.uint32, 2), ("m", np.complex64, 4), ("lo", np.complex64, 4)])
 
 
 def tqs_circuit_program(c: int):
-    """(passes, ops, pos, out_scale) of the compiled fused program (numpy records)."""
+    """(passes, ops, pos, out_scale, gen_index) of the compiled fused program."""
     npass, nops = ctypes.c_int(), ctypes.c_int()
     _check(lib().tqs_circuit_program(c, ctypes.byref(npass), ctypes.byref(nops), None, None, None,
-                                     None))
+                                     None, None))
     passes = np.zeros(npass.value, dtype=PASS_DTYPE)
     ops = np.zeros(nops.value, dtype=OP_DTYPE)
     pos = np.zeros(16, dtype=np.uint8)
     osc = ctypes.c_float()
+    gen = ctypes.c_int()
     _check(lib().tqs_circuit_program(c, None, None, passes.ctypes.data, ops.ctypes.data,
-                                     pos.ctypes.data, ctypes.byref(osc)))
-    return passes, ops, pos, float(osc.value)
+                                     pos.ctypes.data, ctypes.byref(osc), ctypes.byref(gen)))
+    return passes, ops, pos, float(osc.value), gen.value
 
 
 def circuit_from_ops(n: int, ops: Iterable) -> int:

@@ -96,6 +96,9 @@ __device__ __forceinline__ void anti_t(float2 (&a)[16], float2 m01, float2 m10, 
   }
 }
 
+
+
+
 template <int T>
 __device__ __forceinline__ void swap_t(float2 (&a)[16], unsigned act) {
 #pragma unroll
@@ -145,20 +148,20 @@ __device__ __forceinline__ void diag_local(float2 (&a)[16], int t, int c, float2
 }
 
 // Pending per-bit phases: a diagonal factor that depends on one local bit is
-// folded into p_b (applied to the amplitudes with local bit b = 1) and only
+// folded into p[b] (applied to the amplitudes with local bit b = 1) and only
 // multiplied in before a non-diagonal factor on bit b, or at the end of the
 // pass.  Factors that depend on far bits only fold into the scalar `sc`.
 struct Pending {
-  float2 p0, p1, p2, p3;
+  float2 p[4];  // indexed with compile-time positions only
   unsigned dirty;
 };
 
 __device__ __forceinline__ void pend_mul(Pending& pd, int b, float2 v) {
   switch (b) {
-    case 0: pd.p0 = cmul(pd.p0, v); break;
-    case 1: pd.p1 = cmul(pd.p1, v); break;
-    case 2: pd.p2 = cmul(pd.p2, v); break;
-    default: pd.p3 = cmul(pd.p3, v); break;
+    case 0: pd.p[0] = cmul(pd.p[0], v); break;
+    case 1: pd.p[1] = cmul(pd.p[1], v); break;
+    case 2: pd.p[2] = cmul(pd.p[2], v); break;
+    default: pd.p[3] = cmul(pd.p[3], v); break;
   }
   pd.dirty |= 1u << b;
 }
@@ -167,25 +170,28 @@ __device__ __forceinline__ void pend_flush(float2 (&a)[16], Pending& pd, int b) 
   if (!((pd.dirty >> b) & 1)) return;
   const float2 one = make_float2(1.f, 0.f);
   switch (b) {
-    case 0: scale_bit<0>(a, pd.p0); pd.p0 = one; break;
-    case 1: scale_bit<1>(a, pd.p1); pd.p1 = one; break;
-    case 2: scale_bit<2>(a, pd.p2); pd.p2 = one; break;
-    default: scale_bit<3>(a, pd.p3); pd.p3 = one; break;
+    case 0: scale_bit<0>(a, pd.p[0]); pd.p[0] = one; break;
+    case 1: scale_bit<1>(a, pd.p[1]); pd.p[1] = one; break;
+    case 2: scale_bit<2>(a, pd.p[2]); pd.p[2] = one; break;
+    default: scale_bit<3>(a, pd.p[3]); pd.p[3] = one; break;
   }
   pd.dirty &= ~(1u << b);
 }
+
+
 
 __device__ __forceinline__ float2 f2(unsigned x, unsigned y) {
   return make_float2(__uint_as_float(x), __uint_as_float(y));
 }
 
 // Apply the ops of one pass to the 16 amplitudes of one group, then the
-// pass's exact power-of-two scale.  One jump per op on its dispatch code; the
-// next op's header is fetched while the current one runs.
+// pass's exact power-of-two scale.  The next op's header is fetched while the
+// current one runs.
 __device__ __forceinline__ void run_ops(float2 (&a)[16], const FusedOp* __restrict__ ops,
                                         uint32_t count, int base, float scale) {
   Pending pd;
-  pd.p0 = pd.p1 = pd.p2 = pd.p3 = make_float2(1.f, 0.f);
+#pragma unroll
+  for (int b = 0; b < 4; ++b) pd.p[b] = make_float2(1.f, 0.f);
   pd.dirty = 0;
   float2 sc = make_float2(1.f, 0.f);
   bool sc_set = false;
@@ -195,87 +201,93 @@ __device__ __forceinline__ void run_ops(float2 (&a)[16], const FusedOp* __restri
     const uint4 q0 = next;
     if (k + 1 < count) next = __ldg(reinterpret_cast<const uint4*>(ops + k + 1));
     const int code = q0.x & 0xff;
-    if (code < OPC_DIAG) {
-      const int fbit = q0.y >> 8 & 0xff;
-      if (fbit != 0xff && !((base >> fbit) & 1)) continue;  // far control is 0 here
-      const int t = code & 3;
-      const unsigned act = q0.y >> 16;
+    const int fbit = (q0.y >> 8) & 0xff;
+    if (fbit != 0xff && !((base >> fbit) & 1)) continue;  // a far control is 0 here
+    if (code < OPC_DLN) {
+      // non-diagonal: target local position t
+      int t = code & 3;
+      unsigned act = q0.y >> 16;
+      if (code >= OPC_XL && code < OPC_ANTI) {
+        t = (code - OPC_XL) >> 2;
+        act = bit_mask((code - OPC_XL) & 3);
+      }
       pend_flush(a, pd, t);
-      switch (code) {
-        case OPC_H + 0: h_t<0>(a); break;
-        case OPC_H + 1: h_t<1>(a); break;
-        case OPC_H + 2: h_t<2>(a); break;
-        case OPC_H + 3: h_t<3>(a); break;
-        case OPC_SWAP + 0: swap_t<0>(a, act); break;
-        case OPC_SWAP + 1: swap_t<1>(a, act); break;
-        case OPC_SWAP + 2: swap_t<2>(a, act); break;
-        case OPC_SWAP + 3: swap_t<3>(a, act); break;
-        case OPC_ANTI + 0:
-        case OPC_ANTI + 1:
-        case OPC_ANTI + 2:
-        case OPC_ANTI + 3: {
-          const uint4 q1 = __ldg(rec + 1);
-          const uint4 q2 = __ldg(rec + 2);
-          const float2 m01 = f2(q1.z, q1.w), m10 = f2(q2.x, q2.y);
-          switch (t) {
-            case 0: anti_t<0>(a, m01, m10, act); break;
-            case 1: anti_t<1>(a, m01, m10, act); break;
-            case 2: anti_t<2>(a, m01, m10, act); break;
-            default: anti_t<3>(a, m01, m10, act); break;
-          }
-          break;
+      if (code < OPC_X) {
+        switch (t) {
+          case 0: h_t<0>(a); break;
+          case 1: h_t<1>(a); break;
+          case 2: h_t<2>(a); break;
+          default: h_t<3>(a); break;
         }
-        default: {
-          const uint4 q1 = __ldg(rec + 1);
-          const uint4 q2 = __ldg(rec + 2);
-          const uint4 q3 = __ldg(rec + 3);
-          const uint4 q4 = __ldg(rec + 4);
-          Coef m;
-          m.h[0] = f2(q1.x, q1.y);
-          m.h[1] = f2(q1.z, q1.w);
-          m.h[2] = f2(q2.x, q2.y);
-          m.h[3] = f2(q2.z, q2.w);
-          m.l[0] = f2(q3.x, q3.y);
-          m.l[1] = f2(q3.z, q3.w);
-          m.l[2] = f2(q4.x, q4.y);
-          m.l[3] = f2(q4.z, q4.w);
-          switch (t) {
-            case 0: dense_t<0>(a, m, act); break;
-            case 1: dense_t<1>(a, m, act); break;
-            case 2: dense_t<2>(a, m, act); break;
-            default: dense_t<3>(a, m, act); break;
-          }
-          break;
+      } else if (code < OPC_ANTI) {
+        switch (t) {
+          case 0: swap_t<0>(a, act); break;
+          case 1: swap_t<1>(a, act); break;
+          case 2: swap_t<2>(a, act); break;
+          default: swap_t<3>(a, act); break;
+        }
+      } else if (code < OPC_DENSE) {
+        const uint4 q1 = __ldg(rec + 1);
+        const uint4 q2 = __ldg(rec + 2);
+        const float2 m01 = f2(q1.z, q1.w), m10 = f2(q2.x, q2.y);
+        switch (t) {
+          case 0: anti_t<0>(a, m01, m10, act); break;
+          case 1: anti_t<1>(a, m01, m10, act); break;
+          case 2: anti_t<2>(a, m01, m10, act); break;
+          default: anti_t<3>(a, m01, m10, act); break;
+        }
+      } else {
+        const uint4 q1 = __ldg(rec + 1);
+        const uint4 q2 = __ldg(rec + 2);
+        const uint4 q3 = __ldg(rec + 3);
+        const uint4 q4 = __ldg(rec + 4);
+        Coef m;
+        m.h[0] = f2(q1.x, q1.y);
+        m.h[1] = f2(q1.z, q1.w);
+        m.h[2] = f2(q2.x, q2.y);
+        m.h[3] = f2(q2.z, q2.w);
+        m.l[0] = f2(q3.x, q3.y);
+        m.l[1] = f2(q3.z, q3.w);
+        m.l[2] = f2(q4.x, q4.y);
+        m.l[3] = f2(q4.z, q4.w);
+        switch (t) {
+          case 0: dense_t<0>(a, m, act); break;
+          case 1: dense_t<1>(a, m, act); break;
+          case 2: dense_t<2>(a, m, act); break;
+          default: dense_t<3>(a, m, act); break;
         }
       }
       continue;
     }
-    // diagonal: d0 = m0, d1 = m1, ratio d1/d0 = m2
-    const int tloc = (q0.x >> 8) & 0xff;
-    const int t = (q0.x >> 16) & 0xff;
-    const int ckind = q0.x >> 24;
-    const int c = q0.y & 0xff;
-    const uint4 q1 = __ldg(rec + 1);
-    const uint4 q2 = __ldg(rec + 2);
-    const float2 m0 = f2(q1.x, q1.y);
-    const float2 m1 = f2(q1.z, q1.w);
-    const float2 m2 = f2(q2.x, q2.y);
-    if (tloc) {
-      if (ckind == CTL_LOCAL) {
-        diag_local(a, t, c, m0, m1);
-      } else if (ckind == CTL_NONE || ((base >> c) & 1)) {
-        sc = cmul(sc, m0);
-        sc_set = true;
-        pend_mul(pd, t, m2);
-      }
-    } else {
-      const float2 v = ((base >> t) & 1) ? m1 : m0;
-      if (ckind == CTL_LOCAL) {
-        pend_mul(pd, c, v);
-      } else if (ckind == CTL_NONE || ((base >> c) & 1)) {
-        sc = cmul(sc, v);
+    // diagonal ops: d0 = m0, d1 = m1, ratio d1/d0 = m2
+    const bool d0one = (q0.y & 0xff) != 0;
+    if (code < OPC_DFL) {  // local target, no or far control
+      const uint4 q2 = __ldg(rec + 2);
+      if (!d0one) {
+        const uint4 q1 = __ldg(rec + 1);
+        sc = cmul(sc, f2(q1.x, q1.y));
         sc_set = true;
       }
+      pend_mul(pd, code & 3, f2(q2.x, q2.y));
+      continue;
+    }
+    const bool tb = (base >> ((q0.x >> 24) & 0xff)) & 1;
+    if (code < OPC_DFF) {  // far target, local control c
+      if (!tb && d0one) continue;
+      const uint4 q1 = __ldg(rec + 1);
+      pend_mul(pd, code & 3, tb ? f2(q1.z, q1.w) : f2(q1.x, q1.y));
+      continue;
+    }
+    if (code == OPC_DFF) {  // far target, no or far control: a phase of the group
+      if (!tb && d0one) continue;
+      const uint4 q1 = __ldg(rec + 1);
+      sc = cmul(sc, tb ? f2(q1.z, q1.w) : f2(q1.x, q1.y));
+      sc_set = true;
+      continue;
+    }
+    {  // OPC_DLL: both local
+      const uint4 q1 = __ldg(rec + 1);
+      diag_local(a, (q0.x >> 8) & 0xff, (q0.x >> 16) & 0xff, f2(q1.x, q1.y), f2(q1.z, q1.w));
     }
   }
   pend_flush(a, pd, 0);
@@ -368,7 +380,7 @@ __device__ void run_circuit(const FusedLaunch& L, int ci, float2* st, int rank, 
       for (int j = 0; j < 16; ++j) {
         if (gen) {
           const int off = base | ((j & 1) ? b0 : 0) | ((j & 2) ? b1 : 0) | ((j & 4) ? b2 : 0) | ((j & 8) ? b3 : 0);
-          a[j] = make_float2(off == 0 ? 1.f : 0.f, 0.f);
+          a[j] = make_float2(off == cd.gen_index ? 1.f : 0.f, 0.f);
         } else {
           a[j] = st[sb ^ ((j & 1) ? w0 : 0) ^ ((j & 2) ? w1 : 0) ^ ((j & 4) ? w2 : 0) ^ ((j & 8) ? w3 : 0)];
         }

@@ -192,6 +192,7 @@ struct Program {
   uint8_t pos[16];
   int identity = 1;
   float out_scale = 1.0f;
+  int gen_index = 0;  // basis state the program starts from (leading X gates folded)
   double cost = 0.0;
 };
 
@@ -208,9 +209,27 @@ constexpr int kMaxHPerPass = 48;
 // (the mixed-product property of the Kronecker product: consecutive steps'
 // factors on one qubit compose).  The result does not depend on the other
 // circuits of a batch.
-static void compile_program(int n, const std::vector<const Gate*>& gs, Program& P) {
+static void compile_program(int n, const std::vector<const Gate*>& gs_in, Program& P,
+                            bool fold_x = true) {
   P.n = n;
   P.nint = std::max(n, 4);
+  // Leading uncontrolled X factors on a qubit that nothing has touched yet act
+  // on the basis input |0...0> only by flipping that qubit: fold them into the
+  // start index instead of spending butterflies (input |0...0> only).
+  std::vector<const Gate*> gs;
+  gs.reserve(gs_in.size());
+  P.gen_index = 0;
+  {
+    uint32_t touched = 0;
+    for (const Gate* g : gs_in) {
+      if (fold_x && g->kind == TQS_X && !((touched >> g->q[0]) & 1)) {
+        P.gen_index ^= 1 << g->q[0];
+        continue;
+      }
+      touched |= (1u << g->q[0]) | (g->nq == 2 ? (1u << g->q[1]) : 0u);
+      gs.push_back(g);
+    }
+  }
   const int nint = P.nint;
   int phys[16];
   for (int q = 0; q < 16; ++q) phys[q] = q;
@@ -267,27 +286,30 @@ static void compile_program(int n, const std::vector<const Gate*>& gs, Program& 
       const Mat2& u = r.u;
       op.fbit = 0xFF;
       op.act = 0xFFFF;
+      op.tbit = 0xFF;
+      const int tl = loc[r.t];                    // local target position or -1
+      const int cl = r.c >= 0 ? loc[r.c] : -1;    // local control position or -1
+      const bool far_c = r.c >= 0 && cl < 0;
+      if (far_c) op.fbit = static_cast<uint8_t>(r.c);
       if (r.cls != G_DIAG || r.is_h) {
         // non-diagonal: the target is local
-        const int tl = loc[r.t];
-        op.t = static_cast<uint8_t>(tl);
-        op.tloc = 1;
-        if (r.c >= 0) {
-          if (loc[r.c] >= 0) op.act = kBitMask[loc[r.c]];
-          else op.fbit = static_cast<uint8_t>(r.c);
-        }
+        if (cl >= 0) op.act = kBitMask[cl];
         if (r.is_h) {
           op.code = static_cast<uint8_t>(OPC_H + tl);
           ++h_count;
           pass_cost += 0.5;
+        } else if (r.cls == G_ANTI && u.m[1] == cd(1.0) && u.m[2] == cd(1.0)) {
+          if (r.c < 0) op.code = static_cast<uint8_t>(OPC_X + tl);
+          else if (far_c) op.code = static_cast<uint8_t>(OPC_XF + tl);
+          else op.code = static_cast<uint8_t>(OPC_XL + 4 * tl + cl);
+          pass_cost += 0.5;
         } else if (r.cls == G_ANTI) {
-          const bool unit = (u.m[1] == cd(1.0) && u.m[2] == cd(1.0));
-          op.code = static_cast<uint8_t>((unit ? OPC_SWAP : OPC_ANTI) + tl);
+          op.code = static_cast<uint8_t>(OPC_ANTI + tl);
           op.m[1] = to_f2(u.m[1]);
           op.m[2] = to_f2(u.m[2]);
-          pass_cost += unit ? 0.5 : 1.0;
+          pass_cost += 1.0;
         } else {
-          op.code = static_cast<uint8_t>(OPC_DENSE + tl);
+          op.code = static_cast<uint8_t>((r.c < 0 ? OPC_DENSE : OPC_CDENSE) + tl);
           for (int i = 0; i < 4; ++i) {
             op.m[i] = to_f2(u.m[i]);
             const cd hi(op.m[i].x, op.m[i].y);
@@ -296,16 +318,23 @@ static void compile_program(int n, const std::vector<const Gate*>& gs, Program& 
           pass_cost += 3.0;
         }
       } else {
-        op.code = OPC_DIAG;
         op.m[0] = to_f2(u.m[0]);
         op.m[1] = to_f2(u.m[3]);
         op.m[2] = to_f2(u.m[3] / u.m[0]);
-        pass_cost += 0.5;
-        if (loc[r.t] >= 0) { op.tloc = 1; op.t = static_cast<uint8_t>(loc[r.t]); }
-        else { op.tloc = 0; op.t = static_cast<uint8_t>(r.t); }
-        if (r.c < 0) { op.ckind = CTL_NONE; op.c = 0; }
-        else if (loc[r.c] >= 0) { op.ckind = CTL_LOCAL; op.c = static_cast<uint8_t>(loc[r.c]); }
-        else { op.ckind = CTL_FAR; op.c = static_cast<uint8_t>(r.c); }
+        op.d0one = (u.m[0] == cd(1.0)) ? 1 : 0;
+        pass_cost += 0.25;
+        if (tl >= 0) {
+          if (cl >= 0) {
+            op.code = OPC_DLL;
+            op.t = static_cast<uint8_t>(tl);
+            op.c = static_cast<uint8_t>(cl);
+          } else {
+            op.code = static_cast<uint8_t>((far_c ? OPC_DLF : OPC_DLN) + tl);
+          }
+        } else {
+          op.tbit = static_cast<uint8_t>(r.t);
+          op.code = cl >= 0 ? static_cast<uint8_t>(OPC_DFL + cl) : static_cast<uint8_t>(OPC_DFF);
+        }
       }
       P.ops.push_back(op);
     }
@@ -390,7 +419,9 @@ struct tqs_circuit {
   int nsteps = 0;
   // cached fused program and its device copy
   bool prog_valid = false;
-  Program prog;
+  Program prog;       // for the input |0...0> (leading X gates folded)
+  bool prog_init_valid = false;
+  Program prog_init;  // for a given input state (nothing folded)
   DevBuf d_prog;      // FusedCirc + passes + ops
   DevBuf d_counter;   // job counter
   DevBuf d_gscratch;  // TEAM_GLOBAL slot
@@ -490,6 +521,7 @@ tqs_status tqs_add_gate(tqs_circuit* c, int gate, const int* qubits, int nq, con
   c->nsteps = std::max(c->nsteps, step + 1);
   c->gates.push_back(g);
   c->prog_valid = false;
+  c->prog_init_valid = false;
   c->steps_valid = false;
   return TQS_OK;
 }
@@ -519,18 +551,30 @@ static std::vector<const Gate*> step_order(const std::vector<Gate>& gates) {
   return v;
 }
 
-static void ensure_program(tqs_circuit* c) {
-  if (c->prog_valid) return;
-  c->prog = Program();
-  compile_program(c->n, step_order(c->gates), c->prog);
-  c->prog_valid = true;
+static const Program& ensure_program(tqs_circuit* c, bool with_init = false) {
+  if (with_init) {
+    if (!c->prog_init_valid) {
+      c->prog_init = Program();
+      compile_program(c->n, step_order(c->gates), c->prog_init, false);
+      c->prog_init_valid = true;
+    }
+    return c->prog_init;
+  }
+  if (!c->prog_valid) {
+    c->prog = Program();
+    compile_program(c->n, step_order(c->gates), c->prog);
+    c->prog_valid = true;
+  }
+  return c->prog;
 }
 
 static bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
 extern "C" tqs_status tqs_circuit_program(tqs_circuit* c, int* n_passes, int* n_ops, void* h_passes,
-                                          void* h_ops, uint8_t* h_pos, float* h_out_scale) {
+                                          void* h_ops, uint8_t* h_pos, float* h_out_scale,
+                                          int* h_gen_index) {
   if (!c) return fail(TQS_ERR_ARG, "tqs_circuit_program: circuit is NULL");
   ensure_program(c);
+  if (h_gen_index) *h_gen_index = c->prog.gen_index;
   if (n_passes) *n_passes = static_cast<int>(c->prog.passes.size());
   if (n_ops) *n_ops = static_cast<int>(c->prog.ops.size());
   if (h_passes) std::memcpy(h_passes, c->prog.passes.data(), c->prog.passes.size() * sizeof(FusedPass));
@@ -562,6 +606,7 @@ struct Image {
     std::memcpy(fc.pos, P.pos, 16);
     fc.init = nullptr;
     fc.out_scale = P.out_scale;
+    fc.gen_index = P.gen_index;
     const uint32_t op_base = static_cast<uint32_t>(ops.size());
     for (FusedPass ps : P.passes) {
       ps.op_begin += op_base;
@@ -627,8 +672,7 @@ tqs_status tqs_simulate(tqs_circuit* c, const tqs_c64* d_init, tqs_c64* d_out, d
   if (d_init && reinterpret_cast<const void*>(d_init) == reinterpret_cast<const void*>(d_out))
     return fail(TQS_ERR_ARG, "tqs_simulate: d_init must not alias d_out");
   cudaStream_t s = static_cast<cudaStream_t>(stream);
-  ensure_program(c);
-  const Program& P = c->prog;
+  const Program& P = ensure_program(c, d_init != nullptr);
   const int team = team_for(P.nint);
   Image img;
   img.add(P, 0);

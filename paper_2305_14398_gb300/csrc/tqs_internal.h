@@ -19,38 +19,46 @@ namespace tqs {
 // locality.  SWAP factors are qubit relabelings done on the host.
 // ---------------------------------------------------------------------------
 
-// Dispatch code of an op (one jump per op in the kernel):
-//   OPC_H + t      uncontrolled Hadamard without its 2^-1/2 on local position t:
-//                  (x0 + x1, x0 - x1); the pass scale restores the factor exactly
-//   OPC_SWAP + t   anti-diagonal with unit entries (X, CNOT): exchange the pair
-//   OPC_ANTI + t   anti-diagonal [[0, m01], [m10, 0]]
-//   OPC_DENSE + t  general 2x2, coefficients as FP32 hi + lo
-//   OPC_DIAG       diag(d0, d1) on a target of any locality (fields tloc, t, ckind, c)
-// Non-diagonal ops act on the pairs whose low index j0 has its bit set in `act`
-// (all ones, or the control-bit-1 half for a local control), and only in the
-// groups whose base has physical bit `fbit` set (0xFF: no far control).
+// Dispatch code of an op (one jump per op in the kernel).  "+ t": local target
+// position t (0..3); "+ 4 t + c": local target t and local control c.
+//   OPC_H + t        uncontrolled Hadamard without its 2^-1/2: (x0 + x1, x0 - x1);
+//                    the pass scale restores the factor exactly
+//   OPC_X + t        uncontrolled exchange of the pair (X)
+//   OPC_XF + t       exchange where far control bit `fbit` of the group is 1 (CNOT)
+//   OPC_XL + 4t + c  exchange in the pairs whose local control bit c is 1 (CNOT)
+//   OPC_ANTI + t     anti-diagonal [[0, m01], [m10, 0]]; `act` mask / `fbit`
+//   OPC_DENSE + t    uncontrolled 2x2, coefficients as FP32 hi + lo
+//   OPC_CDENSE + t   controlled 2x2 (`act` mask for a local control, `fbit` far)
+//   OPC_DLN + t      diag(d0, d1), local target, uncontrolled
+//   OPC_DLF + t      diag(d0, d1), local target, far control `fbit`
+//   OPC_DFL + c      diag(d0, d1), far target bit `tbit`, local control c
+//   OPC_DFF          diag(d0, d1), far target bit `tbit`, no or far control `fbit`
+//   OPC_DLL          diag(d0, d1), local target t and local control c (fields t, c)
+// Diagonal ops carry d0, d1, d1/d0 and `d0one` = 1 when d0 is exactly 1.
 enum OpCode : uint8_t {
   OPC_H = 0,
-  OPC_SWAP = 4,
-  OPC_ANTI = 8,
-  OPC_DENSE = 12,
-  OPC_DIAG = 16
-};
-
-enum CtlKind : uint8_t {
-  CTL_NONE = 0,   // uncontrolled
-  CTL_LOCAL = 1,  // control is local position `c`
-  CTL_FAR = 2     // control is physical bit `c` outside the pass's local bits
+  OPC_X = 4,
+  OPC_XF = 8,
+  OPC_XL = 12,       // 16 codes (t, c), c != t used
+  OPC_ANTI = 28,
+  OPC_DENSE = 32,
+  OPC_CDENSE = 36,
+  OPC_DLN = 40,
+  OPC_DLF = 44,
+  OPC_DFL = 48,
+  OPC_DFF = 52,
+  OPC_DLL = 53,
+  OPC_COUNT = 54
 };
 
 struct alignas(16) FusedOp {
-  uint8_t code;    // OpCode (+ local target position for non-diagonal ops)
-  uint8_t tloc;    // OPC_DIAG: 1 if the target is local position `t`, else physical bit `t`
-  uint8_t t;
-  uint8_t ckind;   // OPC_DIAG: CtlKind of the control `c`
-  uint8_t c;
-  uint8_t fbit;    // non-diagonal: physical bit of a far control, 0xFF if none
-  uint16_t act;    // non-diagonal: active-pair mask over the 16 local indices
+  uint8_t code;    // OpCode
+  uint8_t t;       // local target position (OPC_DLL)
+  uint8_t c;       // local control position (OPC_DLL)
+  uint8_t tbit;    // physical bit of a far target (OPC_DFL, OPC_DFF)
+  uint8_t d0one;   // diagonal ops: d0 == 1 exactly
+  uint8_t fbit;    // physical bit of a far control, 0xFF if none
+  uint16_t act;    // active-pair mask over the 16 local indices (ANTI, CDENSE)
   uint32_t pad1[2];
   float2 m[4];     // DENSE: m00 m01 m10 m11 | ANTI: -, m01, m10, - | DIAG: d0, d1, d1/d0, -
   float2 lo[4];    // DENSE: m - m_fp32 rounded to FP32 (the FP64 matrix is m + lo)
@@ -76,9 +84,9 @@ struct alignas(16) FusedCirc {
   int32_t team;         // TeamKind
   int32_t identity;     // 1 if the output qubit map is the identity
   uint8_t pos[16];      // physical bit of logical qubit q at the end
-  const float2* init;   // initial state (logical order) or nullptr for |0..0>
+  const float2* init;   // initial state (logical order) or nullptr for a basis state
   float out_scale;      // 1, or 2^-1/2 when an odd Hadamard factor is left over
-  int32_t pad;
+  int32_t gen_index;    // without init: the first pass starts from |gen_index>
 };
 static_assert(sizeof(FusedCirc) == 64, "FusedCirc layout");
 

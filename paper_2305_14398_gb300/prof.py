@@ -5,7 +5,8 @@
 chain: the 40-step random layered circuit-unitary chain at n = COUNT
        (tensor-core BF16x3);
 mix:   COUNT paper-shaped 11-qubit circuits (GHZ / DJ-constant / DJ-balanced /
-       QFT, 25 % each); batch: the first COUNT circuits of the random batched
+       QFT, 25 % each); ghz, dj_constant, dj_balanced, qft: COUNT circuits of one
+       of those kinds; batch: the first COUNT circuits of the random batched
        workload (n = 4..14, depth 5..40).  Runs tqs_batch_run REPS times
        without a graph, then once more timed with CUDA events.
 """
@@ -41,6 +42,8 @@ def main(argv):
         return chain(count, reps)
     if kind == "mix":
         circs = [(11, ops) for _, ops in W.paper_mix(11, count)]
+    elif kind in ("ghz", "dj_constant", "dj_balanced", "qft"):
+        circs = [(11, ops) for k, ops in W.paper_mix(11, 4 * count) if k == kind]
     else:
         circs = W.batch_circuits(count, 3)
     b = B.tqs_batch_create_packed(*B.pack_ops(circs))

@@ -14,18 +14,19 @@ from oracle import fsv_route, kron_route
 from paper_2305_14398_gb300 import binding as B
 from paper_2305_14398_gb300 import workloads as W
 
-OPC_H, OPC_SWAP, OPC_ANTI, OPC_DENSE, OPC_DIAG = 0, 4, 8, 12, 16
-NONE, LOCAL, FAR = 0, 1, 2
+OPC_H, OPC_X, OPC_XF, OPC_XL, OPC_ANTI, OPC_DENSE, OPC_CDENSE = 0, 4, 8, 12, 28, 32, 36
+OPC_DLN, OPC_DLF, OPC_DFL, OPC_DFF, OPC_DLL = 40, 44, 48, 52, 53
+BIT_MASK = [0xAAAA, 0xCCCC, 0xF0F0, 0xFF00]
 
 
 def ins0(x, b):
     return ((x >> b) << (b + 1)) | (x & ((1 << b) - 1))
 
 
-def replay(n, passes, ops, pos, out_scale=1.0):
+def replay(n, passes, ops, pos, out_scale=1.0, gen_index=0):
     nint = max(n, 4)
     st = np.zeros(1 << nint, dtype=np.complex128)
-    st[0] = 1.0
+    st[gen_index] = 1.0
     G = (1 << nint) >> 4
     for ps in passes:
         L = [int(v) for v in ps["L"]]
@@ -43,37 +44,51 @@ def replay(n, passes, ops, pos, out_scale=1.0):
         for op in ops[b0:b0 + cnt]:
             code = int(op["code"])
             m = op["m"].astype(np.complex128)
-            if code == OPC_DIAG:
-                tloc, t, ckind, c = (int(op[k]) for k in ("tloc", "t", "ckind", "c"))
+            fbit = int(op["fbit"])
+            far_on = np.ones(G, bool) if fbit == 255 else ((base >> fbit) & 1) == 1
+            if code >= OPC_DLN:
                 d0, d1, r = m[0], m[1], m[2]
-                if tloc:
-                    if ckind == LOCAL:
-                        for j in range(16):
-                            if (j >> c) & 1:
-                                a[:, j] *= d1 if (j >> t) & 1 else d0
-                    else:
-                        on = np.ones(G, bool) if ckind == NONE else ((base >> c) & 1) == 1
-                        sc[on] *= d0
-                        pend[on, t] *= r
+                if int(op["d0one"]):
+                    assert d0 == 1
+                if code < OPC_DFL:  # local target, none / far control
+                    t = code & 3
+                    sc[far_on] *= d0
+                    pend[far_on, t] *= r
+                elif code < OPC_DFF:  # far target, local control
+                    c = code & 3
+                    v = np.where(((base >> int(op["tbit"])) & 1) == 1, d1, d0)
+                    pend[:, c] *= v
+                elif code == OPC_DFF:  # far target, none / far control
+                    v = np.where(((base >> int(op["tbit"])) & 1) == 1, d1, d0)
+                    sc[far_on] *= v[far_on]
                 else:
-                    v = np.where(((base >> t) & 1) == 1, d1, d0)
-                    if ckind == LOCAL:
-                        pend[:, c] *= v
-                    else:
-                        on = np.ones(G, bool) if ckind == NONE else ((base >> c) & 1) == 1
-                        sc[on] *= v[on]
+                    assert code == OPC_DLL
+                    t, c = int(op["t"]), int(op["c"])
+                    for j in range(16):
+                        if (j >> c) & 1:
+                            a[:, j] *= d1 if (j >> t) & 1 else d0
                 continue
-            assert code < OPC_DIAG
-            t = code & 3
-            assert int(op["t"]) == t and int(op["tloc"]) == 1
-            kind = code & ~3
-            if kind == OPC_DENSE:
-                m = m + op["lo"].astype(np.complex128)
-            elif kind == OPC_H:
-                assert int(op["fbit"]) == 255 and int(op["act"]) == 0xFFFF
+            act = int(op["act"])
+            if code < OPC_X:
+                kind, t = "h", code & 3
                 m = np.array([1, 1, 1, -1], dtype=np.complex128)
-            fbit, act = int(op["fbit"]), int(op["act"])
-            on = np.ones(G, bool) if fbit == 255 else ((base >> fbit) & 1) == 1
+                assert fbit == 255
+            elif code < OPC_XF:
+                kind, t = "x", code & 3
+                assert fbit == 255
+            elif code < OPC_XL:
+                kind, t = "x", code & 3
+            elif code < OPC_ANTI:
+                kind, t, cl = "x", (code - OPC_XL) >> 2, (code - OPC_XL) & 3
+                assert cl != t
+                act = BIT_MASK[cl]
+            elif code < OPC_DENSE:
+                kind, t = "anti", code & 3
+            else:
+                kind, t = "dense", code & 3
+                m = m + op["lo"].astype(np.complex128)
+                if code < OPC_CDENSE:
+                    assert fbit == 255 and act == 0xFFFF
             for j in range(16):
                 if (j >> t) & 1:
                     a[:, j] *= pend[:, t]
@@ -84,15 +99,15 @@ def replay(n, passes, ops, pos, out_scale=1.0):
                 if not (act >> j0) & 1:
                     continue
                 x0, x1 = a[:, j0].copy(), a[:, j1].copy()
-                if kind in (OPC_DENSE, OPC_H):
+                if kind in ("dense", "h"):
                     y0 = m[0] * x0 + m[1] * x1
                     y1 = m[2] * x0 + m[3] * x1
-                elif kind == OPC_SWAP:
+                elif kind == "x":
                     y0, y1 = x1, x0
                 else:
                     y0, y1 = m[1] * x1, m[2] * x0
-                a[on, j0] = y0[on]
-                a[on, j1] = y1[on]
+                a[far_on, j0] = y0[far_on]
+                a[far_on, j1] = y1[far_on]
         for b in range(4):
             for j in range(16):
                 if (j >> b) & 1:
@@ -126,8 +141,8 @@ CASES += [(f"layered{n}", n, W.random_layered(n, 3, (8, n))) for n in (5, 10, 12
 
 @pytest.mark.parametrize("name,n,ops", CASES, ids=[c[0] for c in CASES])
 def test_program_replay_matches_oracle(name, n, ops):
-    passes, prog_ops, pos, osc = compiled(n, ops)
-    got = replay(n, passes, prog_ops, pos, osc)
+    passes, prog_ops, pos, osc, gen = compiled(n, ops)
+    got = replay(n, passes, prog_ops, pos, osc, gen)
     want = fsv_route.simulate(n, ops)
     # the program stores matrices in FP32; the replay computes in FP64
     assert np.max(np.abs(got - want)) < 2e-6
@@ -164,9 +179,11 @@ def test_ghz_steps_and_passes():
     c = B.circuit_from_ops(n, W.ghz_chain(n))
     try:
         assert B.tqs_circuit_info(c)[2] == n
-        passes, ops, pos, osc = B.tqs_circuit_program(c)
-        assert len(ops) == n and len(passes) <= 4
+        passes, ops, pos, osc, gen = B.tqs_circuit_program(c)
+        assert len(ops) == n and len(passes) <= 4 and gen == 0
         assert ops[0]["code"] == OPC_H and osc == np.float32(2 ** -0.5)
+        assert all(OPC_XL <= int(o["code"]) < OPC_ANTI or int(o["code"]) < OPC_X
+                   or OPC_XF <= int(o["code"]) < OPC_XL for o in ops)
     finally:
         B.tqs_circuit_destroy(c)
 
@@ -264,3 +281,12 @@ def test_launch_options():
             B.tqs_set_option(99, 11, 4)
     finally:
         B.tqs_set_option(B.OPT_WARPS_PER_CTA, 11, old)
+
+
+def test_leading_x_gates_fold_into_the_start_state():
+    """QFT on a basis state: the preparing X gates cost no op and no pass."""
+    n, x = 11, 0b10010110101
+    bare = compiled(n, W.qft(n))
+    prep = compiled(n, W.qft_on_basis(n, x))
+    assert prep[4] == x and bare[4] == 0
+    assert len(prep[1]) == len(bare[1]) and len(prep[0]) == len(bare[0])
