@@ -69,7 +69,7 @@ def build(force: bool = False, verbose: bool = False, extra_nvcc=None) -> str:
     for f in cpp:
         src, obj = os.path.join(CSRC, f), os.path.join(BUILD, f + ".o")
         if force or _stale(src, obj, hdr):
-            jobs.append(["g++", "-O2", "-std=c++17", "-fPIC", "-Wall", "-I", os.path.join(cuda, "include"),
+            jobs.append(["g++", "-O2", "-std=c++17", "-fPIC", "-pthread", "-Wall", "-I", os.path.join(cuda, "include"),
                          "-I", CSRC, "-I", INCLUDE, "-c", src, "-o", obj])
     objs = [os.path.join(BUILD, f + ".o") for f in cu + cpp]
 
@@ -88,7 +88,7 @@ def build(force: bool = False, verbose: bool = False, extra_nvcc=None) -> str:
                     print(msg, flush=True)
     if jobs or not os.path.exists(LIB):
         tmp = LIB + ".tmp"
-        run([nvcc, *ARCH, "-shared", "-o", tmp, *objs, "-lcudart", "-lcuda"])
+        run([nvcc, *ARCH, "-shared", "-Xcompiler", "-pthread", "-o", tmp, *objs, "-lcudart", "-lcuda"])
         os.replace(tmp, LIB)
     return LIB
 

@@ -11,12 +11,14 @@
 #include <complex>
 #include <cstdarg>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <deque>
 #include <memory>
 #include <mutex>
 #include <numeric>
 #include <string>
+#include <thread>
 #include <unordered_map>
 #include <vector>
 
@@ -594,6 +596,30 @@ struct Image {
   size_t pass_bytes() const { return passes.size() * sizeof(FusedPass); }
   size_t op_bytes() const { return ops.size() * sizeof(FusedOp); }
   size_t bytes() const { return circ_bytes() + pass_bytes() + op_bytes(); }
+  // Write program P as circuit i whose passes start at pass0 and ops at op0
+  // (the arrays are sized by the caller).
+  void fill(int i, const Program& P, int64_t out_off, int64_t pass0, int64_t op0) {
+    FusedCirc fc{};
+    fc.n = P.n;
+    fc.nint = P.nint;
+    fc.pass_begin = static_cast<int32_t>(pass0);
+    fc.pass_count = static_cast<int32_t>(P.passes.size());
+    fc.out_off = out_off;
+    fc.team = team_for(P.nint);
+    fc.identity = P.identity;
+    std::memcpy(fc.pos, P.pos, 16);
+    fc.init = nullptr;
+    fc.out_scale = P.out_scale;
+    fc.gen_index = P.gen_index;
+    circs[i] = fc;
+    for (size_t k = 0; k < P.passes.size(); ++k) {
+      FusedPass ps = P.passes[k];
+      ps.op_begin += static_cast<uint32_t>(op0);
+      passes[static_cast<size_t>(pass0) + k] = ps;
+    }
+    if (!P.ops.empty())
+      std::memcpy(&ops[static_cast<size_t>(op0)], P.ops.data(), P.ops.size() * sizeof(FusedOp));
+  }
   void add(const Program& P, int64_t out_off) {
     FusedCirc fc{};
     fc.n = P.n;
@@ -888,8 +914,6 @@ struct tqs_batch {
   void* g_probs = nullptr;
   void* g_norms = nullptr;
   int graph_kernels = 0;
-  // host-run buffers
-  DevBuf h_states, h_probs, h_norms;
   ~tqs_batch() {
     if (exec) cudaGraphExecDestroy(exec);
     if (graph) cudaGraphDestroy(graph);
@@ -897,13 +921,43 @@ struct tqs_batch {
   }
 };
 
+// Run body(i) for i in [0, count) on the host cores.
+template <class F>
+static void parallel_for(int count, int grain, F body) {
+  int hw = static_cast<int>(std::max(1u, std::thread::hardware_concurrency()));
+  if (const char* env = std::getenv("TQS_HOST_THREADS")) hw = std::max(1, std::atoi(env));
+  const int nthreads = std::min({hw, 32, std::max(1, count / std::max(1, grain))});
+  std::atomic<int> next{0};
+  auto work = [&]() {
+    for (int i = next.fetch_add(1); i < count; i = next.fetch_add(1)) body(i);
+  };
+  if (nthreads <= 1) {
+    work();
+    return;
+  }
+  std::vector<std::thread> pool;
+  pool.reserve(nthreads - 1);
+  for (int t = 1; t < nthreads; ++t) pool.emplace_back(work);
+  work();
+  for (std::thread& th : pool) th.join();
+}
+
 static tqs_status batch_finish(tqs_batch* b, std::vector<Program>& progs) {
   b->count = static_cast<int>(progs.size());
   b->offsets.assign(b->count + 1, 0);
-  for (int i = 0; i < b->count; ++i) b->offsets[i + 1] = b->offsets[i] + (int64_t(1) << progs[i].n);
+  std::vector<int64_t> pass0(b->count + 1, 0), op0(b->count + 1, 0);
+  for (int i = 0; i < b->count; ++i) {
+    b->offsets[i + 1] = b->offsets[i] + (int64_t(1) << progs[i].n);
+    pass0[i + 1] = pass0[i] + static_cast<int64_t>(progs[i].passes.size());
+    op0[i + 1] = op0[i] + static_cast<int64_t>(progs[i].ops.size());
+  }
+  // the image, filled in parallel from the prefix sums
+  b->img.circs.resize(b->count);
+  b->img.passes.resize(static_cast<size_t>(pass0.back()));
+  b->img.ops.resize(static_cast<size_t>(op0.back()));
+  parallel_for(b->count, 256, [&](int i) { b->img.fill(i, progs[i], b->offsets[i], pass0[i], op0[i]); });
   std::vector<int> idx[3];
   for (int i = 0; i < b->count; ++i) {
-    b->img.add(progs[i], b->offsets[i]);
     const int t = team_for(progs[i].nint);
     idx[t].push_back(i);
     b->max_nint[t] = std::max(b->max_nint[t], progs[i].nint);
@@ -945,33 +999,66 @@ tqs_status tqs_batch_create_packed(int count, const int32_t* h_nq, const int64_t
   std::unique_ptr<tqs_batch> b(new (std::nothrow) tqs_batch());
   if (!b) return fail(TQS_ERR_NOMEM, "tqs_batch_create_packed: out of host memory");
   std::vector<Program> progs(count);
-  std::vector<Gate> gates;
-  std::vector<int> last;
-  std::vector<const Gate*> order;
-  for (int i = 0; i < count; ++i) {
-    const int n = h_nq[i];
-    if (n < 1 || n > TQS_MAX_QUBITS)
-      return fail(TQS_ERR_TOO_MANY_QUBITS, "circuit %d: n %d outside [1, %d]", i, n, TQS_MAX_QUBITS);
-    const int64_t g0 = h_gate_off[i], g1 = h_gate_off[i + 1];
-    if (g1 < g0) return fail(TQS_ERR_ARG, "circuit %d: gate offsets decrease", i);
-    gates.assign(static_cast<size_t>(g1 - g0), Gate{});
-    last.assign(n, -1);
-    for (int64_t k = g0; k < g1; ++k) {
-      const int kind = h_kind[k];
-      const int nq = (kind >= 0 && kind < TQS_GATE_COUNT && is_two_qubit(kind)) ? 2 : 1;
-      Gate& g = gates[static_cast<size_t>(k - g0)];
-      tqs_status s = check_gate(n, kind, h_qubits + 2 * k, nq, h_params + 8 * k, 8, g);
-      if (s != TQS_OK) return s;
-      int step = 0;
-      for (int j = 0; j < g.nq; ++j) step = std::max(step, last[g.q[j]] + 1);
-      g.step = step;
-      for (int j = 0; j < g.nq; ++j) last[g.q[j]] = step;
+  std::vector<int> nsteps(count, 0);
+  // Circuits are independent: compile them on all host cores.  Each worker
+  // records its first failure; the lowest failing circuit index is reported.
+  struct Failure {
+    int index = -1;
+    tqs_status status = TQS_OK;
+    std::string message;
+  };
+  std::mutex fail_mu;
+  Failure first;
+  std::atomic<int> next_circuit{0};
+  auto work = [&]() {
+    std::vector<Gate> gates;
+    std::vector<int> last;
+    for (;;) {
+      const int i = next_circuit.fetch_add(1);
+      if (i >= count) return;
+      auto record = [&](tqs_status st) {
+        std::lock_guard<std::mutex> lock(fail_mu);
+        if (first.index < 0 || i < first.index) {
+          first.index = i;
+          first.status = st;
+          first.message = g_last_error;  // this worker thread's message
+        }
+      };
+      const int n = h_nq[i];
+      if (n < 1 || n > TQS_MAX_QUBITS) {
+        record(fail(TQS_ERR_TOO_MANY_QUBITS, "circuit %d: n %d outside [1, %d]", i, n, TQS_MAX_QUBITS));
+        continue;
+      }
+      const int64_t g0 = h_gate_off[i], g1 = h_gate_off[i + 1];
+      if (g1 < g0) {
+        record(fail(TQS_ERR_ARG, "circuit %d: gate offsets decrease", i));
+        continue;
+      }
+      gates.assign(static_cast<size_t>(g1 - g0), Gate{});
+      last.assign(n, -1);
+      tqs_status st = TQS_OK;
+      for (int64_t k = g0; k < g1 && st == TQS_OK; ++k) {
+        const int kind = h_kind[k];
+        const int nq = (kind >= 0 && kind < TQS_GATE_COUNT && is_two_qubit(kind)) ? 2 : 1;
+        Gate& g = gates[static_cast<size_t>(k - g0)];
+        st = check_gate(n, kind, h_qubits + 2 * k, nq, h_params + 8 * k, 8, g);
+        if (st != TQS_OK) break;
+        int step = 0;
+        for (int j = 0; j < g.nq; ++j) step = std::max(step, last[g.q[j]] + 1);
+        g.step = step;
+        for (int j = 0; j < g.nq; ++j) last[g.q[j]] = step;
+      }
+      if (st != TQS_OK) {
+        record(st);
+        continue;
+      }
+      for (int q = 0; q < n; ++q) nsteps[i] = std::max(nsteps[i], last[q] + 1);
+      compile_program(n, step_order(gates), progs[i]);
     }
-    int nsteps = 0;
-    for (int q = 0; q < n; ++q) nsteps = std::max(nsteps, last[q] + 1);
-    b->total_steps += nsteps;
-    compile_program(n, step_order(gates), progs[i]);
-  }
+  };
+  parallel_for(std::max(1, std::min(count / 64, 32)), 1, [&](int) { work(); });
+  if (first.index >= 0) return fail(first.status, "%s", first.message.c_str());
+  for (int i = 0; i < count; ++i) b->total_steps += nsteps[i];
   tqs_status s = batch_finish(b.get(), progs);
   if (s != TQS_OK) return s;
   *out = b.release();
@@ -1011,11 +1098,11 @@ static tqs_status batch_upload(tqs_batch* b, cudaStream_t s) {
 }
 
 // Enqueue the batch's kernels (memset of the job counters + one launch per
-// team kind present).  Returns the number of kernels launched.
-static tqs_status batch_enqueue(tqs_batch* b, float2* states, double* probs, double* norms,
-                                cudaStream_t s, int* kernels) {
-  char* base = b->d_img.as<char>();
-  int32_t* counters = reinterpret_cast<int32_t*>(base + b->counter_off);
+// team kind present) for a program image at `base`.
+static tqs_status batch_enqueue_at(tqs_batch* b, char* base, size_t order_off, size_t counter_off,
+                                   float2* gscratch, float2* states, double* probs, double* norms,
+                                   cudaStream_t s, int* kernels = nullptr) {
+  int32_t* counters = reinterpret_cast<int32_t*>(base + counter_off);
   TQS_CUDA(cudaMemsetAsync(counters, 0, 3 * sizeof(int32_t), s), "tqs_batch: memset counters");
   int k = 0;
   int first = 0;
@@ -1025,13 +1112,13 @@ static tqs_status batch_enqueue(tqs_batch* b, float2* states, double* probs, dou
     L.circs = reinterpret_cast<const FusedCirc*>(base);
     L.passes = reinterpret_cast<const FusedPass*>(base + b->img.circ_bytes());
     L.ops = reinterpret_cast<const FusedOp*>(base + b->img.circ_bytes() + b->img.pass_bytes());
-    L.order = reinterpret_cast<const int32_t*>(base + b->order_off) + first;
+    L.order = reinterpret_cast<const int32_t*>(base + order_off) + first;
     L.n_jobs = b->n_team[t];
     L.counter = counters + t;
     L.out = states;
     L.probs = probs;
     L.norms = norms;
-    L.gscratch = b->d_gscratch.as<float2>();
+    L.gscratch = gscratch;
     L.team = t;
     L.warps_per_cta = b->plans[t].warps;
     L.slice_q = b->plans[t].slice_q;
@@ -1042,6 +1129,26 @@ static tqs_status batch_enqueue(tqs_batch* b, float2* states, double* probs, dou
   }
   if (kernels) *kernels = k;
   return TQS_OK;
+}
+
+static tqs_status batch_enqueue(tqs_batch* b, float2* states, double* probs, double* norms,
+                                cudaStream_t s, int* kernels) {
+  return batch_enqueue_at(b, b->d_img.as<char>(), b->order_off, b->counter_off,
+                          b->d_gscratch.as<float2>(), states, probs, norms, s, kernels);
+}
+
+// Keep freed stream-ordered allocations in the device's default memory pool
+// (the process's own pool) so that repeated calls do not go back to the driver.
+static void keep_pool_memory() {
+  static std::once_flag once;
+  std::call_once(once, [] {
+    int dev = 0;
+    cudaMemPool_t pool;
+    if (cudaGetDevice(&dev) == cudaSuccess && cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) {
+      uint64_t thr = UINT64_MAX;
+      cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
+    }
+  });
 }
 
 extern "C" {
@@ -1091,16 +1198,32 @@ tqs_status tqs_batch_run_host(tqs_batch* b, tqs_c64* h_states, double* h_probs, 
                               void* stream) {
   if (!b) return fail(TQS_ERR_ARG, "tqs_batch_run_host: batch is NULL");
   cudaStream_t s = static_cast<cudaStream_t>(stream);
-  tqs_status st = batch_upload(b, s);  // the program is this call's input
-  if (st != TQS_OK) return st;
+  keep_pool_memory();
+  // Everything this call needs on the device (the program is its input) comes
+  // stream-ordered from the device's memory pool and goes back to it at the end.
   const size_t amps = static_cast<size_t>(b->offsets.back());
-  TQS_CUDA(b->h_states.ensure(amps * sizeof(float2)), "tqs_batch_run_host: cudaMalloc states");
-  if (h_probs) TQS_CUDA(b->h_probs.ensure(amps * sizeof(double)), "tqs_batch_run_host: cudaMalloc probs");
-  TQS_CUDA(b->h_norms.ensure(size_t(b->count) * sizeof(double)), "tqs_batch_run_host: cudaMalloc norms");
-  float2* ds = b->h_states.as<float2>();
-  double* dp = h_probs ? b->h_probs.as<double>() : nullptr;
-  double* dn = b->h_norms.as<double>();
-  st = batch_enqueue(b, ds, dp, dn, s, nullptr);
+  const size_t order_off = (b->img.bytes() + 255) & ~size_t(255);
+  const size_t counter_off = (order_off + b->order.size() * sizeof(int32_t) + 255) & ~size_t(255);
+  const size_t states_off = counter_off + 256;
+  const size_t probs_off = (states_off + amps * sizeof(float2) + 255) & ~size_t(255);
+  const size_t norms_off = (probs_off + (h_probs ? amps * sizeof(double) : 0) + 255) & ~size_t(255);
+  const size_t total = norms_off + size_t(b->count) * sizeof(double);
+  for (int t = 0; t < 3; ++t) b->plans[t] = plan_for(t, b->max_nint[t], b->n_team[t], 0);
+  const size_t gscr = b->n_team[TEAM_GLOBAL]
+                          ? size_t(b->plans[TEAM_GLOBAL].grid) * (size_t(1) << kGlobalSlotQ) * sizeof(float2)
+                          : 0;
+  char* base = nullptr;
+  TQS_CUDA(cudaMallocAsync(reinterpret_cast<void**>(&base), total + gscr, s),
+           "tqs_batch_run_host: cudaMallocAsync");
+  TQS_CUDA(b->img.upload(base, s), "tqs_batch_run_host: upload program");
+  TQS_CUDA(cudaMemcpyAsync(base + order_off, b->order.data(), b->order.size() * sizeof(int32_t),
+                           cudaMemcpyHostToDevice, s),
+           "tqs_batch_run_host: upload order");
+  float2* ds = reinterpret_cast<float2*>(base + states_off);
+  double* dp = h_probs ? reinterpret_cast<double*>(base + probs_off) : nullptr;
+  double* dn = reinterpret_cast<double*>(base + norms_off);
+  tqs_status st = batch_enqueue_at(b, base, order_off, counter_off,
+                                   reinterpret_cast<float2*>(base + total), ds, dp, dn, s);
   if (st != TQS_OK) return st;
   if (h_states)
     TQS_CUDA(cudaMemcpyAsync(h_states, ds, amps * sizeof(float2), cudaMemcpyDeviceToHost, s), "D2H states");
@@ -1109,6 +1232,7 @@ tqs_status tqs_batch_run_host(tqs_batch* b, tqs_c64* h_states, double* h_probs, 
   if (h_norms)
     TQS_CUDA(cudaMemcpyAsync(h_norms, dn, size_t(b->count) * sizeof(double), cudaMemcpyDeviceToHost, s),
              "D2H norms");
+  TQS_CUDA(cudaFreeAsync(base, s), "tqs_batch_run_host: cudaFreeAsync");
   TQS_CUDA(cudaStreamSynchronize(s), "tqs_batch_run_host: sync");
   return TQS_OK;
 }
