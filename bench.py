@@ -192,6 +192,27 @@ class ClockSampler:
                 "samples": len(inside), "window": window}
 
 
+def replica_circuits(W, rank, batch):
+    """This rank's share: its own seeded batch of the workload (weak scaling;
+    circuits are independent, so ranks exchange no data)."""
+    return [(N_QUBITS, ops) for _, ops in W.paper_mix(N_QUBITS, batch, seed_tag=1 + 1000 * rank)]
+
+
+def max_over_ranks(x, dist, device):
+    """The largest value of x over all ranks (x itself without a process group)."""
+    if dist is None:
+        return float(x)
+    import torch
+    t = torch.tensor([float(x)], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(units_per_rank, world, seconds_max):
+    """Units all ranks processed per second of the slowest rank."""
+    return units_per_rank * world / seconds_max
+
+
 def smi_index(local):
     """nvidia-smi -i argument of this rank's GPU (index or UUID)."""
     cvd = os.environ.get("CUDA_VISIBLE_DEVICES")
@@ -223,7 +244,7 @@ def run_tqs(args):
     B.lib()
 
     # ---------------------------------------------------------- inputs
-    circs = [(N_QUBITS, ops) for _, ops in W.paper_mix(N_QUBITS, args.batch, seed_tag=1 + 1000 * rank)]
+    circs = replica_circuits(W, rank, args.batch)
     from paper_2305_14398_gb300 import autotune
     tuned = autotune.tune_warps_per_cta(circs, sample=4096)
     arrays = B.pack_ops(circs)
@@ -268,12 +289,8 @@ def run_tqs(args):
         dist.barrier()
     sampler.stop()
     step_ms = [s.elapsed_time(e) for s, e in ev]
-    total_s = sum(step_ms) / 1e3
-    if dist:
-        t = torch.tensor([total_s], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_s = float(t.item())
-    value = count * world * args.steps / total_s
+    total_s = max_over_ranks(sum(step_ms) / 1e3, dist, "cuda")
+    value = whole_job_rate(count * args.steps, world, total_s)
     ms_step = 1e3 * total_s / args.steps
 
     # sanity: every norm within 1e-6 of 1
@@ -359,12 +376,8 @@ def run_tqs(args):
             bb = B.tqs_batch_create_packed(*arrays)
             B.tqs_batch_run_host(bb, h_states, h_probs, h_norms)
             B.tqs_batch_destroy(bb)
-        te = time.perf_counter() - te0
-        if dist:
-            t = torch.tensor([te], device="cuda", dtype=torch.float64)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            te = float(t.item())
-        line["e2e"] = {"value": count * world * e2e_steps / te, "unit": "circuits/s",
+        te = max_over_ranks(time.perf_counter() - te0, dist, "cuda")
+        line["e2e"] = {"value": whole_job_rate(count * e2e_steps, world, te), "unit": "circuits/s",
                        "h2d_bytes_per_step": int(prog_bytes),
                        "d2h_bytes_per_step": int(total * 8 + total * 8 + count * 8),
                        "steps": e2e_steps,

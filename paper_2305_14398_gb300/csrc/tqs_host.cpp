@@ -1554,6 +1554,18 @@ tqs_status tqs_server_poll(tqs_server* sv, int64_t* h_done_tags, int max_done, i
     if (!sl.stream) {
       TQS_CUDA(cudaStreamCreateWithFlags(&sl.stream, cudaStreamNonBlocking), "tqs_server: stream");
       TQS_CUDA(cudaEventCreateWithFlags(&sl.done, cudaEventDisableTiming), "tqs_server: event");
+      // Reserve pinned staging up front (cudaMallocHost is slow and
+      // synchronising): room for a batch of 16 MiB of states and its program.
+      void* p = nullptr;
+      TQS_CUDA(grow_pinned(&p, &sl.h_cap_amps, size_t(16) << 20), "tqs_server: cudaMallocHost");
+      sl.h_states = static_cast<float2*>(p);
+      p = nullptr;
+      TQS_CUDA(grow_pinned(&p, &sl.h_cap_norms, size_t(sv->max_batch) * sizeof(double)),
+               "tqs_server: cudaMallocHost");
+      sl.h_norms = static_cast<double*>(p);
+      p = nullptr;
+      TQS_CUDA(grow_pinned(&p, &sl.h_prog_cap, size_t(4) << 20), "tqs_server: cudaMallocHost");
+      sl.h_prog = static_cast<char*>(p);
     }
     size_t bytes = 0;
     while (!sv->queue.empty() && static_cast<int>(sl.reqs.size()) < sv->max_batch &&
