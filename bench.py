@@ -431,8 +431,11 @@ def bench_chain(B, W, torch, peaks):
     out = {"workload": "random layered: 20 x (U3 on every qubit + CNOTs on n/2 seeded pairs), "
                        "40 steps, U = S_40 ... S_1",
            "tensor_peak_tflops": peak, "peak_source": "measured bf16 burst"}
-    for n, prec, reps in [(12, B.PREC_TC_BF16X3, 3), (12, B.PREC_FP32_SIMT, 1),
-                          (13, B.PREC_TC_BF16X3, 2), (14, B.PREC_TC_BF16X3, 1)]:
+    names = {B.PREC_TC_BF16X3: "tc_bf16x3", B.PREC_TC_TF32X3: "tc_tf32x3",
+             B.PREC_FP32_SIMT: "fp32_simt"}
+    for n, prec, reps in [(12, B.PREC_TC_BF16X3, 3), (12, B.PREC_TC_TF32X3, 2),
+                          (12, B.PREC_FP32_SIMT, 1), (13, B.PREC_TC_BF16X3, 2),
+                          (14, B.PREC_TC_BF16X3, 1)]:
         ops = W.random_layered(n, 20, (2, n))
         c = B.circuit_from_ops(n, ops)
         U = torch.empty((1 << n, 1 << n), dtype=torch.complex64, device="cuda")
@@ -447,13 +450,16 @@ def bench_chain(B, W, torch, peaks):
         sec = s.elapsed_time(e) / 1e3 / reps
         N = 1 << n
         gemms = B.tqs_circuit_info(c)[2] - 1
-        key = f"n{n}_{'tc_bf16x3' if prec == B.PREC_TC_BF16X3 else 'fp32_simt'}"
+        key = f"n{n}_{names[prec]}"
         rec = {"ms": 1e3 * sec, "gemms": gemms,
                "useful_complex_gflops": 8.0 * N ** 3 * gemms / sec / 1e9}
-        if prec == B.PREC_TC_BF16X3:
+        if prec != B.PREC_FP32_SIMT:
             issued = 18.0 * N ** 3 * gemms / sec / 1e12  # 3 real GEMMs x 3 split products
             rec["issued_tensor_tflops"] = issued
-            rec["tensor_frac"] = issued / peak
+            # TF32 MMAs run at half the BF16 rate (nominal ratio 1.1 / 2.25 dense)
+            own_peak = peak if prec == B.PREC_TC_BF16X3 else peak * 1.1 / 2.25
+            rec["tensor_peak_tflops"] = own_peak
+            rec["tensor_frac"] = issued / own_peak
         if n == 12:
             cols = [0, 1, 777, 2048, 4095]
             got = U[:, cols].cpu().numpy().astype(np.complex128)

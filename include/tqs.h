@@ -84,8 +84,7 @@ typedef enum {
   TQS_PREC_FP32_SIMT = 0,   /* FP32 CUDA-core complex GEMM (4 real products) */
   TQS_PREC_TC_BF16X3 = 1,   /* tcgen05 tensor cores, 3M complex product, each real
                                product as BF16 hi*hi + hi*lo + lo*hi, FP32 accumulate */
-  TQS_PREC_TC_TF32X3 = 2    /* as above with TF32 hi/lo splits (not built yet:
-                               returns TQS_ERR_UNSUPPORTED) */
+  TQS_PREC_TC_TF32X3 = 2    /* as above with TF32 hi/lo splits (kind::tf32) */
 } tqs_prec;
 
 #define TQS_MAX_QUBITS 16          /* state-vector calls */
@@ -182,7 +181,8 @@ tqs_status tqs_materialize_step(tqs_circuit* c, int step, tqs_c64* d_S, void* st
  *   d_U : 2^n x 2^n tqs_c64, row-major, d_U[r * 2^n + c] = <r|U|c>.
  * n <= TQS_MAX_DENSE_QUBITS; tensor-core precisions need n >= 7.
  * Scratch (cached on the circuit): 36 * 4^n bytes for TQS_PREC_TC_BF16X3
- * (three matrices of six BF16 planes), 24 * 4^n for TQS_PREC_FP32_SIMT.
+ * (three matrices of six BF16 planes), 72 * 4^n for TQS_PREC_TC_TF32X3 (FP32
+ * words), 24 * 4^n for TQS_PREC_FP32_SIMT.
  * The tensor-core form synchronises `stream` before returning and returns
  * TQS_ERR_TIMEOUT if one of its bounded device waits ran out. */
 tqs_status tqs_circuit_unitary(tqs_circuit* c, int prec, tqs_c64* d_U, void* stream);

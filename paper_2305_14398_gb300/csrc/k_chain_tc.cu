@@ -6,13 +6,14 @@
 // The complex product uses three real GEMMs (3M):
 //   T1 = Vr Sr^T, T2 = Vi Si^T, T3 = (Vr + Vi)(Sr + Si)^T,
 //   Re V' = T1 - T2, Im V' = T3 - T1 - T2,
-// and every real operand X is split into BF16 planes X = Xh + Xl, each real
-// GEMM being Xh Yh^T + Xh Yl^T + Xl Yh^T accumulated in FP32 in TMEM.
-// A matrix is stored as 6 BF16 planes [Re h, Re l, Im h, Im l, Sum h, Sum l],
+// and every real operand X is split into planes X = Xh + Xl of the MMA input
+// type (BF16, or TF32 stored in FP32 words), each real GEMM being
+// Xh Yh^T + Xh Yl^T + Xl Yh^T accumulated in FP32 in TMEM.
+// A matrix is stored as 6 planes [Re h, Re l, Im h, Im l, Sum h, Sum l],
 // each N x N row-major, read by 3-D TMA ([plane][row][k]).
 //
-// GEMM tile: 128 x 128 output, K step 64 (one 128-byte swizzled row), 3 stages
-// of {A h, A l, B h, B l} (64 KiB each).  Warp 0 issues TMA, warp 1 issues the
+// GEMM tile: 128 x 128 output, K step one 128-byte swizzled row (64 BF16 or
+// 32 TF32), 3 stages of {A h, A l, B h, B l} (64 KiB each).  Warp 0 issues TMA, warp 1 issues the
 // MMAs (one thread), warps 2-5 read the three accumulators from TMEM and write
 // either the 6 planes of V' or, at the last step, U = V'^T as complex64.
 #include <cuda.h>
@@ -22,6 +23,7 @@
 
 #include "sm100_ptx.h"
 #include "step_entry.h"
+#include "../../include/tqs.h"
 #include "tqs_internal.h"
 
 namespace tqs {
@@ -29,31 +31,84 @@ namespace {
 
 using namespace ptx;
 
-constexpr int BM = 128, BN = 128, BK = 64;
+constexpr int BM = 128, BN = 128;
+constexpr int kRowBytes = 128;                 // one swizzled row of K per tile row
 constexpr int kStages = 3;
-constexpr int kTileBytes = BM * BK * 2;        // 16 KiB, A and B tiles alike
+constexpr int kTileBytes = BM * kRowBytes;     // 16 KiB, A and B tiles alike
 constexpr int kStageBytes = 4 * kTileBytes;    // A hi, A lo, B hi, B lo
 constexpr int kGemmThreads = 192;
 constexpr uint32_t kTmemCols = 512;            // 3 accumulators x 128 columns
 constexpr size_t kGemmSmem = size_t(kStages) * kStageBytes + 1024 + 256;
 constexpr int kGroupM = 16;                    // tile rows per raster band
 
+// Operand precision: the element type of the planes, the MMA kind, and the
+// hi/lo split of an FP32 value.
+template <int PREC>
+struct Prec;
+
+template <>
+struct Prec<TQS_PREC_TC_BF16X3> {
+  using E = __nv_bfloat16;
+  static constexpr int BK = kRowBytes / 2;  // 64
+  static constexpr CUtensorMapDataType kTmaType = CU_TENSOR_MAP_DATA_TYPE_BFLOAT16;
+  static __device__ __forceinline__ void mma(uint32_t d, uint64_t a, uint64_t b, uint32_t acc) {
+    mma_bf16(d, a, b, idesc_bf16_f32(BM, BN), acc);
+  }
+  static __device__ __forceinline__ void split(float x, E& h, E& l) {
+    h = __float2bfloat16_rn(x);
+    l = __float2bfloat16_rn(x - __bfloat162float(h));
+  }
+};
+
+template <>
+struct Prec<TQS_PREC_TC_TF32X3> {
+  using E = float;  // TF32 values (low 13 mantissa bits zero) in FP32 words
+  static constexpr int BK = kRowBytes / 4;  // 32
+  static constexpr CUtensorMapDataType kTmaType = CU_TENSOR_MAP_DATA_TYPE_FLOAT32;
+  static __device__ __forceinline__ void mma(uint32_t d, uint64_t a, uint64_t b, uint32_t acc) {
+    mma_tf32(d, a, b, idesc_tf32_f32(BM, BN), acc);
+  }
+  static __device__ __forceinline__ void split(float x, E& h, E& l) {
+    h = to_tf32(x);
+    l = to_tf32(x - h);
+  }
+};
+
+template <class E>
 struct GemmParams {
   int N;
-  int final_step;            // 1: write U = V'^T (complex64); 0: the 6 planes of V'
-  __nv_bfloat16* planes;     // [6][N][N] output planes (final_step == 0)
-  float2* u;                 // [N][N] output (final_step == 1)
+  int final_step;  // 1: write U = V'^T (complex64); 0: the 6 planes of V'
+  E* planes;       // [6][N][N] output planes (final_step == 0)
+  float2* u;       // [N][N] output (final_step == 1)
   int* err;
 };
 
-__device__ __forceinline__ uint32_t pack_bf16x2(__nv_bfloat16 lo, __nv_bfloat16 hi) {
-  return static_cast<uint32_t>(__bfloat16_as_ushort(lo)) |
-         (static_cast<uint32_t>(__bfloat16_as_ushort(hi)) << 16);
+// Split K FP32 values into hi / lo planes and store them at hp / lp (16-byte stores).
+template <int PREC, int K>
+__device__ __forceinline__ void store_split(const float (&v)[K], typename Prec<PREC>::E* hp,
+                                            typename Prec<PREC>::E* lp) {
+  using E = typename Prec<PREC>::E;
+  constexpr int per16 = 16 / sizeof(E);
+  static_assert(K % per16 == 0, "whole 16-byte stores");
+#pragma unroll
+  for (int i0 = 0; i0 < K; i0 += per16) {
+    union {
+      E e[per16];
+      uint4 u;
+    } h, l;
+#pragma unroll
+    for (int i = 0; i < per16; ++i) Prec<PREC>::split(v[i0 + i], h.e[i], l.e[i]);
+    *reinterpret_cast<uint4*>(hp + i0) = h.u;
+    *reinterpret_cast<uint4*>(lp + i0) = l.u;
+  }
 }
 
+template <int PREC>
 __global__ void __launch_bounds__(kGemmThreads, 1)
     chain_gemm_kernel(const __grid_constant__ CUtensorMap tmA,
-                      const __grid_constant__ CUtensorMap tmB, const GemmParams P) {
+                      const __grid_constant__ CUtensorMap tmB,
+                      const GemmParams<typename Prec<PREC>::E> P) {
+  constexpr int BK = Prec<PREC>::BK;
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>(
       (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
@@ -121,7 +176,6 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
     }
   } else if (warp == 1) {
     if (lane == 0) {
-      const uint32_t idesc = idesc_bf16_f32(BM, BN);
       for (int it = 0; it < iters; ++it) {
         const int s = it % kStages;
         const uint32_t ph = (it / kStages) & 1;
@@ -134,12 +188,12 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
         const uint32_t b_hi = a_hi + 2 * kTileBytes;
         const uint32_t b_lo = a_hi + 3 * kTileBytes;
 #pragma unroll
-        for (int ks = 0; ks < BK / 16; ++ks) {
-          const uint32_t off = ks * 32;  // 16 BF16 along K inside the swizzled row
+        for (int ks = 0; ks < kRowBytes / 32; ++ks) {
+          const uint32_t off = ks * 32;  // one MMA's K (32 bytes) inside the swizzled row
           const uint32_t acc = (kb > 0 || ks > 0) ? 1u : 0u;
-          mma_bf16(d, sw128_kmajor_desc(a_hi + off), sw128_kmajor_desc(b_hi + off), idesc, acc);
-          mma_bf16(d, sw128_kmajor_desc(a_hi + off), sw128_kmajor_desc(b_lo + off), idesc, 1u);
-          mma_bf16(d, sw128_kmajor_desc(a_lo + off), sw128_kmajor_desc(b_hi + off), idesc, 1u);
+          Prec<PREC>::mma(d, sw128_kmajor_desc(a_hi + off), sw128_kmajor_desc(b_hi + off), acc);
+          Prec<PREC>::mma(d, sw128_kmajor_desc(a_hi + off), sw128_kmajor_desc(b_lo + off), 1u);
+          Prec<PREC>::mma(d, sw128_kmajor_desc(a_lo + off), sw128_kmajor_desc(b_hi + off), 1u);
         }
         mma_commit(smem_u32(&empty[s]));  // the stage is free once these MMAs finish
       }
@@ -170,35 +224,18 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
             P.u[static_cast<size_t>(tile_n + c0 + i) * P.N + gm] = make_float2(re, im);
           }
         } else {
-          __nv_bfloat16* rowp = P.planes + static_cast<size_t>(gm) * P.N + tile_n + c0;
+          // in place: t1 <- Re, t2 <- Im, t3 <- Re + Im
 #pragma unroll
-          for (int i0 = 0; i0 < 32; i0 += 8) {
-            uint32_t w[6][4];
-#pragma unroll
-            for (int i = 0; i < 8; i += 2) {
-              float v[3][2];
-#pragma unroll
-              for (int h = 0; h < 2; ++h) {
-                const float a = t1[i0 + i + h], b = t2[i0 + i + h], c = t3[i0 + i + h];
-                v[0][h] = a - b;          // Re
-                v[1][h] = c - a - b;      // Im
-                v[2][h] = v[0][h] + v[1][h];
-              }
-#pragma unroll
-              for (int comp = 0; comp < 3; ++comp) {
-                const __nv_bfloat16 h0 = __float2bfloat16_rn(v[comp][0]);
-                const __nv_bfloat16 h1 = __float2bfloat16_rn(v[comp][1]);
-                const __nv_bfloat16 l0 = __float2bfloat16_rn(v[comp][0] - __bfloat162float(h0));
-                const __nv_bfloat16 l1 = __float2bfloat16_rn(v[comp][1] - __bfloat162float(h1));
-                w[2 * comp][i / 2] = pack_bf16x2(h0, h1);
-                w[2 * comp + 1][i / 2] = pack_bf16x2(l0, l1);
-              }
-            }
-#pragma unroll
-            for (int p = 0; p < 6; ++p)
-              *reinterpret_cast<uint4*>(rowp + p * NN + i0) =
-                  make_uint4(w[p][0], w[p][1], w[p][2], w[p][3]);
+          for (int i = 0; i < 32; ++i) {
+            const float a = t1[i], b = t2[i], c = t3[i];
+            t1[i] = a - b;
+            t2[i] = c - a - b;
+            t3[i] = t1[i] + t2[i];
           }
+          typename Prec<PREC>::E* rowp = P.planes + static_cast<size_t>(gm) * P.N + tile_n + c0;
+          store_split<PREC, 32>(t1, rowp, rowp + NN);
+          store_split<PREC, 32>(t2, rowp + 2 * NN, rowp + 3 * NN);
+          store_split<PREC, 32>(t3, rowp + 4 * NN, rowp + 5 * NN);
         }
       }
     }
@@ -212,53 +249,44 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
 }
 
 // Operand planes of a step unitary: for each entry, Re, Im and Re + Im, each
-// split into BF16 hi + lo.  transpose = 0: plane[r][c] = S[r][c] (the B
-// operand); transpose = 1: plane[c][r] = S[r][c] (the initial V = S_1^T).
-// A thread produces 8 consecutive entries of one output row.
+// split into hi + lo of the MMA input type.  transpose = 0: plane[r][c] =
+// S[r][c] (the B operand); transpose = 1: plane[c][r] = S[r][c] (the initial
+// V = S_1^T).  A thread produces 32 consecutive entries of one output row.
 constexpr int kGenThreads = 256;
 constexpr int kMaxFactors = 16;
 
+template <int PREC>
 __global__ void __launch_bounds__(kGenThreads)
     gen_planes_kernel(const StepFactor* __restrict__ factors, int nf, uint32_t idle, int n,
-                      int transpose, __nv_bfloat16* __restrict__ planes) {
+                      int transpose, typename Prec<PREC>::E* __restrict__ planes) {
   __shared__ StepFactor fs[kMaxFactors];
   for (int i = threadIdx.x; i < nf * static_cast<int>(sizeof(StepFactor) / 8); i += blockDim.x)
     reinterpret_cast<float2*>(fs)[i] = reinterpret_cast<const float2*>(factors)[i];
   __syncthreads();
   const int64_t N = int64_t(1) << n;
   const size_t NN = static_cast<size_t>(N) * N;
-  const int64_t chunks = (N * N) >> 3;
+  const int64_t chunks = (N * N) >> 5;
   const int64_t stride = int64_t(gridDim.x) * blockDim.x;
   for (int64_t e = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; e < chunks; e += stride) {
-    const int64_t flat = e << 3;
+    const int64_t flat = e << 5;
     const uint32_t orow = static_cast<uint32_t>(flat >> n);
     const uint32_t ocol = static_cast<uint32_t>(flat & (N - 1));
-    uint32_t w[6][4];
+    for (int i0 = 0; i0 < 32; i0 += 8) {
+      float re[8], im[8], sm[8];
 #pragma unroll
-    for (int i = 0; i < 8; i += 2) {
-      float v[3][2];
-#pragma unroll
-      for (int h = 0; h < 2; ++h) {
-        const uint32_t r = transpose ? ocol + i + h : orow;
-        const uint32_t c = transpose ? orow : ocol + i + h;
+      for (int i = 0; i < 8; ++i) {
+        const uint32_t r = transpose ? ocol + i0 + i : orow;
+        const uint32_t c = transpose ? orow : ocol + i0 + i;
         const float2 z = step_entry(fs, nf, idle, r, c);
-        v[0][h] = z.x;
-        v[1][h] = z.y;
-        v[2][h] = z.x + z.y;
+        re[i] = z.x;
+        im[i] = z.y;
+        sm[i] = z.x + z.y;
       }
-#pragma unroll
-      for (int comp = 0; comp < 3; ++comp) {
-        const __nv_bfloat16 h0 = __float2bfloat16_rn(v[comp][0]);
-        const __nv_bfloat16 h1 = __float2bfloat16_rn(v[comp][1]);
-        const __nv_bfloat16 l0 = __float2bfloat16_rn(v[comp][0] - __bfloat162float(h0));
-        const __nv_bfloat16 l1 = __float2bfloat16_rn(v[comp][1] - __bfloat162float(h1));
-        w[2 * comp][i / 2] = pack_bf16x2(h0, h1);
-        w[2 * comp + 1][i / 2] = pack_bf16x2(l0, l1);
-      }
+      typename Prec<PREC>::E* base = planes + flat + i0;
+      store_split<PREC, 8>(re, base, base + NN);
+      store_split<PREC, 8>(im, base + 2 * NN, base + 3 * NN);
+      store_split<PREC, 8>(sm, base + 4 * NN, base + 5 * NN);
     }
-#pragma unroll
-    for (int p = 0; p < 6; ++p)
-      *reinterpret_cast<uint4*>(planes + p * NN + flat) = make_uint4(w[p][0], w[p][1], w[p][2], w[p][3]);
   }
 }
 
@@ -283,17 +311,19 @@ EncodeTiledFn encode_fn() {
   return fn;
 }
 
-// [6][N][N] BF16 planes as a 3-D tensor {k, row, plane}, box {64, 128, 1},
-// 128-byte swizzle.
+// [6][N][N] planes as a 3-D tensor {k, row, plane}, box {one 128-byte row, 128
+// rows, 1 plane}, 128-byte swizzle.
+template <int PREC>
 bool make_planes_map(CUtensorMap* m, void* base, int N) {
   EncodeTiledFn fn = encode_fn();
   if (!fn) return false;
+  const cuuint64_t es = sizeof(typename Prec<PREC>::E);
   const cuuint64_t dims[3] = {static_cast<cuuint64_t>(N), static_cast<cuuint64_t>(N), 6};
-  const cuuint64_t strides[2] = {static_cast<cuuint64_t>(N) * 2,
-                                 static_cast<cuuint64_t>(N) * N * 2};
-  const cuuint32_t box[3] = {BK, BM, 1};
+  const cuuint64_t strides[2] = {static_cast<cuuint64_t>(N) * es,
+                                 static_cast<cuuint64_t>(N) * N * es};
+  const cuuint32_t box[3] = {static_cast<cuuint32_t>(Prec<PREC>::BK), BM, 1};
   const cuuint32_t estr[3] = {1, 1, 1};
-  return fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, base, dims, strides, box, estr,
+  return fn(m, Prec<PREC>::kTmaType, 3, base, dims, strides, box, estr,
             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
             CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
@@ -309,18 +339,58 @@ int sms() {
   return v;
 }
 
+template <int PREC>
 cudaError_t launch_gen(const StepFactor* d_factors, const StepDesc& st, int n, int transpose,
-                       __nv_bfloat16* planes, cudaStream_t s) {
+                       typename Prec<PREC>::E* planes, cudaStream_t s) {
   if (st.f_count > kMaxFactors) return cudaErrorInvalidValue;
   const int64_t N = int64_t(1) << n;
-  int64_t blocks = ((N * N) / 8 + kGenThreads - 1) / kGenThreads;
+  int64_t blocks = ((N * N) / 32 + kGenThreads - 1) / kGenThreads;
   const int64_t cap = int64_t(sms()) * 16;
   if (blocks > cap) blocks = cap;
   if (blocks < 1) blocks = 1;
-  gen_planes_kernel<<<static_cast<int>(blocks), kGenThreads, 0, s>>>(
+  gen_planes_kernel<PREC><<<static_cast<int>(blocks), kGenThreads, 0, s>>>(
       d_factors + st.f_begin, st.f_count, st.idle, n, transpose, planes);
   count_launches(1);
   return cudaGetLastError();
+}
+
+template <int PREC>
+cudaError_t chain_tc_impl(const StepFactor* d_factors, const StepDesc* steps, int nsteps, int n,
+                          float2* d_U, void* scratch, int* d_err, cudaStream_t s) {
+  using E = typename Prec<PREC>::E;
+  const int N = 1 << n;
+  const size_t NN = size_t(N) * N;
+  E* V0 = static_cast<E*>(scratch);
+  E* V1 = V0 + 6 * NN;
+  E* S = V1 + 6 * NN;
+  CUtensorMap mV0, mV1, mS;
+  if (!make_planes_map<PREC>(&mV0, V0, N) || !make_planes_map<PREC>(&mV1, V1, N) ||
+      !make_planes_map<PREC>(&mS, S, N))
+    return cudaErrorNotSupported;
+  cudaError_t e = cudaFuncSetAttribute(chain_gemm_kernel<PREC>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       static_cast<int>(kGemmSmem));
+  if (e != cudaSuccess) return e;
+  e = launch_gen<PREC>(d_factors, steps[0], n, 1, V0, s);  // V = S_1^T
+  if (e != cudaSuccess) return e;
+  bool cur0 = true;
+  for (int k = 1; k < nsteps; ++k) {
+    e = launch_gen<PREC>(d_factors, steps[k], n, 0, S, s);
+    if (e != cudaSuccess) return e;
+    GemmParams<E> P;
+    P.N = N;
+    P.final_step = (k == nsteps - 1) ? 1 : 0;
+    P.planes = cur0 ? V1 : V0;
+    P.u = d_U;
+    P.err = d_err;
+    const int grid = (N / BN) * (N / BM);
+    chain_gemm_kernel<PREC><<<grid, kGemmThreads, kGemmSmem, s>>>(cur0 ? mV0 : mV1, mS, P);
+    count_launches(1);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    cur0 = !cur0;
+  }
+  return cudaSuccess;
 }
 
 __global__ void wait_selftest_kernel(int* status, long long wait_cycles) {
@@ -346,46 +416,22 @@ cudaError_t launch_wait_selftest(int* status, long long wait_cycles, cudaStream_
   return cudaGetLastError();
 }
 
-size_t chain_tc_scratch_bytes(int n) {
+size_t chain_tc_scratch_bytes(int n, int prec) {
   const size_t N = size_t(1) << n;
-  return 18 * N * N * sizeof(__nv_bfloat16);  // V, V' and S: 6 planes each
+  const size_t es = prec == TQS_PREC_TC_TF32X3 ? 4 : 2;
+  return 18 * N * N * es;  // V, V' and S: 6 planes each
 }
 
-// U = S_m ... S_1 with the BF16x3 tcgen05 chain.  n >= 7 (N a multiple of 128).
+// U = S_m ... S_1 with the tensor-core chain in precision `prec`
+// (TQS_PREC_TC_BF16X3 or TQS_PREC_TC_TF32X3).  n >= 7 (N a multiple of 128).
 cudaError_t chain_tc(const StepFactor* d_factors, const StepDesc* steps, int nsteps, int n,
-                     float2* d_U, void* scratch, int* d_err, cudaStream_t s) {
+                     int prec, float2* d_U, void* scratch, int* d_err, cudaStream_t s) {
   if (n < 7 || nsteps < 2) return cudaErrorInvalidValue;
-  const int N = 1 << n;
-  const size_t NN = size_t(N) * N;
-  __nv_bfloat16* V0 = static_cast<__nv_bfloat16*>(scratch);
-  __nv_bfloat16* V1 = V0 + 6 * NN;
-  __nv_bfloat16* S = V1 + 6 * NN;
-  CUtensorMap mV0, mV1, mS;
-  if (!make_planes_map(&mV0, V0, N) || !make_planes_map(&mV1, V1, N) || !make_planes_map(&mS, S, N))
-    return cudaErrorNotSupported;
-  cudaError_t e = cudaFuncSetAttribute(chain_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       static_cast<int>(kGemmSmem));
-  if (e != cudaSuccess) return e;
-  e = launch_gen(d_factors, steps[0], n, 1, V0, s);  // V = S_1^T
-  if (e != cudaSuccess) return e;
-  bool cur0 = true;
-  for (int k = 1; k < nsteps; ++k) {
-    e = launch_gen(d_factors, steps[k], n, 0, S, s);
-    if (e != cudaSuccess) return e;
-    GemmParams P;
-    P.N = N;
-    P.final_step = (k == nsteps - 1) ? 1 : 0;
-    P.planes = cur0 ? V1 : V0;
-    P.u = d_U;
-    P.err = d_err;
-    const int grid = (N / BN) * (N / BM);
-    chain_gemm_kernel<<<grid, kGemmThreads, kGemmSmem, s>>>(cur0 ? mV0 : mV1, mS, P);
-    count_launches(1);
-    e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
-    cur0 = !cur0;
-  }
-  return cudaSuccess;
+  if (prec == TQS_PREC_TC_BF16X3)
+    return chain_tc_impl<TQS_PREC_TC_BF16X3>(d_factors, steps, nsteps, n, d_U, scratch, d_err, s);
+  if (prec == TQS_PREC_TC_TF32X3)
+    return chain_tc_impl<TQS_PREC_TC_TF32X3>(d_factors, steps, nsteps, n, d_U, scratch, d_err, s);
+  return cudaErrorInvalidValue;
 }
 
 }  // namespace tqs

@@ -1247,11 +1247,9 @@ tqs_status tqs_circuit_unitary(tqs_circuit* c, int prec, tqs_c64* d_U, void* str
   if (!aligned16(d_U)) return fail(TQS_ERR_ARG, "tqs_circuit_unitary: d_U must be 16-byte aligned");
   if (c->n > TQS_MAX_DENSE_QUBITS)
     return fail(TQS_ERR_TOO_MANY_QUBITS, "tqs_circuit_unitary: n %d > %d", c->n, TQS_MAX_DENSE_QUBITS);
-  if (prec == TQS_PREC_TC_TF32X3)
-    return fail(TQS_ERR_UNSUPPORTED, "tqs_circuit_unitary: TF32x3 is not built");
-  if (prec != TQS_PREC_FP32_SIMT && prec != TQS_PREC_TC_BF16X3)
+  if (prec != TQS_PREC_FP32_SIMT && prec != TQS_PREC_TC_BF16X3 && prec != TQS_PREC_TC_TF32X3)
     return fail(TQS_ERR_ARG, "tqs_circuit_unitary: unknown precision %d", prec);
-  if (prec == TQS_PREC_TC_BF16X3 && c->n < 7)
+  if (prec != TQS_PREC_FP32_SIMT && c->n < 7)
     return fail(TQS_ERR_ARG, "tqs_circuit_unitary: the tensor-core chain needs n >= 7");
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   tqs_status st = upload_factors(c, s);
@@ -1271,10 +1269,10 @@ tqs_status tqs_circuit_unitary(tqs_circuit* c, int prec, tqs_c64* d_U, void* str
              "tqs_circuit_unitary: SIMT chain");
     return TQS_OK;
   }
-  TQS_CUDA(c->d_chain.ensure(chain_tc_scratch_bytes(c->n)), "tqs_circuit_unitary: cudaMalloc");
+  TQS_CUDA(c->d_chain.ensure(chain_tc_scratch_bytes(c->n, prec)), "tqs_circuit_unitary: cudaMalloc");
   TQS_CUDA(c->d_err.ensure(sizeof(int)), "tqs_circuit_unitary: cudaMalloc");
   TQS_CUDA(cudaMemsetAsync(c->d_err.p, 0, sizeof(int), s), "tqs_circuit_unitary: memset");
-  TQS_CUDA(chain_tc(c->d_factors.as<StepFactor>(), c->steps.data(), c->nsteps, c->n, U,
+  TQS_CUDA(chain_tc(c->d_factors.as<StepFactor>(), c->steps.data(), c->nsteps, c->n, prec, U,
                     c->d_chain.p, c->d_err.as<int>(), s),
            "tqs_circuit_unitary: tensor-core chain");
   int err = 0;

@@ -147,9 +147,9 @@ cudaError_t launch_matvec(const float2* d_S, const float2* d_x, float2* d_y, int
 // ---------------------------------------------------------------------------
 // Circuit-unitary chain (Algorithm 1).
 // ---------------------------------------------------------------------------
-size_t chain_tc_scratch_bytes(int n);
+size_t chain_tc_scratch_bytes(int n, int prec);
 cudaError_t chain_tc(const StepFactor* d_factors, const StepDesc* steps, int nsteps, int n,
-                     float2* d_U, void* scratch, int* d_err, cudaStream_t s);
+                     int prec, float2* d_U, void* scratch, int* d_err, cudaStream_t s);
 size_t chain_simt_scratch_bytes(int n);
 cudaError_t chain_simt(const StepFactor* d_factors, const StepDesc* steps, int nsteps, int n,
                        float2* d_U, void* scratch, cudaStream_t s);
