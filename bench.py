@@ -35,9 +35,12 @@ BATCH = 16384
 METRIC = "circuits/s"
 WORKLOAD = "paper-shaped 11-qubit circuits (GHZ / DJ-constant / DJ-balanced / QFT, 25% each)"
 
-# DRAM bytes per launch of the fused warp-team kernel on this workload, from the
-# ncu capture summarised in profiles/ (None until measured for the current kernel).
-NCU_TRAFFIC_BYTES = None
+# DRAM bytes (read + write) per launch of the fused warp-team kernel on this
+# workload, from the ncu capture summarised in profiles/: 19.48 MB read +
+# 207.64 MB written for 8192 circuits of the same mix, scaled by 2 to the
+# 16384 circuits of one step (traffic grows with the circuit count).  Set back
+# to None whenever the kernel changes, until it is captured again.
+NCU_TRAFFIC_BYTES = int(2 * (19_483_648 + 207_640_576))
 
 
 def parse_args():

@@ -1,6 +1,6 @@
 """Small driver for ncu captures of the fused step kernels.
 
-    python -m paper_2305_14398_gb300.prof COUNT {mix|batch} REPS
+    python -m paper_2305_14398_gb300.prof COUNT KIND REPS [noprobs]
 
 chain: the 40-step random layered circuit-unitary chain at n = COUNT
        (tensor-core BF16x3);
@@ -9,6 +9,7 @@ mix:   COUNT paper-shaped 11-qubit circuits (GHZ / DJ-constant / DJ-balanced /
        of those kinds; batch: the first COUNT circuits of the random batched
        workload (n = 4..14, depth 5..40).  Runs tqs_batch_run REPS times
        without a graph, then once more timed with CUDA events.
+noprobs: the same without the FP64 probability output (d_probs = NULL).
 """
 import sys
 
@@ -38,6 +39,7 @@ def main(argv):
     count = int(argv[1]) if len(argv) > 1 else 2048
     kind = argv[2] if len(argv) > 2 else "mix"
     reps = int(argv[3]) if len(argv) > 3 else 4
+    with_probs = not (len(argv) > 4 and argv[4] == "noprobs")
     if kind == "chain":
         return chain(count, reps)
     if kind == "mix":
@@ -49,7 +51,7 @@ def main(argv):
     b = B.tqs_batch_create_packed(*B.pack_ops(circs))
     c, total, _ = B.tqs_batch_info(b)
     st = torch.empty(total, dtype=torch.complex64, device="cuda")
-    pr = torch.empty(total, dtype=torch.float64, device="cuda")
+    pr = torch.empty(total, dtype=torch.float64, device="cuda") if with_probs else None
     nm = torch.empty(c, dtype=torch.float64, device="cuda")
     for _ in range(reps):
         B.tqs_batch_run(b, st, pr, nm, use_graph=False)
