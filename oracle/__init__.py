@@ -18,6 +18,9 @@ It is plain numpy in complex128 and follows the paper step by step:
                     (Appendix A), used to cross-check the method and to compute
                     columns of large circuit unitaries.
 * ``observables`` - probabilities |amplitude|^2, their sum, and marginals.
+* ``collapse``    - simulateAndCollapse (Sec. 5.2): inverse-CDF sampling of an
+                    outcome from the probabilities, and the measure / reset
+                    instructions of the operation interface.
 
 Every function is pinned by the tests under ``tests/test_oracle_*.py``
 against values the paper prints, closed forms and brute force.
