@@ -55,6 +55,8 @@ def parse_args():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-chain", action="store_true")
     ap.add_argument("--no-serving", action="store_true")
+    ap.add_argument("--no-batch", action="store_true")
+    ap.add_argument("--no-sample", action="store_true")
     return ap.parse_args()
 
 
@@ -387,6 +389,15 @@ def run_tqs(args):
                        "path": "tqs_batch_create_packed (host gate arrays) + tqs_batch_run_host "
                                "(pinned host buffers) + tqs_batch_destroy"}
 
+    # ------------------------------------------------ collapse (sampling)
+    if not args.no_sample and rank == 0:
+        line["sample"] = bench_sample(B, torch, b, probs, count, total, flush, hbm_peak)
+
+    # ------------------------------------- random batches (L2- and HBM-sized)
+    if not args.no_batch and rank == 0:
+        sm_mhz = line["clocks"].get("sm_mhz") or 2070.0
+        line["batch"] = bench_batch(B, W, torch, peaks, flush, max(3, min(args.steps, 10)), sm_mhz)
+
     # ------------------------------------------- circuit-unitary chain (a5)
     if not args.no_chain and rank == 0:
         line["chain"] = bench_chain(B, W, torch, peaks)
@@ -421,6 +432,104 @@ def run_tqs(args):
     if dist:
         dist.destroy_process_group()
     return 0
+
+
+def bench_sample(B, torch, b, probs, count, total, flush, hbm_peak, shots=64, reps=5):
+    """simulateAndCollapse's sampling stage over the bench batch: `shots`
+    inverse-CDF draws per circuit from the probabilities the step wrote."""
+    gen = torch.Generator(device="cuda")
+    gen.manual_seed(14398)
+    u = torch.rand(count * shots, dtype=torch.float64, device="cuda", generator=gen)
+    out = torch.empty(count * shots, dtype=torch.int64, device="cuda")
+    stream = torch.cuda.current_stream()
+    B.tqs_batch_sample(b, probs, shots, u, out)
+    torch.cuda.synchronize()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(reps)]
+    for k in range(reps):
+        flush.zero_()
+        ev[k][0].record(stream)
+        B.tqs_batch_sample(b, probs, shots, u, out)
+        ev[k][1].record(stream)
+    torch.cuda.synchronize()
+    sec = sum(s.elapsed_time(e) for s, e in ev) / 1e3 / reps
+    alg = 8.0 * total + 16.0 * count * shots  # probabilities read once; u read, index written
+    return {"workload": f"{shots} shots per circuit from the step's probabilities "
+                        f"({count} circuits)",
+            "ms": 1e3 * sec, "shots_per_s": count * shots / sec,
+            "hbm": {"achieved_gbs": alg / sec / 1e9, "peak": hbm_peak,
+                    "frac": alg / sec / 1e9 / hbm_peak, "algorithmic_bytes": alg},
+            "launches_per_call": 3}
+
+
+# Algorithmic FP32 flops of one gate on an n-qubit state (per-gate update of
+# Appendix A, eq. 12): a dense single-qubit gate is 2 complex MACs (16 flops) per
+# amplitude; a controlled dense gate does that on the control = 1 half; a
+# diagonal (or phased permutation, Y) gate is one complex multiply (8) on half of
+# the amplitudes, a controlled diagonal on a quarter; pure permutations are free.
+_GATE_FLOPS = {"h": 16.0, "rx": 16.0, "ry": 16.0, "u3": 16.0, "cu": 8.0,
+               "y": 4.0, "z": 4.0, "s": 4.0, "t": 4.0, "r": 4.0, "rz": 4.0,
+               "cz": 2.0, "cp": 2.0, "x": 0.0, "cx": 0.0, "cnot": 0.0, "swap": 0.0}
+
+
+def algorithmic_flops(n, ops):
+    return float(1 << n) * sum(_GATE_FLOPS[name] for name, _, _ in ops)
+
+
+def fp32_peak_tflops(sm_mhz):
+    """FP32 FMA peak derived from unit counts and the SM clock: 152 SMs x 128
+    FP32 lanes x 2 flops per FMA."""
+    return 152 * 128 * 2 * sm_mhz * 1e6 / 1e12
+
+
+def bench_batch(B, W, torch, peaks, flush, reps, sm_mhz):
+    """The batched persistent launch on random mixed circuits: 4096 circuits of
+    n = 4..14 (log-uniform, depth U{5..40}; states L2-resident) and 4096
+    circuits all at n = 14 (1.5 GiB of outputs, streamed through HBM).  Each
+    rep is one graph launch with L2 flushed before it (not timed)."""
+    hbm = peaks.get("hbm_gbs", 6800.0)
+    stream = torch.cuda.current_stream()
+    out = {}
+    for key, circs, what in [
+            ("random_4096_n4_14", W.batch_circuits(4096, seed_tag=3),
+             "4096 random mixed circuits, n = floor(exp(U[ln 4, ln 15))), depth U{5..40}"),
+            ("random_4096_n14", W.batch_circuits_fixed_n(4096, 14, seed_tag=5),
+             "4096 random mixed circuits, all n = 14, depth U{5..40}")]:
+        b = B.tqs_batch_create_packed(*B.pack_ops(circs))
+        count, total, _, steps_total, prog_bytes = B.tqs_batch_info(b, extra=True)
+        states = torch.empty(total, dtype=torch.complex64, device="cuda")
+        probs = torch.empty(total, dtype=torch.float64, device="cuda")
+        norms = torch.empty(count, dtype=torch.float64, device="cuda")
+        for _ in range(3):
+            B.tqs_batch_run(b, states, probs, norms, use_graph=True)
+        torch.cuda.synchronize()
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+              for _ in range(reps)]
+        for k in range(reps):
+            flush.zero_()
+            ev[k][0].record(stream)
+            B.tqs_batch_run(b, states, probs, norms, use_graph=True)
+            ev[k][1].record(stream)
+        torch.cuda.synchronize()
+        sec = sum(s.elapsed_time(e) for s, e in ev) / 1e3 / reps
+        alg_bytes = 16.0 * total + 8.0 * count + prog_bytes
+        flops = sum(algorithmic_flops(n, ops) for n, ops in circs)
+        out[key] = {
+            "workload": what, "circuits": count, "steps": steps_total,
+            "ms": 1e3 * sec, "circuits_per_s": count / sec,
+            "hbm": {"achieved_gbs": alg_bytes / sec / 1e9, "peak": hbm,
+                    "frac": alg_bytes / sec / 1e9 / hbm, "algorithmic_bytes": alg_bytes},
+            "alu": {"achieved_tflops": flops / sec / 1e12,
+                    "peak": fp32_peak_tflops(sm_mhz),
+                    "frac": flops / sec / 1e12 / fp32_peak_tflops(sm_mhz),
+                    "algorithmic_flops": flops,
+                    "peak_source": f"derived: 152 SMs x 128 FP32 lanes x 2 x {sm_mhz:.0f} MHz"},
+            "norm_max_err": float((norms.cpu() - 1.0).abs().max()),
+        }
+        B.tqs_batch_destroy(b)
+        del states, probs, norms
+        torch.cuda.empty_cache()
+    return out
 
 
 def bench_chain(B, W, torch, peaks):

@@ -71,12 +71,23 @@ typedef enum {
  * textbook definitions.  Controlled gates (eq. 7, qubits {control, target}):
  * CNOT (eq. 8), CZ, CP (params {phi}) and CU (params: 8 doubles, re/im of
  * u00, u01, u10, u11; must be unitary to 1e-9).  SWAP (qubits {a, b})
- * appears in the QFT circuit of Sec. 2.5. */
+ * appears in the QFT circuit of Sec. 2.5.
+ * Instructions (Sec. 5.2, operation interface; one qubit, no params):
+ * TQS_MEASURE measures the qubit (projective, the state renormalised);
+ * TQS_RESET measures it and, on outcome 1, flips it back to |0>.  Each takes
+ * one caller-supplied uniform u in [0, 1): with S_0 the probability mass of the
+ * indices whose bit is 0 and T the total, the outcome is 0 iff u * T < S_0 (FP64,
+ * summed in a fixed order).  An instruction is a barrier: it forms a step of its
+ * own, after every earlier operation and before every later one.  Circuits with
+ * instructions run through tqs_simulate_measured / tqs_batch_run_measured; the
+ * unitary forms (tqs_simulate, tqs_simulate_plain, tqs_circuit_unitary, the
+ * server) return TQS_ERR_UNSUPPORTED for them. */
 typedef enum {
   TQS_H = 0, TQS_X = 1, TQS_Y = 2, TQS_Z = 3, TQS_S = 4, TQS_T = 5, TQS_R = 6,
   TQS_RX = 7, TQS_RY = 8, TQS_RZ = 9, TQS_U3 = 10,
   TQS_CNOT = 11, TQS_CZ = 12, TQS_CP = 13, TQS_CU = 14, TQS_SWAP = 15,
-  TQS_GATE_COUNT = 16
+  TQS_MEASURE = 16, TQS_RESET = 17,
+  TQS_GATE_COUNT = 18
 } tqs_gate;
 
 /* Arithmetic of the circuit-unitary chain (Algorithm 1). */
@@ -223,6 +234,45 @@ tqs_status tqs_probabilities_noalloc(const tqs_c64* d_state, int n, double* d_pr
 tqs_status tqs_marginal_zero(const tqs_c64* d_state, int n, uint64_t mask,
                              double* d_out, void* stream);
 
+/* Simulate a circuit that may hold TQS_MEASURE / TQS_RESET instructions
+ * (fused form; arguments as tqs_simulate, plus):
+ *   d_u        : one uniform in [0, 1) per instruction, in the order the
+ *                instructions were added (may be NULL if there are none);
+ *   d_outcomes : one int32 outcome (0 or 1) per instruction, same order
+ *                (may be NULL).
+ * With no instruction this is tqs_simulate. */
+tqs_status tqs_simulate_measured(tqs_circuit* c, const tqs_c64* d_init, tqs_c64* d_out,
+                                 double* d_probs, double* d_norm, const double* d_u,
+                                 int32_t* d_outcomes, void* stream);
+
+/* ---------------------------------------------------------------- collapse
+ * simulateAndCollapse (Sec. 5.2): the state collapses to one basis state
+ * drawn with the probabilities p_i = |psi_i|^2 (Sec. 2.1, eq. 2).  Random
+ * numbers are inputs: each shot takes one uniform u in [0, 1) from the caller.
+ * A shot picks, by inverse CDF, the first index i with p_i > 0 and
+ * u * T < C_i, where C_i = p_0 + ... + p_i and T = C_{2^n - 1}, summed in FP64
+ * in the library's fixed order (blocks of 256 entries, chunks of 8 entries
+ * added in index order, an exclusive warp scan over the 32 chunks of a block,
+ * then an exclusive prefix over the blocks); if rounding leaves no such index,
+ * the last index before that point with p_i > 0; -1 when every p_i is 0.
+ * Results are deterministic; an index whose p_i is 0 is never
+ * returned.  The probabilities need not sum to 1. */
+
+/* `shots` samples from one probability vector:
+ *   d_probs : 2^n doubles (for example from tqs_probabilities);
+ *   d_u     : `shots` doubles in [0, 1);  d_out : `shots` int64 indices.
+ * 1 <= n <= 30, shots >= 0.  Scratch (per host thread, cached): 34 doubles
+ * per 256 probabilities plus a few hundred bytes. */
+tqs_status tqs_sample(const double* d_probs, int n, int64_t shots, const double* d_u,
+                      int64_t* d_out, void* stream);
+
+/* simulateAndCollapse for one circuit: simulate it from |0...0> (fused form),
+ * draw one outcome with d_u[0], write its index to d_index[0] (int64) and,
+ * if d_state is not NULL, the collapsed state |index> (2^n tqs_c64) there.
+ * Scratch (cached on the circuit): the state and its probabilities. */
+tqs_status tqs_simulate_and_collapse(tqs_circuit* c, const double* d_u, int64_t* d_index,
+                                     tqs_c64* d_state, void* stream);
+
 /* ------------------------------------------------------------------- batch
  * Many circuits of uneven size and depth simulated by one graph launch of
  * the persistent fused step kernels.  The batch copies what it needs from
@@ -259,6 +309,28 @@ tqs_status tqs_batch_info(const tqs_batch* b, int* count, int64_t* total_amps,
  * replay. */
 tqs_status tqs_batch_run(tqs_batch* b, tqs_c64* d_states, double* d_probs, double* d_norms,
                          int use_graph, void* stream);
+
+/* `shots` samples per circuit of a batch from its probabilities (the
+ * d_probs a tqs_batch_run wrote, same layout):  d_u : count * shots uniforms,
+ * circuit i's shot k at i * shots + k;  d_out : count * shots int64 indices
+ * within circuit i's state, same layout.  Same rule as tqs_sample.  Scratch
+ * (cached on the batch): 34 doubles per 256 amplitudes of the circuits with
+ * n > 13 plus 32 bytes per circuit. */
+tqs_status tqs_batch_sample(tqs_batch* b, const double* d_probs, int shots, const double* d_u,
+                            int64_t* d_out, void* stream);
+
+/* Instruction offsets of a batch: h_off (count+1 int64); circuit i's
+ * instructions take uniforms / write outcomes [h_off[i], h_off[i+1]) in
+ * their order in the circuit.  h_off[count] = all instructions. */
+tqs_status tqs_batch_instructions(const tqs_batch* b, int64_t* h_off);
+
+/* tqs_batch_run for batches that hold instructions: d_u (h_off[count]
+ * doubles) and d_outcomes (h_off[count] int32, may be NULL) in the layout of
+ * tqs_batch_instructions.  tqs_batch_run and tqs_batch_run_host return
+ * TQS_ERR_UNSUPPORTED for such batches. */
+tqs_status tqs_batch_run_measured(tqs_batch* b, tqs_c64* d_states, double* d_probs,
+                                  double* d_norms, const double* d_u, int32_t* d_outcomes,
+                                  int use_graph, void* stream);
 
 /* Host-buffer form of tqs_batch_run: uploads the program, runs, and copies
  * the results into h_states / h_probs / h_norms (host memory, NULL to skip),

@@ -19,7 +19,8 @@ LIB_PATH = os.environ.get("TQS_LIB") or os.path.join(HERE, "libtqs.so")
 HEADER = os.path.join(os.path.dirname(HERE), "include", "tqs.h")
 
 GATE_IDS = {"h": 0, "x": 1, "y": 2, "z": 3, "s": 4, "t": 5, "r": 6, "rx": 7, "ry": 8, "rz": 9,
-            "u3": 10, "cx": 11, "cnot": 11, "cz": 12, "cp": 13, "cu": 14, "swap": 15}
+            "u3": 10, "cx": 11, "cnot": 11, "cz": 12, "cp": 13, "cu": 14, "swap": 15,
+            "measure": 16, "reset": 17}
 TWO_QUBIT_IDS = {11, 12, 13, 14, 15}
 
 PREC_FP32_SIMT = 0
@@ -58,17 +59,23 @@ _SIGS = {
                                  _pi]),
     "tqs_simulate": (_i, [_vp, _vp, _vp, _vp, _vp, _vp]),
     "tqs_simulate_plain": (_i, [_vp, _vp, _vp, _vp]),
+    "tqs_simulate_measured": (_i, [_vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp]),
     "tqs_materialize_step": (_i, [_vp, _i, _vp, _vp]),
     "tqs_circuit_unitary": (_i, [_vp, _i, _vp, _vp]),
     "tqs_probabilities": (_i, [_vp, _i, _vp, _vp, _vp]),
     "tqs_marginal_zero": (_i, [_vp, _i, _u64, _vp, _vp]),
     "tqs_probabilities_noalloc": (_i, [_vp, _i, _vp, _vp, _vp]),
+    "tqs_sample": (_i, [_vp, _i, _i64, _vp, _vp, _vp]),
+    "tqs_simulate_and_collapse": (_i, [_vp, _vp, _vp, _vp, _vp]),
+    "tqs_batch_sample": (_i, [_vp, _vp, _i, _vp, _vp, _vp]),
     "tqs_batch_create": (_i, [ctypes.POINTER(_vp), _i, ctypes.POINTER(_vp)]),
     "tqs_batch_create_packed": (_i, [_i, _vp, _vp, _vp, _vp, _vp, ctypes.POINTER(_vp)]),
     "tqs_batch_info": (_i, [_vp, _pi, ctypes.POINTER(_i64), ctypes.POINTER(_i64),
                             ctypes.POINTER(_i64), _vp]),
     "tqs_batch_run": (_i, [_vp, _vp, _vp, _vp, _i, _vp]),
     "tqs_batch_run_host": (_i, [_vp, _vp, _vp, _vp, _vp]),
+    "tqs_batch_instructions": (_i, [_vp, _vp]),
+    "tqs_batch_run_measured": (_i, [_vp, _vp, _vp, _vp, _vp, _vp, _i, _vp]),
     "tqs_batch_destroy": (_i, [_vp]),
     "tqs_server_create": (_i, [ctypes.c_size_t, _i, _i, ctypes.POINTER(_vp)]),
     "tqs_server_submit_packed": (_i, [_vp, _i64, _i, _i, _vp, _vp, _vp]),
@@ -203,6 +210,14 @@ def tqs_simulate(c: int, out, init=None, probs=None, norm=None, stream=None) -> 
     _check(lib().tqs_simulate(c, _ptr(init), _ptr(out), _ptr(probs), _ptr(norm), _stream(stream)))
 
 
+def tqs_simulate_measured(c: int, out, u=None, outcomes=None, init=None, probs=None, norm=None,
+                          stream=None) -> None:
+    """Circuits with measure / reset instructions: u (float64, one per
+    instruction), outcomes (int32, one per instruction)."""
+    _check(lib().tqs_simulate_measured(c, _ptr(init), _ptr(out), _ptr(probs), _ptr(norm), _ptr(u),
+                                       _ptr(outcomes), _stream(stream)))
+
+
 def tqs_simulate_plain(c: int, out, init=None, stream=None) -> None:
     _check(lib().tqs_simulate_plain(c, _ptr(init), _ptr(out), _stream(stream)))
 
@@ -226,6 +241,25 @@ def tqs_probabilities_noalloc(state, n: int, probs=None, total=None, stream=None
 
 def tqs_marginal_zero(state, n: int, mask: int, out, stream=None) -> None:
     _check(lib().tqs_marginal_zero(_ptr(state), int(n), int(mask), _ptr(out), _stream(stream)))
+
+
+# ---------------------------------------------------------------- collapse
+
+def tqs_sample(probs, n: int, shots: int, u, out, stream=None) -> None:
+    """Inverse-CDF samples: out[k] (int64) from uniform u[k] (float64)."""
+    _check(lib().tqs_sample(_ptr(probs), int(n), int(shots), _ptr(u), _ptr(out), _stream(stream)))
+
+
+def tqs_simulate_and_collapse(c: int, u, index, state=None, stream=None) -> None:
+    """simulateAndCollapse: index[0] (int64) drawn with u[0]; state <- |index>."""
+    _check(lib().tqs_simulate_and_collapse(c, _ptr(u), _ptr(index), _ptr(state),
+                                           _stream(stream)))
+
+
+def tqs_batch_sample(b: int, probs, shots: int, u, out, stream=None) -> None:
+    """`shots` samples per circuit of a batch (layout circuit-major)."""
+    _check(lib().tqs_batch_sample(b, _ptr(probs), int(shots), _ptr(u), _ptr(out),
+                                  _stream(stream)))
 
 
 # ------------------------------------------------------------------- batch
@@ -286,6 +320,21 @@ def tqs_batch_info(b: int, extra: bool = False):
 def tqs_batch_run(b: int, states, probs=None, norms=None, use_graph: bool = True, stream=None) -> None:
     _check(lib().tqs_batch_run(b, _ptr(states), _ptr(probs), _ptr(norms), int(bool(use_graph)),
                                _stream(stream)))
+
+
+def tqs_batch_instructions(b: int) -> np.ndarray:
+    """Instruction offsets (count + 1 int64) of a batch."""
+    count = ctypes.c_int()
+    _check(lib().tqs_batch_info(b, ctypes.byref(count), None, None, None, None))
+    off = np.empty(count.value + 1, dtype=np.int64)
+    _check(lib().tqs_batch_instructions(b, off.ctypes.data))
+    return off
+
+
+def tqs_batch_run_measured(b: int, states, u, outcomes=None, probs=None, norms=None,
+                           use_graph: bool = True, stream=None) -> None:
+    _check(lib().tqs_batch_run_measured(b, _ptr(states), _ptr(probs), _ptr(norms), _ptr(u),
+                                        _ptr(outcomes), int(bool(use_graph)), _stream(stream)))
 
 
 def tqs_batch_run_host(b: int, h_states=None, h_probs=None, h_norms=None, stream=None) -> None:

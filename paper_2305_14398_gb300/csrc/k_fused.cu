@@ -349,6 +349,56 @@ __device__ __forceinline__ void team_sync() {
     __syncthreads();
 }
 
+// Measure / reset instruction (Sec. 5.2 operation interface) on physical bit
+// `bit`: S_0 / S_1 = the |psi|^2 mass with that bit 0 / 1 (FP64 exact squares,
+// summed per thread in index order, then across the team in a fixed order),
+// T = S_0 + S_1; the outcome is 0 iff u T < S_0.  The state is projected on
+// the outcome and scaled by sqrt(T / S_b); a reset with outcome 1 moves the
+// kept half to bit 0.  Any global scale the amplitudes carry cancels in
+// S_b / T.
+template <int TEAM>
+__device__ void instr_pass(const FusedLaunch& L, int nint, int bit, bool reset, uint32_t k,
+                           float2* st, int rank, int size, double* s_red) {
+  const int half = 1 << (nint - 1);
+  const int m = 1 << bit;
+  double s0 = 0.0, s1 = 0.0;
+  for (int j = rank; j < half; j += size) {
+    const int i0 = ins0(j, bit);
+    s0 += prob_f64(st[swz(i0)]);
+    s1 += prob_f64(st[swz(i0 | m)]);
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    s0 += __shfl_xor_sync(0xffffffffu, s0, o);
+    s1 += __shfl_xor_sync(0xffffffffu, s1, o);
+  }
+  if (TEAM != TEAM_WARP) {
+    const int warp = rank >> 5, lane = rank & 31, nw = size >> 5;
+    __syncthreads();
+    if (lane == 0) { s_red[warp] = s0; s_red[16 + warp] = s1; }
+    __syncthreads();
+    s0 = 0.0;
+    s1 = 0.0;
+    for (int w = 0; w < nw; ++w) { s0 += s_red[w]; s1 += s_red[16 + w]; }
+    __syncthreads();
+  }
+  const double T = s0 + s1;
+  int outcome = (L.uniforms[k] * T < s0) ? 0 : 1;
+  if ((outcome ? s1 : s0) == 0.0) outcome ^= 1;  // u outside [0, 1): never pick an empty half
+  const double sb = outcome ? s1 : s0;
+  const float sc = sb > 0.0 ? static_cast<float>(sqrt(T / sb)) : 1.0f;
+  if (rank == 0 && L.outcomes) L.outcomes[k] = outcome;
+  const float2 zero = make_float2(0.f, 0.f);
+  for (int j = rank; j < half; j += size) {
+    const int a0 = swz(ins0(j, bit)), a1 = swz(ins0(j, bit) | m);
+    const float2 v = outcome ? st[a1] : st[a0];
+    const float2 w = make_float2(v.x * sc, v.y * sc);
+    st[a0] = (outcome == 0 || reset) ? w : zero;
+    st[a1] = (outcome == 1 && !reset) ? w : zero;
+  }
+  team_sync<TEAM>();
+}
+
 template <int TEAM>
 __device__ void run_circuit(const FusedLaunch& L, int ci, float2* st, int rank, int size,
                             double* s_red) {
@@ -366,6 +416,10 @@ __device__ void run_circuit(const FusedLaunch& L, int ci, float2* st, int rank, 
   for (int p = 0; p < cd.pass_count; ++p) {
     const uint4 pr = __ldg(reinterpret_cast<const uint4*>(L.passes + cd.pass_begin + p));
     const int l0 = pr.x & 0xff, l1 = (pr.x >> 8) & 0xff, l2 = (pr.x >> 16) & 0xff, l3 = pr.x >> 24;
+    if (l0 == kInstrPass) {
+      instr_pass<TEAM>(L, nint, l1, (l2 & 1) != 0, pr.y, st, rank, size, s_red);
+      continue;
+    }
     const FusedOp* ops = L.ops + pr.y;
     const uint32_t count = pr.z;
     const float scale = __uint_as_float(pr.w);

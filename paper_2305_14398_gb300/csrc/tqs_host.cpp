@@ -93,6 +93,7 @@ struct Mat2 {
 };
 
 static bool is_controlled(int g) { return g == TQS_CNOT || g == TQS_CZ || g == TQS_CP || g == TQS_CU; }
+static bool is_instruction(int g) { return g == TQS_MEASURE || g == TQS_RESET; }
 static bool is_two_qubit(int g) { return is_controlled(g) || g == TQS_SWAP; }
 static int n_params(int g) {
   switch (g) {
@@ -195,6 +196,7 @@ struct Program {
   int identity = 1;
   float out_scale = 1.0f;
   int gen_index = 0;  // basis state the program starts from (leading X gates folded)
+  int n_instr = 0;    // measure / reset instructions (one pass each)
   double cost = 0.0;
 };
 
@@ -349,6 +351,18 @@ static void compile_program(int n, const std::vector<const Gate*>& gs_in, Progra
     raw.clear();
     h_in_pass = 0;
   };
+  // An instruction is a barrier: the gates before it are scheduled (pending),
+  // then it becomes a pass of its own, then scheduling resumes after it.
+  std::vector<int> order(gs.size());
+  std::iota(order.begin(), order.end(), 0);
+  pending.clear();
+  size_t next = 0;
+  auto take_segment = [&]() {
+    pending.clear();
+    while (next < order.size() && !is_instruction(gs[order[next]]->kind)) pending.push_back(order[next++]);
+  };
+  take_segment();
+  for (;;) {
   while (!pending.empty()) {
     uint32_t Lmask = 0, blocked = 0;
     int nL = 0;
@@ -380,6 +394,22 @@ static void compile_program(int n, const std::vector<const Gate*>& gs_in, Progra
     for (; idx < pending.size(); ++idx) still.push_back(pending[idx]);
     emit_pass(Lmask, nL, still.empty());
     pending.swap(still);
+  }
+  if (next >= order.size()) break;
+  {
+    const Gate& g = *gs[order[next++]];
+    if (P.passes.empty()) emit_pass(0u, 0, false);  // the first pass generates the start state
+    FusedPass ps{};
+    ps.L[0] = kInstrPass;
+    ps.L[1] = static_cast<uint8_t>(phys[g.q[0]]);
+    ps.L[2] = g.kind == TQS_RESET ? 1 : 0;
+    ps.op_begin = static_cast<uint32_t>(P.n_instr++);
+    ps.op_count = 0;
+    ps.scale = 1.0f;
+    P.passes.push_back(ps);
+    P.cost += 2.0 * static_cast<double>(1u << nint);
+  }
+  take_segment();
   }
   if (P.passes.empty()) emit_pass(0u, 0, true);
   P.out_scale = h_carry ? static_cast<float>(1.0 / std::sqrt(2.0)) : 1.0f;
@@ -416,6 +446,7 @@ using namespace tqs;
 
 struct tqs_circuit {
   int n = 0;
+  int n_instr = 0;  // measure / reset instructions
   std::vector<Gate> gates;
   std::vector<int> last;  // last step touching each qubit
   int nsteps = 0;
@@ -434,6 +465,8 @@ struct tqs_circuit {
   DevBuf d_factors;
   DevBuf d_plain;     // S scratch + two state vectors
   DevBuf d_partials;  // probability partials
+  DevBuf d_collapse;  // simulateAndCollapse: state + probabilities
+  DevBuf d_sample;    // sampling scratch
   // chain scratch
   DevBuf d_chain;
   DevBuf d_err;
@@ -509,17 +542,35 @@ static tqs_status check_gate(int n, int gate, const int* qubits, int nq, const d
   return TQS_OK;
 }
 
+}  // extern "C"
+
+// ASAP step of the next operation (Sec. 5.2): after the last step touching any
+// of its qubits (`last`: per qubit, -1 if none).  An instruction is a barrier:
+// a step of its own after every earlier step, and every later operation comes
+// after it.
+static void assign_step(std::vector<int>& last, Gate& g) {
+  int step = 0;
+  if (is_instruction(g.kind)) {
+    for (int v : last) step = std::max(step, v + 1);
+    for (int& v : last) v = step;
+  } else {
+    for (int i = 0; i < g.nq; ++i) step = std::max(step, last[g.q[i]] + 1);
+    for (int i = 0; i < g.nq; ++i) last[g.q[i]] = step;
+  }
+  g.step = step;
+}
+
+extern "C" {
+
 tqs_status tqs_add_gate(tqs_circuit* c, int gate, const int* qubits, int nq, const double* params,
                         int np) {
   if (!c) return fail(TQS_ERR_ARG, "tqs_add_gate: circuit is NULL");
   Gate g{};
   tqs_status s = check_gate(c->n, gate, qubits, nq, params, np, g);
   if (s != TQS_OK) return s;
-  // ASAP step: after the last step touching any of the gate's qubits.
-  int step = 0;
-  for (int i = 0; i < g.nq; ++i) step = std::max(step, c->last[g.q[i]] + 1);
-  g.step = step;
-  for (int i = 0; i < g.nq; ++i) c->last[g.q[i]] = step;
+  assign_step(c->last, g);
+  if (is_instruction(gate)) ++c->n_instr;
+  const int step = g.step;
   c->nsteps = std::max(c->nsteps, step + 1);
   c->gates.push_back(g);
   c->prog_valid = false;
@@ -598,7 +649,8 @@ struct Image {
   size_t bytes() const { return circ_bytes() + pass_bytes() + op_bytes(); }
   // Write program P as circuit i whose passes start at pass0 and ops at op0
   // (the arrays are sized by the caller).
-  void fill(int i, const Program& P, int64_t out_off, int64_t pass0, int64_t op0) {
+  void fill(int i, const Program& P, int64_t out_off, int64_t pass0, int64_t op0,
+            int64_t instr0 = 0) {
     FusedCirc fc{};
     fc.n = P.n;
     fc.nint = P.nint;
@@ -614,7 +666,7 @@ struct Image {
     circs[i] = fc;
     for (size_t k = 0; k < P.passes.size(); ++k) {
       FusedPass ps = P.passes[k];
-      ps.op_begin += static_cast<uint32_t>(op0);
+      ps.op_begin += static_cast<uint32_t>(ps.L[0] == kInstrPass ? instr0 : op0);
       passes[static_cast<size_t>(pass0) + k] = ps;
     }
     if (!P.ops.empty())
@@ -635,7 +687,7 @@ struct Image {
     fc.gen_index = P.gen_index;
     const uint32_t op_base = static_cast<uint32_t>(ops.size());
     for (FusedPass ps : P.passes) {
-      ps.op_begin += op_base;
+      if (ps.L[0] != kInstrPass) ps.op_begin += op_base;
       passes.push_back(ps);
     }
     ops.insert(ops.end(), P.ops.begin(), P.ops.end());
@@ -688,11 +740,13 @@ static LaunchPlan plan_for(int team, int max_nint, int jobs, int warps_hint) {
   return lp;
 }
 
-extern "C" {
-
-tqs_status tqs_simulate(tqs_circuit* c, const tqs_c64* d_init, tqs_c64* d_out, double* d_probs,
-                        double* d_norm, void* stream) {
+static tqs_status simulate_impl(tqs_circuit* c, const tqs_c64* d_init, tqs_c64* d_out,
+                                double* d_probs, double* d_norm, const double* d_u,
+                                int32_t* d_outcomes, void* stream) {
   if (!c || !d_out) return fail(TQS_ERR_ARG, "tqs_simulate: NULL circuit or output");
+  if (c->n_instr > 0 && !d_u)
+    return fail(TQS_ERR_ARG, "tqs_simulate_measured: the circuit has %d instruction(s): d_u is NULL",
+                c->n_instr);
   if (!aligned16(d_out) || (d_probs && !aligned16(d_probs)) || (d_init && !aligned16(d_init)))
     return fail(TQS_ERR_ARG, "tqs_simulate: device buffers must be 16-byte aligned");
   if (d_init && reinterpret_cast<const void*>(d_init) == reinterpret_cast<const void*>(d_out))
@@ -723,6 +777,8 @@ tqs_status tqs_simulate(tqs_circuit* c, const tqs_c64* d_init, tqs_c64* d_out, d
   L.out = reinterpret_cast<float2*>(d_out);
   L.probs = d_probs;
   L.norms = d_norm;
+  L.uniforms = d_u;
+  L.outcomes = d_outcomes;
   LaunchPlan lp = plan_for(team, P.nint, 1, 1);
   if (team == TEAM_GLOBAL) {
     TQS_CUDA(c->d_gscratch.ensure((size_t(1) << kGlobalSlotQ) * sizeof(float2)),
@@ -735,6 +791,22 @@ tqs_status tqs_simulate(tqs_circuit* c, const tqs_c64* d_init, tqs_c64* d_out, d
   L.grid = 1;
   TQS_CUDA(launch_fused(L, s), "tqs_simulate: launch");
   return TQS_OK;
+}
+
+extern "C" {
+
+tqs_status tqs_simulate(tqs_circuit* c, const tqs_c64* d_init, tqs_c64* d_out, double* d_probs,
+                        double* d_norm, void* stream) {
+  if (c && c->n_instr > 0)
+    return fail(TQS_ERR_UNSUPPORTED,
+                "tqs_simulate: the circuit holds measure/reset instructions: use tqs_simulate_measured");
+  return simulate_impl(c, d_init, d_out, d_probs, d_norm, nullptr, nullptr, stream);
+}
+
+tqs_status tqs_simulate_measured(tqs_circuit* c, const tqs_c64* d_init, tqs_c64* d_out,
+                                 double* d_probs, double* d_norm, const double* d_u,
+                                 int32_t* d_outcomes, void* stream) {
+  return simulate_impl(c, d_init, d_out, d_probs, d_norm, d_u, d_outcomes, stream);
 }
 
 }  // extern "C"
@@ -802,6 +874,8 @@ static tqs_status upload_factors(tqs_circuit* c, cudaStream_t s) {
 extern "C" {
 
 tqs_status tqs_materialize_step(tqs_circuit* c, int step, tqs_c64* d_S, void* stream) {
+  if (c && c->n_instr > 0)
+    return fail(TQS_ERR_UNSUPPORTED, "tqs_materialize_step: the circuit holds measure/reset instructions");
   if (!c || !d_S) return fail(TQS_ERR_ARG, "tqs_materialize_step: NULL argument");
   if (c->n > TQS_MAX_DENSE_QUBITS)
     return fail(TQS_ERR_TOO_MANY_QUBITS, "tqs_materialize_step: n %d > %d", c->n,
@@ -819,6 +893,8 @@ tqs_status tqs_materialize_step(tqs_circuit* c, int step, tqs_c64* d_S, void* st
 }
 
 tqs_status tqs_simulate_plain(tqs_circuit* c, const tqs_c64* d_init, tqs_c64* d_out, void* stream) {
+  if (c && c->n_instr > 0)
+    return fail(TQS_ERR_UNSUPPORTED, "tqs_simulate_plain: the circuit holds measure/reset instructions");
   if (!c || !d_out) return fail(TQS_ERR_ARG, "tqs_simulate_plain: NULL argument");
   if (c->n > TQS_MAX_DENSE_QUBITS)
     return fail(TQS_ERR_TOO_MANY_QUBITS, "tqs_simulate_plain: n %d > %d", c->n,
@@ -893,10 +969,69 @@ tqs_status tqs_marginal_zero(const tqs_c64* d_state, int n, uint64_t mask, doubl
 
 // ------------------------------------------------------------------ batch
 
+// Segment tables of an inverse-CDF sampling call (see k_sample.cu).
+struct SamplePlan {
+  std::vector<SampleSeg> gsegs, ssegs;
+  int64_t nblocks = 0;
+  int smem_q = 0;
+  size_t off_g = 0, off_s = 0, off_bsum = 0, off_bpre = 0, off_cpre = 0, off_tot = 0, bytes = 0;
+  void layout() {
+    auto up = [](size_t x) { return (x + 255) & ~size_t(255); };
+    off_g = 0;
+    off_s = up(gsegs.size() * sizeof(SampleSeg));
+    off_bsum = off_s + up(ssegs.size() * sizeof(SampleSeg));
+    off_bpre = off_bsum + up(size_t(nblocks) * sizeof(double));
+    off_cpre = off_bpre + up(size_t(nblocks) * sizeof(double));
+    off_tot = off_cpre + up(size_t(nblocks) * (kSampleBlk / kSampleChunk) * sizeof(double));
+    bytes = off_tot + up(gsegs.size() * sizeof(double));
+  }
+  // Segment `index` of 2^n probabilities at p_off; small ones go to the
+  // shared-memory path when allowed.
+  void add(int64_t index, int64_t p_off, int n, bool allow_smem) {
+    if (allow_smem && n <= kSampleSmemMaxQ) {
+      ssegs.push_back(SampleSeg{p_off, n, 0, index});
+      smem_q = std::max(smem_q, n);
+    } else {
+      gsegs.push_back(SampleSeg{p_off, n, static_cast<int32_t>(nblocks), index});
+      nblocks += sample_blocks(n);
+    }
+  }
+  cudaError_t upload(char* base, cudaStream_t s) const {
+    cudaError_t e = cudaSuccess;
+    if (!gsegs.empty())
+      e = cudaMemcpyAsync(base + off_g, gsegs.data(), gsegs.size() * sizeof(SampleSeg),
+                          cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess && !ssegs.empty())
+      e = cudaMemcpyAsync(base + off_s, ssegs.data(), ssegs.size() * sizeof(SampleSeg),
+                          cudaMemcpyHostToDevice, s);
+    return e;
+  }
+  SampleLaunch launch(char* base, const double* probs, const double* u, int64_t shots,
+                      int64_t* out) const {
+    SampleLaunch L{};
+    L.probs = probs;
+    L.gsegs = reinterpret_cast<const SampleSeg*>(base + off_g);
+    L.n_gseg = static_cast<int32_t>(gsegs.size());
+    L.nblocks = nblocks;
+    L.bsum = reinterpret_cast<double*>(base + off_bsum);
+    L.bpre = reinterpret_cast<double*>(base + off_bpre);
+    L.cpre = reinterpret_cast<double*>(base + off_cpre);
+    L.tot = reinterpret_cast<double*>(base + off_tot);
+    L.ssegs = reinterpret_cast<const SampleSeg*>(base + off_s);
+    L.n_sseg = static_cast<int32_t>(ssegs.size());
+    L.smem_q = smem_q;
+    L.u = u;
+    L.shots = shots;
+    L.out = out;
+    return L;
+  }
+};
+
 struct tqs_batch {
   int count = 0;
   int64_t total_steps = 0;
   std::vector<int64_t> offsets;  // count + 1
+  std::vector<int64_t> instr_off;  // count + 1: instruction (uniform / outcome) offsets
   Image img;
   std::vector<int32_t> order;    // [warp jobs][cta jobs][global jobs]
   int n_team[3] = {0, 0, 0};
@@ -905,6 +1040,8 @@ struct tqs_batch {
   size_t order_off = 0, counter_off = 0;
   bool uploaded = false;
   DevBuf d_gscratch;
+  DevBuf d_sample;               // sampling: segment tables + block sums / prefixes
+  std::unique_ptr<SamplePlan> sample_plan;
   LaunchPlan plans[3];
   // graph cache
   cudaStream_t cap_stream = nullptr;
@@ -913,6 +1050,8 @@ struct tqs_batch {
   void* g_states = nullptr;
   void* g_probs = nullptr;
   void* g_norms = nullptr;
+  const void* g_u = nullptr;
+  void* g_outcomes = nullptr;
   int graph_kernels = 0;
   ~tqs_batch() {
     if (exec) cudaGraphExecDestroy(exec);
@@ -946,8 +1085,10 @@ static tqs_status batch_finish(tqs_batch* b, std::vector<Program>& progs) {
   b->count = static_cast<int>(progs.size());
   b->offsets.assign(b->count + 1, 0);
   std::vector<int64_t> pass0(b->count + 1, 0), op0(b->count + 1, 0);
+  b->instr_off.assign(b->count + 1, 0);
   for (int i = 0; i < b->count; ++i) {
     b->offsets[i + 1] = b->offsets[i] + (int64_t(1) << progs[i].n);
+    b->instr_off[i + 1] = b->instr_off[i] + progs[i].n_instr;
     pass0[i + 1] = pass0[i] + static_cast<int64_t>(progs[i].passes.size());
     op0[i + 1] = op0[i] + static_cast<int64_t>(progs[i].ops.size());
   }
@@ -955,7 +1096,10 @@ static tqs_status batch_finish(tqs_batch* b, std::vector<Program>& progs) {
   b->img.circs.resize(b->count);
   b->img.passes.resize(static_cast<size_t>(pass0.back()));
   b->img.ops.resize(static_cast<size_t>(op0.back()));
-  parallel_for(b->count, 256, [&](int i) { b->img.fill(i, progs[i], b->offsets[i], pass0[i], op0[i]); });
+  if (b->instr_off.back() > 0xFFFFFFFFll) return fail(TQS_ERR_ARG, "tqs_batch: too many instructions");
+  parallel_for(b->count, 256, [&](int i) {
+    b->img.fill(i, progs[i], b->offsets[i], pass0[i], op0[i], b->instr_off[i]);
+  });
   std::vector<int> idx[3];
   for (int i = 0; i < b->count; ++i) {
     const int t = team_for(progs[i].nint);
@@ -1043,10 +1187,7 @@ tqs_status tqs_batch_create_packed(int count, const int32_t* h_nq, const int64_t
         Gate& g = gates[static_cast<size_t>(k - g0)];
         st = check_gate(n, kind, h_qubits + 2 * k, nq, h_params + 8 * k, 8, g);
         if (st != TQS_OK) break;
-        int step = 0;
-        for (int j = 0; j < g.nq; ++j) step = std::max(step, last[g.q[j]] + 1);
-        g.step = step;
-        for (int j = 0; j < g.nq; ++j) last[g.q[j]] = step;
+        assign_step(last, g);
       }
       if (st != TQS_OK) {
         record(st);
@@ -1101,7 +1242,8 @@ static tqs_status batch_upload(tqs_batch* b, cudaStream_t s) {
 // team kind present) for a program image at `base`.
 static tqs_status batch_enqueue_at(tqs_batch* b, char* base, size_t order_off, size_t counter_off,
                                    float2* gscratch, float2* states, double* probs, double* norms,
-                                   cudaStream_t s, int* kernels = nullptr) {
+                                   cudaStream_t s, int* kernels = nullptr,
+                                   const double* u = nullptr, int32_t* outcomes = nullptr) {
   int32_t* counters = reinterpret_cast<int32_t*>(base + counter_off);
   TQS_CUDA(cudaMemsetAsync(counters, 0, 3 * sizeof(int32_t), s), "tqs_batch: memset counters");
   int k = 0;
@@ -1119,6 +1261,8 @@ static tqs_status batch_enqueue_at(tqs_batch* b, char* base, size_t order_off, s
     L.probs = probs;
     L.norms = norms;
     L.gscratch = gscratch;
+    L.uniforms = u;
+    L.outcomes = outcomes;
     L.team = t;
     L.warps_per_cta = b->plans[t].warps;
     L.slice_q = b->plans[t].slice_q;
@@ -1132,9 +1276,10 @@ static tqs_status batch_enqueue_at(tqs_batch* b, char* base, size_t order_off, s
 }
 
 static tqs_status batch_enqueue(tqs_batch* b, float2* states, double* probs, double* norms,
-                                cudaStream_t s, int* kernels) {
+                                cudaStream_t s, int* kernels, const double* u = nullptr,
+                                int32_t* outcomes = nullptr) {
   return batch_enqueue_at(b, b->d_img.as<char>(), b->order_off, b->counter_off,
-                          b->d_gscratch.as<float2>(), states, probs, norms, s, kernels);
+                          b->d_gscratch.as<float2>(), states, probs, norms, s, kernels, u, outcomes);
 }
 
 // Keep freed stream-ordered allocations in the device's default memory pool
@@ -1151,10 +1296,9 @@ static void keep_pool_memory() {
   });
 }
 
-extern "C" {
-
-tqs_status tqs_batch_run(tqs_batch* b, tqs_c64* d_states, double* d_probs, double* d_norms,
-                         int use_graph, void* stream) {
+static tqs_status batch_run_impl(tqs_batch* b, tqs_c64* d_states, double* d_probs, double* d_norms,
+                                 const double* d_u, int32_t* d_outcomes, int use_graph,
+                                 void* stream) {
   if (!b || !d_states) return fail(TQS_ERR_ARG, "tqs_batch_run: NULL batch or states");
   if (!aligned16(d_states) || (d_probs && !aligned16(d_probs)))
     return fail(TQS_ERR_ARG, "tqs_batch_run: device buffers must be 16-byte aligned");
@@ -1164,8 +1308,9 @@ tqs_status tqs_batch_run(tqs_batch* b, tqs_c64* d_states, double* d_probs, doubl
     if (st != TQS_OK) return st;
   }
   float2* states = reinterpret_cast<float2*>(d_states);
-  if (!use_graph) return batch_enqueue(b, states, d_probs, d_norms, s, nullptr);
-  if (!b->exec || b->g_states != d_states || b->g_probs != d_probs || b->g_norms != d_norms) {
+  if (!use_graph) return batch_enqueue(b, states, d_probs, d_norms, s, nullptr, d_u, d_outcomes);
+  if (!b->exec || b->g_states != d_states || b->g_probs != d_probs || b->g_norms != d_norms ||
+      b->g_u != d_u || b->g_outcomes != d_outcomes) {
     if (b->exec) { cudaGraphExecDestroy(b->exec); b->exec = nullptr; }
     if (b->graph) { cudaGraphDestroy(b->graph); b->graph = nullptr; }
     if (!b->cap_stream)
@@ -1176,7 +1321,8 @@ tqs_status tqs_batch_run(tqs_batch* b, tqs_c64* d_states, double* d_probs, doubl
              "tqs_batch: begin capture");
     const int64_t before = tqs_launch_count();
     int kernels = 0;
-    tqs_status st = batch_enqueue(b, states, d_probs, d_norms, b->cap_stream, &kernels);
+    tqs_status st = batch_enqueue(b, states, d_probs, d_norms, b->cap_stream, &kernels, d_u,
+                                  d_outcomes);
     cudaGraph_t g = nullptr;
     cudaError_t e = cudaStreamEndCapture(b->cap_stream, &g);
     count_launches(before - tqs_launch_count());  // captured launches did not run yet
@@ -1187,6 +1333,8 @@ tqs_status tqs_batch_run(tqs_batch* b, tqs_c64* d_states, double* d_probs, doubl
     b->g_states = d_states;
     b->g_probs = d_probs;
     b->g_norms = d_norms;
+    b->g_u = d_u;
+    b->g_outcomes = d_outcomes;
     b->graph_kernels = kernels;
   }
   TQS_CUDA(cudaGraphLaunch(b->exec, s), "tqs_batch: graph launch");
@@ -1194,9 +1342,35 @@ tqs_status tqs_batch_run(tqs_batch* b, tqs_c64* d_states, double* d_probs, doubl
   return TQS_OK;
 }
 
+extern "C" {
+
+tqs_status tqs_batch_run(tqs_batch* b, tqs_c64* d_states, double* d_probs, double* d_norms,
+                         int use_graph, void* stream) {
+  if (b && b->instr_off.back() > 0)
+    return fail(TQS_ERR_UNSUPPORTED,
+                "tqs_batch_run: the batch holds measure/reset instructions: use tqs_batch_run_measured");
+  return batch_run_impl(b, d_states, d_probs, d_norms, nullptr, nullptr, use_graph, stream);
+}
+
+tqs_status tqs_batch_run_measured(tqs_batch* b, tqs_c64* d_states, double* d_probs,
+                                  double* d_norms, const double* d_u, int32_t* d_outcomes,
+                                  int use_graph, void* stream) {
+  if (b && b->instr_off.back() > 0 && !d_u)
+    return fail(TQS_ERR_ARG, "tqs_batch_run_measured: the batch holds instructions: d_u is NULL");
+  return batch_run_impl(b, d_states, d_probs, d_norms, d_u, d_outcomes, use_graph, stream);
+}
+
+tqs_status tqs_batch_instructions(const tqs_batch* b, int64_t* h_off) {
+  if (!b || !h_off) return fail(TQS_ERR_ARG, "tqs_batch_instructions: NULL argument");
+  std::memcpy(h_off, b->instr_off.data(), b->instr_off.size() * sizeof(int64_t));
+  return TQS_OK;
+}
+
 tqs_status tqs_batch_run_host(tqs_batch* b, tqs_c64* h_states, double* h_probs, double* h_norms,
                               void* stream) {
   if (!b) return fail(TQS_ERR_ARG, "tqs_batch_run_host: batch is NULL");
+  if (b->instr_off.back() > 0)
+    return fail(TQS_ERR_UNSUPPORTED, "tqs_batch_run_host: the batch holds measure/reset instructions");
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   keep_pool_memory();
   // Everything this call needs on the device (the program is its input) comes
@@ -1243,6 +1417,9 @@ tqs_status tqs_batch_destroy(tqs_batch* b) {
 }
 
 tqs_status tqs_circuit_unitary(tqs_circuit* c, int prec, tqs_c64* d_U, void* stream) {
+  if (c && c->n_instr > 0)
+    return fail(TQS_ERR_UNSUPPORTED,
+                "tqs_circuit_unitary: measure/reset instructions have no circuit unitary");
   if (!c || !d_U) return fail(TQS_ERR_ARG, "tqs_circuit_unitary: NULL argument");
   if (!aligned16(d_U)) return fail(TQS_ERR_ARG, "tqs_circuit_unitary: d_U must be 16-byte aligned");
   if (c->n > TQS_MAX_DENSE_QUBITS)
@@ -1506,10 +1683,10 @@ tqs_status tqs_server_submit_packed(tqs_server* sv, int64_t tag, int n_qubits, i
     Gate& g = gates[k];
     tqs_status st = check_gate(n_qubits, kind, h_qubits + 2 * k, nq, h_params + 8 * k, 8, g);
     if (st != TQS_OK) return st;
-    int step = 0;
-    for (int j = 0; j < g.nq; ++j) step = std::max(step, last[g.q[j]] + 1);
-    g.step = step;
-    for (int j = 0; j < g.nq; ++j) last[g.q[j]] = step;
+    if (is_instruction(kind))
+      return fail(TQS_ERR_UNSUPPORTED,
+                  "tqs_server_submit_packed: measure/reset instructions are not served");
+    assign_step(last, g);
   }
   SrvReq r;
   r.tag = tag;
@@ -1649,6 +1826,94 @@ tqs_status tqs_selftest_wait_timeout(int64_t wait_cycles, void* stream) {
   TQS_CUDA(cudaMemcpyAsync(&h, status.p, sizeof(int), cudaMemcpyDeviceToHost, s), "read status");
   TQS_CUDA(cudaStreamSynchronize(s), "tqs_selftest_wait_timeout: sync");
   if (h) return fail(TQS_ERR_TIMEOUT, "tqs_selftest_wait_timeout: the wait ran out (expected)");
+  return TQS_OK;
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------- collapse
+// Inverse-CDF sampling (simulateAndCollapse, Sec. 5.2).  Scratch layout:
+// [global-path segments][shared-memory-path segments][block totals]
+// [block prefixes][chunk prefixes][segment totals].
+
+namespace {
+
+DevBuf& sample_scratch_tls() {
+  static thread_local DevBuf buf;
+  return buf;
+}
+
+}  // namespace
+
+// One probability vector, global path (its shots spread over the whole GPU).
+static tqs_status sample_one_state(DevBuf& buf, const double* d_probs, int n, int64_t shots,
+                                   const double* d_u, int64_t* d_out, cudaStream_t s,
+                                   const char* who) {
+  SamplePlan plan;
+  plan.add(0, 0, n, false);
+  plan.layout();
+  TQS_CUDA(buf.ensure(plan.bytes), "sample: cudaMalloc scratch");
+  TQS_CUDA(plan.upload(buf.as<char>(), s), "sample: upload segment");
+  TQS_CUDA(launch_sample(plan.launch(buf.as<char>(), d_probs, d_u, shots, d_out), s), who);
+  return TQS_OK;
+}
+
+extern "C" {
+
+tqs_status tqs_sample(const double* d_probs, int n, int64_t shots, const double* d_u,
+                      int64_t* d_out, void* stream) {
+  if (!d_probs) return fail(TQS_ERR_ARG, "tqs_sample: d_probs is NULL");
+  if (n < 1 || n > 30) return fail(TQS_ERR_TOO_MANY_QUBITS, "tqs_sample: n %d outside [1, 30]", n);
+  if (shots < 0) return fail(TQS_ERR_ARG, "tqs_sample: shots < 0");
+  if (shots > 0 && (!d_u || !d_out)) return fail(TQS_ERR_ARG, "tqs_sample: NULL d_u or d_out");
+  return sample_one_state(sample_scratch_tls(), d_probs, n, shots, d_u, d_out,
+                          static_cast<cudaStream_t>(stream), "tqs_sample: launch");
+}
+
+tqs_status tqs_simulate_and_collapse(tqs_circuit* c, const double* d_u, int64_t* d_index,
+                                     tqs_c64* d_state, void* stream) {
+  if (!c || !d_u || !d_index)
+    return fail(TQS_ERR_ARG, "tqs_simulate_and_collapse: NULL circuit, d_u or d_index");
+  if (d_state && !aligned16(d_state))
+    return fail(TQS_ERR_ARG, "tqs_simulate_and_collapse: d_state must be 16-byte aligned");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const size_t N = size_t(1) << c->n;
+  const size_t state_bytes = d_state ? 0 : N * sizeof(float2);
+  TQS_CUDA(c->d_collapse.ensure(state_bytes + N * sizeof(double)),
+           "tqs_simulate_and_collapse: cudaMalloc scratch");
+  tqs_c64* st = d_state ? d_state : c->d_collapse.as<tqs_c64>();
+  double* probs = reinterpret_cast<double*>(c->d_collapse.as<char>() + state_bytes);
+  tqs_status r = tqs_simulate(c, nullptr, st, probs, nullptr, stream);
+  if (r != TQS_OK) return r;
+  r = sample_one_state(c->d_sample, probs, c->n, 1, d_u, d_index, s,
+                       "tqs_simulate_and_collapse: sample");
+  if (r != TQS_OK) return r;
+  if (d_state)
+    TQS_CUDA(launch_set_basis(reinterpret_cast<float2*>(d_state), c->n, d_index, s),
+             "tqs_simulate_and_collapse: collapsed state");
+  return TQS_OK;
+}
+
+tqs_status tqs_batch_sample(tqs_batch* b, const double* d_probs, int shots, const double* d_u,
+                            int64_t* d_out, void* stream) {
+  if (!b || !d_probs) return fail(TQS_ERR_ARG, "tqs_batch_sample: NULL batch or d_probs");
+  if (!aligned16(d_probs)) return fail(TQS_ERR_ARG, "tqs_batch_sample: d_probs must be 16-byte aligned");
+  if (shots < 0) return fail(TQS_ERR_ARG, "tqs_batch_sample: shots < 0");
+  if (shots > 0 && (!d_u || !d_out)) return fail(TQS_ERR_ARG, "tqs_batch_sample: NULL d_u or d_out");
+  if (shots == 0) return TQS_OK;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if (!b->sample_plan) {
+    auto plan = std::make_unique<SamplePlan>();
+    for (int i = 0; i < b->count; ++i) plan->add(i, b->offsets[i], b->img.circs[i].n, true);
+    plan->layout();
+    TQS_CUDA(b->d_sample.ensure(plan->bytes), "tqs_batch_sample: cudaMalloc scratch");
+    TQS_CUDA(plan->upload(b->d_sample.as<char>(), s), "tqs_batch_sample: upload segments");
+    TQS_CUDA(cudaStreamSynchronize(s), "tqs_batch_sample: upload segments");
+    b->sample_plan = std::move(plan);
+  }
+  TQS_CUDA(launch_sample(b->sample_plan->launch(b->d_sample.as<char>(), d_probs, d_u, shots, d_out),
+                         s),
+           "tqs_batch_sample: launch");
   return TQS_OK;
 }
 

@@ -71,6 +71,11 @@ struct alignas(16) FusedPass {
   uint32_t op_count;
   float scale;         // exact power of two applied to every amplitude at the pass end
 };
+// A measure / reset instruction is a pass of its own, marked L[0] = kInstrPass:
+// L[1] = physical bit of the qubit, L[2] = 1 for a reset, op_begin = index of
+// its uniform and outcome (instruction ordinal plus the circuit's offset in
+// the batch), op_count = 0.
+constexpr uint8_t kInstrPass = 0xFF;
 static_assert(sizeof(FusedPass) == 16, "FusedPass layout");
 
 enum TeamKind : int32_t { TEAM_WARP = 0, TEAM_CTA = 1, TEAM_GLOBAL = 2 };
@@ -110,6 +115,8 @@ struct FusedLaunch {
   double* probs;            // nullable
   double* norms;            // nullable
   float2* gscratch;         // TEAM_GLOBAL: per-CTA state slots (2^16 amplitudes each)
+  const double* uniforms;   // instructions: one uniform each (nullable without instructions)
+  int32_t* outcomes;        // instructions: one outcome each (nullable)
   int32_t team;             // TeamKind of this launch
   int32_t warps_per_cta;    // TEAM_WARP
   int32_t slice_q;          // TEAM_WARP: log2 amplitudes per warp slice; TEAM_CTA: log2 per CTA
@@ -160,6 +167,50 @@ cudaError_t chain_simt(const StepFactor* d_factors, const StepDesc* steps, int n
 int probs_partial_count(int n);
 cudaError_t launch_probs(const float2* d_state, int n, double* d_probs, uint64_t zero_mask,
                          double* d_partials, int n_partials, double* d_sum, cudaStream_t s);
+
+// ---------------------------------------------------------------------------
+// Inverse-CDF sampling (collapse of simulateAndCollapse, Sec. 5.2).
+// ---------------------------------------------------------------------------
+constexpr int kSampleBlk = 256;    // probabilities per block of the cumulative sums
+constexpr int kSampleChunk = 8;    // consecutive probabilities summed by one lane
+__host__ __device__ inline int64_t sample_blocks(int n) {
+  return n >= 8 ? (int64_t(1) << (n - 8)) : 1;
+}
+
+struct SampleSeg {
+  int64_t p_off;    // offset of the segment's probabilities
+  int32_t n;        // the segment holds 2^n probabilities
+  int32_t blk_off;  // offset of its blocks in bsum / bpre (global path)
+  int64_t index;    // position of the segment in the caller's layout (u / out)
+};
+static_assert(sizeof(SampleSeg) == 24, "SampleSeg layout");
+
+// Segments with n <= kSampleSmemMaxQ can be sampled by one CTA each, with the
+// probabilities staged in shared memory; larger ones take the global path
+// (block tables, block prefix, one thread per shot).  Both paths compute the
+// same cumulative sums in the same order, so they give identical indices.
+constexpr int kSampleSmemMaxQ = 13;
+
+struct SampleLaunch {
+  const double* probs;     // device
+  const SampleSeg* gsegs;  // device: segments of the global path, ascending blk_off
+  int32_t n_gseg;
+  int64_t nblocks;         // sum of sample_blocks(n) over the global segments
+  double* bsum;            // device scratch [nblocks]: block totals
+  double* bpre;            // device scratch [nblocks]: exclusive block prefix per segment
+  double* cpre;            // device scratch [nblocks * 32]: exclusive chunk prefix in its block
+  double* tot;             // device scratch [n_gseg]: segment totals
+  const SampleSeg* ssegs;  // device: segments of the shared-memory path
+  int32_t n_sseg;
+  int32_t smem_q;          // log2 of the largest shared-memory segment
+  const double* u;         // device [segments * shots] uniforms in [0, 1)
+  int64_t shots;           // per segment
+  int64_t* out;            // device [segments * shots] sampled indices within the segment
+};
+
+cudaError_t launch_sample(const SampleLaunch& L, cudaStream_t s);
+// d_state[i] = (i == *d_index) for i < 2^n (the collapsed basis state).
+cudaError_t launch_set_basis(float2* d_state, int n, const int64_t* d_index, cudaStream_t s);
 
 // Process-wide count of kernel launches enqueued by this library.
 void count_launches(int64_t k);

@@ -207,6 +207,14 @@ def batch_circuits(count: int = 4096, seed_tag: int = 3) -> List[Tuple[int, List
     return [(n, random_mixed(n, d, (seed_tag, 1, i))) for i, (n, d) in enumerate(sizes)]
 
 
+def batch_circuits_fixed_n(count: int, n: int, seed_tag: int = 5) -> List[Tuple[int, List[Op]]]:
+    """The batched workload with every circuit at ``n`` qubits (depth ~ U{5..40}):
+    at n = 14 its states (128 KiB each) stream through HBM instead of L2."""
+    g = rng(seed_tag, 0)
+    depths = [int(g.integers(5, 41)) for _ in range(count)]
+    return [(n, random_mixed(n, d, (seed_tag, 1, i))) for i, d in enumerate(depths)]
+
+
 def paper_mix(n: int, count: int, seed_tag: int = 1) -> List[Tuple[str, List[Op]]]:
     """``count`` circuits shaped like the paper's n-qubit programs, cycling
     GHZ, DJ-constant, DJ-balanced and QFT on a seeded basis state."""

@@ -10,7 +10,8 @@ No GPU is needed: only host entry points are called.
 import numpy as np
 import pytest
 
-from oracle import fsv_route, kron_route
+from measure_cases import safe_uniforms, with_instructions
+from oracle import collapse, fsv_route, kron_route
 from paper_2305_14398_gb300 import binding as B
 from paper_2305_14398_gb300 import workloads as W
 
@@ -23,13 +24,29 @@ def ins0(x, b):
     return ((x >> b) << (b + 1)) | (x & ((1 << b) - 1))
 
 
-def replay(n, passes, ops, pos, out_scale=1.0, gen_index=0):
+def replay(n, passes, ops, pos, out_scale=1.0, gen_index=0, uniforms=None, outcomes=None):
     nint = max(n, 4)
     st = np.zeros(1 << nint, dtype=np.complex128)
     st[gen_index] = 1.0
     G = (1 << nint) >> 4
-    for ps in passes:
+    for pi, ps in enumerate(passes):
         L = [int(v) for v in ps["L"]]
+        if L[0] == 255:  # measure / reset instruction on physical bit L[1]
+            assert pi > 0 and int(ps["op_count"]) == 0
+            idx = np.arange(1 << nint)
+            bit = (idx >> L[1]) & 1
+            p = np.abs(st) ** 2
+            s0, t = float(np.sum(p[bit == 0])), float(np.sum(p))
+            k = int(ps["op_begin"])
+            b = 0 if uniforms[k] * t < s0 else 1
+            outcomes.append((k, b))
+            kept = np.where(bit == b, st, 0.0) / np.sqrt((s0 if b == 0 else t - s0) / t)
+            if L[2] and b == 1:
+                st = np.zeros_like(kept)
+                st[idx ^ (1 << L[1])] = kept
+            else:
+                st = kept
+            continue
         assert L == sorted(L) and len(set(L)) == 4 and max(L) < nint
         g = np.arange(G, dtype=np.int64)
         base = g
@@ -290,3 +307,69 @@ def test_leading_x_gates_fold_into_the_start_state():
     prep = compiled(n, W.qft_on_basis(n, x))
     assert prep[4] == x and bare[4] == 0
     assert len(prep[1]) == len(bare[1]) and len(prep[0]) == len(bare[0])
+
+
+# ------------------------------------------------ measure / reset instructions
+
+MEAS_CASES = [(n, s) for n in (1, 2, 3, 5, 8, 11) for s in range(3)]
+
+
+@pytest.mark.parametrize("n,seed", MEAS_CASES)
+def test_program_replay_with_instructions_matches_oracle(n, seed):
+    ops = with_instructions(n, 100 * n + seed)
+    u = safe_uniforms(n, ops, seed)
+    passes, prog_ops, pos, osc, gen = compiled(n, ops)
+    marks = [int(p["op_begin"]) for p in passes if int(p["L"][0]) == 255]
+    assert marks == list(range(len(u)))
+    outs = []
+    got = replay(n, passes, prog_ops, pos, osc, gen, uniforms=u, outcomes=outs)
+    want, want_outs = collapse.simulate_measured(n, ops, u)
+    assert [b for _, b in outs] == want_outs
+    assert np.max(np.abs(got - want)) < 2e-6
+
+
+def test_instruction_is_a_barrier_step():
+    ops = [("h", (0,), ()), ("h", (1,), ()), ("measure", (0,), ()), ("h", (2,), ()),
+           ("x", (1,), ())]
+    c = B.circuit_from_ops(3, ops)
+    try:
+        assert B.tqs_circuit_steps(c) == [0, 0, 1, 2, 2]
+        assert B.tqs_circuit_info(c)[2] == 3
+    finally:
+        B.tqs_circuit_destroy(c)
+
+
+def test_instruction_reads_the_relabelled_bit():
+    """After SWAP(0, 2) the logical qubit 0 lives on physical bit 2."""
+    passes, _, pos, _, _ = compiled(3, [("h", (1,), ()), ("swap", (0, 2), ()), ("measure", (0,), ())])
+    ins = [p for p in passes if int(p["L"][0]) == 255]
+    assert len(ins) == 1 and int(ins[0]["L"][1]) == int(pos[0]) == 2
+
+
+def test_unitary_forms_reject_instructions():
+    ops = [("h", (0,), ()), ("measure", (0,), ())]
+    c = B.circuit_from_ops(2, ops)
+    try:
+        for call in (lambda: B.tqs_simulate(c, None, stream=0),
+                     lambda: B.tqs_simulate_plain(c, None, stream=0),
+                     lambda: B.tqs_circuit_unitary(c, B.PREC_FP32_SIMT, None, stream=0)):
+            with pytest.raises(B.TqsError) as e:
+                call()
+            assert e.value.name == "TQS_ERR_UNSUPPORTED"
+    finally:
+        B.tqs_circuit_destroy(c)
+    b = B.tqs_batch_create_packed(*B.pack_ops([(2, ops), (3, W.ghz_chain(3)), (2, ops + ops)]))
+    try:
+        assert B.tqs_batch_instructions(b).tolist() == [0, 1, 1, 3]
+        with pytest.raises(B.TqsError) as e:
+            B.tqs_batch_run(b, None, stream=0)
+        assert e.value.name == "TQS_ERR_UNSUPPORTED"
+    finally:
+        B.tqs_batch_destroy(b)
+    sv = B.tqs_server_create(1 << 30, 1, 4)
+    try:
+        with pytest.raises(B.TqsError) as e:
+            B.tqs_server_submit_packed(sv, 0, 2, B.pack_request(ops))
+        assert e.value.name == "TQS_ERR_UNSUPPORTED"
+    finally:
+        B.tqs_server_destroy(sv)
