@@ -8,7 +8,8 @@ It is plain numpy in complex128 and follows the paper step by step:
 
 * ``gates``       - gate matrices: Table 1 (H, X, Y, Z, R_phi), S and T
                     (named in Sec. 5.2), the controlled form of eq. 7 / eq. 8,
-                    and the textbook rotations used by the synthetic workloads.
+                    the textbook rotations used by the synthetic workloads, and
+                    custom k-qubit unitaries (Sec. 5.2 operation interface).
 * ``kron_route``  - the unitary-matrix method itself: circuit steps (Sec. 5.2),
                     the step unitary as a Kronecker product of the step's
                     factors (Algorithm 2, eq. 9s1) with controlled gates as

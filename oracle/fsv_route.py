@@ -42,9 +42,21 @@ def _pair_update(psi: np.ndarray, i0: np.ndarray, i1: np.ndarray, u: np.ndarray)
 
 
 def apply_op(psi: np.ndarray, n: int, op: Op) -> None:
-    """Apply one operation in place (eq. 12 and its two-qubit forms)."""
+    """Apply one operation in place (eq. 12 and its two-qubit forms; a custom
+    k-qubit unitary updates each group of 2^k amplitudes whose indices differ
+    only in its qubits by its matrix)."""
     name, qs, ps = op
-    if name == "swap":
+    if name == "unitary":
+        m = gates.custom_matrix(qs, ps)
+        base = _indices_with(n, [(q, 0) for q in qs])
+        j = np.arange(m.shape[0], dtype=np.int64)
+        local = np.zeros_like(j)
+        for t, q in enumerate(qs):
+            local |= ((j >> t) & 1) << q
+        idx = base[:, None] + local[None, :]
+        psi[idx] = np.tensordot(psi[idx], m, axes=([1], [1])) if psi.ndim == 1 else \
+            np.einsum("gc...,rc->gr...", psi[idx], m)
+    elif name == "swap":
         a, b = qs
         i01 = _indices_with(n, [(a, 0), (b, 1)])
         i10 = i01 ^ ((1 << a) | (1 << b))

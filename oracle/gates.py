@@ -109,3 +109,33 @@ def two_qubit_matrix_ct(name: str, params: Sequence[float] = ()) -> np.ndarray:
 
 def is_two_qubit(name: str) -> bool:
     return name in ("cx", "cz", "cp", "cu", "swap")
+
+
+# ------------------------------------------------------------ custom unitaries
+# Sec. 5.2 (operation interface): a custom unitary, registered by the user, is
+# applied to a range of qubits.  Here it is the op ("unitary", qubits, params):
+# k = len(qubits) qubits, params = the 2^k x 2^k matrix row-major as interleaved
+# (re, im) numbers; bit t of the matrix's local index is qubit qubits[t]
+# (little-endian, as for the state).
+
+MAX_CUSTOM_QUBITS = 5
+
+
+def custom_matrix(qubits: Sequence[int], params: Sequence[float]) -> np.ndarray:
+    k = len(qubits)
+    if not 1 <= k <= MAX_CUSTOM_QUBITS:
+        raise ValueError("a custom unitary acts on 1..5 qubits")
+    d = 1 << k
+    v = np.asarray(params, dtype=np.float64)
+    if v.size != 2 * d * d:
+        raise ValueError(f"a {k}-qubit custom unitary takes {2 * d * d} numbers")
+    return (v[0::2] + 1j * v[1::2]).reshape(d, d)
+
+
+def custom_params(m: np.ndarray) -> Tuple[float, ...]:
+    """The params of ("unitary", qubits, params) for matrix m."""
+    m = np.asarray(m, dtype=np.complex128)
+    out = np.empty(2 * m.size)
+    out[0::2] = m.real.reshape(-1)
+    out[1::2] = m.imag.reshape(-1)
+    return tuple(out.tolist())

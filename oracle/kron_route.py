@@ -39,9 +39,12 @@ def validate(n: int, ops: Sequence[Op]) -> None:
     if n < 1:
         raise ValueError("a circuit needs at least one qubit")
     for name, qs, ps in ops:
-        want = 2 if gates.is_two_qubit(name) else 1
-        if len(qs) != want:
-            raise ValueError(f"{name} takes {want} qubit(s)")
+        if name == "unitary":
+            gates.custom_matrix(qs, ps)
+        else:
+            want = 2 if gates.is_two_qubit(name) else 1
+            if len(qs) != want:
+                raise ValueError(f"{name} takes {want} qubit(s)")
         if any(q < 0 or q >= n for q in qs):
             raise ValueError(f"{name}: qubit out of range")
         if len(set(qs)) != len(qs):
@@ -85,6 +88,21 @@ def _swap_column_map(n: int, swaps: Sequence[Tuple[int, int]]) -> np.ndarray:
     return out
 
 
+def _embedded_custom(n: int, qs: Sequence[int], m: np.ndarray) -> np.ndarray:
+    """A custom factor on qubits qs with identity on the others: entry (r, c) is
+    m[local(r), local(c)] when r and c agree on every other qubit, else 0
+    (the Kronecker product with the identity, for qubits in any order)."""
+    dim = 1 << n
+    idx = np.arange(dim, dtype=np.int64)
+    local = np.zeros(dim, dtype=np.int64)
+    mask = 0
+    for t, q in enumerate(qs):
+        local |= ((idx >> q) & 1) << t
+        mask |= 1 << q
+    same = (idx[:, None] & ~mask) == (idx[None, :] & ~mask)
+    return np.where(same, m[local[:, None], local[None, :]], 0.0)
+
+
 def step_unitary(n: int, step: Sequence[Op]) -> np.ndarray:
     """Dense 2^n x 2^n step unitary of one step (Algorithm 2 with eq. 7)."""
     if n > MAX_DENSE_QUBITS:
@@ -92,13 +110,16 @@ def step_unitary(n: int, step: Sequence[Op]) -> np.ndarray:
     fixed: Dict[int, np.ndarray] = {}
     controlled: List[Tuple[int, int, List[Tuple[np.ndarray, np.ndarray]]]] = []
     swaps: List[Tuple[int, int]] = []
+    customs: List[Tuple[Tuple[int, ...], np.ndarray]] = []
     used = set()
     for name, qs, ps in step:
         for q in qs:
             if q in used:
                 raise ValueError("operations of one step must act on disjoint qubits")
             used.add(q)
-        if name == "swap":
+        if name == "unitary":
+            customs.append((tuple(qs), gates.custom_matrix(qs, ps)))
+        elif name == "swap":
             swaps.append((qs[0], qs[1]))
         elif gates.is_two_qubit(name):
             controlled.append((qs[0], qs[1], gates.two_qubit_terms(name, ps)))
@@ -118,6 +139,10 @@ def step_unitary(n: int, step: Sequence[Op]) -> np.ndarray:
         s += _kron_chain(op_list)
     if swaps:
         s = s[:, _swap_column_map(n, swaps)]
+    # custom factors act on qubits no other factor touches: they commute with
+    # the rest and multiply it
+    for qs, m in customs:
+        s = s @ _embedded_custom(n, qs, m)
     return s
 
 
