@@ -122,6 +122,28 @@ tqs_status tqs_circuit_destroy(tqs_circuit* c);
 tqs_status tqs_add_gate(tqs_circuit* c, int gate, const int* qubits, int nq,
                         const double* params, int np);
 
+/* Custom unitaries (Sec. 5.2, operation interface: the data of a custom
+ * function is registered with the operation data provider under a unique
+ * name, then applied to qubits; insertion checks that data of the right
+ * format and size was registered).
+ * tqs_register_unitary: m holds the 2^k x 2^k matrix row-major as interleaved
+ * (re, im) doubles (2 * 4^k of them), 1 <= k <= 5; it must be unitary to 1e-9
+ * (every entry of M^dagger M - I).  The registry is process-wide and
+ * thread-safe; registering a name again replaces its data for circuits built
+ * afterwards (circuits keep the data they were built with).  The matrix is
+ * copied.  Errors: TQS_ERR_ARG. */
+tqs_status tqs_register_unitary(const char* name, int k, const double* m);
+
+/* Append the registered unitary `name` on qubits[0..k): bit t of the matrix's
+ * local row / column index is the bit of qubit qubits[t] (little-endian, as
+ * for the state).  k must equal the registered size.  Like every operation
+ * it joins the step after the last step touching one of its qubits.  Errors:
+ * TQS_ERR_ARG (no such name, k mismatch), TQS_ERR_QUBIT_RANGE,
+ * TQS_ERR_QUBIT_DUP.  Circuits with custom unitaries run in every form
+ * (fused, plain, circuit unitary, batches built from handles); the packed
+ * batch and server formats have no custom kind. */
+tqs_status tqs_add_custom(tqs_circuit* c, const char* name, const int* qubits, int k);
+
 /* Sizes of the circuit: qubits, gates, and steps of the step table. */
 tqs_status tqs_circuit_info(const tqs_circuit* c, int* n_qubits, int* n_gates, int* n_steps);
 

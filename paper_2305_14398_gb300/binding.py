@@ -53,6 +53,8 @@ _SIGS = {
     "tqs_circuit_create": (_i, [_i, ctypes.POINTER(_vp)]),
     "tqs_circuit_destroy": (_i, [_vp]),
     "tqs_add_gate": (_i, [_vp, _i, _pi, _i, _pd, _i]),
+    "tqs_register_unitary": (_i, [ctypes.c_char_p, _i, _pd]),
+    "tqs_add_custom": (_i, [_vp, ctypes.c_char_p, _pi, _i]),
     "tqs_circuit_info": (_i, [_vp, _pi, _pi, _pi]),
     "tqs_circuit_steps": (_i, [_vp, _pi]),
     "tqs_circuit_program": (_i, [_vp, _pi, _pi, _vp, _vp, _vp, ctypes.POINTER(ctypes.c_float),
@@ -157,6 +159,28 @@ def tqs_add_gate(c: int, gate, qubits: Sequence[int], params: Sequence[float] = 
     _check(lib().tqs_add_gate(c, gid, qs, len(qubits), ps, len(params)))
 
 
+def tqs_register_unitary(name: str, m) -> None:
+    """Register a 2^k x 2^k unitary (complex array) under `name`."""
+    m = np.asarray(m, dtype=np.complex128)
+    k = int(m.shape[0]).bit_length() - 1
+    flat = np.empty(2 * m.size, dtype=np.float64)
+    flat[0::2] = m.real.reshape(-1)
+    flat[1::2] = m.imag.reshape(-1)
+    arr = (ctypes.c_double * flat.size)(*flat.tolist())
+    _check(lib().tqs_register_unitary(name.encode(), k, arr))
+
+
+def tqs_add_custom(c: int, name: str, qubits: Sequence[int]) -> None:
+    qs = (ctypes.c_int * len(qubits))(*[int(q) for q in qubits])
+    _check(lib().tqs_add_custom(c, name.encode(), qs, len(qubits)))
+
+
+def _custom_name(qubits, params) -> str:
+    import hashlib
+    h = hashlib.sha1(np.asarray(params, dtype=np.float64).tobytes()).hexdigest()[:20]
+    return f"_m{len(qubits)}_{h}"
+
+
 def tqs_circuit_info(c: int) -> Tuple[int, int, int]:
     n, g, s = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
     _check(lib().tqs_circuit_info(c, ctypes.byref(n), ctypes.byref(g), ctypes.byref(s)))
@@ -197,7 +221,16 @@ def circuit_from_ops(n: int, ops: Iterable) -> int:
     c = tqs_circuit_create(n)
     try:
         for name, qs, ps in ops:
-            tqs_add_gate(c, name, qs, ps)
+            if name == "unitary":
+                # ("unitary", qubits, params): params = the 2^k x 2^k matrix,
+                # row-major, interleaved (re, im)
+                v = np.asarray(ps, dtype=np.float64)
+                d = 1 << len(qs)
+                key = _custom_name(qs, v)
+                tqs_register_unitary(key, (v[0::2] + 1j * v[1::2]).reshape(d, d))
+                tqs_add_custom(c, key, qs)
+            else:
+                tqs_add_gate(c, name, qs, ps)
     except Exception:
         tqs_circuit_destroy(c)
         raise

@@ -357,7 +357,7 @@ __device__ __forceinline__ void team_sync() {
 // kept half to bit 0.  Any global scale the amplitudes carry cancels in
 // S_b / T.
 template <int TEAM>
-__device__ void instr_pass(const FusedLaunch& L, int nint, int bit, bool reset, uint32_t k,
+__device__ __noinline__ void instr_pass(const FusedLaunch& L, int nint, int bit, bool reset, uint32_t k,
                            float2* st, int rank, int size, double* s_red) {
   const int half = 1 << (nint - 1);
   const int m = 1 << bit;
@@ -399,6 +399,59 @@ __device__ void instr_pass(const FusedLaunch& L, int nint, int bit, bool reset, 
   team_sync<TEAM>();
 }
 
+// Custom k-qubit unitary (Sec. 5.2 operation interface), 2 <= k <= 5 (the
+// pass's scale word holds the mask of the k physical bits): the
+// amplitudes fall into groups of G = 2^k whose indices differ only in the k
+// physical bits; out[r] = sum_c M[r][c] in[c] per group (the per-gate update
+// of eq. 12 widened to k qubits).  A warp takes 32 / G groups at a time, lane
+// r of a group computing row r from the group's amplitudes (read by all its
+// lanes) and the transposed coefficients (consecutive lanes, consecutive
+// words); FP32 lo parts are accumulated before hi parts.  Warps work on
+// disjoint groups; within a warp every read of a group precedes its writes.
+// Physical index of matrix-local index j: bit t of j goes to bit (bits >> 5t) & 31.
+__device__ __forceinline__ int wide_local(int j, int k, uint32_t bits) {
+  int v = 0;
+#pragma unroll
+  for (int t = 0; t < kMaxCustomQubits; ++t)
+    if (t < k) v |= ((j >> t) & 1) << ((bits >> (5 * t)) & 31);
+  return v;
+}
+
+template <int TEAM>
+__device__ __noinline__ void wide_pass(const FusedLaunch& L, int nint, int k, uint32_t coef_off,
+                          uint32_t bits, uint32_t mask, float2* st, int rank, int size) {
+  const int G = 1 << k;
+  const int lane = rank & 31, warp = rank >> 5, nwarps = size >> 5;
+  const int per_warp = 32 >> k;
+  const int sub = lane >> k, r = lane & (G - 1);
+  const int loc_r = wide_local(r, k, bits);
+  const int ngroups = 1 << (nint - k);
+  const float2* mh = L.coef + coef_off;
+  const float2* ml = mh + G * G;
+  for (int g0 = warp * per_warp; g0 < ngroups; g0 += nwarps * per_warp) {
+    const int g = g0 + sub;
+    const bool on = g < ngroups;
+    int base = g;
+    for (uint32_t m = mask; m != 0; m &= m - 1) base = ins0(base, __ffs(m) - 1);
+    float ar = 0.f, ai = 0.f;  // lo products
+    float br = 0.f, bi = 0.f;  // hi products
+    if (on) {
+      for (int c = 0; c < G; ++c) {
+        const float2 x = st[swz(base | wide_local(c, k, bits))];
+        const float2 h = __ldg(mh + c * G + r), l = __ldg(ml + c * G + r);
+        ar = fmaf(l.x, x.x, fmaf(-l.y, x.y, ar));
+        ai = fmaf(l.x, x.y, fmaf(l.y, x.x, ai));
+        br = fmaf(h.x, x.x, fmaf(-h.y, x.y, br));
+        bi = fmaf(h.x, x.y, fmaf(h.y, x.x, bi));
+      }
+    }
+    __syncwarp();
+    if (on) st[swz(base | loc_r)] = make_float2(ar + br, ai + bi);
+    __syncwarp();
+  }
+  team_sync<TEAM>();
+}
+
 template <int TEAM>
 __device__ void run_circuit(const FusedLaunch& L, int ci, float2* st, int rank, int size,
                             double* s_red) {
@@ -418,6 +471,10 @@ __device__ void run_circuit(const FusedLaunch& L, int ci, float2* st, int rank, 
     const int l0 = pr.x & 0xff, l1 = (pr.x >> 8) & 0xff, l2 = (pr.x >> 16) & 0xff, l3 = pr.x >> 24;
     if (l0 == kInstrPass) {
       instr_pass<TEAM>(L, nint, l1, (l2 & 1) != 0, pr.y, st, rank, size, s_red);
+      continue;
+    }
+    if (l0 == kWidePass) {
+      wide_pass<TEAM>(L, nint, l1, pr.y, pr.z, pr.w, st, rank, size);
       continue;
     }
     const FusedOp* ops = L.ops + pr.y;

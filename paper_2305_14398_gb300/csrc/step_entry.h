@@ -2,8 +2,9 @@
 // the product over the step's factors of the factor's entry at the bits it
 // acts on, times the identity (a Kronecker delta) on idle qubits.  A
 // two-qubit factor's 4x4 matrix is indexed by (bit q0 << 1) | bit q1 (eq. 7
-// with the control first).  Shared by the plain materialiser and the chain's
-// operand generator.
+// with the control first); a custom k-qubit factor's matrix by the local
+// index whose bit t is the bit of qubit qc[t].  Shared by the plain
+// materialiser and the chain's operand generator.
 #pragma once
 
 #include "tqs_internal.h"
@@ -21,6 +22,15 @@ __device__ __forceinline__ float2 step_entry(const StepFactor* fs, int nf, uint3
   for (int k = 0; k < nf; ++k) {
     const StepFactor& f = fs[k];
     int idx;
+    if (f.custom) {
+      int rr = 0, cc = 0;
+      for (int t = 0; t < f.nq; ++t) {
+        rr |= ((r >> f.qc[t]) & 1) << t;
+        cc |= ((c >> f.qc[t]) & 1) << t;
+      }
+      v = step_cmul(v, f.coef[(rr << f.nq) + cc]);
+      continue;
+    }
     if (f.nq == 1) {
       idx = ((r >> f.q0) & 1) * 2 + ((c >> f.q0) & 1);
     } else {

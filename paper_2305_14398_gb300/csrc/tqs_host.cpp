@@ -149,15 +149,33 @@ static bool is_unitary(const Mat2& u, double tol) {
   return std::abs(e00 - 1.0) <= tol && std::abs(e11 - 1.0) <= tol && std::abs(e01) <= tol;
 }
 
+// A registered custom unitary (Sec. 5.2: custom unitary data is registered
+// with the operation data provider, then applied to qubits).
+struct CustomMat {
+  int k = 0;              // qubits
+  std::vector<cd> m;      // 2^k x 2^k, row-major; local index bit t = qubit t of the gate
+};
+
+// Internal kind of a custom unitary (outside the tqs_gate range).
+constexpr int kCustomKind = 64;
+
 // One recorded operation.
 struct Gate {
   int kind;
-  int q[2];
+  int q[kMaxCustomQubits];  // qubits (controlled: {control, target}; custom: local bit order)
   int nq;
   double p[8];
-  Mat2 u;     // single-qubit matrix, or the controlled U
+  Mat2 u;     // single-qubit matrix, the controlled U, or a 1-qubit custom matrix
   int step;   // step index (ASAP)
+  std::shared_ptr<const CustomMat> cm;  // custom unitaries with k >= 2
 };
+
+static bool is_wide(const Gate& g) { return g.kind == kCustomKind && g.nq >= 2; }
+static uint32_t qubit_mask(const Gate& g) {
+  uint32_t m = 0;
+  for (int i = 0; i < g.nq; ++i) m |= 1u << g.q[i];
+  return m;
+}
 
 static inline float2 to_f2(cd z) {
   return make_float2(static_cast<float>(z.real()), static_cast<float>(z.imag()));
@@ -197,6 +215,7 @@ struct Program {
   float out_scale = 1.0f;
   int gen_index = 0;  // basis state the program starts from (leading X gates folded)
   int n_instr = 0;    // measure / reset instructions (one pass each)
+  std::vector<float2> coef;  // custom unitaries' coefficients (wide passes)
   double cost = 0.0;
 };
 
@@ -230,7 +249,7 @@ static void compile_program(int n, const std::vector<const Gate*>& gs_in, Progra
         P.gen_index ^= 1 << g->q[0];
         continue;
       }
-      touched |= (1u << g->q[0]) | (g->nq == 2 ? (1u << g->q[1]) : 0u);
+      touched |= qubit_mask(*g);
       gs.push_back(g);
     }
   }
@@ -359,7 +378,8 @@ static void compile_program(int n, const std::vector<const Gate*>& gs_in, Progra
   size_t next = 0;
   auto take_segment = [&]() {
     pending.clear();
-    while (next < order.size() && !is_instruction(gs[order[next]]->kind)) pending.push_back(order[next++]);
+    while (next < order.size() && !is_instruction(gs[order[next]]->kind) && !is_wide(*gs[order[next]]))
+      pending.push_back(order[next++]);
   };
   take_segment();
   for (;;) {
@@ -372,7 +392,7 @@ static void compile_program(int n, const std::vector<const Gate*>& gs_in, Progra
     for (; idx < pending.size(); ++idx) {
       if (blocked == all) break;
       const Gate& g = *gs[pending[idx]];
-      const uint32_t qm = (1u << g.q[0]) | (g.nq == 2 ? (1u << g.q[1]) : 0u);
+      const uint32_t qm = qubit_mask(g);
       if (qm & blocked) {  // an earlier gate on one of its qubits waits: so must it,
         blocked |= qm;     // and every later gate on any of its qubits
         still.push_back(pending[idx]);
@@ -400,14 +420,39 @@ static void compile_program(int n, const std::vector<const Gate*>& gs_in, Progra
     const Gate& g = *gs[order[next++]];
     if (P.passes.empty()) emit_pass(0u, 0, false);  // the first pass generates the start state
     FusedPass ps{};
-    ps.L[0] = kInstrPass;
-    ps.L[1] = static_cast<uint8_t>(phys[g.q[0]]);
-    ps.L[2] = g.kind == TQS_RESET ? 1 : 0;
-    ps.op_begin = static_cast<uint32_t>(P.n_instr++);
-    ps.op_count = 0;
-    ps.scale = 1.0f;
+    if (is_wide(g)) {
+      // custom k-qubit unitary: FP32 hi + lo coefficients, transposed
+      const int k = g.nq, G = 1 << k;
+      ps.L[0] = kWidePass;
+      ps.L[1] = static_cast<uint8_t>(k);
+      ps.op_begin = static_cast<uint32_t>(P.coef.size());
+      uint32_t bits = 0, mask = 0;
+      for (int t = 0; t < k; ++t) {
+        bits |= static_cast<uint32_t>(phys[g.q[t]]) << (5 * t);
+        mask |= 1u << phys[g.q[t]];
+      }
+      ps.op_count = bits;
+      std::memcpy(&ps.scale, &mask, sizeof(mask));
+      const size_t c0 = P.coef.size();
+      P.coef.resize(c0 + 2 * size_t(G) * G);
+      for (int r = 0; r < G; ++r)
+        for (int c = 0; c < G; ++c) {
+          const cd v = g.cm->m[size_t(r) * G + c];
+          const float2 hi = to_f2(v);
+          P.coef[c0 + size_t(c) * G + r] = hi;
+          P.coef[c0 + size_t(G) * G + size_t(c) * G + r] = to_f2(v - cd(hi.x, hi.y));
+        }
+      P.cost += 8.0 * G * static_cast<double>(1u << nint);
+    } else {
+      ps.L[0] = kInstrPass;
+      ps.L[1] = static_cast<uint8_t>(phys[g.q[0]]);
+      ps.L[2] = g.kind == TQS_RESET ? 1 : 0;
+      ps.op_begin = static_cast<uint32_t>(P.n_instr++);
+      ps.op_count = 0;
+      ps.scale = 1.0f;
+      P.cost += 2.0 * static_cast<double>(1u << nint);
+    }
     P.passes.push_back(ps);
-    P.cost += 2.0 * static_cast<double>(1u << nint);
   }
   take_segment();
   }
@@ -461,6 +506,8 @@ struct tqs_circuit {
   // cached plain-form step table
   bool steps_valid = false;
   std::vector<StepFactor> factors;
+  std::vector<int64_t> factor_coef;  // per factor: offset in coef_pool, -1 if none
+  std::vector<float2> coef_pool;     // custom factors' entries (row-major, FP32)
   std::vector<StepDesc> steps;
   DevBuf d_factors;
   DevBuf d_plain;     // S scratch + two state vectors
@@ -579,6 +626,81 @@ tqs_status tqs_add_gate(tqs_circuit* c, int gate, const int* qubits, int nq, con
   return TQS_OK;
 }
 
+}  // extern "C"
+
+// Process-wide registry of custom unitaries (the operation data provider of
+// Sec. 5.2): name -> matrix.  Circuits keep their own reference to the data
+// they were built with.
+static std::mutex g_registry_mu;
+static std::unordered_map<std::string, std::shared_ptr<const CustomMat>> g_registry;
+
+extern "C" {
+
+tqs_status tqs_register_unitary(const char* name, int k, const double* m) {
+  if (!name || !*name || !m) return fail(TQS_ERR_ARG, "tqs_register_unitary: NULL name or matrix");
+  if (k < 1 || k > kMaxCustomQubits)
+    return fail(TQS_ERR_ARG, "tqs_register_unitary: k %d outside [1, %d]", k, kMaxCustomQubits);
+  auto cm = std::make_shared<CustomMat>();
+  const int G = 1 << k;
+  cm->k = k;
+  cm->m.resize(size_t(G) * G);
+  for (size_t i = 0; i < cm->m.size(); ++i) {
+    if (!std::isfinite(m[2 * i]) || !std::isfinite(m[2 * i + 1]))
+      return fail(TQS_ERR_ARG, "tqs_register_unitary: non-finite entry");
+    cm->m[i] = cd(m[2 * i], m[2 * i + 1]);
+  }
+  // unitary to 1e-9: every entry of M^dagger M - I
+  for (int a = 0; a < G; ++a)
+    for (int b = 0; b < G; ++b) {
+      cd acc = 0.0;
+      for (int r = 0; r < G; ++r) acc += std::conj(cm->m[size_t(r) * G + a]) * cm->m[size_t(r) * G + b];
+      if (std::abs(acc - (a == b ? 1.0 : 0.0)) > 1e-9)
+        return fail(TQS_ERR_ARG, "tqs_register_unitary: '%s' is not unitary to 1e-9", name);
+    }
+  std::lock_guard<std::mutex> lock(g_registry_mu);
+  g_registry[name] = std::move(cm);
+  return TQS_OK;
+}
+
+tqs_status tqs_add_custom(tqs_circuit* c, const char* name, const int* qubits, int k) {
+  if (!c || !name || !qubits) return fail(TQS_ERR_ARG, "tqs_add_custom: NULL argument");
+  std::shared_ptr<const CustomMat> cm;
+  {
+    std::lock_guard<std::mutex> lock(g_registry_mu);
+    auto it = g_registry.find(name);
+    if (it == g_registry.end())
+      return fail(TQS_ERR_ARG, "tqs_add_custom: no unitary registered as '%s'", name);
+    cm = it->second;
+  }
+  if (k != cm->k)
+    return fail(TQS_ERR_ARG, "tqs_add_custom: '%s' acts on %d qubit(s), got %d", name, cm->k, k);
+  for (int i = 0; i < k; ++i) {
+    if (qubits[i] < 0 || qubits[i] >= c->n)
+      return fail(TQS_ERR_QUBIT_RANGE, "qubit %d outside [0, %d)", qubits[i], c->n);
+    for (int j = 0; j < i; ++j)
+      if (qubits[j] == qubits[i])
+        return fail(TQS_ERR_QUBIT_DUP, "tqs_add_custom: qubit %d twice", qubits[i]);
+  }
+  Gate g{};
+  g.kind = kCustomKind;
+  g.nq = k;
+  for (int i = 0; i < k; ++i) g.q[i] = qubits[i];
+  for (int i = k; i < kMaxCustomQubits; ++i) g.q[i] = qubits[0];
+  if (k == 1) {
+    for (int i = 0; i < 4; ++i) g.u.m[i] = cm->m[i];  // a dense single-qubit factor
+  } else {
+    g.u = Mat2{{1.0, 0.0, 0.0, 1.0}};
+    g.cm = cm;
+  }
+  assign_step(c->last, g);
+  c->nsteps = std::max(c->nsteps, g.step + 1);
+  c->gates.push_back(g);
+  c->prog_valid = false;
+  c->prog_init_valid = false;
+  c->steps_valid = false;
+  return TQS_OK;
+}
+
 tqs_status tqs_circuit_info(const tqs_circuit* c, int* n_qubits, int* n_gates, int* n_steps) {
   if (!c) return fail(TQS_ERR_ARG, "tqs_circuit_info: circuit is NULL");
   if (n_qubits) *n_qubits = c->n;
@@ -638,19 +760,37 @@ extern "C" tqs_status tqs_circuit_program(tqs_circuit* c, int* n_passes, int* n_
 }
 
 
-// Device image of one or more programs: [FusedCirc x count][FusedPass...][FusedOp...]
+// Device image of one or more programs:
+// [FusedCirc x count][FusedPass...][FusedOp...][custom coefficients (float2)...]
 struct Image {
   std::vector<FusedCirc> circs;
   std::vector<FusedPass> passes;
   std::vector<FusedOp> ops;
+  std::vector<float2> coef;
   size_t circ_bytes() const { return circs.size() * sizeof(FusedCirc); }
   size_t pass_bytes() const { return passes.size() * sizeof(FusedPass); }
   size_t op_bytes() const { return ops.size() * sizeof(FusedOp); }
-  size_t bytes() const { return circ_bytes() + pass_bytes() + op_bytes(); }
+  size_t coef_bytes() const { return coef.size() * sizeof(float2); }
+  size_t coef_at() const { return circ_bytes() + pass_bytes() + op_bytes(); }
+  size_t bytes() const { return coef_at() + coef_bytes(); }
+  // Device pointers of the parts of an image uploaded at `base`.
+  void point(FusedLaunch& L, const char* base) const {
+    L.circs = reinterpret_cast<const FusedCirc*>(base);
+    L.passes = reinterpret_cast<const FusedPass*>(base + circ_bytes());
+    L.ops = reinterpret_cast<const FusedOp*>(base + circ_bytes() + pass_bytes());
+    L.coef = reinterpret_cast<const float2*>(base + coef_at());
+  }
+  // Pass record with its op / instruction / coefficient offset rebased.
+  static FusedPass rebase(FusedPass ps, int64_t op0, int64_t instr0, int64_t coef0) {
+    if (ps.L[0] == kInstrPass) ps.op_begin += static_cast<uint32_t>(instr0);
+    else if (ps.L[0] == kWidePass) ps.op_begin += static_cast<uint32_t>(coef0);
+    else ps.op_begin += static_cast<uint32_t>(op0);
+    return ps;
+  }
   // Write program P as circuit i whose passes start at pass0 and ops at op0
   // (the arrays are sized by the caller).
   void fill(int i, const Program& P, int64_t out_off, int64_t pass0, int64_t op0,
-            int64_t instr0 = 0) {
+            int64_t instr0 = 0, int64_t coef0 = 0) {
     FusedCirc fc{};
     fc.n = P.n;
     fc.nint = P.nint;
@@ -664,13 +804,12 @@ struct Image {
     fc.out_scale = P.out_scale;
     fc.gen_index = P.gen_index;
     circs[i] = fc;
-    for (size_t k = 0; k < P.passes.size(); ++k) {
-      FusedPass ps = P.passes[k];
-      ps.op_begin += static_cast<uint32_t>(ps.L[0] == kInstrPass ? instr0 : op0);
-      passes[static_cast<size_t>(pass0) + k] = ps;
-    }
+    for (size_t k = 0; k < P.passes.size(); ++k)
+      passes[static_cast<size_t>(pass0) + k] = rebase(P.passes[k], op0, instr0, coef0);
     if (!P.ops.empty())
       std::memcpy(&ops[static_cast<size_t>(op0)], P.ops.data(), P.ops.size() * sizeof(FusedOp));
+    if (!P.coef.empty())
+      std::memcpy(&coef[static_cast<size_t>(coef0)], P.coef.data(), P.coef.size() * sizeof(float2));
   }
   void add(const Program& P, int64_t out_off) {
     FusedCirc fc{};
@@ -685,12 +824,11 @@ struct Image {
     fc.init = nullptr;
     fc.out_scale = P.out_scale;
     fc.gen_index = P.gen_index;
-    const uint32_t op_base = static_cast<uint32_t>(ops.size());
-    for (FusedPass ps : P.passes) {
-      if (ps.L[0] != kInstrPass) ps.op_begin += op_base;
-      passes.push_back(ps);
-    }
+    const int64_t op_base = static_cast<int64_t>(ops.size());
+    const int64_t coef_base = static_cast<int64_t>(coef.size());
+    for (const FusedPass& ps : P.passes) passes.push_back(rebase(ps, op_base, 0, coef_base));
     ops.insert(ops.end(), P.ops.begin(), P.ops.end());
+    coef.insert(coef.end(), P.coef.begin(), P.coef.end());
     circs.push_back(fc);
   }
   cudaError_t upload(void* dst, cudaStream_t s) const {
@@ -703,6 +841,9 @@ struct Image {
     if (!ops.empty())
       e = cudaMemcpyAsync(d + circ_bytes() + pass_bytes(), ops.data(), op_bytes(),
                           cudaMemcpyHostToDevice, s);
+    if (e != cudaSuccess) return e;
+    if (!coef.empty())
+      e = cudaMemcpyAsync(d + coef_at(), coef.data(), coef_bytes(), cudaMemcpyHostToDevice, s);
     return e;
   }
 };
@@ -768,9 +909,7 @@ static tqs_status simulate_impl(tqs_circuit* c, const tqs_c64* d_init, tqs_c64* 
            "tqs_simulate: upload order");
   TQS_CUDA(cudaMemsetAsync(c->d_counter.p, 0, sizeof(int32_t), s), "tqs_simulate: memset");
   FusedLaunch L{};
-  L.circs = reinterpret_cast<const FusedCirc*>(base);
-  L.passes = reinterpret_cast<const FusedPass*>(base + img.circ_bytes());
-  L.ops = reinterpret_cast<const FusedOp*>(base + img.circ_bytes() + img.pass_bytes());
+  img.point(L, base);
   L.order = reinterpret_cast<const int32_t*>(base + order_off);
   L.n_jobs = 1;
   L.counter = c->d_counter.as<int32_t>();
@@ -816,6 +955,8 @@ tqs_status tqs_simulate_measured(tqs_circuit* c, const tqs_c64* d_init, tqs_c64*
 static void ensure_steps(tqs_circuit* c) {
   if (c->steps_valid) return;
   c->factors.clear();
+  c->factor_coef.clear();
+  c->coef_pool.clear();
   c->steps.assign(c->nsteps, StepDesc{0, 0, 0, 0});
   const uint32_t all = (1u << c->n) - 1u;
   std::vector<std::vector<const Gate*>> by_step(c->nsteps);
@@ -824,7 +965,15 @@ static void ensure_steps(tqs_circuit* c) {
     StepDesc d{static_cast<int32_t>(c->factors.size()), 0, all, 0};
     for (const Gate* g : by_step[k]) {
       StepFactor f{};
-      if (!is_two_qubit(g->kind)) {
+      int64_t coef_at = -1;
+      if (is_wide(*g)) {
+        f.nq = static_cast<uint8_t>(g->nq);
+        f.custom = 1;
+        for (int t = 0; t < g->nq; ++t) f.qc[t] = static_cast<uint8_t>(g->q[t]);
+        coef_at = static_cast<int64_t>(c->coef_pool.size());
+        for (const cd& v : g->cm->m) c->coef_pool.push_back(to_f2(v));
+        d.idle &= ~qubit_mask(*g);
+      } else if (!is_two_qubit(g->kind)) {
         f.nq = 1;
         f.q0 = f.q1 = static_cast<uint8_t>(g->q[0]);
         for (int i = 0; i < 4; ++i) f.m[i] = to_f2(g->u.m[i]);
@@ -853,6 +1002,7 @@ static void ensure_steps(tqs_circuit* c) {
         d.idle &= ~((1u << g->q[0]) | (1u << g->q[1]));
       }
       c->factors.push_back(f);
+      c->factor_coef.push_back(coef_at);
       ++d.f_count;
     }
     c->steps[k] = d;
@@ -860,14 +1010,25 @@ static void ensure_steps(tqs_circuit* c) {
   c->steps_valid = true;
 }
 
+// Device step table: [StepFactor...][custom entries (float2)...]; each custom
+// factor's `coef` points into the second part.
 static tqs_status upload_factors(tqs_circuit* c, cudaStream_t s) {
   ensure_steps(c);
-  const size_t bytes = std::max<size_t>(c->factors.size(), 1) * sizeof(StepFactor);
+  const size_t fbytes = (std::max<size_t>(c->factors.size(), 1) * sizeof(StepFactor) + 15) & ~size_t(15);
+  const size_t bytes = fbytes + c->coef_pool.size() * sizeof(float2);
   TQS_CUDA(c->d_factors.ensure(bytes), "cudaMalloc step table");
-  if (!c->factors.empty())
-    TQS_CUDA(cudaMemcpyAsync(c->d_factors.p, c->factors.data(), c->factors.size() * sizeof(StepFactor),
+  const float2* pool = reinterpret_cast<const float2*>(c->d_factors.as<char>() + fbytes);
+  std::vector<StepFactor> fs = c->factors;
+  for (size_t i = 0; i < fs.size(); ++i)
+    if (c->factor_coef[i] >= 0) fs[i].coef = pool + c->factor_coef[i];
+  if (!fs.empty())
+    TQS_CUDA(cudaMemcpyAsync(c->d_factors.p, fs.data(), fs.size() * sizeof(StepFactor),
                              cudaMemcpyHostToDevice, s),
              "upload step table");
+  if (!c->coef_pool.empty())
+    TQS_CUDA(cudaMemcpyAsync(c->d_factors.as<char>() + fbytes, c->coef_pool.data(),
+                             c->coef_pool.size() * sizeof(float2), cudaMemcpyHostToDevice, s),
+             "upload custom entries");
   return TQS_OK;
 }
 
@@ -1084,21 +1245,24 @@ static void parallel_for(int count, int grain, F body) {
 static tqs_status batch_finish(tqs_batch* b, std::vector<Program>& progs) {
   b->count = static_cast<int>(progs.size());
   b->offsets.assign(b->count + 1, 0);
-  std::vector<int64_t> pass0(b->count + 1, 0), op0(b->count + 1, 0);
+  std::vector<int64_t> pass0(b->count + 1, 0), op0(b->count + 1, 0), coef0(b->count + 1, 0);
   b->instr_off.assign(b->count + 1, 0);
   for (int i = 0; i < b->count; ++i) {
     b->offsets[i + 1] = b->offsets[i] + (int64_t(1) << progs[i].n);
     b->instr_off[i + 1] = b->instr_off[i] + progs[i].n_instr;
     pass0[i + 1] = pass0[i] + static_cast<int64_t>(progs[i].passes.size());
     op0[i + 1] = op0[i] + static_cast<int64_t>(progs[i].ops.size());
+    coef0[i + 1] = coef0[i] + static_cast<int64_t>(progs[i].coef.size());
   }
+  if (b->instr_off.back() > 0xFFFFFFFFll || op0.back() > 0xFFFFFFFFll || coef0.back() > 0xFFFFFFFFll)
+    return fail(TQS_ERR_ARG, "tqs_batch: program too large for 32-bit offsets");
   // the image, filled in parallel from the prefix sums
   b->img.circs.resize(b->count);
   b->img.passes.resize(static_cast<size_t>(pass0.back()));
   b->img.ops.resize(static_cast<size_t>(op0.back()));
-  if (b->instr_off.back() > 0xFFFFFFFFll) return fail(TQS_ERR_ARG, "tqs_batch: too many instructions");
+  b->img.coef.resize(static_cast<size_t>(coef0.back()));
   parallel_for(b->count, 256, [&](int i) {
-    b->img.fill(i, progs[i], b->offsets[i], pass0[i], op0[i], b->instr_off[i]);
+    b->img.fill(i, progs[i], b->offsets[i], pass0[i], op0[i], b->instr_off[i], coef0[i]);
   });
   std::vector<int> idx[3];
   for (int i = 0; i < b->count; ++i) {
@@ -1251,9 +1415,7 @@ static tqs_status batch_enqueue_at(tqs_batch* b, char* base, size_t order_off, s
   for (int t = 0; t < 3; ++t) {
     if (b->n_team[t] == 0) continue;
     FusedLaunch L{};
-    L.circs = reinterpret_cast<const FusedCirc*>(base);
-    L.passes = reinterpret_cast<const FusedPass*>(base + b->img.circ_bytes());
-    L.ops = reinterpret_cast<const FusedOp*>(base + b->img.circ_bytes() + b->img.pass_bytes());
+    b->img.point(L, base);
     L.order = reinterpret_cast<const int32_t*>(base + order_off) + first;
     L.n_jobs = b->n_team[t];
     L.counter = counters + t;
@@ -1610,9 +1772,7 @@ static tqs_status server_launch(tqs_server* sv, SrvSlot& sl) {
   for (int t = 0; t < 3; ++t) {
     if (n_team[t] == 0) continue;
     FusedLaunch L{};
-    L.circs = reinterpret_cast<const FusedCirc*>(base);
-    L.passes = reinterpret_cast<const FusedPass*>(base + img.circ_bytes());
-    L.ops = reinterpret_cast<const FusedOp*>(base + img.circ_bytes() + img.pass_bytes());
+    img.point(L, base);
     L.order = reinterpret_cast<const int32_t*>(base + order_off) + first;
     L.n_jobs = n_team[t];
     L.counter = counters + t;

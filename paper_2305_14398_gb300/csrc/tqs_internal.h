@@ -76,6 +76,14 @@ struct alignas(16) FusedPass {
 // its uniform and outcome (instruction ordinal plus the circuit's offset in
 // the batch), op_count = 0.
 constexpr uint8_t kInstrPass = 0xFF;
+// A custom k-qubit unitary (2 <= k <= 5) is a pass of its own, marked
+// L[0] = kWidePass: L[1] = k, op_begin = offset of its coefficients in the
+// coefficient array (2^k x 2^k FP32 hi parts then lo parts, both stored
+// transposed: entry (r, c) at c * 2^k + r), op_count = the physical bit of
+// matrix index bit t in bits 5t..5t+4, and the scale word holds (as a uint32)
+// the mask of those k physical bits.
+constexpr uint8_t kWidePass = 0xFE;
+constexpr int kMaxCustomQubits = 5;
 static_assert(sizeof(FusedPass) == 16, "FusedPass layout");
 
 enum TeamKind : int32_t { TEAM_WARP = 0, TEAM_CTA = 1, TEAM_GLOBAL = 2 };
@@ -115,6 +123,7 @@ struct FusedLaunch {
   double* probs;            // nullable
   double* norms;            // nullable
   float2* gscratch;         // TEAM_GLOBAL: per-CTA state slots (2^16 amplitudes each)
+  const float2* coef;       // custom unitaries: coefficient array (nullable without them)
   const double* uniforms;   // instructions: one uniform each (nullable without instructions)
   int32_t* outcomes;        // instructions: one outcome each (nullable)
   int32_t team;             // TeamKind of this launch
@@ -131,13 +140,16 @@ int fused_max_ctas_per_sm(int team, int warps_per_cta, int slice_q);
 // ---------------------------------------------------------------------------
 
 struct StepFactor {
-  uint8_t nq;      // 1 or 2
-  uint8_t q0, q1;  // qubits (q0 = control for controlled gates)
-  uint8_t pad[5];
+  uint8_t nq;      // 1 or 2 for built-in gates; k for a custom factor
+  uint8_t q0, q1;  // built-in: qubits (q0 = control for controlled gates)
+  uint8_t custom;  // 1: custom k-qubit factor, entries at `coef`
+  uint8_t qc[kMaxCustomQubits];  // custom: qubit of local index bit t
+  uint8_t pad[7];
+  const float2* coef;  // custom: 2^k x 2^k entries, row-major (device memory)
   float2 m[16];    // nq = 1: 2x2 row-major in m[0..3]; nq = 2: 4x4 row-major,
                    // local index (bit q0 << 1) | bit q1
 };
-static_assert(sizeof(StepFactor) == 136, "StepFactor layout");
+static_assert(sizeof(StepFactor) == 152, "StepFactor layout");
 
 struct StepDesc {
   int32_t f_begin;   // index into the factor array

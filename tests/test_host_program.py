@@ -24,13 +24,29 @@ def ins0(x, b):
     return ((x >> b) << (b + 1)) | (x & ((1 << b) - 1))
 
 
-def replay(n, passes, ops, pos, out_scale=1.0, gen_index=0, uniforms=None, outcomes=None):
+def replay(n, passes, ops, pos, out_scale=1.0, gen_index=0, uniforms=None, outcomes=None,
+           customs=()):
     nint = max(n, 4)
     st = np.zeros(1 << nint, dtype=np.complex128)
     st[gen_index] = 1.0
     G = (1 << nint) >> 4
+    customs = list(customs)
     for pi, ps in enumerate(passes):
         L = [int(v) for v in ps["L"]]
+        if L[0] == 254:  # custom k-qubit unitary: the next custom matrix, on the
+            k = L[1]     # physical bits packed 5 bits each in op_count
+            assert pi > 0 and 2 <= k <= 5
+            m = customs.pop(0)
+            assert m.shape == (1 << k, 1 << k)
+            bits = [(int(ps["op_count"]) >> (5 * t)) & 31 for t in range(k)]
+            mask = int(np.asarray(ps["scale"], dtype=np.float32).view(np.uint32))
+            assert mask == sum(1 << b for b in bits) and len(set(bits)) == k and max(bits) < nint
+            idx = np.arange(1 << nint)
+            base = idx[(idx & mask) == 0]
+            loc = np.array([sum(((j >> t) & 1) << bits[t] for t in range(k)) for j in range(1 << k)])
+            grp = base[:, None] + loc[None, :]
+            st[grp] = st[grp] @ m.T
+            continue
         if L[0] == 255:  # measure / reset instruction on physical bit L[1]
             assert pi > 0 and int(ps["op_count"]) == 0
             idx = np.arange(1 << nint)
@@ -373,3 +389,69 @@ def test_unitary_forms_reject_instructions():
         assert e.value.name == "TQS_ERR_UNSUPPORTED"
     finally:
         B.tqs_server_destroy(sv)
+
+
+# ------------------------------------------------------------ custom unitaries
+
+def rand_unitary(k, seed):
+    rng = np.random.default_rng(seed)
+    a = rng.normal(size=(1 << k, 1 << k)) + 1j * rng.normal(size=(1 << k, 1 << k))
+    q, r = np.linalg.qr(a)
+    return q * (np.diag(r) / np.abs(np.diag(r)))
+
+
+def with_customs(n, seed):
+    """Random circuit with custom unitaries of k = 1..min(5, n) spliced in,
+    one of them after a SWAP (so its qubits are relabelled)."""
+    from oracle import gates as G
+    rng = np.random.default_rng(seed)
+    ops = list(W.random_small(n, 4 * n, (12, n, seed)))
+    mats = []
+    for j, k in enumerate(range(1, min(5, n) + 1)):
+        qs = tuple(int(q) for q in rng.permutation(n)[:k])
+        m = rand_unitary(k, 10 * seed + k)
+        at = int(rng.integers(0, len(ops) + 1))
+        ins = [("unitary", qs, G.custom_params(m))]
+        if j == 1 and n >= 2:
+            ins = [("swap", (qs[0], (qs[0] + 1) % n), ())] + ins
+        ops[at:at] = ins
+        if k >= 2:
+            mats.append((at, m))
+    # wide customs appear in the program in circuit order
+    order = [op for op in ops if op[0] == "unitary" and len(op[1]) >= 2]
+    return ops, [G.custom_matrix(op[1], op[2]) for op in order]
+
+
+@pytest.mark.parametrize("n,seed", [(n, s) for n in (2, 3, 5, 7, 11) for s in range(2)])
+def test_program_replay_with_customs_matches_oracle(n, seed):
+    ops, mats = with_customs(n, 40 * n + seed)
+    passes, prog_ops, pos, osc, gen = compiled(n, ops)
+    assert sum(1 for p in passes if int(p["L"][0]) == 254) == len(mats)
+    got = replay(n, passes, prog_ops, pos, osc, gen, customs=mats)
+    want = fsv_route.simulate(n, ops)
+    assert np.max(np.abs(got - want)) < 2e-6
+
+
+def test_custom_registry_errors():
+    m = rand_unitary(2, 1)
+    B.tqs_register_unitary("reg_test_u2", m)
+    c = B.tqs_circuit_create(4)
+    try:
+        B.tqs_add_custom(c, "reg_test_u2", (3, 1))
+        for args, status in [(("no_such_name", (0, 1)), "TQS_ERR_ARG"),
+                             (("reg_test_u2", (0, 1, 2)), "TQS_ERR_ARG"),
+                             (("reg_test_u2", (0, 4)), "TQS_ERR_QUBIT_RANGE"),
+                             (("reg_test_u2", (2, 2)), "TQS_ERR_QUBIT_DUP")]:
+            with pytest.raises(B.TqsError) as e:
+                B.tqs_add_custom(c, *args)
+            assert e.value.name == status
+        assert B.tqs_circuit_info(c)[1] == 1
+    finally:
+        B.tqs_circuit_destroy(c)
+    bad = m.copy()
+    bad[0, 0] += 1e-6
+    with pytest.raises(B.TqsError) as e:
+        B.tqs_register_unitary("reg_test_bad", bad)
+    assert e.value.name == "TQS_ERR_ARG"
+    with pytest.raises(B.TqsError):
+        B.tqs_register_unitary("reg_test_big", np.eye(64))
