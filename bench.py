@@ -57,6 +57,7 @@ def parse_args():
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--no-sample", action="store_true")
+    ap.add_argument("--no-fsv", action="store_true")
     return ap.parse_args()
 
 
@@ -398,6 +399,10 @@ def run_tqs(args):
         sm_mhz = line["clocks"].get("sm_mhz") or 2070.0
         line["batch"] = bench_batch(B, W, torch, peaks, flush, max(3, min(args.steps, 10)), sm_mhz)
 
+    # ------------------------------------------ full state vector (large n)
+    if not args.no_fsv and rank == 0:
+        line["fsv"] = bench_fsv(B, W, torch, hbm_peak, line["clocks"].get("sm_mhz") or 2070.0)
+
     # ------------------------------------------- circuit-unitary chain (a5)
     if not args.no_chain and rank == 0:
         line["chain"] = bench_chain(B, W, torch, peaks)
@@ -528,6 +533,43 @@ def bench_batch(B, W, torch, peaks, flush, reps, sm_mhz):
         }
         B.tqs_batch_destroy(b)
         del states, probs, norms
+        torch.cuda.empty_cache()
+    return out
+
+
+def bench_fsv(B, W, torch, hbm_peak, sm_mhz):
+    """Full-state-vector backend on states in HBM: random layered circuits
+    (10 x (U3 on every qubit + CNOTs on n/2 seeded pairs)) at n = 24, 28, 30.
+    Each pass streams the state once (read + write): 16 * 2^n algorithmic
+    bytes per pass; the ALU fraction counts the algorithmic FP32 flops of the
+    per-gate update (eq. 12)."""
+    out = {"workload": "random layered: 10 x (U3 on every qubit + CNOTs on n/2 seeded pairs)"}
+    for n, reps in ((24, 5), (28, 3), (30, 2)):
+        ops = W.random_layered(n, 10, (9, n))
+        c = B.circuit_from_ops(n, ops)
+        st = torch.zeros(1 << n, dtype=torch.complex64, device="cuda")
+        st[0] = 1.0
+        passes, tile = B.tqs_fsv_passes(c)
+        B.tqs_simulate_fsv(c, st)  # compile + upload, warm
+        torch.cuda.synchronize()
+        s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        s.record()
+        for _ in range(reps):
+            B.tqs_simulate_fsv(c, st)
+        e.record()
+        torch.cuda.synchronize()
+        sec = s.elapsed_time(e) / 1e3 / reps
+        alg = 16.0 * (1 << n) * passes
+        flops = algorithmic_flops(n, ops)
+        out[f"n{n}"] = {"gates": len(ops), "passes": passes, "tile_bits": tile, "ms": 1e3 * sec,
+                        "gates_per_s": len(ops) / sec,
+                        "hbm": {"achieved_gbs": alg / sec / 1e9, "peak": hbm_peak,
+                                "frac": alg / sec / 1e9 / hbm_peak, "algorithmic_bytes": alg},
+                        "alu": {"achieved_tflops": flops / sec / 1e12, "peak": fp32_peak_tflops(sm_mhz),
+                                "frac": flops / sec / 1e12 / fp32_peak_tflops(sm_mhz),
+                                "algorithmic_flops": flops}}
+        B.tqs_circuit_destroy(c)
+        del st
         torch.cuda.empty_cache()
     return out
 

@@ -98,7 +98,8 @@ typedef enum {
   TQS_PREC_TC_TF32X3 = 2    /* as above with TF32 hi/lo splits (kind::tf32) */
 } tqs_prec;
 
-#define TQS_MAX_QUBITS 16          /* state-vector calls */
+#define TQS_MAX_QUBITS 16          /* fused state-vector calls, batches, server */
+#define TQS_MAX_FSV_QUBITS 34      /* circuits; tqs_simulate_fsv (2^34 x 8 B = 128 GiB) */
 #define TQS_MAX_DENSE_QUBITS 14    /* calls that hold a 2^n x 2^n matrix */
 
 /* ------------------------------------------------------------------ circuit
@@ -107,8 +108,10 @@ typedef enum {
  * are created as operations are added ("as soon as possible": an operation
  * joins the step after the last step that touches one of its qubits). */
 
-/* Create an empty circuit of 1 <= n_qubits <= TQS_MAX_QUBITS qubits.
- * *out receives the handle (owned by the caller until tqs_circuit_destroy). */
+/* Create an empty circuit of 1 <= n_qubits <= TQS_MAX_FSV_QUBITS qubits.
+ * *out receives the handle (owned by the caller until tqs_circuit_destroy).
+ * Calls other than tqs_simulate_fsv need n <= TQS_MAX_QUBITS (the dense-matrix
+ * forms n <= TQS_MAX_DENSE_QUBITS) and return TQS_ERR_TOO_MANY_QUBITS above. */
 tqs_status tqs_circuit_create(int n_qubits, tqs_circuit** out);
 
 /* Destroy a circuit and any device memory it caches.  NULL is accepted. */
@@ -219,6 +222,24 @@ tqs_status tqs_materialize_step(tqs_circuit* c, int step, tqs_c64* d_S, void* st
  * The tensor-core form synchronises `stream` before returning and returns
  * TQS_ERR_TIMEOUT if one of its bounded device waits ran out. */
 tqs_status tqs_circuit_unitary(tqs_circuit* c, int prec, tqs_c64* d_U, void* stream);
+
+/* ----------------------------------------------------- full state vector
+ * The per-gate state-vector update of Appendix A (eq. 12; the paper's future
+ * work) for states held in HBM, up to TQS_MAX_FSV_QUBITS qubits: d_state
+ * (2^n tqs_c64, in place, 16-byte aligned; the caller initialises it) goes
+ * through the circuit's gates in the order they were added.  Gates are
+ * grouped into passes; each pass is one launch that streams the state
+ * through shared memory in tiles of 2^12 amplitudes (the 5 lowest qubits plus
+ * up to 7 more that the pass's gates act on non-diagonally; controls and
+ * diagonal gates may sit on any qubit), so the state crosses HBM twice per
+ * pass.  Custom unitaries are supported; measure/reset instructions return
+ * TQS_ERR_UNSUPPORTED.  Scratch (cached on the circuit): the pass program.
+ * FP32 amplitudes, FP32 hi + lo coefficients. */
+tqs_status tqs_simulate_fsv(tqs_circuit* c, tqs_c64* d_state, void* stream);
+
+/* Pass count and tile bits of the circuit's full-state-vector program (host
+ * only; either output may be NULL). */
+tqs_status tqs_fsv_passes(tqs_circuit* c, int* n_passes, int* tile_bits);
 
 /* ---------------------------------------------------------- probabilities
  * p_i = |psi_i|^2 in FP64 (the products of the FP32 parts are exact in

@@ -61,6 +61,8 @@ _SIGS = {
                                  _pi]),
     "tqs_simulate": (_i, [_vp, _vp, _vp, _vp, _vp, _vp]),
     "tqs_simulate_plain": (_i, [_vp, _vp, _vp, _vp]),
+    "tqs_simulate_fsv": (_i, [_vp, _vp, _vp]),
+    "tqs_fsv_passes": (_i, [_vp, _pi, _pi]),
     "tqs_simulate_measured": (_i, [_vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp]),
     "tqs_materialize_step": (_i, [_vp, _i, _vp, _vp]),
     "tqs_circuit_unitary": (_i, [_vp, _i, _vp, _vp]),
@@ -249,6 +251,18 @@ def tqs_simulate_measured(c: int, out, u=None, outcomes=None, init=None, probs=N
     instruction), outcomes (int32, one per instruction)."""
     _check(lib().tqs_simulate_measured(c, _ptr(init), _ptr(out), _ptr(probs), _ptr(norm), _ptr(u),
                                        _ptr(outcomes), _stream(stream)))
+
+
+def tqs_simulate_fsv(c: int, state, stream=None) -> None:
+    """Full-state-vector backend: the circuit applied to `state` in place."""
+    _check(lib().tqs_simulate_fsv(c, _ptr(state), _stream(stream)))
+
+
+def tqs_fsv_passes(c: int) -> Tuple[int, int]:
+    """(passes, tile bits) of the circuit's full-state-vector program."""
+    p, t = ctypes.c_int(), ctypes.c_int()
+    _check(lib().tqs_fsv_passes(c, ctypes.byref(p), ctypes.byref(t)))
+    return p.value, t.value
 
 
 def tqs_simulate_plain(c: int, out, init=None, stream=None) -> None:

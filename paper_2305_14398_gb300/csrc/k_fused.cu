@@ -584,6 +584,89 @@ __global__ void __launch_bounds__(TEAM == TEAM_CTA ? kCtaThreads : 512)
   }
 }
 
+// ------------------------------------------------- full state vector tiles
+// One pass of the full-state-vector backend (Appendix A, eq. 12, on states in
+// HBM): the CTA streams the state through shared memory one tile at a time
+// (the 2^T amplitudes that agree outside the tile bits; the lowest bits are
+// tile bits, so loads and stores move 256-byte runs), runs the pass's tile
+// program on it exactly like a fused program on a CTA team (4-bit register
+// passes, wide passes for custom unitaries), and writes it back through the
+// program's final qubit map.  Far controls and far diagonal bits of the
+// program are virtual qubits T, T+1, ... whose values, fixed per tile, are
+// or-ed into each group's index.
+
+// The bits of v deposited, lowest first, at the set bits of mask.
+__device__ __forceinline__ uint64_t deposit64(uint64_t v, uint64_t mask) {
+  uint64_t r = 0;
+  for (; mask != 0; mask &= mask - 1, v >>= 1)
+    if (v & 1) r |= mask & (~mask + 1);
+  return r;
+}
+
+constexpr int kFsvHighQ = kFsvTileQ - kFsvLowQ;
+
+__global__ void __launch_bounds__(kFsvThreads)
+    fsv_tile_kernel(const __grid_constant__ FusedLaunch L, const __grid_constant__ FsvTile F) {
+  extern __shared__ float4 smem_raw[];
+  float2* st = reinterpret_cast<float2*>(smem_raw);
+  __shared__ uint64_t hoff[1 << kFsvHighQ];
+  const int tid = threadIdx.x;
+  const FusedCirc cd = L.circs[0];
+  const int T = F.T, NT = 1 << T, G = NT >> 4;
+  const int nlow = T < kFsvLowQ ? T : kFsvLowQ;
+  const int lowm = (1 << nlow) - 1;
+  const uint64_t high = F.mask & ~static_cast<uint64_t>(lowm);
+  for (int h = tid; h < (NT >> nlow); h += kFsvThreads) hoff[h] = deposit64(h, high);
+  const uint64_t all = (F.n >= 64) ? ~0ull : ((1ull << F.n) - 1);
+  const uint64_t comp = all & ~F.mask;
+  const uint64_t ntiles = 1ull << (F.n - T);
+  PosMap pw;
+  { const ulonglong2 pv = *reinterpret_cast<const ulonglong2*>(cd.pos); pw.lo = pv.x; pw.hi = pv.y; }
+  float2* g = F.state;
+  __syncthreads();
+  for (uint64_t j = blockIdx.x; j < ntiles; j += gridDim.x) {
+    const uint64_t gbase = deposit64(j, comp);
+    int ext = 0;
+    for (int v = 0; v < F.nfar; ++v) ext |= static_cast<int>((gbase >> F.far[v]) & 1) << (T + v);
+    for (int e = tid; e < NT; e += kFsvThreads)
+      st[swz(e)] = g[gbase + hoff[e >> nlow] + (e & lowm)];
+    __syncthreads();
+    for (int p = 0; p < cd.pass_count; ++p) {
+      const uint4 pr = __ldg(reinterpret_cast<const uint4*>(L.passes + cd.pass_begin + p));
+      const int l0 = pr.x & 0xff, l1 = (pr.x >> 8) & 0xff, l2 = (pr.x >> 16) & 0xff, l3 = pr.x >> 24;
+      if (l0 == kWidePass) {
+        wide_pass<TEAM_CTA>(L, T, l1, pr.y, pr.z, pr.w, st, tid, kFsvThreads);
+        continue;
+      }
+      const FusedOp* ops = L.ops + pr.y;
+      const uint32_t count = pr.z;
+      const float scale = __uint_as_float(pr.w);
+      const int w0 = swz(1 << l0), w1 = swz(1 << l1), w2 = swz(1 << l2), w3 = swz(1 << l3);
+      for (int gi = tid; gi < G; gi += kFsvThreads) {
+        const int base = ins0(ins0(ins0(ins0(gi, l0), l1), l2), l3);
+        const int sb = swz(base);
+        float2 a[16];
+#pragma unroll
+        for (int q = 0; q < 16; ++q)
+          a[q] = st[sb ^ ((q & 1) ? w0 : 0) ^ ((q & 2) ? w1 : 0) ^ ((q & 4) ? w2 : 0) ^ ((q & 8) ? w3 : 0)];
+        run_ops(a, ops, count, base | ext, scale);
+#pragma unroll
+        for (int q = 0; q < 16; ++q)
+          st[sb ^ ((q & 1) ? w0 : 0) ^ ((q & 2) ? w1 : 0) ^ ((q & 4) ? w2 : 0) ^ ((q & 8) ? w3 : 0)] = a[q];
+      }
+      __syncthreads();
+    }
+    // tile qubit i of the result sits at physical tile bit pos[i]
+    const float osc = cd.out_scale;
+    for (int e = tid; e < NT; e += kFsvThreads) {
+      float2 v = st[swz(cd.identity ? e : pfwd_of(e, pw, T))];
+      if (osc != 1.0f) v = make_float2(v.x * osc, v.y * osc);
+      g[gbase + hoff[e >> nlow] + (e & lowm)] = v;
+    }
+    __syncthreads();
+  }
+}
+
 size_t fused_smem_bytes(int team, int warps_per_cta, int slice_q) {
   if (team == TEAM_WARP) return (static_cast<size_t>(warps_per_cta) << slice_q) * sizeof(float2);
   if (team == TEAM_CTA) return (static_cast<size_t>(1) << slice_q) * sizeof(float2);
@@ -619,6 +702,28 @@ int fused_max_ctas_per_sm(int team, int warps_per_cta, int slice_q) {
   }
   if (e != cudaSuccess) return 0;
   return blocks;
+}
+
+cudaError_t launch_fsv_tile(const FusedLaunch& L, const FsvTile& F, cudaStream_t s) {
+  static int per_sm = 0, sms = 0;
+  const int smem_max = static_cast<int>((size_t(1) << kFsvTileQ) * sizeof(float2));
+  if (per_sm == 0) {
+    cudaError_t e = cudaFuncSetAttribute(fsv_tile_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         smem_max);
+    if (e != cudaSuccess) return e;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fsv_tile_kernel, kFsvThreads, smem_max);
+    if (per_sm < 1) per_sm = 1;
+  }
+  const uint64_t ntiles = 1ull << (F.n - F.T);
+  const uint64_t cap = static_cast<uint64_t>(per_sm) * static_cast<uint64_t>(sms > 0 ? sms : 152);
+  const int grid = static_cast<int>(ntiles < cap ? ntiles : cap);
+  const size_t smem = (size_t(1) << F.T) * sizeof(float2);
+  fsv_tile_kernel<<<grid, kFsvThreads, smem, s>>>(L, F);
+  count_launches(1);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_fused(const FusedLaunch& L, cudaStream_t s) {

@@ -219,6 +219,19 @@ struct Program {
   double cost = 0.0;
 };
 
+// Full-state-vector program: per pass the tile bits, the far bits it tests
+// and its tile program (FusedCirc k of `progs`, compiled by compile_program).
+struct FsvPassInfo {
+  uint64_t mask = 0;
+  int nfar = 0;
+  uint8_t far[kFsvMaxFar + 1] = {};
+};
+struct FsvProgram {
+  int T = 0;  // tile bits per pass
+  std::vector<FsvPassInfo> passes;
+  std::vector<Program> progs;  // one per pass
+};
+
 // At most this many unscaled Hadamard butterflies per pass (bounds the growth
 // of the unscaled amplitudes to 2^kMaxHPerPass before the pass rescale).
 constexpr int kMaxHPerPass = 48;
@@ -254,8 +267,8 @@ static void compile_program(int n, const std::vector<const Gate*>& gs_in, Progra
     }
   }
   const int nint = P.nint;
-  int phys[16];
-  for (int q = 0; q < 16; ++q) phys[q] = q;
+  int phys[32];
+  for (int q = 0; q < 32; ++q) phys[q] = q;
   const uint32_t all = (n >= 32) ? 0xffffffffu : ((1u << n) - 1u);
   std::vector<int> pending(gs.size()), still;
   std::iota(pending.begin(), pending.end(), 0);
@@ -267,7 +280,7 @@ static void compile_program(int n, const std::vector<const Gate*>& gs_in, Progra
     int t, c;     // physical bits (c = -1: uncontrolled)
   };
   std::vector<Raw> raw;
-  int last_touch[16];
+  int last_touch[32];
   int h_in_pass = 0;
   int h_carry = 0;  // Hadamard factors 2^-1/2 not yet applied
   auto push_raw = [&](const Gate& g, GClass cls, int t, int c) {
@@ -294,8 +307,8 @@ static void compile_program(int n, const std::vector<const Gate*>& gs_in, Progra
     for (int b = 0; nL < 4 && b < nint; ++b)  // padding: the lowest free bits
       if (!((Lmask >> b) & 1)) { Lmask |= 1u << b; ++nL; }
     FusedPass ps{};
-    int loc[16];
-    for (int b = 0; b < 16; ++b) loc[b] = -1;
+    int loc[32];
+    for (int b = 0; b < 32; ++b) loc[b] = -1;
     int k = 0;
     for (int b = 0; b < nint; ++b)
       if ((Lmask >> b) & 1) { ps.L[k] = static_cast<uint8_t>(b); loc[b] = k++; }
@@ -386,7 +399,7 @@ static void compile_program(int n, const std::vector<const Gate*>& gs_in, Progra
   while (!pending.empty()) {
     uint32_t Lmask = 0, blocked = 0;
     int nL = 0;
-    for (int b = 0; b < 16; ++b) last_touch[b] = -1;
+    for (int b = 0; b < 32; ++b) last_touch[b] = -1;
     still.clear();
     size_t idx = 0;
     for (; idx < pending.size(); ++idx) {
@@ -489,277 +502,6 @@ using namespace tqs;
 
 // ------------------------------------------------------------------ circuit
 
-struct tqs_circuit {
-  int n = 0;
-  int n_instr = 0;  // measure / reset instructions
-  std::vector<Gate> gates;
-  std::vector<int> last;  // last step touching each qubit
-  int nsteps = 0;
-  // cached fused program and its device copy
-  bool prog_valid = false;
-  Program prog;       // for the input |0...0> (leading X gates folded)
-  bool prog_init_valid = false;
-  Program prog_init;  // for a given input state (nothing folded)
-  DevBuf d_prog;      // FusedCirc + passes + ops
-  DevBuf d_counter;   // job counter
-  DevBuf d_gscratch;  // TEAM_GLOBAL slot
-  // cached plain-form step table
-  bool steps_valid = false;
-  std::vector<StepFactor> factors;
-  std::vector<int64_t> factor_coef;  // per factor: offset in coef_pool, -1 if none
-  std::vector<float2> coef_pool;     // custom factors' entries (row-major, FP32)
-  std::vector<StepDesc> steps;
-  DevBuf d_factors;
-  DevBuf d_plain;     // S scratch + two state vectors
-  DevBuf d_partials;  // probability partials
-  DevBuf d_collapse;  // simulateAndCollapse: state + probabilities
-  DevBuf d_sample;    // sampling scratch
-  // chain scratch
-  DevBuf d_chain;
-  DevBuf d_err;
-};
-
-extern "C" {
-
-const char* tqs_last_error(void) { return g_last_error.c_str(); }
-
-const char* tqs_status_string(int s) {
-  switch (s) {
-    case TQS_OK: return "TQS_OK";
-    case TQS_ERR_ARG: return "TQS_ERR_ARG";
-    case TQS_ERR_QUBIT_RANGE: return "TQS_ERR_QUBIT_RANGE";
-    case TQS_ERR_QUBIT_DUP: return "TQS_ERR_QUBIT_DUP";
-    case TQS_ERR_TOO_MANY_QUBITS: return "TQS_ERR_TOO_MANY_QUBITS";
-    case TQS_ERR_NOMEM: return "TQS_ERR_NOMEM";
-    case TQS_ERR_BUDGET: return "TQS_ERR_BUDGET";
-    case TQS_ERR_CUDA: return "TQS_ERR_CUDA";
-    case TQS_ERR_TIMEOUT: return "TQS_ERR_TIMEOUT";
-    case TQS_ERR_STATE: return "TQS_ERR_STATE";
-    case TQS_ERR_UNSUPPORTED: return "TQS_ERR_UNSUPPORTED";
-    default: return "TQS_ERR_UNKNOWN";
-  }
-}
-
-int64_t tqs_launch_count(void) { return g_launches.load(); }
-
-tqs_status tqs_circuit_create(int n_qubits, tqs_circuit** out) {
-  if (!out) return fail(TQS_ERR_ARG, "tqs_circuit_create: out is NULL");
-  *out = nullptr;
-  if (n_qubits < 1) return fail(TQS_ERR_ARG, "tqs_circuit_create: n_qubits must be >= 1");
-  if (n_qubits > TQS_MAX_QUBITS)
-    return fail(TQS_ERR_TOO_MANY_QUBITS, "tqs_circuit_create: n_qubits %d > %d", n_qubits,
-                TQS_MAX_QUBITS);
-  tqs_circuit* c = new (std::nothrow) tqs_circuit();
-  if (!c) return fail(TQS_ERR_NOMEM, "tqs_circuit_create: out of host memory");
-  c->n = n_qubits;
-  c->last.assign(n_qubits, -1);
-  *out = c;
-  return TQS_OK;
-}
-
-tqs_status tqs_circuit_destroy(tqs_circuit* c) {
-  delete c;
-  return TQS_OK;
-}
-
-static tqs_status check_gate(int n, int gate, const int* qubits, int nq, const double* params,
-                             int np, Gate& g) {
-  if (gate < 0 || gate >= TQS_GATE_COUNT) return fail(TQS_ERR_ARG, "unknown gate id %d", gate);
-  const int want = is_two_qubit(gate) ? 2 : 1;
-  if (!qubits || nq != want)
-    return fail(TQS_ERR_ARG, "gate %d takes %d qubit(s), got %d", gate, want, nq);
-  const int need = n_params(gate);
-  if (np < need || (need > 0 && !params))
-    return fail(TQS_ERR_ARG, "gate %d takes %d parameter(s), got %d", gate, need, np);
-  for (int i = 0; i < nq; ++i)
-    if (qubits[i] < 0 || qubits[i] >= n)
-      return fail(TQS_ERR_QUBIT_RANGE, "qubit %d outside [0, %d)", qubits[i], n);
-  if (nq == 2 && qubits[0] == qubits[1])
-    return fail(TQS_ERR_QUBIT_DUP, "gate %d uses qubit %d twice", gate, qubits[0]);
-  g.kind = gate;
-  g.nq = nq;
-  g.q[0] = qubits[0];
-  g.q[1] = nq == 2 ? qubits[1] : qubits[0];
-  for (int i = 0; i < 8; ++i) g.p[i] = (i < need) ? params[i] : 0.0;
-  for (int i = 0; i < need; ++i)
-    if (!std::isfinite(g.p[i])) return fail(TQS_ERR_ARG, "gate %d: non-finite parameter", gate);
-  g.u = gate_matrix(gate, g.p);
-  if (gate == TQS_CU && !is_unitary(g.u, 1e-9))
-    return fail(TQS_ERR_ARG, "CU matrix is not unitary to 1e-9");
-  return TQS_OK;
-}
-
-}  // extern "C"
-
-// ASAP step of the next operation (Sec. 5.2): after the last step touching any
-// of its qubits (`last`: per qubit, -1 if none).  An instruction is a barrier:
-// a step of its own after every earlier step, and every later operation comes
-// after it.
-static void assign_step(std::vector<int>& last, Gate& g) {
-  int step = 0;
-  if (is_instruction(g.kind)) {
-    for (int v : last) step = std::max(step, v + 1);
-    for (int& v : last) v = step;
-  } else {
-    for (int i = 0; i < g.nq; ++i) step = std::max(step, last[g.q[i]] + 1);
-    for (int i = 0; i < g.nq; ++i) last[g.q[i]] = step;
-  }
-  g.step = step;
-}
-
-extern "C" {
-
-tqs_status tqs_add_gate(tqs_circuit* c, int gate, const int* qubits, int nq, const double* params,
-                        int np) {
-  if (!c) return fail(TQS_ERR_ARG, "tqs_add_gate: circuit is NULL");
-  Gate g{};
-  tqs_status s = check_gate(c->n, gate, qubits, nq, params, np, g);
-  if (s != TQS_OK) return s;
-  assign_step(c->last, g);
-  if (is_instruction(gate)) ++c->n_instr;
-  const int step = g.step;
-  c->nsteps = std::max(c->nsteps, step + 1);
-  c->gates.push_back(g);
-  c->prog_valid = false;
-  c->prog_init_valid = false;
-  c->steps_valid = false;
-  return TQS_OK;
-}
-
-}  // extern "C"
-
-// Process-wide registry of custom unitaries (the operation data provider of
-// Sec. 5.2): name -> matrix.  Circuits keep their own reference to the data
-// they were built with.
-static std::mutex g_registry_mu;
-static std::unordered_map<std::string, std::shared_ptr<const CustomMat>> g_registry;
-
-extern "C" {
-
-tqs_status tqs_register_unitary(const char* name, int k, const double* m) {
-  if (!name || !*name || !m) return fail(TQS_ERR_ARG, "tqs_register_unitary: NULL name or matrix");
-  if (k < 1 || k > kMaxCustomQubits)
-    return fail(TQS_ERR_ARG, "tqs_register_unitary: k %d outside [1, %d]", k, kMaxCustomQubits);
-  auto cm = std::make_shared<CustomMat>();
-  const int G = 1 << k;
-  cm->k = k;
-  cm->m.resize(size_t(G) * G);
-  for (size_t i = 0; i < cm->m.size(); ++i) {
-    if (!std::isfinite(m[2 * i]) || !std::isfinite(m[2 * i + 1]))
-      return fail(TQS_ERR_ARG, "tqs_register_unitary: non-finite entry");
-    cm->m[i] = cd(m[2 * i], m[2 * i + 1]);
-  }
-  // unitary to 1e-9: every entry of M^dagger M - I
-  for (int a = 0; a < G; ++a)
-    for (int b = 0; b < G; ++b) {
-      cd acc = 0.0;
-      for (int r = 0; r < G; ++r) acc += std::conj(cm->m[size_t(r) * G + a]) * cm->m[size_t(r) * G + b];
-      if (std::abs(acc - (a == b ? 1.0 : 0.0)) > 1e-9)
-        return fail(TQS_ERR_ARG, "tqs_register_unitary: '%s' is not unitary to 1e-9", name);
-    }
-  std::lock_guard<std::mutex> lock(g_registry_mu);
-  g_registry[name] = std::move(cm);
-  return TQS_OK;
-}
-
-tqs_status tqs_add_custom(tqs_circuit* c, const char* name, const int* qubits, int k) {
-  if (!c || !name || !qubits) return fail(TQS_ERR_ARG, "tqs_add_custom: NULL argument");
-  std::shared_ptr<const CustomMat> cm;
-  {
-    std::lock_guard<std::mutex> lock(g_registry_mu);
-    auto it = g_registry.find(name);
-    if (it == g_registry.end())
-      return fail(TQS_ERR_ARG, "tqs_add_custom: no unitary registered as '%s'", name);
-    cm = it->second;
-  }
-  if (k != cm->k)
-    return fail(TQS_ERR_ARG, "tqs_add_custom: '%s' acts on %d qubit(s), got %d", name, cm->k, k);
-  for (int i = 0; i < k; ++i) {
-    if (qubits[i] < 0 || qubits[i] >= c->n)
-      return fail(TQS_ERR_QUBIT_RANGE, "qubit %d outside [0, %d)", qubits[i], c->n);
-    for (int j = 0; j < i; ++j)
-      if (qubits[j] == qubits[i])
-        return fail(TQS_ERR_QUBIT_DUP, "tqs_add_custom: qubit %d twice", qubits[i]);
-  }
-  Gate g{};
-  g.kind = kCustomKind;
-  g.nq = k;
-  for (int i = 0; i < k; ++i) g.q[i] = qubits[i];
-  for (int i = k; i < kMaxCustomQubits; ++i) g.q[i] = qubits[0];
-  if (k == 1) {
-    for (int i = 0; i < 4; ++i) g.u.m[i] = cm->m[i];  // a dense single-qubit factor
-  } else {
-    g.u = Mat2{{1.0, 0.0, 0.0, 1.0}};
-    g.cm = cm;
-  }
-  assign_step(c->last, g);
-  c->nsteps = std::max(c->nsteps, g.step + 1);
-  c->gates.push_back(g);
-  c->prog_valid = false;
-  c->prog_init_valid = false;
-  c->steps_valid = false;
-  return TQS_OK;
-}
-
-tqs_status tqs_circuit_info(const tqs_circuit* c, int* n_qubits, int* n_gates, int* n_steps) {
-  if (!c) return fail(TQS_ERR_ARG, "tqs_circuit_info: circuit is NULL");
-  if (n_qubits) *n_qubits = c->n;
-  if (n_gates) *n_gates = static_cast<int>(c->gates.size());
-  if (n_steps) *n_steps = c->nsteps;
-  return TQS_OK;
-}
-
-tqs_status tqs_circuit_steps(const tqs_circuit* c, int* h_step_of_gate) {
-  if (!c || !h_step_of_gate) return fail(TQS_ERR_ARG, "tqs_circuit_steps: NULL argument");
-  for (size_t i = 0; i < c->gates.size(); ++i) h_step_of_gate[i] = c->gates[i].step;
-  return TQS_OK;
-}
-
-}  // extern "C"
-
-// Gates in step order (stable within a step).
-static std::vector<const Gate*> step_order(const std::vector<Gate>& gates) {
-  std::vector<const Gate*> v;
-  v.reserve(gates.size());
-  for (const Gate& g : gates) v.push_back(&g);
-  std::stable_sort(v.begin(), v.end(), [](const Gate* a, const Gate* b) { return a->step < b->step; });
-  return v;
-}
-
-static const Program& ensure_program(tqs_circuit* c, bool with_init = false) {
-  if (with_init) {
-    if (!c->prog_init_valid) {
-      c->prog_init = Program();
-      compile_program(c->n, step_order(c->gates), c->prog_init, false);
-      c->prog_init_valid = true;
-    }
-    return c->prog_init;
-  }
-  if (!c->prog_valid) {
-    c->prog = Program();
-    compile_program(c->n, step_order(c->gates), c->prog);
-    c->prog_valid = true;
-  }
-  return c->prog;
-}
-
-static bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
-extern "C" tqs_status tqs_circuit_program(tqs_circuit* c, int* n_passes, int* n_ops, void* h_passes,
-                                          void* h_ops, uint8_t* h_pos, float* h_out_scale,
-                                          int* h_gen_index) {
-  if (!c) return fail(TQS_ERR_ARG, "tqs_circuit_program: circuit is NULL");
-  ensure_program(c);
-  if (h_gen_index) *h_gen_index = c->prog.gen_index;
-  if (n_passes) *n_passes = static_cast<int>(c->prog.passes.size());
-  if (n_ops) *n_ops = static_cast<int>(c->prog.ops.size());
-  if (h_passes) std::memcpy(h_passes, c->prog.passes.data(), c->prog.passes.size() * sizeof(FusedPass));
-  if (h_ops) std::memcpy(h_ops, c->prog.ops.data(), c->prog.ops.size() * sizeof(FusedOp));
-  if (h_pos) std::memcpy(h_pos, c->prog.pos, 16);
-  if (h_out_scale) *h_out_scale = c->prog.out_scale;
-  return TQS_OK;
-}
-
-
 // Device image of one or more programs:
 // [FusedCirc x count][FusedPass...][FusedOp...][custom coefficients (float2)...]
 struct Image {
@@ -848,6 +590,286 @@ struct Image {
   }
 };
 
+
+struct tqs_circuit {
+  int n = 0;
+  int n_instr = 0;  // measure / reset instructions
+  std::vector<Gate> gates;
+  std::vector<int> last;  // last step touching each qubit
+  int nsteps = 0;
+  // cached fused program and its device copy
+  bool prog_valid = false;
+  Program prog;       // for the input |0...0> (leading X gates folded)
+  bool prog_init_valid = false;
+  Program prog_init;  // for a given input state (nothing folded)
+  DevBuf d_prog;      // FusedCirc + passes + ops
+  DevBuf d_counter;   // job counter
+  DevBuf d_gscratch;  // TEAM_GLOBAL slot
+  // cached plain-form step table
+  bool steps_valid = false;
+  std::vector<StepFactor> factors;
+  std::vector<int64_t> factor_coef;  // per factor: offset in coef_pool, -1 if none
+  std::vector<float2> coef_pool;     // custom factors' entries (row-major, FP32)
+  std::vector<StepDesc> steps;
+  DevBuf d_factors;
+  DevBuf d_plain;     // S scratch + two state vectors
+  DevBuf d_partials;  // probability partials
+  DevBuf d_collapse;  // simulateAndCollapse: state + probabilities
+  bool fsv_valid = false;
+  FsvProgram fsv;     // full-state-vector passes
+  Image fsv_img;      // their tile programs
+  DevBuf d_fsv;       // device copy of fsv_img
+  DevBuf d_sample;    // sampling scratch
+  // chain scratch
+  DevBuf d_chain;
+  DevBuf d_err;
+};
+
+extern "C" {
+
+const char* tqs_last_error(void) { return g_last_error.c_str(); }
+
+const char* tqs_status_string(int s) {
+  switch (s) {
+    case TQS_OK: return "TQS_OK";
+    case TQS_ERR_ARG: return "TQS_ERR_ARG";
+    case TQS_ERR_QUBIT_RANGE: return "TQS_ERR_QUBIT_RANGE";
+    case TQS_ERR_QUBIT_DUP: return "TQS_ERR_QUBIT_DUP";
+    case TQS_ERR_TOO_MANY_QUBITS: return "TQS_ERR_TOO_MANY_QUBITS";
+    case TQS_ERR_NOMEM: return "TQS_ERR_NOMEM";
+    case TQS_ERR_BUDGET: return "TQS_ERR_BUDGET";
+    case TQS_ERR_CUDA: return "TQS_ERR_CUDA";
+    case TQS_ERR_TIMEOUT: return "TQS_ERR_TIMEOUT";
+    case TQS_ERR_STATE: return "TQS_ERR_STATE";
+    case TQS_ERR_UNSUPPORTED: return "TQS_ERR_UNSUPPORTED";
+    default: return "TQS_ERR_UNKNOWN";
+  }
+}
+
+int64_t tqs_launch_count(void) { return g_launches.load(); }
+
+tqs_status tqs_circuit_create(int n_qubits, tqs_circuit** out) {
+  if (!out) return fail(TQS_ERR_ARG, "tqs_circuit_create: out is NULL");
+  *out = nullptr;
+  if (n_qubits < 1) return fail(TQS_ERR_ARG, "tqs_circuit_create: n_qubits must be >= 1");
+  if (n_qubits > TQS_MAX_FSV_QUBITS)
+    return fail(TQS_ERR_TOO_MANY_QUBITS, "tqs_circuit_create: n_qubits %d > %d", n_qubits,
+                TQS_MAX_FSV_QUBITS);
+  tqs_circuit* c = new (std::nothrow) tqs_circuit();
+  if (!c) return fail(TQS_ERR_NOMEM, "tqs_circuit_create: out of host memory");
+  c->n = n_qubits;
+  c->last.assign(n_qubits, -1);
+  *out = c;
+  return TQS_OK;
+}
+
+tqs_status tqs_circuit_destroy(tqs_circuit* c) {
+  delete c;
+  return TQS_OK;
+}
+
+static tqs_status check_gate(int n, int gate, const int* qubits, int nq, const double* params,
+                             int np, Gate& g) {
+  if (gate < 0 || gate >= TQS_GATE_COUNT) return fail(TQS_ERR_ARG, "unknown gate id %d", gate);
+  const int want = is_two_qubit(gate) ? 2 : 1;
+  if (!qubits || nq != want)
+    return fail(TQS_ERR_ARG, "gate %d takes %d qubit(s), got %d", gate, want, nq);
+  const int need = n_params(gate);
+  if (np < need || (need > 0 && !params))
+    return fail(TQS_ERR_ARG, "gate %d takes %d parameter(s), got %d", gate, need, np);
+  for (int i = 0; i < nq; ++i)
+    if (qubits[i] < 0 || qubits[i] >= n)
+      return fail(TQS_ERR_QUBIT_RANGE, "qubit %d outside [0, %d)", qubits[i], n);
+  if (nq == 2 && qubits[0] == qubits[1])
+    return fail(TQS_ERR_QUBIT_DUP, "gate %d uses qubit %d twice", gate, qubits[0]);
+  g.kind = gate;
+  g.nq = nq;
+  g.q[0] = qubits[0];
+  g.q[1] = nq == 2 ? qubits[1] : qubits[0];
+  for (int i = 0; i < 8; ++i) g.p[i] = (i < need) ? params[i] : 0.0;
+  for (int i = 0; i < need; ++i)
+    if (!std::isfinite(g.p[i])) return fail(TQS_ERR_ARG, "gate %d: non-finite parameter", gate);
+  g.u = gate_matrix(gate, g.p);
+  if (gate == TQS_CU && !is_unitary(g.u, 1e-9))
+    return fail(TQS_ERR_ARG, "CU matrix is not unitary to 1e-9");
+  return TQS_OK;
+}
+
+}  // extern "C"
+
+// ASAP step of the next operation (Sec. 5.2): after the last step touching any
+// of its qubits (`last`: per qubit, -1 if none).  An instruction is a barrier:
+// a step of its own after every earlier step, and every later operation comes
+// after it.
+static void assign_step(std::vector<int>& last, Gate& g) {
+  int step = 0;
+  if (is_instruction(g.kind)) {
+    for (int v : last) step = std::max(step, v + 1);
+    for (int& v : last) v = step;
+  } else {
+    for (int i = 0; i < g.nq; ++i) step = std::max(step, last[g.q[i]] + 1);
+    for (int i = 0; i < g.nq; ++i) last[g.q[i]] = step;
+  }
+  g.step = step;
+}
+
+extern "C" {
+
+tqs_status tqs_add_gate(tqs_circuit* c, int gate, const int* qubits, int nq, const double* params,
+                        int np) {
+  if (!c) return fail(TQS_ERR_ARG, "tqs_add_gate: circuit is NULL");
+  Gate g{};
+  tqs_status s = check_gate(c->n, gate, qubits, nq, params, np, g);
+  if (s != TQS_OK) return s;
+  assign_step(c->last, g);
+  if (is_instruction(gate)) ++c->n_instr;
+  const int step = g.step;
+  c->nsteps = std::max(c->nsteps, step + 1);
+  c->gates.push_back(g);
+  c->prog_valid = false;
+  c->prog_init_valid = false;
+  c->steps_valid = false;
+  c->fsv_valid = false;
+  return TQS_OK;
+}
+
+}  // extern "C"
+
+// Process-wide registry of custom unitaries (the operation data provider of
+// Sec. 5.2): name -> matrix.  Circuits keep their own reference to the data
+// they were built with.
+static std::mutex g_registry_mu;
+static std::unordered_map<std::string, std::shared_ptr<const CustomMat>> g_registry;
+
+extern "C" {
+
+tqs_status tqs_register_unitary(const char* name, int k, const double* m) {
+  if (!name || !*name || !m) return fail(TQS_ERR_ARG, "tqs_register_unitary: NULL name or matrix");
+  if (k < 1 || k > kMaxCustomQubits)
+    return fail(TQS_ERR_ARG, "tqs_register_unitary: k %d outside [1, %d]", k, kMaxCustomQubits);
+  auto cm = std::make_shared<CustomMat>();
+  const int G = 1 << k;
+  cm->k = k;
+  cm->m.resize(size_t(G) * G);
+  for (size_t i = 0; i < cm->m.size(); ++i) {
+    if (!std::isfinite(m[2 * i]) || !std::isfinite(m[2 * i + 1]))
+      return fail(TQS_ERR_ARG, "tqs_register_unitary: non-finite entry");
+    cm->m[i] = cd(m[2 * i], m[2 * i + 1]);
+  }
+  // unitary to 1e-9: every entry of M^dagger M - I
+  for (int a = 0; a < G; ++a)
+    for (int b = 0; b < G; ++b) {
+      cd acc = 0.0;
+      for (int r = 0; r < G; ++r) acc += std::conj(cm->m[size_t(r) * G + a]) * cm->m[size_t(r) * G + b];
+      if (std::abs(acc - (a == b ? 1.0 : 0.0)) > 1e-9)
+        return fail(TQS_ERR_ARG, "tqs_register_unitary: '%s' is not unitary to 1e-9", name);
+    }
+  std::lock_guard<std::mutex> lock(g_registry_mu);
+  g_registry[name] = std::move(cm);
+  return TQS_OK;
+}
+
+tqs_status tqs_add_custom(tqs_circuit* c, const char* name, const int* qubits, int k) {
+  if (!c || !name || !qubits) return fail(TQS_ERR_ARG, "tqs_add_custom: NULL argument");
+  std::shared_ptr<const CustomMat> cm;
+  {
+    std::lock_guard<std::mutex> lock(g_registry_mu);
+    auto it = g_registry.find(name);
+    if (it == g_registry.end())
+      return fail(TQS_ERR_ARG, "tqs_add_custom: no unitary registered as '%s'", name);
+    cm = it->second;
+  }
+  if (k != cm->k)
+    return fail(TQS_ERR_ARG, "tqs_add_custom: '%s' acts on %d qubit(s), got %d", name, cm->k, k);
+  for (int i = 0; i < k; ++i) {
+    if (qubits[i] < 0 || qubits[i] >= c->n)
+      return fail(TQS_ERR_QUBIT_RANGE, "qubit %d outside [0, %d)", qubits[i], c->n);
+    for (int j = 0; j < i; ++j)
+      if (qubits[j] == qubits[i])
+        return fail(TQS_ERR_QUBIT_DUP, "tqs_add_custom: qubit %d twice", qubits[i]);
+  }
+  Gate g{};
+  g.kind = kCustomKind;
+  g.nq = k;
+  for (int i = 0; i < k; ++i) g.q[i] = qubits[i];
+  for (int i = k; i < kMaxCustomQubits; ++i) g.q[i] = qubits[0];
+  if (k == 1) {
+    for (int i = 0; i < 4; ++i) g.u.m[i] = cm->m[i];  // a dense single-qubit factor
+  } else {
+    g.u = Mat2{{1.0, 0.0, 0.0, 1.0}};
+    g.cm = cm;
+  }
+  assign_step(c->last, g);
+  c->nsteps = std::max(c->nsteps, g.step + 1);
+  c->gates.push_back(g);
+  c->prog_valid = false;
+  c->prog_init_valid = false;
+  c->steps_valid = false;
+  c->fsv_valid = false;
+  return TQS_OK;
+}
+
+tqs_status tqs_circuit_info(const tqs_circuit* c, int* n_qubits, int* n_gates, int* n_steps) {
+  if (!c) return fail(TQS_ERR_ARG, "tqs_circuit_info: circuit is NULL");
+  if (n_qubits) *n_qubits = c->n;
+  if (n_gates) *n_gates = static_cast<int>(c->gates.size());
+  if (n_steps) *n_steps = c->nsteps;
+  return TQS_OK;
+}
+
+tqs_status tqs_circuit_steps(const tqs_circuit* c, int* h_step_of_gate) {
+  if (!c || !h_step_of_gate) return fail(TQS_ERR_ARG, "tqs_circuit_steps: NULL argument");
+  for (size_t i = 0; i < c->gates.size(); ++i) h_step_of_gate[i] = c->gates[i].step;
+  return TQS_OK;
+}
+
+}  // extern "C"
+
+// Gates in step order (stable within a step).
+static std::vector<const Gate*> step_order(const std::vector<Gate>& gates) {
+  std::vector<const Gate*> v;
+  v.reserve(gates.size());
+  for (const Gate& g : gates) v.push_back(&g);
+  std::stable_sort(v.begin(), v.end(), [](const Gate* a, const Gate* b) { return a->step < b->step; });
+  return v;
+}
+
+static const Program& ensure_program(tqs_circuit* c, bool with_init = false) {
+  if (with_init) {
+    if (!c->prog_init_valid) {
+      c->prog_init = Program();
+      compile_program(c->n, step_order(c->gates), c->prog_init, false);
+      c->prog_init_valid = true;
+    }
+    return c->prog_init;
+  }
+  if (!c->prog_valid) {
+    c->prog = Program();
+    compile_program(c->n, step_order(c->gates), c->prog);
+    c->prog_valid = true;
+  }
+  return c->prog;
+}
+
+static bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
+extern "C" tqs_status tqs_circuit_program(tqs_circuit* c, int* n_passes, int* n_ops, void* h_passes,
+                                          void* h_ops, uint8_t* h_pos, float* h_out_scale,
+                                          int* h_gen_index) {
+  if (!c) return fail(TQS_ERR_ARG, "tqs_circuit_program: circuit is NULL");
+  if (c->n > TQS_MAX_QUBITS)
+    return fail(TQS_ERR_TOO_MANY_QUBITS, "tqs_circuit_program: n %d > %d", c->n, TQS_MAX_QUBITS);
+  ensure_program(c);
+  if (h_gen_index) *h_gen_index = c->prog.gen_index;
+  if (n_passes) *n_passes = static_cast<int>(c->prog.passes.size());
+  if (n_ops) *n_ops = static_cast<int>(c->prog.ops.size());
+  if (h_passes) std::memcpy(h_passes, c->prog.passes.data(), c->prog.passes.size() * sizeof(FusedPass));
+  if (h_ops) std::memcpy(h_ops, c->prog.ops.data(), c->prog.ops.size() * sizeof(FusedOp));
+  if (h_pos) std::memcpy(h_pos, c->prog.pos, 16);
+  if (h_out_scale) *h_out_scale = c->prog.out_scale;
+  return TQS_OK;
+}
+
+
 // Everything after the C-ABI entry points below shares these launch helpers.
 struct LaunchPlan {
   int team;
@@ -884,6 +906,9 @@ static LaunchPlan plan_for(int team, int max_nint, int jobs, int warps_hint) {
 static tqs_status simulate_impl(tqs_circuit* c, const tqs_c64* d_init, tqs_c64* d_out,
                                 double* d_probs, double* d_norm, const double* d_u,
                                 int32_t* d_outcomes, void* stream) {
+  if (c && c->n > TQS_MAX_QUBITS)
+    return fail(TQS_ERR_TOO_MANY_QUBITS, "tqs_simulate: n %d > %d (tqs_simulate_fsv takes up to %d)",
+                c->n, TQS_MAX_QUBITS, TQS_MAX_FSV_QUBITS);
   if (!c || !d_out) return fail(TQS_ERR_ARG, "tqs_simulate: NULL circuit or output");
   if (c->n_instr > 0 && !d_u)
     return fail(TQS_ERR_ARG, "tqs_simulate_measured: the circuit has %d instruction(s): d_u is NULL",
@@ -1289,6 +1314,9 @@ tqs_status tqs_batch_create(tqs_circuit* const* cs, int count, tqs_batch** out) 
   std::vector<Program> progs(count);
   for (int i = 0; i < count; ++i) {
     if (!cs[i]) return fail(TQS_ERR_ARG, "tqs_batch_create: circuit %d is NULL", i);
+    if (cs[i]->n > TQS_MAX_QUBITS)
+      return fail(TQS_ERR_TOO_MANY_QUBITS, "tqs_batch_create: circuit %d has n %d > %d", i,
+                  cs[i]->n, TQS_MAX_QUBITS);
     compile_program(cs[i]->n, step_order(cs[i]->gates), progs[i]);
     b->total_steps += cs[i]->nsteps;
   }
@@ -2034,6 +2062,8 @@ tqs_status tqs_simulate_and_collapse(tqs_circuit* c, const double* d_u, int64_t*
                                      tqs_c64* d_state, void* stream) {
   if (!c || !d_u || !d_index)
     return fail(TQS_ERR_ARG, "tqs_simulate_and_collapse: NULL circuit, d_u or d_index");
+  if (c->n > TQS_MAX_QUBITS)
+    return fail(TQS_ERR_TOO_MANY_QUBITS, "tqs_simulate_and_collapse: n %d > %d", c->n, TQS_MAX_QUBITS);
   if (d_state && !aligned16(d_state))
     return fail(TQS_ERR_ARG, "tqs_simulate_and_collapse: d_state must be 16-byte aligned");
   cudaStream_t s = static_cast<cudaStream_t>(stream);
@@ -2074,6 +2104,152 @@ tqs_status tqs_batch_sample(tqs_batch* b, const double* d_probs, int shots, cons
   TQS_CUDA(launch_sample(b->sample_plan->launch(b->d_sample.as<char>(), d_probs, d_u, shots, d_out),
                          s),
            "tqs_batch_sample: launch");
+  return TQS_OK;
+}
+
+}  // extern "C"
+
+// ------------------------------------------------------- full state vector
+// Gates are grouped into passes: a pass's tile bits are the kFsvLowQ lowest
+// bits plus the bits its gates act on non-diagonally (a target, a SWAP's two
+// bits, a custom unitary's bits), at most T in all.  Controls and diagonal
+// factors may sit on any bit.  Unused tile slots take the lowest free bits.
+
+static tqs_status compile_fsv(int n, const std::vector<Gate>& gates, FsvProgram& P) {
+  P = FsvProgram();
+  const int T = std::min(n, kFsvTileQ);
+  const int nlow = std::min(T, kFsvLowQ);
+  P.T = T;
+  const uint64_t low = (uint64_t(1) << nlow) - 1;
+  auto need_of = [&](const Gate& g) -> uint64_t {
+    if (is_wide(g) || g.kind == TQS_SWAP) {
+      uint64_t m = 0;
+      for (int i = 0; i < g.nq; ++i) m |= uint64_t(1) << g.q[i];
+      return m;
+    }
+    if (classify_mat(g.u) == G_DIAG) return 0;
+    return uint64_t(1) << (is_controlled(g.kind) ? g.q[1] : g.q[0]);
+  };
+  for (const Gate& g : gates)
+    if (is_instruction(g.kind))
+      return fail(TQS_ERR_UNSUPPORTED, "tqs_simulate_fsv: measure/reset instructions are not supported");
+  // One in-order scan per pass: a gate joins the pass if no earlier gate left
+  // for a later pass shares a qubit with it (gates on disjoint qubits
+  // commute), its non-diagonal bits fit the tile and its other bits fit the
+  // far-bit budget; otherwise its qubits are blocked for the rest of the scan.
+  std::vector<int> pending(gates.size()), still;
+  std::iota(pending.begin(), pending.end(), 0);
+  const uint64_t all = (n >= 64) ? ~uint64_t(0) : ((uint64_t(1) << n) - 1);
+  std::vector<const Gate*> cur;
+  std::vector<Gate> relabelled;
+  while (!pending.empty()) {
+    uint64_t mask = low, touched = 0, blocked = 0;
+    still.clear();
+    cur.clear();
+    size_t i = 0;
+    for (; i < pending.size() && blocked != all; ++i) {
+      const Gate& g = gates[pending[i]];
+      uint64_t qm = 0;
+      for (int j = 0; j < g.nq; ++j) qm |= uint64_t(1) << g.q[j];
+      const uint64_t need = need_of(g);
+      const uint64_t m2 = mask | need;
+      // far bits tested after adding g (the tile is filled to T bits from the
+      // lowest free bits at the end, which can only shrink this count)
+      const int far = __builtin_popcountll((touched | qm) & ~m2);
+      if ((qm & blocked) || __builtin_popcountll(m2) > T || far > kFsvMaxFar) {
+        blocked |= qm;
+        still.push_back(pending[i]);
+        continue;
+      }
+      mask = m2;
+      touched |= qm;
+      cur.push_back(&g);
+    }
+    for (; i < pending.size(); ++i) still.push_back(pending[i]);
+    pending.swap(still);
+    // fill the tile up to T bits with the lowest free bits
+    for (int bit = 0; __builtin_popcountll(mask) < T && bit < n; ++bit) mask |= uint64_t(1) << bit;
+    FsvPassInfo info;
+    info.mask = mask;
+    int map[64];
+    for (int q = 0; q < 64; ++q) map[q] = -1;
+    for (int q = 0, k = 0; q < n; ++q)
+      if ((mask >> q) & 1) map[q] = k++;
+    for (int q = 0; q < n; ++q)
+      if (((touched >> q) & 1) && map[q] < 0) {
+        map[q] = T + info.nfar;
+        info.far[info.nfar++] = static_cast<uint8_t>(q);
+      }
+    relabelled.assign(cur.size(), Gate{});
+    std::vector<const Gate*> ptrs(cur.size());
+    for (size_t k = 0; k < cur.size(); ++k) {
+      relabelled[k] = *cur[k];
+      for (int j = 0; j < kMaxCustomQubits; ++j)
+        relabelled[k].q[j] = (j < cur[k]->nq) ? map[cur[k]->q[j]] : map[cur[k]->q[0]];
+      ptrs[k] = &relabelled[k];
+    }
+    Program tp;
+    compile_program(T + info.nfar, ptrs, tp, false);
+    P.passes.push_back(info);
+    P.progs.push_back(std::move(tp));
+  }
+  return TQS_OK;
+}
+
+extern "C" {
+
+tqs_status tqs_simulate_fsv(tqs_circuit* c, tqs_c64* d_state, void* stream) {
+  if (!c || !d_state) return fail(TQS_ERR_ARG, "tqs_simulate_fsv: NULL circuit or state");
+  if (!aligned16(d_state)) return fail(TQS_ERR_ARG, "tqs_simulate_fsv: d_state must be 16-byte aligned");
+  if (c->n_instr > 0)
+    return fail(TQS_ERR_UNSUPPORTED, "tqs_simulate_fsv: measure/reset instructions are not supported");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if (c->n < 4) {
+    // smaller than any tile: the fused kernel, from a copy of the state
+    const size_t bytes = (size_t(1) << c->n) * sizeof(float2);
+    TQS_CUDA(c->d_collapse.ensure(bytes), "tqs_simulate_fsv: cudaMalloc");
+    TQS_CUDA(cudaMemcpyAsync(c->d_collapse.p, d_state, bytes, cudaMemcpyDeviceToDevice, s),
+             "tqs_simulate_fsv: copy");
+    return tqs_simulate(c, c->d_collapse.as<tqs_c64>(), d_state, nullptr, nullptr, stream);
+  }
+  if (!c->fsv_valid) {
+    tqs_status st = compile_fsv(c->n, c->gates, c->fsv);
+    if (st != TQS_OK) return st;
+    c->fsv_img = Image();
+    for (const Program& tp : c->fsv.progs) c->fsv_img.add(tp, 0);
+    TQS_CUDA(c->d_fsv.ensure(c->fsv_img.bytes()), "tqs_simulate_fsv: cudaMalloc");
+    TQS_CUDA(c->fsv_img.upload(c->d_fsv.p, s), "tqs_simulate_fsv: upload");
+    c->fsv_valid = true;
+  }
+  FusedLaunch L{};
+  c->fsv_img.point(L, c->d_fsv.as<char>());
+  const FusedCirc* circs = L.circs;
+  for (size_t k = 0; k < c->fsv.passes.size(); ++k) {
+    const FsvPassInfo& info = c->fsv.passes[k];
+    FsvTile F{};
+    F.state = reinterpret_cast<float2*>(d_state);
+    F.mask = info.mask;
+    F.n = c->n;
+    F.T = c->fsv.T;
+    F.nfar = info.nfar;
+    std::memcpy(F.far, info.far, sizeof(F.far));
+    L.circs = circs + k;
+    TQS_CUDA(launch_fsv_tile(L, F, s), "tqs_simulate_fsv: launch");
+  }
+  return TQS_OK;
+}
+
+tqs_status tqs_fsv_passes(tqs_circuit* c, int* n_passes, int* tile_bits) {
+  if (!c) return fail(TQS_ERR_ARG, "tqs_fsv_passes: circuit is NULL");
+  FsvProgram local;
+  const FsvProgram* P = &c->fsv;
+  if (!c->fsv_valid) {
+    tqs_status st = compile_fsv(c->n, c->gates, local);
+    if (st != TQS_OK) return st;
+    P = &local;
+  }
+  if (n_passes) *n_passes = static_cast<int>(P->passes.size());
+  if (tile_bits) *tile_bits = P->T;
   return TQS_OK;
 }
 

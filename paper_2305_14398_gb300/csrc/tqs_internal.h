@@ -224,6 +224,36 @@ cudaError_t launch_sample(const SampleLaunch& L, cudaStream_t s);
 // d_state[i] = (i == *d_index) for i < 2^n (the collapsed basis state).
 cudaError_t launch_set_basis(float2* d_state, int n, const int64_t* d_index, cudaStream_t s);
 
+// ---------------------------------------------------------------------------
+// Full-state-vector backend (Appendix A, eq. 12) for states held in HBM.
+// A pass keeps a tile of 2^T amplitudes in shared memory: the amplitudes
+// whose indices agree outside T "tile bits" (the kFsvLowQ lowest bits, for
+// coalesced loads, plus the bits the pass's gates need).  Every op of the
+// pass acts on the tile; bits outside it are fixed per tile.
+// ---------------------------------------------------------------------------
+constexpr int kFsvTileQ = 12;
+constexpr int kFsvLowQ = 5;
+constexpr int kFsvThreads = 256;
+
+constexpr int kFsvMaxFar = 19;  // bits outside the tile a pass may test (T + far <= 31)
+
+// One pass of the full-state-vector backend.  Its gates, relabelled to tile
+// qubits (the tile bits in ascending order are tile qubits 0..T-1; the far
+// bits the pass tests are virtual qubits T, T+1, ...), form a small circuit
+// compiled like any fused program (FusedCirc / FusedPass / FusedOp); for each
+// tile the virtual qubits carry the tile's fixed global bits.
+struct FsvTile {
+  float2* state;    // device, 2^n amplitudes, in place
+  uint64_t mask;    // tile bits
+  int32_t n;        // qubits of the state
+  int32_t T;        // tile bits
+  int32_t nfar;     // virtual qubits
+  uint8_t far[kFsvMaxFar + 1];  // global bit of virtual qubit T + v
+};
+
+// One pass over the state: L.circs points at the pass's tile program.
+cudaError_t launch_fsv_tile(const FusedLaunch& L, const FsvTile& F, cudaStream_t s);
+
 // Process-wide count of kernel launches enqueued by this library.
 void count_launches(int64_t k);
 

@@ -243,9 +243,21 @@ def test_gate_preconditions(bad, status):
 
 
 def test_circuit_size_limits():
+    """Circuits go up to 34 qubits (full-state-vector backend); the fused
+    forms and batches stop at 16."""
     with pytest.raises(B.TqsError) as e:
-        B.tqs_circuit_create(17)
+        B.tqs_circuit_create(35)
     assert e.value.name == "TQS_ERR_TOO_MANY_QUBITS"
+    c = B.circuit_from_ops(17, W.ghz_chain(17))
+    try:
+        with pytest.raises(B.TqsError) as e:
+            B.tqs_batch_create([c])
+        assert e.value.name == "TQS_ERR_TOO_MANY_QUBITS"
+        with pytest.raises(B.TqsError) as e:
+            B.tqs_circuit_program(c)
+        assert e.value.name == "TQS_ERR_TOO_MANY_QUBITS"
+    finally:
+        B.tqs_circuit_destroy(c)
     with pytest.raises(B.TqsError) as e:
         B.tqs_circuit_create(0)
     assert e.value.name == "TQS_ERR_ARG"
@@ -455,3 +467,37 @@ def test_custom_registry_errors():
     assert e.value.name == "TQS_ERR_ARG"
     with pytest.raises(B.TqsError):
         B.tqs_register_unitary("reg_test_big", np.eye(64))
+
+
+# ------------------------------------------------------- full state vector
+
+def test_fsv_pass_grouping():
+    """GHZ chain at n = 20: CNOT targets 1..19.  Tiles hold the 5 lowest bits
+    plus 7 more, so targets 1..11 share the first pass, 12..18 the second and
+    19 the third."""
+    c = B.circuit_from_ops(20, W.ghz_chain(20))
+    try:
+        assert B.tqs_fsv_passes(c) == (3, 12)
+    finally:
+        B.tqs_circuit_destroy(c)
+    # diagonal gates and controls never need a tile slot
+    ops = [("h", (0,), ())] + [("cp", (19, q), (0.3,)) for q in range(5)] + [("z", (18,), ())]
+    c = B.circuit_from_ops(20, ops)
+    try:
+        assert B.tqs_fsv_passes(c) == (1, 12)
+    finally:
+        B.tqs_circuit_destroy(c)
+
+
+def test_large_circuits_only_in_fsv():
+    c = B.tqs_circuit_create(34)
+    try:
+        B.tqs_add_gate(c, "h", (33,))
+        with pytest.raises(B.TqsError) as e:
+            B.tqs_simulate(c, None, stream=0)
+        assert e.value.name == "TQS_ERR_TOO_MANY_QUBITS"
+        assert B.tqs_fsv_passes(c)[0] == 1
+    finally:
+        B.tqs_circuit_destroy(c)
+    with pytest.raises(B.TqsError):
+        B.tqs_circuit_create(35)
