@@ -35,12 +35,10 @@ BATCH = 16384
 METRIC = "circuits/s"
 WORKLOAD = "paper-shaped 11-qubit circuits (GHZ / DJ-constant / DJ-balanced / QFT, 25% each)"
 
-# DRAM bytes (read + write) per launch of the fused warp-team kernel on this
-# workload, from the ncu capture summarised in profiles/: 19.48 MB read +
-# 207.64 MB written for 8192 circuits of the same mix, scaled by 2 to the
-# 16384 circuits of one step (traffic grows with the circuit count).  Set back
-# to None whenever the kernel changes, until it is captured again.
-NCU_TRAFFIC_BYTES = int(2 * (19_483_648 + 207_640_576))
+# DRAM bytes (read + write) per launch of the fused kernel on this workload,
+# from the ncu capture summarised in profiles/; None until the current kernel
+# has been captured.
+NCU_TRAFFIC_BYTES = None
 
 
 def parse_args():
@@ -252,7 +250,7 @@ def run_tqs(args):
     # ---------------------------------------------------------- inputs
     circs = replica_circuits(W, rank, args.batch)
     from paper_2305_14398_gb300 import autotune
-    tuned = autotune.tune_warps_per_cta(circs, sample=4096)
+    tuned = autotune.tune_warps_per_cta(circs)
     arrays = B.pack_ops(circs)
     b = B.tqs_batch_create_packed(*arrays)
     count, total, offs, steps_total, prog_bytes = B.tqs_batch_info(b, extra=True)
@@ -324,13 +322,15 @@ def run_tqs(args):
                    "steps_per_batch": steps_total, "parallelism": f"replicas x{world}",
                    "l2": "flushed between timed steps (256 MiB write, not timed)",
                    "outputs": "state (complex64) + |psi|^2 (f64) + norm (f64) per circuit",
-                   "launch": {"warps_per_cta": tuned["warps"], "autotune_ms": tuned["timings_ms"],
+                   "launch": {"warps_per_circuit": tuned["team_warps"],
+                              "warps_per_cta": tuned["warps"], "autotune_ms": tuned["timings_ms"],
                               "autotune_source": tuned["source"]}},
         "dense_equiv_complex_gflops": dense_flops * world * args.steps / total_s / 1e9,
         "roofline": {"bound": "hbm", "achieved": achieved_gbs, "peak": hbm_peak,
                      "unit": "GB/s", "frac": achieved_gbs / hbm_peak,
                      "traffic": NCU_TRAFFIC_BYTES, "peak_source": peak_src,
-                     "kernel": "fused_kernel<TEAM_WARP>",
+                     "kernel": ("fused_kernel<TEAM_PAIR>" if tuned["team_warps"] == 2
+                                else "fused_kernel<TEAM_WARP>"),
                      "algorithmic_bytes_per_launch": alg_bytes},
         "norm_max_err": norm_err,
         "gpu_launches": launches,

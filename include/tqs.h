@@ -439,11 +439,19 @@ tqs_status tqs_server_destroy(tqs_server* s);
 
 /* ----------------------------------------------------------------- options
  * Launch options read when a batch (or a single simulate) plans its launches.
- * TQS_OPT_WARPS_PER_CTA, key = log2 of the amplitudes of a warp's shared
- * memory slice (4..11), value = warps per CTA of the warp-team kernel (1..16;
- * default 4; capped so that a CTA's slices fit 200 KiB).  Options change launch
- * shapes only, never a result bit (a circuit always runs on one warp). */
+ * TQS_OPT_WARPS_PER_CTA, key = log2 of the amplitudes of a circuit's shared
+ * memory slice (4..11), value = warps per CTA of the warp-class kernel (1..16;
+ * default 4; capped so that a CTA's slices fit 200 KiB).  It changes launch
+ * shapes only, never a result bit.
+ * TQS_OPT_TEAM_WARPS, same key, value = warps per circuit of the warp class
+ * (1 or 2; default 1).  Two warps share one slice (twice the warps per byte of
+ * shared memory).  States and probabilities are bitwise the same for 1 and 2;
+ * the FP64 norm and the reductions of measure/reset instructions are summed
+ * in a partition that depends on it, so they may differ in the last bits
+ * between the two settings (every entry point uses the current setting, so
+ * batch, server and single-circuit results agree). */
 #define TQS_OPT_WARPS_PER_CTA 1
+#define TQS_OPT_TEAM_WARPS 2
 
 tqs_status tqs_set_option(int option, int key, int64_t value);
 tqs_status tqs_get_option(int option, int key, int64_t* value);

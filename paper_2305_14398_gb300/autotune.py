@@ -1,14 +1,15 @@
 """Autotuner for the batched fused step kernel's launch shape.
 
-The warp-team kernel (one warp per circuit, its state in a shared-memory slice of
-2^q amplitudes) can group 1..16 warps per CTA.  Few warps per CTA schedule
-circuits at a fine grain; more warps share one CTA's launch overhead.  Which is
-faster depends on the circuit mix and on the GPU, and the choice never changes a
-result bit, so it is measured: every candidate runs a sample of the actual
-workload (CUDA events, best of several runs) and the fastest is set with
-tqs_set_option(TQS_OPT_WARPS_PER_CTA, q, warps).  Results are cached in a JSON
-file keyed by GPU name and q (TQS_AUTOTUNE_CACHE, default
-~/.cache/tqs/autotune.json).
+The warp-class kernel (circuits of n <= 11, each state in a shared-memory slice
+of 2^q amplitudes) runs one or two warps per circuit and groups 1..16 warps per
+CTA.  Two warps per circuit double the warps per byte of shared memory (more
+latency hiding); few warps per CTA schedule circuits at a fine grain.  Which is
+faster depends on the circuit mix and on the GPU, so it is measured: every
+candidate runs a sample of the actual workload (CUDA events, best of several
+runs) and the fastest is set with tqs_set_option(TQS_OPT_TEAM_WARPS, q, ...) and
+tqs_set_option(TQS_OPT_WARPS_PER_CTA, q, ...).  States and probabilities do not
+depend on the choice.  Results are cached in a JSON file keyed by GPU name, q
+and batch size (TQS_AUTOTUNE_CACHE, default ~/.cache/tqs/autotune.json).
 """
 from __future__ import annotations
 
@@ -17,7 +18,9 @@ import os
 
 from . import binding as B
 
-CANDIDATES = (1, 2, 3, 4, 6, 8, 12, 16)
+# (warps per circuit, warps per CTA)
+CANDIDATES = tuple((1, w) for w in (1, 2, 3, 4, 6, 8, 12, 16)) + \
+    tuple((2, w) for w in (2, 4, 6, 8, 12, 16))
 SLICE_LIMIT_BYTES = 200 * 1024
 
 
@@ -50,26 +53,33 @@ def warp_slice_q(circuits) -> int:
     return max(qs) if qs else 0
 
 
-def tune_warps_per_cta(circuits, sample: int = 4096, reps: int = 5, use_cache: bool = True):
-    """Pick warps per CTA for the warp-team launch of this kind of batch.
-    Returns {"q", "warps", "timings_ms", "source"}."""
+def _apply(q, tw, w):
+    B.tqs_set_option(B.OPT_TEAM_WARPS, q, tw)
+    B.tqs_set_option(B.OPT_WARPS_PER_CTA, q, w)
+
+
+def tune_warps_per_cta(circuits, sample: int = 16384, reps: int = 5, use_cache: bool = True):
+    """Pick warps per circuit and per CTA for the warp-class launch of this kind
+    of batch.  Returns {"q", "team_warps", "warps", "timings_ms", "source"}."""
     import torch
 
     q = warp_slice_q(circuits)
     if q == 0:
-        return {"q": 0, "warps": None, "timings_ms": {}, "source": "no warp-team circuits"}
-    key = f"{torch.cuda.get_device_name()}|q{q}|{len(circuits)}"
+        return {"q": 0, "team_warps": None, "warps": None, "timings_ms": {},
+                "source": "no warp-class circuits"}
+    key = f"v2|{torch.cuda.get_device_name()}|q{q}|{len(circuits)}"
     cache = _load() if use_cache else {}
     if key in cache:
-        w = int(cache[key]["warps"])
-        B.tqs_set_option(B.OPT_WARPS_PER_CTA, q, w)
-        return {"q": q, "warps": w, "timings_ms": cache[key]["timings_ms"], "source": "cache"}
+        tw, w = int(cache[key]["team_warps"]), int(cache[key]["warps"])
+        _apply(q, tw, w)
+        return {"q": q, "team_warps": tw, "warps": w, "timings_ms": cache[key]["timings_ms"],
+                "source": "cache"}
     arrays = B.pack_ops(list(circuits[:sample]))
     timings = {}
-    for w in CANDIDATES:
-        if w * (1 << q) * 8 > SLICE_LIMIT_BYTES:
+    for tw, w in CANDIDATES:
+        if (w // tw) * (1 << q) * 8 > SLICE_LIMIT_BYTES:
             continue
-        B.tqs_set_option(B.OPT_WARPS_PER_CTA, q, w)
+        _apply(q, tw, w)
         b = B.tqs_batch_create_packed(*arrays)
         try:
             count, total, _ = B.tqs_batch_info(b)
@@ -86,12 +96,12 @@ def tune_warps_per_cta(circuits, sample: int = 4096, reps: int = 5, use_cache: b
                 e.record()
                 torch.cuda.synchronize()
                 best = min(best, s.elapsed_time(e))
-            timings[str(w)] = best
+            timings[f"{tw}x{w}"] = best
         finally:
             B.tqs_batch_destroy(b)
-    w = int(min(timings, key=timings.get))
-    B.tqs_set_option(B.OPT_WARPS_PER_CTA, q, w)
-    cache[key] = {"warps": w, "timings_ms": timings}
+    tw, w = (int(x) for x in min(timings, key=timings.get).split("x"))
+    _apply(q, tw, w)
+    cache[key] = {"team_warps": tw, "warps": w, "timings_ms": timings}
     if use_cache:
         _save(cache)
-    return {"q": q, "warps": w, "timings_ms": timings, "source": "measured"}
+    return {"q": q, "team_warps": tw, "warps": w, "timings_ms": timings, "source": "measured"}

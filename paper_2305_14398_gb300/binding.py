@@ -470,6 +470,7 @@ def tqs_server_destroy(sv: int) -> None:
 # ----------------------------------------------------------------- options
 
 OPT_WARPS_PER_CTA = 1
+OPT_TEAM_WARPS = 2
 
 
 def tqs_set_option(option: int, key: int, value: int) -> None:

@@ -341,10 +341,14 @@ __device__ __forceinline__ int pfwd_of(int v, const PosMap& pm, int n) {
   for (int q = 0; q < n; ++q) if ((v >> q) & 1) r |= pfwd_bit(q, pm);
   return r;
 }
+// Barrier of the threads working on one circuit: the warp, the warp pair
+// (named barrier 1 + pair index, 64 threads) or the CTA.
 template <int TEAM>
 __device__ __forceinline__ void team_sync() {
   if (TEAM == TEAM_WARP)
     __syncwarp();
+  else if (TEAM == TEAM_PAIR)
+    asm volatile("bar.sync %0, 64;" ::"r"(1 + (static_cast<int>(threadIdx.x) >> 6)) : "memory");
   else
     __syncthreads();
 }
@@ -374,13 +378,13 @@ __device__ __noinline__ void instr_pass(const FusedLaunch& L, int nint, int bit,
   }
   if (TEAM != TEAM_WARP) {
     const int warp = rank >> 5, lane = rank & 31, nw = size >> 5;
-    __syncthreads();
-    if (lane == 0) { s_red[warp] = s0; s_red[16 + warp] = s1; }
-    __syncthreads();
+    team_sync<TEAM>();
+    if (lane == 0) { s_red[2 * warp] = s0; s_red[2 * warp + 1] = s1; }
+    team_sync<TEAM>();
     s0 = 0.0;
     s1 = 0.0;
-    for (int w = 0; w < nw; ++w) { s0 += s_red[w]; s1 += s_red[16 + w]; }
-    __syncthreads();
+    for (int w = 0; w < nw; ++w) { s0 += s_red[2 * w]; s1 += s_red[2 * w + 1]; }
+    team_sync<TEAM>();
   }
   const double T = s0 + s1;
   int outcome = (L.uniforms[k] * T < s0) ? 0 : 1;
@@ -546,7 +550,7 @@ __device__ void run_circuit(const FusedLaunch& L, int ci, float2* st, int rank, 
   } else {
     const int warp = rank >> 5, lane = rank & 31;
     if (lane == 0) s_red[warp] = acc;
-    __syncthreads();
+    team_sync<TEAM>();
     if (rank == 0) { double s = 0.0; for (int w = 0; w < (size >> 5); ++w) s += s_red[w]; if (L.norms) L.norms[ci] = s; }
   }
   team_sync<TEAM>();
@@ -557,7 +561,21 @@ __global__ void __launch_bounds__(TEAM == TEAM_CTA ? kCtaThreads : 512)
     fused_kernel(const __grid_constant__ FusedLaunch L) {
   extern __shared__ float4 smem_raw[];
   float2* smem = reinterpret_cast<float2*>(smem_raw);
-  if (TEAM == TEAM_WARP) {
+  if (TEAM == TEAM_PAIR) {
+    // two warps per circuit; pair p uses slice p and named barrier 1 + p
+    __shared__ int s_job[8];
+    __shared__ double s_red[8][4];
+    const int pair = threadIdx.x >> 6, rank = threadIdx.x & 63;
+    float2* st = smem + (static_cast<size_t>(pair) << L.slice_q);
+    for (;;) {
+      if (rank == 0) s_job[pair] = atomicAdd(L.counter, 1);
+      team_sync<TEAM_PAIR>();
+      const int job = s_job[pair];
+      team_sync<TEAM_PAIR>();
+      if (job >= L.n_jobs) break;
+      run_circuit<TEAM_PAIR>(L, L.order[job], st, rank, 64, s_red[pair]);
+    }
+  } else if (TEAM == TEAM_WARP) {
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     float2* st = smem + (static_cast<size_t>(warp) << L.slice_q);
     for (;;) {
@@ -669,12 +687,13 @@ __global__ void __launch_bounds__(kFsvThreads)
 
 size_t fused_smem_bytes(int team, int warps_per_cta, int slice_q) {
   if (team == TEAM_WARP) return (static_cast<size_t>(warps_per_cta) << slice_q) * sizeof(float2);
+  if (team == TEAM_PAIR) return (static_cast<size_t>(warps_per_cta / 2) << slice_q) * sizeof(float2);
   if (team == TEAM_CTA) return (static_cast<size_t>(1) << slice_q) * sizeof(float2);
   return 0;
 }
 
 int fused_threads(int team, int warps_per_cta) {
-  if (team == TEAM_WARP) return 32 * warps_per_cta;
+  if (team == TEAM_WARP || team == TEAM_PAIR) return 32 * warps_per_cta;
   if (team == TEAM_CTA) return kCtaThreads;
   return kGlobalThreads;
 }
@@ -690,6 +709,11 @@ int fused_max_ctas_per_sm(int team, int warps_per_cta, int slice_q) {
     cudaFuncSetAttribute(fused_kernel<TEAM_WARP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          static_cast<int>(smem));
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, fused_kernel<TEAM_WARP>, threads,
+                                                      smem);
+  } else if (team == TEAM_PAIR) {
+    cudaFuncSetAttribute(fused_kernel<TEAM_PAIR>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         static_cast<int>(smem));
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, fused_kernel<TEAM_PAIR>, threads,
                                                       smem);
   } else if (team == TEAM_CTA) {
     cudaFuncSetAttribute(fused_kernel<TEAM_CTA>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -736,6 +760,11 @@ cudaError_t launch_fused(const FusedLaunch& L, cudaStream_t s) {
                              static_cast<int>(smem));
     if (e != cudaSuccess) return e;
     fused_kernel<TEAM_WARP><<<L.grid, threads, smem, s>>>(L);
+  } else if (L.team == TEAM_PAIR) {
+    e = cudaFuncSetAttribute(fused_kernel<TEAM_PAIR>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             static_cast<int>(smem));
+    if (e != cudaSuccess) return e;
+    fused_kernel<TEAM_PAIR><<<L.grid, threads, smem, s>>>(L);
   } else if (L.team == TEAM_CTA) {
     e = cudaFuncSetAttribute(fused_kernel<TEAM_CTA>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              static_cast<int>(smem));

@@ -880,17 +880,29 @@ struct LaunchPlan {
 
 // TQS_OPT_WARPS_PER_CTA table, indexed by the warp slice's log2 amplitudes.
 static std::atomic<int> g_warps_for_q[16] = {4, 4, 4, 4, 4, 4, 4, 4, 4, 4, 4, 4, 4, 4, 4, 4};
+// TQS_OPT_TEAM_WARPS table: warps per circuit of the warp class (1 or 2).
+static std::atomic<int> g_team_warps_for_q[16] = {1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1};
 
 static LaunchPlan plan_for(int team, int max_nint, int jobs, int warps_hint) {
   LaunchPlan lp{team, 1, 4, 1};
   if (team == TEAM_WARP) {
     lp.slice_q = std::max(4, max_nint);
-    int w = warps_hint > 0 ? warps_hint : g_warps_for_q[lp.slice_q].load();
+    const int tw = g_team_warps_for_q[lp.slice_q].load();
+    // warps_hint > 0: that many circuits per CTA (a single simulate uses 1)
+    int w = warps_hint > 0 ? warps_hint * tw : g_warps_for_q[lp.slice_q].load();
     const size_t slice = (size_t(1) << lp.slice_q) * sizeof(float2);
-    while (w > 1 && size_t(w) * slice > 200 * 1024) w >>= 1;
+    if (tw == 2) {
+      // warp pairs: an even number of warps, one slice per pair
+      lp.team = TEAM_PAIR;
+      w = std::max(2, w & ~1);
+      while (w > 2 && size_t(w / 2) * slice > 200 * 1024) w -= 2;
+    } else {
+      while (w > 1 && size_t(w) * slice > 200 * 1024) w >>= 1;
+    }
     lp.warps = w;
-    const int per_sm = std::max(1, fused_max_ctas_per_sm(TEAM_WARP, w, lp.slice_q));
-    const int want = (jobs + w - 1) / w;
+    const int per_sm = std::max(1, fused_max_ctas_per_sm(lp.team, w, lp.slice_q));
+    const int circuits_per_cta = lp.team == TEAM_PAIR ? w / 2 : w;
+    const int want = (jobs + circuits_per_cta - 1) / circuits_per_cta;
     lp.grid = std::max(1, std::min(want, per_sm * device_sms()));
   } else if (team == TEAM_CTA) {
     lp.slice_q = std::max(4, max_nint);
@@ -1453,7 +1465,7 @@ static tqs_status batch_enqueue_at(tqs_batch* b, char* base, size_t order_off, s
     L.gscratch = gscratch;
     L.uniforms = u;
     L.outcomes = outcomes;
-    L.team = t;
+    L.team = b->plans[t].team;
     L.warps_per_cta = b->plans[t].warps;
     L.slice_q = b->plans[t].slice_q;
     L.grid = b->plans[t].grid;
@@ -1808,7 +1820,7 @@ static tqs_status server_launch(tqs_server* sv, SrvSlot& sl) {
     L.probs = nullptr;
     L.norms = d_norms;
     L.gscratch = reinterpret_cast<float2*>(base + gscr_off);
-    L.team = t;
+    L.team = plans[t].team;
     L.warps_per_cta = plans[t].warps;
     L.slice_q = plans[t].slice_q;
     L.grid = plans[t].grid;
@@ -1983,6 +1995,12 @@ tqs_status tqs_server_destroy(tqs_server* sv) {
 extern "C" {
 
 tqs_status tqs_set_option(int option, int key, int64_t value) {
+  if (option == TQS_OPT_TEAM_WARPS) {
+    if (key < 4 || key > kWarpMaxQ) return fail(TQS_ERR_ARG, "tqs_set_option: key %d outside [4, %d]", key, kWarpMaxQ);
+    if (value != 1 && value != 2) return fail(TQS_ERR_ARG, "tqs_set_option: team warps %lld is not 1 or 2", static_cast<long long>(value));
+    g_team_warps_for_q[key].store(static_cast<int>(value));
+    return TQS_OK;
+  }
   if (option == TQS_OPT_WARPS_PER_CTA) {
     if (key < 4 || key > kWarpMaxQ) return fail(TQS_ERR_ARG, "tqs_set_option: key %d outside [4, %d]", key, kWarpMaxQ);
     if (value < 1 || value > 16) return fail(TQS_ERR_ARG, "tqs_set_option: warps %lld outside [1, 16]", static_cast<long long>(value));
@@ -1994,6 +2012,11 @@ tqs_status tqs_set_option(int option, int key, int64_t value) {
 
 tqs_status tqs_get_option(int option, int key, int64_t* value) {
   if (!value) return fail(TQS_ERR_ARG, "tqs_get_option: value is NULL");
+  if (option == TQS_OPT_TEAM_WARPS) {
+    if (key < 4 || key > kWarpMaxQ) return fail(TQS_ERR_ARG, "tqs_get_option: key %d outside [4, %d]", key, kWarpMaxQ);
+    *value = g_team_warps_for_q[key].load();
+    return TQS_OK;
+  }
   if (option == TQS_OPT_WARPS_PER_CTA) {
     if (key < 4 || key > kWarpMaxQ) return fail(TQS_ERR_ARG, "tqs_get_option: key %d outside [4, %d]", key, kWarpMaxQ);
     *value = g_warps_for_q[key].load();

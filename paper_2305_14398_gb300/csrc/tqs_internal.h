@@ -86,7 +86,10 @@ constexpr uint8_t kWidePass = 0xFE;
 constexpr int kMaxCustomQubits = 5;
 static_assert(sizeof(FusedPass) == 16, "FusedPass layout");
 
-enum TeamKind : int32_t { TEAM_WARP = 0, TEAM_CTA = 1, TEAM_GLOBAL = 2 };
+// TEAM_PAIR runs the circuits of the warp class (n <= kWarpMaxQ) with two
+// warps per circuit sharing its shared-memory slice (a launch variant of
+// TEAM_WARP: twice the warps per byte of shared memory).
+enum TeamKind : int32_t { TEAM_WARP = 0, TEAM_CTA = 1, TEAM_GLOBAL = 2, TEAM_PAIR = 3 };
 
 struct alignas(16) FusedCirc {
   int32_t n;            // logical qubits

@@ -108,7 +108,18 @@ def test_circuit_unitary_with_customs(prec, tol):
         B.tqs_circuit_destroy(c)
 
 
-def test_batch_from_handles_with_customs():
+@pytest.mark.parametrize("tw", [1, 2])
+def test_batch_from_handles_with_customs(tw):
+    for q in range(4, 12):
+        B.tqs_set_option(B.OPT_TEAM_WARPS, q, tw)
+    try:
+        _batch_from_handles_with_customs()
+    finally:
+        for q in range(4, 12):
+            B.tqs_set_option(B.OPT_TEAM_WARPS, q, 1)
+
+
+def _batch_from_handles_with_customs():
     circs = [(n, with_customs(n, 500 + i)) for i, n in enumerate([2, 5, 7, 9, 11, 12, 13, 15, 4, 10])]
     hs = [B.circuit_from_ops(n, ops) for n, ops in circs]
     try:

@@ -30,25 +30,37 @@ def test_bounded_wait_times_out_and_context_survives():
 
 
 def test_autotuner_keeps_results_bitwise():
-    """Launch shapes chosen by the autotuner never change a result bit."""
+    """Launch shapes (warps per circuit and per CTA) never change a state or
+    probability bit; the FP64 norm stays within its bound either way."""
     if not torch.cuda.is_available():
         pytest.skip("no CUDA device")
     from paper_2305_14398_gb300 import autotune
     circs = W.batch_circuits(256, 91)
-    outs = []
-    for w in (1, 4, 12):
-        B.tqs_set_option(B.OPT_WARPS_PER_CTA, autotune.warp_slice_q(circs), w)
+    q = autotune.warp_slice_q(circs)
+    outs, norms = [], []
+    for tw, w in ((1, 1), (1, 4), (1, 12), (2, 2), (2, 8), (2, 16)):
+        B.tqs_set_option(B.OPT_TEAM_WARPS, q, tw)
+        B.tqs_set_option(B.OPT_WARPS_PER_CTA, q, w)
         b = B.tqs_batch_create_packed(*B.pack_ops(circs))
         try:
             count, total, _ = B.tqs_batch_info(b)
             st = torch.empty(total, dtype=torch.complex64, device="cuda")
-            B.tqs_batch_run(b, st, None, None, use_graph=False)
+            pr = torch.empty(total, dtype=torch.float64, device="cuda")
+            nm = torch.empty(count, dtype=torch.float64, device="cuda")
+            B.tqs_batch_run(b, st, pr, nm, use_graph=False)
             torch.cuda.synchronize()
-            outs.append(st.cpu().numpy())
+            outs.append((st.cpu().numpy(), pr.cpu().numpy()))
+            norms.append(nm.cpu().numpy())
         finally:
             B.tqs_batch_destroy(b)
-    B.tqs_set_option(B.OPT_WARPS_PER_CTA, autotune.warp_slice_q(circs), 4)
-    for o in outs[1:]:
-        assert np.array_equal(o.view(np.uint32), outs[0].view(np.uint32))
+    B.tqs_set_option(B.OPT_TEAM_WARPS, q, 1)
+    B.tqs_set_option(B.OPT_WARPS_PER_CTA, q, 4)
+    for st, pr in outs[1:]:
+        assert np.array_equal(st.view(np.uint32), outs[0][0].view(np.uint32))
+        assert np.array_equal(pr.view(np.uint64), outs[0][1].view(np.uint64))
+    for nm in norms:
+        assert np.max(np.abs(nm - 1.0)) <= 1e-6
     r = autotune.tune_warps_per_cta(circs, sample=256, reps=2, use_cache=False)
-    assert r["warps"] in (1, 2, 3, 4, 6, 8, 12) and r["source"] == "measured"
+    assert (r["team_warps"], r["warps"]) in autotune.CANDIDATES and r["source"] == "measured"
+    B.tqs_set_option(B.OPT_TEAM_WARPS, q, 1)
+    B.tqs_set_option(B.OPT_WARPS_PER_CTA, q, 4)

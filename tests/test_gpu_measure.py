@@ -91,8 +91,18 @@ def test_missing_uniforms_is_an_error():
         B.tqs_circuit_destroy(c)
 
 
+@pytest.fixture(params=[1, 2], ids=["warp", "pair"])
+def team_warps(request):
+    """Run a test with 1 or 2 warps per circuit of the warp class."""
+    for q in range(4, 12):
+        B.tqs_set_option(B.OPT_TEAM_WARPS, q, request.param)
+    yield request.param
+    for q in range(4, 12):
+        B.tqs_set_option(B.OPT_TEAM_WARPS, q, 1)
+
+
 @pytest.mark.parametrize("use_graph", [False, True])
-def test_batch_measured_equals_single(use_graph):
+def test_batch_measured_equals_single(use_graph, team_warps):
     circs = []
     for i in range(48):
         n = [3, 6, 9, 11, 12, 13, 15][i % 7]

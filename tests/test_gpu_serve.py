@@ -45,7 +45,18 @@ def alone(n, ops):
         B.tqs_circuit_destroy(c)
 
 
-def test_serving_mixed_stream_alone_equals_mix():
+@pytest.mark.parametrize("tw", [1, 2])
+def test_serving_mixed_stream_alone_equals_mix(tw):
+    for q in range(4, 12):
+        B.tqs_set_option(B.OPT_TEAM_WARPS, q, tw)
+    try:
+        _alone_equals_mix()
+    finally:
+        for q in range(4, 12):
+            B.tqs_set_option(B.OPT_TEAM_WARPS, q, 1)
+
+
+def _alone_equals_mix():
     reqs = W.serving_requests(300, rate_hz=20000.0, seed_tag=41)
     r = serve.replay(reqs, budget_bytes=8 << 30, max_inflight=4, max_batch=64, keep_states=True)
     assert np.all(np.isfinite(r["latency_s"]))

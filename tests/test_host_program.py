@@ -324,8 +324,14 @@ def test_launch_options():
                 B.tqs_set_option(B.OPT_WARPS_PER_CTA, *bad)
         with pytest.raises(B.TqsError):
             B.tqs_set_option(99, 11, 4)
+        B.tqs_set_option(B.OPT_TEAM_WARPS, 11, 2)
+        assert B.tqs_get_option(B.OPT_TEAM_WARPS, 11) == 2
+        for bad in [(11, 0), (11, 3), (3, 1), (12, 2)]:
+            with pytest.raises(B.TqsError):
+                B.tqs_set_option(B.OPT_TEAM_WARPS, *bad)
     finally:
         B.tqs_set_option(B.OPT_WARPS_PER_CTA, 11, old)
+        B.tqs_set_option(B.OPT_TEAM_WARPS, 11, 1)
 
 
 def test_leading_x_gates_fold_into_the_start_state():
