@@ -138,12 +138,15 @@ __device__ __forceinline__ unsigned bit_mask(int b) {
 }
 
 // Controlled diagonal with both qubits local: amplitudes with the control bit
-// set are multiplied by d0 (target 0) or d1 (target 1).
-__device__ __forceinline__ void diag_local(float2 (&a)[16], int t, int c, float2 d0, float2 d1) {
+// set are multiplied by d0 (target 0) or d1 (target 1); when d0 is exactly 1
+// only the control = target = 1 quarter changes.
+__device__ __forceinline__ void diag_local(float2 (&a)[16], int t, int c, float2 d0, float2 d1,
+                                           bool d0one) {
   const unsigned cm = bit_mask(c), tm = bit_mask(t);
+  const unsigned on = d0one ? (cm & tm) : cm;
 #pragma unroll
   for (int j = 0; j < 16; ++j) {
-    if ((cm >> j) & 1) a[j] = cmul(a[j], ((tm >> j) & 1) ? d1 : d0);
+    if ((on >> j) & 1) a[j] = cmul(a[j], ((tm >> j) & 1) ? d1 : d0);
   }
 }
 
@@ -287,7 +290,8 @@ __device__ __forceinline__ void run_ops(float2 (&a)[16], const FusedOp* __restri
     }
     {  // OPC_DLL: both local
       const uint4 q1 = __ldg(rec + 1);
-      diag_local(a, (q0.x >> 8) & 0xff, (q0.x >> 16) & 0xff, f2(q1.x, q1.y), f2(q1.z, q1.w));
+      diag_local(a, (q0.x >> 8) & 0xff, (q0.x >> 16) & 0xff, f2(q1.x, q1.y), f2(q1.z, q1.w),
+                 d0one);
     }
   }
   pend_flush(a, pd, 0);
@@ -524,6 +528,7 @@ __device__ void run_circuit(const FusedLaunch& L, int ci, float2* st, int rank, 
     const int p_one = cd.identity ? 1 : pfwd_bit(0, pw);
     int p_hi = 0;
     const int iters = (N + 2 * size - 1) >> sh;
+#pragma unroll 4
     for (int k = 0; k < iters; ++k) {
       if (k > 0) {
         const int q = sh + (__ffs(k) - 1);

@@ -313,11 +313,14 @@ static void compile_program(int n, const std::vector<const Gate*>& gs_in, Progra
     for (int b = 0; b < nint; ++b)
       if ((Lmask >> b) & 1) { ps.L[k] = static_cast<uint8_t>(b); loc[b] = k++; }
     ps.op_begin = static_cast<uint32_t>(P.ops.size());
-    ps.op_count = static_cast<uint32_t>(raw.size());
     double pass_cost = 6.0;
     int h_count = 0;
     static const uint16_t kBitMask[4] = {0xAAAA, 0xCCCC, 0xF0F0, 0xFF00};
     for (const Raw& r : raw) {
+      // a factor that fused to the identity (H H, X X, ...) does nothing
+      if (!r.is_h && std::abs(r.u.m[0] - 1.0) <= 1e-15 && std::abs(r.u.m[3] - 1.0) <= 1e-15 &&
+          std::abs(r.u.m[1]) <= 1e-15 && std::abs(r.u.m[2]) <= 1e-15)
+        continue;
       FusedOp op{};
       const Mat2& u = r.u;
       op.fbit = 0xFF;
@@ -374,6 +377,7 @@ static void compile_program(int n, const std::vector<const Gate*>& gs_in, Progra
       }
       P.ops.push_back(op);
     }
+    ps.op_count = static_cast<uint32_t>(P.ops.size() - ps.op_begin);
     // exact power-of-two rescale for this pass's unscaled Hadamards
     const int tot = h_carry + h_count;
     ps.scale = std::ldexp(1.0f, -(tot / 2));
@@ -470,6 +474,18 @@ static void compile_program(int n, const std::vector<const Gate*>& gs_in, Progra
   take_segment();
   }
   if (P.passes.empty()) emit_pass(0u, 0, true);
+  // drop passes left with nothing to do (every factor fused to the identity);
+  // the first pass stays, it generates the start state
+  {
+    size_t k = 1;
+    for (size_t i = 1; i < P.passes.size(); ++i) {
+      const FusedPass& ps = P.passes[i];
+      if (ps.L[0] != kInstrPass && ps.L[0] != kWidePass && ps.op_count == 0 && ps.scale == 1.0f)
+        continue;
+      P.passes[k++] = ps;
+    }
+    P.passes.resize(std::min(k, P.passes.size()));
+  }
   P.out_scale = h_carry ? static_cast<float>(1.0 / std::sqrt(2.0)) : 1.0f;
   P.identity = 1;
   for (int q = 0; q < 16; ++q) {
