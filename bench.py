@@ -35,10 +35,12 @@ BATCH = 16384
 METRIC = "circuits/s"
 WORKLOAD = "paper-shaped 11-qubit circuits (GHZ / DJ-constant / DJ-balanced / QFT, 25% each)"
 
-# DRAM bytes (read + write) per launch of the fused kernel on this workload,
-# from the ncu capture summarised in profiles/; None until the current kernel
-# has been captured.
-NCU_TRAFFIC_BYTES = None
+# DRAM bytes (read + write) per launch of the fused kernel (two warps per
+# circuit, the autotuned shape) on this workload, from the ncu capture
+# summarised in profiles/: 36.18 MB read + 476.56 MB written for one launch
+# over the 16384 circuits of a step.  Set back to None whenever the kernel
+# changes, until it is captured again.
+NCU_TRAFFIC_BYTES = 36_182_016 + 476_563_712
 
 
 def parse_args():

@@ -1,6 +1,6 @@
 """Small driver for ncu captures of the fused step kernels.
 
-    python -m paper_2305_14398_gb300.prof COUNT KIND REPS [noprobs]
+    python -m paper_2305_14398_gb300.prof COUNT KIND REPS [noprobs] [TWxW]
 
 chain: the 40-step random layered circuit-unitary chain at n = COUNT
        (tensor-core BF16x3);
@@ -10,6 +10,8 @@ mix:   COUNT paper-shaped 11-qubit circuits (GHZ / DJ-constant / DJ-balanced /
        workload (n = 4..14, depth 5..40).  Runs tqs_batch_run REPS times
        without a graph, then once more timed with CUDA events.
 noprobs: the same without the FP64 probability output (d_probs = NULL).
+TWxW (e.g. 2x16): warps per circuit and per CTA of the 11-qubit warp class
+(the bench's autotuned shape), set before the batch is planned.
 """
 import sys
 
@@ -39,7 +41,12 @@ def main(argv):
     count = int(argv[1]) if len(argv) > 1 else 2048
     kind = argv[2] if len(argv) > 2 else "mix"
     reps = int(argv[3]) if len(argv) > 3 else 4
-    with_probs = not (len(argv) > 4 and argv[4] == "noprobs")
+    with_probs = "noprobs" not in argv[4:]
+    for a in argv[4:]:
+        if "x" in a and a.replace("x", "").isdigit():
+            tw, w = (int(v) for v in a.split("x"))
+            B.tqs_set_option(B.OPT_TEAM_WARPS, 11, tw)
+            B.tqs_set_option(B.OPT_WARPS_PER_CTA, 11, w)
     if kind == "chain":
         return chain(count, reps)
     if kind == "mix":
