@@ -375,9 +375,12 @@ tqs_status tqs_batch_run_measured(tqs_batch* b, tqs_c64* d_states, double* d_pro
                                   double* d_norms, const double* d_u, int32_t* d_outcomes,
                                   int use_graph, void* stream);
 
-/* Host-buffer form of tqs_batch_run: uploads the program, runs, and copies
+/* Host-buffer form of tqs_batch_run: uploads the program, runs, and delivers
  * the results into h_states / h_probs / h_norms (host memory, NULL to skip),
- * then synchronises `stream`.  Pinned host memory makes the copies faster. */
+ * then synchronises `stream`.  A buffer that is page-locked and mapped into
+ * the device's address space (cudaHostAlloc / cudaHostRegister, torch's
+ * pin_memory) is written by the kernel directly (over NVLink-C2C on
+ * Grace-Blackwell); any other buffer receives a copy from device memory. */
 tqs_status tqs_batch_run_host(tqs_batch* b, tqs_c64* h_states, double* h_probs,
                               double* h_norms, void* stream);
 

@@ -217,6 +217,28 @@ struct Program {
   int n_instr = 0;    // measure / reset instructions (one pass each)
   std::vector<float2> coef;  // custom unitaries' coefficients (wide passes)
   double cost = 0.0;
+  // Empty the program for reuse (keeps the vectors' capacity).
+  void reset() {
+    passes.clear();
+    ops.clear();
+    coef.clear();
+    n = 0;
+    nint = 4;
+    identity = 1;
+    out_scale = 1.0f;
+    gen_index = 0;
+    n_instr = 0;
+    cost = 0.0;
+  }
+};
+
+// A scheduled factor of the pass being built (compile_program).
+struct CompileRaw {
+  Mat2 u;
+  GClass cls;
+  bool is_h;    // unfused uncontrolled Hadamard
+  bool single;  // uncontrolled single-qubit factor
+  int t, c;     // physical bits (c = -1: uncontrolled)
 };
 
 // Full-state-vector program: per pass the tile bits, the far bits it tests
@@ -252,8 +274,12 @@ static void compile_program(int n, const std::vector<const Gate*>& gs_in, Progra
   // Leading uncontrolled X factors on a qubit that nothing has touched yet act
   // on the basis input |0...0> only by flipping that qubit: fold them into the
   // start index instead of spending butterflies (input |0...0> only).
-  std::vector<const Gate*> gs;
-  gs.reserve(gs_in.size());
+  // scratch reused across calls on this thread (no allocation per circuit)
+  static thread_local std::vector<const Gate*> gs_tls;
+  static thread_local std::vector<int> pending_tls, still_tls, order_tls;
+  static thread_local std::vector<CompileRaw> raw_tls;
+  std::vector<const Gate*>& gs = gs_tls;
+  gs.clear();
   P.gen_index = 0;
   {
     uint32_t touched = 0;
@@ -270,16 +296,13 @@ static void compile_program(int n, const std::vector<const Gate*>& gs_in, Progra
   int phys[32];
   for (int q = 0; q < 32; ++q) phys[q] = q;
   const uint32_t all = (n >= 32) ? 0xffffffffu : ((1u << n) - 1u);
-  std::vector<int> pending(gs.size()), still;
-  std::iota(pending.begin(), pending.end(), 0);
-  struct Raw {
-    Mat2 u;
-    GClass cls;
-    bool is_h;    // unfused uncontrolled Hadamard
-    bool single;  // uncontrolled single-qubit factor
-    int t, c;     // physical bits (c = -1: uncontrolled)
-  };
-  std::vector<Raw> raw;
+  std::vector<int>& pending = pending_tls;
+  std::vector<int>& still = still_tls;
+  pending.clear();
+  still.clear();
+  using Raw = CompileRaw;
+  std::vector<Raw>& raw = raw_tls;
+  raw.clear();
   int last_touch[32];
   int h_in_pass = 0;
   int h_carry = 0;  // Hadamard factors 2^-1/2 not yet applied
@@ -389,7 +412,8 @@ static void compile_program(int n, const std::vector<const Gate*>& gs_in, Progra
   };
   // An instruction is a barrier: the gates before it are scheduled (pending),
   // then it becomes a pass of its own, then scheduling resumes after it.
-  std::vector<int> order(gs.size());
+  std::vector<int>& order = order_tls;
+  order.resize(gs.size());
   std::iota(order.begin(), order.end(), 0);
   pending.clear();
   size_t next = 0;
@@ -518,13 +542,67 @@ using namespace tqs;
 
 // ------------------------------------------------------------------ circuit
 
+// Allocator whose value-initialisation is a no-op: resize() of a large image
+// leaves the new elements for the parallel fill to write.
+template <class T>
+struct NoInitAlloc : std::allocator<T> {
+  template <class U>
+  struct rebind { using other = NoInitAlloc<U>; };
+  NoInitAlloc() = default;
+  template <class U>
+  NoInitAlloc(const NoInitAlloc<U>&) noexcept {}
+  template <class U, class... Args>
+  void construct(U* p, Args&&... args) {
+    if constexpr (sizeof...(Args) == 0) ::new (static_cast<void*>(p)) U;
+    else ::new (static_cast<void*>(p)) U(std::forward<Args>(args)...);
+  }
+};
+
+// A compiled program's parts, wherever they are stored.
+struct ProgView {
+  int n = 0, nint = 4, n_instr = 0, identity = 1, gen_index = 0;
+  float out_scale = 1.0f;
+  double cost = 0.0;
+  uint8_t pos[16] = {};
+  const FusedPass* passes = nullptr;
+  size_t np = 0;
+  const FusedOp* ops = nullptr;
+  size_t no = 0;
+  const float2* coef = nullptr;
+  size_t nc = 0;
+};
+
+static ProgView view_meta(const Program& P) {
+  ProgView v;
+  v.n = P.n;
+  v.nint = P.nint;
+  v.n_instr = P.n_instr;
+  v.identity = P.identity;
+  v.gen_index = P.gen_index;
+  v.out_scale = P.out_scale;
+  v.cost = P.cost;
+  std::memcpy(v.pos, P.pos, 16);
+  v.np = P.passes.size();
+  v.no = P.ops.size();
+  v.nc = P.coef.size();
+  return v;
+}
+
+static ProgView view_of(const Program& P) {
+  ProgView v = view_meta(P);
+  v.passes = P.passes.data();
+  v.ops = P.ops.data();
+  v.coef = P.coef.data();
+  return v;
+}
+
 // Device image of one or more programs:
 // [FusedCirc x count][FusedPass...][FusedOp...][custom coefficients (float2)...]
 struct Image {
-  std::vector<FusedCirc> circs;
-  std::vector<FusedPass> passes;
-  std::vector<FusedOp> ops;
-  std::vector<float2> coef;
+  std::vector<FusedCirc, NoInitAlloc<FusedCirc>> circs;
+  std::vector<FusedPass, NoInitAlloc<FusedPass>> passes;
+  std::vector<FusedOp, NoInitAlloc<FusedOp>> ops;
+  std::vector<float2, NoInitAlloc<float2>> coef;
   size_t circ_bytes() const { return circs.size() * sizeof(FusedCirc); }
   size_t pass_bytes() const { return passes.size() * sizeof(FusedPass); }
   size_t op_bytes() const { return ops.size() * sizeof(FusedOp); }
@@ -547,13 +625,13 @@ struct Image {
   }
   // Write program P as circuit i whose passes start at pass0 and ops at op0
   // (the arrays are sized by the caller).
-  void fill(int i, const Program& P, int64_t out_off, int64_t pass0, int64_t op0,
+  void fill(int i, const ProgView& P, int64_t out_off, int64_t pass0, int64_t op0,
             int64_t instr0 = 0, int64_t coef0 = 0) {
     FusedCirc fc{};
     fc.n = P.n;
     fc.nint = P.nint;
     fc.pass_begin = static_cast<int32_t>(pass0);
-    fc.pass_count = static_cast<int32_t>(P.passes.size());
+    fc.pass_count = static_cast<int32_t>(P.np);
     fc.out_off = out_off;
     fc.team = team_for(P.nint);
     fc.identity = P.identity;
@@ -562,12 +640,10 @@ struct Image {
     fc.out_scale = P.out_scale;
     fc.gen_index = P.gen_index;
     circs[i] = fc;
-    for (size_t k = 0; k < P.passes.size(); ++k)
+    for (size_t k = 0; k < P.np; ++k)
       passes[static_cast<size_t>(pass0) + k] = rebase(P.passes[k], op0, instr0, coef0);
-    if (!P.ops.empty())
-      std::memcpy(&ops[static_cast<size_t>(op0)], P.ops.data(), P.ops.size() * sizeof(FusedOp));
-    if (!P.coef.empty())
-      std::memcpy(&coef[static_cast<size_t>(coef0)], P.coef.data(), P.coef.size() * sizeof(float2));
+    if (P.no) std::memcpy(&ops[static_cast<size_t>(op0)], P.ops, P.no * sizeof(FusedOp));
+    if (P.nc) std::memcpy(&coef[static_cast<size_t>(coef0)], P.coef, P.nc * sizeof(float2));
   }
   void add(const Program& P, int64_t out_off) {
     FusedCirc fc{};
@@ -842,11 +918,17 @@ tqs_status tqs_circuit_steps(const tqs_circuit* c, int* h_step_of_gate) {
 }  // extern "C"
 
 // Gates in step order (stable within a step).
-static std::vector<const Gate*> step_order(const std::vector<Gate>& gates) {
-  std::vector<const Gate*> v;
-  v.reserve(gates.size());
-  for (const Gate& g : gates) v.push_back(&g);
-  std::stable_sort(v.begin(), v.end(), [](const Gate* a, const Gate* b) { return a->step < b->step; });
+static const std::vector<const Gate*>& step_order(const std::vector<Gate>& gates) {
+  // counting sort by step, stable, into scratch reused on this thread
+  static thread_local std::vector<const Gate*> v;
+  static thread_local std::vector<int> start;
+  int nsteps = 0;
+  for (const Gate& g : gates) nsteps = std::max(nsteps, g.step + 1);
+  start.assign(static_cast<size_t>(nsteps) + 1, 0);
+  for (const Gate& g : gates) ++start[g.step + 1];
+  for (int k = 0; k < nsteps; ++k) start[k + 1] += start[k];
+  v.resize(gates.size());
+  for (const Gate& g : gates) v[start[g.step]++] = &g;
   return v;
 }
 
@@ -1295,7 +1377,7 @@ static void parallel_for(int count, int grain, F body) {
   for (std::thread& th : pool) th.join();
 }
 
-static tqs_status batch_finish(tqs_batch* b, std::vector<Program>& progs) {
+static tqs_status batch_finish(tqs_batch* b, const std::vector<ProgView>& progs) {
   b->count = static_cast<int>(progs.size());
   b->offsets.assign(b->count + 1, 0);
   std::vector<int64_t> pass0(b->count + 1, 0), op0(b->count + 1, 0), coef0(b->count + 1, 0);
@@ -1303,9 +1385,9 @@ static tqs_status batch_finish(tqs_batch* b, std::vector<Program>& progs) {
   for (int i = 0; i < b->count; ++i) {
     b->offsets[i + 1] = b->offsets[i] + (int64_t(1) << progs[i].n);
     b->instr_off[i + 1] = b->instr_off[i] + progs[i].n_instr;
-    pass0[i + 1] = pass0[i] + static_cast<int64_t>(progs[i].passes.size());
-    op0[i + 1] = op0[i] + static_cast<int64_t>(progs[i].ops.size());
-    coef0[i + 1] = coef0[i] + static_cast<int64_t>(progs[i].coef.size());
+    pass0[i + 1] = pass0[i] + static_cast<int64_t>(progs[i].np);
+    op0[i + 1] = op0[i] + static_cast<int64_t>(progs[i].no);
+    coef0[i + 1] = coef0[i] + static_cast<int64_t>(progs[i].nc);
   }
   if (b->instr_off.back() > 0xFFFFFFFFll || op0.back() > 0xFFFFFFFFll || coef0.back() > 0xFFFFFFFFll)
     return fail(TQS_ERR_ARG, "tqs_batch: program too large for 32-bit offsets");
@@ -1348,7 +1430,9 @@ tqs_status tqs_batch_create(tqs_circuit* const* cs, int count, tqs_batch** out) 
     compile_program(cs[i]->n, step_order(cs[i]->gates), progs[i]);
     b->total_steps += cs[i]->nsteps;
   }
-  tqs_status s = batch_finish(b.get(), progs);
+  std::vector<ProgView> views(count);
+  for (int i = 0; i < count; ++i) views[i] = view_of(progs[i]);
+  tqs_status s = batch_finish(b.get(), views);
   if (s != TQS_OK) return s;
   *out = b.release();
   return TQS_OK;
@@ -1362,10 +1446,21 @@ tqs_status tqs_batch_create_packed(int count, const int32_t* h_nq, const int64_t
   *out = nullptr;
   std::unique_ptr<tqs_batch> b(new (std::nothrow) tqs_batch());
   if (!b) return fail(TQS_ERR_NOMEM, "tqs_batch_create_packed: out of host memory");
-  std::vector<Program> progs(count);
+  std::vector<ProgView> views(count);
   std::vector<int> nsteps(count, 0);
+  std::vector<int> owner(count, 0);
   // Circuits are independent: compile them on all host cores.  Each worker
-  // records its first failure; the lowest failing circuit index is reported.
+  // compiles into one reused Program and appends the result to its own
+  // buffers (no allocation per circuit); views into those buffers are taken
+  // once every worker is done.  Each worker records its first failure; the
+  // lowest failing circuit index is reported.
+  struct WorkerBuf {
+    std::vector<FusedPass> passes;
+    std::vector<FusedOp> ops;
+    std::vector<float2> coef;
+  };
+  const int nworkers = std::max(1, std::min(count / 64, 32));
+  std::vector<WorkerBuf> bufs(static_cast<size_t>(nworkers));
   struct Failure {
     int index = -1;
     tqs_status status = TQS_OK;
@@ -1374,9 +1469,13 @@ tqs_status tqs_batch_create_packed(int count, const int32_t* h_nq, const int64_t
   std::mutex fail_mu;
   Failure first;
   std::atomic<int> next_circuit{0};
+  std::atomic<int> next_worker{0};
   auto work = [&]() {
-    std::vector<Gate> gates;
-    std::vector<int> last;
+    const int w = next_worker.fetch_add(1);
+    WorkerBuf& buf = bufs[static_cast<size_t>(w)];
+    static thread_local std::vector<Gate> gates;
+    static thread_local std::vector<int> last;
+    static thread_local Program tp;
     for (;;) {
       const int i = next_circuit.fetch_add(1);
       if (i >= count) return;
@@ -1414,13 +1513,31 @@ tqs_status tqs_batch_create_packed(int count, const int32_t* h_nq, const int64_t
         continue;
       }
       for (int q = 0; q < n; ++q) nsteps[i] = std::max(nsteps[i], last[q] + 1);
-      compile_program(n, step_order(gates), progs[i]);
+      tp.reset();
+      compile_program(n, step_order(gates), tp);
+      ProgView v = view_meta(tp);
+      // offsets into this worker's buffers, turned into pointers later
+      v.passes = reinterpret_cast<const FusedPass*>(buf.passes.size());
+      v.ops = reinterpret_cast<const FusedOp*>(buf.ops.size());
+      v.coef = reinterpret_cast<const float2*>(buf.coef.size());
+      buf.passes.insert(buf.passes.end(), tp.passes.begin(), tp.passes.end());
+      buf.ops.insert(buf.ops.end(), tp.ops.begin(), tp.ops.end());
+      buf.coef.insert(buf.coef.end(), tp.coef.begin(), tp.coef.end());
+      views[i] = v;
+      owner[i] = w;
     }
   };
-  parallel_for(std::max(1, std::min(count / 64, 32)), 1, [&](int) { work(); });
+  parallel_for(nworkers, 1, [&](int) { work(); });
   if (first.index >= 0) return fail(first.status, "%s", first.message.c_str());
-  for (int i = 0; i < count; ++i) b->total_steps += nsteps[i];
-  tqs_status s = batch_finish(b.get(), progs);
+  for (int i = 0; i < count; ++i) {
+    const WorkerBuf& buf = bufs[static_cast<size_t>(owner[i])];
+    ProgView& v = views[i];
+    v.passes = buf.passes.data() + reinterpret_cast<size_t>(v.passes);
+    v.ops = buf.ops.data() + reinterpret_cast<size_t>(v.ops);
+    v.coef = buf.coef.data() + reinterpret_cast<size_t>(v.coef);
+    b->total_steps += nsteps[i];
+  }
+  tqs_status s = batch_finish(b.get(), views);
   if (s != TQS_OK) return s;
   *out = b.release();
   return TQS_OK;
@@ -1584,6 +1701,37 @@ tqs_status tqs_batch_instructions(const tqs_batch* b, int64_t* h_off) {
   return TQS_OK;
 }
 
+}  // extern "C"
+
+// Device alias of a host range the GPU can write directly: page-locked,
+// mapped into the device's address space, one contiguous alias over the whole
+// range (on Grace-Blackwell the kernel's stores then cross NVLink-C2C straight
+// into host memory).  nullptr when any check fails; the caller then stages
+// through device memory.
+static void* mapped_alias(void* h, size_t bytes) {
+  if (!h || bytes == 0) return nullptr;
+  char* first = static_cast<char*>(h);
+  char* last = first + bytes - 1;
+  void* d0 = nullptr;
+  void* d1 = nullptr;
+  for (char* p : {first, last}) {
+    cudaPointerAttributes a{};
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess || a.type != cudaMemoryTypeHost) {
+      cudaGetLastError();
+      return nullptr;
+    }
+  }
+  if (cudaHostGetDevicePointer(&d0, first, 0) != cudaSuccess ||
+      cudaHostGetDevicePointer(&d1, last, 0) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  if (static_cast<char*>(d1) != static_cast<char*>(d0) + (bytes - 1) || !aligned16(d0)) return nullptr;
+  return d0;
+}
+
+extern "C" {
+
 tqs_status tqs_batch_run_host(tqs_batch* b, tqs_c64* h_states, double* h_probs, double* h_norms,
                               void* stream) {
   if (!b) return fail(TQS_ERR_ARG, "tqs_batch_run_host: batch is NULL");
@@ -1594,34 +1742,39 @@ tqs_status tqs_batch_run_host(tqs_batch* b, tqs_c64* h_states, double* h_probs, 
   // Everything this call needs on the device (the program is its input) comes
   // stream-ordered from the device's memory pool and goes back to it at the end.
   const size_t amps = static_cast<size_t>(b->offsets.back());
+  // outputs whose host buffers the GPU can write directly skip the device copy
+  float2* zs = static_cast<float2*>(mapped_alias(h_states, amps * sizeof(float2)));
+  double* zp = static_cast<double*>(mapped_alias(h_probs, amps * sizeof(double)));
+  double* zn = static_cast<double*>(mapped_alias(h_norms, size_t(b->count) * sizeof(double)));
   const size_t order_off = (b->img.bytes() + 255) & ~size_t(255);
   const size_t counter_off = (order_off + b->order.size() * sizeof(int32_t) + 255) & ~size_t(255);
   const size_t states_off = counter_off + 256;
-  const size_t probs_off = (states_off + amps * sizeof(float2) + 255) & ~size_t(255);
-  const size_t norms_off = (probs_off + (h_probs ? amps * sizeof(double) : 0) + 255) & ~size_t(255);
-  const size_t total = norms_off + size_t(b->count) * sizeof(double);
+  const size_t probs_off = (states_off + (zs ? 0 : amps * sizeof(float2)) + 255) & ~size_t(255);
+  const size_t norms_off = (probs_off + (h_probs && !zp ? amps * sizeof(double) : 0) + 255) & ~size_t(255);
+  const size_t total = norms_off + (zn ? 0 : size_t(b->count) * sizeof(double));
   for (int t = 0; t < 3; ++t) b->plans[t] = plan_for(t, b->max_nint[t], b->n_team[t], 0);
   const size_t gscr = b->n_team[TEAM_GLOBAL]
                           ? size_t(b->plans[TEAM_GLOBAL].grid) * (size_t(1) << kGlobalSlotQ) * sizeof(float2)
                           : 0;
   char* base = nullptr;
-  TQS_CUDA(cudaMallocAsync(reinterpret_cast<void**>(&base), total + gscr, s),
+  TQS_CUDA(cudaMallocAsync(reinterpret_cast<void**>(&base), ((total + 255) & ~size_t(255)) + gscr, s),
            "tqs_batch_run_host: cudaMallocAsync");
   TQS_CUDA(b->img.upload(base, s), "tqs_batch_run_host: upload program");
   TQS_CUDA(cudaMemcpyAsync(base + order_off, b->order.data(), b->order.size() * sizeof(int32_t),
                            cudaMemcpyHostToDevice, s),
            "tqs_batch_run_host: upload order");
-  float2* ds = reinterpret_cast<float2*>(base + states_off);
-  double* dp = h_probs ? reinterpret_cast<double*>(base + probs_off) : nullptr;
-  double* dn = reinterpret_cast<double*>(base + norms_off);
+  float2* ds = zs ? zs : reinterpret_cast<float2*>(base + states_off);
+  double* dp = zp ? zp : (h_probs ? reinterpret_cast<double*>(base + probs_off) : nullptr);
+  double* dn = zn ? zn : reinterpret_cast<double*>(base + norms_off);
+  const size_t gscr_at = (total + 255) & ~size_t(255);
   tqs_status st = batch_enqueue_at(b, base, order_off, counter_off,
-                                   reinterpret_cast<float2*>(base + total), ds, dp, dn, s);
+                                   reinterpret_cast<float2*>(base + gscr_at), ds, dp, dn, s);
   if (st != TQS_OK) return st;
-  if (h_states)
+  if (h_states && !zs)
     TQS_CUDA(cudaMemcpyAsync(h_states, ds, amps * sizeof(float2), cudaMemcpyDeviceToHost, s), "D2H states");
-  if (h_probs)
+  if (h_probs && !zp)
     TQS_CUDA(cudaMemcpyAsync(h_probs, dp, amps * sizeof(double), cudaMemcpyDeviceToHost, s), "D2H probs");
-  if (h_norms)
+  if (h_norms && !zn)
     TQS_CUDA(cudaMemcpyAsync(h_norms, dn, size_t(b->count) * sizeof(double), cudaMemcpyDeviceToHost, s),
              "D2H norms");
   TQS_CUDA(cudaFreeAsync(base, s), "tqs_batch_run_host: cudaFreeAsync");

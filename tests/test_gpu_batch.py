@@ -123,3 +123,25 @@ def test_host_buffer_entry_point():
         B.tqs_batch_destroy(b)
     assert np.array_equal(hs.view(np.uint32), st.view(np.uint32))
     assert np.array_equal(hp, pr) and np.array_equal(hn, nm)
+
+
+@pytest.mark.parametrize("mode", ["pinned", "mixed"])
+def test_host_buffer_entry_point_pinned(mode):
+    """Page-locked host buffers are written by the kernel directly (no device
+    copy); results equal the device run bit for bit.  In "mixed", only the
+    probabilities are page-locked (states and norms take the copy path)."""
+    circs = mixed_workload(40, 66)
+    offs, [(st, pr, nm)] = run_batch(circs)
+    b = B.tqs_batch_create_packed(*B.pack_ops(circs))
+    try:
+        count, total, _ = B.tqs_batch_info(b)
+        pin = (lambda t: t.pin_memory()) if mode == "pinned" else (lambda t: t)
+        hs = pin(torch.empty(total, dtype=torch.complex64))
+        hp = torch.empty(total, dtype=torch.float64).pin_memory()
+        hn = pin(torch.empty(count, dtype=torch.float64))
+        for _ in range(2):
+            B.tqs_batch_run_host(b, hs, hp, hn)
+    finally:
+        B.tqs_batch_destroy(b)
+    assert np.array_equal(hs.numpy().view(np.uint32), st.view(np.uint32))
+    assert np.array_equal(hp.numpy(), pr) and np.array_equal(hn.numpy(), nm)
