@@ -5,8 +5,12 @@
 // are added; the data provider supplies each operation's matrix separately
 // from the circuit structure.  Sec. 5.3: stages 1-3 (steps, operations per
 // step, operation data) run here; stages 4-6 run in the kernels.
+#include <unistd.h>
+
 #include <algorithm>
 #include <atomic>
+#include <condition_variable>
+#include <functional>
 #include <cmath>
 #include <complex>
 #include <cstdarg>
@@ -15,6 +19,7 @@
 #include <cstring>
 #include <deque>
 #include <memory>
+#include <new>
 #include <mutex>
 #include <numeric>
 #include <string>
@@ -558,55 +563,139 @@ struct NoInitAlloc : std::allocator<T> {
   }
 };
 
-// A compiled program's parts, wherever they are stored.
-struct ProgView {
+// Allocator for image buffers: host memory that is page-locked when the CUDA
+// runtime allows it (cudaHostRegister), so that uploads of the image are
+// asynchronous DMA rather than copies through a driver staging buffer.  It
+// falls back to plain memory (no GPU, or registration refused).  Image buffers
+// are recycled, so the registration cost is paid once per buffer.
+template <class T>
+struct LockedAlloc {
+  using value_type = T;
+  LockedAlloc() = default;
+  template <class U>
+  LockedAlloc(const LockedAlloc<U>&) noexcept {}
+  template <class U>
+  struct rebind { using other = LockedAlloc<U>; };
+  T* allocate(size_t n) {
+    const size_t bytes = std::max<size_t>(n * sizeof(T), 1);
+    void* p = std::malloc(bytes);
+    if (!p) throw std::bad_alloc();
+    if (bytes >= (size_t(1) << 16) && cudaHostRegister(p, bytes, cudaHostRegisterDefault) != cudaSuccess)
+      cudaGetLastError();
+    return static_cast<T*>(p);
+  }
+  void deallocate(T* p, size_t n) {
+    if (n * sizeof(T) >= (size_t(1) << 16) && cudaHostUnregister(p) != cudaSuccess) cudaGetLastError();
+    std::free(p);
+  }
+  template <class U, class... Args>
+  void construct(U* p, Args&&... args) {
+    if constexpr (sizeof...(Args) == 0) ::new (static_cast<void*>(p)) U;
+    else ::new (static_cast<void*>(p)) U(std::forward<Args>(args)...);
+  }
+  template <class U>
+  bool operator==(const LockedAlloc<U>&) const { return true; }
+  template <class U>
+  bool operator!=(const LockedAlloc<U>&) const { return false; }
+};
+
+// Passes, ops and custom coefficients of a run of programs (one host worker's
+// share of a batch, or all of a small image).
+struct ImageSeg {
+  std::vector<FusedPass, LockedAlloc<FusedPass>> passes;
+  std::vector<FusedOp, LockedAlloc<FusedOp>> ops;
+  std::vector<float2, LockedAlloc<float2>> coef;
+  void clear() {
+    passes.clear();
+    ops.clear();
+    coef.clear();
+  }
+};
+
+// Where a compiled program of a batch sits before the image is assembled:
+// its header fields and its passes / ops / coefficients at local offsets of
+// segment `seg` (passes still numbered program-locally).
+struct CircMeta {
   int n = 0, nint = 4, n_instr = 0, identity = 1, gen_index = 0;
   float out_scale = 1.0f;
   double cost = 0.0;
   uint8_t pos[16] = {};
-  const FusedPass* passes = nullptr;
-  size_t np = 0;
-  const FusedOp* ops = nullptr;
-  size_t no = 0;
-  const float2* coef = nullptr;
-  size_t nc = 0;
+  int seg = 0;
+  size_t lp = 0, np = 0, lo = 0, no = 0, lc = 0, nc = 0;
 };
 
-static ProgView view_meta(const Program& P) {
-  ProgView v;
-  v.n = P.n;
-  v.nint = P.nint;
-  v.n_instr = P.n_instr;
-  v.identity = P.identity;
-  v.gen_index = P.gen_index;
-  v.out_scale = P.out_scale;
-  v.cost = P.cost;
-  std::memcpy(v.pos, P.pos, 16);
-  v.np = P.passes.size();
-  v.no = P.ops.size();
-  v.nc = P.coef.size();
-  return v;
+// Append program P's parts to segment sg (program-local numbering) and
+// describe where they went.
+static CircMeta append_program(const Program& P, ImageSeg& sg, int seg) {
+  CircMeta m;
+  m.n = P.n;
+  m.nint = P.nint;
+  m.n_instr = P.n_instr;
+  m.identity = P.identity;
+  m.gen_index = P.gen_index;
+  m.out_scale = P.out_scale;
+  m.cost = P.cost;
+  std::memcpy(m.pos, P.pos, 16);
+  m.seg = seg;
+  m.lp = sg.passes.size();
+  m.np = P.passes.size();
+  m.lo = sg.ops.size();
+  m.no = P.ops.size();
+  m.lc = sg.coef.size();
+  m.nc = P.coef.size();
+  sg.passes.insert(sg.passes.end(), P.passes.begin(), P.passes.end());
+  sg.ops.insert(sg.ops.end(), P.ops.begin(), P.ops.end());
+  sg.coef.insert(sg.coef.end(), P.coef.begin(), P.coef.end());
+  return m;
 }
 
-static ProgView view_of(const Program& P) {
-  ProgView v = view_meta(P);
-  v.passes = P.passes.data();
-  v.ops = P.ops.data();
-  v.coef = P.coef.data();
-  return v;
+// Recycled segments: a destroyed batch hands its buffers back, so a steady
+// stream of batches reuses memory that is already mapped.
+static std::mutex g_seg_mu;
+static std::vector<ImageSeg> g_seg_pool;
+
+static ImageSeg take_seg() {
+  std::lock_guard<std::mutex> lock(g_seg_mu);
+  if (g_seg_pool.empty()) return ImageSeg();
+  ImageSeg sg = std::move(g_seg_pool.back());
+  g_seg_pool.pop_back();
+  sg.clear();
+  return sg;
+}
+
+static void give_segs(std::vector<ImageSeg>& segs) {
+  std::lock_guard<std::mutex> lock(g_seg_mu);
+  for (ImageSeg& sg : segs)
+    if (g_seg_pool.size() < 64) g_seg_pool.push_back(std::move(sg));
+  segs.clear();
 }
 
 // Device image of one or more programs:
 // [FusedCirc x count][FusedPass...][FusedOp...][custom coefficients (float2)...]
+// The passes, ops and coefficients are held as consecutive segments.
 struct Image {
-  std::vector<FusedCirc, NoInitAlloc<FusedCirc>> circs;
-  std::vector<FusedPass, NoInitAlloc<FusedPass>> passes;
-  std::vector<FusedOp, NoInitAlloc<FusedOp>> ops;
-  std::vector<float2, NoInitAlloc<float2>> coef;
+  std::vector<FusedCirc, LockedAlloc<FusedCirc>> circs;
+  std::vector<ImageSeg> segs;
+  size_t npass = 0, nop = 0, ncoef = 0;  // totals over the segments
+  ~Image() { give_segs(segs); }
+  Image() = default;
+  Image(const Image&) = delete;
+  Image& operator=(const Image&) = delete;
+  Image(Image&& o) noexcept { *this = std::move(o); }
+  Image& operator=(Image&& o) noexcept {
+    give_segs(segs);
+    circs = std::move(o.circs);
+    segs = std::move(o.segs);
+    npass = o.npass;
+    nop = o.nop;
+    ncoef = o.ncoef;
+    o.npass = o.nop = o.ncoef = 0;
+    return *this;
+  }
   size_t circ_bytes() const { return circs.size() * sizeof(FusedCirc); }
-  size_t pass_bytes() const { return passes.size() * sizeof(FusedPass); }
-  size_t op_bytes() const { return ops.size() * sizeof(FusedOp); }
-  size_t coef_bytes() const { return coef.size() * sizeof(float2); }
+  size_t pass_bytes() const { return npass * sizeof(FusedPass); }
+  size_t op_bytes() const { return nop * sizeof(FusedOp); }
+  size_t coef_bytes() const { return ncoef * sizeof(float2); }
   size_t coef_at() const { return circ_bytes() + pass_bytes() + op_bytes(); }
   size_t bytes() const { return coef_at() + coef_bytes(); }
   // Device pointers of the parts of an image uploaded at `base`.
@@ -623,33 +712,11 @@ struct Image {
     else ps.op_begin += static_cast<uint32_t>(op0);
     return ps;
   }
-  // Write program P as circuit i whose passes start at pass0 and ops at op0
-  // (the arrays are sized by the caller).
-  void fill(int i, const ProgView& P, int64_t out_off, int64_t pass0, int64_t op0,
-            int64_t instr0 = 0, int64_t coef0 = 0) {
+  static FusedCirc circ_of(const Program& P, int64_t pass0, int64_t out_off) {
     FusedCirc fc{};
     fc.n = P.n;
     fc.nint = P.nint;
     fc.pass_begin = static_cast<int32_t>(pass0);
-    fc.pass_count = static_cast<int32_t>(P.np);
-    fc.out_off = out_off;
-    fc.team = team_for(P.nint);
-    fc.identity = P.identity;
-    std::memcpy(fc.pos, P.pos, 16);
-    fc.init = nullptr;
-    fc.out_scale = P.out_scale;
-    fc.gen_index = P.gen_index;
-    circs[i] = fc;
-    for (size_t k = 0; k < P.np; ++k)
-      passes[static_cast<size_t>(pass0) + k] = rebase(P.passes[k], op0, instr0, coef0);
-    if (P.no) std::memcpy(&ops[static_cast<size_t>(op0)], P.ops, P.no * sizeof(FusedOp));
-    if (P.nc) std::memcpy(&coef[static_cast<size_t>(coef0)], P.coef, P.nc * sizeof(float2));
-  }
-  void add(const Program& P, int64_t out_off) {
-    FusedCirc fc{};
-    fc.n = P.n;
-    fc.nint = P.nint;
-    fc.pass_begin = static_cast<int32_t>(passes.size());
     fc.pass_count = static_cast<int32_t>(P.passes.size());
     fc.out_off = out_off;
     fc.team = team_for(P.nint);
@@ -658,30 +725,55 @@ struct Image {
     fc.init = nullptr;
     fc.out_scale = P.out_scale;
     fc.gen_index = P.gen_index;
-    const int64_t op_base = static_cast<int64_t>(ops.size());
-    const int64_t coef_base = static_cast<int64_t>(coef.size());
-    for (const FusedPass& ps : P.passes) passes.push_back(rebase(ps, op_base, 0, coef_base));
-    ops.insert(ops.end(), P.ops.begin(), P.ops.end());
-    coef.insert(coef.end(), P.coef.begin(), P.coef.end());
-    circs.push_back(fc);
+    return fc;
+  }
+  // Append program P (its outputs at amplitude offset out_off).
+  void add(const Program& P, int64_t out_off) {
+    if (segs.empty()) segs.push_back(take_seg());
+    ImageSeg& sg = segs.back();
+    circs.push_back(circ_of(P, static_cast<int64_t>(npass), out_off));
+    for (const FusedPass& ps : P.passes)
+      sg.passes.push_back(rebase(ps, static_cast<int64_t>(nop), 0, static_cast<int64_t>(ncoef)));
+    sg.ops.insert(sg.ops.end(), P.ops.begin(), P.ops.end());
+    sg.coef.insert(sg.coef.end(), P.coef.begin(), P.coef.end());
+    npass += P.passes.size();
+    nop += P.ops.size();
+    ncoef += P.coef.size();
+  }
+  // Copy the image, laid out as on the device, to host memory at dst.
+  void copy_to(char* dst) const {
+    std::memcpy(dst, circs.data(), circ_bytes());
+    size_t p = circ_bytes(), o = p + pass_bytes(), c = coef_at();
+    for (const ImageSeg& sg : segs) {
+      if (!sg.passes.empty()) std::memcpy(dst + p, sg.passes.data(), sg.passes.size() * sizeof(FusedPass));
+      if (!sg.ops.empty()) std::memcpy(dst + o, sg.ops.data(), sg.ops.size() * sizeof(FusedOp));
+      if (!sg.coef.empty()) std::memcpy(dst + c, sg.coef.data(), sg.coef.size() * sizeof(float2));
+      p += sg.passes.size() * sizeof(FusedPass);
+      o += sg.ops.size() * sizeof(FusedOp);
+      c += sg.coef.size() * sizeof(float2);
+    }
   }
   cudaError_t upload(void* dst, cudaStream_t s) const {
     char* d = static_cast<char*>(dst);
     cudaError_t e = cudaMemcpyAsync(d, circs.data(), circ_bytes(), cudaMemcpyHostToDevice, s);
-    if (e != cudaSuccess) return e;
-    if (!passes.empty())
-      e = cudaMemcpyAsync(d + circ_bytes(), passes.data(), pass_bytes(), cudaMemcpyHostToDevice, s);
-    if (e != cudaSuccess) return e;
-    if (!ops.empty())
-      e = cudaMemcpyAsync(d + circ_bytes() + pass_bytes(), ops.data(), op_bytes(),
-                          cudaMemcpyHostToDevice, s);
-    if (e != cudaSuccess) return e;
-    if (!coef.empty())
-      e = cudaMemcpyAsync(d + coef_at(), coef.data(), coef_bytes(), cudaMemcpyHostToDevice, s);
+    size_t p = circ_bytes(), o = p + pass_bytes(), c = coef_at();
+    for (const ImageSeg& sg : segs) {
+      if (e == cudaSuccess && !sg.passes.empty())
+        e = cudaMemcpyAsync(d + p, sg.passes.data(), sg.passes.size() * sizeof(FusedPass),
+                            cudaMemcpyHostToDevice, s);
+      if (e == cudaSuccess && !sg.ops.empty())
+        e = cudaMemcpyAsync(d + o, sg.ops.data(), sg.ops.size() * sizeof(FusedOp),
+                            cudaMemcpyHostToDevice, s);
+      if (e == cudaSuccess && !sg.coef.empty())
+        e = cudaMemcpyAsync(d + c, sg.coef.data(), sg.coef.size() * sizeof(float2),
+                            cudaMemcpyHostToDevice, s);
+      p += sg.passes.size() * sizeof(FusedPass);
+      o += sg.ops.size() * sizeof(FusedOp);
+      c += sg.coef.size() * sizeof(float2);
+    }
     return e;
   }
 };
-
 
 struct tqs_circuit {
   int n = 0;
@@ -1357,47 +1449,138 @@ struct tqs_batch {
 };
 
 // Run body(i) for i in [0, count) on the host cores.
+// Persistent host worker threads for parallel_for: created on first use and
+// kept, so per-thread scratch (compile buffers) survives from one batch to
+// the next.  One job runs at a time; the calling thread takes part.  A child
+// process after fork() gets its own pool.
+class HostPool {
+ public:
+  static HostPool& get() {
+    static std::mutex mu;
+    static HostPool* pool = nullptr;
+    static pid_t owner = 0;
+    std::lock_guard<std::mutex> lock(mu);
+    if (!pool || owner != getpid()) {  // the parent's threads do not exist after fork()
+      pool = new HostPool();           // kept until exit: its threads wait for work
+      owner = getpid();
+    }
+    return *pool;
+  }
+  int size() const { return static_cast<int>(threads_.size()) + 1; }
+  // body(i) for i in [0, count) on up to `width` threads (the caller included).
+  void run(int count, int width, const std::function<void(int)>& body) {
+    std::lock_guard<std::mutex> one_job(run_mu_);
+    {
+      std::lock_guard<std::mutex> lock(mu_);
+      body_ = &body;
+      count_ = count;
+      next_.store(0);
+      width_ = std::min(width, size());
+      pending_ = width_ - 1;
+      ++generation_;
+    }
+    cv_.notify_all();
+    drain();
+    std::unique_lock<std::mutex> lock(mu_);
+    done_cv_.wait(lock, [&] { return pending_ == 0; });
+    body_ = nullptr;
+  }
+
+ private:
+  HostPool() {
+    const int hw = static_cast<int>(std::max(1u, std::thread::hardware_concurrency()));
+    for (int t = 1; t < std::min(hw, 32); ++t) threads_.emplace_back([this, t] { loop(t); });
+  }
+  void drain() {
+    for (int i = next_.fetch_add(1); i < count_; i = next_.fetch_add(1)) (*body_)(i);
+  }
+  void loop(int index) {
+    uint64_t seen = 0;
+    for (;;) {
+      std::unique_lock<std::mutex> lock(mu_);
+      cv_.wait(lock, [&] { return generation_ != seen; });
+      seen = generation_;
+      const bool take_part = index < width_;
+      lock.unlock();
+      if (!take_part) continue;
+      drain();
+      lock.lock();
+      if (--pending_ == 0) done_cv_.notify_all();
+    }
+  }
+  std::vector<std::thread> threads_;
+  std::mutex run_mu_, mu_;
+  std::condition_variable cv_, done_cv_;
+  const std::function<void(int)>* body_ = nullptr;
+  int count_ = 0, width_ = 1, pending_ = 0;
+  uint64_t generation_ = 0;
+  std::atomic<int> next_{0};
+};
+
+// Run body(i) for i in [0, count) on the host cores (at most TQS_HOST_THREADS
+// of them when that variable is set), `grain` items per thread at least.
 template <class F>
 static void parallel_for(int count, int grain, F body) {
   int hw = static_cast<int>(std::max(1u, std::thread::hardware_concurrency()));
   if (const char* env = std::getenv("TQS_HOST_THREADS")) hw = std::max(1, std::atoi(env));
-  const int nthreads = std::min({hw, 32, std::max(1, count / std::max(1, grain))});
-  std::atomic<int> next{0};
-  auto work = [&]() {
-    for (int i = next.fetch_add(1); i < count; i = next.fetch_add(1)) body(i);
-  };
-  if (nthreads <= 1) {
-    work();
+  const int width = std::min({hw, 32, std::max(1, count / std::max(1, grain))});
+  if (width <= 1) {
+    for (int i = 0; i < count; ++i) body(i);
     return;
   }
-  std::vector<std::thread> pool;
-  pool.reserve(nthreads - 1);
-  for (int t = 1; t < nthreads; ++t) pool.emplace_back(work);
-  work();
-  for (std::thread& th : pool) th.join();
+  const std::function<void(int)> fn = body;
+  HostPool::get().run(count, width, fn);
 }
 
-static tqs_status batch_finish(tqs_batch* b, const std::vector<ProgView>& progs) {
+// Assemble the batch image from compiled programs held in segments: the
+// device arrays are the segments concatenated in order, so a program's global
+// offsets are its segment's base plus its local offsets.  Headers are written
+// and passes renumbered in parallel, in place.
+static tqs_status batch_finish(tqs_batch* b, const std::vector<CircMeta>& progs,
+                               std::vector<ImageSeg>&& segs) {
   b->count = static_cast<int>(progs.size());
   b->offsets.assign(b->count + 1, 0);
-  std::vector<int64_t> pass0(b->count + 1, 0), op0(b->count + 1, 0), coef0(b->count + 1, 0);
   b->instr_off.assign(b->count + 1, 0);
   for (int i = 0; i < b->count; ++i) {
     b->offsets[i + 1] = b->offsets[i] + (int64_t(1) << progs[i].n);
     b->instr_off[i + 1] = b->instr_off[i] + progs[i].n_instr;
-    pass0[i + 1] = pass0[i] + static_cast<int64_t>(progs[i].np);
-    op0[i + 1] = op0[i] + static_cast<int64_t>(progs[i].no);
-    coef0[i + 1] = coef0[i] + static_cast<int64_t>(progs[i].nc);
   }
-  if (b->instr_off.back() > 0xFFFFFFFFll || op0.back() > 0xFFFFFFFFll || coef0.back() > 0xFFFFFFFFll)
+  const size_t nseg = segs.size();
+  std::vector<int64_t> pbase(nseg + 1, 0), obase(nseg + 1, 0), cbase(nseg + 1, 0);
+  for (size_t w = 0; w < nseg; ++w) {
+    pbase[w + 1] = pbase[w] + static_cast<int64_t>(segs[w].passes.size());
+    obase[w + 1] = obase[w] + static_cast<int64_t>(segs[w].ops.size());
+    cbase[w + 1] = cbase[w] + static_cast<int64_t>(segs[w].coef.size());
+  }
+  if (b->instr_off.back() > 0xFFFFFFFFll || obase.back() > 0xFFFFFFFFll || cbase.back() > 0xFFFFFFFFll ||
+      pbase.back() > 0x7FFFFFFFll)
     return fail(TQS_ERR_ARG, "tqs_batch: program too large for 32-bit offsets");
-  // the image, filled in parallel from the prefix sums
   b->img.circs.resize(b->count);
-  b->img.passes.resize(static_cast<size_t>(pass0.back()));
-  b->img.ops.resize(static_cast<size_t>(op0.back()));
-  b->img.coef.resize(static_cast<size_t>(coef0.back()));
+  b->img.segs = std::move(segs);
+  b->img.npass = static_cast<size_t>(pbase.back());
+  b->img.nop = static_cast<size_t>(obase.back());
+  b->img.ncoef = static_cast<size_t>(cbase.back());
   parallel_for(b->count, 256, [&](int i) {
-    b->img.fill(i, progs[i], b->offsets[i], pass0[i], op0[i], b->instr_off[i], coef0[i]);
+    const CircMeta& m = progs[i];
+    ImageSeg& sg = b->img.segs[static_cast<size_t>(m.seg)];
+    const int64_t p0 = pbase[m.seg] + static_cast<int64_t>(m.lp);
+    const int64_t o0 = obase[m.seg] + static_cast<int64_t>(m.lo);
+    const int64_t c0 = cbase[m.seg] + static_cast<int64_t>(m.lc);
+    FusedCirc fc{};
+    fc.n = m.n;
+    fc.nint = m.nint;
+    fc.pass_begin = static_cast<int32_t>(p0);
+    fc.pass_count = static_cast<int32_t>(m.np);
+    fc.out_off = b->offsets[i];
+    fc.team = team_for(m.nint);
+    fc.identity = m.identity;
+    std::memcpy(fc.pos, m.pos, 16);
+    fc.init = nullptr;
+    fc.out_scale = m.out_scale;
+    fc.gen_index = m.gen_index;
+    b->img.circs[i] = fc;
+    for (size_t k = 0; k < m.np; ++k)
+      sg.passes[m.lp + k] = Image::rebase(sg.passes[m.lp + k], o0, b->instr_off[i], c0);
   });
   std::vector<int> idx[3];
   for (int i = 0; i < b->count; ++i) {
@@ -1430,9 +1613,11 @@ tqs_status tqs_batch_create(tqs_circuit* const* cs, int count, tqs_batch** out) 
     compile_program(cs[i]->n, step_order(cs[i]->gates), progs[i]);
     b->total_steps += cs[i]->nsteps;
   }
-  std::vector<ProgView> views(count);
-  for (int i = 0; i < count; ++i) views[i] = view_of(progs[i]);
-  tqs_status s = batch_finish(b.get(), views);
+  std::vector<ImageSeg> segs;
+  segs.push_back(take_seg());
+  std::vector<CircMeta> metas(count);
+  for (int i = 0; i < count; ++i) metas[i] = append_program(progs[i], segs[0], 0);
+  tqs_status s = batch_finish(b.get(), metas, std::move(segs));
   if (s != TQS_OK) return s;
   *out = b.release();
   return TQS_OK;
@@ -1446,21 +1631,19 @@ tqs_status tqs_batch_create_packed(int count, const int32_t* h_nq, const int64_t
   *out = nullptr;
   std::unique_ptr<tqs_batch> b(new (std::nothrow) tqs_batch());
   if (!b) return fail(TQS_ERR_NOMEM, "tqs_batch_create_packed: out of host memory");
-  std::vector<ProgView> views(count);
+  std::vector<CircMeta> metas(count);
   std::vector<int> nsteps(count, 0);
-  std::vector<int> owner(count, 0);
-  // Circuits are independent: compile them on all host cores.  Each worker
-  // compiles into one reused Program and appends the result to its own
-  // buffers (no allocation per circuit); views into those buffers are taken
-  // once every worker is done.  Each worker records its first failure; the
-  // lowest failing circuit index is reported.
-  struct WorkerBuf {
-    std::vector<FusedPass> passes;
-    std::vector<FusedOp> ops;
-    std::vector<float2> coef;
-  };
-  const int nworkers = std::max(1, std::min(count / 64, 32));
-  std::vector<WorkerBuf> bufs(static_cast<size_t>(nworkers));
+  // Circuits are independent: compile them on all host cores.  Worker w takes
+  // the contiguous range [w C / W, (w + 1) C / W) and compiles into one reused
+  // Program, appending the result to its own segment, reserved up front from
+  // the gate counts of its range (fusion only shrinks a program: at most one
+  // op per gate and one pass per gate plus one), so it never reallocates.
+  // Each worker records its first failure; the lowest failing circuit index
+  // is reported.
+  int width = static_cast<int>(std::max(1u, std::thread::hardware_concurrency()));
+  if (const char* env = std::getenv("TQS_HOST_THREADS")) width = std::max(1, std::atoi(env));
+  const int nworkers = std::max(1, std::min({count / 64, 32, width}));
+  std::vector<ImageSeg> segs(static_cast<size_t>(nworkers));
   struct Failure {
     int index = -1;
     tqs_status status = TQS_OK;
@@ -1468,17 +1651,20 @@ tqs_status tqs_batch_create_packed(int count, const int32_t* h_nq, const int64_t
   };
   std::mutex fail_mu;
   Failure first;
-  std::atomic<int> next_circuit{0};
-  std::atomic<int> next_worker{0};
-  auto work = [&]() {
-    const int w = next_worker.fetch_add(1);
-    WorkerBuf& buf = bufs[static_cast<size_t>(w)];
+  for (int w = 0; w < nworkers; ++w) segs[static_cast<size_t>(w)] = take_seg();
+  parallel_for(nworkers, 1, [&](int w) {
+    const int lo = static_cast<int>(int64_t(count) * w / nworkers);
+    const int hi = static_cast<int>(int64_t(count) * (w + 1) / nworkers);
+    ImageSeg& sg = segs[static_cast<size_t>(w)];
+    const int64_t span = h_gate_off[hi] - h_gate_off[lo];
+    if (span >= 0) {
+      sg.passes.reserve(static_cast<size_t>(span) + static_cast<size_t>(hi - lo));
+      sg.ops.reserve(static_cast<size_t>(span));
+    }
     static thread_local std::vector<Gate> gates;
     static thread_local std::vector<int> last;
     static thread_local Program tp;
-    for (;;) {
-      const int i = next_circuit.fetch_add(1);
-      if (i >= count) return;
+    for (int i = lo; i < hi; ++i) {
       auto record = [&](tqs_status st) {
         std::lock_guard<std::mutex> lock(fail_mu);
         if (first.index < 0 || i < first.index) {
@@ -1515,29 +1701,15 @@ tqs_status tqs_batch_create_packed(int count, const int32_t* h_nq, const int64_t
       for (int q = 0; q < n; ++q) nsteps[i] = std::max(nsteps[i], last[q] + 1);
       tp.reset();
       compile_program(n, step_order(gates), tp);
-      ProgView v = view_meta(tp);
-      // offsets into this worker's buffers, turned into pointers later
-      v.passes = reinterpret_cast<const FusedPass*>(buf.passes.size());
-      v.ops = reinterpret_cast<const FusedOp*>(buf.ops.size());
-      v.coef = reinterpret_cast<const float2*>(buf.coef.size());
-      buf.passes.insert(buf.passes.end(), tp.passes.begin(), tp.passes.end());
-      buf.ops.insert(buf.ops.end(), tp.ops.begin(), tp.ops.end());
-      buf.coef.insert(buf.coef.end(), tp.coef.begin(), tp.coef.end());
-      views[i] = v;
-      owner[i] = w;
+      metas[i] = append_program(tp, sg, w);
     }
-  };
-  parallel_for(nworkers, 1, [&](int) { work(); });
-  if (first.index >= 0) return fail(first.status, "%s", first.message.c_str());
-  for (int i = 0; i < count; ++i) {
-    const WorkerBuf& buf = bufs[static_cast<size_t>(owner[i])];
-    ProgView& v = views[i];
-    v.passes = buf.passes.data() + reinterpret_cast<size_t>(v.passes);
-    v.ops = buf.ops.data() + reinterpret_cast<size_t>(v.ops);
-    v.coef = buf.coef.data() + reinterpret_cast<size_t>(v.coef);
-    b->total_steps += nsteps[i];
+  });
+  if (first.index >= 0) {
+    give_segs(segs);
+    return fail(first.status, "%s", first.message.c_str());
   }
-  tqs_status s = batch_finish(b.get(), views);
+  for (int i = 0; i < count; ++i) b->total_steps += nsteps[i];
+  tqs_status s = batch_finish(b.get(), metas, std::move(segs));
   if (s != TQS_OK) return s;
   *out = b.release();
   return TQS_OK;
@@ -1778,7 +1950,14 @@ tqs_status tqs_batch_run_host(tqs_batch* b, tqs_c64* h_states, double* h_probs, 
     TQS_CUDA(cudaMemcpyAsync(h_norms, dn, size_t(b->count) * sizeof(double), cudaMemcpyDeviceToHost, s),
              "D2H norms");
   TQS_CUDA(cudaFreeAsync(base, s), "tqs_batch_run_host: cudaFreeAsync");
-  TQS_CUDA(cudaStreamSynchronize(s), "tqs_batch_run_host: sync");
+  // wait without spinning, so that host threads compiling other batches keep the cores
+  cudaEvent_t done = nullptr;
+  TQS_CUDA(cudaEventCreateWithFlags(&done, cudaEventBlockingSync | cudaEventDisableTiming),
+           "tqs_batch_run_host: event");
+  cudaError_t e = cudaEventRecord(done, s);
+  if (e == cudaSuccess) e = cudaEventSynchronize(done);
+  cudaEventDestroy(done);
+  TQS_CUDA(e, "tqs_batch_run_host: sync");
   return TQS_OK;
 }
 
@@ -1955,10 +2134,7 @@ static tqs_status server_launch(tqs_server* sv, SrvSlot& sl) {
     TQS_CUDA(grow_pinned(&p, &sl.h_prog_cap, prog_bytes), "tqs_server: cudaMallocHost");
     sl.h_prog = static_cast<char*>(p);
   }
-  std::memcpy(sl.h_prog, img.circs.data(), img.circ_bytes());
-  if (!img.passes.empty()) std::memcpy(sl.h_prog + img.circ_bytes(), img.passes.data(), img.pass_bytes());
-  if (!img.ops.empty())
-    std::memcpy(sl.h_prog + img.circ_bytes() + img.pass_bytes(), img.ops.data(), img.op_bytes());
+  img.copy_to(sl.h_prog);
   std::memcpy(sl.h_prog + order_off, order.data(), order.size() * sizeof(int32_t));
   {
     void* p = sl.h_states;
