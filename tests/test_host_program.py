@@ -507,3 +507,30 @@ def test_large_circuits_only_in_fsv():
         B.tqs_circuit_destroy(c)
     with pytest.raises(B.TqsError):
         B.tqs_circuit_create(35)
+
+
+@pytest.mark.filterwarnings("ignore::DeprecationWarning")
+def test_host_pool_survives_fork():
+    """Batch creation runs on a persistent pool of host threads; a child
+    process forked after the pool exists gets a pool of its own (the parent's
+    threads do not exist there) and creates batches normally."""
+    import os
+    circs = [(n, W.random_mixed(n, 6, (17, n, i))) for i, n in enumerate([5, 9, 11, 12] * 64)]
+    arrays = B.pack_ops(circs)
+    b = B.tqs_batch_create_packed(*arrays)   # starts the pool in this process
+    count0 = B.tqs_batch_info(b)[0]
+    B.tqs_batch_destroy(b)
+    pid = os.fork()
+    if pid == 0:
+        code = 1
+        try:
+            bb = B.tqs_batch_create_packed(*arrays)
+            code = 0 if B.tqs_batch_info(bb)[0] == count0 else 2
+            B.tqs_batch_destroy(bb)
+        finally:
+            os._exit(code)
+    _, status = os.waitpid(pid, 0)
+    assert os.WIFEXITED(status) and os.WEXITSTATUS(status) == 0
+    b = B.tqs_batch_create_packed(*arrays)
+    assert B.tqs_batch_info(b)[0] == count0
+    B.tqs_batch_destroy(b)
