@@ -12,16 +12,19 @@
 //     the last chunk;
 //   * block prefix: each thread of a CTA sums a contiguous run of block
 //     totals, the runs are combined in order (warp scan, then warp totals);
-//   * C_i = (bpre_b + cpre_{b,l}) + p_{first of chunk} + ... + p_i.
+//   * chunk base cbase_{b,l} = bpre_b + cpre_{b,l};
+//   * C_i = cbase_{b,l} + p_{first of chunk} + ... + p_i.
 // A shot with uniform u and target u T (T: the segment total) takes the last
-// block b with bpre_b <= target, the last chunk l of it with bpre_b + cpre_{b,l}
-// <= target, and the first entry i of that chunk with p_i > 0 and target <
+// block b with bpre_b <= target, the last chunk l of it with cbase_{b,l} <=
+// target, and the first entry i of that chunk with p_i > 0 and target <
 // C_i.  If there is none (rounding, or u T >= T), the last index at or before
 // that point with p_i > 0; -1 when every probability is 0.
 //
 // GB300's FP64 rate is about 1/64 of its FP32 rate, so the design keeps FP64
-// operations few: the tables cost about 14 warp-wide FP64 additions per 256
-// entries, and a shot is one thread's binary searches plus at most 8 adds.
+// operations few: the tables cost about 15 warp-wide FP64 additions per 256
+// entries (the chunk bases bpre_b + cpre_{b,l} are stored absolute), and a
+// shot is one multiply, binary searches that compare the FP64 bit patterns as
+// integers (the order of non-negative doubles), and at most 8 adds.
 // Two paths share that arithmetic: segments of up to 2^13 entries are staged
 // in shared memory by one CTA each, which builds the tables there and runs
 // every shot of the segment; larger segments use three kernels over global
@@ -99,16 +102,27 @@ __device__ void block_prefix_cta(const double* bs, double* bp, int64_t nb, doubl
   if (b0 < nb && b1 == nb) *tot = acc;
 }
 
+// a <= b for non-negative doubles, as integers on their bit patterns.
+__device__ __forceinline__ bool le_bits(double a, double b) {
+  return __double_as_longlong(a) <= __double_as_longlong(b);
+}
+
+// Chunk prefixes of the blocks [0, nb) made absolute: cp[b * 32 + l] becomes
+// bp[b] + cp[b * 32 + l] (whole CTA).
+__device__ void absolute_chunks(const double* bp, double* cp, int64_t nb) {
+  for (int64_t e = threadIdx.x; e < nb * kChunks; e += kThreads) cp[e] = bp[e / kChunks] + cp[e];
+}
+
 // Last index <= i with p > 0, or -1 (one thread; reached only after rounding
 // or for u T >= T).
 __device__ int64_t last_nonzero_upto(const double* p, int64_t i) {
   for (; i >= 0; --i)
-    if (p[i] > 0.0) return i;
+    if (__double_as_longlong(p[i]) > 0) return i;
   return -1;
 }
 
-// One shot (one thread).  p: the segment's entries; bp, cp: its block and
-// chunk prefixes (global or shared memory).
+// One shot (one thread).  p: the segment's entries; bp: its block prefix; cp:
+// its absolute chunk bases (global or shared memory).
 __device__ int64_t sample_shot(const double* p, int64_t len, const double* bp, const double* cp,
                                int64_t nb, double T, double u) {
   const double target = u * T;
@@ -116,22 +130,21 @@ __device__ int64_t sample_shot(const double* p, int64_t len, const double* bp, c
   int64_t lo = 0, hi = nb - 1;
   while (lo < hi) {
     const int64_t mid = (lo + hi + 1) >> 1;
-    if (bp[mid] <= target) lo = mid; else hi = mid - 1;
+    if (le_bits(bp[mid], target)) lo = mid; else hi = mid - 1;
   }
   const int64_t b = lo;
-  const double base = bp[b];
   const double* cpb = cp + b * kChunks;
   int l = 0, h = kChunks - 1;
   while (l < h) {
     const int mid = (l + h + 1) >> 1;
-    if (base + cpb[mid] <= target) l = mid; else h = mid - 1;
+    if (le_bits(cpb[mid], target)) l = mid; else h = mid - 1;
   }
   const int64_t i0 = b * kSampleBlk + int64_t(l) * kSampleChunk;
-  double c = base + cpb[l];
+  double c = cpb[l];
   for (int j = 0; j < kSampleChunk && i0 + j < len; ++j) {
     const double x = p[i0 + j];
     c += x;
-    if (x > 0.0 && target < c) return i0 + j;
+    if (__double_as_longlong(x) > 0 && !le_bits(c, target)) return i0 + j;
   }
   const int64_t end = i0 + kSampleChunk - 1 < len - 1 ? i0 + kSampleChunk - 1 : len - 1;
   return last_nonzero_upto(p, end);
@@ -158,6 +171,8 @@ __global__ void __launch_bounds__(kThreads)
   const SampleSeg sg = L.gsegs[blockIdx.x];
   block_prefix_cta(L.bsum + sg.blk_off, L.bpre + sg.blk_off, sample_blocks(sg.n),
                    L.tot + blockIdx.x, wtot, wpre);
+  __syncthreads();
+  absolute_chunks(L.bpre + sg.blk_off, L.cpre + int64_t(sg.blk_off) * kChunks, sample_blocks(sg.n));
 }
 
 __global__ void __launch_bounds__(kThreads)
@@ -204,6 +219,8 @@ __global__ void __launch_bounds__(kThreads)
   }
   __syncthreads();
   block_prefix_cta(sbs, sbp, nb, &s_tot, wtot, wpre);
+  __syncthreads();
+  absolute_chunks(sbp, scp, nb);
   __syncthreads();
   const double T = s_tot;
   for (int64_t k = t; k < L.shots; k += kThreads) {

@@ -213,7 +213,8 @@ struct SampleLaunch {
   int64_t nblocks;         // sum of sample_blocks(n) over the global segments
   double* bsum;            // device scratch [nblocks]: block totals
   double* bpre;            // device scratch [nblocks]: exclusive block prefix per segment
-  double* cpre;            // device scratch [nblocks * 32]: exclusive chunk prefix in its block
+  double* cpre;            // device scratch [nblocks * 32]: chunk bases (exclusive prefix in the
+                           // block, then made absolute by adding the block prefix)
   double* tot;             // device scratch [n_gseg]: segment totals
   const SampleSeg* ssegs;  // device: segments of the shared-memory path
   int32_t n_sseg;
