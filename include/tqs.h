@@ -432,6 +432,11 @@ tqs_status tqs_server_poll(tqs_server* s, int64_t* h_done_tags, int max_done, in
  * (host, or NULL) and forget it.  TQS_ERR_STATE if `tag` is not finished. */
 tqs_status tqs_server_take(tqs_server* s, int64_t tag, tqs_c64* h_state, double* h_norm);
 
+/* Cancel a request that is still queued (not yet launched): it is dropped
+ * and produces no result.  TQS_ERR_STATE if it is running or finished,
+ * TQS_ERR_ARG if the server has no request with that tag. */
+tqs_status tqs_server_cancel(tqs_server* s, int64_t tag);
+
 /* Counters (each may be NULL): queued requests, requests in flight, requests
  * finished so far, device bytes held now and at most so far. */
 tqs_status tqs_server_stats(const tqs_server* s, int64_t* queued, int64_t* inflight,
@@ -439,6 +444,26 @@ tqs_status tqs_server_stats(const tqs_server* s, int64_t* queued, int64_t* infli
 
 /* Wait for in-flight work, then free everything.  NULL is accepted. */
 tqs_status tqs_server_destroy(tqs_server* s);
+
+/* --------------------------------------------------------------- allocator
+ * Device scratch (programs, step tables, operand planes, partial sums, batch
+ * and server buffers) comes from cudaMalloc / cudaMallocAsync unless the
+ * caller installs its own allocator (for example a framework's caching
+ * allocator), process-wide:
+ *   alloc(bytes, stream, ctx) -> device pointer (16-byte aligned) or NULL;
+ *   free(ptr, stream, ctx).
+ * `stream` is the stream the buffer is used on (NULL for buffers cached on a
+ * handle).  A free with a stream is stream-ordered: work already queued on
+ * that stream may still use the buffer, so the allocator must not give it to
+ * other streams before that work completes (as a per-stream caching
+ * allocator or cudaFreeAsync behaves).  A free with a NULL stream follows a
+ * device synchronisation.  Every buffer is returned to the allocator that
+ * made it.  An allocation that returns NULL fails the call with
+ * TQS_ERR_NOMEM.  tqs_set_allocator(NULL, NULL, NULL) restores the default.
+ * The callbacks may be called from any host thread that calls the library. */
+typedef void* (*tqs_alloc_fn)(size_t bytes, void* stream, void* ctx);
+typedef void (*tqs_free_fn)(void* ptr, void* stream, void* ctx);
+tqs_status tqs_set_allocator(tqs_alloc_fn alloc, tqs_free_fn free, void* ctx);
 
 /* ----------------------------------------------------------------- options
  * Launch options read when a batch (or a single simulate) plans its launches.

@@ -89,6 +89,8 @@ _SIGS = {
                               ctypes.POINTER(_i64), ctypes.POINTER(_i64), ctypes.POINTER(_i64)]),
     "tqs_server_destroy": (_i, [_vp]),
     "tqs_set_option": (_i, [_i, _i, _i64]),
+    "tqs_set_allocator": (_i, [_vp, _vp, _vp]),
+    "tqs_server_cancel": (_i, [_vp, _i64]),
     "tqs_get_option": (_i, [_i, _i, ctypes.POINTER(_i64)]),
     "tqs_selftest_wait_timeout": (_i, [_i64, _vp]),
     "tqs_last_error": (ctypes.c_char_p, []),
@@ -485,3 +487,43 @@ def tqs_get_option(option: int, key: int) -> int:
 
 def tqs_selftest_wait_timeout(wait_cycles: int, stream=None) -> None:
     _check(lib().tqs_selftest_wait_timeout(int(wait_cycles), _stream(stream)))
+
+
+# --------------------------------------------------------------- allocator
+
+ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)
+FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p)
+_allocator_refs = None  # keeps the ctypes callbacks alive while installed
+
+
+def tqs_set_allocator(alloc=None, free=None) -> None:
+    """Install alloc(bytes, stream) -> device pointer (0 / None on failure) and
+    free(ptr, stream) as the library's device allocator; no arguments restore
+    cudaMalloc / cudaFree."""
+    global _allocator_refs
+    if alloc is None:
+        _check(lib().tqs_set_allocator(None, None, None))
+        _allocator_refs = None
+        return
+    ca = ALLOC_FN(lambda n, stream, ctx: alloc(int(n), stream or 0) or None)
+    cf = FREE_FN(lambda p, stream, ctx: free(int(p), stream or 0))
+    _check(lib().tqs_set_allocator(ctypes.cast(ca, _vp), ctypes.cast(cf, _vp), None))
+    _allocator_refs = (ca, cf)
+
+
+def use_torch_allocator(device=None) -> None:
+    """Route the library's device scratch through torch's caching allocator."""
+    import torch
+    dev = torch.cuda.current_device() if device is None else int(device)
+
+    def alloc(n, stream):
+        return torch.cuda.caching_allocator_alloc(n, dev, stream if stream else None)
+
+    def free(p, stream):
+        torch.cuda.caching_allocator_delete(p)
+
+    tqs_set_allocator(alloc, free)
+
+
+def tqs_server_cancel(sv: int, tag: int) -> None:
+    _check(lib().tqs_server_cancel(sv, int(tag)))

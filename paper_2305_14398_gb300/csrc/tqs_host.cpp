@@ -64,23 +64,62 @@ static tqs_status cuda_fail(cudaError_t e, const char* what) {
     if (e_ != cudaSuccess) return cuda_fail(e_, what); \
   } while (0)
 
-// A device buffer owned by a handle (cudaMalloc / cudaFree).
+// Device allocator of the library's scratch: cudaMalloc / cudaFree, or the
+// caller's callbacks (tqs_set_allocator).  Every buffer remembers the
+// allocator that made it and is returned to that one.
+struct Allocator {
+  tqs_alloc_fn alloc = nullptr;  // nullptr: cudaMalloc / cudaFree
+  tqs_free_fn free = nullptr;
+  void* ctx = nullptr;
+};
+static std::mutex g_alloc_mu;
+static Allocator g_alloc;
+
+static Allocator current_allocator() {
+  std::lock_guard<std::mutex> lock(g_alloc_mu);
+  return g_alloc;
+}
+
+// Allocate `bytes` of device memory for use on `s` with allocator A.
+static cudaError_t dev_alloc(const Allocator& A, void** p, size_t bytes, cudaStream_t s) {
+  if (!A.alloc) return cudaMalloc(p, bytes);
+  *p = A.alloc(bytes, s, A.ctx);
+  return *p ? cudaSuccess : cudaErrorMemoryAllocation;
+}
+
+// Return p to allocator A.  With s = nullptr the device is synchronised
+// first (as cudaFree does), so no queued work still reads the buffer when the
+// caller's allocator hands it out again; with a stream, frees are
+// stream-ordered on it.
+static void dev_free(const Allocator& A, void* p, cudaStream_t s) {
+  if (!p) return;
+  if (!A.alloc) {
+    cudaFree(p);
+    return;
+  }
+  if (!s) cudaDeviceSynchronize();
+  A.free(p, s, A.ctx);
+}
+
+// A device buffer owned by a handle.
 struct DevBuf {
   void* p = nullptr;
   size_t bytes = 0;
+  Allocator by;  // the allocator that made p
   DevBuf() = default;
   DevBuf(const DevBuf&) = delete;
   DevBuf& operator=(const DevBuf&) = delete;
   ~DevBuf() { release(); }
   void release() {
-    if (p) cudaFree(p);
+    if (p) dev_free(by, p, nullptr);
     p = nullptr;
     bytes = 0;
   }
   cudaError_t ensure(size_t n) {
     if (n <= bytes && p) return cudaSuccess;
     release();
-    cudaError_t e = cudaMalloc(&p, n ? n : 16);
+    by = current_allocator();
+    cudaError_t e = dev_alloc(by, &p, n ? n : 16, nullptr);
     if (e == cudaSuccess) bytes = n;
     else p = nullptr;
     return e;
@@ -1929,8 +1968,15 @@ tqs_status tqs_batch_run_host(tqs_batch* b, tqs_c64* h_states, double* h_probs, 
                           ? size_t(b->plans[TEAM_GLOBAL].grid) * (size_t(1) << kGlobalSlotQ) * sizeof(float2)
                           : 0;
   char* base = nullptr;
-  TQS_CUDA(cudaMallocAsync(reinterpret_cast<void**>(&base), ((total + 255) & ~size_t(255)) + gscr, s),
-           "tqs_batch_run_host: cudaMallocAsync");
+  const Allocator A = current_allocator();
+  if (A.alloc) {
+    void* q = nullptr;
+    TQS_CUDA(dev_alloc(A, &q, ((total + 255) & ~size_t(255)) + gscr, s), "tqs_batch_run_host: allocator");
+    base = static_cast<char*>(q);
+  } else {
+    TQS_CUDA(cudaMallocAsync(reinterpret_cast<void**>(&base), ((total + 255) & ~size_t(255)) + gscr, s),
+             "tqs_batch_run_host: cudaMallocAsync");
+  }
   TQS_CUDA(b->img.upload(base, s), "tqs_batch_run_host: upload program");
   TQS_CUDA(cudaMemcpyAsync(base + order_off, b->order.data(), b->order.size() * sizeof(int32_t),
                            cudaMemcpyHostToDevice, s),
@@ -1949,7 +1995,8 @@ tqs_status tqs_batch_run_host(tqs_batch* b, tqs_c64* h_states, double* h_probs, 
   if (h_norms && !zn)
     TQS_CUDA(cudaMemcpyAsync(h_norms, dn, size_t(b->count) * sizeof(double), cudaMemcpyDeviceToHost, s),
              "D2H norms");
-  TQS_CUDA(cudaFreeAsync(base, s), "tqs_batch_run_host: cudaFreeAsync");
+  if (A.alloc) dev_free(A, base, s);
+  else TQS_CUDA(cudaFreeAsync(base, s), "tqs_batch_run_host: cudaFreeAsync");
   // wait without spinning, so that host threads compiling other batches keep the cores
   cudaEvent_t done = nullptr;
   TQS_CUDA(cudaEventCreateWithFlags(&done, cudaEventBlockingSync | cudaEventDisableTiming),
@@ -2147,7 +2194,14 @@ static tqs_status server_launch(tqs_server* sv, SrvSlot& sl) {
   }
   cudaStream_t s = sl.stream;
   char* base = nullptr;
-  TQS_CUDA(cudaMallocAsync(reinterpret_cast<void**>(&base), total, s), "tqs_server: cudaMallocAsync");
+  const Allocator A = current_allocator();
+  if (A.alloc) {
+    void* q = nullptr;
+    TQS_CUDA(dev_alloc(A, &q, total, s), "tqs_server: allocator");
+    base = static_cast<char*>(q);
+  } else {
+    TQS_CUDA(cudaMallocAsync(reinterpret_cast<void**>(&base), total, s), "tqs_server: cudaMallocAsync");
+  }
   TQS_CUDA(cudaMemcpyAsync(base, sl.h_prog, prog_bytes, cudaMemcpyHostToDevice, s), "tqs_server: H2D");
   int32_t* counters = reinterpret_cast<int32_t*>(base + counter_off);
   TQS_CUDA(cudaMemsetAsync(counters, 0, 3 * sizeof(int32_t), s), "tqs_server: memset");
@@ -2177,7 +2231,8 @@ static tqs_status server_launch(tqs_server* sv, SrvSlot& sl) {
   TQS_CUDA(cudaMemcpyAsync(sl.h_norms, d_norms, sl.reqs.size() * sizeof(double),
                            cudaMemcpyDeviceToHost, s),
            "tqs_server: D2H norms");
-  TQS_CUDA(cudaFreeAsync(base, s), "tqs_server: cudaFreeAsync");
+  if (A.alloc) dev_free(A, base, s);
+  else TQS_CUDA(cudaFreeAsync(base, s), "tqs_server: cudaFreeAsync");
   TQS_CUDA(cudaEventRecord(sl.done, s), "tqs_server: event");
   sl.busy = true;
   return TQS_OK;
@@ -2317,6 +2372,25 @@ tqs_status tqs_server_take(tqs_server* sv, int64_t tag, tqs_c64* h_state, double
   return TQS_OK;
 }
 
+tqs_status tqs_server_cancel(tqs_server* sv, int64_t tag) {
+  if (!sv) return fail(TQS_ERR_ARG, "tqs_server_cancel: server is NULL");
+  for (auto it = sv->queue.begin(); it != sv->queue.end(); ++it) {
+    if (it->tag == tag) {
+      sv->queue.erase(it);
+      return TQS_OK;
+    }
+  }
+  for (const SrvSlot& sl : sv->slots)
+    for (const SrvReq& r : sl.reqs)
+      if (sl.busy && r.tag == tag)
+        return fail(TQS_ERR_STATE, "tqs_server_cancel: request %lld is running",
+                    static_cast<long long>(tag));
+  if (sv->results.count(tag))
+    return fail(TQS_ERR_STATE, "tqs_server_cancel: request %lld has finished",
+                static_cast<long long>(tag));
+  return fail(TQS_ERR_ARG, "tqs_server_cancel: no request %lld", static_cast<long long>(tag));
+}
+
 tqs_status tqs_server_stats(const tqs_server* sv, int64_t* queued, int64_t* inflight, int64_t* done,
                             int64_t* bytes_in_use, int64_t* peak_bytes) {
   if (!sv) return fail(TQS_ERR_ARG, "tqs_server_stats: server is NULL");
@@ -2338,6 +2412,16 @@ tqs_status tqs_server_destroy(tqs_server* sv) {
 }  // extern "C"
 
 extern "C" {
+
+tqs_status tqs_set_allocator(tqs_alloc_fn alloc, tqs_free_fn free_fn, void* ctx) {
+  if ((alloc == nullptr) != (free_fn == nullptr))
+    return fail(TQS_ERR_ARG, "tqs_set_allocator: give both callbacks or neither");
+  std::lock_guard<std::mutex> lock(g_alloc_mu);
+  g_alloc.alloc = alloc;
+  g_alloc.free = free_fn;
+  g_alloc.ctx = ctx;
+  return TQS_OK;
+}
 
 tqs_status tqs_set_option(int option, int key, int64_t value) {
   if (option == TQS_OPT_TEAM_WARPS) {

@@ -534,3 +534,53 @@ def test_host_pool_survives_fork():
     b = B.tqs_batch_create_packed(*arrays)
     assert B.tqs_batch_info(b)[0] == count0
     B.tqs_batch_destroy(b)
+
+
+# ------------------------------------------------ allocator and cancellation
+
+def test_allocator_failure_is_nomem():
+    """A caller allocator that refuses memory fails the call with
+    TQS_ERR_NOMEM before any device work (host-side fault injection)."""
+    calls = []
+
+    def refuse(n, stream):
+        calls.append(n)
+        return 0
+
+    B.tqs_set_allocator(refuse, lambda p, s: None)
+    try:
+        c = B.circuit_from_ops(5, W.ghz_chain(5))
+        try:
+            st = B.lib().tqs_simulate(c, None, 256, None, None, None)
+            assert B.STATUS[st] == "TQS_ERR_NOMEM" and calls
+            st = B.lib().tqs_circuit_unitary(c, B.PREC_FP32_SIMT, 256, None)
+            assert B.STATUS[st] == "TQS_ERR_NOMEM"
+        finally:
+            B.tqs_circuit_destroy(c)
+        b = B.tqs_batch_create_packed(*B.pack_ops([(6, W.ghz_chain(6))] * 4))
+        try:
+            st = B.lib().tqs_batch_run(b, 256, None, None, 0, None)
+            assert B.STATUS[st] == "TQS_ERR_NOMEM"
+        finally:
+            B.tqs_batch_destroy(b)
+        st = B.lib().tqs_probabilities(256, 10, None, 512, None)
+        assert B.STATUS[st] == "TQS_ERR_NOMEM"
+    finally:
+        B.tqs_set_allocator()
+    # one callback without the other is an argument error
+    assert B.STATUS[B.lib().tqs_set_allocator(B.ALLOC_FN(lambda n, s, c: None), None, None)] == "TQS_ERR_ARG"
+
+
+def test_server_cancel_host_side():
+    sv = B.tqs_server_create(1 << 30, 1, 8)
+    try:
+        for tag in range(3):
+            B.tqs_server_submit_packed(sv, tag, 5, B.pack_request(W.ghz_chain(5)))
+        B.tqs_server_cancel(sv, 1)
+        assert B.tqs_server_stats(sv)["queued"] == 2
+        for tag, status in ((1, "TQS_ERR_ARG"), (7, "TQS_ERR_ARG")):
+            with pytest.raises(B.TqsError) as e:
+                B.tqs_server_cancel(sv, tag)
+            assert e.value.name == status
+    finally:
+        B.tqs_server_destroy(sv)
