@@ -88,6 +88,45 @@ print(json.dumps({"circuits": done, "seconds": dt}))
 """
 
 
+ORACLE_EXTRA_SNIPPET = r"""
+import json, sys, time
+sys.path.insert(0, %(root)r)
+from oracle import fsv_route
+from paper_2305_14398_gb300 import workloads as W
+out = {}
+mix = W.paper_mix(%(n)d, 64, seed_tag=1)
+t0 = time.perf_counter()
+for _, ops in mix:
+    fsv_route.simulate(%(n)d, ops)
+out["fsv_circuits_per_s"] = len(mix) / (time.perf_counter() - t0)
+n = 12
+ops = W.random_layered(n, 20, (2, n))
+cols = [0, 1, 2, 3]
+t0 = time.perf_counter()
+fsv_route.unitary_columns(n, ops, cols)
+dt = time.perf_counter() - t0
+out["chain_n12_columns"] = len(cols)
+out["chain_n12_seconds_full_estimate"] = dt / len(cols) * (1 << n)
+print(json.dumps(out))
+"""
+
+
+def oracle_extra():
+    """Further CPU baselines of the oracle, one thread: the per-gate route
+    (eq. 12) on 64 circuits of the bench mix, and the circuit-unitary chain
+    at n = 12 by the column route (4 columns timed, the full 4096-column
+    unitary extrapolated)."""
+    env = dict(os.environ)
+    for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+        env[k] = "1"
+    code = ORACLE_EXTRA_SNIPPET % {"root": ROOT, "n": N_QUBITS}
+    r = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True,
+                       timeout=900)
+    if r.returncode != 0:
+        raise RuntimeError("oracle sample failed: " + r.stderr[-2000:])
+    return json.loads(r.stdout.strip().splitlines()[-1])
+
+
 def oracle_sample(kinds, tag=1):
     """Time the oracle's literal route (Algorithm 1/2: Kronecker step matrix +
     dense matvec per step, FP64) on the given circuits of the mix, one thread,
@@ -465,6 +504,14 @@ def run_tqs(args):
                       f"in each of {ra['procs']} concurrent single-thread processes (one per host "
                       f"core), literal Kronecker route (Algorithm 1/2), FP64",
             "value_1_core": r1["circuits"] / r1["seconds"],
+        }
+        ex = oracle_extra()
+        line["cpu_baseline_other"] = {
+            "per_gate_route_circuits_per_s_1_core": ex["fsv_circuits_per_s"],
+            "per_gate_route_sample": "64 circuits of the bench mix, eq. 12 per gate, FP64, 1 thread",
+            "chain_n12_seconds_1_core_estimate": ex["chain_n12_seconds_full_estimate"],
+            "chain_n12_sample": f"{ex['chain_n12_columns']} columns of the 40-step random layered "
+                                "unitary by the column route, extrapolated to 4096 columns",
         }
 
     B.tqs_batch_destroy(b)
