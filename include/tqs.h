@@ -465,6 +465,15 @@ typedef void* (*tqs_alloc_fn)(size_t bytes, void* stream, void* ctx);
 typedef void (*tqs_free_fn)(void* ptr, void* stream, void* ctx);
 tqs_status tqs_set_allocator(tqs_alloc_fn alloc, tqs_free_fn free, void* ctx);
 
+/* Bounds-checked build (compiled with -DTQS_CHECKED; a debugging aid with no
+ * counterpart in the paper): the fused, batch, instruction, custom-unitary
+ * and full-state-vector kernels test every state, tile and output index; an
+ * out-of-range index is counted and the access redirected to element 0
+ * instead of faulting.  *count receives the number of such accesses since
+ * the last reset (reset != 0 clears it); always 0 in the normal build.
+ * Synchronises the device. */
+tqs_status tqs_check_violations(uint32_t* count, int reset);
+
 /* ----------------------------------------------------------------- options
  * Launch options read when a batch (or a single simulate) plans its launches.
  * TQS_OPT_WARPS_PER_CTA, key = log2 of the amplitudes of a circuit's shared

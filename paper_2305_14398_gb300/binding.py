@@ -90,6 +90,7 @@ _SIGS = {
     "tqs_server_destroy": (_i, [_vp]),
     "tqs_set_option": (_i, [_i, _i, _i64]),
     "tqs_set_allocator": (_i, [_vp, _vp, _vp]),
+    "tqs_check_violations": (_i, [_vp, _i]),
     "tqs_server_cancel": (_i, [_vp, _i64]),
     "tqs_get_option": (_i, [_i, _i, ctypes.POINTER(_i64)]),
     "tqs_selftest_wait_timeout": (_i, [_i64, _vp]),
@@ -403,6 +404,14 @@ def tqs_batch_destroy(b: int) -> None:
 
 def tqs_launch_count() -> int:
     return int(lib().tqs_launch_count())
+
+
+def tqs_check_violations(reset: bool = False) -> int:
+    """Out-of-range accesses the bounds-checked library (libtqs_checked.so)
+    has recorded; always 0 for the normal build."""
+    v = ctypes.c_uint32()
+    _check(lib().tqs_check_violations(ctypes.byref(v), 1 if reset else 0))
+    return int(v.value)
 
 
 def tqs_last_error() -> str:

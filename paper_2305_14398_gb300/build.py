@@ -1,9 +1,11 @@
 """Build the sm_103a library libtqs.so in-tree (nvcc + g++, no cmake).
 
-    python -m paper_2305_14398_gb300.build [--force]
+    python -m paper_2305_14398_gb300.build [--force] [--checked]
 
 Every translation unit compiles in parallel; the shared library lands next to
 this file and the objects under _build/.  Rebuilds only what changed.
+--checked builds the bounds-checked variant (-DTQS_CHECKED) as
+libtqs_checked.so, objects under _build_checked/.
 """
 from __future__ import annotations
 
@@ -18,6 +20,8 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libtqs.so")
+BUILD_CHECKED = os.path.join(HERE, "_build_checked")
+LIB_CHECKED = os.path.join(HERE, "libtqs_checked.so")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
@@ -51,15 +55,19 @@ def _stale(src: str, obj: str, hdr_mtime: float) -> bool:
     return t < os.path.getmtime(src) or t < hdr_mtime
 
 
-def build(force: bool = False, verbose: bool = False, extra_nvcc=None) -> str:
+def build(force: bool = False, verbose: bool = False, extra_nvcc=None, checked: bool = False) -> str:
     cuda = _cuda_home()
     nvcc = os.path.join(cuda, "bin", "nvcc")
-    os.makedirs(BUILD, exist_ok=True)
+    build_dir = BUILD_CHECKED if checked else BUILD
+    lib_path = LIB_CHECKED if checked else LIB
+    if checked:
+        extra_nvcc = list(extra_nvcc or []) + ["-DTQS_CHECKED"]
+    os.makedirs(build_dir, exist_ok=True)
     cu, cpp = _sources()
     hdr = _headers_mtime()
     jobs = []
     for f in cu:
-        src, obj = os.path.join(CSRC, f), os.path.join(BUILD, f + ".o")
+        src, obj = os.path.join(CSRC, f), os.path.join(build_dir, f + ".o")
         if force or _stale(src, obj, hdr):
             cmd = [nvcc, *ARCH, "-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC",
                    "--expt-relaxed-constexpr", "-I", CSRC, "-I", INCLUDE, "-c", src, "-o", obj]
@@ -67,11 +75,11 @@ def build(force: bool = False, verbose: bool = False, extra_nvcc=None) -> str:
                 cmd[1:1] = list(extra_nvcc)
             jobs.append(cmd)
     for f in cpp:
-        src, obj = os.path.join(CSRC, f), os.path.join(BUILD, f + ".o")
+        src, obj = os.path.join(CSRC, f), os.path.join(build_dir, f + ".o")
         if force or _stale(src, obj, hdr):
             jobs.append(["g++", "-O2", "-std=c++17", "-fPIC", "-pthread", "-Wall", "-I", os.path.join(cuda, "include"),
                          "-I", CSRC, "-I", INCLUDE, "-c", src, "-o", obj])
-    objs = [os.path.join(BUILD, f + ".o") for f in cu + cpp]
+    objs = [os.path.join(build_dir, f + ".o") for f in cu + cpp]
 
     def run(cmd):
         if verbose:
@@ -86,13 +94,12 @@ def build(force: bool = False, verbose: bool = False, extra_nvcc=None) -> str:
             for msg in ex.map(run, jobs):
                 if verbose and msg.strip():
                     print(msg, flush=True)
-    if jobs or not os.path.exists(LIB):
-        tmp = LIB + ".tmp"
+    if jobs or not os.path.exists(lib_path):
+        tmp = lib_path + ".tmp"
         run([nvcc, *ARCH, "-shared", "-Xcompiler", "-pthread", "-o", tmp, *objs, "-lcudart", "-lcuda"])
-        os.replace(tmp, LIB)
-    return LIB
+        os.replace(tmp, lib_path)
+    return lib_path
 
 
 if __name__ == "__main__":
-    build(force="--force" in sys.argv, verbose=True)
-    print(LIB)
+    print(build(force="--force" in sys.argv, verbose=True, checked="--checked" in sys.argv))

@@ -6,6 +6,7 @@
 // Kept transposed like the tensor-core chain: V = U^T, V' = V S_k^T, so both
 // operands are read along K.  Tile: 64 x 64 complex outputs per 256-thread
 // block, 4 x 4 per thread, K step 16 staged in shared memory.
+#include "checked.h"
 #include "tqs_internal.h"
 
 namespace tqs {
@@ -40,8 +41,9 @@ __global__ void __launch_bounds__(kSimtThreads)
     for (int r = 0; r < 4; ++r) {
       const int idx = threadIdx.x + r * kSimtThreads;  // 0..1023
       const int row = idx >> 4, kk = idx & 15;
-      As[kk][row] = A[static_cast<size_t>(m0 + row) * N + k0 + kk];
-      Bs[kk][row] = B[static_cast<size_t>(n0 + row) * N + k0 + kk];
+      const size_t NN = static_cast<size_t>(N) * N;
+      As[kk][TQS_IX(row, TM)] = A[TQS_IX(static_cast<size_t>(m0 + row) * N + k0 + kk, NN)];
+      Bs[kk][TQS_IX(row, TN)] = B[TQS_IX(static_cast<size_t>(n0 + row) * N + k0 + kk, NN)];
     }
     __syncthreads();
 #pragma unroll
@@ -63,10 +65,11 @@ __global__ void __launch_bounds__(kSimtThreads)
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
       const int m = m0 + ty + 16 * i, n = n0 + tx + 16 * j;
+      const size_t NN = static_cast<size_t>(N) * N;
       if (transpose_out)
-        D[static_cast<size_t>(n) * N + m] = acc[i][j];
+        D[TQS_IX(static_cast<size_t>(n) * N + m, NN)] = acc[i][j];
       else
-        D[static_cast<size_t>(m) * N + n] = acc[i][j];
+        D[TQS_IX(static_cast<size_t>(m) * N + n, NN)] = acc[i][j];
     }
 }
 
@@ -89,11 +92,13 @@ __global__ void transpose_kernel(const float2* __restrict__ src, float2* __restr
   __shared__ float2 t[32][33];
   const int x = blockIdx.x * 32 + threadIdx.x;
   for (int r = threadIdx.y; r < 32; r += 8)
-    t[r][threadIdx.x] = src[static_cast<size_t>(blockIdx.y * 32 + r) * N + x];
+    t[r][threadIdx.x] = src[TQS_IX(static_cast<size_t>(blockIdx.y * 32 + r) * N + x,
+                                   static_cast<size_t>(N) * N)];
   __syncthreads();
   const int x2 = blockIdx.y * 32 + threadIdx.x;
   for (int r = threadIdx.y; r < 32; r += 8)
-    dst[static_cast<size_t>(blockIdx.x * 32 + r) * N + x2] = t[threadIdx.x][r];
+    dst[TQS_IX(static_cast<size_t>(blockIdx.x * 32 + r) * N + x2, static_cast<size_t>(N) * N)] =
+        t[threadIdx.x][r];
 }
 
 __global__ void transpose_small_kernel(const float2* __restrict__ src, float2* __restrict__ dst,
@@ -105,6 +110,8 @@ __global__ void transpose_small_kernel(const float2* __restrict__ src, float2* _
 }
 
 }  // namespace
+
+TQS_DEFINE_VIOLATIONS(violations_chain_simt)
 
 size_t chain_simt_scratch_bytes(int n) {
   const size_t N = size_t(1) << n;

@@ -21,6 +21,7 @@
 
 #include <mutex>
 
+#include "checked.h"
 #include "sm100_ptx.h"
 #include "step_entry.h"
 #include "../../include/tqs.h"
@@ -131,6 +132,8 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
   const int tile_m = (first_m + in_band % gsize) * BM;  // rows of V = rows of V'
   const int tile_n = (in_band / gsize) * BN;            // rows of S = columns of V'
   const int iters = (P.N / BK) * 3;                     // (k block, real GEMM j) pairs
+  (void)TQS_IX(tile_m, P.N - BM + 1);                   // whole tiles inside the N x N planes
+  (void)TQS_IX(tile_n, P.N - BN + 1);
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < kStages; ++s) {
@@ -221,7 +224,7 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
           for (int i = 0; i < 32; ++i) {
             const float re = t1[i] - t2[i];
             const float im = t3[i] - t1[i] - t2[i];
-            P.u[static_cast<size_t>(tile_n + c0 + i) * P.N + gm] = make_float2(re, im);
+            P.u[TQS_IX(static_cast<size_t>(tile_n + c0 + i) * P.N + gm, NN)] = make_float2(re, im);
           }
         } else {
           // in place: t1 <- Re, t2 <- Im, t3 <- Re + Im
@@ -232,7 +235,8 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
             t2[i] = c - a - b;
             t3[i] = t1[i] + t2[i];
           }
-          typename Prec<PREC>::E* rowp = P.planes + static_cast<size_t>(gm) * P.N + tile_n + c0;
+          typename Prec<PREC>::E* rowp = P.planes + static_cast<size_t>(TQS_IX(gm, P.N)) * P.N +
+                                         TQS_IX(tile_n + c0, P.N - 31);
           store_split<PREC, 32>(t1, rowp, rowp + NN);
           store_split<PREC, 32>(t2, rowp + 2 * NN, rowp + 3 * NN);
           store_split<PREC, 32>(t3, rowp + 4 * NN, rowp + 5 * NN);
@@ -261,7 +265,8 @@ __global__ void __launch_bounds__(kGenThreads)
                       int transpose, typename Prec<PREC>::E* __restrict__ planes) {
   __shared__ StepFactor fs[kMaxFactors];
   for (int i = threadIdx.x; i < nf * static_cast<int>(sizeof(StepFactor) / 8); i += blockDim.x)
-    reinterpret_cast<float2*>(fs)[i] = reinterpret_cast<const float2*>(factors)[i];
+    reinterpret_cast<float2*>(fs)[TQS_IX(i, int(sizeof(fs) / 8))] =
+        reinterpret_cast<const float2*>(factors)[i];
   __syncthreads();
   const int64_t N = int64_t(1) << n;
   const size_t NN = static_cast<size_t>(N) * N;
@@ -282,7 +287,7 @@ __global__ void __launch_bounds__(kGenThreads)
         im[i] = z.y;
         sm[i] = z.x + z.y;
       }
-      typename Prec<PREC>::E* base = planes + flat + i0;
+      typename Prec<PREC>::E* base = planes + TQS_IX(static_cast<size_t>(flat + i0), NN - 7);
       store_split<PREC, 8>(re, base, base + NN);
       store_split<PREC, 8>(im, base + 2 * NN, base + 3 * NN);
       store_split<PREC, 8>(sm, base + 4 * NN, base + 5 * NN);
@@ -409,6 +414,8 @@ __global__ void wait_selftest_kernel(int* status, long long wait_cycles) {
 }
 
 }  // namespace
+
+TQS_DEFINE_VIOLATIONS(violations_chain_tc)
 
 cudaError_t launch_wait_selftest(int* status, long long wait_cycles, cudaStream_t s) {
   wait_selftest_kernel<<<1, 1, 0, s>>>(status, wait_cycles);

@@ -13,10 +13,12 @@
 // Teams: one warp per circuit (n <= 11), one CTA per circuit (n <= 14), or one
 // CTA on global scratch (n <= 16).  Warps/CTAs pull circuits from an atomic
 // job counter (costliest first), so one persistent launch runs a whole batch.
+#include "checked.h"
 #include "exact_sq.h"
 #include "tqs_internal.h"
 
 namespace tqs {
+
 namespace {
 
 __device__ __forceinline__ float2 cmul(float2 a, float2 b) {
@@ -372,8 +374,8 @@ __device__ __noinline__ void instr_pass(const FusedLaunch& L, int nint, int bit,
   double s0 = 0.0, s1 = 0.0;
   for (int j = rank; j < half; j += size) {
     const int i0 = ins0(j, bit);
-    s0 += prob_f64(st[swz(i0)]);
-    s1 += prob_f64(st[swz(i0 | m)]);
+    s0 += prob_f64(st[TQS_IX(swz(i0), 2 * half)]);
+    s1 += prob_f64(st[TQS_IX(swz(i0 | m), 2 * half)]);
   }
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
@@ -398,7 +400,7 @@ __device__ __noinline__ void instr_pass(const FusedLaunch& L, int nint, int bit,
   if (rank == 0 && L.outcomes) L.outcomes[k] = outcome;
   const float2 zero = make_float2(0.f, 0.f);
   for (int j = rank; j < half; j += size) {
-    const int a0 = swz(ins0(j, bit)), a1 = swz(ins0(j, bit) | m);
+    const int a0 = TQS_IX(swz(ins0(j, bit)), 2 * half), a1 = TQS_IX(swz(ins0(j, bit) | m), 2 * half);
     const float2 v = outcome ? st[a1] : st[a0];
     const float2 w = make_float2(v.x * sc, v.y * sc);
     st[a0] = (outcome == 0 || reset) ? w : zero;
@@ -445,7 +447,7 @@ __device__ __noinline__ void wide_pass(const FusedLaunch& L, int nint, int k, ui
     float br = 0.f, bi = 0.f;  // hi products
     if (on) {
       for (int c = 0; c < G; ++c) {
-        const float2 x = st[swz(base | wide_local(c, k, bits))];
+        const float2 x = st[TQS_IX(swz(base | wide_local(c, k, bits)), 1 << nint)];
         const float2 h = __ldg(mh + c * G + r), l = __ldg(ml + c * G + r);
         ar = fmaf(l.x, x.x, fmaf(-l.y, x.y, ar));
         ai = fmaf(l.x, x.y, fmaf(l.y, x.x, ai));
@@ -454,7 +456,7 @@ __device__ __noinline__ void wide_pass(const FusedLaunch& L, int nint, int k, ui
       }
     }
     __syncwarp();
-    if (on) st[swz(base | loc_r)] = make_float2(ar + br, ai + bi);
+    if (on) st[TQS_IX(swz(base | loc_r), 1 << nint)] = make_float2(ar + br, ai + bi);
     __syncwarp();
   }
   team_sync<TEAM>();
@@ -471,7 +473,7 @@ __device__ void run_circuit(const FusedLaunch& L, int ci, float2* st, int rank, 
   if (init != nullptr) {
     const int NI = 1 << nint, N = 1 << n;
     for (int i = rank; i < NI; i += size)
-      st[swz(i)] = (i < N) ? init[i] : make_float2(0.f, 0.f);
+      st[TQS_IX(swz(i), NI)] = (i < N) ? init[i] : make_float2(0.f, 0.f);
     team_sync<TEAM>();
   }
   for (int p = 0; p < cd.pass_count; ++p) {
@@ -501,13 +503,13 @@ __device__ void run_circuit(const FusedLaunch& L, int ci, float2* st, int rank, 
           const int off = base | ((j & 1) ? b0 : 0) | ((j & 2) ? b1 : 0) | ((j & 4) ? b2 : 0) | ((j & 8) ? b3 : 0);
           a[j] = make_float2(off == cd.gen_index ? 1.f : 0.f, 0.f);
         } else {
-          a[j] = st[sb ^ ((j & 1) ? w0 : 0) ^ ((j & 2) ? w1 : 0) ^ ((j & 4) ? w2 : 0) ^ ((j & 8) ? w3 : 0)];
+          a[j] = st[TQS_IX(sb ^ ((j & 1) ? w0 : 0) ^ ((j & 2) ? w1 : 0) ^ ((j & 4) ? w2 : 0) ^ ((j & 8) ? w3 : 0), 1 << nint)];
         }
       }
       run_ops(a, ops, count, base, scale);
 #pragma unroll
       for (int j = 0; j < 16; ++j)
-        st[sb ^ ((j & 1) ? w0 : 0) ^ ((j & 2) ? w1 : 0) ^ ((j & 4) ? w2 : 0) ^ ((j & 8) ? w3 : 0)] = a[j];
+        st[TQS_IX(sb ^ ((j & 1) ? w0 : 0) ^ ((j & 2) ? w1 : 0) ^ ((j & 4) ? w2 : 0) ^ ((j & 8) ? w3 : 0), 1 << nint)] = a[j];
     }
     team_sync<TEAM>();
   }
@@ -537,11 +539,12 @@ __device__ void run_circuit(const FusedLaunch& L, int ci, float2* st, int rank, 
       const int gk = k ^ (k >> 1);
       const int i = i0 + (gk << sh);
       const int p0 = p_lo ^ p_hi;
-      float2 v0 = st[swz(p0)];
-      float2 v1 = st[swz(p0 ^ p_one)];
+      float2 v0 = st[TQS_IX(swz(p0), 1 << nint)];
+      float2 v1 = st[TQS_IX(swz(p0 ^ p_one), 1 << nint)];
       if (oscale != 1.0f) { v0 = make_float2(v0.x * oscale, v0.y * oscale); v1 = make_float2(v1.x * oscale, v1.y * oscale); }
-      *reinterpret_cast<float4*>(out + i) = make_float4(v0.x, v0.y, v1.x, v1.y);
-      if (probs) *reinterpret_cast<double2*>(probs + i) = make_double2(prob_f64(v0), prob_f64(v1));
+      *reinterpret_cast<float4*>(out + TQS_IX(i, N - 1)) = make_float4(v0.x, v0.y, v1.x, v1.y);
+      if (probs)
+        *reinterpret_cast<double2*>(probs + TQS_IX(i, N - 1)) = make_double2(prob_f64(v0), prob_f64(v1));
       kahan_add(fmaf(v0.x, v0.x, v0.y * v0.y), nsum, ncomp);
       kahan_add(fmaf(v1.x, v1.x, v1.y * v1.y), nsum, ncomp);
     }
@@ -652,7 +655,7 @@ __global__ void __launch_bounds__(kFsvThreads)
     int ext = 0;
     for (int v = 0; v < F.nfar; ++v) ext |= static_cast<int>((gbase >> F.far[v]) & 1) << (T + v);
     for (int e = tid; e < NT; e += kFsvThreads)
-      st[swz(e)] = g[gbase + hoff[e >> nlow] + (e & lowm)];
+      st[TQS_IX(swz(e), NT)] = g[TQS_IX(gbase + hoff[e >> nlow] + (e & lowm), 1ull << F.n)];
     __syncthreads();
     for (int p = 0; p < cd.pass_count; ++p) {
       const uint4 pr = __ldg(reinterpret_cast<const uint4*>(L.passes + cd.pass_begin + p));
@@ -671,20 +674,20 @@ __global__ void __launch_bounds__(kFsvThreads)
         float2 a[16];
 #pragma unroll
         for (int q = 0; q < 16; ++q)
-          a[q] = st[sb ^ ((q & 1) ? w0 : 0) ^ ((q & 2) ? w1 : 0) ^ ((q & 4) ? w2 : 0) ^ ((q & 8) ? w3 : 0)];
+          a[q] = st[TQS_IX(sb ^ ((q & 1) ? w0 : 0) ^ ((q & 2) ? w1 : 0) ^ ((q & 4) ? w2 : 0) ^ ((q & 8) ? w3 : 0), NT)];
         run_ops(a, ops, count, base | ext, scale);
 #pragma unroll
         for (int q = 0; q < 16; ++q)
-          st[sb ^ ((q & 1) ? w0 : 0) ^ ((q & 2) ? w1 : 0) ^ ((q & 4) ? w2 : 0) ^ ((q & 8) ? w3 : 0)] = a[q];
+          st[TQS_IX(sb ^ ((q & 1) ? w0 : 0) ^ ((q & 2) ? w1 : 0) ^ ((q & 4) ? w2 : 0) ^ ((q & 8) ? w3 : 0), NT)] = a[q];
       }
       __syncthreads();
     }
     // tile qubit i of the result sits at physical tile bit pos[i]
     const float osc = cd.out_scale;
     for (int e = tid; e < NT; e += kFsvThreads) {
-      float2 v = st[swz(cd.identity ? e : pfwd_of(e, pw, T))];
+      float2 v = st[TQS_IX(swz(cd.identity ? e : pfwd_of(e, pw, T)), NT)];
       if (osc != 1.0f) v = make_float2(v.x * osc, v.y * osc);
-      g[gbase + hoff[e >> nlow] + (e & lowm)] = v;
+      g[TQS_IX(gbase + hoff[e >> nlow] + (e & lowm), 1ull << F.n)] = v;
     }
     __syncthreads();
   }
@@ -754,6 +757,8 @@ cudaError_t launch_fsv_tile(const FusedLaunch& L, const FsvTile& F, cudaStream_t
   count_launches(1);
   return cudaGetLastError();
 }
+
+TQS_DEFINE_VIOLATIONS(violations_fused)
 
 cudaError_t launch_fused(const FusedLaunch& L, cudaStream_t s) {
   if (L.n_jobs <= 0) return cudaSuccess;

@@ -2,6 +2,7 @@
 // written out as a dense matrix) and stage 6 applied per step (eq. 11, dense
 // matrix-vector product).  This is the baseline the fused kernel is measured
 // against; both kernels stream the 2^n x 2^n complex64 matrix through HBM.
+#include "checked.h"
 #include "step_entry.h"
 #include "tqs_internal.h"
 
@@ -19,7 +20,8 @@ __global__ void __launch_bounds__(kMatThreads)
                        float2* __restrict__ S) {
   __shared__ StepFactor fs[kMaxFactors];
   for (int i = threadIdx.x; i < nf * static_cast<int>(sizeof(StepFactor) / 8); i += blockDim.x)
-    reinterpret_cast<float2*>(fs)[i] = reinterpret_cast<const float2*>(factors)[i];
+    reinterpret_cast<float2*>(fs)[TQS_IX(i, int(sizeof(fs) / 8))] =
+        reinterpret_cast<const float2*>(factors)[i];
   __syncthreads();
   const int64_t N = int64_t(1) << n;
   const int64_t pairs = (N * N) >> 1;
@@ -30,7 +32,7 @@ __global__ void __launch_bounds__(kMatThreads)
     const uint32_t c = static_cast<uint32_t>(flat & (N - 1));
     const float2 v0 = step_entry(fs, nf, idle, r, c);
     const float2 v1 = step_entry(fs, nf, idle, r, c + 1);
-    __stcs(reinterpret_cast<float4*>(S + flat), make_float4(v0.x, v0.y, v1.x, v1.y));
+    __stcs(reinterpret_cast<float4*>(S) + TQS_IX(e, pairs), make_float4(v0.x, v0.y, v1.x, v1.y));
   }
 }
 
@@ -44,12 +46,12 @@ __global__ void __launch_bounds__(kMvWarps * 32)
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int64_t row = int64_t(blockIdx.x) * kMvWarps + warp;
   if (row >= N) return;
-  const float4* srow = reinterpret_cast<const float4*>(S + row * N);
+  const float4* srow = reinterpret_cast<const float4*>(S) + TQS_IX(row, N) * (N >> 1);
   const float4* x4 = reinterpret_cast<const float4*>(x);
   float re = 0.f, im = 0.f;
   for (int64_t k = lane; k < (N >> 1); k += 32) {
-    const float4 s = __ldcs(srow + k);
-    const float4 v = __ldg(x4 + k);
+    const float4 s = __ldcs(srow + TQS_IX(k, N >> 1));
+    const float4 v = __ldg(x4 + TQS_IX(k, N >> 1));
     re = fmaf(s.x, v.x, re);
     re = fmaf(-s.y, v.y, re);
     re = fmaf(s.z, v.z, re);
@@ -66,6 +68,12 @@ __global__ void __launch_bounds__(kMvWarps * 32)
   }
   if (lane == 0) y[row] = make_float2(re, im);
 }
+
+}  // namespace
+
+TQS_DEFINE_VIOLATIONS(violations_plain)
+
+namespace {
 
 int sm_count() {
   static int sms = 0;

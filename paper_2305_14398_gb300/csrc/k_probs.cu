@@ -10,6 +10,7 @@
 #include <mutex>
 
 #include "../../include/tqs.h"
+#include "checked.h"
 #include "tqs_internal.h"
 
 namespace tqs {
@@ -27,24 +28,24 @@ __global__ void __launch_bounds__(kProbThreads)
   if (end > N) end = N;
   double acc = 0.0;
   for (int64_t i = begin + 2 * threadIdx.x; i < end; i += 2 * kProbThreads) {
-    const float4 v = __ldcs(reinterpret_cast<const float4*>(st + i));
+    const float4 v = __ldcs(reinterpret_cast<const float4*>(st) + TQS_IX(i >> 1, N >> 1));
     const double x0 = v.x, y0 = v.y, x1 = v.z, y1 = v.w;
     const double q0 = fma(x0, x0, y0 * y0);
     const double q1 = fma(x1, x1, y1 * y1);
-    if (probs) __stcs(reinterpret_cast<double2*>(probs + i), make_double2(q0, q1));
+    if (probs) __stcs(reinterpret_cast<double2*>(probs) + TQS_IX(i >> 1, N >> 1), make_double2(q0, q1));
     if ((static_cast<uint64_t>(i) & zero_mask) == 0) acc += q0;
     if ((static_cast<uint64_t>(i + 1) & zero_mask) == 0) acc += q1;
   }
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
   __shared__ double red[kProbThreads / 32];
-  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+  if ((threadIdx.x & 31) == 0) red[TQS_IX(threadIdx.x >> 5, kProbThreads / 32)] = acc;
   __syncthreads();
   if (threadIdx.x == 0) {
     double s = 0.0;
 #pragma unroll
     for (int w = 0; w < kProbThreads / 32; ++w) s += red[w];
-    partials[blockIdx.x] = s;
+    partials[TQS_IX(blockIdx.x, gridDim.x)] = s;
   }
 }
 
@@ -58,6 +59,8 @@ __global__ void sum_partials_kernel(const double* __restrict__ partials, int cou
 }
 
 }  // namespace
+
+TQS_DEFINE_VIOLATIONS(violations_probs)
 
 int probs_partial_count(int n) {
   const int64_t N = int64_t(1) << n;

@@ -29,6 +29,7 @@
 // in shared memory by one CTA each, which builds the tables there and runs
 // every shot of the segment; larger segments use three kernels over global
 // memory (block tables, block prefix, shots).
+#include "checked.h"
 #include "tqs_internal.h"
 
 namespace tqs {
@@ -65,7 +66,7 @@ __device__ __forceinline__ double block_tables(const double* p, int64_t len, int
   const int64_t i0 = b * kSampleBlk + int64_t(lane) * kSampleChunk;
   double t = 0.0;
 #pragma unroll
-  for (int j = 0; j < kSampleChunk; ++j) t += (i0 + j < len) ? p[i0 + j] : 0.0;
+  for (int j = 0; j < kSampleChunk; ++j) t += (i0 + j < len) ? p[TQS_IX(i0 + j, len)] : 0.0;
   const double incl = warp_incl_scan(t, lane);
   const double up = __shfl_up_sync(kFull, incl, 1);
   cpre[lane] = lane > 0 ? up : 0.0;
@@ -83,11 +84,11 @@ __device__ void block_prefix_cta(const double* bs, double* bp, int64_t nb, doubl
   const int64_t b0 = int64_t(t) * chunk;
   const int64_t b1 = b0 + chunk < nb ? b0 + chunk : nb;
   double s = 0.0;
-  for (int64_t b = b0; b < b1; ++b) s += bs[b];
+  for (int64_t b = b0; b < b1; ++b) s += bs[TQS_IX(b, nb)];
   const double incl = warp_incl_scan(s, lane);
   const double up = __shfl_up_sync(kFull, incl, 1);
   const double excl = lane > 0 ? up : 0.0;
-  if (lane == 31) wtot[warp] = incl;
+  if (lane == 31) wtot[TQS_IX(warp, kThreads / 32)] = incl;
   __syncthreads();
   if (t == 0) {
     double a = 0.0;
@@ -96,8 +97,8 @@ __device__ void block_prefix_cta(const double* bs, double* bp, int64_t nb, doubl
   __syncthreads();
   double acc = wpre[warp] + excl;
   for (int64_t b = b0; b < b1; ++b) {
-    bp[b] = acc;
-    acc += bs[b];
+    bp[TQS_IX(b, nb)] = acc;
+    acc += bs[TQS_IX(b, nb)];
   }
   if (b0 < nb && b1 == nb) *tot = acc;
 }
@@ -110,14 +111,15 @@ __device__ __forceinline__ bool le_bits(double a, double b) {
 // Chunk prefixes of the blocks [0, nb) made absolute: cp[b * 32 + l] becomes
 // bp[b] + cp[b * 32 + l] (whole CTA).
 __device__ void absolute_chunks(const double* bp, double* cp, int64_t nb) {
-  for (int64_t e = threadIdx.x; e < nb * kChunks; e += kThreads) cp[e] = bp[e / kChunks] + cp[e];
+  for (int64_t e = threadIdx.x; e < nb * kChunks; e += kThreads)
+    cp[e] = bp[TQS_IX(e / kChunks, nb)] + cp[e];
 }
 
 // Last index <= i with p > 0, or -1 (one thread; reached only after rounding
 // or for u T >= T).
-__device__ int64_t last_nonzero_upto(const double* p, int64_t i) {
+__device__ int64_t last_nonzero_upto(const double* p, int64_t len, int64_t i) {
   for (; i >= 0; --i)
-    if (__double_as_longlong(p[i]) > 0) return i;
+    if (__double_as_longlong(p[TQS_IX(i, len)]) > 0) return i;
   return -1;
 }
 
@@ -126,28 +128,28 @@ __device__ int64_t last_nonzero_upto(const double* p, int64_t i) {
 __device__ int64_t sample_shot(const double* p, int64_t len, const double* bp, const double* cp,
                                int64_t nb, double T, double u) {
   const double target = u * T;
-  if (!(target < T)) return last_nonzero_upto(p, len - 1);
+  if (!(target < T)) return last_nonzero_upto(p, len, len - 1);
   int64_t lo = 0, hi = nb - 1;
   while (lo < hi) {
     const int64_t mid = (lo + hi + 1) >> 1;
-    if (le_bits(bp[mid], target)) lo = mid; else hi = mid - 1;
+    if (le_bits(bp[TQS_IX(mid, nb)], target)) lo = mid; else hi = mid - 1;
   }
   const int64_t b = lo;
-  const double* cpb = cp + b * kChunks;
+  const double* cpb = cp + TQS_IX(b, nb) * kChunks;
   int l = 0, h = kChunks - 1;
   while (l < h) {
     const int mid = (l + h + 1) >> 1;
-    if (le_bits(cpb[mid], target)) l = mid; else h = mid - 1;
+    if (le_bits(cpb[TQS_IX(mid, kChunks)], target)) l = mid; else h = mid - 1;
   }
   const int64_t i0 = b * kSampleBlk + int64_t(l) * kSampleChunk;
-  double c = cpb[l];
+  double c = cpb[TQS_IX(l, kChunks)];
   for (int j = 0; j < kSampleChunk && i0 + j < len; ++j) {
-    const double x = p[i0 + j];
+    const double x = p[TQS_IX(i0 + j, len)];
     c += x;
     if (__double_as_longlong(x) > 0 && !le_bits(c, target)) return i0 + j;
   }
   const int64_t end = i0 + kSampleChunk - 1 < len - 1 ? i0 + kSampleChunk - 1 : len - 1;
-  return last_nonzero_upto(p, end);
+  return last_nonzero_upto(p, len, end);
 }
 
 // ------------------------------------------------------------ global path
@@ -158,17 +160,19 @@ __global__ void __launch_bounds__(kThreads)
   const int64_t warps = int64_t(gridDim.x) * (kThreads / 32);
   for (int64_t gb = int64_t(blockIdx.x) * (kThreads / 32) + (threadIdx.x >> 5); gb < L.nblocks;
        gb += warps) {
-    const SampleSeg sg = L.gsegs[seg_of_block(L.gsegs, L.n_gseg, gb)];
+    const SampleSeg sg = L.gsegs[TQS_IX(seg_of_block(L.gsegs, L.n_gseg, gb), L.n_gseg)];
+    (void)TQS_IX(sg.p_off + (int64_t(1) << sg.n) - 1, L.probs_len);
     const double t = block_tables(L.probs + sg.p_off, int64_t(1) << sg.n, gb - sg.blk_off, lane,
-                                  L.cpre + gb * kChunks);
-    if (lane == 0) L.bsum[gb] = t;
+                                  L.cpre + TQS_IX(gb, L.nblocks) * kChunks);
+    if (lane == 0) L.bsum[TQS_IX(gb, L.nblocks)] = t;
   }
 }
 
 __global__ void __launch_bounds__(kThreads)
     block_prefix_kernel(const SampleLaunch L) {
   __shared__ double wtot[kThreads / 32], wpre[kThreads / 32];
-  const SampleSeg sg = L.gsegs[blockIdx.x];
+  const SampleSeg sg = L.gsegs[TQS_IX(blockIdx.x, L.n_gseg)];
+  (void)TQS_IX(sg.blk_off + sample_blocks(sg.n) - 1, L.nblocks);
   block_prefix_cta(L.bsum + sg.blk_off, L.bpre + sg.blk_off, sample_blocks(sg.n),
                    L.tot + blockIdx.x, wtot, wpre);
   __syncthreads();
@@ -181,8 +185,8 @@ __global__ void __launch_bounds__(kThreads)
   for (int64_t k = int64_t(blockIdx.x) * kThreads + threadIdx.x; k < total;
        k += int64_t(gridDim.x) * kThreads) {
     const int g = static_cast<int>(k / L.shots);
-    const SampleSeg sg = L.gsegs[g];
-    const int64_t kk = sg.index * L.shots + (k - int64_t(g) * L.shots);
+    const SampleSeg sg = L.gsegs[TQS_IX(g, L.n_gseg)];
+    const int64_t kk = TQS_IX(sg.index * L.shots + (k - int64_t(g) * L.shots), L.n_segs * L.shots);
     L.out[kk] = sample_shot(L.probs + sg.p_off, int64_t(1) << sg.n, L.bpre + sg.blk_off,
                             L.cpre + int64_t(sg.blk_off) * kChunks, sample_blocks(sg.n), L.tot[g],
                             L.u[kk]);
@@ -200,31 +204,35 @@ __global__ void __launch_bounds__(kThreads)
   __shared__ double s_tot;
   constexpr int kMaxBlocks = 1 << (kSampleSmemMaxQ - 8);
   __shared__ double sbs[kMaxBlocks], sbp[kMaxBlocks];
-  const SampleSeg sg = L.ssegs[blockIdx.x];
+  const SampleSeg sg = L.ssegs[TQS_IX(blockIdx.x, L.n_sseg)];
   const int64_t len = int64_t(1) << sg.n;
   const int64_t nb = sample_blocks(sg.n);
   double* sp = sm;
   double* scp = sm + (size_t(1) << L.smem_q);
   const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+  const int64_t qlen = int64_t(1) << L.smem_q;
+  const int64_t nchunks = (qlen < kSampleBlk ? kSampleBlk : qlen) / kSampleChunk;
+  (void)TQS_IX(sg.p_off + len - 1, L.probs_len);
   const double2* gp = reinterpret_cast<const double2*>(L.probs + sg.p_off);
   for (int64_t i = t; i < len / 2; i += kThreads) {
     const double2 v = __ldcs(gp + i);
-    sp[2 * i] = v.x;
-    sp[2 * i + 1] = v.y;
+    sp[TQS_IX(2 * i, qlen)] = v.x;
+    sp[TQS_IX(2 * i + 1, qlen)] = v.y;
   }
   __syncthreads();
   for (int64_t b = warp; b < nb; b += kThreads / 32) {
-    const double bt = block_tables(sp, len, b, lane, scp + b * kChunks);
-    if (lane == 0) sbs[b] = bt;
+    const double bt = block_tables(sp, len, b, lane, scp + TQS_IX(b * kChunks + lane, nchunks) - lane);
+    if (lane == 0) sbs[TQS_IX(b, kMaxBlocks)] = bt;
   }
   __syncthreads();
+  (void)TQS_IX(nb - 1, kMaxBlocks);
   block_prefix_cta(sbs, sbp, nb, &s_tot, wtot, wpre);
   __syncthreads();
   absolute_chunks(sbp, scp, nb);
   __syncthreads();
   const double T = s_tot;
   for (int64_t k = t; k < L.shots; k += kThreads) {
-    const int64_t kk = sg.index * L.shots + k;
+    const int64_t kk = TQS_IX(sg.index * L.shots + k, L.n_segs * L.shots);
     L.out[kk] = sample_shot(sp, len, sbp, scp, nb, T, __ldcs(L.u + kk));
   }
 }
@@ -243,6 +251,8 @@ int grid_for(int64_t items, int per_cta) {
 }
 
 }  // namespace
+
+TQS_DEFINE_VIOLATIONS(violations_sample)
 
 cudaError_t launch_sample(const SampleLaunch& L, cudaStream_t s) {
   int k = 0;

@@ -1399,7 +1399,7 @@ tqs_status tqs_marginal_zero(const tqs_c64* d_state, int n, uint64_t mask, doubl
 // Segment tables of an inverse-CDF sampling call (see k_sample.cu).
 struct SamplePlan {
   std::vector<SampleSeg> gsegs, ssegs;
-  int64_t nblocks = 0;
+  int64_t nblocks = 0, probs_end = 0, n_segs = 0;
   int smem_q = 0;
   size_t off_g = 0, off_s = 0, off_bsum = 0, off_bpre = 0, off_cpre = 0, off_tot = 0, bytes = 0;
   void layout() {
@@ -1415,6 +1415,8 @@ struct SamplePlan {
   // Segment `index` of 2^n probabilities at p_off; small ones go to the
   // shared-memory path when allowed.
   void add(int64_t index, int64_t p_off, int n, bool allow_smem) {
+    probs_end = std::max(probs_end, p_off + (int64_t(1) << n));
+    n_segs = std::max(n_segs, index + 1);
     if (allow_smem && n <= kSampleSmemMaxQ) {
       ssegs.push_back(SampleSeg{p_off, n, 0, index});
       smem_q = std::max(smem_q, n);
@@ -1450,6 +1452,8 @@ struct SamplePlan {
     L.u = u;
     L.shots = shots;
     L.out = out;
+    L.probs_len = probs_end;
+    L.n_segs = n_segs;
     return L;
   }
 };
@@ -2412,6 +2416,21 @@ tqs_status tqs_server_destroy(tqs_server* sv) {
 }  // extern "C"
 
 extern "C" {
+
+tqs_status tqs_check_violations(uint32_t* count, int reset) {
+  if (!count) return fail(TQS_ERR_ARG, "tqs_check_violations: count is NULL");
+  using Counter = cudaError_t (*)(unsigned int*, bool);
+  static const Counter counters[] = {violations_fused,  violations_plain,      violations_probs,
+                                     violations_sample, violations_chain_simt, violations_chain_tc};
+  uint32_t total = 0;
+  for (Counter f : counters) {
+    unsigned int v = 0;
+    TQS_CUDA(f(&v, reset != 0), "tqs_check_violations");
+    total += v;
+  }
+  *count = total;
+  return TQS_OK;
+}
 
 tqs_status tqs_set_allocator(tqs_alloc_fn alloc, tqs_free_fn free_fn, void* ctx) {
   if ((alloc == nullptr) != (free_fn == nullptr))

@@ -222,6 +222,8 @@ struct SampleLaunch {
   const double* u;         // device [segments * shots] uniforms in [0, 1)
   int64_t shots;           // per segment
   int64_t* out;            // device [segments * shots] sampled indices within the segment
+  int64_t probs_len;       // entries of probs the segments span (bounds checks)
+  int64_t n_segs;          // segments (bounds checks: u and out hold n_segs * shots)
 };
 
 cudaError_t launch_sample(const SampleLaunch& L, cudaStream_t s);
@@ -257,6 +259,16 @@ struct FsvTile {
 
 // One pass over the state: L.circs points at the pass's tile program.
 cudaError_t launch_fsv_tile(const FusedLaunch& L, const FsvTile& F, cudaStream_t s);
+
+// Out-of-range accesses counted by the bounds-checked build (-DTQS_CHECKED;
+// always 0 otherwise) in the kernels of one source file, optionally reset.
+// Synchronous.
+cudaError_t violations_fused(unsigned int* count, bool reset);
+cudaError_t violations_plain(unsigned int* count, bool reset);
+cudaError_t violations_probs(unsigned int* count, bool reset);
+cudaError_t violations_sample(unsigned int* count, bool reset);
+cudaError_t violations_chain_simt(unsigned int* count, bool reset);
+cudaError_t violations_chain_tc(unsigned int* count, bool reset);
 
 // Process-wide count of kernel launches enqueued by this library.
 void count_launches(int64_t k);
