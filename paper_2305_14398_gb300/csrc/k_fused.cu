@@ -347,6 +347,14 @@ __device__ __forceinline__ int pfwd_of(int v, const PosMap& pm, int n) {
   for (int q = 0; q < n; ++q) if ((v >> q) & 1) r |= pfwd_bit(q, pm);
   return r;
 }
+// Prefetch [p, p + bytes) into L1, one 128-byte line per thread of the team.
+__device__ __forceinline__ void prefetch_l1_range(const void* p, size_t bytes, int rank, int size) {
+  const uintptr_t a = reinterpret_cast<uintptr_t>(p);
+  const uintptr_t end = a + bytes;
+  for (uintptr_t l = (a & ~uintptr_t(127)) + uintptr_t(rank) * 128; l < end; l += uintptr_t(size) * 128)
+    asm volatile("prefetch.global.L1 [%0];" ::"l"(l));
+}
+
 // Barrier of the threads working on one circuit: the warp, the warp pair
 // (named barrier 1 + pair index, 64 threads) or the CTA.
 template <int TEAM>
@@ -464,10 +472,14 @@ __device__ __noinline__ void wide_pass(const FusedLaunch& L, int nint, int k, ui
 
 template <int TEAM>
 __device__ void run_circuit(const FusedLaunch& L, int ci, float2* st, int rank, int size,
-                            double* s_red) {
+                            double* s_red, int& next_job, int& next_ci, int* s_slot) {
   const FusedCirc cd = L.circs[ci];
   const int nint = cd.nint;
   const int n = cd.n;
+  // The team brings the circuit's pass and op records into L1 together: one
+  // L2 round trip, instead of one per op for the first group of each pass.
+  prefetch_l1_range(L.passes + cd.pass_begin, cd.pass_count * sizeof(FusedPass), rank, size);
+  prefetch_l1_range(L.ops + cd.op_begin, cd.op_count * sizeof(FusedOp), rank, size);
   const int G = 1 << (nint - 4);
   const float2* init = cd.init;
   if (init != nullptr) {
@@ -513,6 +525,18 @@ __device__ void run_circuit(const FusedLaunch& L, int ci, float2* st, int rank, 
     }
     team_sync<TEAM>();
   }
+  // Warp and pair teams: the next job (its atomic was issued when this
+  // circuit started) is shared with the team here and its circuit index is
+  // loaded, so both latencies hide behind the output phase.
+  if (TEAM == TEAM_WARP) {
+    next_job = __shfl_sync(0xffffffffu, next_job, 0);
+  } else if (TEAM == TEAM_PAIR) {
+    if (rank == 0) *s_slot = next_job;
+    team_sync<TEAM>();
+    next_job = *s_slot;
+  }
+  if (TEAM == TEAM_WARP || TEAM == TEAM_PAIR)
+    next_ci = next_job < L.n_jobs ? __ldg(L.order + next_job) : 0;
   // Output: logical index i holds the amplitude at physical index P(i).  A
   // thread writes i = 2 rank + 2 size k (two amplitudes, one 16-byte store);
   // k runs in Gray-code order so P(i) changes by one XOR per iteration.
@@ -561,6 +585,8 @@ __device__ void run_circuit(const FusedLaunch& L, int ci, float2* st, int rank, 
     team_sync<TEAM>();
     if (rank == 0) { double s = 0.0; for (int w = 0; w < (size >> 5); ++w) s += s_red[w]; if (L.norms) L.norms[ci] = s; }
   }
+  if ((TEAM == TEAM_WARP || TEAM == TEAM_PAIR) && rank == 0 && next_job < L.n_jobs)
+    prefetch_l1_range(L.circs + next_ci, sizeof(FusedCirc), 0, 1);
   team_sync<TEAM>();
 }
 
@@ -575,23 +601,32 @@ __global__ void __launch_bounds__(TEAM == TEAM_CTA ? kCtaThreads : 512)
     __shared__ double s_red[8][4];
     const int pair = threadIdx.x >> 6, rank = threadIdx.x & 63;
     float2* st = smem + (static_cast<size_t>(pair) << L.slice_q);
-    for (;;) {
-      if (rank == 0) s_job[pair] = atomicAdd(L.counter, 1);
-      team_sync<TEAM_PAIR>();
-      const int job = s_job[pair];
-      team_sync<TEAM_PAIR>();
-      if (job >= L.n_jobs) break;
-      run_circuit<TEAM_PAIR>(L, L.order[job], st, rank, 64, s_red[pair]);
+    // Each circuit takes the team's next job from the counter when it starts
+    // and hands it over before its output phase (run_circuit).
+    if (rank == 0) s_job[pair] = atomicAdd(L.counter, 1);
+    team_sync<TEAM_PAIR>();
+    int job = s_job[pair];
+    team_sync<TEAM_PAIR>();
+    int ci = job < L.n_jobs ? __ldg(L.order + job) : 0;
+    while (job < L.n_jobs) {
+      int next_job = rank == 0 ? atomicAdd(L.counter, 1) : 0;
+      int next_ci = 0;
+      run_circuit<TEAM_PAIR>(L, ci, st, rank, 64, s_red[pair], next_job, next_ci, &s_job[pair]);
+      job = next_job;
+      ci = next_ci;
     }
   } else if (TEAM == TEAM_WARP) {
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     float2* st = smem + (static_cast<size_t>(warp) << L.slice_q);
-    for (;;) {
-      int job = 0;
-      if (lane == 0) job = atomicAdd(L.counter, 1);
-      job = __shfl_sync(0xffffffffu, job, 0);
-      if (job >= L.n_jobs) break;
-      run_circuit<TEAM_WARP>(L, L.order[job], st, lane, 32, nullptr);
+    int job = lane == 0 ? atomicAdd(L.counter, 1) : 0;
+    job = __shfl_sync(0xffffffffu, job, 0);
+    int ci = job < L.n_jobs ? __ldg(L.order + job) : 0;
+    while (job < L.n_jobs) {
+      int next_job = lane == 0 ? atomicAdd(L.counter, 1) : 0;
+      int next_ci = 0;
+      run_circuit<TEAM_WARP>(L, ci, st, lane, 32, nullptr, next_job, next_ci, nullptr);
+      job = next_job;
+      ci = next_ci;
     }
   } else {
     __shared__ int s_job;
@@ -605,7 +640,9 @@ __global__ void __launch_bounds__(TEAM == TEAM_CTA ? kCtaThreads : 512)
       const int job = s_job;
       __syncthreads();
       if (job >= L.n_jobs) break;
-      run_circuit<TEAM>(L, L.order[job], st, threadIdx.x, blockDim.x, s_red);
+      int unused_job = 0, unused_ci = 0;
+      run_circuit<TEAM>(L, L.order[job], st, threadIdx.x, blockDim.x, s_red, unused_job, unused_ci,
+                        nullptr);
     }
   }
 }

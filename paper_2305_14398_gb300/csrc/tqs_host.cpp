@@ -751,14 +751,15 @@ struct Image {
     else ps.op_begin += static_cast<uint32_t>(op0);
     return ps;
   }
-  static FusedCirc circ_of(const Program& P, int64_t pass0, int64_t out_off) {
+  static FusedCirc circ_of(const Program& P, int64_t pass0, int64_t op0, int64_t out_off) {
     FusedCirc fc{};
-    fc.n = P.n;
-    fc.nint = P.nint;
+    fc.n = static_cast<int16_t>(P.n);
+    fc.nint = static_cast<int16_t>(P.nint);
     fc.pass_begin = static_cast<int32_t>(pass0);
     fc.pass_count = static_cast<int32_t>(P.passes.size());
     fc.out_off = out_off;
-    fc.team = team_for(P.nint);
+    fc.op_begin = static_cast<int32_t>(op0);
+    fc.op_count = static_cast<int32_t>(P.ops.size());
     fc.identity = P.identity;
     std::memcpy(fc.pos, P.pos, 16);
     fc.init = nullptr;
@@ -770,7 +771,7 @@ struct Image {
   void add(const Program& P, int64_t out_off) {
     if (segs.empty()) segs.push_back(take_seg());
     ImageSeg& sg = segs.back();
-    circs.push_back(circ_of(P, static_cast<int64_t>(npass), out_off));
+    circs.push_back(circ_of(P, static_cast<int64_t>(npass), static_cast<int64_t>(nop), out_off));
     for (const FusedPass& ps : P.passes)
       sg.passes.push_back(rebase(ps, static_cast<int64_t>(nop), 0, static_cast<int64_t>(ncoef)));
     sg.ops.insert(sg.ops.end(), P.ops.begin(), P.ops.end());
@@ -1610,12 +1611,13 @@ static tqs_status batch_finish(tqs_batch* b, const std::vector<CircMeta>& progs,
     const int64_t o0 = obase[m.seg] + static_cast<int64_t>(m.lo);
     const int64_t c0 = cbase[m.seg] + static_cast<int64_t>(m.lc);
     FusedCirc fc{};
-    fc.n = m.n;
-    fc.nint = m.nint;
+    fc.n = static_cast<int16_t>(m.n);
+    fc.nint = static_cast<int16_t>(m.nint);
     fc.pass_begin = static_cast<int32_t>(p0);
     fc.pass_count = static_cast<int32_t>(m.np);
     fc.out_off = b->offsets[i];
-    fc.team = team_for(m.nint);
+    fc.op_begin = static_cast<int32_t>(o0);
+    fc.op_count = static_cast<int32_t>(m.no);
     fc.identity = m.identity;
     std::memcpy(fc.pos, m.pos, 16);
     fc.init = nullptr;

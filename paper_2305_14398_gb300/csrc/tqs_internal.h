@@ -92,13 +92,14 @@ static_assert(sizeof(FusedPass) == 16, "FusedPass layout");
 enum TeamKind : int32_t { TEAM_WARP = 0, TEAM_CTA = 1, TEAM_GLOBAL = 2, TEAM_PAIR = 3 };
 
 struct alignas(16) FusedCirc {
-  int32_t n;            // logical qubits
-  int32_t nint;         // internal qubits = max(n, 4)
+  int16_t n;            // logical qubits
+  int16_t nint;         // internal qubits = max(n, 4)
   int32_t pass_begin;   // index into the pass array
   int32_t pass_count;
-  int64_t out_off;      // amplitude offset of this circuit's outputs
-  int32_t team;         // TeamKind
   int32_t identity;     // 1 if the output qubit map is the identity
+  int64_t out_off;      // amplitude offset of this circuit's outputs
+  int32_t op_begin;     // the circuit's op records: [op_begin, op_begin + op_count)
+  int32_t op_count;     //   (prefetched into L1 when the circuit starts)
   uint8_t pos[16];      // physical bit of logical qubit q at the end
   const float2* init;   // initial state (logical order) or nullptr for a basis state
   float out_scale;      // 1, or 2^-1/2 when an odd Hadamard factor is left over

@@ -4,6 +4,8 @@
 
 chain: the 40-step random layered circuit-unitary chain at n = COUNT
        (tensor-core BF16x3);
+fsv:   the full-state-vector backend on a random layered circuit
+       (10 x (U3 on every qubit + CNOTs on n/2 seeded pairs)) at n = COUNT;
 mix:   COUNT paper-shaped 11-qubit circuits (GHZ / DJ-constant / DJ-balanced /
        QFT, 25 % each); ghz, dj_constant, dj_balanced, qft: COUNT circuits of one
        of those kinds; batch: the first COUNT circuits of the random batched
@@ -37,6 +39,25 @@ def chain(n, reps):
     B.tqs_circuit_destroy(c)
 
 
+def fsv(n, reps):
+    ops = W.random_layered(n, 10, (9, n))
+    c = B.circuit_from_ops(n, ops)
+    st = torch.zeros(1 << n, dtype=torch.complex64, device="cuda")
+    st[0] = 1.0
+    passes, _ = B.tqs_fsv_passes(c)
+    for _ in range(reps):
+        B.tqs_simulate_fsv(c, st)
+    torch.cuda.synchronize()
+    s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    s.record()
+    B.tqs_simulate_fsv(c, st)
+    e.record()
+    torch.cuda.synchronize()
+    print("fsv", n, "passes", passes, "ms %.3f" % s.elapsed_time(e),
+          "norm %.7f" % float((st.abs() ** 2).sum()))
+    B.tqs_circuit_destroy(c)
+
+
 def main(argv):
     count = int(argv[1]) if len(argv) > 1 else 2048
     kind = argv[2] if len(argv) > 2 else "mix"
@@ -49,6 +70,8 @@ def main(argv):
             B.tqs_set_option(B.OPT_WARPS_PER_CTA, 11, w)
     if kind == "chain":
         return chain(count, reps)
+    if kind == "fsv":
+        return fsv(count, reps)
     if kind == "mix":
         circs = [(11, ops) for _, ops in W.paper_mix(11, count)]
     elif kind in ("ghz", "dj_constant", "dj_balanced", "qft"):
