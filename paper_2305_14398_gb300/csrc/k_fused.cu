@@ -72,16 +72,22 @@ __device__ __forceinline__ float2 sel(bool on, float2 y, float2 x) {
   return make_float2(on ? y.x : x.x, on ? y.y : x.y);
 }
 
-template <int T>
+// CTRL = false: every pair (an uncontrolled factor, no selects).
+template <int T, bool CTRL>
 __device__ __forceinline__ void dense_t(float2 (&a)[16], const Coef& m, unsigned act) {
 #pragma unroll
   for (int p = 0; p < 8; ++p) {
     const int j0 = ((p >> T) << (T + 1)) | (p & ((1 << T) - 1));
     const int j1 = j0 | (1 << T);
-    const bool on = (act >> j0) & 1;
     const float2 x0 = a[j0], x1 = a[j1];
-    a[j0] = sel(on, cmac2_hl(m.h[0], m.l[0], x0, m.h[1], m.l[1], x1), x0);
-    a[j1] = sel(on, cmac2_hl(m.h[2], m.l[2], x0, m.h[3], m.l[3], x1), x1);
+    if (CTRL) {
+      const bool on = (act >> j0) & 1;
+      a[j0] = sel(on, cmac2_hl(m.h[0], m.l[0], x0, m.h[1], m.l[1], x1), x0);
+      a[j1] = sel(on, cmac2_hl(m.h[2], m.l[2], x0, m.h[3], m.l[3], x1), x1);
+    } else {
+      a[j0] = cmac2_hl(m.h[0], m.l[0], x0, m.h[1], m.l[1], x1);
+      a[j1] = cmac2_hl(m.h[2], m.l[2], x0, m.h[3], m.l[3], x1);
+    }
   }
 }
 
@@ -192,6 +198,11 @@ __device__ __forceinline__ float2 f2(unsigned x, unsigned y) {
 // Apply the ops of one pass to the 16 amplitudes of one group, then the
 // pass's exact power-of-two scale.  The next op's header is fetched while the
 // current one runs.
+// SPLIT_DENSE: uncontrolled dense factors take a select-free copy of the
+// butterfly (more code; the full-state-vector tiles, dominated by dense
+// single-qubit factors, use it; the fused teams keep one copy, which keeps
+// them free of register spills).
+template <bool SPLIT_DENSE>
 __device__ __forceinline__ void run_ops(float2 (&a)[16], const FusedOp* __restrict__ ops,
                                         uint32_t count, int base, float scale) {
   Pending pd;
@@ -255,11 +266,20 @@ __device__ __forceinline__ void run_ops(float2 (&a)[16], const FusedOp* __restri
         m.l[1] = f2(q3.z, q3.w);
         m.l[2] = f2(q4.x, q4.y);
         m.l[3] = f2(q4.z, q4.w);
-        switch (t) {
-          case 0: dense_t<0>(a, m, act); break;
-          case 1: dense_t<1>(a, m, act); break;
-          case 2: dense_t<2>(a, m, act); break;
-          default: dense_t<3>(a, m, act); break;
+        if (SPLIT_DENSE && code < OPC_CDENSE) {
+          switch (t) {
+            case 0: dense_t<0, false>(a, m, act); break;
+            case 1: dense_t<1, false>(a, m, act); break;
+            case 2: dense_t<2, false>(a, m, act); break;
+            default: dense_t<3, false>(a, m, act); break;
+          }
+        } else {
+          switch (t) {
+            case 0: dense_t<0, true>(a, m, act); break;
+            case 1: dense_t<1, true>(a, m, act); break;
+            case 2: dense_t<2, true>(a, m, act); break;
+            default: dense_t<3, true>(a, m, act); break;
+          }
         }
       }
       continue;
@@ -518,7 +538,7 @@ __device__ void run_circuit(const FusedLaunch& L, int ci, float2* st, int rank, 
           a[j] = st[TQS_IX(sb ^ ((j & 1) ? w0 : 0) ^ ((j & 2) ? w1 : 0) ^ ((j & 4) ? w2 : 0) ^ ((j & 8) ? w3 : 0), 1 << nint)];
         }
       }
-      run_ops(a, ops, count, base, scale);
+      run_ops<false>(a, ops, count, base, scale);
 #pragma unroll
       for (int j = 0; j < 16; ++j)
         st[TQS_IX(sb ^ ((j & 1) ? w0 : 0) ^ ((j & 2) ? w1 : 0) ^ ((j & 4) ? w2 : 0) ^ ((j & 8) ? w3 : 0), 1 << nint)] = a[j];
@@ -712,7 +732,7 @@ __global__ void __launch_bounds__(kFsvThreads)
 #pragma unroll
         for (int q = 0; q < 16; ++q)
           a[q] = st[TQS_IX(sb ^ ((q & 1) ? w0 : 0) ^ ((q & 2) ? w1 : 0) ^ ((q & 4) ? w2 : 0) ^ ((q & 8) ? w3 : 0), NT)];
-        run_ops(a, ops, count, base | ext, scale);
+        run_ops<true>(a, ops, count, base | ext, scale);
 #pragma unroll
         for (int q = 0; q < 16; ++q)
           st[TQS_IX(sb ^ ((q & 1) ? w0 : 0) ^ ((q & 2) ? w1 : 0) ^ ((q & 4) ? w2 : 0) ^ ((q & 8) ? w3 : 0), NT)] = a[q];
