@@ -655,7 +655,8 @@ def bench_fsv(B, W, torch, hbm_peak, sm_mhz):
     (10 x (U3 on every qubit + CNOTs on n/2 seeded pairs)) at n = 24, 28, 30.
     Each pass streams the state once (read + write): 16 * 2^n algorithmic
     bytes per pass; the ALU fraction counts the algorithmic FP32 flops of the
-    per-gate update (eq. 12)."""
+    per-gate update (eq. 12).  Also: the per-gate form (one pass per gate) at
+    n = 24, and the fused kernel beside the tiled passes at n = 16."""
     out = {"workload": "random layered: 10 x (U3 on every qubit + CNOTs on n/2 seeded pairs)"}
     for n, reps in ((24, 5), (28, 3), (30, 2)):
         ops = W.random_layered(n, 10, (9, n))
@@ -684,6 +685,57 @@ def bench_fsv(B, W, torch, hbm_peak, sm_mhz):
         B.tqs_circuit_destroy(c)
         del st
         torch.cuda.empty_cache()
+    # The per-gate form of eq. 12 (one pass over the state per gate) at n = 24,
+    # and the fused kernel on the same kind of circuit at n = 16 (its largest
+    # size) beside the tiled passes.
+    n = 24
+    ops = W.random_layered(n, 10, (9, n))
+    c = B.circuit_from_ops(n, ops)
+    st = torch.zeros(1 << n, dtype=torch.complex64, device="cuda")
+    st[0] = 1.0
+    B.tqs_set_option(B.OPT_FSV_MAX_GATES, 0, 1)
+    try:
+        passes, _ = B.tqs_fsv_passes(c)
+        B.tqs_simulate_fsv(c, st)
+        torch.cuda.synchronize()
+        s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        s.record()
+        B.tqs_simulate_fsv(c, st)
+        e.record()
+        torch.cuda.synchronize()
+    finally:
+        B.tqs_set_option(B.OPT_FSV_MAX_GATES, 0, 0)
+    sec = s.elapsed_time(e) / 1e3
+    alg = 16.0 * (1 << n) * passes
+    out["per_gate_n24"] = {"passes": passes, "ms": 1e3 * sec,
+                           "hbm": {"achieved_gbs": alg / sec / 1e9, "frac": alg / sec / 1e9 / hbm_peak},
+                           "grouped_ms": out["n24"]["ms"]}
+    B.tqs_circuit_destroy(c)
+    del st
+    n = 16
+    ops = W.random_layered(n, 10, (9, n))
+    c = B.circuit_from_ops(n, ops)
+    st = torch.zeros(1 << n, dtype=torch.complex64, device="cuda")
+    st[0] = 1.0
+    fused_out = torch.empty(1 << n, dtype=torch.complex64, device="cuda")
+    times = {}
+    for name, fn in (("fused_ms", lambda: B.tqs_simulate(c, fused_out)),
+                     ("fsv_ms", lambda: B.tqs_simulate_fsv(c, st))):
+        fn()
+        torch.cuda.synchronize()
+        s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        s.record()
+        for _ in range(5):
+            fn()
+        e.record()
+        torch.cuda.synchronize()
+        times[name] = s.elapsed_time(e) / 5
+    out["vs_fused_n16"] = dict(times, fsv_passes=B.tqs_fsv_passes(c)[0],
+                               note="one circuit; the fused kernel runs it on one CTA "
+                                    "(global-scratch team), the tiled passes on the whole GPU")
+    B.tqs_circuit_destroy(c)
+    del st, fused_out
+    torch.cuda.empty_cache()
     return out
 
 

@@ -486,9 +486,15 @@ tqs_status tqs_check_violations(uint32_t* count, int reset);
  * the FP64 norm and the reductions of measure/reset instructions are summed
  * in a partition that depends on it, so they may differ in the last bits
  * between the two settings (every entry point uses the current setting, so
- * batch, server and single-circuit results agree). */
+ * batch, server and single-circuit results agree).
+ * TQS_OPT_FSV_MAX_GATES, key = 0, value = gates per pass of the
+ * full-state-vector backend at most (0, the default: as many as fit a tile).
+ * 1 gives the per-gate form of eq. 12 (Appendix A): one pass over the state
+ * in HBM per gate.  Read by tqs_simulate_fsv and tqs_fsv_passes (a circuit's
+ * cached passes are rebuilt when it changed). */
 #define TQS_OPT_WARPS_PER_CTA 1
 #define TQS_OPT_TEAM_WARPS 2
+#define TQS_OPT_FSV_MAX_GATES 3
 
 tqs_status tqs_set_option(int option, int key, int64_t value);
 tqs_status tqs_get_option(int option, int key, int64_t* value);

@@ -294,6 +294,7 @@ struct FsvPassInfo {
 };
 struct FsvProgram {
   int T = 0;  // tile bits per pass
+  int max_gates = 0;  // gates per pass at most (0: no limit) it was compiled with
   std::vector<FsvPassInfo> passes;
   std::vector<Program> progs;  // one per pass
 };
@@ -1111,6 +1112,8 @@ struct LaunchPlan {
 // TQS_OPT_WARPS_PER_CTA table, indexed by the warp slice's log2 amplitudes.
 static std::atomic<int> g_warps_for_q[16] = {4, 4, 4, 4, 4, 4, 4, 4, 4, 4, 4, 4, 4, 4, 4, 4};
 // TQS_OPT_TEAM_WARPS table: warps per circuit of the warp class (1 or 2).
+// Gates per full-state-vector pass at most (0: as many as fit a tile).
+static std::atomic<int> g_fsv_max_gates{0};
 static std::atomic<int> g_team_warps_for_q[16] = {1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1};
 
 static LaunchPlan plan_for(int team, int max_nint, int jobs, int warps_hint) {
@@ -2457,6 +2460,12 @@ tqs_status tqs_set_option(int option, int key, int64_t value) {
     g_warps_for_q[key].store(static_cast<int>(value));
     return TQS_OK;
   }
+  if (option == TQS_OPT_FSV_MAX_GATES) {
+    if (key != 0) return fail(TQS_ERR_ARG, "tqs_set_option: key %d of TQS_OPT_FSV_MAX_GATES is not 0", key);
+    if (value < 0 || value > (int64_t(1) << 30)) return fail(TQS_ERR_ARG, "tqs_set_option: gates per pass %lld outside [0, 2^30]", static_cast<long long>(value));
+    g_fsv_max_gates.store(static_cast<int>(value));
+    return TQS_OK;
+  }
   return fail(TQS_ERR_ARG, "tqs_set_option: unknown option %d", option);
 }
 
@@ -2470,6 +2479,11 @@ tqs_status tqs_get_option(int option, int key, int64_t* value) {
   if (option == TQS_OPT_WARPS_PER_CTA) {
     if (key < 4 || key > kWarpMaxQ) return fail(TQS_ERR_ARG, "tqs_get_option: key %d outside [4, %d]", key, kWarpMaxQ);
     *value = g_warps_for_q[key].load();
+    return TQS_OK;
+  }
+  if (option == TQS_OPT_FSV_MAX_GATES) {
+    if (key != 0) return fail(TQS_ERR_ARG, "tqs_get_option: key %d of TQS_OPT_FSV_MAX_GATES is not 0", key);
+    *value = g_fsv_max_gates.load();
     return TQS_OK;
   }
   return fail(TQS_ERR_ARG, "tqs_get_option: unknown option %d", option);
@@ -2588,8 +2602,9 @@ tqs_status tqs_batch_sample(tqs_batch* b, const double* d_probs, int shots, cons
 // bits, a custom unitary's bits), at most T in all.  Controls and diagonal
 // factors may sit on any bit.  Unused tile slots take the lowest free bits.
 
-static tqs_status compile_fsv(int n, const std::vector<Gate>& gates, FsvProgram& P) {
+static tqs_status compile_fsv(int n, const std::vector<Gate>& gates, int max_gates, FsvProgram& P) {
   P = FsvProgram();
+  P.max_gates = max_gates;
   const int T = std::min(n, kFsvTileQ);
   const int nlow = std::min(T, kFsvLowQ);
   P.T = T;
@@ -2620,7 +2635,9 @@ static tqs_status compile_fsv(int n, const std::vector<Gate>& gates, FsvProgram&
     still.clear();
     cur.clear();
     size_t i = 0;
-    for (; i < pending.size() && blocked != all; ++i) {
+    for (; i < pending.size() && blocked != all &&
+           (max_gates == 0 || cur.size() < static_cast<size_t>(max_gates));
+         ++i) {
       const Gate& g = gates[pending[i]];
       uint64_t qm = 0;
       for (int j = 0; j < g.nq; ++j) qm |= uint64_t(1) << g.q[j];
@@ -2685,8 +2702,9 @@ tqs_status tqs_simulate_fsv(tqs_circuit* c, tqs_c64* d_state, void* stream) {
              "tqs_simulate_fsv: copy");
     return tqs_simulate(c, c->d_collapse.as<tqs_c64>(), d_state, nullptr, nullptr, stream);
   }
-  if (!c->fsv_valid) {
-    tqs_status st = compile_fsv(c->n, c->gates, c->fsv);
+  const int max_gates = g_fsv_max_gates.load();
+  if (!c->fsv_valid || c->fsv.max_gates != max_gates) {
+    tqs_status st = compile_fsv(c->n, c->gates, max_gates, c->fsv);
     if (st != TQS_OK) return st;
     c->fsv_img = Image();
     for (const Program& tp : c->fsv.progs) c->fsv_img.add(tp, 0);
@@ -2716,8 +2734,9 @@ tqs_status tqs_fsv_passes(tqs_circuit* c, int* n_passes, int* tile_bits) {
   if (!c) return fail(TQS_ERR_ARG, "tqs_fsv_passes: circuit is NULL");
   FsvProgram local;
   const FsvProgram* P = &c->fsv;
-  if (!c->fsv_valid) {
-    tqs_status st = compile_fsv(c->n, c->gates, local);
+  const int max_gates = g_fsv_max_gates.load();
+  if (!c->fsv_valid || c->fsv.max_gates != max_gates) {
+    tqs_status st = compile_fsv(c->n, c->gates, max_gates, local);
     if (st != TQS_OK) return st;
     P = &local;
   }

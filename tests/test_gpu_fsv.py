@@ -6,6 +6,8 @@ eq. 12) against the FP64 oracle, through the C ABI.
   kernel);
 * n = 24, random layered circuit, element by element (the oracle handles
   2^24 amplitudes in seconds);
+* the per-gate form (TQS_OPT_FSV_MAX_GATES = 1, one pass per gate) against
+  the oracle and the grouped passes;
 * n = 28: the GHZ closed form (two amplitudes 2^-1/2, the rest 0) and the
   QFT closed form on a basis state at sampled indices, plus the FP64 norm;
   these hold at any size.
@@ -91,6 +93,30 @@ def test_fsv_n24_random_layered():
     got = run_fsv(n, ops).cpu().numpy().astype(np.complex128)
     want = fsv_route.simulate(n, ops)
     assert np.max(np.abs(got - want)) <= AMP_TOL
+
+
+@pytest.mark.parametrize("n,limit", [(9, 1), (18, 1), (18, 3)])
+def test_fsv_per_gate_form(n, limit):
+    ops = mixed_circuit(n, 77 * n)
+    grouped = run_fsv(n, ops).cpu().numpy()
+    B.tqs_set_option(B.OPT_FSV_MAX_GATES, 0, limit)
+    try:
+        c = B.circuit_from_ops(n, ops)
+        try:
+            passes = B.tqs_fsv_passes(c)[0]
+            st = basis(n)
+            B.tqs_simulate_fsv(c, st)
+            torch.cuda.synchronize()
+            got = st.cpu().numpy()
+        finally:
+            B.tqs_circuit_destroy(c)
+    finally:
+        B.tqs_set_option(B.OPT_FSV_MAX_GATES, 0, 0)
+    if limit == 1 and n >= 4:
+        assert passes == len(ops)
+    want = fsv_route.simulate(n, ops)
+    assert np.max(np.abs(got.astype(np.complex128) - want)) <= AMP_TOL
+    assert np.max(np.abs(got - grouped)) <= 2 * AMP_TOL
 
 
 def test_fsv_n28_closed_forms():

@@ -495,6 +495,28 @@ def test_fsv_pass_grouping():
         B.tqs_circuit_destroy(c)
 
 
+def test_fsv_gates_per_pass_option():
+    """TQS_OPT_FSV_MAX_GATES = 1 is the per-gate form (one pass per gate);
+    the cached passes follow the option; bad keys and values are refused."""
+    ops = W.random_layered(16, 2, (19, 16))
+    c = B.circuit_from_ops(16, ops)
+    try:
+        grouped = B.tqs_fsv_passes(c)[0]
+        B.tqs_set_option(B.OPT_FSV_MAX_GATES, 0, 1)
+        assert B.tqs_get_option(B.OPT_FSV_MAX_GATES, 0) == 1
+        assert B.tqs_fsv_passes(c)[0] == len(ops)
+        B.tqs_set_option(B.OPT_FSV_MAX_GATES, 0, 5)
+        assert B.tqs_fsv_passes(c)[0] >= -(-len(ops) // 5)
+    finally:
+        B.tqs_set_option(B.OPT_FSV_MAX_GATES, 0, 0)
+        B.tqs_circuit_destroy(c)
+    assert grouped < len(ops)
+    for key, value in ((1, 1), (0, -1)):
+        with pytest.raises(B.TqsError) as e:
+            B.tqs_set_option(B.OPT_FSV_MAX_GATES, key, value)
+        assert e.value.name == "TQS_ERR_ARG"
+
+
 def test_large_circuits_only_in_fsv():
     c = B.tqs_circuit_create(34)
     try:
