@@ -543,17 +543,22 @@ static void compile_program(int n, const std::vector<const Gate*>& gs_in, Progra
   take_segment();
   }
   if (P.passes.empty()) emit_pass(0u, 0, true);
-  // drop passes left with nothing to do (every factor fused to the identity);
-  // the first pass stays, it generates the start state
+  // Drop passes left with nothing to do (every factor fused to the identity).
+  // The first pass kept generates the start state, so it must be a register
+  // pass: an empty one stays in front of a leading instruction or custom
+  // unitary, and one stays when nothing else is left.
   {
-    size_t k = 1;
-    for (size_t i = 1; i < P.passes.size(); ++i) {
-      const FusedPass& ps = P.passes[i];
-      if (ps.L[0] != kInstrPass && ps.L[0] != kWidePass && ps.op_count == 0 && ps.scale == 1.0f)
-        continue;
+    auto normal = [](const FusedPass& ps) { return ps.L[0] != kInstrPass && ps.L[0] != kWidePass; };
+    const FusedPass first = P.passes[0];
+    size_t k = 0;
+    for (size_t i = 0; i < P.passes.size(); ++i) {
+      const FusedPass ps = P.passes[i];
+      if (normal(ps) && ps.op_count == 0 && ps.scale == 1.0f) continue;
+      if (k == 0 && !normal(ps)) P.passes[k++] = first;
       P.passes[k++] = ps;
     }
-    P.passes.resize(std::min(k, P.passes.size()));
+    if (k == 0) P.passes[k++] = first;
+    P.passes.resize(k);
   }
   P.out_scale = h_carry ? static_cast<float>(1.0 / std::sqrt(2.0)) : 1.0f;
   P.identity = 1;
