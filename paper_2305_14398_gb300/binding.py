@@ -203,7 +203,7 @@ PASS_DTYPE = np.dtype([("L", np.uint8, 4), ("op_begin", np.uint32), ("op_count",
                        ("scale", np.float32)])
 OP_DTYPE = np.dtype([("code", np.uint8), ("t", np.uint8), ("c", np.uint8), ("tbit", np.uint8),
                      ("d0one", np.uint8), ("fbit", np.uint8), ("act", np.uint16),
-                     ("pad1", np.uint32, 2), ("m", np.complex64, 4), ("lo", np.complex64, 4)])
+                     ("hc", np.complex64), ("m", np.complex64, 4), ("lo", np.complex64, 4)])
 
 
 def tqs_circuit_program(c: int):

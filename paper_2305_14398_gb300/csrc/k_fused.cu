@@ -158,6 +158,33 @@ __device__ __forceinline__ void diag_local(float2 (&a)[16], int t, int c, float2
   }
 }
 
+// The common controlled phase (d0 exactly 1) with both qubits local: only the
+// four amplitudes with local bits T and C both set change.  Compile-time
+// positions, so no predicated work on the other twelve.
+template <int T, int C>
+__device__ __forceinline__ void phase_tc(float2 (&a)[16], float2 d1) {
+#pragma unroll
+  for (int j = 0; j < 16; ++j)
+    if (((j >> T) & 1) && ((j >> C) & 1)) a[j] = cmul(a[j], d1);
+}
+
+__device__ __forceinline__ void phase_local(float2 (&a)[16], int t, int c, float2 d1) {
+  switch (t * 4 + c) {
+    case 1: phase_tc<0, 1>(a, d1); break;
+    case 2: phase_tc<0, 2>(a, d1); break;
+    case 3: phase_tc<0, 3>(a, d1); break;
+    case 4: phase_tc<1, 0>(a, d1); break;
+    case 6: phase_tc<1, 2>(a, d1); break;
+    case 7: phase_tc<1, 3>(a, d1); break;
+    case 8: phase_tc<2, 0>(a, d1); break;
+    case 9: phase_tc<2, 1>(a, d1); break;
+    case 11: phase_tc<2, 3>(a, d1); break;
+    case 12: phase_tc<3, 0>(a, d1); break;
+    case 13: phase_tc<3, 1>(a, d1); break;
+    default: phase_tc<3, 2>(a, d1); break;
+  }
+}
+
 // Pending per-bit phases: a diagonal factor that depends on one local bit is
 // folded into p[b] (applied to the amplitudes with local bit b = 1) and only
 // multiplied in before a non-diagonal factor on bit b, or at the end of the
@@ -284,36 +311,44 @@ __device__ __forceinline__ void run_ops(float2 (&a)[16], const FusedOp* __restri
       }
       continue;
     }
-    // diagonal ops: d0 = m0, d1 = m1, ratio d1/d0 = m2
+    // diagonal ops: d0 = m0, d1 = m1, ratio d1/d0 = m2; the header's hc holds
+    // d1/d0 (local target, no local control) or d1 (the rest), so only ops
+    // whose d0 is not exactly 1 load more than the header
     const bool d0one = (q0.y & 0xff) != 0;
+    const float2 hc = f2(q0.z, q0.w);
     if (code < OPC_DFL) {  // local target, no or far control
-      const uint4 q2 = __ldg(rec + 2);
       if (!d0one) {
         const uint4 q1 = __ldg(rec + 1);
         sc = cmul(sc, f2(q1.x, q1.y));
         sc_set = true;
       }
-      pend_mul(pd, code & 3, f2(q2.x, q2.y));
+      pend_mul(pd, code & 3, hc);
       continue;
     }
     const bool tb = (base >> ((q0.x >> 24) & 0xff)) & 1;
-    if (code < OPC_DFF) {  // far target, local control c
+    if (code <= OPC_DFF) {  // far target: local control c (DFL) or none / far (DFF)
       if (!tb && d0one) continue;
-      const uint4 q1 = __ldg(rec + 1);
-      pend_mul(pd, code & 3, tb ? f2(q1.z, q1.w) : f2(q1.x, q1.y));
-      continue;
-    }
-    if (code == OPC_DFF) {  // far target, no or far control: a phase of the group
-      if (!tb && d0one) continue;
-      const uint4 q1 = __ldg(rec + 1);
-      sc = cmul(sc, tb ? f2(q1.z, q1.w) : f2(q1.x, q1.y));
-      sc_set = true;
+      float2 v = hc;
+      if (!tb) {
+        const uint4 q1 = __ldg(rec + 1);
+        v = f2(q1.x, q1.y);
+      }
+      if (code < OPC_DFF) {
+        pend_mul(pd, code & 3, v);
+      } else {  // a phase of the group
+        sc = cmul(sc, v);
+        sc_set = true;
+      }
       continue;
     }
     {  // OPC_DLL: both local
-      const uint4 q1 = __ldg(rec + 1);
-      diag_local(a, (q0.x >> 8) & 0xff, (q0.x >> 16) & 0xff, f2(q1.x, q1.y), f2(q1.z, q1.w),
-                 d0one);
+      const int t = (q0.x >> 8) & 0xff, c = (q0.x >> 16) & 0xff;
+      if (d0one) {
+        phase_local(a, t, c, hc);
+      } else {
+        const uint4 q1 = __ldg(rec + 1);
+        diag_local(a, t, c, f2(q1.x, q1.y), hc, false);
+      }
     }
   }
   pend_flush(a, pd, 0);

@@ -429,6 +429,7 @@ static void compile_program(int n, const std::vector<const Gate*>& gs_in, Progra
         op.m[1] = to_f2(u.m[3]);
         op.m[2] = to_f2(u.m[3] / u.m[0]);
         op.d0one = (u.m[0] == cd(1.0)) ? 1 : 0;
+        op.hc = (tl >= 0 && cl < 0) ? op.m[2] : op.m[1];
         pass_cost += 0.25;
         if (tl >= 0) {
           if (cl >= 0) {

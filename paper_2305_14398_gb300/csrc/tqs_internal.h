@@ -34,7 +34,8 @@ namespace tqs {
 //   OPC_DFL + c      diag(d0, d1), far target bit `tbit`, local control c
 //   OPC_DFF          diag(d0, d1), far target bit `tbit`, no or far control `fbit`
 //   OPC_DLL          diag(d0, d1), local target t and local control c (fields t, c)
-// Diagonal ops carry d0, d1, d1/d0 and `d0one` = 1 when d0 is exactly 1.
+// Diagonal ops carry d0, d1, d1/d0 and `d0one` = 1 when d0 is exactly 1; the
+// coefficient they use when d0 is 1 is repeated in the header (`hc`).
 enum OpCode : uint8_t {
   OPC_H = 0,
   OPC_X = 4,
@@ -59,7 +60,8 @@ struct alignas(16) FusedOp {
   uint8_t d0one;   // diagonal ops: d0 == 1 exactly
   uint8_t fbit;    // physical bit of a far control, 0xFF if none
   uint16_t act;    // active-pair mask over the 16 local indices (ANTI, CDENSE)
-  uint32_t pad1[2];
+  float2 hc;       // diagonal ops, in the header so no further load is needed in the
+                   // common case: d1/d0 (DLN, DLF) or d1 (DFL, DFF, DLL)
   float2 m[4];     // DENSE: m00 m01 m10 m11 | ANTI: -, m01, m10, - | DIAG: d0, d1, d1/d0, -
   float2 lo[4];    // DENSE: m - m_fp32 rounded to FP32 (the FP64 matrix is m + lo)
 };
