@@ -609,7 +609,7 @@ __device__ void run_circuit(const FusedLaunch& L, int ci, float2* st, int rank, 
     const int p_one = cd.identity ? 1 : pfwd_bit(0, pw);
     int p_hi = 0;
     const int iters = (N + 2 * size - 1) >> sh;
-#pragma unroll 1
+#pragma unroll 2
     for (int k = 0; k < iters; ++k) {
       if (k > 0) {
         const int q = sh + (__ffs(k) - 1);
