@@ -387,6 +387,7 @@ def run_tqs(args):
                               "warps_per_cta": tuned["warps"], "autotune_ms": tuned["timings_ms"],
                               "autotune_source": tuned["source"]}},
         "dense_equiv_complex_gflops": dense_flops * world * args.steps / total_s / 1e9,
+        "step_ms_stats": step_stats(step_ms),
         "roofline": {"bound": "hbm", "achieved": achieved_gbs, "peak": hbm_peak,
                      "unit": "GB/s", "frac": achieved_gbs / hbm_peak,
                      "traffic": NCU_TRAFFIC_BYTES if tuned["team_warps"] == 2 else None,
@@ -417,6 +418,21 @@ def run_tqs(args):
         torch.cuda.synchronize()
         plain_s = s.elapsed_time(e) / 1e3
         plain_steps = sum(B.tqs_circuit_info(h)[2] for h in handles) * reps
+        # the fused kernel on the same circuits, one launch per circuit
+        # (single-circuit latency: one warp team on one SM)
+        probs1 = torch.empty(N, dtype=torch.float64, device="cuda")
+        norm1 = torch.empty(1, dtype=torch.float64, device="cuda")
+        for h in handles:
+            B.tqs_simulate(h, out, probs=probs1, norm=norm1)
+        torch.cuda.synchronize()
+        reps1 = 50
+        s.record(stream)
+        for _ in range(reps1):
+            for h in handles:
+                B.tqs_simulate(h, out, probs=probs1, norm=norm1)
+        e.record(stream)
+        torch.cuda.synchronize()
+        single_s = s.elapsed_time(e) / 1e3
         for h in handles:
             B.tqs_circuit_destroy(h)
         plain_rate = 4 * reps / plain_s
@@ -426,6 +442,12 @@ def run_tqs(args):
             "dense_equiv_complex_gflops": 8.0 * (4 ** N_QUBITS) * plain_steps / plain_s / 1e9,
             "hbm_gbs_algorithmic": 16.0 * (4 ** N_QUBITS) * plain_steps / plain_s / 1e9,
             "fused_speedup": value / world / plain_rate,
+            "fused_single": {"value": 4 * reps1 / single_s, "unit": "circuits/s",
+                             "latency_us": 1e6 * single_s / (4 * reps1),
+                             "sample": "the same 4 circuits, one tqs_simulate each (state, "
+                                       "probabilities, norm), 50 repetitions, back to back on "
+                                       "one stream",
+                             "speedup_vs_plain": (4 * reps1 / single_s) / plain_rate},
         }
 
     # ------------------------------------------------------- end to end
@@ -520,6 +542,16 @@ def run_tqs(args):
     if dist:
         dist.destroy_process_group()
     return 0
+
+
+def step_stats(ms):
+    """Mean, p50, p99, min and max of per-step device times (this rank)."""
+    v = sorted(ms)
+
+    def pct(q):
+        return v[min(len(v) - 1, int(round(q * (len(v) - 1))))]
+    return {"mean": sum(v) / len(v), "p50": pct(0.5), "p99": pct(0.99), "min": v[0], "max": v[-1],
+            "count": len(v)}
 
 
 def e2e_pipelined(B, arrays, bufs, steps):
@@ -719,7 +751,15 @@ def bench_fsv(B, W, torch, hbm_peak, sm_mhz):
     st[0] = 1.0
     fused_out = torch.empty(1 << n, dtype=torch.complex64, device="cuda")
     times = {}
+
+    def one_cta():
+        B.tqs_set_option(B.OPT_MULTI_CTAS, 0, 1)
+        try:
+            B.tqs_simulate(c, fused_out)
+        finally:
+            B.tqs_set_option(B.OPT_MULTI_CTAS, 0, 8)
     for name, fn in (("fused_ms", lambda: B.tqs_simulate(c, fused_out)),
+                     ("fused_one_cta_ms", one_cta),
                      ("fsv_ms", lambda: B.tqs_simulate_fsv(c, st))):
         fn()
         torch.cuda.synchronize()
@@ -731,8 +771,9 @@ def bench_fsv(B, W, torch, hbm_peak, sm_mhz):
         torch.cuda.synchronize()
         times[name] = s.elapsed_time(e) / 5
     out["vs_fused_n16"] = dict(times, fsv_passes=B.tqs_fsv_passes(c)[0],
-                               note="one circuit; the fused kernel runs it on one CTA "
-                                    "(global-scratch team), the tiled passes on the whole GPU")
+                               note="one circuit; fused_ms: the fused kernel on 8 CTAs "
+                                    "(TEAM_MULTI, grid barrier per pass), fused_one_cta_ms: on one "
+                                    "CTA (the batch form), fsv_ms: the tiled passes on the whole GPU")
     B.tqs_circuit_destroy(c)
     del st, fused_out
     torch.cuda.empty_cache()

@@ -491,10 +491,20 @@ tqs_status tqs_check_violations(uint32_t* count, int reset);
  * full-state-vector backend at most (0, the default: as many as fit a tile).
  * 1 gives the per-gate form of eq. 12 (Appendix A): one pass over the state
  * in HBM per gate.  Read by tqs_simulate_fsv and tqs_fsv_passes (a circuit's
- * cached passes are rebuilt when it changed). */
+ * cached passes are rebuilt when it changed).
+ * TQS_OPT_MULTI_CTAS, key = 0, value = CTAs at most for one circuit of 15 or
+ * 16 qubits in tqs_simulate (0 or 1: one CTA; default 8; at most 64).  The
+ * CTAs (a cooperative launch) share the circuit's passes, one thread per
+ * amplitude group, and meet at a grid barrier after each pass; CTA 0 writes
+ * the outputs exactly as one CTA would, so states, probabilities and the norm
+ * are bitwise the same for every value.  Circuits with measure / reset
+ * instructions or custom unitaries always take one CTA.  A grid barrier that
+ * waits longer than about a second (it cannot while the launch is
+ * cooperative) stops waiting and leaves NaN in the norm and in amplitude 0. */
 #define TQS_OPT_WARPS_PER_CTA 1
 #define TQS_OPT_TEAM_WARPS 2
 #define TQS_OPT_FSV_MAX_GATES 3
+#define TQS_OPT_MULTI_CTAS 4
 
 tqs_status tqs_set_option(int option, int key, int64_t value);
 tqs_status tqs_get_option(int option, int key, int64_t* value);

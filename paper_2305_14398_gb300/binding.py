@@ -483,6 +483,7 @@ def tqs_server_destroy(sv: int) -> None:
 OPT_WARPS_PER_CTA = 1
 OPT_TEAM_WARPS = 2
 OPT_FSV_MAX_GATES = 3
+OPT_MULTI_CTAS = 4
 
 
 def tqs_set_option(option: int, key: int, value: int) -> None:

@@ -422,6 +422,49 @@ __device__ __forceinline__ void team_sync() {
     __syncthreads();
 }
 
+// Grid barrier of the TEAM_MULTI CTAs (all co-resident: cooperative
+// launch).  Thread 0 of each CTA arrives on a monotone counter (zeroed before
+// the launch) and waits, at most kGridBarrierCycles, until every CTA has
+// arrived as often; a time-out is recorded and later barriers do not wait.
+struct GridBar {
+  unsigned int* ctr;
+  int* err;
+  unsigned int target;
+};
+
+__device__ __forceinline__ unsigned int ld_acquire_u32(const unsigned int* p) {
+  unsigned int v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+__device__ __forceinline__ void grid_sync(GridBar& b) {
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    b.target += gridDim.x;
+    __threadfence();
+    atomicAdd(b.ctr, 1u);
+    if (*reinterpret_cast<volatile int*>(b.err) == 0) {
+      const long long t0 = clock64();
+      while (ld_acquire_u32(b.ctr) < b.target) {
+        if (clock64() - t0 > kGridBarrierCycles) {
+          atomicExch(b.err, 1);
+          break;
+        }
+      }
+    }
+    __threadfence();
+  }
+  __syncthreads();
+}
+
+// State loads: TEAM_MULTI reads what other CTAs wrote, so it bypasses L1.
+template <int TEAM>
+__device__ __forceinline__ float2 ld_state(const float2* p) {
+  if (TEAM == TEAM_MULTI) return __ldcg(p);
+  return *p;
+}
+
 // Measure / reset instruction (Sec. 5.2 operation interface) on physical bit
 // `bit`: S_0 / S_1 = the |psi|^2 mass with that bit 0 / 1 (FP64 exact squares,
 // summed per thread in index order, then across the team in a fixed order),
@@ -527,7 +570,8 @@ __device__ __noinline__ void wide_pass(const FusedLaunch& L, int nint, int k, ui
 
 template <int TEAM>
 __device__ void run_circuit(const FusedLaunch& L, int ci, float2* st, int rank, int size,
-                            double* s_red, int& next_job, int& next_ci, int* s_slot) {
+                            double* s_red, int& next_job, int& next_ci, int* s_slot,
+                            GridBar* bar = nullptr) {
   const FusedCirc cd = L.circs[ci];
   const int nint = cd.nint;
   const int n = cd.n;
@@ -541,7 +585,7 @@ __device__ void run_circuit(const FusedLaunch& L, int ci, float2* st, int rank, 
     const int NI = 1 << nint, N = 1 << n;
     for (int i = rank; i < NI; i += size)
       st[TQS_IX(swz(i), NI)] = (i < N) ? init[i] : make_float2(0.f, 0.f);
-    team_sync<TEAM>();
+    if (TEAM == TEAM_MULTI) grid_sync(*bar); else team_sync<TEAM>();
   }
   for (int p = 0; p < cd.pass_count; ++p) {
     const uint4 pr = __ldg(reinterpret_cast<const uint4*>(L.passes + cd.pass_begin + p));
@@ -570,7 +614,7 @@ __device__ void run_circuit(const FusedLaunch& L, int ci, float2* st, int rank, 
           const int off = base | ((j & 1) ? b0 : 0) | ((j & 2) ? b1 : 0) | ((j & 4) ? b2 : 0) | ((j & 8) ? b3 : 0);
           a[j] = make_float2(off == cd.gen_index ? 1.f : 0.f, 0.f);
         } else {
-          a[j] = st[TQS_IX(sb ^ ((j & 1) ? w0 : 0) ^ ((j & 2) ? w1 : 0) ^ ((j & 4) ? w2 : 0) ^ ((j & 8) ? w3 : 0), 1 << nint)];
+          a[j] = ld_state<TEAM>(&st[TQS_IX(sb ^ ((j & 1) ? w0 : 0) ^ ((j & 2) ? w1 : 0) ^ ((j & 4) ? w2 : 0) ^ ((j & 8) ? w3 : 0), 1 << nint)]);
         }
       }
       run_ops<false>(a, ops, count, base, scale);
@@ -578,7 +622,13 @@ __device__ void run_circuit(const FusedLaunch& L, int ci, float2* st, int rank, 
       for (int j = 0; j < 16; ++j)
         st[TQS_IX(sb ^ ((j & 1) ? w0 : 0) ^ ((j & 2) ? w1 : 0) ^ ((j & 4) ? w2 : 0) ^ ((j & 8) ? w3 : 0), 1 << nint)] = a[j];
     }
-    team_sync<TEAM>();
+    if (TEAM == TEAM_MULTI) grid_sync(*bar); else team_sync<TEAM>();
+  }
+  // TEAM_MULTI: CTA 0 alone writes the outputs, as a TEAM_GLOBAL CTA would.
+  if (TEAM == TEAM_MULTI) {
+    if (blockIdx.x != 0) return;
+    rank = threadIdx.x;
+    size = blockDim.x;
   }
   // Warp and pair teams: the next job (its atomic was issued when this
   // circuit started) is shared with the team here and its circuit index is
@@ -618,8 +668,8 @@ __device__ void run_circuit(const FusedLaunch& L, int ci, float2* st, int rank, 
       const int gk = k ^ (k >> 1);
       const int i = i0 + (gk << sh);
       const int p0 = p_lo ^ p_hi;
-      float2 v0 = st[TQS_IX(swz(p0), 1 << nint)];
-      float2 v1 = st[TQS_IX(swz(p0 ^ p_one), 1 << nint)];
+      float2 v0 = ld_state<TEAM>(&st[TQS_IX(swz(p0), 1 << nint)]);
+      float2 v1 = ld_state<TEAM>(&st[TQS_IX(swz(p0 ^ p_one), 1 << nint)]);
       if (oscale != 1.0f) { v0 = make_float2(v0.x * oscale, v0.y * oscale); v1 = make_float2(v1.x * oscale, v1.y * oscale); }
       *reinterpret_cast<float4*>(out + TQS_IX(i, N - 1)) = make_float4(v0.x, v0.y, v1.x, v1.y);
       if (probs)
@@ -639,6 +689,12 @@ __device__ void run_circuit(const FusedLaunch& L, int ci, float2* st, int rank, 
     if (lane == 0) s_red[warp] = acc;
     team_sync<TEAM>();
     if (rank == 0) { double s = 0.0; for (int w = 0; w < (size >> 5); ++w) s += s_red[w]; if (L.norms) L.norms[ci] = s; }
+  }
+  if (TEAM == TEAM_MULTI && rank == 0 && *reinterpret_cast<volatile int*>(L.err) != 0) {
+    // a grid barrier timed out: the outputs are not valid, make that visible
+    const float nan = __int_as_float(0x7fffffff);
+    if (L.norms) L.norms[ci] = static_cast<double>(nan);
+    out[0] = make_float2(nan, nan);
   }
   if ((TEAM == TEAM_WARP || TEAM == TEAM_PAIR) && rank == 0 && next_job < L.n_jobs)
     prefetch_l1_range(L.circs + next_ci, sizeof(FusedCirc), 0, 1);
@@ -683,6 +739,12 @@ __global__ void __launch_bounds__(TEAM == TEAM_CTA ? kCtaThreads : 512)
       job = next_job;
       ci = next_ci;
     }
+  } else if (TEAM == TEAM_MULTI) {
+    __shared__ double s_red[32];
+    GridBar bar{reinterpret_cast<unsigned int*>(L.counter), L.err, 0u};
+    int unused_job = 0, unused_ci = 0;
+    run_circuit<TEAM_MULTI>(L, L.order[0], L.gscratch, blockIdx.x * blockDim.x + threadIdx.x,
+                            gridDim.x * blockDim.x, s_red, unused_job, unused_ci, nullptr, &bar);
   } else {
     __shared__ int s_job;
     __shared__ double s_red[32];
@@ -872,6 +934,13 @@ cudaError_t launch_fused(const FusedLaunch& L, cudaStream_t s) {
                              static_cast<int>(smem));
     if (e != cudaSuccess) return e;
     fused_kernel<TEAM_CTA><<<L.grid, threads, smem, s>>>(L);
+  } else if (L.team == TEAM_MULTI) {
+    // cooperative: the CTAs wait on one another at the grid barriers
+    FusedLaunch arg = L;
+    void* args[] = {&arg};
+    e = cudaLaunchCooperativeKernel(reinterpret_cast<const void*>(fused_kernel<TEAM_MULTI>),
+                                    dim3(L.grid), dim3(threads), args, 0, s);
+    if (e != cudaSuccess) return e;
   } else {
     fused_kernel<TEAM_GLOBAL><<<L.grid, threads, 0, s>>>(L);
   }

@@ -1154,6 +1154,27 @@ static LaunchPlan plan_for(int team, int max_nint, int jobs, int warps_hint) {
   return lp;
 }
 
+// CTAs for a single global-class circuit: one per 512 groups of a pass (a
+// thread per group), at most TQS_OPT_MULTI_CTAS; 1 when the program holds
+// instructions or custom unitaries, or the device has no cooperative launch.
+static std::atomic<int> g_multi_ctas{8};
+static int multi_ctas_for(const Program& P) {
+  const int limit = g_multi_ctas.load();
+  if (limit < 2 || P.nint <= kCtaMaxQ) return 1;
+  for (const FusedPass& ps : P.passes)
+    if (ps.L[0] == kInstrPass || ps.L[0] == kWidePass) return 1;
+  static int coop = -1;
+  if (coop < 0) {
+    int dev = 0, v = 0;
+    cudaGetDevice(&dev);
+    if (cudaDeviceGetAttribute(&v, cudaDevAttrCooperativeLaunch, dev) != cudaSuccess) v = 0;
+    coop = v;
+  }
+  if (!coop) return 1;
+  const int groups = 1 << (P.nint - 4);
+  return std::max(1, std::min(limit, groups / kGlobalThreads));
+}
+
 static tqs_status simulate_impl(tqs_circuit* c, const tqs_c64* d_init, tqs_c64* d_out,
                                 double* d_probs, double* d_norm, const double* d_u,
                                 int32_t* d_outcomes, void* stream) {
@@ -1183,7 +1204,7 @@ static tqs_status simulate_impl(tqs_circuit* c, const tqs_c64* d_init, tqs_c64* 
   char* base = c->d_prog.as<char>();
   TQS_CUDA(cudaMemcpyAsync(base + order_off, zero_order, sizeof(int32_t), cudaMemcpyHostToDevice, s),
            "tqs_simulate: upload order");
-  TQS_CUDA(cudaMemsetAsync(c->d_counter.p, 0, sizeof(int32_t), s), "tqs_simulate: memset");
+  TQS_CUDA(cudaMemsetAsync(c->d_counter.p, 0, 2 * sizeof(int32_t), s), "tqs_simulate: memset");
   FusedLaunch L{};
   img.point(L, base);
   L.order = reinterpret_cast<const int32_t*>(base + order_off);
@@ -1204,6 +1225,14 @@ static tqs_status simulate_impl(tqs_circuit* c, const tqs_c64* d_init, tqs_c64* 
   L.warps_per_cta = lp.warps;
   L.slice_q = lp.slice_q;
   L.grid = 1;
+  // A single circuit of the global class runs on several CTAs (TEAM_MULTI,
+  // bitwise the same results) when it has no instructions or custom unitaries.
+  const int multi = multi_ctas_for(P);
+  if (team == TEAM_GLOBAL && multi >= 2) {
+    L.team = TEAM_MULTI;
+    L.grid = multi;
+    L.err = c->d_counter.as<int32_t>() + 1;  // zeroed with the counter above
+  }
   TQS_CUDA(launch_fused(L, s), "tqs_simulate: launch");
   return TQS_OK;
 }
@@ -2466,6 +2495,12 @@ tqs_status tqs_set_option(int option, int key, int64_t value) {
     g_warps_for_q[key].store(static_cast<int>(value));
     return TQS_OK;
   }
+  if (option == TQS_OPT_MULTI_CTAS) {
+    if (key != 0) return fail(TQS_ERR_ARG, "tqs_set_option: key %d of TQS_OPT_MULTI_CTAS is not 0", key);
+    if (value < 0 || value > 64) return fail(TQS_ERR_ARG, "tqs_set_option: CTAs %lld outside [0, 64]", static_cast<long long>(value));
+    g_multi_ctas.store(static_cast<int>(value));
+    return TQS_OK;
+  }
   if (option == TQS_OPT_FSV_MAX_GATES) {
     if (key != 0) return fail(TQS_ERR_ARG, "tqs_set_option: key %d of TQS_OPT_FSV_MAX_GATES is not 0", key);
     if (value < 0 || value > (int64_t(1) << 30)) return fail(TQS_ERR_ARG, "tqs_set_option: gates per pass %lld outside [0, 2^30]", static_cast<long long>(value));
@@ -2485,6 +2520,11 @@ tqs_status tqs_get_option(int option, int key, int64_t* value) {
   if (option == TQS_OPT_WARPS_PER_CTA) {
     if (key < 4 || key > kWarpMaxQ) return fail(TQS_ERR_ARG, "tqs_get_option: key %d outside [4, %d]", key, kWarpMaxQ);
     *value = g_warps_for_q[key].load();
+    return TQS_OK;
+  }
+  if (option == TQS_OPT_MULTI_CTAS) {
+    if (key != 0) return fail(TQS_ERR_ARG, "tqs_get_option: key %d of TQS_OPT_MULTI_CTAS is not 0", key);
+    *value = g_multi_ctas.load();
     return TQS_OK;
   }
   if (option == TQS_OPT_FSV_MAX_GATES) {

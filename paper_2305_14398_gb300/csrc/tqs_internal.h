@@ -91,7 +91,16 @@ static_assert(sizeof(FusedPass) == 16, "FusedPass layout");
 // TEAM_PAIR runs the circuits of the warp class (n <= kWarpMaxQ) with two
 // warps per circuit sharing its shared-memory slice (a launch variant of
 // TEAM_WARP: twice the warps per byte of shared memory).
-enum TeamKind : int32_t { TEAM_WARP = 0, TEAM_CTA = 1, TEAM_GLOBAL = 2, TEAM_PAIR = 3 };
+// TEAM_MULTI: one circuit of the global class on several co-resident CTAs
+// (a cooperative launch): they share its global scratch slot and meet at a
+// bounded grid barrier after every pass; CTA 0 alone writes the outputs with
+// exactly the TEAM_GLOBAL output phase, so results are bitwise those of
+// TEAM_GLOBAL.  Single circuits without instructions or custom unitaries.
+enum TeamKind : int32_t { TEAM_WARP = 0, TEAM_CTA = 1, TEAM_GLOBAL = 2, TEAM_PAIR = 3, TEAM_MULTI = 4 };
+
+// Grid barrier of TEAM_MULTI: spins at most this many SM cycles (about 1 s),
+// then records a time-out in FusedLaunch::err and stops waiting.
+constexpr long long kGridBarrierCycles = 2000000000LL;
 
 struct alignas(16) FusedCirc {
   int16_t n;            // logical qubits
@@ -132,6 +141,7 @@ struct FusedLaunch {
   const float2* coef;       // custom unitaries: coefficient array (nullable without them)
   const double* uniforms;   // instructions: one uniform each (nullable without instructions)
   int32_t* outcomes;        // instructions: one outcome each (nullable)
+  int32_t* err;             // TEAM_MULTI: set to 1 when a grid barrier timed out
   int32_t team;             // TeamKind of this launch
   int32_t warps_per_cta;    // TEAM_WARP
   int32_t slice_q;          // TEAM_WARP: log2 amplitudes per warp slice; TEAM_CTA: log2 per CTA

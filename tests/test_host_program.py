@@ -517,6 +517,20 @@ def test_fsv_gates_per_pass_option():
         assert e.value.name == "TQS_ERR_ARG"
 
 
+def test_multi_cta_option():
+    assert B.tqs_get_option(B.OPT_MULTI_CTAS, 0) == 8
+    try:
+        for v in (0, 1, 3, 64):
+            B.tqs_set_option(B.OPT_MULTI_CTAS, 0, v)
+            assert B.tqs_get_option(B.OPT_MULTI_CTAS, 0) == v
+        for key, value in ((1, 2), (0, -1), (0, 65)):
+            with pytest.raises(B.TqsError) as e:
+                B.tqs_set_option(B.OPT_MULTI_CTAS, key, value)
+            assert e.value.name == "TQS_ERR_ARG"
+    finally:
+        B.tqs_set_option(B.OPT_MULTI_CTAS, 0, 8)
+
+
 def test_large_circuits_only_in_fsv():
     c = B.tqs_circuit_create(34)
     try:
