@@ -400,6 +400,40 @@ def run_tqs(args):
     }
     line["clocks"] = sampler.summary(t0, t1)
 
+    # ------------------------------------------------------- end to end
+    if not args.no_e2e:
+        bufs = [(torch.empty(total, dtype=torch.complex64).pin_memory(),
+                 torch.empty(total, dtype=torch.float64).pin_memory(),
+                 torch.empty(count, dtype=torch.float64).pin_memory()) for _ in range(2)]
+        e2e_steps = max(3, min(args.steps, 10))
+        for k in range(2):  # warm: creation scratch, device pool, both buffer sets
+            bb = B.tqs_batch_create_packed(*arrays)
+            B.tqs_batch_run_host(bb, *bufs[k])
+            B.tqs_batch_destroy(bb)
+        if dist:
+            dist.barrier()
+        # sequential: create, run, destroy, one batch after the other
+        te0 = time.perf_counter()
+        for k in range(e2e_steps):
+            bb = B.tqs_batch_create_packed(*arrays)
+            B.tqs_batch_run_host(bb, *bufs[k % 2])
+            B.tqs_batch_destroy(bb)
+        te_seq = max_over_ranks(time.perf_counter() - te0, dist, "cuda")
+        if dist:
+            dist.barrier()
+        # pipelined: a second host thread creates batch k + 1 while batch k runs
+        te_pipe = max_over_ranks(e2e_pipelined(B, arrays, bufs, e2e_steps), dist, "cuda")
+        line["e2e"] = {"value": whole_job_rate(count * e2e_steps, world, te_pipe), "unit": "circuits/s",
+                       "h2d_bytes_per_step": int(prog_bytes),
+                       "d2h_bytes_per_step": int(total * 8 + total * 8 + count * 8),
+                       "steps": e2e_steps,
+                       "sequential_value": whole_job_rate(count * e2e_steps, world, te_seq),
+                       "path": "tqs_batch_create_packed (host gate arrays) + tqs_batch_run_host "
+                               "(page-locked host buffers, written by the kernel over C2C) + "
+                               "tqs_batch_destroy; value: creation of the next batch on a second "
+                               "host thread overlaps the current run; sequential_value: one batch "
+                               "after the other"}
+
     # ------------------------------------------------------- plain form
     if not args.no_plain and rank == 0:
         mix = W.paper_mix(N_QUBITS, 4, seed_tag=1)
@@ -449,40 +483,6 @@ def run_tqs(args):
                                        "one stream",
                              "speedup_vs_plain": (4 * reps1 / single_s) / plain_rate},
         }
-
-    # ------------------------------------------------------- end to end
-    if not args.no_e2e:
-        bufs = [(torch.empty(total, dtype=torch.complex64).pin_memory(),
-                 torch.empty(total, dtype=torch.float64).pin_memory(),
-                 torch.empty(count, dtype=torch.float64).pin_memory()) for _ in range(2)]
-        e2e_steps = max(3, min(args.steps, 10))
-        for k in range(2):  # warm: creation scratch, device pool, both buffer sets
-            bb = B.tqs_batch_create_packed(*arrays)
-            B.tqs_batch_run_host(bb, *bufs[k])
-            B.tqs_batch_destroy(bb)
-        if dist:
-            dist.barrier()
-        # sequential: create, run, destroy, one batch after the other
-        te0 = time.perf_counter()
-        for k in range(e2e_steps):
-            bb = B.tqs_batch_create_packed(*arrays)
-            B.tqs_batch_run_host(bb, *bufs[k % 2])
-            B.tqs_batch_destroy(bb)
-        te_seq = max_over_ranks(time.perf_counter() - te0, dist, "cuda")
-        if dist:
-            dist.barrier()
-        # pipelined: a second host thread creates batch k + 1 while batch k runs
-        te_pipe = max_over_ranks(e2e_pipelined(B, arrays, bufs, e2e_steps), dist, "cuda")
-        line["e2e"] = {"value": whole_job_rate(count * e2e_steps, world, te_pipe), "unit": "circuits/s",
-                       "h2d_bytes_per_step": int(prog_bytes),
-                       "d2h_bytes_per_step": int(total * 8 + total * 8 + count * 8),
-                       "steps": e2e_steps,
-                       "sequential_value": whole_job_rate(count * e2e_steps, world, te_seq),
-                       "path": "tqs_batch_create_packed (host gate arrays) + tqs_batch_run_host "
-                               "(page-locked host buffers, written by the kernel over C2C) + "
-                               "tqs_batch_destroy; value: creation of the next batch on a second "
-                               "host thread overlaps the current run; sequential_value: one batch "
-                               "after the other"}
 
     # ------------------------------------------------ collapse (sampling)
     if not args.no_sample and rank == 0:

@@ -493,7 +493,9 @@ tqs_status tqs_check_violations(uint32_t* count, int reset);
  * in HBM per gate.  Read by tqs_simulate_fsv and tqs_fsv_passes (a circuit's
  * cached passes are rebuilt when it changed).
  * TQS_OPT_MULTI_CTAS, key = 0, value = CTAs at most for one circuit of 15 or
- * 16 qubits in tqs_simulate (0 or 1: one CTA; default 8; at most 64).  The
+ * 16 qubits in tqs_simulate, and for each such request of a server batch that
+ * holds few of them (together at most the SMs divided by the server's batches
+ * in flight) (0 or 1: one CTA; default 8; at most 64).  The
  * CTAs (a cooperative launch) share the circuit's passes, one thread per
  * amplitude group, and meet at a grid barrier after each pass; CTA 0 writes
  * the outputs exactly as one CTA would, so states, probabilities and the norm

@@ -422,14 +422,17 @@ __device__ __forceinline__ void team_sync() {
     __syncthreads();
 }
 
-// Grid barrier of the TEAM_MULTI CTAs (all co-resident: cooperative
-// launch).  Thread 0 of each CTA arrives on a monotone counter (zeroed before
-// the launch) and waits, at most kGridBarrierCycles, until every CTA has
-// arrived as often; a time-out is recorded and later barriers do not wait.
+// Barrier of the K TEAM_MULTI CTAs of one circuit (all co-resident:
+// cooperative launch).  Thread 0 of each arrives on the circuit's monotone
+// counter (zeroed before the launch) and waits, at most kGridBarrierCycles,
+// until all K have arrived as often; a time-out is recorded and later
+// barriers do not wait.
 struct GridBar {
   unsigned int* ctr;
   int* err;
   unsigned int target;
+  unsigned int nblocks;  // CTAs that meet at this barrier
+  bool leader;           // the first of them: writes the outputs
 };
 
 __device__ __forceinline__ unsigned int ld_acquire_u32(const unsigned int* p) {
@@ -441,7 +444,7 @@ __device__ __forceinline__ unsigned int ld_acquire_u32(const unsigned int* p) {
 __device__ __forceinline__ void grid_sync(GridBar& b) {
   __syncthreads();
   if (threadIdx.x == 0) {
-    b.target += gridDim.x;
+    b.target += b.nblocks;
     __threadfence();
     atomicAdd(b.ctr, 1u);
     if (*reinterpret_cast<volatile int*>(b.err) == 0) {
@@ -624,9 +627,9 @@ __device__ void run_circuit(const FusedLaunch& L, int ci, float2* st, int rank, 
     }
     if (TEAM == TEAM_MULTI) grid_sync(*bar); else team_sync<TEAM>();
   }
-  // TEAM_MULTI: CTA 0 alone writes the outputs, as a TEAM_GLOBAL CTA would.
+  // TEAM_MULTI: the first CTA alone writes the outputs, as a TEAM_GLOBAL CTA would.
   if (TEAM == TEAM_MULTI) {
-    if (blockIdx.x != 0) return;
+    if (!bar->leader) return;
     rank = threadIdx.x;
     size = blockDim.x;
   }
@@ -741,10 +744,14 @@ __global__ void __launch_bounds__(TEAM == TEAM_CTA ? kCtaThreads : 512)
     }
   } else if (TEAM == TEAM_MULTI) {
     __shared__ double s_red[32];
-    GridBar bar{reinterpret_cast<unsigned int*>(L.counter), L.err, 0u};
+    const int K = L.ctas_per_job;
+    const int job = blockIdx.x / K, local = blockIdx.x - job * K;
+    GridBar bar{reinterpret_cast<unsigned int*>(L.counter) + job, L.err, 0u,
+                static_cast<unsigned int>(K), local == 0};
     int unused_job = 0, unused_ci = 0;
-    run_circuit<TEAM_MULTI>(L, L.order[0], L.gscratch, blockIdx.x * blockDim.x + threadIdx.x,
-                            gridDim.x * blockDim.x, s_red, unused_job, unused_ci, nullptr, &bar);
+    run_circuit<TEAM_MULTI>(L, L.order[job], L.gscratch + (static_cast<size_t>(job) << kGlobalSlotQ),
+                            local * blockDim.x + threadIdx.x, K * blockDim.x, s_red, unused_job,
+                            unused_ci, nullptr, &bar);
   } else {
     __shared__ int s_job;
     __shared__ double s_red[32];

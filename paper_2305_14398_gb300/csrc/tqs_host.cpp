@@ -1158,6 +1158,7 @@ static LaunchPlan plan_for(int team, int max_nint, int jobs, int warps_hint) {
 // thread per group), at most TQS_OPT_MULTI_CTAS; 1 when the program holds
 // instructions or custom unitaries, or the device has no cooperative launch.
 static std::atomic<int> g_multi_ctas{8};
+constexpr int kMaxMultiJobs = 60;  // barrier counters that fit the server's counter block
 static int multi_ctas_for(const Program& P) {
   const int limit = g_multi_ctas.load();
   if (limit < 2 || P.nint <= kCtaMaxQ) return 1;
@@ -1231,6 +1232,7 @@ static tqs_status simulate_impl(tqs_circuit* c, const tqs_c64* d_init, tqs_c64* 
   if (team == TEAM_GLOBAL && multi >= 2) {
     L.team = TEAM_MULTI;
     L.grid = multi;
+    L.ctas_per_job = multi;
     L.err = c->d_counter.as<int32_t>() + 1;  // zeroed with the counter above
   }
   TQS_CUDA(launch_fused(L, s), "tqs_simulate: launch");
@@ -2210,13 +2212,26 @@ static tqs_status server_launch(tqs_server* sv, SrvSlot& sl) {
   const size_t amps = static_cast<size_t>(sl.offsets.back());
   LaunchPlan plans[3];
   for (int t = 0; t < 3; ++t) plans[t] = plan_for(t, max_nint[t], n_team[t], 0);
+  // Few global-class requests: K cooperating CTAs each (TEAM_MULTI),
+  // bitwise the same results as one CTA each.  The J K CTAs take at most an
+  // equal share of the SMs per slot in flight, so the cooperative grids of all
+  // slots fit the GPU together (one such CTA per SM) and none waits at a
+  // barrier for SMs held by another waiting grid.
+  int multi_k = 0;
+  const int J = n_team[TEAM_GLOBAL];
+  if (J > 0 && J <= kMaxMultiJobs) {
+    int k = 64;
+    for (int32_t i : idx[TEAM_GLOBAL]) k = std::min(k, multi_ctas_for(sl.reqs[i].prog));
+    const int share = device_sms() / std::max<int>(1, static_cast<int>(sv->slots.size()));
+    if (k >= 2 && J * k <= share) multi_k = k;
+  }
   const size_t order_off = (img.bytes() + 255) & ~size_t(255);
   const size_t counter_off = (order_off + order.size() * sizeof(int32_t) + 255) & ~size_t(255);
   const size_t states_off = counter_off + 256;
   const size_t norms_off = (states_off + amps * sizeof(float2) + 255) & ~size_t(255);
   const size_t gscr_off = (norms_off + sl.reqs.size() * sizeof(double) + 255) & ~size_t(255);
   const size_t gscr_bytes =
-      n_team[TEAM_GLOBAL] ? size_t(plans[TEAM_GLOBAL].grid) << kGlobalSlotQ : size_t(0);
+      J ? size_t(std::max(plans[TEAM_GLOBAL].grid, J)) << kGlobalSlotQ : size_t(0);
   const size_t total = gscr_off + gscr_bytes * sizeof(float2);
   // the program goes through pinned memory so the copy is truly asynchronous
   const size_t prog_bytes = order_off + order.size() * sizeof(int32_t);
@@ -2248,7 +2263,10 @@ static tqs_status server_launch(tqs_server* sv, SrvSlot& sl) {
   }
   TQS_CUDA(cudaMemcpyAsync(base, sl.h_prog, prog_bytes, cudaMemcpyHostToDevice, s), "tqs_server: H2D");
   int32_t* counters = reinterpret_cast<int32_t*>(base + counter_off);
-  TQS_CUDA(cudaMemsetAsync(counters, 0, 3 * sizeof(int32_t), s), "tqs_server: memset");
+  // team counters [0, 3), the TEAM_MULTI time-out word [3] and its per-job
+  // barrier counters [4, 4 + J)
+  TQS_CUDA(cudaMemsetAsync(counters, 0, (4 + (multi_k ? J : 0)) * sizeof(int32_t), s),
+           "tqs_server: memset");
   float2* d_states = reinterpret_cast<float2*>(base + states_off);
   double* d_norms = reinterpret_cast<double*>(base + norms_off);
   int first = 0;
@@ -2267,6 +2285,13 @@ static tqs_status server_launch(tqs_server* sv, SrvSlot& sl) {
     L.warps_per_cta = plans[t].warps;
     L.slice_q = plans[t].slice_q;
     L.grid = plans[t].grid;
+    if (t == TEAM_GLOBAL && multi_k) {
+      L.team = TEAM_MULTI;
+      L.ctas_per_job = multi_k;
+      L.grid = J * multi_k;
+      L.counter = counters + 4;
+      L.err = counters + 3;
+    }
     TQS_CUDA(launch_fused(L, s), "tqs_server: launch");
     first += n_team[t];
   }

@@ -91,11 +91,12 @@ static_assert(sizeof(FusedPass) == 16, "FusedPass layout");
 // TEAM_PAIR runs the circuits of the warp class (n <= kWarpMaxQ) with two
 // warps per circuit sharing its shared-memory slice (a launch variant of
 // TEAM_WARP: twice the warps per byte of shared memory).
-// TEAM_MULTI: one circuit of the global class on several co-resident CTAs
-// (a cooperative launch): they share its global scratch slot and meet at a
-// bounded grid barrier after every pass; CTA 0 alone writes the outputs with
-// exactly the TEAM_GLOBAL output phase, so results are bitwise those of
-// TEAM_GLOBAL.  Single circuits without instructions or custom unitaries.
+// TEAM_MULTI: each circuit of the global class on K co-resident CTAs (a
+// cooperative launch): they share its global scratch slot and meet at a
+// bounded barrier of the K after every pass; the first of the K alone writes
+// the outputs with exactly the TEAM_GLOBAL output phase, so results are
+// bitwise those of TEAM_GLOBAL.  Circuits without instructions or custom
+// unitaries, few enough that all their CTAs are resident at once.
 enum TeamKind : int32_t { TEAM_WARP = 0, TEAM_CTA = 1, TEAM_GLOBAL = 2, TEAM_PAIR = 3, TEAM_MULTI = 4 };
 
 // Grid barrier of TEAM_MULTI: spins at most this many SM cycles (about 1 s),
@@ -142,6 +143,9 @@ struct FusedLaunch {
   const double* uniforms;   // instructions: one uniform each (nullable without instructions)
   int32_t* outcomes;        // instructions: one outcome each (nullable)
   int32_t* err;             // TEAM_MULTI: set to 1 when a grid barrier timed out
+  int32_t ctas_per_job;     // TEAM_MULTI: CTAs per circuit; job j runs on CTAs
+                            // [j K, (j + 1) K), its barrier counter is counter[j],
+                            // its scratch slot gscratch + j 2^kGlobalSlotQ
   int32_t team;             // TeamKind of this launch
   int32_t warps_per_cta;    // TEAM_WARP
   int32_t slice_q;          // TEAM_WARP: log2 amplitudes per warp slice; TEAM_CTA: log2 per CTA
