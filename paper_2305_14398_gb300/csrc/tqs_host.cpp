@@ -917,6 +917,9 @@ static tqs_status check_gate(int n, int gate, const int* qubits, int nq, const d
   g.nq = nq;
   g.q[0] = qubits[0];
   g.q[1] = nq == 2 ? qubits[1] : qubits[0];
+  for (int i = 2; i < kMaxCustomQubits; ++i) g.q[i] = g.q[0];
+  g.step = 0;
+  if (g.cm) g.cm.reset();
   for (int i = 0; i < 8; ++i) g.p[i] = (i < need) ? params[i] : 0.0;
   for (int i = 0; i < need; ++i)
     if (!std::isfinite(g.p[i])) return fail(TQS_ERR_ARG, "gate %d: non-finite parameter", gate);
@@ -1768,7 +1771,7 @@ tqs_status tqs_batch_create_packed(int count, const int32_t* h_nq, const int64_t
         record(fail(TQS_ERR_ARG, "circuit %d: gate offsets decrease", i));
         continue;
       }
-      gates.assign(static_cast<size_t>(g1 - g0), Gate{});
+      gates.resize(static_cast<size_t>(g1 - g0));  // check_gate sets every field
       last.assign(n, -1);
       tqs_status st = TQS_OK;
       for (int64_t k = g0; k < g1 && st == TQS_OK; ++k) {
