@@ -4,6 +4,8 @@
 
 chain: the 40-step random layered circuit-unitary chain at n = COUNT
        (tensor-core BF16x3);
+plain: the plain materialised form (tqs_simulate_plain) on one circuit of each
+       paper kind at n = COUNT, REPS times;
 fsv:   the full-state-vector backend on a random layered circuit
        (10 x (U3 on every qubit + CNOTs on n/2 seeded pairs)) at n = COUNT;
 mix:   COUNT paper-shaped 11-qubit circuits (GHZ / DJ-constant / DJ-balanced /
@@ -58,6 +60,25 @@ def fsv(n, reps):
     B.tqs_circuit_destroy(c)
 
 
+def plain(n, reps):
+    handles = [B.circuit_from_ops(n, ops) for _, ops in W.paper_mix(n, 4)]
+    out = torch.empty(1 << n, dtype=torch.complex64, device="cuda")
+    for _ in range(reps):
+        for h in handles:
+            B.tqs_simulate_plain(h, out)
+    torch.cuda.synchronize()
+    s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    s.record()
+    for h in handles:
+        B.tqs_simulate_plain(h, out)
+    e.record()
+    torch.cuda.synchronize()
+    steps = sum(B.tqs_circuit_info(h)[2] for h in handles)
+    print("plain", n, "steps", steps, "ms %.3f" % s.elapsed_time(e))
+    for h in handles:
+        B.tqs_circuit_destroy(h)
+
+
 def main(argv):
     count = int(argv[1]) if len(argv) > 1 else 2048
     kind = argv[2] if len(argv) > 2 else "mix"
@@ -72,6 +93,8 @@ def main(argv):
         return chain(count, reps)
     if kind == "fsv":
         return fsv(count, reps)
+    if kind == "plain":
+        return plain(count, reps)
     if kind == "mix":
         circs = [(11, ops) for _, ops in W.paper_mix(11, count)]
     elif kind in ("ghz", "dj_constant", "dj_balanced", "qft"):
