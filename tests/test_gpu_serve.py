@@ -79,3 +79,22 @@ def test_serving_small_budget_forces_queueing():
     assert r["stats"]["peak_bytes"] <= budget
     assert r["stats"]["done"] == len(reqs)
     assert r["stats"]["bytes_in_use"] == 0
+
+
+@pytest.mark.parametrize("count,inflight", [(4, 4), (12, 4), (12, 1)])
+def test_large_requests_bitwise_alone(count, inflight):
+    """Batches of 15-16 qubit requests only: a few run on cooperating CTAs
+    (their CTAs at most the SMs divided by the batches in flight), more on one
+    CTA each; every result is bitwise the circuit simulated alone."""
+    reqs = []
+    for i in range(count):
+        n = 16 if i % 2 == 0 else 15
+        ops = W.random_layered(n, 3, (91, i)) if i % 3 else W.qft_on_basis(n, 7 * i + 1)
+        reqs.append((0.0, "large", n, ops))
+    r = serve.replay(reqs, budget_bytes=8 << 30, max_inflight=inflight, max_batch=64,
+                     keep_states=True)
+    check_norms(reqs, r["norms"])
+    for i, (_, _, n, ops) in enumerate(reqs):
+        st, nm = alone(n, ops)
+        assert np.array_equal(st.view(np.uint32), r["states"][i].view(np.uint32)), (i, n)
+        assert nm == r["norms"][i]
