@@ -4,7 +4,8 @@ file: fused batches over every team kind (one and two warps per circuit),
 measure/reset instructions, custom unitaries, the full-state-vector backend,
 the plain materialised form, the circuit-unitary chain (FP32 SIMT and both
 tensor-core splits), probabilities and marginals, sampling on its
-shared-memory and global paths, and simulateAndCollapse.  Prints one JSON
+shared-memory and global paths, simulateAndCollapse, and single 15-16 qubit
+circuits on cooperating CTAs.  Prints one JSON
 line: a digest of every output and the bounds-check violation count."""
 import hashlib
 import json
@@ -56,6 +57,16 @@ def main():
         torch.cuda.synchronize()
         digest.update(out.cpu().numpy().tobytes())
         digest.update(oc.cpu().numpy().tobytes())
+        B.tqs_circuit_destroy(c)
+    for n in (15, 16):  # single circuits on cooperating CTAs (TEAM_MULTI)
+        c = B.circuit_from_ops(n, W.random_layered(n, 3, (78, n)))
+        out = torch.empty(1 << n, dtype=torch.complex64, device="cuda")
+        pr = torch.empty(1 << n, dtype=torch.float64, device="cuda")
+        nm = torch.empty(1, dtype=torch.float64, device="cuda")
+        B.tqs_simulate(c, out, probs=pr, norm=nm)
+        torch.cuda.synchronize()
+        for t in (out, pr, nm):
+            digest.update(t.cpu().numpy().tobytes())
         B.tqs_circuit_destroy(c)
     for n in (14, 20):
         ops = W.random_small(n, 3 * n, (72, n)) + [
