@@ -323,6 +323,8 @@ static void compile_program(int n, const std::vector<const Gate*>& gs_in, Progra
   static thread_local std::vector<const Gate*> gs_tls;
   static thread_local std::vector<int> pending_tls, still_tls, order_tls;
   static thread_local std::vector<CompileRaw> raw_tls;
+  static thread_local std::vector<uint32_t> qmask_tls;  // per entry of gs: its qubit mask
+  static thread_local std::vector<GClass> cls_tls;      // per entry of gs: its class
   std::vector<const Gate*>& gs = gs_tls;
   gs.clear();
   P.gen_index = 0;
@@ -336,6 +338,14 @@ static void compile_program(int n, const std::vector<const Gate*>& gs_in, Progra
       touched |= qubit_mask(*g);
       gs.push_back(g);
     }
+  }
+  std::vector<uint32_t>& qmask = qmask_tls;
+  std::vector<GClass>& gcls = cls_tls;
+  qmask.resize(gs.size());
+  gcls.resize(gs.size());
+  for (size_t i = 0; i < gs.size(); ++i) {
+    qmask[i] = qubit_mask(*gs[i]);
+    gcls[i] = (is_instruction(gs[i]->kind) || is_wide(*gs[i])) ? G_DENSE : classify(*gs[i]);
   }
   const int nint = P.nint;
   int phys[32];
@@ -479,13 +489,13 @@ static void compile_program(int n, const std::vector<const Gate*>& gs_in, Progra
     for (; idx < pending.size(); ++idx) {
       if (blocked == all) break;
       const Gate& g = *gs[pending[idx]];
-      const uint32_t qm = qubit_mask(g);
+      const uint32_t qm = qmask[pending[idx]];
       if (qm & blocked) {  // an earlier gate on one of its qubits waits: so must it,
         blocked |= qm;     // and every later gate on any of its qubits
         still.push_back(pending[idx]);
         continue;
       }
-      const GClass cls = classify(g);
+      const GClass cls = gcls[pending[idx]];
       if (cls == G_SWAP) { std::swap(phys[g.q[0]], phys[g.q[1]]); continue; }
       const int tq = is_controlled(g.kind) ? g.q[1] : g.q[0];
       const int cq = is_controlled(g.kind) ? g.q[0] : -1;
@@ -716,20 +726,53 @@ static void give_segs(std::vector<ImageSeg>& segs) {
   segs.clear();
 }
 
+// Large circuit-descriptor arrays are recycled like the segments, so a
+// stream of batches pins no fresh pages for them either.
+using CircVec = std::vector<FusedCirc, LockedAlloc<FusedCirc>>;
+static std::mutex g_circ_mu;
+static std::vector<CircVec> g_circ_pool;
+
+static CircVec take_circs(size_t count) {
+  CircVec v;
+  if (count * sizeof(FusedCirc) >= (size_t(1) << 16)) {
+    std::lock_guard<std::mutex> lock(g_circ_mu);
+    for (size_t i = 0; i < g_circ_pool.size(); ++i)
+      if (g_circ_pool[i].capacity() >= count) {
+        v = std::move(g_circ_pool[i]);
+        g_circ_pool.erase(g_circ_pool.begin() + static_cast<std::ptrdiff_t>(i));
+        break;
+      }
+  }
+  v.resize(count);  // default-initialised: every entry is written by the caller
+  return v;
+}
+
+static void give_circs(CircVec& v) {
+  if (v.capacity() * sizeof(FusedCirc) >= (size_t(1) << 16)) {
+    std::lock_guard<std::mutex> lock(g_circ_mu);
+    if (g_circ_pool.size() < 8) g_circ_pool.push_back(std::move(v));
+  }
+  v = CircVec();
+}
+
 // Device image of one or more programs:
 // [FusedCirc x count][FusedPass...][FusedOp...][custom coefficients (float2)...]
 // The passes, ops and coefficients are held as consecutive segments.
 struct Image {
-  std::vector<FusedCirc, LockedAlloc<FusedCirc>> circs;
+  CircVec circs;
   std::vector<ImageSeg> segs;
   size_t npass = 0, nop = 0, ncoef = 0;  // totals over the segments
-  ~Image() { give_segs(segs); }
+  ~Image() {
+    give_segs(segs);
+    give_circs(circs);
+  }
   Image() = default;
   Image(const Image&) = delete;
   Image& operator=(const Image&) = delete;
   Image(Image&& o) noexcept { *this = std::move(o); }
   Image& operator=(Image&& o) noexcept {
     give_segs(segs);
+    give_circs(circs);
     circs = std::move(o.circs);
     segs = std::move(o.segs);
     npass = o.npass;
@@ -1060,18 +1103,22 @@ tqs_status tqs_circuit_steps(const tqs_circuit* c, int* h_step_of_gate) {
 }  // extern "C"
 
 // Gates in step order (stable within a step).
-static const std::vector<const Gate*>& step_order(const std::vector<Gate>& gates) {
-  // counting sort by step, stable, into scratch reused on this thread
+// The first `count` gates in step order: counting sort by step, stable, into
+// scratch reused on this thread.
+static const std::vector<const Gate*>& step_order(const Gate* gates, size_t count) {
   static thread_local std::vector<const Gate*> v;
   static thread_local std::vector<int> start;
   int nsteps = 0;
-  for (const Gate& g : gates) nsteps = std::max(nsteps, g.step + 1);
+  for (size_t i = 0; i < count; ++i) nsteps = std::max(nsteps, gates[i].step + 1);
   start.assign(static_cast<size_t>(nsteps) + 1, 0);
-  for (const Gate& g : gates) ++start[g.step + 1];
+  for (size_t i = 0; i < count; ++i) ++start[gates[i].step + 1];
   for (int k = 0; k < nsteps; ++k) start[k + 1] += start[k];
-  v.resize(gates.size());
-  for (const Gate& g : gates) v[start[g.step]++] = &g;
+  v.resize(count);
+  for (size_t i = 0; i < count; ++i) v[start[gates[i].step]++] = &gates[i];
   return v;
+}
+static const std::vector<const Gate*>& step_order(const std::vector<Gate>& gates) {
+  return step_order(gates.data(), gates.size());
 }
 
 static const Program& ensure_program(tqs_circuit* c, bool with_init = false) {
@@ -1642,7 +1689,7 @@ static tqs_status batch_finish(tqs_batch* b, const std::vector<CircMeta>& progs,
   if (b->instr_off.back() > 0xFFFFFFFFll || obase.back() > 0xFFFFFFFFll || cbase.back() > 0xFFFFFFFFll ||
       pbase.back() > 0x7FFFFFFFll)
     return fail(TQS_ERR_ARG, "tqs_batch: program too large for 32-bit offsets");
-  b->img.circs.resize(b->count);
+  b->img.circs = take_circs(static_cast<size_t>(b->count));
   b->img.segs = std::move(segs);
   b->img.npass = static_cast<size_t>(pbase.back());
   b->img.nop = static_cast<size_t>(obase.back());
@@ -1670,17 +1717,25 @@ static tqs_status batch_finish(tqs_batch* b, const std::vector<CircMeta>& progs,
     for (size_t k = 0; k < m.np; ++k)
       sg.passes[m.lp + k] = Image::rebase(sg.passes[m.lp + k], o0, b->instr_off[i], c0);
   });
-  std::vector<int> idx[3];
+  // job order per team kind: costliest first, ties in batch order (sorted on
+  // compact (cost, index) keys)
+  struct Key {
+    double cost;
+    int i;
+  };
+  std::vector<Key> idx[3];
   for (int i = 0; i < b->count; ++i) {
     const int t = team_for(progs[i].nint);
-    idx[t].push_back(i);
+    idx[t].push_back(Key{progs[i].cost, i});
     b->max_nint[t] = std::max(b->max_nint[t], progs[i].nint);
   }
+  b->order.reserve(static_cast<size_t>(b->count));
   for (int t = 0; t < 3; ++t) {
-    std::stable_sort(idx[t].begin(), idx[t].end(),
-                     [&](int a, int c) { return progs[a].cost > progs[c].cost; });
+    std::sort(idx[t].begin(), idx[t].end(), [](const Key& a, const Key& c) {
+      return a.cost > c.cost || (a.cost == c.cost && a.i < c.i);
+    });
     b->n_team[t] = static_cast<int>(idx[t].size());
-    b->order.insert(b->order.end(), idx[t].begin(), idx[t].end());
+    for (const Key& k : idx[t]) b->order.push_back(k.i);
   }
   return TQS_OK;
 }
@@ -1771,7 +1826,9 @@ tqs_status tqs_batch_create_packed(int count, const int32_t* h_nq, const int64_t
         record(fail(TQS_ERR_ARG, "circuit %d: gate offsets decrease", i));
         continue;
       }
-      gates.resize(static_cast<size_t>(g1 - g0));  // check_gate sets every field
+      // the buffer only grows (check_gate sets every field of the gates used)
+      const size_t ng = static_cast<size_t>(g1 - g0);
+      if (gates.size() < ng) gates.resize(ng);
       last.assign(n, -1);
       tqs_status st = TQS_OK;
       for (int64_t k = g0; k < g1 && st == TQS_OK; ++k) {
@@ -1788,7 +1845,7 @@ tqs_status tqs_batch_create_packed(int count, const int32_t* h_nq, const int64_t
       }
       for (int q = 0; q < n; ++q) nsteps[i] = std::max(nsteps[i], last[q] + 1);
       tp.reset();
-      compile_program(n, step_order(gates), tp);
+      compile_program(n, step_order(gates.data(), ng), tp);
       metas[i] = append_program(tp, sg, w);
     }
   });
