@@ -507,6 +507,11 @@ tqs_status tqs_check_violations(uint32_t* count, int reset);
 #define TQS_OPT_TEAM_WARPS 2
 #define TQS_OPT_FSV_MAX_GATES 3
 #define TQS_OPT_MULTI_CTAS 4
+/* TQS_OPT_HOST_WRITES, key = 0: 1 (default) lets tqs_batch_run_host's kernels
+ * write outputs that live in page-locked host memory directly (over
+ * NVLink-C2C on Grace-Blackwell); 0 writes them to device memory first and
+ * copies them with the DMA engines.  Results are bitwise the same. */
+#define TQS_OPT_HOST_WRITES 5
 
 tqs_status tqs_set_option(int option, int key, int64_t value);
 tqs_status tqs_get_option(int option, int key, int64_t* value);

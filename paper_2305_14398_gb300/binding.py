@@ -484,6 +484,7 @@ OPT_WARPS_PER_CTA = 1
 OPT_TEAM_WARPS = 2
 OPT_FSV_MAX_GATES = 3
 OPT_MULTI_CTAS = 4
+OPT_HOST_WRITES = 5
 
 
 def tqs_set_option(option: int, key: int, value: int) -> None:

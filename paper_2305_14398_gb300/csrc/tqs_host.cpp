@@ -2040,6 +2040,10 @@ tqs_status tqs_batch_instructions(const tqs_batch* b, int64_t* h_off) {
 // range (on Grace-Blackwell the kernel's stores then cross NVLink-C2C straight
 // into host memory).  nullptr when any check fails; the caller then stages
 // through device memory.
+// TQS_OPT_HOST_WRITES: 1 (default) lets tqs_batch_run_host's kernels write
+// page-locked host outputs directly; 0 stages them in device memory and copies.
+static std::atomic<int> g_host_writes{1};
+
 static void* mapped_alias(void* h, size_t bytes) {
   if (!h || bytes == 0) return nullptr;
   char* first = static_cast<char*>(h);
@@ -2075,9 +2079,11 @@ tqs_status tqs_batch_run_host(tqs_batch* b, tqs_c64* h_states, double* h_probs, 
   // stream-ordered from the device's memory pool and goes back to it at the end.
   const size_t amps = static_cast<size_t>(b->offsets.back());
   // outputs whose host buffers the GPU can write directly skip the device copy
-  float2* zs = static_cast<float2*>(mapped_alias(h_states, amps * sizeof(float2)));
-  double* zp = static_cast<double*>(mapped_alias(h_probs, amps * sizeof(double)));
-  double* zn = static_cast<double*>(mapped_alias(h_norms, size_t(b->count) * sizeof(double)));
+  const bool direct = g_host_writes.load() != 0;
+  float2* zs = direct ? static_cast<float2*>(mapped_alias(h_states, amps * sizeof(float2))) : nullptr;
+  double* zp = direct ? static_cast<double*>(mapped_alias(h_probs, amps * sizeof(double))) : nullptr;
+  double* zn = direct ? static_cast<double*>(mapped_alias(h_norms, size_t(b->count) * sizeof(double)))
+                      : nullptr;
   const size_t order_off = (b->img.bytes() + 255) & ~size_t(255);
   const size_t counter_off = (order_off + b->order.size() * sizeof(int32_t) + 255) & ~size_t(255);
   const size_t states_off = counter_off + 256;
@@ -2595,6 +2601,12 @@ tqs_status tqs_set_option(int option, int key, int64_t value) {
     g_warps_for_q[key].store(static_cast<int>(value));
     return TQS_OK;
   }
+  if (option == TQS_OPT_HOST_WRITES) {
+    if (key != 0) return fail(TQS_ERR_ARG, "tqs_set_option: key %d of TQS_OPT_HOST_WRITES is not 0", key);
+    if (value != 0 && value != 1) return fail(TQS_ERR_ARG, "tqs_set_option: host writes %lld is not 0 or 1", static_cast<long long>(value));
+    g_host_writes.store(static_cast<int>(value));
+    return TQS_OK;
+  }
   if (option == TQS_OPT_MULTI_CTAS) {
     if (key != 0) return fail(TQS_ERR_ARG, "tqs_set_option: key %d of TQS_OPT_MULTI_CTAS is not 0", key);
     if (value < 0 || value > 64) return fail(TQS_ERR_ARG, "tqs_set_option: CTAs %lld outside [0, 64]", static_cast<long long>(value));
@@ -2620,6 +2632,11 @@ tqs_status tqs_get_option(int option, int key, int64_t* value) {
   if (option == TQS_OPT_WARPS_PER_CTA) {
     if (key < 4 || key > kWarpMaxQ) return fail(TQS_ERR_ARG, "tqs_get_option: key %d outside [4, %d]", key, kWarpMaxQ);
     *value = g_warps_for_q[key].load();
+    return TQS_OK;
+  }
+  if (option == TQS_OPT_HOST_WRITES) {
+    if (key != 0) return fail(TQS_ERR_ARG, "tqs_get_option: key %d of TQS_OPT_HOST_WRITES is not 0", key);
+    *value = g_host_writes.load();
     return TQS_OK;
   }
   if (option == TQS_OPT_MULTI_CTAS) {

@@ -125,17 +125,26 @@ def test_host_buffer_entry_point():
     assert np.array_equal(hp, pr) and np.array_equal(hn, nm)
 
 
-@pytest.mark.parametrize("mode", ["pinned", "mixed"])
+@pytest.mark.parametrize("mode", ["pinned", "mixed", "copies"])
 def test_host_buffer_entry_point_pinned(mode):
     """Page-locked host buffers are written by the kernel directly (no device
     copy); results equal the device run bit for bit.  In "mixed", only the
-    probabilities are page-locked (states and norms take the copy path)."""
+    probabilities are page-locked (states and norms take the copy path); in
+    "copies", TQS_OPT_HOST_WRITES = 0 stages every output in device memory."""
+    B.tqs_set_option(B.OPT_HOST_WRITES, 0, 0 if mode == "copies" else 1)
+    try:
+        _host_buffers(mode)
+    finally:
+        B.tqs_set_option(B.OPT_HOST_WRITES, 0, 1)
+
+
+def _host_buffers(mode):
     circs = mixed_workload(40, 66)
     offs, [(st, pr, nm)] = run_batch(circs)
     b = B.tqs_batch_create_packed(*B.pack_ops(circs))
     try:
         count, total, _ = B.tqs_batch_info(b)
-        pin = (lambda t: t.pin_memory()) if mode == "pinned" else (lambda t: t)
+        pin = (lambda t: t.pin_memory()) if mode != "mixed" else (lambda t: t)
         hs = pin(torch.empty(total, dtype=torch.complex64))
         hp = torch.empty(total, dtype=torch.float64).pin_memory()
         hn = pin(torch.empty(count, dtype=torch.float64))

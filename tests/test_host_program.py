@@ -517,6 +517,19 @@ def test_fsv_gates_per_pass_option():
         assert e.value.name == "TQS_ERR_ARG"
 
 
+def test_host_writes_option():
+    assert B.tqs_get_option(B.OPT_HOST_WRITES, 0) == 1
+    try:
+        B.tqs_set_option(B.OPT_HOST_WRITES, 0, 0)
+        assert B.tqs_get_option(B.OPT_HOST_WRITES, 0) == 0
+        for key, value in ((1, 1), (0, 2)):
+            with pytest.raises(B.TqsError) as e:
+                B.tqs_set_option(B.OPT_HOST_WRITES, key, value)
+            assert e.value.name == "TQS_ERR_ARG"
+    finally:
+        B.tqs_set_option(B.OPT_HOST_WRITES, 0, 1)
+
+
 def test_multi_cta_option():
     assert B.tqs_get_option(B.OPT_MULTI_CTAS, 0) == 8
     try:
