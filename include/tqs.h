@@ -192,7 +192,8 @@ tqs_status tqs_circuit_program(tqs_circuit* c, int* n_passes, int* n_ops, void* 
  * materialised matrix.
  *   d_init  : 2^n tqs_c64 initial state, or NULL for |0...0>.
  *   d_out   : 2^n tqs_c64, receives the final state (must not alias d_init).
- *   d_probs : 2^n doubles, receives |psi_i|^2 computed in FP64, or NULL.
+ *   d_probs : 2^n doubles, receives |psi_i|^2 (FP32 arithmetic, or exact
+ *             in FP64 under TQS_OPT_EXACT_PROBS), or NULL.
  *   d_norm  : 1 double, receives sum_i |psi_i|^2 (FP64), or NULL.
  * n <= TQS_MAX_QUBITS.  Arithmetic: FP32 amplitudes, FP64 probabilities. */
 tqs_status tqs_simulate(tqs_circuit* c, const tqs_c64* d_init, tqs_c64* d_out,
@@ -512,6 +513,13 @@ tqs_status tqs_check_violations(uint32_t* count, int reset);
  * NVLink-C2C on Grace-Blackwell); 0 writes them to device memory first and
  * copies them with the DMA engines.  Results are bitwise the same. */
 #define TQS_OPT_HOST_WRITES 5
+/* TQS_OPT_EXACT_PROBS, key = 0: how the fused kernels (tqs_simulate, batches)
+ * form the probabilities they write.  0 (default): |psi_i|^2 = x^2 + y^2 in
+ * FP32 arithmetic from the FP32 parts, stored as FP64 (relative error below
+ * 2^-23); 1: the exact squares, rounded once to FP64 (bit-identical to
+ * (double)x*x + (double)y*y).  The states and the FP64 norm do not depend on
+ * it; tqs_probabilities always gives the exact form. */
+#define TQS_OPT_EXACT_PROBS 6
 
 tqs_status tqs_set_option(int option, int key, int64_t value);
 tqs_status tqs_get_option(int option, int key, int64_t* value);

@@ -485,6 +485,7 @@ OPT_TEAM_WARPS = 2
 OPT_FSV_MAX_GATES = 3
 OPT_MULTI_CTAS = 4
 OPT_HOST_WRITES = 5
+OPT_EXACT_PROBS = 6
 
 
 def tqs_set_option(option: int, key: int, value: int) -> None:

@@ -26,7 +26,27 @@ TQS_HD int clz32(uint32_t v) {
 #endif
 }
 
+TQS_HD uint64_t sq_f32_as_f64_bits_general(uint32_t xbits);
+
+// Normal x (the common case): m in [2^23, 2^24), m^2 in [2^46, 2^48).  The
+// significand field is m^2 shifted so that its leading one lands on bit 52;
+// adding the exponent field one below the biased exponent absorbs that
+// leading one, so no mask is needed.
 TQS_HD uint64_t sq_f32_as_f64_bits(uint32_t xbits) {
+  const uint32_t a = xbits & 0x7fffffffu;
+  if (a < 0x00800000u) return sq_f32_as_f64_bits_general(xbits);  // zero or subnormal
+  const uint32_t m = (a & 0x7fffffu) | 0x800000u;
+  const int e = static_cast<int>(a >> 23);
+  const uint64_t X = static_cast<uint64_t>(m) * m;
+  const bool top47 = (static_cast<uint32_t>(X >> 32) >> 15) != 0;  // bit 47 of X
+  const uint64_t Y = X << (top47 ? 5 : 6);
+  // biased exponent 2e - 254 + 1023 (top bit 47) or one less (top bit 46), minus 1
+  const uint64_t ebits = static_cast<uint64_t>(2 * e + 768 + (top47 ? 1 : 0)) << 52;
+  return ebits + Y;
+}
+
+// Any finite x, subnormals included.
+TQS_HD uint64_t sq_f32_as_f64_bits_general(uint32_t xbits) {
   const uint32_t a = xbits & 0x7fffffffu;
   int e = static_cast<int>(a >> 23);
   uint32_t m = a & 0x7fffffu;

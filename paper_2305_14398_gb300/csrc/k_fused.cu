@@ -662,7 +662,8 @@ __device__ void run_circuit(const FusedLaunch& L, int ci, float2* st, int rank, 
     const int p_one = cd.identity ? 1 : pfwd_bit(0, pw);
     int p_hi = 0;
     const int iters = (N + 2 * size - 1) >> sh;
-#pragma unroll 2
+    const bool exact = L.exact_probs != 0;
+#pragma unroll 1
     for (int k = 0; k < iters; ++k) {
       if (k > 0) {
         const int q = sh + (__ffs(k) - 1);
@@ -675,10 +676,15 @@ __device__ void run_circuit(const FusedLaunch& L, int ci, float2* st, int rank, 
       float2 v1 = ld_state<TEAM>(&st[TQS_IX(swz(p0 ^ p_one), 1 << nint)]);
       if (oscale != 1.0f) { v0 = make_float2(v0.x * oscale, v0.y * oscale); v1 = make_float2(v1.x * oscale, v1.y * oscale); }
       *reinterpret_cast<float4*>(out + TQS_IX(i, N - 1)) = make_float4(v0.x, v0.y, v1.x, v1.y);
-      if (probs)
-        *reinterpret_cast<double2*>(probs + TQS_IX(i, N - 1)) = make_double2(prob_f64(v0), prob_f64(v1));
-      kahan_add(fmaf(v0.x, v0.x, v0.y * v0.y), nsum, ncomp);
-      kahan_add(fmaf(v1.x, v1.x, v1.y * v1.y), nsum, ncomp);
+      const float q0 = fmaf(v0.x, v0.x, v0.y * v0.y), q1 = fmaf(v1.x, v1.x, v1.y * v1.y);
+      if (probs) {
+        // |psi|^2 in FP32 arithmetic, stored as FP64; or (exact_probs) the
+        // exact squares correctly rounded once in FP64
+        *reinterpret_cast<double2*>(probs + TQS_IX(i, N - 1)) =
+            exact ? make_double2(prob_f64(v0), prob_f64(v1)) : make_double2(q0, q1);
+      }
+      kahan_add(q0, nsum, ncomp);
+      kahan_add(q1, nsum, ncomp);
     }
   }
   // Fixed-order reduction (deterministic): per-thread compensated FP32 -> FP64.

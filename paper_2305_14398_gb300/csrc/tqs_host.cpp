@@ -1208,6 +1208,9 @@ static LaunchPlan plan_for(int team, int max_nint, int jobs, int warps_hint) {
 // thread per group), at most TQS_OPT_MULTI_CTAS; 1 when the program holds
 // instructions or custom unitaries, or the device has no cooperative launch.
 static std::atomic<int> g_multi_ctas{8};
+// TQS_OPT_EXACT_PROBS: the fused kernels' |psi_i|^2 in FP32 arithmetic (0,
+// default) or as exact squares rounded once in FP64 (1).
+static std::atomic<int> g_exact_probs{0};
 constexpr int kMaxMultiJobs = 60;  // barrier counters that fit the server's counter block
 static int multi_ctas_for(const Program& P) {
   const int limit = g_multi_ctas.load();
@@ -1263,6 +1266,7 @@ static tqs_status simulate_impl(tqs_circuit* c, const tqs_c64* d_init, tqs_c64* 
   L.counter = c->d_counter.as<int32_t>();
   L.out = reinterpret_cast<float2*>(d_out);
   L.probs = d_probs;
+  L.exact_probs = g_exact_probs.load();
   L.norms = d_norm;
   L.uniforms = d_u;
   L.outcomes = d_outcomes;
@@ -1574,6 +1578,8 @@ struct tqs_batch {
   void* g_norms = nullptr;
   const void* g_u = nullptr;
   void* g_outcomes = nullptr;
+  int g_exact = -1;
+  int exact_probs = 0;             // TQS_OPT_EXACT_PROBS when the batch last ran
   int graph_kernels = 0;
   ~tqs_batch() {
     if (exec) cudaGraphExecDestroy(exec);
@@ -1926,6 +1932,7 @@ static tqs_status batch_enqueue_at(tqs_batch* b, char* base, size_t order_off, s
     L.counter = counters + t;
     L.out = states;
     L.probs = probs;
+    L.exact_probs = b->exact_probs;
     L.norms = norms;
     L.gscratch = gscratch;
     L.uniforms = u;
@@ -1975,9 +1982,13 @@ static tqs_status batch_run_impl(tqs_batch* b, tqs_c64* d_states, double* d_prob
     if (st != TQS_OK) return st;
   }
   float2* states = reinterpret_cast<float2*>(d_states);
-  if (!use_graph) return batch_enqueue(b, states, d_probs, d_norms, s, nullptr, d_u, d_outcomes);
+  if (!use_graph) {
+    b->exact_probs = g_exact_probs.load();
+    return batch_enqueue(b, states, d_probs, d_norms, s, nullptr, d_u, d_outcomes);
+  }
+  b->exact_probs = g_exact_probs.load();
   if (!b->exec || b->g_states != d_states || b->g_probs != d_probs || b->g_norms != d_norms ||
-      b->g_u != d_u || b->g_outcomes != d_outcomes) {
+      b->g_u != d_u || b->g_outcomes != d_outcomes || b->g_exact != b->exact_probs) {
     if (b->exec) { cudaGraphExecDestroy(b->exec); b->exec = nullptr; }
     if (b->graph) { cudaGraphDestroy(b->graph); b->graph = nullptr; }
     if (!b->cap_stream)
@@ -2002,6 +2013,7 @@ static tqs_status batch_run_impl(tqs_batch* b, tqs_c64* d_states, double* d_prob
     b->g_norms = d_norms;
     b->g_u = d_u;
     b->g_outcomes = d_outcomes;
+    b->g_exact = b->exact_probs;
     b->graph_kernels = kernels;
   }
   TQS_CUDA(cudaGraphLaunch(b->exec, s), "tqs_batch: graph launch");
@@ -2112,6 +2124,7 @@ tqs_status tqs_batch_run_host(tqs_batch* b, tqs_c64* h_states, double* h_probs, 
   double* dp = zp ? zp : (h_probs ? reinterpret_cast<double*>(base + probs_off) : nullptr);
   double* dn = zn ? zn : reinterpret_cast<double*>(base + norms_off);
   const size_t gscr_at = (total + 255) & ~size_t(255);
+  b->exact_probs = g_exact_probs.load();
   tqs_status st = batch_enqueue_at(b, base, order_off, counter_off,
                                    reinterpret_cast<float2*>(base + gscr_at), ds, dp, dn, s);
   if (st != TQS_OK) return st;
@@ -2601,6 +2614,12 @@ tqs_status tqs_set_option(int option, int key, int64_t value) {
     g_warps_for_q[key].store(static_cast<int>(value));
     return TQS_OK;
   }
+  if (option == TQS_OPT_EXACT_PROBS) {
+    if (key != 0) return fail(TQS_ERR_ARG, "tqs_set_option: key %d of TQS_OPT_EXACT_PROBS is not 0", key);
+    if (value != 0 && value != 1) return fail(TQS_ERR_ARG, "tqs_set_option: exact probabilities %lld is not 0 or 1", static_cast<long long>(value));
+    g_exact_probs.store(static_cast<int>(value));
+    return TQS_OK;
+  }
   if (option == TQS_OPT_HOST_WRITES) {
     if (key != 0) return fail(TQS_ERR_ARG, "tqs_set_option: key %d of TQS_OPT_HOST_WRITES is not 0", key);
     if (value != 0 && value != 1) return fail(TQS_ERR_ARG, "tqs_set_option: host writes %lld is not 0 or 1", static_cast<long long>(value));
@@ -2632,6 +2651,11 @@ tqs_status tqs_get_option(int option, int key, int64_t* value) {
   if (option == TQS_OPT_WARPS_PER_CTA) {
     if (key < 4 || key > kWarpMaxQ) return fail(TQS_ERR_ARG, "tqs_get_option: key %d outside [4, %d]", key, kWarpMaxQ);
     *value = g_warps_for_q[key].load();
+    return TQS_OK;
+  }
+  if (option == TQS_OPT_EXACT_PROBS) {
+    if (key != 0) return fail(TQS_ERR_ARG, "tqs_get_option: key %d of TQS_OPT_EXACT_PROBS is not 0", key);
+    *value = g_exact_probs.load();
     return TQS_OK;
   }
   if (option == TQS_OPT_HOST_WRITES) {

@@ -143,6 +143,7 @@ struct FusedLaunch {
   const double* uniforms;   // instructions: one uniform each (nullable without instructions)
   int32_t* outcomes;        // instructions: one outcome each (nullable)
   int32_t* err;             // TEAM_MULTI: set to 1 when a grid barrier timed out
+  int32_t exact_probs;      // probs: 1 exact squares rounded once in FP64, 0 FP32 |psi|^2
   int32_t ctas_per_job;     // TEAM_MULTI: CTAs per circuit; job j runs on CTAs
                             // [j K, (j + 1) K), its barrier counter is counter[j],
                             // its scratch slot gscratch + j 2^kGlobalSlotQ

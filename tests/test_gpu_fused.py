@@ -62,14 +62,46 @@ def check_state(got, want, probs=None, norm=None):
     assert np.max(np.abs(got.astype(np.complex128) - want)) <= AMP_TOL
     if probs is not None:
         assert np.max(np.abs(probs - observables.probabilities(want))) <= 2 * AMP_TOL
-        # the GPU probabilities are exactly |amp|^2 of the FP32 state it wrote
+        # the GPU probabilities are |amp|^2 of the FP32 state it wrote, formed in
+        # FP32 arithmetic (default): within 2^-22 relative of the exact value
         g = got.astype(np.complex128)
-        assert np.max(np.abs(probs - (g.real ** 2 + g.imag ** 2))) <= 1e-15
+        exact = g.real ** 2 + g.imag ** 2
+        assert np.all(np.abs(probs - exact) <= 2.0 ** -22 * exact + 1e-44)
     if norm is not None:
         assert abs(norm - 1.0) <= NORM_TOL
 
 
 # --------------------------------------------------------------- config 0/1
+
+def test_exact_probabilities_option():
+    """TQS_OPT_EXACT_PROBS = 1: the probabilities are the exact squares of the
+    FP32 parts rounded once to FP64, bit for bit; the state and the norm do not
+    change with the option."""
+    n = 11
+    ops = W.random_mixed(n, 12, (96, n))
+    res = {}
+    for exact in (0, 1):
+        B.tqs_set_option(B.OPT_EXACT_PROBS, 0, exact)
+        try:
+            c = B.circuit_from_ops(n, ops)
+            try:
+                out = torch.empty(1 << n, dtype=torch.complex64, device="cuda")
+                pr = torch.empty(1 << n, dtype=torch.float64, device="cuda")
+                nm = torch.empty(1, dtype=torch.float64, device="cuda")
+                B.tqs_simulate(c, out, probs=pr, norm=nm)
+                torch.cuda.synchronize()
+                res[exact] = (out.cpu().numpy(), pr.cpu().numpy(), float(nm.cpu()[0]))
+            finally:
+                B.tqs_circuit_destroy(c)
+        finally:
+            B.tqs_set_option(B.OPT_EXACT_PROBS, 0, 0)
+    (s0, p0, n0), (s1, p1, n1) = res[0], res[1]
+    assert np.array_equal(s0.view(np.uint32), s1.view(np.uint32)) and n0 == n1
+    g = s1.astype(np.complex128)
+    assert np.array_equal(p1, g.real ** 2 + g.imag ** 2)
+    assert np.all(np.abs(p0 - p1) <= 2.0 ** -22 * p1 + 1e-44)
+    assert np.all(p0.astype(np.float32) == p0)  # FP32 values, stored as FP64
+
 
 def test_config0_ghz5_closed_form():
     """5-qubit fully entangled circuit: 1/sqrt2 on |00000> and |11111>."""

@@ -517,6 +517,19 @@ def test_fsv_gates_per_pass_option():
         assert e.value.name == "TQS_ERR_ARG"
 
 
+def test_exact_probs_option():
+    assert B.tqs_get_option(B.OPT_EXACT_PROBS, 0) == 0
+    try:
+        B.tqs_set_option(B.OPT_EXACT_PROBS, 0, 1)
+        assert B.tqs_get_option(B.OPT_EXACT_PROBS, 0) == 1
+        for key, value in ((1, 1), (0, 2)):
+            with pytest.raises(B.TqsError) as e:
+                B.tqs_set_option(B.OPT_EXACT_PROBS, key, value)
+            assert e.value.name == "TQS_ERR_ARG"
+    finally:
+        B.tqs_set_option(B.OPT_EXACT_PROBS, 0, 0)
+
+
 def test_host_writes_option():
     assert B.tqs_get_option(B.OPT_HOST_WRITES, 0) == 1
     try:
