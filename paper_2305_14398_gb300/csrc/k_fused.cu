@@ -91,19 +91,6 @@ __device__ __forceinline__ void dense_t(float2 (&a)[16], const Coef& m, unsigned
   }
 }
 
-template <int T>
-__device__ __forceinline__ void anti_t(float2 (&a)[16], float2 m01, float2 m10, unsigned act) {
-#pragma unroll
-  for (int p = 0; p < 8; ++p) {
-    const int j0 = ((p >> T) << (T + 1)) | (p & ((1 << T) - 1));
-    const int j1 = j0 | (1 << T);
-    const bool on = (act >> j0) & 1;
-    const float2 x0 = a[j0], x1 = a[j1];
-    a[j0] = sel(on, cmul(m01, x1), x0);
-    a[j1] = sel(on, cmul(m10, x0), x1);
-  }
-}
-
 
 
 
@@ -268,16 +255,6 @@ __device__ __forceinline__ void run_ops(float2 (&a)[16], const FusedOp* __restri
           case 1: swap_t<1>(a, act); break;
           case 2: swap_t<2>(a, act); break;
           default: swap_t<3>(a, act); break;
-        }
-      } else if (code < OPC_DENSE) {
-        const uint4 q1 = __ldg(rec + 1);
-        const uint4 q2 = __ldg(rec + 2);
-        const float2 m01 = f2(q1.z, q1.w), m10 = f2(q2.x, q2.y);
-        switch (t) {
-          case 0: anti_t<0>(a, m01, m10, act); break;
-          case 1: anti_t<1>(a, m01, m10, act); break;
-          case 2: anti_t<2>(a, m01, m10, act); break;
-          default: anti_t<3>(a, m01, m10, act); break;
         }
       } else {
         const uint4 q1 = __ldg(rec + 1);

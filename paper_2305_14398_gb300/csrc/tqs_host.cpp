@@ -420,12 +420,7 @@ static void compile_program(int n, const std::vector<const Gate*>& gs_in, Progra
           else if (far_c) op.code = static_cast<uint8_t>(OPC_XF + tl);
           else op.code = static_cast<uint8_t>(OPC_XL + 4 * tl + cl);
           pass_cost += 0.5;
-        } else if (r.cls == G_ANTI) {
-          op.code = static_cast<uint8_t>(OPC_ANTI + tl);
-          op.m[1] = to_f2(u.m[1]);
-          op.m[2] = to_f2(u.m[2]);
-          pass_cost += 1.0;
-        } else {
+        } else {  // dense, or anti-diagonal other than X (as a dense factor)
           op.code = static_cast<uint8_t>((r.c < 0 ? OPC_DENSE : OPC_CDENSE) + tl);
           for (int i = 0; i < 4; ++i) {
             op.m[i] = to_f2(u.m[i]);

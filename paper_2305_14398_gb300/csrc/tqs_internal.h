@@ -26,7 +26,8 @@ namespace tqs {
 //   OPC_X + t        uncontrolled exchange of the pair (X)
 //   OPC_XF + t       exchange where far control bit `fbit` of the group is 1 (CNOT)
 //   OPC_XL + 4t + c  exchange in the pairs whose local control bit c is 1 (CNOT)
-//   OPC_ANTI + t     anti-diagonal [[0, m01], [m10, 0]]; `act` mask / `fbit`
+//   OPC_ANTI + t     (reserved; anti-diagonal factors other than X run as DENSE:
+//                    fewer kernel code paths, and their coefficients get hi + lo)
 //   OPC_DENSE + t    uncontrolled 2x2, coefficients as FP32 hi + lo
 //   OPC_CDENSE + t   controlled 2x2 (`act` mask for a local control, `fbit` far)
 //   OPC_DLN + t      diag(d0, d1), local target, uncontrolled
