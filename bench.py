@@ -37,10 +37,10 @@ WORKLOAD = "paper-shaped 11-qubit circuits (GHZ / DJ-constant / DJ-balanced / QF
 
 # DRAM bytes (read + write) per launch of the fused kernel (two warps per
 # circuit, the autotuned shape) on this workload, from the ncu capture
-# summarised in profiles/: 36.72 MB read + 476.60 MB written for one launch
+# summarised in profiles/: 36.70 MB read + 476.53 MB written for one launch
 # over the 16384 circuits of a step.  Set back to None whenever the kernel
 # changes, until it is captured again.
-NCU_TRAFFIC_BYTES = 36_718_592 + 476_595_456
+NCU_TRAFFIC_BYTES = 36_699_392 + 476_533_760
 
 
 def parse_args():
