@@ -872,6 +872,13 @@ struct tqs_circuit {
   bool prog_init_valid = false;
   Program prog_init;  // for a given input state (nothing folded)
   DevBuf d_prog;      // FusedCirc + passes + ops
+  // what d_prog holds: the program (prog or prog_init) and the initial-state
+  // pointer it was uploaded with (valid while `uploaded`)
+  bool uploaded = false;
+  const void* uploaded_prog = nullptr;
+  const void* uploaded_init = nullptr;
+  cudaEvent_t upload_done = nullptr;  // recorded after the upload, on upload_stream
+  cudaStream_t upload_stream = nullptr;
   DevBuf d_counter;   // job counter
   DevBuf d_gscratch;  // TEAM_GLOBAL slot
   // cached plain-form step table
@@ -892,6 +899,9 @@ struct tqs_circuit {
   // chain scratch
   DevBuf d_chain;
   DevBuf d_err;
+  ~tqs_circuit() {
+    if (upload_done) cudaEventDestroy(upload_done);
+  }
 };
 
 extern "C" {
@@ -1000,6 +1010,7 @@ tqs_status tqs_add_gate(tqs_circuit* c, int gate, const int* qubits, int nq, con
   c->gates.push_back(g);
   c->prog_valid = false;
   c->prog_init_valid = false;
+  c->uploaded = false;
   c->steps_valid = false;
   c->fsv_valid = false;
   return TQS_OK;
@@ -1076,6 +1087,7 @@ tqs_status tqs_add_custom(tqs_circuit* c, const char* name, const int* qubits, i
   c->gates.push_back(g);
   c->prog_valid = false;
   c->prog_init_valid = false;
+  c->uploaded = false;
   c->steps_valid = false;
   c->fsv_valid = false;
   return TQS_OK;
@@ -1245,14 +1257,31 @@ static tqs_status simulate_impl(tqs_circuit* c, const tqs_c64* d_init, tqs_c64* 
   img.add(P, 0);
   img.circs[0].init = reinterpret_cast<const float2*>(d_init);
   const size_t order_off = (img.bytes() + 255) & ~size_t(255);
-  TQS_CUDA(c->d_prog.ensure(order_off + 256), "tqs_simulate: cudaMalloc program");
-  TQS_CUDA(img.upload(c->d_prog.p, s), "tqs_simulate: upload program");
+  // The device program is uploaded once per (program, initial-state pointer)
+  // and reused by later calls on the circuit.
+  if (!c->uploaded || c->uploaded_prog != &P || c->uploaded_init != d_init) {
+    c->uploaded = false;
+    TQS_CUDA(c->d_prog.ensure(order_off + 256), "tqs_simulate: cudaMalloc program");
+    TQS_CUDA(img.upload(c->d_prog.p, s), "tqs_simulate: upload program");
+    // order[0] = 0 lives right after the image
+    static const int32_t zero_order[1] = {0};
+    TQS_CUDA(cudaMemcpyAsync(c->d_prog.as<char>() + order_off, zero_order, sizeof(int32_t),
+                             cudaMemcpyHostToDevice, s),
+             "tqs_simulate: upload order");
+    if (!c->upload_done)
+      TQS_CUDA(cudaEventCreateWithFlags(&c->upload_done, cudaEventDisableTiming),
+               "tqs_simulate: event");
+    TQS_CUDA(cudaEventRecord(c->upload_done, s), "tqs_simulate: event");
+    c->upload_stream = s;
+    c->uploaded = true;
+    c->uploaded_prog = &P;
+    c->uploaded_init = d_init;
+  } else if (s != c->upload_stream) {
+    // another stream reuses the program: its kernels wait for the upload
+    TQS_CUDA(cudaStreamWaitEvent(s, c->upload_done, 0), "tqs_simulate: wait upload");
+  }
   TQS_CUDA(c->d_counter.ensure(2 * sizeof(int32_t)), "tqs_simulate: cudaMalloc counter");
-  // order[0] = 0 lives right after the image; counter is zeroed per launch
-  static const int32_t zero_order[1] = {0};
   char* base = c->d_prog.as<char>();
-  TQS_CUDA(cudaMemcpyAsync(base + order_off, zero_order, sizeof(int32_t), cudaMemcpyHostToDevice, s),
-           "tqs_simulate: upload order");
   TQS_CUDA(cudaMemsetAsync(c->d_counter.p, 0, 2 * sizeof(int32_t), s), "tqs_simulate: memset");
   FusedLaunch L{};
   img.point(L, base);

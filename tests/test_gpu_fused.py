@@ -252,3 +252,38 @@ def test_abi_errors_on_gpu():
             B.tqs_materialize_step(c, 99, out)
     finally:
         B.tqs_circuit_destroy(c)
+
+
+def test_program_upload_reused_and_refreshed():
+    """tqs_simulate keeps a circuit's device program between calls: repeated
+    calls (also from another stream, and alternating initial states) give the
+    same results, and adding a gate refreshes the program."""
+    n = 9
+    ops = W.random_mixed(n, 8, (97, n))
+    want = fsv_route.simulate(n, ops)
+    rng = np.random.default_rng(98)
+    v = rng.normal(size=1 << n) + 1j * rng.normal(size=1 << n)
+    v /= np.linalg.norm(v)
+    init = torch.from_numpy(v.astype(np.complex64)).cuda()
+    want_init = fsv_route.simulate(n, ops, v)
+    c = B.circuit_from_ops(n, ops)
+    try:
+        other = torch.cuda.Stream()
+        for stream, x, w in ((None, None, want), (None, None, want), (other, None, want),
+                             (None, init, want_init), (None, None, want), (other, init, want_init)):
+            out = torch.empty(1 << n, dtype=torch.complex64, device="cuda")
+            if stream is not None:
+                other.wait_stream(torch.cuda.current_stream())
+            B.tqs_simulate(c, out, init=x, stream=stream)
+            if stream is not None:
+                torch.cuda.current_stream().wait_stream(other)
+            torch.cuda.synchronize()
+            assert np.max(np.abs(out.cpu().numpy().astype(np.complex128) - w)) <= AMP_TOL
+        B.tqs_add_gate(c, "h", (3,))
+        out = torch.empty(1 << n, dtype=torch.complex64, device="cuda")
+        B.tqs_simulate(c, out)
+        torch.cuda.synchronize()
+        want2 = fsv_route.simulate(n, list(ops) + [("h", (3,), ())])
+        assert np.max(np.abs(out.cpu().numpy().astype(np.complex128) - want2)) <= AMP_TOL
+    finally:
+        B.tqs_circuit_destroy(c)
