@@ -256,11 +256,11 @@ cudaError_t launch_set_basis(float2* d_state, int n, const int64_t* d_index, cud
 // coalesced loads, plus the bits the pass's gates need).  Every op of the
 // pass acts on the tile; bits outside it are fixed per tile.
 // ---------------------------------------------------------------------------
-constexpr int kFsvTileQ = 12;
+constexpr int kFsvTileQ = 13;
 constexpr int kFsvLowQ = 5;
 constexpr int kFsvThreads = 256;
 
-constexpr int kFsvMaxFar = 19;  // bits outside the tile a pass may test (T + far <= 31)
+constexpr int kFsvMaxFar = 18;  // bits outside the tile a pass may test (T + far <= 31)
 
 // One pass of the full-state-vector backend.  Its gates, relabelled to tile
 // qubits (the tile bits in ascending order are tile qubits 0..T-1; the far

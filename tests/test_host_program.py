@@ -479,18 +479,24 @@ def test_custom_registry_errors():
 
 def test_fsv_pass_grouping():
     """GHZ chain at n = 20: CNOT targets 1..19.  Tiles hold the 5 lowest bits
-    plus 7 more, so targets 1..11 share the first pass, 12..18 the second and
-    19 the third."""
+    plus 8 more, so targets 1..12 share the first pass and 13..19 the second;
+    at n = 30 the targets 13..20 and 21..28 take passes of their own, 29 the
+    last."""
+    c = B.circuit_from_ops(30, W.ghz_chain(30))
+    try:
+        assert B.tqs_fsv_passes(c) == (4, 13)
+    finally:
+        B.tqs_circuit_destroy(c)
     c = B.circuit_from_ops(20, W.ghz_chain(20))
     try:
-        assert B.tqs_fsv_passes(c) == (3, 12)
+        assert B.tqs_fsv_passes(c) == (2, 13)
     finally:
         B.tqs_circuit_destroy(c)
     # diagonal gates and controls never need a tile slot
     ops = [("h", (0,), ())] + [("cp", (19, q), (0.3,)) for q in range(5)] + [("z", (18,), ())]
     c = B.circuit_from_ops(20, ops)
     try:
-        assert B.tqs_fsv_passes(c) == (1, 12)
+        assert B.tqs_fsv_passes(c) == (1, 13)
     finally:
         B.tqs_circuit_destroy(c)
 
