@@ -2816,7 +2816,9 @@ tqs_status tqs_batch_sample(tqs_batch* b, const double* d_probs, int shots, cons
 static tqs_status compile_fsv(int n, const std::vector<Gate>& gates, int max_gates, FsvProgram& P) {
   P = FsvProgram();
   P.max_gates = max_gates;
-  const int T = std::min(n, kFsvTileQ);
+  // 2^13-amplitude tiles from 24 qubits on (fewer passes); below that 2^12,
+  // so that a state still spreads over enough tiles to fill the GPU
+  const int T = std::min(n, n >= 24 ? kFsvTileQ : kFsvTileQ - 1);
   const int nlow = std::min(T, kFsvLowQ);
   P.T = T;
   const uint64_t low = (uint64_t(1) << nlow) - 1;

@@ -478,10 +478,10 @@ def test_custom_registry_errors():
 # ------------------------------------------------------- full state vector
 
 def test_fsv_pass_grouping():
-    """GHZ chain at n = 20: CNOT targets 1..19.  Tiles hold the 5 lowest bits
-    plus 8 more, so targets 1..12 share the first pass and 13..19 the second;
-    at n = 30 the targets 13..20 and 21..28 take passes of their own, 29 the
-    last."""
+    """GHZ chain, CNOT targets 1..n-1.  At n = 20 tiles hold the 5 lowest bits
+    plus 7 more (2^12 amplitudes below 24 qubits), so targets 1..11 share the
+    first pass, 12..18 the second and 19 the third; at n = 30 (2^13-amplitude
+    tiles: 8 more bits) 1..12, 13..20 and 21..28 take a pass each, 29 the last."""
     c = B.circuit_from_ops(30, W.ghz_chain(30))
     try:
         assert B.tqs_fsv_passes(c) == (4, 13)
@@ -489,14 +489,14 @@ def test_fsv_pass_grouping():
         B.tqs_circuit_destroy(c)
     c = B.circuit_from_ops(20, W.ghz_chain(20))
     try:
-        assert B.tqs_fsv_passes(c) == (2, 13)
+        assert B.tqs_fsv_passes(c) == (3, 12)
     finally:
         B.tqs_circuit_destroy(c)
     # diagonal gates and controls never need a tile slot
     ops = [("h", (0,), ())] + [("cp", (19, q), (0.3,)) for q in range(5)] + [("z", (18,), ())]
     c = B.circuit_from_ops(20, ops)
     try:
-        assert B.tqs_fsv_passes(c) == (1, 13)
+        assert B.tqs_fsv_passes(c) == (1, 12)
     finally:
         B.tqs_circuit_destroy(c)
 
