@@ -125,7 +125,7 @@ static_assert(sizeof(FusedCirc) == 64, "FusedCirc layout");
 // states live in global scratch (L2-resident) and are worked by a CTA.
 constexpr int kWarpMaxQ = 11;
 constexpr int kCtaMaxQ = 14;
-constexpr int kCtaThreads = 256;
+constexpr int kCtaThreads = 512;
 constexpr int kGlobalThreads = 512;
 constexpr int kGlobalSlotQ = 16;   // log2 amplitudes per TEAM_GLOBAL scratch slot
 

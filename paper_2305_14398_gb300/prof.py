@@ -11,7 +11,8 @@ fsv:   the full-state-vector backend on a random layered circuit
 mix:   COUNT paper-shaped 11-qubit circuits (GHZ / DJ-constant / DJ-balanced /
        QFT, 25 % each); ghz, dj_constant, dj_balanced, qft: COUNT circuits of one
        of those kinds; batch: the first COUNT circuits of the random batched
-       workload (n = 4..14, depth 5..40).  Runs tqs_batch_run REPS times
+       workload (n = 4..14, depth 5..40); n14: COUNT random circuits at n = 14.
+       Runs tqs_batch_run REPS times
        without a graph, then once more timed with CUDA events.
 noprobs: the same without the FP64 probability output (d_probs = NULL).
 TWxW (e.g. 2x16): warps per circuit and per CTA of the 11-qubit warp class
@@ -99,6 +100,8 @@ def main(argv):
         circs = [(11, ops) for _, ops in W.paper_mix(11, count)]
     elif kind in ("ghz", "dj_constant", "dj_balanced", "qft"):
         circs = [(11, ops) for k, ops in W.paper_mix(11, 4 * count) if k == kind]
+    elif kind == "n14":
+        circs = W.batch_circuits_fixed_n(count, 14)
     else:
         circs = W.batch_circuits(count, 3)
     b = B.tqs_batch_create_packed(*B.pack_ops(circs))
