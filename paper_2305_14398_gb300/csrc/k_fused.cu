@@ -8,11 +8,14 @@
 // 4 thread-local qubit bits (see tqs_internal.h); a team of threads holds the
 // circuit's state in shared memory (or, above 2^14 amplitudes, in L2-resident
 // global scratch) and runs the passes, then writes the state in logical
-// order, |psi_i|^2 in FP64, and the FP64 norm.
+// order, |psi_i|^2 (FP32 arithmetic, or exact in FP64) stored as FP64, and
+// the FP64 norm.
 //
-// Teams: one warp per circuit (n <= 11), one CTA per circuit (n <= 14), or one
-// CTA on global scratch (n <= 16).  Warps/CTAs pull circuits from an atomic
-// job counter (costliest first), so one persistent launch runs a whole batch.
+// Teams: one warp or a pair of warps per circuit (n <= 11), one 512-thread CTA
+// per circuit (n <= 14), one CTA on global scratch (n <= 16), or several
+// cooperating CTAs on global scratch for a few 15-16 qubit circuits
+// (TEAM_MULTI).  Warps/CTAs pull circuits from an atomic job counter
+// (costliest first), so one persistent launch runs a whole batch.
 #include "checked.h"
 #include "exact_sq.h"
 #include "tqs_internal.h"
