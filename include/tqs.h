@@ -230,10 +230,10 @@ tqs_status tqs_circuit_unitary(tqs_circuit* c, int prec, tqs_c64* d_U, void* str
  * (2^n tqs_c64, in place, 16-byte aligned; the caller initialises it) goes
  * through the circuit's gates in the order they were added.  Gates are
  * grouped into passes; each pass is one launch that streams the state
- * through shared memory in tiles of 2^12 amplitudes (the 5 lowest qubits plus
- * up to 7 more that the pass's gates act on non-diagonally; controls and
- * diagonal gates may sit on any qubit), so the state crosses HBM twice per
- * pass.  Custom unitaries are supported; measure/reset instructions return
+ * through shared memory in tiles of 2^13 amplitudes from 24 qubits on, 2^12
+ * below (the 5 lowest qubits plus up to 8, or 7, more that the pass's gates
+ * act on non-diagonally; controls and diagonal gates may sit on any qubit),
+ * so the state crosses HBM twice per pass.  Custom unitaries are supported; measure/reset instructions return
  * TQS_ERR_UNSUPPORTED.  Scratch (cached on the circuit): the pass program.
  * FP32 amplitudes, FP32 hi + lo coefficients. */
 tqs_status tqs_simulate_fsv(tqs_circuit* c, tqs_c64* d_state, void* stream);
