@@ -195,7 +195,11 @@ tqs_status tqs_circuit_program(tqs_circuit* c, int* n_passes, int* n_ops, void* 
  *   d_probs : 2^n doubles, receives |psi_i|^2 (FP32 arithmetic, or exact
  *             in FP64 under TQS_OPT_EXACT_PROBS), or NULL.
  *   d_norm  : 1 double, receives sum_i |psi_i|^2 (FP64), or NULL.
- * n <= TQS_MAX_QUBITS.  Arithmetic: FP32 amplitudes, FP64 probabilities. */
+ * n <= TQS_MAX_QUBITS.  Arithmetic: FP32 amplitudes, probabilities stored as
+ * FP64, FP64 norm.  The circuit's device program is uploaded on the first
+ * call and kept until the circuit changes (or d_init changes between NULL and
+ * a buffer); a 15-16 qubit circuit runs on several cooperating CTAs
+ * (TQS_OPT_MULTI_CTAS).  A circuit handle is used by one stream at a time. */
 tqs_status tqs_simulate(tqs_circuit* c, const tqs_c64* d_init, tqs_c64* d_out,
                         double* d_probs, double* d_norm, void* stream);
 
