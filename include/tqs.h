@@ -197,8 +197,8 @@ tqs_status tqs_circuit_program(tqs_circuit* c, int* n_passes, int* n_ops, void* 
  *   d_norm  : 1 double, receives sum_i |psi_i|^2 (FP64), or NULL.
  * n <= TQS_MAX_QUBITS.  Arithmetic: FP32 amplitudes, probabilities stored as
  * FP64, FP64 norm.  The circuit's device program is uploaded on the first
- * call and kept until the circuit changes (or d_init changes between NULL and
- * a buffer); a 15-16 qubit circuit runs on several cooperating CTAs
+ * call and kept until the circuit or the d_init pointer changes; a 15-16
+ * qubit circuit runs on several cooperating CTAs
  * (TQS_OPT_MULTI_CTAS).  A circuit handle is used by one stream at a time. */
 tqs_status tqs_simulate(tqs_circuit* c, const tqs_c64* d_init, tqs_c64* d_out,
                         double* d_probs, double* d_norm, void* stream);
