@@ -8,10 +8,8 @@ CDF on a uniform grid, invariants (norm 1 after a measurement, measurement
 commuting with gates on other qubits), and planted mistakes that one of them
 catches.
 """
-import math
 
 import numpy as np
-import pytest
 
 from oracle import collapse, fsv_route, observables
 from paper_2305_14398_gb300 import workloads as W
