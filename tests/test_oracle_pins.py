@@ -85,6 +85,34 @@ def test_eq7_controlled_u_structure():
     assert maxabs(m, want) < 1e-15
 
 
+def test_cz_pins():
+    """CZ (controlled-Z, eq. 7 with U = Z of Table 1), pinned three ways that do
+    not go through the oracle's own controlled-gate table:
+    * on every basis state of 3 qubits, CZ(c, t) multiplies |x> by -1 exactly
+      when bits c and t of x are both 1 and leaves it alone otherwise;
+    * it is symmetric: CZ(c, t) = CZ(t, c) (a wrong table, e.g. C-X or C-Y,
+      is not);
+    * H_t CNOT(c, t) H_t = CZ(c, t), with CNOT pinned by the printed eq. 8 and
+      H by the printed Table 1; and CZ = CP(pi) entrywise (R_pi = Z)."""
+    n = 3
+    pairs = [(c, t) for c in range(n) for t in range(n) if c != t]
+    for c, t in pairs:
+        for x in range(1 << n):
+            e = np.zeros(1 << n, dtype=np.complex128)
+            e[x] = 1.0
+            sign = -1.0 if (x >> c) & 1 and (x >> t) & 1 else 1.0
+            for route in (kron_route, fsv_route):
+                prep = [("x", (q,), ()) for q in range(n) if (x >> q) & 1]
+                assert maxabs(route.simulate(n, prep + [("cz", (c, t), ())]), sign * e) == 0.0
+        u_ct = kron_route.step_unitary(n, [("cz", (c, t), ())])
+        u_tc = kron_route.step_unitary(n, [("cz", (t, c), ())])
+        assert maxabs(u_ct, u_tc) == 0.0
+        h = kron_route.step_unitary(n, [("h", (t,), ())])
+        cx = kron_route.step_unitary(n, [("cx", (c, t), ())])
+        assert maxabs(h @ cx @ h, u_ct) < 1e-15
+        assert maxabs(kron_route.step_unitary(n, [("cp", (c, t), (math.pi,))]), u_ct) < 1e-15
+
+
 def test_eq11_bell_printed():
     """Eq. 11: S_2 S_1 |00> = (1/sqrt2, 0, 0, 1/sqrt2), for the printed
     matrices (mirror reading) and for the Bell listing H(0), CNOT(0, 1)."""
@@ -362,3 +390,18 @@ def test_planted_sign_mistake_is_caught(monkeypatch):
     monkeypatch.setattr(gates, "single_qubit_matrix", bad)
     psi = fsv_route.simulate(2, [("h", (0,), ()), ("h", (0,), ())])
     assert abs(observables.total(observables.probabilities(psi)) - 1.0) > 0.1
+
+
+@pytest.mark.parametrize("wrong", ["x", "y", "s"])
+def test_planted_cz_mistake_is_caught(monkeypatch, wrong):
+    """A wrong CZ target matrix (C-X, C-Y or C-S) must break the CZ pins."""
+    orig = gates.controlled_target_matrix
+
+    def bad(name, params=()):
+        if name == "cz":
+            return gates.single_qubit_matrix(wrong)
+        return orig(name, params)
+
+    monkeypatch.setattr(gates, "controlled_target_matrix", bad)
+    with pytest.raises(AssertionError):
+        test_cz_pins()
