@@ -228,6 +228,25 @@ tqs_status tqs_materialize_step(tqs_circuit* c, int step, tqs_c64* d_S, void* st
  * TQS_ERR_TIMEOUT if one of its bounded device waits ran out. */
 tqs_status tqs_circuit_unitary(tqs_circuit* c, int prec, tqs_c64* d_U, void* stream);
 
+/* A block of columns of the circuit unitary, U[:, col0 : col0 + ncols], by the
+ * same chain (Algorithm 1).  Column j of U is the circuit applied to |j>, and
+ * U <- S_k U acts on each column alone, so a column block needs only its own
+ * columns and the step unitaries, which every caller generates from the step
+ * table: blocks on different GPUs need no communication (the column-sharded
+ * chain), and blocks computed separately are bitwise the columns of the whole
+ * tqs_circuit_unitary result in the same precision.
+ *   d_U : 2^n rows of ncols tqs_c64, d_U[r * ldu + j] = <r|U|col0 + j>,
+ *         ldu >= ncols (ldu = 2^n with d_U pointing at column col0 of a full
+ *         row-major U fills that block of it).
+ * Limits as tqs_circuit_unitary; for n >= 7, col0 and ncols must be multiples
+ * of 128 (the tensor-core tile), else TQS_ERR_ARG; a block outside the 2^n
+ * columns is TQS_ERR_ARG.  Scratch (cached on the circuit): the step matrix's
+ * operands plus two ncols x 2^n chain matrices (BF16x3: 12 * 4^n +
+ * 24 * ncols * 2^n bytes; TF32x3 twice that; FP32 SIMT: 8 * 4^n +
+ * 16 * ncols * 2^n). */
+tqs_status tqs_circuit_unitary_cols(tqs_circuit* c, int prec, int col0, int ncols, tqs_c64* d_U,
+                                    int64_t ldu, void* stream);
+
 /* ----------------------------------------------------- full state vector
  * The per-gate state-vector update of Appendix A (eq. 12; the paper's future
  * work) for states held in HBM, up to TQS_MAX_FSV_QUBITS qubits: d_state
@@ -263,12 +282,15 @@ tqs_status tqs_probabilities(const tqs_c64* d_state, int n, double* d_probs,
  * convenience.  Same arguments, results and determinism as tqs_probabilities.
  *   - Scratch: the per-block partial sums live in one fixed device array of
  *     1024 doubles (8 KiB) that every GPU loading the library holds until the
- *     process exits.  1 <= n <= 30 (at most 1024 partial sums); larger n
- *     returns TQS_ERR_TOO_MANY_QUBITS.
+ *     process exits; it holds the partial sums of every allowed n.
+ *     1 <= n <= 30, as for tqs_probabilities; other n return
+ *     TQS_ERR_TOO_MANY_QUBITS.
  *   - The first call on each device looks up the array's device address
  *     (cudaGetSymbolAddress) with that device current and caches it; make
- *     that first call before any stream capture.  No call allocates or frees
- *     device memory.
+ *     that first call before any stream capture.  The cached address is that
+ *     of the device's primary context (the CUDA runtime's): do not call after
+ *     cudaDeviceReset, or with another context of the same device current.
+ *     No call allocates or frees device memory.
  *   - Every call on a GPU shares that GPU's copy of the array.  Each call
  *     overwrites all the partial sums it reads, so nothing carries over
  *     between calls, but calls that overlap on the same GPU (for example on
@@ -371,6 +393,18 @@ tqs_status tqs_batch_sample(tqs_batch* b, const double* d_probs, int shots, cons
  * instructions take uniforms / write outcomes [h_off[i], h_off[i+1]) in
  * their order in the circuit.  h_off[count] = all instructions. */
 tqs_status tqs_batch_instructions(const tqs_batch* b, int64_t* h_off);
+
+/* Launch shape of a batch's persistent kernel for one size class (0: circuits
+ * of n <= 11, run by one or two warps each; 1: n = 12..14, one CTA each with
+ * the state in shared memory; 2: n = 15..16, one CTA each on global scratch),
+ * as the last tqs_batch_run chose it from the options in force then (a
+ * scheduling fact: results do not depend on it).  Outputs (each may be
+ * NULL): jobs = circuits of that class, grid = CTAs, threads = threads per
+ * CTA, teams = circuits that run at once (the persistent teams; each takes
+ * about jobs / teams circuits from the job counter).  All are 0 for a class
+ * the batch does not hold.  TQS_ERR_STATE before the batch's first run. */
+tqs_status tqs_batch_launch_info(const tqs_batch* b, int size_class, int* jobs, int* grid,
+                                 int* threads, int* teams);
 
 /* tqs_batch_run for batches that hold instructions: d_u (h_off[count]
  * doubles) and d_outcomes (h_off[count] int32, may be NULL) in the layout of
@@ -546,6 +580,16 @@ const char* tqs_status_string(int status);
 /* Number of this library's kernel launches enqueued so far by this process
  * (a graph replay counts its kernel nodes). */
 int64_t tqs_launch_count(void);
+
+/* ------------------------------------------------------------- measurement
+ * The device's FP32 FMA rate, measured: one launch in which every thread of
+ * 8 blocks of 256 per SM runs 8 independent chains of 16 * iters fused
+ * multiply-adds (2 flops each), timed with CUDA events on `stream` after one
+ * warm-up launch (synchronises the stream).  *h_tflops = flops / time;
+ * *h_ms (may be NULL) = the timed launch.  The denominator of the FP32-bound
+ * roofline fractions (the paper has no counterpart: its evaluation reports
+ * speedups only).  iters >= 1; 20000 takes about 10 ms on a GB300. */
+tqs_status tqs_measure_fp32_peak(int iters, double* h_tflops, double* h_ms, void* stream);
 
 #ifdef __cplusplus
 }

@@ -66,6 +66,8 @@ _SIGS = {
     "tqs_simulate_measured": (_i, [_vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp]),
     "tqs_materialize_step": (_i, [_vp, _i, _vp, _vp]),
     "tqs_circuit_unitary": (_i, [_vp, _i, _vp, _vp]),
+    "tqs_circuit_unitary_cols": (_i, [_vp, _i, _i, _i, _vp, _i64, _vp]),
+    "tqs_measure_fp32_peak": (_i, [_i, _pd, _pd, _vp]),
     "tqs_probabilities": (_i, [_vp, _i, _vp, _vp, _vp]),
     "tqs_marginal_zero": (_i, [_vp, _i, _u64, _vp, _vp]),
     "tqs_probabilities_noalloc": (_i, [_vp, _i, _vp, _vp, _vp]),
@@ -79,6 +81,7 @@ _SIGS = {
     "tqs_batch_run": (_i, [_vp, _vp, _vp, _vp, _i, _vp]),
     "tqs_batch_run_host": (_i, [_vp, _vp, _vp, _vp, _vp]),
     "tqs_batch_instructions": (_i, [_vp, _vp]),
+    "tqs_batch_launch_info": (_i, [_vp, _i, _pi, _pi, _pi, _pi]),
     "tqs_batch_run_measured": (_i, [_vp, _vp, _vp, _vp, _vp, _vp, _i, _vp]),
     "tqs_batch_destroy": (_i, [_vp]),
     "tqs_server_create": (_i, [ctypes.c_size_t, _i, _i, ctypes.POINTER(_vp)]),
@@ -280,6 +283,14 @@ def tqs_circuit_unitary(c: int, prec: int, U, stream=None) -> None:
     _check(lib().tqs_circuit_unitary(c, int(prec), _ptr(U), _stream(stream)))
 
 
+def tqs_circuit_unitary_cols(c: int, prec: int, col0: int, ncols: int, U, ldu: Optional[int] = None,
+                             stream=None) -> None:
+    """Columns [col0, col0 + ncols) of the circuit unitary into U (a 2^n x ldu
+    row-major view; ldu defaults to ncols, a compact block)."""
+    _check(lib().tqs_circuit_unitary_cols(c, int(prec), int(col0), int(ncols), _ptr(U),
+                                          int(ncols if ldu is None else ldu), _stream(stream)))
+
+
 def tqs_probabilities(state, n: int, probs=None, total=None, stream=None) -> None:
     _check(lib().tqs_probabilities(_ptr(state), int(n), _ptr(probs), _ptr(total), _stream(stream)))
 
@@ -381,6 +392,13 @@ def tqs_batch_instructions(b: int) -> np.ndarray:
     return off
 
 
+def tqs_batch_launch_info(b: int, size_class: int):
+    """{"jobs", "grid", "threads", "teams"} of one size class's last launch."""
+    v = [ctypes.c_int() for _ in range(4)]
+    _check(lib().tqs_batch_launch_info(b, size_class, *[ctypes.byref(x) for x in v]))
+    return dict(zip(("jobs", "grid", "threads", "teams"), (x.value for x in v)))
+
+
 def tqs_batch_run_measured(b: int, states, u, outcomes=None, probs=None, norms=None,
                            use_graph: bool = True, stream=None) -> None:
     _check(lib().tqs_batch_run_measured(b, _ptr(states), _ptr(probs), _ptr(norms), _ptr(u),
@@ -400,6 +418,13 @@ def tqs_batch_run_host(b: int, h_states=None, h_probs=None, h_norms=None, stream
 
 def tqs_batch_destroy(b: int) -> None:
     _check(lib().tqs_batch_destroy(b))
+
+
+def tqs_measure_fp32_peak(iters: int = 20000, stream=None):
+    """(TFLOP/s, ms) of the FP32 FMA microkernel."""
+    t, ms = ctypes.c_double(), ctypes.c_double()
+    _check(lib().tqs_measure_fp32_peak(int(iters), ctypes.byref(t), ctypes.byref(ms), _stream(stream)))
+    return t.value, ms.value
 
 
 def tqs_launch_count() -> int:

@@ -362,6 +362,25 @@ tqs_status tqs_batch_instructions(const tqs_batch* b, int64_t* h_off) {
   return TQS_OK;
 }
 
+tqs_status tqs_batch_launch_info(const tqs_batch* b, int size_class, int* jobs, int* grid,
+                                 int* threads, int* teams) {
+  if (!b || size_class < 0 || size_class > 2)
+    return fail(TQS_ERR_ARG, "tqs_batch_launch_info: NULL batch or size class outside 0..2");
+  if (!b->uploaded) return fail(TQS_ERR_STATE, "tqs_batch_launch_info: the batch has not run yet");
+  const LaunchPlan& lp = b->plans[size_class];
+  const int n_jobs = b->n_team[size_class];
+  int per_cta = 1;
+  if (lp.team == TEAM_WARP) per_cta = lp.warps;
+  else if (lp.team == TEAM_PAIR) per_cta = lp.warps / 2;
+  if (jobs) *jobs = n_jobs;
+  if (grid) *grid = n_jobs ? lp.grid : 0;
+  const int nthreads = (lp.team == TEAM_WARP || lp.team == TEAM_PAIR) ? 32 * lp.warps
+                       : lp.team == TEAM_CTA ? kCtaThreads : kGlobalThreads;
+  if (threads) *threads = n_jobs ? nthreads : 0;
+  if (teams) *teams = n_jobs ? lp.grid * per_cta : 0;
+  return TQS_OK;
+}
+
 }  // extern "C"
 
 
@@ -440,18 +459,29 @@ tqs_status tqs_batch_destroy(tqs_batch* b) {
   return TQS_OK;
 }
 
-tqs_status tqs_circuit_unitary(tqs_circuit* c, int prec, tqs_c64* d_U, void* stream) {
+}  // extern "C"
+
+// Columns [col0, col0 + ncols) of the circuit unitary (Algorithm 1) into
+// d_U[r * ldu + j] = U[r][col0 + j]; the whole unitary is the block col0 = 0,
+// ncols = ldu = 2^n.
+static tqs_status unitary_block(tqs_circuit* c, int prec, int col0, int ncols, tqs_c64* d_U,
+                                int64_t ldu, void* stream, const char* who) {
   if (c && c->n_instr > 0)
-    return fail(TQS_ERR_UNSUPPORTED,
-                "tqs_circuit_unitary: measure/reset instructions have no circuit unitary");
-  if (!c || !d_U) return fail(TQS_ERR_ARG, "tqs_circuit_unitary: NULL argument");
-  if (!aligned16(d_U)) return fail(TQS_ERR_ARG, "tqs_circuit_unitary: d_U must be 16-byte aligned");
+    return fail(TQS_ERR_UNSUPPORTED, "%s: measure/reset instructions have no circuit unitary", who);
+  if (!c || !d_U) return fail(TQS_ERR_ARG, "%s: NULL argument", who);
+  if (!aligned16(d_U)) return fail(TQS_ERR_ARG, "%s: d_U must be 16-byte aligned", who);
   if (c->n > TQS_MAX_DENSE_QUBITS)
-    return fail(TQS_ERR_TOO_MANY_QUBITS, "tqs_circuit_unitary: n %d > %d", c->n, TQS_MAX_DENSE_QUBITS);
+    return fail(TQS_ERR_TOO_MANY_QUBITS, "%s: n %d > %d", who, c->n, TQS_MAX_DENSE_QUBITS);
   if (prec != TQS_PREC_FP32_SIMT && prec != TQS_PREC_TC_BF16X3 && prec != TQS_PREC_TC_TF32X3)
-    return fail(TQS_ERR_ARG, "tqs_circuit_unitary: unknown precision %d", prec);
+    return fail(TQS_ERR_ARG, "%s: unknown precision %d", who, prec);
   if (prec != TQS_PREC_FP32_SIMT && c->n < 7)
-    return fail(TQS_ERR_ARG, "tqs_circuit_unitary: the tensor-core chain needs n >= 7");
+    return fail(TQS_ERR_ARG, "%s: the tensor-core chain needs n >= 7", who);
+  const int N = 1 << c->n;
+  if (col0 < 0 || ncols < 1 || col0 > N - ncols || ldu < ncols)
+    return fail(TQS_ERR_ARG, "%s: column block [%d, %d + %d) or ldu %lld outside the %d columns", who,
+                col0, col0, ncols, static_cast<long long>(ldu), N);
+  if (c->n >= 7 && (col0 % 128 != 0 || ncols % 128 != 0))
+    return fail(TQS_ERR_ARG, "%s: for n >= 7, col0 and ncols must be multiples of 128", who);
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   tqs_status st = upload_factors(c, s);
   if (st != TQS_OK) return st;
@@ -459,29 +489,53 @@ tqs_status tqs_circuit_unitary(tqs_circuit* c, int prec, tqs_c64* d_U, void* str
   if (c->nsteps <= 1) {
     // Algorithm 1 with at most one step: U = S_1 (or the identity).
     StepDesc d = c->nsteps == 1 ? c->steps[0] : StepDesc{0, 0, (1u << c->n) - 1u, 0};
-    TQS_CUDA(launch_materialize(c->d_factors.as<StepFactor>(), d, c->n, U, s),
+    if (col0 == 0 && ncols == N && ldu == N) {
+      TQS_CUDA(launch_materialize(c->d_factors.as<StepFactor>(), d, c->n, U, s),
+               "tqs_circuit_unitary: materialize");
+      return TQS_OK;
+    }
+    TQS_CUDA(c->d_chain.ensure(size_t(N) * N * sizeof(float2)), "tqs_circuit_unitary: cudaMalloc");
+    float2* S = c->d_chain.as<float2>();
+    TQS_CUDA(launch_materialize(c->d_factors.as<StepFactor>(), d, c->n, S, s),
              "tqs_circuit_unitary: materialize");
+    TQS_CUDA(cudaMemcpy2DAsync(U, size_t(ldu) * sizeof(float2), S + col0, size_t(N) * sizeof(float2),
+                               size_t(ncols) * sizeof(float2), size_t(N), cudaMemcpyDeviceToDevice, s),
+             "tqs_circuit_unitary: copy block");
     return TQS_OK;
   }
   if (prec == TQS_PREC_FP32_SIMT) {
-    TQS_CUDA(c->d_chain.ensure(chain_simt_scratch_bytes(c->n)), "tqs_circuit_unitary: cudaMalloc");
-    TQS_CUDA(chain_simt(c->d_factors.as<StepFactor>(), c->steps.data(), c->nsteps, c->n, U,
-                        c->d_chain.p, s),
+    TQS_CUDA(c->d_chain.ensure(chain_simt_scratch_bytes(c->n, ncols)), "tqs_circuit_unitary: cudaMalloc");
+    TQS_CUDA(chain_simt(c->d_factors.as<StepFactor>(), c->steps.data(), c->nsteps, c->n, col0, ncols,
+                        U, ldu, c->d_chain.p, s),
              "tqs_circuit_unitary: SIMT chain");
     return TQS_OK;
   }
-  TQS_CUDA(c->d_chain.ensure(chain_tc_scratch_bytes(c->n, prec)), "tqs_circuit_unitary: cudaMalloc");
+  TQS_CUDA(c->d_chain.ensure(chain_tc_scratch_bytes(c->n, prec, ncols)), "tqs_circuit_unitary: cudaMalloc");
   TQS_CUDA(c->d_err.ensure(sizeof(int)), "tqs_circuit_unitary: cudaMalloc");
   TQS_CUDA(cudaMemsetAsync(c->d_err.p, 0, sizeof(int), s), "tqs_circuit_unitary: memset");
-  TQS_CUDA(chain_tc(c->d_factors.as<StepFactor>(), c->steps.data(), c->nsteps, c->n, prec, U,
-                    c->d_chain.p, c->d_err.as<int>(), s),
+  TQS_CUDA(chain_tc(c->d_factors.as<StepFactor>(), c->steps.data(), c->nsteps, c->n, prec, col0, ncols,
+                    U, ldu, c->d_chain.p, c->d_err.as<int>(), s),
            "tqs_circuit_unitary: tensor-core chain");
   int err = 0;
   TQS_CUDA(cudaMemcpyAsync(&err, c->d_err.p, sizeof(int), cudaMemcpyDeviceToHost, s),
            "tqs_circuit_unitary: read status");
   TQS_CUDA(cudaStreamSynchronize(s), "tqs_circuit_unitary: sync");
-  if (err) return fail(TQS_ERR_TIMEOUT, "tqs_circuit_unitary: a device wait ran out");
+  if (err) return fail(TQS_ERR_TIMEOUT, "%s: a device wait ran out", who);
   return TQS_OK;
+}
+
+extern "C" {
+
+tqs_status tqs_circuit_unitary(tqs_circuit* c, int prec, tqs_c64* d_U, void* stream) {
+  if (c && c->n > TQS_MAX_DENSE_QUBITS)
+    return fail(TQS_ERR_TOO_MANY_QUBITS, "tqs_circuit_unitary: n %d > %d", c->n, TQS_MAX_DENSE_QUBITS);
+  const int N = c ? 1 << c->n : 1;
+  return unitary_block(c, prec, 0, N, d_U, N, stream, "tqs_circuit_unitary");
+}
+
+tqs_status tqs_circuit_unitary_cols(tqs_circuit* c, int prec, int col0, int ncols, tqs_c64* d_U,
+                                    int64_t ldu, void* stream) {
+  return unitary_block(c, prec, col0, ncols, d_U, ldu, stream, "tqs_circuit_unitary_cols");
 }
 
 }  // extern "C"
