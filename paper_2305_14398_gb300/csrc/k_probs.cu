@@ -93,7 +93,10 @@ cudaError_t launch_probs(const float2* d_state, int n, double* d_probs, uint64_t
 // not use the array's name as a device address: the address is looked up with
 // cudaGetSymbolAddress once per device, with that device current, and cached.
 // Each call overwrites all the partials it reads, so nothing needs clearing
-// between calls; calls that overlap on the GPU share the array and race.
+// between calls; calls that overlap on the GPU share the array and race.  The
+// cached address belongs to the device's primary context (the one the CUDA
+// runtime uses): it is not valid after cudaDeviceReset or in another context
+// made current on the same device.
 // ---------------------------------------------------------------------------
 constexpr int kStaticPartials = kMaxPartials;  // 1024 doubles = 8 KiB
 static __device__ __align__(256) double g_static_partials[kStaticPartials];
@@ -121,11 +124,9 @@ extern "C" tqs_status tqs_probabilities_noalloc(const tqs_c64* d_state, int n, d
     set_last_error("tqs_probabilities_noalloc: device buffers must be 16-byte aligned");
     return TQS_ERR_ARG;
   }
+  // probs_partial_count never exceeds kMaxPartials, which the array holds
+  static_assert(kStaticPartials >= kMaxPartials, "the fixed array holds every partial count");
   const int parts = probs_partial_count(n);
-  if (parts > kStaticPartials) {
-    set_last_error("tqs_probabilities_noalloc: needs more partial sums than the fixed 1024");
-    return TQS_ERR_TOO_MANY_QUBITS;
-  }
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess || dev < 0 || dev >= kMaxDevices) {

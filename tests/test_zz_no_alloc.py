@@ -61,3 +61,43 @@ def test_noalloc_sum_only_and_size_limit():
     with pytest.raises(B.TqsError) as e:
         B.tqs_probabilities_noalloc(d, 31, None, s)
     assert e.value.name == "TQS_ERR_TOO_MANY_QUBITS"
+
+
+def test_noalloc_calls_no_allocator():
+    """With a counting allocator installed (tqs_set_allocator routes every
+    library scratch allocation through it), the allocation-free entry point
+    never calls it, and the device's free memory does not change across the
+    calls (after one warm call, which may load the library's kernels)."""
+    counts = {"alloc": 0, "free": 0}
+
+    def alloc(n, stream):
+        counts["alloc"] += 1
+        return None  # refuse: a call that needed memory would fail
+
+    def free(p, stream):
+        counts["free"] += 1
+
+    inputs = []
+    for n in (1, 11, 20):
+        g = W.rng(71, n)
+        psi = (g.normal(size=1 << n) + 1j * g.normal(size=1 << n)).astype(np.complex64)
+        inputs.append((n, torch.from_numpy(psi).cuda(),
+                       torch.empty(1 << n, dtype=torch.float64, device="cuda"),
+                       torch.empty(1, dtype=torch.float64, device="cuda")))
+    B.tqs_probabilities_noalloc(inputs[0][1], inputs[0][0], inputs[0][2], inputs[0][3])
+    torch.cuda.synchronize()
+    B.tqs_set_allocator(alloc, free)
+    try:
+        free0 = torch.cuda.mem_get_info()[0]
+        for _ in range(2):
+            for n, d, p, s in inputs:
+                B.tqs_probabilities_noalloc(d, n, p, s)
+        torch.cuda.synchronize()
+        free1 = torch.cuda.mem_get_info()[0]
+    finally:
+        B.tqs_set_allocator()
+    assert counts == {"alloc": 0, "free": 0}
+    assert free1 == free0
+    for n, d, p, s in inputs:
+        x = d.cpu().numpy().astype(np.complex128)
+        assert abs(float(s.cpu()[0]) - float(np.sum(np.abs(x) ** 2))) <= 1e-12 * (1 << n)
