@@ -78,9 +78,11 @@ struct Prec<TQS_PREC_TC_TF32X3> {
 template <class E>
 struct GemmParams {
   int N;
-  int final_step;  // 1: write U = V'^T (complex64); 0: the 6 planes of V'
-  E* planes;       // [6][N][N] output planes (final_step == 0)
-  float2* u;       // [N][N] output (final_step == 1)
+  int M;           // rows of V and V' (columns of the U block): a multiple of BM, <= N
+  int final_step;  // 1: write the U block = V'^T (complex64); 0: the 6 planes of V'
+  E* planes;       // [6][M][N] output planes (final_step == 0)
+  float2* u;       // final_step == 1: U block, entry (r, j) at u[r * ldu + j], r < N, j < M
+  int64_t ldu;
   int* err;
 };
 
@@ -123,7 +125,7 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
   // Grouped raster: consecutive CTAs walk down a band of kGroupM tile rows
   // before moving right, so the CTAs resident at one time share a few A and B
   // panels in L2 instead of streaming all of B once per tile row.
-  const int num_m = P.N / BM, num_n = P.N / BN;
+  const int num_m = P.M / BM, num_n = P.N / BN;
   const int pid = blockIdx.x;
   const int band = pid / (kGroupM * num_n);
   const int first_m = band * kGroupM;
@@ -132,7 +134,7 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
   const int tile_m = (first_m + in_band % gsize) * BM;  // rows of V = rows of V'
   const int tile_n = (in_band / gsize) * BN;            // rows of S = columns of V'
   const int iters = (P.N / BK) * 3;                     // (k block, real GEMM j) pairs
-  (void)TQS_IX(tile_m, P.N - BM + 1);                   // whole tiles inside the N x N planes
+  (void)TQS_IX(tile_m, P.M - BM + 1);                   // whole tiles inside the M x N planes
   (void)TQS_IX(tile_n, P.N - BN + 1);
 
   if (threadIdx.x == 0) {
@@ -211,7 +213,8 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
     if (ok) {
       const uint32_t tl = tmem_base + (static_cast<uint32_t>(q * 32) << 16);
       const int gm = tile_m + row;
-      const size_t NN = static_cast<size_t>(P.N) * P.N;
+      const size_t PS = static_cast<size_t>(P.M) * P.N;  // plane stride
+      const size_t ulen = static_cast<size_t>(P.N - 1) * static_cast<size_t>(P.ldu) + P.M;
       for (int c0 = 0; c0 < BN; c0 += 32) {
         float t1[32], t2[32], t3[32];
         tmem_ld32(tl + 0 * BN + c0, t1);
@@ -224,7 +227,8 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
           for (int i = 0; i < 32; ++i) {
             const float re = t1[i] - t2[i];
             const float im = t3[i] - t1[i] - t2[i];
-            P.u[TQS_IX(static_cast<size_t>(tile_n + c0 + i) * P.N + gm, NN)] = make_float2(re, im);
+            P.u[TQS_IX(static_cast<size_t>(tile_n + c0 + i) * static_cast<size_t>(P.ldu) + gm, ulen)] =
+                make_float2(re, im);
           }
         } else {
           // in place: t1 <- Re, t2 <- Im, t3 <- Re + Im
@@ -235,11 +239,11 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
             t2[i] = c - a - b;
             t3[i] = t1[i] + t2[i];
           }
-          typename Prec<PREC>::E* rowp = P.planes + static_cast<size_t>(TQS_IX(gm, P.N)) * P.N +
+          typename Prec<PREC>::E* rowp = P.planes + static_cast<size_t>(TQS_IX(gm, P.M)) * P.N +
                                          TQS_IX(tile_n + c0, P.N - 31);
-          store_split<PREC, 32>(t1, rowp, rowp + NN);
-          store_split<PREC, 32>(t2, rowp + 2 * NN, rowp + 3 * NN);
-          store_split<PREC, 32>(t3, rowp + 4 * NN, rowp + 5 * NN);
+          store_split<PREC, 32>(t1, rowp, rowp + PS);
+          store_split<PREC, 32>(t2, rowp + 2 * PS, rowp + 3 * PS);
+          store_split<PREC, 32>(t3, rowp + 4 * PS, rowp + 5 * PS);
         }
       }
     }
@@ -254,23 +258,25 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
 
 // Operand planes of a step unitary: for each entry, Re, Im and Re + Im, each
 // split into hi + lo of the MMA input type.  transpose = 0: plane[r][c] =
-// S[r][c] (the B operand); transpose = 1: plane[c][r] = S[r][c] (the initial
-// V = S_1^T).  A thread produces 32 consecutive entries of one output row.
+// S[r][c] (the B operand, rows = N, row0 = 0); transpose = 1: plane[j][r] =
+// S[r][row0 + j] for j < rows (rows row0.. of the initial V = S_1^T: the
+// columns row0.. of S_1).  Planes are rows x N, `rows * N` entries apart.  A
+// thread produces 32 consecutive entries of one output row.
 constexpr int kGenThreads = 256;
 constexpr int kMaxFactors = 16;
 
 template <int PREC>
 __global__ void __launch_bounds__(kGenThreads)
     gen_planes_kernel(const StepFactor* __restrict__ factors, int nf, uint32_t idle, int n,
-                      int transpose, typename Prec<PREC>::E* __restrict__ planes) {
+                      int transpose, int row0, int rows, typename Prec<PREC>::E* __restrict__ planes) {
   __shared__ StepFactor fs[kMaxFactors];
   for (int i = threadIdx.x; i < nf * static_cast<int>(sizeof(StepFactor) / 8); i += blockDim.x)
     reinterpret_cast<float2*>(fs)[TQS_IX(i, int(sizeof(fs) / 8))] =
         reinterpret_cast<const float2*>(factors)[i];
   __syncthreads();
   const int64_t N = int64_t(1) << n;
-  const size_t NN = static_cast<size_t>(N) * N;
-  const int64_t chunks = (N * N) >> 5;
+  const size_t PS = static_cast<size_t>(rows) * N;  // plane stride
+  const int64_t chunks = static_cast<int64_t>(PS) >> 5;
   const int64_t stride = int64_t(gridDim.x) * blockDim.x;
   for (int64_t e = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; e < chunks; e += stride) {
     const int64_t flat = e << 5;
@@ -280,17 +286,17 @@ __global__ void __launch_bounds__(kGenThreads)
       float re[8], im[8], sm[8];
 #pragma unroll
       for (int i = 0; i < 8; ++i) {
-        const uint32_t r = transpose ? ocol + i0 + i : orow;
-        const uint32_t c = transpose ? orow : ocol + i0 + i;
+        const uint32_t r = transpose ? ocol + i0 + i : orow + row0;
+        const uint32_t c = transpose ? orow + row0 : ocol + i0 + i;
         const float2 z = step_entry(fs, nf, idle, r, c);
         re[i] = z.x;
         im[i] = z.y;
         sm[i] = z.x + z.y;
       }
-      typename Prec<PREC>::E* base = planes + TQS_IX(static_cast<size_t>(flat + i0), NN - 7);
-      store_split<PREC, 8>(re, base, base + NN);
-      store_split<PREC, 8>(im, base + 2 * NN, base + 3 * NN);
-      store_split<PREC, 8>(sm, base + 4 * NN, base + 5 * NN);
+      typename Prec<PREC>::E* base = planes + TQS_IX(static_cast<size_t>(flat + i0), PS - 7);
+      store_split<PREC, 8>(re, base, base + PS);
+      store_split<PREC, 8>(im, base + 2 * PS, base + 3 * PS);
+      store_split<PREC, 8>(sm, base + 4 * PS, base + 5 * PS);
     }
   }
 }
@@ -316,16 +322,16 @@ EncodeTiledFn encode_fn() {
   return fn;
 }
 
-// [6][N][N] planes as a 3-D tensor {k, row, plane}, box {one 128-byte row, 128
-// rows, 1 plane}, 128-byte swizzle.
+// [6][rows][N] planes as a 3-D tensor {k, row, plane}, box {one 128-byte row,
+// 128 rows, 1 plane}, 128-byte swizzle.
 template <int PREC>
-bool make_planes_map(CUtensorMap* m, void* base, int N) {
+bool make_planes_map(CUtensorMap* m, void* base, int N, int rows) {
   EncodeTiledFn fn = encode_fn();
   if (!fn) return false;
   const cuuint64_t es = sizeof(typename Prec<PREC>::E);
-  const cuuint64_t dims[3] = {static_cast<cuuint64_t>(N), static_cast<cuuint64_t>(N), 6};
+  const cuuint64_t dims[3] = {static_cast<cuuint64_t>(N), static_cast<cuuint64_t>(rows), 6};
   const cuuint64_t strides[2] = {static_cast<cuuint64_t>(N) * es,
-                                 static_cast<cuuint64_t>(N) * N * es};
+                                 static_cast<cuuint64_t>(rows) * N * es};
   const cuuint32_t box[3] = {static_cast<cuuint32_t>(Prec<PREC>::BK), BM, 1};
   const cuuint32_t estr[3] = {1, 1, 1};
   return fn(m, Prec<PREC>::kTmaType, 3, base, dims, strides, box, estr,
@@ -346,49 +352,52 @@ int sms() {
 
 template <int PREC>
 cudaError_t launch_gen(const StepFactor* d_factors, const StepDesc& st, int n, int transpose,
-                       typename Prec<PREC>::E* planes, cudaStream_t s) {
+                       int row0, int rows, typename Prec<PREC>::E* planes, cudaStream_t s) {
   if (st.f_count > kMaxFactors) return cudaErrorInvalidValue;
   const int64_t N = int64_t(1) << n;
-  int64_t blocks = ((N * N) / 32 + kGenThreads - 1) / kGenThreads;
+  int64_t blocks = ((int64_t(rows) * N) / 32 + kGenThreads - 1) / kGenThreads;
   const int64_t cap = int64_t(sms()) * 16;
   if (blocks > cap) blocks = cap;
   if (blocks < 1) blocks = 1;
   gen_planes_kernel<PREC><<<static_cast<int>(blocks), kGenThreads, 0, s>>>(
-      d_factors + st.f_begin, st.f_count, st.idle, n, transpose, planes);
+      d_factors + st.f_begin, st.f_count, st.idle, n, transpose, row0, rows, planes);
   count_launches(1);
   return cudaGetLastError();
 }
 
 template <int PREC>
 cudaError_t chain_tc_impl(const StepFactor* d_factors, const StepDesc* steps, int nsteps, int n,
-                          float2* d_U, void* scratch, int* d_err, cudaStream_t s) {
+                          int col0, int ncols, float2* d_U, int64_t ldu, void* scratch, int* d_err,
+                          cudaStream_t s) {
   using E = typename Prec<PREC>::E;
   const int N = 1 << n;
-  const size_t NN = size_t(N) * N;
+  const size_t MN = size_t(ncols) * N;  // the block's V planes: ncols rows of V
   E* V0 = static_cast<E*>(scratch);
-  E* V1 = V0 + 6 * NN;
-  E* S = V1 + 6 * NN;
+  E* V1 = V0 + 6 * MN;
+  E* S = V1 + 6 * MN;
   CUtensorMap mV0, mV1, mS;
-  if (!make_planes_map<PREC>(&mV0, V0, N) || !make_planes_map<PREC>(&mV1, V1, N) ||
-      !make_planes_map<PREC>(&mS, S, N))
+  if (!make_planes_map<PREC>(&mV0, V0, N, ncols) || !make_planes_map<PREC>(&mV1, V1, N, ncols) ||
+      !make_planes_map<PREC>(&mS, S, N, N))
     return cudaErrorNotSupported;
   cudaError_t e = cudaFuncSetAttribute(chain_gemm_kernel<PREC>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        static_cast<int>(kGemmSmem));
   if (e != cudaSuccess) return e;
-  e = launch_gen<PREC>(d_factors, steps[0], n, 1, V0, s);  // V = S_1^T
+  e = launch_gen<PREC>(d_factors, steps[0], n, 1, col0, ncols, V0, s);  // V = rows of S_1^T
   if (e != cudaSuccess) return e;
   bool cur0 = true;
   for (int k = 1; k < nsteps; ++k) {
-    e = launch_gen<PREC>(d_factors, steps[k], n, 0, S, s);
+    e = launch_gen<PREC>(d_factors, steps[k], n, 0, 0, N, S, s);
     if (e != cudaSuccess) return e;
     GemmParams<E> P;
     P.N = N;
+    P.M = ncols;
     P.final_step = (k == nsteps - 1) ? 1 : 0;
     P.planes = cur0 ? V1 : V0;
     P.u = d_U;
+    P.ldu = ldu;
     P.err = d_err;
-    const int grid = (N / BN) * (N / BM);
+    const int grid = (N / BN) * (ncols / BM);
     chain_gemm_kernel<PREC><<<grid, kGemmThreads, kGemmSmem, s>>>(cur0 ? mV0 : mV1, mS, P);
     count_launches(1);
     e = cudaGetLastError();
@@ -423,21 +432,28 @@ cudaError_t launch_wait_selftest(int* status, long long wait_cycles, cudaStream_
   return cudaGetLastError();
 }
 
-size_t chain_tc_scratch_bytes(int n, int prec) {
+size_t chain_tc_scratch_bytes(int n, int prec, int ncols) {
   const size_t N = size_t(1) << n;
   const size_t es = prec == TQS_PREC_TC_TF32X3 ? 4 : 2;
-  return 18 * N * N * es;  // V, V' and S: 6 planes each
+  return (12 * size_t(ncols) * N + 6 * N * N) * es;  // V and V' (ncols rows), S: 6 planes each
 }
 
-// U = S_m ... S_1 with the tensor-core chain in precision `prec`
-// (TQS_PREC_TC_BF16X3 or TQS_PREC_TC_TF32X3).  n >= 7 (N a multiple of 128).
+// Columns [col0, col0 + ncols) of U = S_m ... S_1 with the tensor-core chain
+// in precision `prec` (TQS_PREC_TC_BF16X3 or TQS_PREC_TC_TF32X3): the rows
+// col0.. of V = U^T, each step V <- V S_k^T, written as U[r][col0 + j] at
+// d_U[r * ldu + j].  n >= 7; col0 and ncols multiples of 128.
 cudaError_t chain_tc(const StepFactor* d_factors, const StepDesc* steps, int nsteps, int n,
-                     int prec, float2* d_U, void* scratch, int* d_err, cudaStream_t s) {
-  if (n < 7 || nsteps < 2) return cudaErrorInvalidValue;
+                     int prec, int col0, int ncols, float2* d_U, int64_t ldu, void* scratch,
+                     int* d_err, cudaStream_t s) {
+  if (n < 7 || nsteps < 2 || col0 % BM || ncols % BM || ncols < BM || col0 + ncols > (1 << n) ||
+      ldu < ncols)
+    return cudaErrorInvalidValue;
   if (prec == TQS_PREC_TC_BF16X3)
-    return chain_tc_impl<TQS_PREC_TC_BF16X3>(d_factors, steps, nsteps, n, d_U, scratch, d_err, s);
+    return chain_tc_impl<TQS_PREC_TC_BF16X3>(d_factors, steps, nsteps, n, col0, ncols, d_U, ldu,
+                                             scratch, d_err, s);
   if (prec == TQS_PREC_TC_TF32X3)
-    return chain_tc_impl<TQS_PREC_TC_TF32X3>(d_factors, steps, nsteps, n, d_U, scratch, d_err, s);
+    return chain_tc_impl<TQS_PREC_TC_TF32X3>(d_factors, steps, nsteps, n, col0, ncols, d_U, ldu,
+                                             scratch, d_err, s);
   return cudaErrorInvalidValue;
 }
 
