@@ -409,6 +409,13 @@ def run_tqs(args):
     }
     line["clocks"] = sampler.summary(t0, t1)
 
+    # ----------------------------------------------- measured peaks (rank 0)
+    mpeaks = {}
+    if rank == 0:
+        from paper_2305_14398_gb300 import peaks as _peaks
+        mpeaks = _peaks.measure(B, torch)
+        line["measured_peaks"] = mpeaks
+
     # ------------------------------------------------------- end to end
     if not args.no_e2e:
         bufs = [(torch.empty(total, dtype=torch.complex64).pin_memory(),
@@ -493,22 +500,31 @@ def run_tqs(args):
                              "speedup_vs_plain": (4 * reps1 / single_s) / plain_rate},
         }
 
+    if not args.no_plain and rank == 0:
+        line["plain"]["cublas_cgemv"] = bench_cublas_plain(B, W, torch)
+
     # ------------------------------------------------ collapse (sampling)
     if not args.no_sample and rank == 0:
         line["sample"] = bench_sample(B, torch, b, probs, count, total, flush, hbm_peak)
 
     # ------------------------------------- random batches (L2- and HBM-sized)
     if not args.no_batch and rank == 0:
-        sm_mhz = line["clocks"].get("sm_mhz") or 2070.0
-        line["batch"] = bench_batch(B, W, torch, peaks, flush, max(3, min(args.steps, 10)), sm_mhz)
+        line["batch"] = bench_batch(B, W, torch, peaks, flush, max(3, min(args.steps, 10)),
+                                    mpeaks["fp32_fma_tflops"])
 
     # ------------------------------------------ full state vector (large n)
     if not args.no_fsv and rank == 0:
-        line["fsv"] = bench_fsv(B, W, torch, hbm_peak, line["clocks"].get("sm_mhz") or 2070.0)
+        line["fsv"] = bench_fsv(B, W, torch, hbm_peak, mpeaks["fp32_fma_tflops"])
 
     # ------------------------------------------- circuit-unitary chain (a5)
     if not args.no_chain and rank == 0:
-        line["chain"] = bench_chain(B, W, torch, peaks)
+        line["chain"] = bench_chain(B, W, torch, peaks, mpeaks)
+        line["chain"]["cublas"] = bench_cublas_chain(B, W, torch)
+    # the column-sharded chain: every rank its own block of columns, no exchange
+    if not args.no_chain:
+        sh = bench_chain_sharded(B, W, torch, dist, rank, world, peaks)
+        if rank == 0:
+            line["chain_sharded"] = sh
 
     # ----------------------------------------------------- serving loop (a8)
     if not args.no_serving and rank == 0:
@@ -636,13 +652,7 @@ def algorithmic_flops(n, ops):
     return float(1 << n) * sum(_GATE_FLOPS[name] for name, _, _ in ops)
 
 
-def fp32_peak_tflops(sm_mhz):
-    """FP32 FMA peak derived from unit counts and the SM clock: 152 SMs x 128
-    FP32 lanes x 2 flops per FMA."""
-    return 152 * 128 * 2 * sm_mhz * 1e6 / 1e12
-
-
-def bench_batch(B, W, torch, peaks, flush, reps, sm_mhz):
+def bench_batch(B, W, torch, peaks, flush, reps, fp32_peak):
     """The batched persistent launch on random mixed circuits: 4096 circuits of
     n = 4..14 (log-uniform, depth U{5..40}; states L2-resident) and 4096
     circuits all at n = 14 (1.5 GiB of outputs, streamed through HBM).  Each
@@ -680,10 +690,10 @@ def bench_batch(B, W, torch, peaks, flush, reps, sm_mhz):
             "hbm": {"achieved_gbs": alg_bytes / sec / 1e9, "peak": hbm,
                     "frac": alg_bytes / sec / 1e9 / hbm, "algorithmic_bytes": alg_bytes},
             "alu": {"achieved_tflops": flops / sec / 1e12,
-                    "peak": fp32_peak_tflops(sm_mhz),
-                    "frac": flops / sec / 1e12 / fp32_peak_tflops(sm_mhz),
+                    "peak": fp32_peak,
+                    "frac": flops / sec / 1e12 / fp32_peak,
                     "algorithmic_flops": flops,
-                    "peak_source": f"derived: 152 SMs x 128 FP32 lanes x 2 x {sm_mhz:.0f} MHz"},
+                    "peak_source": "measured FP32 FMA microkernel (measured_peaks)"},
             "norm_max_err": float((norms.cpu() - 1.0).abs().max()),
         }
         B.tqs_batch_destroy(b)
@@ -692,7 +702,7 @@ def bench_batch(B, W, torch, peaks, flush, reps, sm_mhz):
     return out
 
 
-def bench_fsv(B, W, torch, hbm_peak, sm_mhz):
+def bench_fsv(B, W, torch, hbm_peak, fp32_peak):
     """Full-state-vector backend on states in HBM: random layered circuits
     (10 x (U3 on every qubit + CNOTs on n/2 seeded pairs)) at n = 24, 28, 30.
     Each pass streams the state once (read + write): 16 * 2^n algorithmic
@@ -721,8 +731,8 @@ def bench_fsv(B, W, torch, hbm_peak, sm_mhz):
                         "gates_per_s": len(ops) / sec,
                         "hbm": {"achieved_gbs": alg / sec / 1e9, "peak": hbm_peak,
                                 "frac": alg / sec / 1e9 / hbm_peak, "algorithmic_bytes": alg},
-                        "alu": {"achieved_tflops": flops / sec / 1e12, "peak": fp32_peak_tflops(sm_mhz),
-                                "frac": flops / sec / 1e12 / fp32_peak_tflops(sm_mhz),
+                        "alu": {"achieved_tflops": flops / sec / 1e12, "peak": fp32_peak,
+                                "frac": flops / sec / 1e12 / fp32_peak,
                                 "algorithmic_flops": flops}}
         B.tqs_circuit_destroy(c)
         del st
@@ -790,7 +800,7 @@ def bench_fsv(B, W, torch, hbm_peak, sm_mhz):
     return out
 
 
-def bench_chain(B, W, torch, peaks):
+def bench_chain(B, W, torch, peaks, mpeaks):
     """Algorithm 1 on the random layered circuits (20 layers, 40 steps) at
     n = 12, 13, 14: tensor-core BF16x3 chain (and FP32 SIMT at n = 12), with the
     error of sampled columns against the FP64 oracle at n = 12."""
@@ -798,9 +808,11 @@ def bench_chain(B, W, torch, peaks):
     from oracle import fsv_route
 
     peak = peaks.get("bf16_tflops", 1927.5)
+    tf32 = mpeaks.get("tf32_tflops")
     out = {"workload": "random layered: 20 x (U3 on every qubit + CNOTs on n/2 seeded pairs), "
                        "40 steps, U = S_40 ... S_1",
-           "tensor_peak_tflops": peak, "peak_source": "measured bf16 burst"}
+           "tensor_peak_tflops": peak, "peak_source": "measured bf16 burst",
+           "tf32_peak_tflops": tf32, "tf32_peak_source": "measured TF32 cuBLAS burst (measured_peaks)"}
     names = {B.PREC_TC_BF16X3: "tc_bf16x3", B.PREC_TC_TF32X3: "tc_tf32x3",
              B.PREC_FP32_SIMT: "fp32_simt"}
     for n, prec, reps in [(12, B.PREC_TC_BF16X3, 3), (12, B.PREC_TC_TF32X3, 2),
@@ -826,8 +838,7 @@ def bench_chain(B, W, torch, peaks):
         if prec != B.PREC_FP32_SIMT:
             issued = 18.0 * N ** 3 * gemms / sec / 1e12  # 3 real GEMMs x 3 split products
             rec["issued_tensor_tflops"] = issued
-            # TF32 MMAs run at half the BF16 rate (nominal ratio 1.1 / 2.25 dense)
-            own_peak = peak if prec == B.PREC_TC_BF16X3 else peak * 1.1 / 2.25
+            own_peak = peak if prec == B.PREC_TC_BF16X3 else tf32
             rec["tensor_peak_tflops"] = own_peak
             rec["tensor_frac"] = issued / own_peak
         if n == 12:
@@ -839,6 +850,234 @@ def bench_chain(B, W, torch, peaks):
         del U
         torch.cuda.empty_cache()
     return out
+
+
+# ------------------------------------------------- cuBLAS reference points
+
+def _cublas():
+    """ctypes handle of the cuBLAS library torch has loaded (found in the
+    process's mappings after a torch GEMM), or None."""
+    import ctypes
+    path = None
+    try:
+        with open("/proc/self/maps") as f:
+            for ln in f:
+                if "libcublas.so" in ln and "libcublasLt" not in ln:
+                    path = ln.split()[-1]
+                    break
+    except OSError:
+        return None
+    if path is None:
+        return None
+    L = ctypes.CDLL(path)
+    vp, i = ctypes.c_void_p, ctypes.c_int
+    L.cublasSetStream_v2.argtypes = [vp, vp]
+    L.cublasCgemm3m.argtypes = [vp, i, i, i, i, i, vp, vp, i, vp, i, vp, vp, i]
+    L.cublasCgemv_v2.argtypes = [vp, i, i, i, vp, vp, i, vp, i, vp, vp, i]
+    return L
+
+
+def cublas_gemm3m(L, torch, S, U, out):
+    """out = S @ U (row-major complex64, N x N) by cublasCgemm3m: in column-major
+    terms out^T = U^T S^T."""
+    import ctypes
+    import numpy as np
+    N = S.shape[0]
+    h = ctypes.c_void_p(torch.cuda.current_blas_handle())
+    L.cublasSetStream_v2(h, ctypes.c_void_p(torch.cuda.current_stream().cuda_stream))
+    one = np.array([1.0, 0.0], dtype=np.float32)
+    zero = np.array([0.0, 0.0], dtype=np.float32)
+    st = L.cublasCgemm3m(h, 0, 0, N, N, N, one.ctypes.data, ctypes.c_void_p(U.data_ptr()), N,
+                         ctypes.c_void_p(S.data_ptr()), N, zero.ctypes.data,
+                         ctypes.c_void_p(out.data_ptr()), N)
+    if st != 0:
+        raise RuntimeError(f"cublasCgemm3m status {st}")
+
+
+def cublas_gemv(L, torch, S, x, y):
+    """y = S x (row-major complex64 S, N x N) by cublasCgemv: column-major S^T,
+    transposed."""
+    import ctypes
+    import numpy as np
+    N = S.shape[0]
+    h = ctypes.c_void_p(torch.cuda.current_blas_handle())
+    L.cublasSetStream_v2(h, ctypes.c_void_p(torch.cuda.current_stream().cuda_stream))
+    one = np.array([1.0, 0.0], dtype=np.float32)
+    zero = np.array([0.0, 0.0], dtype=np.float32)
+    st = L.cublasCgemv_v2(h, 1, N, N, one.ctypes.data, ctypes.c_void_p(S.data_ptr()), N,
+                          ctypes.c_void_p(x.data_ptr()), 1, zero.ctypes.data,
+                          ctypes.c_void_p(y.data_ptr()), 1)
+    if st != 0:
+        raise RuntimeError(f"cublasCgemv status {st}")
+
+
+def bench_cublas_plain(B, W, torch, n=11, reps=3):
+    """Library yardstick for the plain form: cuBLAS cgemv on the same
+    materialised step matrices S_k as matvec_kernel, one circuit of each paper
+    kind.  Three timings per circuit, each a back-to-back run of all its steps:
+    the library's materialisation alone (tqs_materialize_step), materialise +
+    cuBLAS cgemv per step, and the library's plain form (tqs_simulate_plain:
+    materialise + matvec_kernel per step); the mat-vecs' own times follow by
+    difference."""
+    import numpy as np
+    from oracle import fsv_route
+    torch.matmul(torch.ones(8, 8, device="cuda"), torch.ones(8, 8, device="cuda"))  # cuBLAS loaded
+    L = _cublas()
+    if L is None:
+        return {"unavailable": "libcublas not found in the process"}
+    N = 1 << n
+    S = torch.empty((N, N), dtype=torch.complex64, device="cuda")
+    x = torch.zeros(N, dtype=torch.complex64, device="cuda")
+    y = torch.empty(N, dtype=torch.complex64, device="cuda")
+    out = torch.empty(N, dtype=torch.complex64, device="cuda")
+    t = {"mat": 0.0, "mat_cgemv": 0.0, "plain": 0.0}
+    steps_all = 0
+    err = 0.0
+    for _, ops in W.paper_mix(n, 4, seed_tag=1):
+        c = B.circuit_from_ops(n, ops)
+        try:
+            steps = B.tqs_circuit_info(c)[2]
+
+            def run(kind):
+                nonlocal x, y
+                if kind == "plain":
+                    B.tqs_simulate_plain(c, out)
+                    return
+                x.zero_()
+                x[0] = 1.0
+                for k in range(steps):
+                    B.tqs_materialize_step(c, k, S)
+                    if kind == "mat_cgemv":
+                        cublas_gemv(L, torch, S, x, y)
+                        x, y = y, x
+            for kind in t:
+                run(kind)
+                torch.cuda.synchronize()
+                s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                s0.record()
+                for _ in range(reps):
+                    run(kind)
+                s1.record()
+                torch.cuda.synchronize()
+                t[kind] += s0.elapsed_time(s1) / 1e3 / reps
+            run("mat_cgemv")
+            torch.cuda.synchronize()
+            err = max(err, float(np.max(np.abs(x.cpu().numpy().astype(np.complex128)
+                                              - fsv_route.simulate(n, ops)))))
+            steps_all += steps
+        finally:
+            B.tqs_circuit_destroy(c)
+    mv_lib = t["mat_cgemv"] - t["mat"]
+    mv_ours = t["plain"] - t["mat"]
+    return {"what": "cuBLAS cgemv (cublasCgemv) on the same materialised S_k; baseline only",
+            "steps": steps_all,
+            "materialize_us_per_step": 1e6 * t["mat"] / steps_all,
+            "materialize_plus_cgemv_us_per_step": 1e6 * t["mat_cgemv"] / steps_all,
+            "plain_form_us_per_step": 1e6 * t["plain"] / steps_all,
+            "cgemv_us_per_step_derived": 1e6 * mv_lib / steps_all,
+            "matvec_kernel_us_per_step_derived": 1e6 * mv_ours / steps_all,
+            "cgemv_gbs_algorithmic": 8.0 * N * N * steps_all / mv_lib / 1e9 if mv_lib > 0 else None,
+            "matvec_kernel_gbs_algorithmic": 8.0 * N * N * steps_all / mv_ours / 1e9 if mv_ours > 0 else None,
+            "note": "S_k is read right after it is written (32 MiB, L2-resident) in both forms",
+            "max_abs_err_vs_oracle": err}
+
+
+def bench_cublas_chain(B, W, torch):
+    """Library yardsticks for the chain (Algorithm 1, U <- S_k U): cuBLAS
+    cgemm (torch.matmul complex64, FP32) and cgemm3m (ctypes) on the same step
+    matrices (materialised by tqs_materialize_step) at n = 12 (whole chain,
+    error against the oracle's columns) and n = 13, 14 (one product timed,
+    times the chain's product count)."""
+    import numpy as np
+    from oracle import fsv_route
+    L = _cublas()
+    out = {"what": "cuBLAS complex64 GEMM chain on the same S_k; baseline only (never the hot path)"}
+    for n in (12, 13, 14):
+        N = 1 << n
+        ops = W.random_layered(n, 20, (2, n))
+        c = B.circuit_from_ops(n, ops)
+        try:
+            steps = B.tqs_circuit_info(c)[2]
+            S = torch.empty((N, N), dtype=torch.complex64, device="cuda")
+            U = torch.empty((N, N), dtype=torch.complex64, device="cuda")
+            V = torch.empty((N, N), dtype=torch.complex64, device="cuda")
+            for name in ("cgemm", "cgemm3m"):
+                if name == "cgemm3m" and L is None:
+                    out[f"n{n}_cublas_cgemm3m"] = {"unavailable": "libcublas not found in the process"}
+                    continue
+                full = n == 12
+                ks = range(1, steps) if full else [1]
+                B.tqs_materialize_step(c, 0, U)
+                t = 0.0
+                for k in ks:
+                    B.tqs_materialize_step(c, k, S)
+                    torch.cuda.synchronize()
+                    s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                    s0.record()
+                    if name == "cgemm":
+                        torch.matmul(S, U, out=V)
+                    else:
+                        cublas_gemm3m(L, torch, S, U, V)
+                    s1.record()
+                    torch.cuda.synchronize()
+                    t += s0.elapsed_time(s1) / 1e3
+                    U, V = V, U
+                per = t / len(ks)
+                rec = {"ms_per_product": 1e3 * per, "chain_ms": 1e3 * per * (steps - 1),
+                       "chain_ms_source": "timed" if full else "one product x (steps - 1)",
+                       "useful_complex_tflops": 8.0 * N ** 3 / per / 1e12}
+                if full:
+                    cols = [0, 1, 777, 2048, 4095]
+                    got = U[:, cols].cpu().numpy().astype(np.complex128)
+                    rec["max_abs_err_vs_oracle"] = float(np.max(np.abs(
+                        got - fsv_route.unitary_columns(n, ops, cols))))
+                out[f"n{n}_cublas_{name}"] = rec
+            del S, U, V
+            torch.cuda.empty_cache()
+        finally:
+            B.tqs_circuit_destroy(c)
+    return out
+
+
+def bench_chain_sharded(B, W, torch, dist, rank, world, peaks, n=13, reps=2):
+    """The column-sharded circuit-unitary chain (Algorithm 1 by column blocks):
+    rank r computes U[:, block r] of the 40-step random layered chain at n = 13
+    (BF16x3 tensor cores) with tqs_circuit_unitary_cols, generating every step
+    unitary itself; no data is exchanged (only the timing: max over ranks).
+    At one rank the block is the whole unitary."""
+    from paper_2305_14398_gb300 import shard
+
+    col0, ncols = shard.rank_block(n, rank, world)
+    N = 1 << n
+    ops = W.random_layered(n, 20, (2, n))
+    c = B.circuit_from_ops(n, ops)
+    sec = 0.0
+    try:
+        if ncols > 0:
+            blk = torch.empty((N, ncols), dtype=torch.complex64, device="cuda")
+            B.tqs_circuit_unitary_cols(c, B.PREC_TC_BF16X3, col0, ncols, blk)
+        torch.cuda.synchronize()
+        if dist:
+            dist.barrier()
+        s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        s.record()
+        for _ in range(reps):
+            if ncols > 0:
+                B.tqs_circuit_unitary_cols(c, B.PREC_TC_BF16X3, col0, ncols, blk)
+        e.record()
+        torch.cuda.synchronize()
+        sec = s.elapsed_time(e) / 1e3 / reps
+        gemms = B.tqs_circuit_info(c)[2] - 1
+    finally:
+        B.tqs_circuit_destroy(c)
+    slowest = max_over_ranks(sec, dist, "cuda")
+    useful = 8.0 * N * N * N * gemms  # complex MACs of all ranks' blocks together
+    return {"workload": f"random layered n = {n}, 40 steps, BF16x3; rank r computes columns "
+                        "shard.rank_block(n, r, world); no exchange",
+            "ranks": world, "ms": 1e3 * slowest, "columns_per_rank": ncols,
+            "useful_complex_gflops_whole_job": useful / slowest / 1e9 if slowest > 0 else None,
+            "issued_tensor_tflops_whole_job": 18.0 * N ** 3 * gemms / slowest / 1e12 if slowest > 0 else None,
+            "tensor_peak_tflops_per_gpu": peaks.get("bf16_tflops", 1927.5)}
 
 
 def main():
