@@ -174,15 +174,19 @@ tqs_status tqs_circuit_steps(const tqs_circuit* c, int* h_step_of_gate);
  *               c, 52 far target, 53 both local (fields t, c).  fbit: far
  *               control bit (255 none); tbit: far target bit; act: active-pair
  *               mask over the 16 local indices; d0one: d0 == 1 exactly.
- *   h_pos    : NULL or 16 bytes, the physical bit of each logical qubit at
- *              the end (SWAP factors are relabelings).
+ *   h_map    : NULL or 17 uint16, the output map: logical index y of the
+ *              result is the program's physical index h_map[16] ^ (XOR of
+ *              h_map[q] over the set bits q of y), an affine map over GF(2)
+ *              (SWAP factors relabel qubits; the trailing permutation gates
+ *              X, CNOT, SWAP with no later other gate on their qubits are
+ *              folded into it instead of being applied).
  *   h_out_scale : NULL or 1 float, the factor applied to the output state.
  *   h_gen_index : NULL or 1 int, the basis state the program starts from
  *              (leading X gates on untouched qubits are folded into it; the
  *              program for a given input state folds nothing).
  * Host memory only; no device work. */
 tqs_status tqs_circuit_program(tqs_circuit* c, int* n_passes, int* n_ops, void* h_passes,
-                               void* h_ops, uint8_t* h_pos, float* h_out_scale,
+                               void* h_ops, uint16_t* h_map, float* h_out_scale,
                                int* h_gen_index);
 
 /* ---------------------------------------------------------------- simulate

@@ -210,13 +210,15 @@ OP_DTYPE = np.dtype([("code", np.uint8), ("t", np.uint8), ("c", np.uint8), ("tbi
 
 
 def tqs_circuit_program(c: int):
-    """(passes, ops, pos, out_scale, gen_index) of the compiled fused program."""
+    """(passes, ops, out_map, out_scale, gen_index) of the compiled fused
+    program; out_map: 17 uint16, the columns of the output map and its
+    offset (see include/tqs.h)."""
     npass, nops = ctypes.c_int(), ctypes.c_int()
     _check(lib().tqs_circuit_program(c, ctypes.byref(npass), ctypes.byref(nops), None, None, None,
                                      None, None))
     passes = np.zeros(npass.value, dtype=PASS_DTYPE)
     ops = np.zeros(nops.value, dtype=OP_DTYPE)
-    pos = np.zeros(16, dtype=np.uint8)
+    pos = np.zeros(17, dtype=np.uint16)
     osc = ctypes.c_float()
     gen = ctypes.c_int()
     _check(lib().tqs_circuit_program(c, None, None, passes.ctypes.data, ops.ctypes.data,

@@ -51,8 +51,8 @@ static tqs_status batch_finish(tqs_batch* b, const std::vector<CircMeta>& progs,
     fc.out_off = b->offsets[i];
     fc.op_begin = static_cast<int32_t>(o0);
     fc.op_count = static_cast<int32_t>(m.no);
-    fc.identity = m.identity;
-    std::memcpy(fc.pos, m.pos, 16);
+    fc.col_off = m.col_off;
+    std::memcpy(fc.col, m.col, sizeof(fc.col));
     fc.init = nullptr;
     fc.out_scale = m.out_scale;
     fc.gen_index = m.gen_index;

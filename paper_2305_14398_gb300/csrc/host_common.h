@@ -250,8 +250,8 @@ struct Program {
   int n = 0, nint = 4;
   std::vector<FusedPass> passes;
   std::vector<FusedOp> ops;
-  uint8_t pos[16];
-  int identity = 1;
+  uint16_t col[16];       // output map (FusedCirc)
+  uint16_t col_off = 0;
   float out_scale = 1.0f;
   int gen_index = 0;  // basis state the program starts from (leading X gates folded)
   int n_instr = 0;    // measure / reset instructions (one pass each)
@@ -264,7 +264,7 @@ struct Program {
     coef.clear();
     n = 0;
     nint = 4;
-    identity = 1;
+    col_off = 0;
     out_scale = 1.0f;
     gen_index = 0;
     n_instr = 0;
@@ -308,8 +308,10 @@ constexpr int kMaxHPerPass = 48;
 // (the mixed-product property of the Kronecker product: consecutive steps'
 // factors on one qubit compose).  The result does not depend on the other
 // circuits of a batch.
+// absorb: fold the trailing permutation gates into the output map (not in
+// the full-state-vector tile programs, whose write-back is the tile's own).
 void compile_program(int n, const std::vector<const Gate*>& gs_in, Program& P,
-                     bool fold_x = true);
+                     bool fold_x = true, bool absorb = true);
 
 inline int team_for(int nint) {
   if (nint <= kWarpMaxQ) return TEAM_WARP;
@@ -403,10 +405,11 @@ struct ImageSeg {
 // its header fields and its passes / ops / coefficients at local offsets of
 // segment `seg` (passes still numbered program-locally).
 struct CircMeta {
-  int n = 0, nint = 4, n_instr = 0, identity = 1, gen_index = 0;
+  int n = 0, nint = 4, n_instr = 0, gen_index = 0;
   float out_scale = 1.0f;
   double cost = 0.0;
-  uint8_t pos[16] = {};
+  uint16_t col[16] = {};
+  uint16_t col_off = 0;
   int seg = 0;
   size_t lp = 0, np = 0, lo = 0, no = 0, lc = 0, nc = 0;
 };
@@ -418,11 +421,11 @@ inline CircMeta append_program(const Program& P, ImageSeg& sg, int seg) {
   m.n = P.n;
   m.nint = P.nint;
   m.n_instr = P.n_instr;
-  m.identity = P.identity;
+  m.col_off = P.col_off;
   m.gen_index = P.gen_index;
   m.out_scale = P.out_scale;
   m.cost = P.cost;
-  std::memcpy(m.pos, P.pos, 16);
+  std::memcpy(m.col, P.col, sizeof(m.col));
   m.seg = seg;
   m.lp = sg.passes.size();
   m.np = P.passes.size();
@@ -541,8 +544,8 @@ struct Image {
     fc.out_off = out_off;
     fc.op_begin = static_cast<int32_t>(op0);
     fc.op_count = static_cast<int32_t>(P.ops.size());
-    fc.identity = P.identity;
-    std::memcpy(fc.pos, P.pos, 16);
+    fc.col_off = P.col_off;
+    std::memcpy(fc.col, P.col, sizeof(fc.col));
     fc.init = nullptr;
     fc.out_scale = P.out_scale;
     fc.gen_index = P.gen_index;

@@ -5,8 +5,203 @@
 
 namespace tqs {
 
+namespace {
+
+// A unit-modulus phase z in FP32: of the four pairs that round z's parts
+// down or up, the one whose squared modulus is nearest 1 (ties: nearest z).
+// Every amplitude a phase multiplies shares its modulus error, so this error,
+// unlike the rounding of the products, adds up over a circuit's phases in the
+// norm; choosing the pair keeps it to about a quarter of plain rounding.
+// Other values (not of modulus 1 to 1e-12) round to nearest.
+float2 to_unit_f2(cd z) {
+  const float2 rn = to_f2(z);
+  if (std::abs(std::abs(z) - 1.0) > 1e-12) return rn;
+  // the FP32 values just below and just above each part (equal when exact)
+  auto bracket = [](double v, float r, float& lo, float& hi) {
+    lo = hi = r;
+    if (double(r) < v) hi = std::nextafter(r, INFINITY);
+    if (double(r) > v) lo = std::nextafter(r, -INFINITY);
+  };
+  float xs[2], ys[2];
+  bracket(z.real(), rn.x, xs[0], xs[1]);
+  bracket(z.imag(), rn.y, ys[0], ys[1]);
+  float2 best = rn;
+  double best_m = std::abs(double(rn.x) * rn.x + double(rn.y) * rn.y - 1.0);
+  double best_d = std::abs(cd(rn.x, rn.y) - z);
+  for (int i = 0; i < 4; ++i) {
+    const float x = xs[i & 1], y = ys[i >> 1];
+    const double m = std::abs(double(x) * x + double(y) * y - 1.0);
+    const double d = std::abs(cd(x, y) - z);
+    if (m < best_m || (m == best_m && d < best_d)) {
+      best = make_float2(x, y);
+      best_m = m;
+      best_d = d;
+    }
+  }
+  return best;
+}
+
+// One phase factor of a merged diagonal op: multiply the amplitudes with local
+// position `tgt` set (tgt 4: the whole group) by v when the group's physical
+// bit f is 1 (f 0xFF: always).
+struct DiagEnt {
+  int tgt;
+  uint8_t f;
+  float2 v;
+};
+
+// The phase factors of a diagonal op whose action is such a product (every
+// diagonal op except a local-local one and a far target under a far
+// control), or 0.  diag(d0, d1) = d0 diag(1, d1 / d0): with d0 exactly 1 one
+// factor, else two.
+int diag_entries(const FusedOp& op, DiagEnt* e) {
+  const int code = op.code;
+  const bool one = op.d0one != 0;
+  const float2 d0 = op.m[0], d1 = op.m[1], r = op.m[2];
+  if (code >= OPC_DLN && code < OPC_DLF) {  // local target, uncontrolled
+    const int t = code - OPC_DLN;
+    if (one) { e[0] = {t, 0xFF, r}; return 1; }
+    e[0] = {4, 0xFF, d0};
+    e[1] = {t, 0xFF, r};
+    return 2;
+  }
+  if (code >= OPC_DLF && code < OPC_DFL) {  // local target, far control
+    const int t = code - OPC_DLF;
+    if (one) { e[0] = {t, op.fbit, r}; return 1; }
+    e[0] = {4, op.fbit, d0};
+    e[1] = {t, op.fbit, r};
+    return 2;
+  }
+  if (code >= OPC_DFL && code < OPC_DFF) {  // far target, local control c
+    const int c = code - OPC_DFL;
+    if (one) { e[0] = {c, op.tbit, d1}; return 1; }
+    e[0] = {c, 0xFF, d0};
+    e[1] = {c, op.tbit, r};
+    return 2;
+  }
+  if (code == OPC_DFF && op.fbit == 0xFF) {  // far target, uncontrolled
+    if (one) { e[0] = {4, op.tbit, d1}; return 1; }
+    e[0] = {4, 0xFF, d0};
+    e[1] = {4, op.tbit, r};
+    return 2;
+  }
+  return 0;
+}
+
+// u = diag(alpha, gamma) H diag(1, beta) with alpha, beta, gamma in
+// {1, -1, i, -i}: true when u has that form (to 1e-14); d2 = diag(1, beta)
+// acts first, then H, then d1.
+bool hadamard_split(const Mat2& u, Mat2& d2, Mat2& d1) {
+  const double s = 1.0 / std::sqrt(2.0);
+  for (int i = 0; i < 4; ++i)
+    if (std::abs(std::abs(u.m[i]) - s) > 1e-14) return false;
+  // only phases that FP32 holds exactly (1, -1, i, -i): multiplying by them
+  // is exact, so the split keeps the amplitudes' norm as the dense form does
+  auto snap = [](cd z, cd& out) {
+    const double re = std::round(z.real()), im = std::round(z.imag());
+    if (std::abs(z - cd(re, im)) > 1e-14 || std::abs(re) + std::abs(im) != 1.0) return false;
+    out = cd(re, im);
+    return true;
+  };
+  cd alpha, gamma, beta;
+  if (!snap(u.m[0] / s, alpha) || !snap(u.m[2] / s, gamma) || !snap(u.m[1] / u.m[0], beta)) return false;
+  if (std::abs(s * alpha * beta - u.m[1]) > 1e-14 || std::abs(-s * gamma * beta - u.m[3]) > 1e-14)
+    return false;
+  d2 = {{1.0, 0.0, 0.0, beta}};
+  d1 = {{alpha, 0.0, 0.0, gamma}};
+  return true;
+}
+
+// Local target position of a non-diagonal op.
+int nondiag_target(int code) {
+  if (code >= OPC_XL && code < OPC_ANTI) return (code - OPC_XL) >> 2;
+  return code & 3;
+}
+
+// Merge the pass's phase factors (ops [begin, end)) into OPC_DLIST ops of up
+// to 8 factors per target.  The kernel only accumulates such factors (per
+// local position, or for the group) and multiplies them in before the next
+// non-diagonal op on that position or at the end of the pass, so factors on
+// one position between two non-diagonal ops on it commute with everything in
+// between: each list is emitted just before the next non-diagonal op on its
+// position (or at the end of the pass).
+void merge_diagonals(std::vector<FusedOp>& ops, size_t begin) {
+  static thread_local std::vector<FusedOp> out;
+  out.clear();
+  DiagEnt open[5][8];
+  int nopen[5] = {0, 0, 0, 0, 0};
+  auto flush = [&](int t) {
+    if (nopen[t] == 0) return;
+    if (nopen[t] == 1 && (t < 4 || open[t][0].f != 0xFF)) {
+      // one factor: the single diagonal op with d0 exactly 1 that does the
+      // same (header only, no factor list to load)
+      const DiagEnt& e = open[t][0];
+      FusedOp op{};
+      op.d0one = 1;
+      op.act = 0xFFFF;
+      op.tbit = 0xFF;
+      op.fbit = 0xFF;
+      op.m[0] = make_float2(1.f, 0.f);
+      op.m[1] = e.v;
+      op.m[2] = e.v;
+      op.hc = e.v;
+      if (t == 4) {
+        op.code = OPC_DFF;
+        op.tbit = e.f;
+      } else if (e.f == 0xFF) {
+        op.code = static_cast<uint8_t>(OPC_DLN + t);
+      } else {
+        op.code = static_cast<uint8_t>(OPC_DLF + t);
+        op.fbit = e.f;
+      }
+      out.push_back(op);
+      nopen[t] = 0;
+      return;
+    }
+    FusedOp op{};
+    op.code = OPC_DLIST;
+    op.t = static_cast<uint8_t>(t);
+    op.c = static_cast<uint8_t>(nopen[t]);
+    op.tbit = 0xFF;
+    op.fbit = 0xFF;
+    op.act = 0xFFFF;
+    uint8_t fb[8];
+    float2 v[8];
+    for (int k = 0; k < 8; ++k) {
+      fb[k] = k < nopen[t] ? open[t][k].f : 0xFF;
+      v[k] = k < nopen[t] ? open[t][k].v : make_float2(1.f, 0.f);
+    }
+    std::memcpy(&op.hc, fb, 8);
+    for (int k = 0; k < 4; ++k) {
+      op.m[k] = v[k];
+      op.lo[k] = v[4 + k];
+    }
+    out.push_back(op);
+    nopen[t] = 0;
+  };
+  for (size_t i = begin; i < ops.size(); ++i) {
+    const FusedOp& op = ops[i];
+    DiagEnt es[2];
+    const int ne = diag_entries(op, es);
+    if (ne > 0) {
+      for (int k = 0; k < ne; ++k) {
+        if (nopen[es[k].tgt] == 8) flush(es[k].tgt);
+        open[es[k].tgt][nopen[es[k].tgt]++] = es[k];
+      }
+      continue;
+    }
+    if (op.code < OPC_DLN) flush(nondiag_target(op.code));
+    out.push_back(op);
+  }
+  for (int t = 0; t < 5; ++t) flush(t);
+  ops.resize(begin);
+  ops.insert(ops.end(), out.begin(), out.end());
+}
+
+}  // namespace
+
 void compile_program(int n, const std::vector<const Gate*>& gs_in, Program& P,
-                      bool fold_x) {
+                      bool fold_x, bool absorb) {
   P.n = n;
   P.nint = std::max(n, 4);
   // Leading uncontrolled X factors on a qubit that nothing has touched yet act
@@ -31,6 +226,35 @@ void compile_program(int n, const std::vector<const Gate*>& gs_in, Program& P,
       touched |= qubit_mask(*g);
       gs.push_back(g);
     }
+  }
+  // Trailing permutation gates: an X, CNOT or SWAP with no later gate of
+  // another kind on its qubits only permutes the final amplitudes, psi(y) =
+  // phi(F(y)) with F an affine map over GF(2) (X: y ^ e_q; CNOT(c, t):
+  // y ^ y_c e_t; SWAP: exchange two bits; each its own inverse).  Such gates
+  // are taken out of the program and F goes into the output map.  Gates of
+  // one step act on disjoint qubits, so the scan in step order is the
+  // circuit's own order up to commuting gates.
+  static thread_local std::vector<const Gate*> tail_tls;
+  std::vector<const Gate*>& tail = tail_tls;
+  tail.clear();
+  if (absorb) {
+    static thread_local std::vector<char> take_tls;
+    std::vector<char>& take = take_tls;
+    take.assign(gs.size(), 0);
+    uint32_t blocked = 0;  // qubits with a later gate that stays in the program
+    for (size_t i = gs.size(); i-- > 0;) {
+      const Gate& g = *gs[i];
+      const uint32_t qm = qubit_mask(g);
+      const bool perm = g.kind == TQS_X || g.kind == TQS_CNOT || g.kind == TQS_SWAP;
+      if (perm && !(qm & blocked)) take[i] = 1;
+      else blocked |= qm;
+    }
+    size_t k = 0;
+    for (size_t i = 0; i < gs.size(); ++i) {
+      if (take[i]) tail.push_back(gs[i]);
+      else gs[k++] = gs[i];
+    }
+    gs.resize(k);
   }
   std::vector<uint32_t>& qmask = qmask_tls;
   std::vector<GClass>& gcls = cls_tls;
@@ -87,11 +311,11 @@ void compile_program(int n, const std::vector<const Gate*>& gs_in, Program& P,
     double pass_cost = 6.0;
     int h_count = 0;
     static const uint16_t kBitMask[4] = {0xAAAA, 0xCCCC, 0xF0F0, 0xFF00};
-    for (const Raw& r : raw) {
+    auto emit_raw = [&](const Raw& r) {
       // a factor that fused to the identity (H H, X X, ...) does nothing
       if (!r.is_h && std::abs(r.u.m[0] - 1.0) <= 1e-15 && std::abs(r.u.m[3] - 1.0) <= 1e-15 &&
           std::abs(r.u.m[1]) <= 1e-15 && std::abs(r.u.m[2]) <= 1e-15)
-        continue;
+        return;
       FusedOp op{};
       const Mat2& u = r.u;
       op.fbit = 0xFF;
@@ -123,9 +347,9 @@ void compile_program(int n, const std::vector<const Gate*>& gs_in, Program& P,
           pass_cost += 3.0;
         }
       } else {
-        op.m[0] = to_f2(u.m[0]);
-        op.m[1] = to_f2(u.m[3]);
-        op.m[2] = to_f2(u.m[3] / u.m[0]);
+        op.m[0] = to_unit_f2(u.m[0]);
+        op.m[1] = to_unit_f2(u.m[3]);
+        op.m[2] = to_unit_f2(u.m[3] / u.m[0]);
         op.d0one = (u.m[0] == cd(1.0)) ? 1 : 0;
         op.hc = (tl >= 0 && cl < 0) ? op.m[2] : op.m[1];
         pass_cost += 0.25;
@@ -143,7 +367,23 @@ void compile_program(int n, const std::vector<const Gate*>& gs_in, Program& P,
         }
       }
       P.ops.push_back(op);
+    };
+    for (const Raw& r : raw) {
+      // An uncontrolled factor diag(alpha, gamma) H diag(1, beta) with phases
+      // in {1, -1, i, -i} (X H, H X, Z H, H Z, Y H, ...) runs as an exact
+      // unscaled Hadamard between exact phase factors instead of a dense
+      // butterfly.
+      Mat2 d1, d2;
+      if (r.single && !r.is_h && r.cls != G_DIAG && h_count < kMaxHPerPass &&
+          hadamard_split(r.u, d2, d1)) {
+        emit_raw({d2, G_DIAG, false, true, r.t, -1});
+        emit_raw({gate_matrix(TQS_H, nullptr), G_DENSE, true, true, r.t, -1});
+        emit_raw({d1, G_DIAG, false, true, r.t, -1});
+        continue;
+      }
+      emit_raw(r);
     }
+    merge_diagonals(P.ops, ps.op_begin);
     ps.op_count = static_cast<uint32_t>(P.ops.size() - ps.op_begin);
     // exact power-of-two rescale for this pass's unscaled Hadamards
     const int tot = h_carry + h_count;
@@ -260,11 +500,38 @@ void compile_program(int n, const std::vector<const Gate*>& gs_in, Program& P,
     P.passes.resize(k);
   }
   P.out_scale = h_carry ? static_cast<float>(1.0 / std::sqrt(2.0)) : 1.0f;
-  P.identity = 1;
-  for (int q = 0; q < 16; ++q) {
-    P.pos[q] = static_cast<uint8_t>(q < n ? phys[q] : q);
-    if (q < n && phys[q] != q) P.identity = 0;
+  // A register pass last multiplies every amplitude by its scale 2^-k (an
+  // exact power of two).  The leftover 2^-1/2 is folded into that scale, so
+  // the output phase multiplies by nothing (where the pass applies no phase
+  // scalar the result is bitwise that of a separate multiply by 2^-1/2).
+  if (P.out_scale != 1.0f && P.passes.back().L[0] != kInstrPass && P.passes.back().L[0] != kWidePass) {
+    P.passes.back().scale *= P.out_scale;
+    P.out_scale = 1.0f;
   }
+  // Output map: F (the folded tail, columns over logical bits, offset v)
+  // composed with the relabeling phys.  F(y) = g_1(g_2(... g_k(y))) for the
+  // tail g_1 .. g_k: built by F <- F o g for g in order.
+  uint32_t fcol[32];
+  uint32_t fv = 0;
+  for (int q = 0; q < 32; ++q) fcol[q] = 1u << q;
+  for (const Gate* g : tail) {
+    if (g->kind == TQS_X) {
+      fv ^= fcol[g->q[0]];
+    } else if (g->kind == TQS_CNOT) {
+      fcol[g->q[0]] ^= fcol[g->q[1]];
+    } else {
+      std::swap(fcol[g->q[0]], fcol[g->q[1]]);
+    }
+  }
+  auto relabel = [&](uint32_t v) {
+    uint32_t r = 0;
+    for (int q = 0; q < n && q < 32; ++q)
+      if ((v >> q) & 1) r |= 1u << phys[q];
+    return r;
+  };
+  for (int q = 0; q < 16; ++q)
+    P.col[q] = static_cast<uint16_t>(q < n ? relabel(fcol[q]) : (1u << q));
+  P.col_off = static_cast<uint16_t>(relabel(fv));
   P.cost += 2.0 * static_cast<double>(1u << n);
 }
 

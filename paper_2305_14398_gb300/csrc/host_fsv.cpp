@@ -178,7 +178,7 @@ static tqs_status compile_fsv(int n, const std::vector<Gate>& gates, int max_gat
       ptrs[k] = &relabelled[k];
     }
     Program tp;
-    compile_program(T + info.nfar, ptrs, tp, false);
+    compile_program(T + info.nfar, ptrs, tp, false, false);
     P.passes.push_back(info);
     P.progs.push_back(std::move(tp));
   }

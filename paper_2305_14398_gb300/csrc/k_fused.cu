@@ -291,6 +291,48 @@ __device__ __forceinline__ void run_ops(float2 (&a)[16], const FusedOp* __restri
       }
       continue;
     }
+    if (code == OPC_DLIST) {
+      // up to 8 phase factors, each on when its physical bit of the group is
+      // set (byte 0xFF: always), multiplied into the pending factor of one
+      // local position or into the group's scalar
+      const int tgt = (q0.x >> 8) & 0xff, cnt = (q0.x >> 16) & 0xff;
+      const uint4 q1 = __ldg(rec + 1), q2 = __ldg(rec + 2);
+      float2 acc = make_float2(1.f, 0.f);
+      const float2 one = make_float2(1.f, 0.f);
+      const unsigned fb[2] = {q0.z, q0.w};
+      const uint4 qv[2] = {q1, q2};
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        if (e < cnt) {
+          const int f = (fb[0] >> (8 * e)) & 0xff;
+          const bool on = f == 0xff || ((base >> f) & 1);
+          const uint4 w = qv[e >> 1];
+          const float2 v = (e & 1) ? f2(w.z, w.w) : f2(w.x, w.y);
+          acc = cmul(acc, on ? v : one);
+        }
+      }
+      if (cnt > 4) {
+        const uint4 q3 = __ldg(rec + 3), q4 = __ldg(rec + 4);
+        const uint4 qw[2] = {q3, q4};
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+          if (e + 4 < cnt) {
+            const int f = (fb[1] >> (8 * e)) & 0xff;
+            const bool on = f == 0xff || ((base >> f) & 1);
+            const uint4 w = qw[e >> 1];
+            const float2 v = (e & 1) ? f2(w.z, w.w) : f2(w.x, w.y);
+            acc = cmul(acc, on ? v : one);
+          }
+        }
+      }
+      if (tgt < 4) {
+        pend_mul(pd, tgt, acc);
+      } else {
+        sc = cmul(sc, acc);
+        sc_set = true;
+      }
+      continue;
+    }
     // diagonal ops: d0 = m0, d1 = m1, ratio d1/d0 = m2; the header's hc holds
     // d1/d0 (local target, no local control) or d1 (the rest), so only ops
     // whose d0 is not exactly 1 load more than the header
@@ -346,16 +388,6 @@ __device__ __forceinline__ void run_ops(float2 (&a)[16], const FusedOp* __restri
   }
 }
 
-// Compensated (Kahan) FP32 accumulation of |v|^2 for the per-circuit norm:
-// the per-thread partial sums are exact to a few FP32 ulps and are combined
-// across threads in FP64.
-__device__ __forceinline__ void kahan_add(float p, float& sum, float& comp) {
-  const float y = p - comp;
-  const float t = sum + y;
-  comp = (t - sum) - y;
-  sum = t;
-}
-
 // |v|^2 correctly rounded to FP64: the two squares are exact FP64 values built
 // with integer operations; one FP64 add rounds their sum.
 __device__ __forceinline__ double prob_f64(float2 v) {
@@ -366,20 +398,12 @@ __device__ __forceinline__ double prob_f64(float2 v) {
   return __dadd_rn(a, b);
 }
 
-// P(v): the physical index of logical index v, the XOR of 2^pos[q] over the
-// set bits q of v (the output map is a bit permutation, linear over XOR).
-struct PosMap {
-  unsigned long long lo, hi;  // pos[0..7], pos[8..15] as bytes
-};
-
-// P(v): physical index of logical index v, the XOR of 2^pos[q] over the set
-// bits q of v (the final qubit map is a bit permutation, linear over XOR).
-__device__ __forceinline__ int pfwd_bit(int q, const PosMap& pm) {
-  return 1 << static_cast<int>(((q < 8 ? pm.lo : pm.hi) >> ((q & 7) * 8)) & 0xff);
-}
-__device__ __forceinline__ int pfwd_of(int v, const PosMap& pm, int n) {
+// The output map's linear part (FusedCirc::col): the XOR of col[q] over the
+// set bits q of v, v < 2^n.
+__device__ __forceinline__ int map_lin(const FusedCirc* c, int v, int n) {
   int r = 0;
-  for (int q = 0; q < n; ++q) if ((v >> q) & 1) r |= pfwd_bit(q, pm);
+  for (int q = 0; q < n; ++q)
+    if ((v >> q) & 1) r ^= __ldg(&c->col[q]);
   return r;
 }
 // Prefetch [p, p + bytes) into L1, one 128-byte line per thread of the team.
@@ -625,50 +649,72 @@ __device__ void run_circuit(const FusedLaunch& L, int ci, float2* st, int rank, 
   }
   if (TEAM == TEAM_WARP || TEAM == TEAM_PAIR)
     next_ci = next_job < L.n_jobs ? __ldg(L.order + next_job) : 0;
-  // Output: logical index i holds the amplitude at physical index P(i).  A
-  // thread writes i = 2 rank + 2 size k (two amplitudes, one 16-byte store);
-  // k runs in Gray-code order so P(i) changes by one XOR per iteration.
+  // Output: logical index i holds the amplitude at physical index P(i) =
+  // col_off ^ lin(i) (the output map), whose shared-memory slot is A(i) =
+  // swz(P(i)).  lin and swz are linear over GF(2), so A(i) is swz(col_off)
+  // XOR the columns swz(col[q]) over the set bits q of i.  A thread writes the pairs
+  // i, i + 1 with i = 2 rank + 2 size g (one 16-byte store of the state, one
+  // of the probabilities); g runs in blocks of 8 in Gray-code order, so each
+  // step changes A by one XOR of a column held in a register.
   const int N = 1 << n;
-  PosMap pw;
-  { const ulonglong2 pv = *reinterpret_cast<const ulonglong2*>(cd.pos); pw.lo = pv.x; pw.hi = pv.y; }
-  float2* out = L.out + cd.out_off;
-  double* probs = L.probs ? L.probs + cd.out_off : nullptr;
-  const float oscale = cd.out_scale;
-  const int sh = 31 - __clz(2 * size);
-  const int i0 = 2 * rank;
-  float nsum = 0.f, ncomp = 0.f;
-  if (i0 < N) {
-    const int p_lo = cd.identity ? i0 : pfwd_of(i0, pw, n);
-    const int p_one = cd.identity ? 1 : pfwd_bit(0, pw);
-    int p_hi = 0;
-    const int iters = (N + 2 * size - 1) >> sh;
-    const bool exact = L.exact_probs != 0;
+  float2* const outc = L.out + cd.out_off;
+  double* const probc = L.probs ? L.probs + cd.out_off : nullptr;
+  double acc = 0.0;
+  {
+    const FusedCirc* cg = L.circs + ci;
+    // log2 of the index stride between a thread's pairs (2 size): fixed for
+    // the warp and pair teams, so the stores take immediate offsets
+    constexpr int kSh = TEAM == TEAM_WARP ? 6 : TEAM == TEAM_PAIR ? 7 : 0;
+    const int sh = kSh ? kSh : 31 - __clz(2 * size);
+    const int i0 = 2 * rank;
+    if (i0 < N) {
+      const float oscale = cd.out_scale;
+      const bool exact = L.exact_probs != 0;
+      auto col = [&](int q) { return q < n ? swz(__ldg(&cg->col[q])) : 0; };
+      const int a1 = col(0);
+      const int c0 = col(sh), c1 = col(sh + 1), c2 = col(sh + 2);
+      const int a_i0 = swz(cd.col_off ^ map_lin(cg, i0, n));
+      const int iters = N > (1 << sh) ? (N >> sh) : 1;  // pairs per thread
+      const int NI = 1 << nint;
 #pragma unroll 1
-    for (int k = 0; k < iters; ++k) {
-      if (k > 0) {
-        const int q = sh + (__ffs(k) - 1);
-        p_hi ^= cd.identity ? (1 << q) : pfwd_bit(q, pw);
+      for (int blk = 0; blk < iters; blk += 8) {
+        // A at the block's first pair: the block index's bits sh + 3 ...
+        int ab = a_i0;
+        for (int q = 3; (blk >> q) != 0; ++q)
+          if ((blk >> q) & 1) ab ^= col(sh + q);
+        const int ib = i0 + (blk << sh);  // the block's first pair
+        float s[8];
+#pragma unroll
+        for (int r = 0; r < 8; ++r) {
+          s[r] = 0.f;
+          const int gr = r ^ (r >> 1);  // Gray code: consecutive r differ in one bit
+          if (r < iters) {
+            const int a = ab ^ ((gr & 1) ? c0 : 0) ^ ((gr & 2) ? c1 : 0) ^ ((gr & 4) ? c2 : 0);
+            float2 v0 = ld_state<TEAM>(&st[TQS_IX(a, NI)]);
+            float2 v1 = ld_state<TEAM>(&st[TQS_IX(a ^ a1, NI)]);
+            if (oscale != 1.0f) {
+              v0 = make_float2(v0.x * oscale, v0.y * oscale);
+              v1 = make_float2(v1.x * oscale, v1.y * oscale);
+            }
+            const int i = ib + (gr << sh);
+            *reinterpret_cast<float4*>(outc + TQS_IX(i, N - 1)) = make_float4(v0.x, v0.y, v1.x, v1.y);
+            const float q0 = fmaf(v0.x, v0.x, v0.y * v0.y), q1 = fmaf(v1.x, v1.x, v1.y * v1.y);
+            if (probc) {
+              // |psi|^2 in FP32 arithmetic, stored as FP64; or (exact_probs) the
+              // exact squares correctly rounded once in FP64
+              *reinterpret_cast<double2*>(probc + TQS_IX(i, N - 1)) =
+                  exact ? make_double2(prob_f64(v0), prob_f64(v1)) : make_double2(q0, q1);
+            }
+            s[r] = q0 + q1;
+          }
+        }
+        // the block's 16 values summed as a tree in FP32, then added in FP64
+        acc += static_cast<double>(((s[0] + s[1]) + (s[2] + s[3])) + ((s[4] + s[5]) + (s[6] + s[7])));
       }
-      const int gk = k ^ (k >> 1);
-      const int i = i0 + (gk << sh);
-      const int p0 = p_lo ^ p_hi;
-      float2 v0 = ld_state<TEAM>(&st[TQS_IX(swz(p0), 1 << nint)]);
-      float2 v1 = ld_state<TEAM>(&st[TQS_IX(swz(p0 ^ p_one), 1 << nint)]);
-      if (oscale != 1.0f) { v0 = make_float2(v0.x * oscale, v0.y * oscale); v1 = make_float2(v1.x * oscale, v1.y * oscale); }
-      *reinterpret_cast<float4*>(out + TQS_IX(i, N - 1)) = make_float4(v0.x, v0.y, v1.x, v1.y);
-      const float q0 = fmaf(v0.x, v0.x, v0.y * v0.y), q1 = fmaf(v1.x, v1.x, v1.y * v1.y);
-      if (probs) {
-        // |psi|^2 in FP32 arithmetic, stored as FP64; or (exact_probs) the
-        // exact squares correctly rounded once in FP64
-        *reinterpret_cast<double2*>(probs + TQS_IX(i, N - 1)) =
-            exact ? make_double2(prob_f64(v0), prob_f64(v1)) : make_double2(q0, q1);
-      }
-      kahan_add(q0, nsum, ncomp);
-      kahan_add(q1, nsum, ncomp);
     }
   }
-  // Fixed-order reduction (deterministic): per-thread compensated FP32 -> FP64.
-  double acc = static_cast<double>(nsum) - static_cast<double>(ncomp);
+  // Fixed-order reduction (deterministic): per-thread FP64 partials, warp
+  // butterfly, then the warps of the team in order.
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
   if (TEAM == TEAM_WARP) {
@@ -683,7 +729,7 @@ __device__ void run_circuit(const FusedLaunch& L, int ci, float2* st, int rank, 
     // a grid barrier timed out: the outputs are not valid, make that visible
     const float nan = __int_as_float(0x7fffffff);
     if (L.norms) L.norms[ci] = static_cast<double>(nan);
-    out[0] = make_float2(nan, nan);
+    outc[0] = make_float2(nan, nan);
   }
   if ((TEAM == TEAM_WARP || TEAM == TEAM_PAIR) && rank == 0 && next_job < L.n_jobs)
     prefetch_l1_range(L.circs + next_ci, sizeof(FusedCirc), 0, 1);
@@ -793,8 +839,15 @@ __global__ void __launch_bounds__(kFsvThreads)
   const uint64_t all = (F.n >= 64) ? ~0ull : ((1ull << F.n) - 1);
   const uint64_t comp = all & ~F.mask;
   const uint64_t ntiles = 1ull << (F.n - T);
-  PosMap pw;
-  { const ulonglong2 pv = *reinterpret_cast<const ulonglong2*>(cd.pos); pw.lo = pv.x; pw.hi = pv.y; }
+  // write-back map of tile element e = tid + kFsvThreads k: P(tid) ^ lin(kFsvThreads k),
+  // the second part from the columns of the bits above the thread index
+  // (T <= kFsvTileQ = kThrQ + 5)
+  constexpr int kThrQ = 8;  // log2 kFsvThreads
+  static_assert((1 << kThrQ) == kFsvThreads && kFsvTileQ <= kThrQ + 5, "tile threads");
+  const int p_tid = cd.col_off ^ map_lin(L.circs, tid, T);
+  int hcol[5];
+#pragma unroll
+  for (int j = 0; j < 5; ++j) hcol[j] = kThrQ + j < T ? __ldg(&L.circs->col[kThrQ + j]) : 0;
   float2* g = F.state;
   __syncthreads();
   for (uint64_t j = blockIdx.x; j < ntiles; j += gridDim.x) {
@@ -832,7 +885,10 @@ __global__ void __launch_bounds__(kFsvThreads)
     // tile qubit i of the result sits at physical tile bit pos[i]
     const float osc = cd.out_scale;
     for (int e = tid; e < NT; e += kFsvThreads) {
-      float2 v = st[TQS_IX(swz(cd.identity ? e : pfwd_of(e, pw, T)), NT)];
+      const int k = e >> kThrQ;
+      const int pk = ((k & 1) ? hcol[0] : 0) ^ ((k & 2) ? hcol[1] : 0) ^ ((k & 4) ? hcol[2] : 0) ^
+                     ((k & 8) ? hcol[3] : 0) ^ ((k & 16) ? hcol[4] : 0);
+      float2 v = st[TQS_IX(swz(p_tid ^ pk), NT)];
       if (osc != 1.0f) v = make_float2(v.x * osc, v.y * osc);
       g[TQS_IX(gbase + hoff[e >> nlow] + (e & lowm), 1ull << F.n)] = v;
     }

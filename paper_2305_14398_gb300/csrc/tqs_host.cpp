@@ -183,7 +183,7 @@ tqs_status tqs_circuit_steps(const tqs_circuit* c, int* h_step_of_gate) {
 
 
 extern "C" tqs_status tqs_circuit_program(tqs_circuit* c, int* n_passes, int* n_ops, void* h_passes,
-                                          void* h_ops, uint8_t* h_pos, float* h_out_scale,
+                                          void* h_ops, uint16_t* h_map, float* h_out_scale,
                                           int* h_gen_index) {
   if (!c) return fail(TQS_ERR_ARG, "tqs_circuit_program: circuit is NULL");
   if (c->n > TQS_MAX_QUBITS)
@@ -194,7 +194,10 @@ extern "C" tqs_status tqs_circuit_program(tqs_circuit* c, int* n_passes, int* n_
   if (n_ops) *n_ops = static_cast<int>(c->prog.ops.size());
   if (h_passes) std::memcpy(h_passes, c->prog.passes.data(), c->prog.passes.size() * sizeof(FusedPass));
   if (h_ops) std::memcpy(h_ops, c->prog.ops.data(), c->prog.ops.size() * sizeof(FusedOp));
-  if (h_pos) std::memcpy(h_pos, c->prog.pos, 16);
+  if (h_map) {
+    std::memcpy(h_map, c->prog.col, sizeof(c->prog.col));
+    h_map[16] = c->prog.col_off;
+  }
   if (h_out_scale) *h_out_scale = c->prog.out_scale;
   return TQS_OK;
 }

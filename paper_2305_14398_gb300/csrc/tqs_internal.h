@@ -35,6 +35,11 @@ namespace tqs {
 //   OPC_DFL + c      diag(d0, d1), far target bit `tbit`, local control c
 //   OPC_DFF          diag(d0, d1), far target bit `tbit`, no or far control `fbit`
 //   OPC_DLL          diag(d0, d1), local target t and local control c (fields t, c)
+//   OPC_DLIST        up to 8 phase factors merged into one op: field t = the
+//                    local position they multiply (0..3: the amplitudes with
+//                    that local bit set; 4: the whole group), field c = their
+//                    count; factor e (m[0..3], then lo[0..3]) applies when
+//                    the group's physical bit hc-byte e is 1 (0xFF: always)
 // Diagonal ops carry d0, d1, d1/d0 and `d0one` = 1 when d0 is exactly 1; the
 // coefficient they use when d0 is 1 is repeated in the header (`hc`).
 enum OpCode : uint8_t {
@@ -50,7 +55,8 @@ enum OpCode : uint8_t {
   OPC_DFL = 48,
   OPC_DFF = 52,
   OPC_DLL = 53,
-  OPC_COUNT = 54
+  OPC_DLIST = 54,
+  OPC_COUNT = 55
 };
 
 struct alignas(16) FusedOp {
@@ -104,21 +110,27 @@ enum TeamKind : int32_t { TEAM_WARP = 0, TEAM_CTA = 1, TEAM_GLOBAL = 2, TEAM_PAI
 // then records a time-out in FusedLaunch::err and stops waiting.
 constexpr long long kGridBarrierCycles = 2000000000LL;
 
+// Output map: logical index y of the result is physical index
+// col_off ^ (XOR of col[q] over the set bits q of y), an affine map over
+// GF(2): a bit permutation (SWAP factors relabel qubits) composed with the
+// permutation gates (X, CNOT, SWAP) at the end of the circuit, which are not
+// applied to the amplitudes but folded into this map.
 struct alignas(16) FusedCirc {
   int16_t n;            // logical qubits
   int16_t nint;         // internal qubits = max(n, 4)
   int32_t pass_begin;   // index into the pass array
   int32_t pass_count;
-  int32_t identity;     // 1 if the output qubit map is the identity
+  uint16_t col_off;     // output map: physical index of logical index 0
+  uint16_t pad;
   int64_t out_off;      // amplitude offset of this circuit's outputs
   int32_t op_begin;     // the circuit's op records: [op_begin, op_begin + op_count)
   int32_t op_count;     //   (prefetched into L1 when the circuit starts)
-  uint8_t pos[16];      // physical bit of logical qubit q at the end
+  uint16_t col[16];     // output map: physical index bits of logical qubit q
   const float2* init;   // initial state (logical order) or nullptr for a basis state
   float out_scale;      // 1, or 2^-1/2 when an odd Hadamard factor is left over
   int32_t gen_index;    // without init: the first pass starts from |gen_index>
 };
-static_assert(sizeof(FusedCirc) == 64, "FusedCirc layout");
+static_assert(sizeof(FusedCirc) == 80, "FusedCirc layout");
 
 // Team limits: a warp team holds up to 2^kWarpMaxQ amplitudes in its shared
 // memory slice; a CTA team up to 2^kCtaMaxQ in its CTA's shared memory; larger

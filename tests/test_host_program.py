@@ -16,7 +16,7 @@ from paper_2305_14398_gb300 import binding as B
 from paper_2305_14398_gb300 import workloads as W
 
 OPC_H, OPC_X, OPC_XF, OPC_XL, OPC_ANTI, OPC_DENSE, OPC_CDENSE = 0, 4, 8, 12, 28, 32, 36
-OPC_DLN, OPC_DLF, OPC_DFL, OPC_DFF, OPC_DLL = 40, 44, 48, 52, 53
+OPC_DLN, OPC_DLF, OPC_DFL, OPC_DFF, OPC_DLL, OPC_DLIST = 40, 44, 48, 52, 53, 54
 BIT_MASK = [0xAAAA, 0xCCCC, 0xF0F0, 0xFF00]
 
 
@@ -79,6 +79,20 @@ def replay(n, passes, ops, pos, out_scale=1.0, gen_index=0, uniforms=None, outco
             m = op["m"].astype(np.complex128)
             fbit = int(op["fbit"])
             far_on = np.ones(G, bool) if fbit == 255 else ((base >> fbit) & 1) == 1
+            if code == OPC_DLIST:  # up to 8 phase factors on one position / the group
+                tgt, cnt = int(op["t"]), int(op["c"])
+                assert 1 <= cnt <= 8 and 0 <= tgt <= 4 and fbit == 255
+                fb = np.frombuffer(np.array([op["hc"]], dtype=np.complex64).tobytes(), dtype=np.uint8)
+                vs = np.concatenate([op["m"], op["lo"]]).astype(np.complex128)
+                acc = np.ones(G, dtype=np.complex128)
+                for e in range(cnt):
+                    on = np.ones(G, bool) if fb[e] == 255 else ((base >> int(fb[e])) & 1) == 1
+                    acc[on] *= vs[e]
+                if tgt < 4:
+                    pend[:, tgt] *= acc
+                else:
+                    sc *= acc
+                continue
             if code >= OPC_DLN:
                 d0, d1, r = m[0], m[1], m[2]
                 if int(op["d0one"]):
@@ -147,10 +161,11 @@ def replay(n, passes, ops, pos, out_scale=1.0, gen_index=0, uniforms=None, outco
                     a[:, j] *= pend[:, b]
         a *= sc[:, None] * float(ps["scale"])
         st[idx] = a
+    # output map: physical index of logical y = map[16] ^ XOR of map[q] over y's set bits
     i = np.arange(1 << n, dtype=np.int64)
-    phys = np.zeros_like(i)
+    phys = np.full_like(i, int(pos[16]))
     for q in range(n):
-        phys |= ((i >> q) & 1) << int(pos[q])
+        phys ^= ((i >> q) & 1) * int(pos[q])
     return st[phys] * out_scale
 
 
@@ -207,18 +222,39 @@ def test_steps_are_asap():
 
 
 def test_ghz_steps_and_passes():
-    """GHZ chain on n qubits: n steps; the compiler needs ceil(n/4)+ passes."""
+    """GHZ chain on n qubits: n steps.  The CNOT chain is the circuit's
+    permutation tail: it is folded into the output map, so the program is the
+    one Hadamard on q0 (one pass) and the map sends logical y to the physical
+    index whose bit k is y_k ^ y_{k-1} (the inverse of the prefix parities the
+    chain computes)."""
     n = 11
     c = B.circuit_from_ops(n, W.ghz_chain(n))
     try:
         assert B.tqs_circuit_info(c)[2] == n
-        passes, ops, pos, osc, gen = B.tqs_circuit_program(c)
-        assert len(ops) == n and len(passes) <= 4 and gen == 0
-        assert ops[0]["code"] == OPC_H and osc == np.float32(2 ** -0.5)
-        assert all(OPC_XL <= int(o["code"]) < OPC_ANTI or int(o["code"]) < OPC_X
-                   or OPC_XF <= int(o["code"]) < OPC_XL for o in ops)
+        passes, ops, out_map, osc, gen = B.tqs_circuit_program(c)
+        assert len(ops) == 1 and len(passes) == 1 and gen == 0
+        # the one unscaled Hadamard's 2^-1/2 sits in the last pass's scale
+        assert ops[0]["code"] == OPC_H and osc == 1.0
+        assert float(passes[0]["scale"]) == float(np.float32(2 ** -0.5))
+        assert int(out_map[16]) == 0
+        for q in range(n):
+            want = (1 << q) | ((1 << (q + 1)) if q + 1 < n else 0)
+            assert int(out_map[q]) == want, q
     finally:
         B.tqs_circuit_destroy(c)
+
+
+def test_permutation_tail_only_when_last():
+    """A CNOT followed by a non-permutation gate on one of its qubits stays in
+    the program; X, CNOT and SWAP after every other gate on their qubits are
+    folded into the output map."""
+    n = 3
+    kept = compiled(n, [("h", (0,), ()), ("cx", (0, 1), ()), ("h", (1,), ())])
+    folded = compiled(n, [("h", (0,), ()), ("h", (2,), ()), ("cx", (0, 1), ()), ("x", (2,), ()),
+                          ("swap", (1, 2), ())])
+    assert any(OPC_XF <= int(o["code"]) < OPC_ANTI for o in kept[1])
+    assert all(int(o["code"]) < OPC_X for o in folded[1])
+    assert int(folded[2][16]) != 0  # the X on q2 is the map's offset
 
 
 @pytest.mark.parametrize("bad,status", [
@@ -377,7 +413,7 @@ def test_instruction_reads_the_relabelled_bit():
     """After SWAP(0, 2) the logical qubit 0 lives on physical bit 2."""
     passes, _, pos, _, _ = compiled(3, [("h", (1,), ()), ("swap", (0, 2), ()), ("measure", (0,), ())])
     ins = [p for p in passes if int(p["L"][0]) == 255]
-    assert len(ins) == 1 and int(ins[0]["L"][1]) == int(pos[0]) == 2
+    assert len(ins) == 1 and int(ins[0]["L"][1]) == 2 and int(pos[0]) == 1 << 2
 
 
 def test_unitary_forms_reject_instructions():
