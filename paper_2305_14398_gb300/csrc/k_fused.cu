@@ -110,24 +110,36 @@ __device__ __forceinline__ void swap_t(float2 (&a)[16], unsigned act) {
   }
 }
 
-// Hadamard butterfly without its 2^-1/2 (restored by the pass scale).
+// Hadamard butterfly without its 2^-1/2 (restored by the pass scale):
+// x0 <- x0 + x1, then x1 <- x0' - 2 x1 (= x0 - x1 up to one more rounding of
+// the sum), so each output overwrites an input that is no longer needed and
+// the butterfly needs no temporary registers.
 template <int T>
 __device__ __forceinline__ void h_t(float2 (&a)[16]) {
 #pragma unroll
   for (int p = 0; p < 8; ++p) {
     const int j0 = ((p >> T) << (T + 1)) | (p & ((1 << T) - 1));
     const int j1 = j0 | (1 << T);
-    const float2 x0 = a[j0], x1 = a[j1];
-    a[j0] = make_float2(x0.x + x1.x, x0.y + x1.y);
-    a[j1] = make_float2(x0.x - x1.x, x0.y - x1.y);
+    a[j0].x += a[j1].x;
+    a[j0].y += a[j1].y;
+    a[j1].x = fmaf(-2.f, a[j1].x, a[j0].x);
+    a[j1].y = fmaf(-2.f, a[j1].y, a[j0].y);
   }
+}
+
+// a <- a b in place: both products that need the old a.y are formed first,
+// so the results overwrite a.x and a.y without a temporary copy.
+__device__ __forceinline__ void cmul_in(float2& a, float2 b) {
+  const float t = a.y * b.y, u = a.y * b.x;
+  a.y = fmaf(a.x, b.y, u);
+  a.x = fmaf(a.x, b.x, -t);
 }
 
 template <int B>
 __device__ __forceinline__ void scale_bit(float2 (&a)[16], float2 ph) {
 #pragma unroll
   for (int j = 0; j < 16; ++j)
-    if ((j >> B) & 1) a[j] = cmul(a[j], ph);
+    if ((j >> B) & 1) cmul_in(a[j], ph);
 }
 
 // 16-bit masks of the local indices j whose bit b is set.
@@ -155,7 +167,7 @@ template <int T, int C>
 __device__ __forceinline__ void phase_tc(float2 (&a)[16], float2 d1) {
 #pragma unroll
   for (int j = 0; j < 16; ++j)
-    if (((j >> T) & 1) && ((j >> C) & 1)) a[j] = cmul(a[j], d1);
+    if (((j >> T) & 1) && ((j >> C) & 1)) cmul_in(a[j], d1);
 }
 
 __device__ __forceinline__ void phase_local(float2 (&a)[16], int t, int c, float2 d1) {
@@ -216,9 +228,9 @@ __device__ __forceinline__ float2 f2(unsigned x, unsigned y) {
 // pass's exact power-of-two scale.  The next op's header is fetched while the
 // current one runs.
 // SPLIT_DENSE: uncontrolled dense factors take a select-free copy of the
-// butterfly (more code; the full-state-vector tiles, dominated by dense
-// single-qubit factors, use it; the fused teams keep one copy, which keeps
-// them free of register spills).
+// butterfly (more code; the full-state-vector tiles and the CTA-sized teams,
+// dominated by dense single-qubit factors, use it; the warp and pair teams
+// keep one copy, measured faster on the paper-shaped circuits).
 template <bool SPLIT_DENSE>
 __device__ __forceinline__ void run_ops(float2 (&a)[16], const FusedOp* __restrict__ ops,
                                         uint32_t count, int base, float scale) {
@@ -295,6 +307,7 @@ __device__ __forceinline__ void run_ops(float2 (&a)[16], const FusedOp* __restri
       // up to 8 phase factors, each on when its physical bit of the group is
       // set (byte 0xFF: always), multiplied into the pending factor of one
       // local position or into the group's scalar
+      // the list is padded to 4 or 8 factors with (0xFF, 1): no per-factor guard
       const int tgt = (q0.x >> 8) & 0xff, cnt = (q0.x >> 16) & 0xff;
       const uint4 q1 = __ldg(rec + 1), q2 = __ldg(rec + 2);
       float2 acc = make_float2(1.f, 0.f);
@@ -303,26 +316,22 @@ __device__ __forceinline__ void run_ops(float2 (&a)[16], const FusedOp* __restri
       const uint4 qv[2] = {q1, q2};
 #pragma unroll
       for (int e = 0; e < 4; ++e) {
-        if (e < cnt) {
-          const int f = (fb[0] >> (8 * e)) & 0xff;
-          const bool on = f == 0xff || ((base >> f) & 1);
-          const uint4 w = qv[e >> 1];
-          const float2 v = (e & 1) ? f2(w.z, w.w) : f2(w.x, w.y);
-          acc = cmul(acc, on ? v : one);
-        }
+        const int f = (fb[0] >> (8 * e)) & 0xff;
+        const bool on = f == 0xff || ((base >> f) & 1);
+        const uint4 w = qv[e >> 1];
+        const float2 v = (e & 1) ? f2(w.z, w.w) : f2(w.x, w.y);
+        acc = cmul(acc, on ? v : one);
       }
       if (cnt > 4) {
         const uint4 q3 = __ldg(rec + 3), q4 = __ldg(rec + 4);
         const uint4 qw[2] = {q3, q4};
 #pragma unroll
         for (int e = 0; e < 4; ++e) {
-          if (e + 4 < cnt) {
-            const int f = (fb[1] >> (8 * e)) & 0xff;
-            const bool on = f == 0xff || ((base >> f) & 1);
-            const uint4 w = qw[e >> 1];
-            const float2 v = (e & 1) ? f2(w.z, w.w) : f2(w.x, w.y);
-            acc = cmul(acc, on ? v : one);
-          }
+          const int f = (fb[1] >> (8 * e)) & 0xff;
+          const bool on = f == 0xff || ((base >> f) & 1);
+          const uint4 w = qw[e >> 1];
+          const float2 v = (e & 1) ? f2(w.z, w.w) : f2(w.x, w.y);
+          acc = cmul(acc, on ? v : one);
         }
       }
       if (tgt < 4) {
@@ -624,7 +633,9 @@ __device__ void run_circuit(const FusedLaunch& L, int ci, float2* st, int rank, 
           a[j] = ld_state<TEAM>(&st[TQS_IX(sb ^ ((j & 1) ? w0 : 0) ^ ((j & 2) ? w1 : 0) ^ ((j & 4) ? w2 : 0) ^ ((j & 8) ? w3 : 0), 1 << nint)]);
         }
       }
-      run_ops<false>(a, ops, count, base, scale);
+      // select-free dense butterflies where they pay: the CTA-sized teams,
+      // whose random-circuit workloads are dense-gate heavy
+      run_ops<TEAM != TEAM_WARP && TEAM != TEAM_PAIR>(a, ops, count, base, scale);
 #pragma unroll
       for (int j = 0; j < 16; ++j)
         st[TQS_IX(sb ^ ((j & 1) ? w0 : 0) ^ ((j & 2) ? w1 : 0) ^ ((j & 4) ? w2 : 0) ^ ((j & 8) ? w3 : 0), 1 << nint)] = a[j];
