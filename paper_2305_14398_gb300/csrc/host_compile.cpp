@@ -1,6 +1,8 @@
 // The fused-pass compiler (compile_program): a circuit's steps into passes of 4
 // local qubit bits with their ops (declared, with its description, in
 // host_common.h).
+#include <deque>
+
 #include "host_common.h"
 
 namespace tqs {
@@ -112,6 +114,41 @@ bool hadamard_split(const Mat2& u, Mat2& d2, Mat2& d1) {
   return true;
 }
 
+bool is_identity2(const Mat2& u) {
+  return std::abs(u.m[0] - 1.0) <= 1e-15 && std::abs(u.m[3] - 1.0) <= 1e-15 &&
+         std::abs(u.m[1]) <= 1e-15 && std::abs(u.m[2]) <= 1e-15;
+}
+
+// True when z is 1, -1, i or -i (to 1e-14): FP32 holds it exactly and a
+// multiply by it is exact.
+bool exact_phase(cd z) {
+  const double re = std::round(z.real()), im = std::round(z.imag());
+  return std::abs(z - cd(re, im)) <= 1e-14 && std::abs(re) + std::abs(im) == 1.0;
+}
+
+// Relative cost of an uncontrolled single-qubit factor as the kernel runs it
+// (unit: one unscaled Hadamard or exchange; exact phases accumulate per bit
+// and cost half; a dense butterfly with FP32 hi + lo coefficients several).
+// A phase that FP32 does not hold exactly counts as much as a dense
+// butterfly: as a factor of its own it multiplies the amplitudes by a
+// coefficient whose modulus is off 1 by up to an FP32 ulp, and over many
+// such factors that adds up in the norm, while fused into a neighbouring
+// non-diagonal factor it rides on the hi + lo coefficients.
+double single_cost(const Mat2& u, bool is_h) {
+  if (is_h) return 1.0;
+  if (is_identity2(u)) return 0.0;
+  switch (classify_mat(u)) {
+    case G_DIAG: return exact_phase(u.m[0]) && exact_phase(u.m[3]) ? 0.5 : 3.5;
+    case G_ANTI:
+      if (u.m[1] == cd(1.0) && u.m[2] == cd(1.0)) return 1.0;
+      return exact_phase(u.m[1]) && exact_phase(u.m[2]) ? 1.5 : 3.5;
+    default: {
+      Mat2 d1, d2;
+      return hadamard_split(u, d2, d1) ? 1.5 : 3.5;
+    }
+  }
+}
+
 // Local target position of a non-diagonal op.
 int nondiag_target(int code) {
   if (code >= OPC_XL && code < OPC_ANTI) return (code - OPC_XL) >> 2;
@@ -204,9 +241,6 @@ void compile_program(int n, const std::vector<const Gate*>& gs_in, Program& P,
                       bool fold_x, bool absorb) {
   P.n = n;
   P.nint = std::max(n, 4);
-  // Leading uncontrolled X factors on a qubit that nothing has touched yet act
-  // on the basis input |0...0> only by flipping that qubit: fold them into the
-  // start index instead of spending butterflies (input |0...0> only).
   // scratch reused across calls on this thread (no allocation per circuit)
   static thread_local std::vector<const Gate*> gs_tls;
   static thread_local std::vector<int> pending_tls, still_tls, order_tls;
@@ -216,17 +250,7 @@ void compile_program(int n, const std::vector<const Gate*>& gs_in, Program& P,
   std::vector<const Gate*>& gs = gs_tls;
   gs.clear();
   P.gen_index = 0;
-  {
-    uint32_t touched = 0;
-    for (const Gate* g : gs_in) {
-      if (fold_x && g->kind == TQS_X && !((touched >> g->q[0]) & 1)) {
-        P.gen_index ^= 1 << g->q[0];
-        continue;
-      }
-      touched |= qubit_mask(*g);
-      gs.push_back(g);
-    }
-  }
+  gs.assign(gs_in.begin(), gs_in.end());
   // Trailing permutation gates: an X, CNOT or SWAP with no later gate of
   // another kind on its qubits only permutes the final amplitudes, psi(y) =
   // phi(F(y)) with F an affine map over GF(2) (X: y ^ e_q; CNOT(c, t):
@@ -256,6 +280,77 @@ void compile_program(int n, const std::vector<const Gate*>& gs_in, Program& P,
     }
     gs.resize(k);
   }
+  // Leading uncontrolled X factors on a qubit that nothing has touched yet act
+  // on the basis input |0...0> only by flipping that qubit: fold them into the
+  // start index instead of spending butterflies (input |0...0> only; before
+  // the fusion below could merge them into later gates).
+  {
+    static thread_local std::vector<const Gate*> xf_tls;
+    std::vector<const Gate*>& xf = xf_tls;
+    xf.clear();
+    uint32_t touched = 0;
+    for (const Gate* g : gs) {
+      if (fold_x && g->kind == TQS_X && !((touched >> g->q[0]) & 1)) {
+        P.gen_index ^= 1 << g->q[0];
+        continue;
+      }
+      touched |= qubit_mask(*g);
+      xf.push_back(g);
+    }
+    gs.swap(xf);
+  }
+  // Circuit-wide fusion of single-qubit factors: consecutive uncontrolled
+  // single-qubit gates on one qubit (no other gate on it in between; the
+  // gates in between act on other qubits and commute) multiply into one
+  // factor at the first one's place, by the mixed-product property of the
+  // Kronecker product, unless the product runs costlier than the two apart.
+  // Products equal to the identity (H H, X X, ...) disappear; an exact X
+  // product is an X gate (an exchange).
+  static thread_local std::deque<Gate> fused_tls;
+  static thread_local std::vector<const Gate*> fl_tls;
+  std::deque<Gate>& fused = fused_tls;
+  std::vector<const Gate*>& fl = fl_tls;
+  fused.clear();
+  fl.clear();
+  {
+    int open[32];
+    for (int q = 0; q < 32; ++q) open[q] = -1;
+    for (const Gate* g : gs) {
+      const bool single = g->nq == 1 && !is_instruction(g->kind) && !is_two_qubit(g->kind);
+      if (!single) {
+        fl.push_back(g);
+        for (uint32_t m = qubit_mask(*g); m; m &= m - 1) open[__builtin_ctz(m)] = -1;
+        continue;
+      }
+      const int q = g->q[0];
+      if (open[q] >= 0) {
+        const Gate* pg = fl[static_cast<size_t>(open[q])];
+        const Mat2 uf = mat_mul(g->u, pg->u);
+        if (single_cost(uf, false) <=
+            single_cost(pg->u, pg->kind == TQS_H) + single_cost(g->u, g->kind == TQS_H)) {
+          if (is_identity2(uf)) {
+            fl[static_cast<size_t>(open[q])] = nullptr;
+            open[q] = -1;
+            continue;
+          }
+          fused.push_back(*pg);
+          Gate& f = fused.back();
+          f.u = uf;
+          f.cm.reset();
+          const bool is_x = uf.m[0] == cd(0.0) && uf.m[3] == cd(0.0) && uf.m[1] == cd(1.0) && uf.m[2] == cd(1.0);
+          f.kind = is_x ? TQS_X : TQS_U3;
+          fl[static_cast<size_t>(open[q])] = &f;
+          continue;
+        }
+      }
+      fl.push_back(g);
+      open[q] = static_cast<int>(fl.size()) - 1;
+    }
+  }
+  gs.clear();
+  for (const Gate* g : fl)
+    if (g != nullptr) gs.push_back(g);
+
   std::vector<uint32_t>& qmask = qmask_tls;
   std::vector<GClass>& gcls = cls_tls;
   qmask.resize(gs.size());
@@ -283,12 +378,18 @@ void compile_program(int n, const std::vector<const Gate*>& gs_in, Program& P,
     if (single) {
       const int last = last_touch[t];
       if (last >= 0 && raw[last].single && raw[last].t == t) {
+        // consecutive factors on one qubit multiply (the mixed-product
+        // property), unless the product is costlier than the two apart
+        // (a Hadamard and a general phase: a dense butterfly)
         Raw& r = raw[last];
-        if (r.is_h) --h_in_pass;
-        r.u = mat_mul(g.u, r.u);
-        r.is_h = false;
-        r.cls = classify_mat(r.u);
-        return;
+        const Mat2 uf = mat_mul(g.u, r.u);
+        if (single_cost(uf, false) <= single_cost(r.u, r.is_h) + single_cost(g.u, g.kind == TQS_H)) {
+          if (r.is_h) --h_in_pass;
+          r.u = uf;
+          r.is_h = false;
+          r.cls = classify_mat(r.u);
+          return;
+        }
       }
     }
     const bool is_h = single && g.kind == TQS_H && h_in_pass < kMaxHPerPass;
@@ -379,6 +480,15 @@ void compile_program(int n, const std::vector<const Gate*>& gs_in, Program& P,
         emit_raw({d2, G_DIAG, false, true, r.t, -1});
         emit_raw({gate_matrix(TQS_H, nullptr), G_DENSE, true, true, r.t, -1});
         emit_raw({d1, G_DIAG, false, true, r.t, -1});
+        continue;
+      }
+      // An uncontrolled anti-diagonal factor [[0, b], [c, 0]] other than X
+      // with exact phases (Y, X Z, ...) is X diag(c, b): phases, then an
+      // exchange.
+      if (r.single && !r.is_h && r.cls == G_ANTI && !(r.u.m[1] == cd(1.0) && r.u.m[2] == cd(1.0)) &&
+          exact_phase(r.u.m[1]) && exact_phase(r.u.m[2])) {
+        emit_raw({Mat2{{r.u.m[2], 0.0, 0.0, r.u.m[1]}}, G_DIAG, false, true, r.t, -1});
+        emit_raw({gate_matrix(TQS_X, nullptr), G_ANTI, false, true, r.t, -1});
         continue;
       }
       emit_raw(r);
