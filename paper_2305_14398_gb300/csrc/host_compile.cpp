@@ -15,31 +15,65 @@ namespace {
 // unlike the rounding of the products, adds up over a circuit's phases in the
 // norm; choosing the pair keeps it to about a quarter of plain rounding.
 // Other values (not of modulus 1 to 1e-12) round to nearest.
+// The FP32 neighbour of a finite float x one ulp up (up) or down.
+float fstep(float x, bool up) {
+  uint32_t b;
+  std::memcpy(&b, &x, 4);
+  if ((b & 0x7fffffffu) == 0) b = up ? 1u : 0x80000001u;       // +-0: the smallest denormal
+  else if ((b >> 31) == 0) b = up ? b + 1 : b - 1;             // positive
+  else b = up ? b - 1 : b + 1;                                 // negative
+  float r;
+  std::memcpy(&r, &b, 4);
+  return r;
+}
+
 float2 to_unit_f2(cd z) {
-  const float2 rn = to_f2(z);
-  if (std::abs(std::abs(z) - 1.0) > 1e-12) return rn;
-  // the FP32 values just below and just above each part (equal when exact)
-  auto bracket = [](double v, float r, float& lo, float& hi) {
-    lo = hi = r;
-    if (double(r) < v) hi = std::nextafter(r, INFINITY);
-    if (double(r) > v) lo = std::nextafter(r, -INFINITY);
+  // Circuits of a batch share most of their phases (the controlled phases of
+  // a QFT, S, T, ...): a small direct-mapped cache per host thread, keyed by
+  // the bits of z, answers repeats.
+  struct Entry {
+    uint64_t re = 0, im = 0;
+    float2 r;
+    bool used = false;
   };
-  float xs[2], ys[2];
-  bracket(z.real(), rn.x, xs[0], xs[1]);
-  bracket(z.imag(), rn.y, ys[0], ys[1]);
+  static thread_local Entry cache[256];
+  uint64_t kre, kim;
+  const double zre = z.real(), zim = z.imag();
+  std::memcpy(&kre, &zre, 8);
+  std::memcpy(&kim, &zim, 8);
+  Entry& ent = cache[((kre * 0x9E3779B97F4A7C15ull) ^ (kim * 0xC2B2AE3D27D4EB4Full)) >> 56];
+  if (ent.used && ent.re == kre && ent.im == kim) return ent.r;
+  const float2 rn = to_f2(z);
+  const double zr = z.real(), zi = z.imag();
   float2 best = rn;
-  double best_m = std::abs(double(rn.x) * rn.x + double(rn.y) * rn.y - 1.0);
-  double best_d = std::abs(cd(rn.x, rn.y) - z);
-  for (int i = 0; i < 4; ++i) {
-    const float x = xs[i & 1], y = ys[i >> 1];
-    const double m = std::abs(double(x) * x + double(y) * y - 1.0);
-    const double d = std::abs(cd(x, y) - z);
-    if (m < best_m || (m == best_m && d < best_d)) {
-      best = make_float2(x, y);
-      best_m = m;
-      best_d = d;
+  if (std::abs(zr * zr + zi * zi - 1.0) <= 2e-12) {
+    // the FP32 values just below and just above each part (equal when exact)
+    float xs[2] = {rn.x, rn.x}, ys[2] = {rn.y, rn.y};
+    if (double(rn.x) < zr) xs[1] = fstep(rn.x, true);
+    if (double(rn.x) > zr) xs[0] = fstep(rn.x, false);
+    if (double(rn.y) < zi) ys[1] = fstep(rn.y, true);
+    if (double(rn.y) > zi) ys[0] = fstep(rn.y, false);
+    if (xs[0] != xs[1] || ys[0] != ys[1]) {
+      // squared distances: the same order as the distances, without square roots
+      auto dist2 = [&](float x, float y) { return (x - zr) * (x - zr) + (y - zi) * (y - zi); };
+      double best_m = std::abs(double(rn.x) * rn.x + double(rn.y) * rn.y - 1.0);
+      double best_d = dist2(rn.x, rn.y);
+      for (int k = 0; k < 4; ++k) {
+        const float x = xs[k & 1], y = ys[k >> 1];
+        const double m = std::abs(double(x) * x + double(y) * y - 1.0);
+        const double d = dist2(x, y);
+        if (m < best_m || (m == best_m && d < best_d)) {
+          best = make_float2(x, y);
+          best_m = m;
+          best_d = d;
+        }
+      }
     }
   }
+  ent.re = kre;
+  ent.im = kim;
+  ent.r = best;
+  ent.used = true;
   return best;
 }
 
@@ -95,8 +129,8 @@ int diag_entries(const FusedOp& op, DiagEnt* e) {
 // acts first, then H, then d1.
 bool hadamard_split(const Mat2& u, Mat2& d2, Mat2& d1) {
   const double s = 1.0 / std::sqrt(2.0);
-  for (int i = 0; i < 4; ++i)
-    if (std::abs(std::abs(u.m[i]) - s) > 1e-14) return false;
+  for (int i = 0; i < 4; ++i)  // |u_i|^2 = 1/2
+    if (std::abs(std::norm(u.m[i]) - 0.5) > 2e-14) return false;
   // only phases that FP32 holds exactly (1, -1, i, -i): multiplying by them
   // is exact, so the split keeps the amplitudes' norm as the dense form does
   auto snap = [](cd z, cd& out) {
@@ -115,8 +149,8 @@ bool hadamard_split(const Mat2& u, Mat2& d2, Mat2& d1) {
 }
 
 bool is_identity2(const Mat2& u) {
-  return std::abs(u.m[0] - 1.0) <= 1e-15 && std::abs(u.m[3] - 1.0) <= 1e-15 &&
-         std::abs(u.m[1]) <= 1e-15 && std::abs(u.m[2]) <= 1e-15;
+  return std::norm(u.m[0] - 1.0) <= 1e-30 && std::norm(u.m[3] - 1.0) <= 1e-30 &&
+         std::norm(u.m[1]) <= 1e-30 && std::norm(u.m[2]) <= 1e-30;
 }
 
 // True when z is 1, -1, i or -i (to 1e-14): FP32 holds it exactly and a
@@ -231,8 +265,45 @@ void merge_diagonals(std::vector<FusedOp>& ops, size_t begin) {
     out.push_back(op);
   }
   for (int t = 0; t < 5; ++t) flush(t);
+  // Runs of two or more local-local diagonal factors (OPC_DLL) become one
+  // 16-entry diagonal: entry j is the product, in FP64 of the factors' FP32
+  // values, of the run's factors at local index j, rounded once (they
+  // commute, so the run's order does not matter).
   ops.resize(begin);
-  ops.insert(ops.end(), out.begin(), out.end());
+  for (size_t i = 0; i < out.size();) {
+    size_t j = i;
+    while (j < out.size() && out[j].code == OPC_DLL) ++j;
+    if (j - i < 2) {
+      ops.push_back(out[i]);
+      ++i;
+      continue;
+    }
+    cd d[16];
+    for (int e = 0; e < 16; ++e) d[e] = 1.0;
+    for (size_t k = i; k < j; ++k) {
+      const FusedOp& op = out[k];
+      const cd d0(op.m[0].x, op.m[0].y), d1(op.m[1].x, op.m[1].y);
+      for (int e = 0; e < 16; ++e)
+        if ((e >> op.c) & 1) d[e] *= ((e >> op.t) & 1) ? d1 : d0;
+    }
+    FusedOp a{}, b{};
+    a.code = OPC_DIAG16;
+    b.code = OPC_NOP;
+    for (FusedOp* r : {&a, &b}) {
+      r->fbit = 0xFF;
+      r->tbit = 0xFF;
+      r->act = 0xFFFF;
+    }
+    for (int e = 0; e < 4; ++e) {
+      a.m[e] = to_unit_f2(d[e]);
+      a.lo[e] = to_unit_f2(d[4 + e]);
+      b.m[e] = to_unit_f2(d[8 + e]);
+      b.lo[e] = to_unit_f2(d[12 + e]);
+    }
+    ops.push_back(a);
+    ops.push_back(b);
+    i = j;
+  }
 }
 
 }  // namespace
@@ -414,9 +485,7 @@ void compile_program(int n, const std::vector<const Gate*>& gs_in, Program& P,
     static const uint16_t kBitMask[4] = {0xAAAA, 0xCCCC, 0xF0F0, 0xFF00};
     auto emit_raw = [&](const Raw& r) {
       // a factor that fused to the identity (H H, X X, ...) does nothing
-      if (!r.is_h && std::abs(r.u.m[0] - 1.0) <= 1e-15 && std::abs(r.u.m[3] - 1.0) <= 1e-15 &&
-          std::abs(r.u.m[1]) <= 1e-15 && std::abs(r.u.m[2]) <= 1e-15)
-        return;
+      if (!r.is_h && is_identity2(r.u)) return;
       FusedOp op{};
       const Mat2& u = r.u;
       op.fbit = 0xFF;

@@ -303,6 +303,23 @@ __device__ __forceinline__ void run_ops(float2 (&a)[16], const FusedOp* __restri
       }
       continue;
     }
+    if (code >= OPC_DIAG16) {
+      if (code == OPC_DIAG16) {
+        // entry j multiplies amplitude j: 0..7 here, 8..15 in the next record
+        const uint4 q1 = __ldg(rec + 1), q2 = __ldg(rec + 2), q3 = __ldg(rec + 3), q4 = __ldg(rec + 4);
+        const uint4 r1 = __ldg(rec + 6), r2 = __ldg(rec + 7), r3 = __ldg(rec + 8), r4 = __ldg(rec + 9);
+        const uint4 w[8] = {q1, q2, q3, q4, r1, r2, r3, r4};
+#pragma unroll
+        for (int j = 0; j < 16; ++j) {
+          const uint4 v = w[j >> 1];
+          cmul_in(a[j], (j & 1) ? f2(v.z, v.w) : f2(v.x, v.y));
+        }
+        // skip the second record (and fetch the header after it)
+        ++k;
+        if (k + 1 < count) next = __ldg(reinterpret_cast<const uint4*>(ops + k + 1));
+      }
+      continue;  // OPC_NOP: the second record of an OPC_DIAG16
+    }
     if (code == OPC_DLIST) {
       // up to 8 phase factors, each on when its physical bit of the group is
       // set (byte 0xFF: always), multiplied into the pending factor of one

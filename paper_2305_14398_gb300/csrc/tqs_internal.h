@@ -35,6 +35,11 @@ namespace tqs {
 //   OPC_DFL + c      diag(d0, d1), far target bit `tbit`, local control c
 //   OPC_DFF          diag(d0, d1), far target bit `tbit`, no or far control `fbit`
 //   OPC_DLL          diag(d0, d1), local target t and local control c (fields t, c)
+//   OPC_DIAG16       a diagonal over the 16 local indices: entry j (the
+//                    product of a run of OPC_DLL factors) multiplies
+//                    amplitude j; entries 0..7 in m[0..3], lo[0..3] of this
+//                    record, 8..15 in those of the next record (OPC_NOP)
+//   OPC_NOP          does nothing (the second record of an OPC_DIAG16)
 //   OPC_DLIST        up to 8 phase factors merged into one op: field t = the
 //                    local position they multiply (0..3: the amplitudes with
 //                    that local bit set; 4: the whole group), field c = their
@@ -56,7 +61,9 @@ enum OpCode : uint8_t {
   OPC_DFF = 52,
   OPC_DLL = 53,
   OPC_DLIST = 54,
-  OPC_COUNT = 55
+  OPC_DIAG16 = 55,
+  OPC_NOP = 56,
+  OPC_COUNT = 57
 };
 
 struct alignas(16) FusedOp {

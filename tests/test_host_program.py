@@ -16,7 +16,7 @@ from paper_2305_14398_gb300 import binding as B
 from paper_2305_14398_gb300 import workloads as W
 
 OPC_H, OPC_X, OPC_XF, OPC_XL, OPC_ANTI, OPC_DENSE, OPC_CDENSE = 0, 4, 8, 12, 28, 32, 36
-OPC_DLN, OPC_DLF, OPC_DFL, OPC_DFF, OPC_DLL, OPC_DLIST = 40, 44, 48, 52, 53, 54
+OPC_DLN, OPC_DLF, OPC_DFL, OPC_DFF, OPC_DLL, OPC_DLIST, OPC_DIAG16, OPC_NOP = 40, 44, 48, 52, 53, 54, 55, 56
 BIT_MASK = [0xAAAA, 0xCCCC, 0xF0F0, 0xFF00]
 
 
@@ -74,8 +74,17 @@ def replay(n, passes, ops, pos, out_scale=1.0, gen_index=0, uniforms=None, outco
         pend = np.ones((G, 4), dtype=np.complex128)
         sc = np.ones(G, dtype=np.complex128)
         b0, cnt = int(ps["op_begin"]), int(ps["op_count"])
-        for op in ops[b0:b0 + cnt]:
+        prog = ops[b0:b0 + cnt]
+        for k, op in enumerate(prog):
             code = int(op["code"])
+            if code == OPC_NOP:  # second record of a 16-entry diagonal
+                assert k > 0 and int(prog[k - 1]["code"]) == OPC_DIAG16
+                continue
+            if code == OPC_DIAG16:  # entry j multiplies local amplitude j
+                assert int(prog[k + 1]["code"]) == OPC_NOP
+                d = np.concatenate([op["m"], op["lo"], prog[k + 1]["m"], prog[k + 1]["lo"]]).astype(np.complex128)
+                a *= d[None, :]
+                continue
             m = op["m"].astype(np.complex128)
             fbit = int(op["fbit"])
             far_on = np.ones(G, bool) if fbit == 255 else ((base >> fbit) & 1) == 1
