@@ -144,6 +144,26 @@ inline int n_params(int g) {
   }
 }
 
+// e^{i phi} (std::polar), remembered per host thread in a small direct-mapped
+// table keyed by phi's bits: the phase gates of a batch repeat the same few
+// angles (a QFT's controlled phases), and sin/cos dominate building them.
+inline cd unit_phase(double phi) {
+  struct Entry {
+    uint64_t key = 0;
+    cd v;
+    bool used = false;
+  };
+  static thread_local Entry table[128];
+  uint64_t k;
+  std::memcpy(&k, &phi, 8);
+  Entry& e = table[(k * 0x9E3779B97F4A7C15ull) >> 57];
+  if (e.used && e.key == k) return e.v;
+  e.key = k;
+  e.v = std::polar(1.0, phi);
+  e.used = true;
+  return e.v;
+}
+
 // Single-qubit matrix of a gate, or the U of a controlled gate.
 inline Mat2 gate_matrix(int g, const double* p) {
   const double r2 = 1.0 / std::sqrt(2.0);
@@ -155,8 +175,8 @@ inline Mat2 gate_matrix(int g, const double* p) {
     case TQS_Y: u = {{0.0, -I, I, 0.0}}; break;
     case TQS_Z: case TQS_CZ: u = {{1.0, 0.0, 0.0, -1.0}}; break;
     case TQS_S: u = {{1.0, 0.0, 0.0, I}}; break;
-    case TQS_T: u = {{1.0, 0.0, 0.0, std::polar(1.0, M_PI / 4.0)}}; break;
-    case TQS_R: case TQS_CP: u = {{1.0, 0.0, 0.0, std::polar(1.0, p[0])}}; break;
+    case TQS_T: u = {{1.0, 0.0, 0.0, unit_phase(M_PI / 4.0)}}; break;
+    case TQS_R: case TQS_CP: u = {{1.0, 0.0, 0.0, unit_phase(p[0])}}; break;
     case TQS_RX: {
       const double c = std::cos(p[0] / 2), s = std::sin(p[0] / 2);
       u = {{c, -I * s, -I * s, c}};
@@ -167,7 +187,7 @@ inline Mat2 gate_matrix(int g, const double* p) {
       u = {{c, -s, s, c}};
       break;
     }
-    case TQS_RZ: u = {{std::polar(1.0, -p[0] / 2), 0.0, 0.0, std::polar(1.0, p[0] / 2)}}; break;
+    case TQS_RZ: u = {{unit_phase(-p[0] / 2), 0.0, 0.0, unit_phase(p[0] / 2)}}; break;
     case TQS_U3: {
       const double c = std::cos(p[0] / 2), s = std::sin(p[0] / 2);
       u = {{c, -std::polar(1.0, p[2]) * s, std::polar(1.0, p[1]) * s,

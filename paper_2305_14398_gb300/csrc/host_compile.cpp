@@ -9,12 +9,6 @@ namespace tqs {
 
 namespace {
 
-// A unit-modulus phase z in FP32: of the four pairs that round z's parts
-// down or up, the one whose squared modulus is nearest 1 (ties: nearest z).
-// Every amplitude a phase multiplies shares its modulus error, so this error,
-// unlike the rounding of the products, adds up over a circuit's phases in the
-// norm; choosing the pair keeps it to about a quarter of plain rounding.
-// Other values (not of modulus 1 to 1e-12) round to nearest.
 // The FP32 neighbour of a finite float x one ulp up (up) or down.
 float fstep(float x, bool up) {
   uint32_t b;
@@ -27,6 +21,12 @@ float fstep(float x, bool up) {
   return r;
 }
 
+// A unit-modulus phase z in FP32: of the four pairs that round z's parts
+// down or up, the one whose squared modulus is nearest 1 (ties: nearest z).
+// Every amplitude a phase multiplies shares its modulus error, so this error,
+// unlike the rounding of the products, adds up over a circuit's phases in the
+// norm; choosing the pair keeps it to about a quarter of plain rounding.
+// Other values (not of modulus 1 to 1e-12) round to nearest.
 float2 to_unit_f2(cd z) {
   // Circuits of a batch share most of their phases (the controlled phases of
   // a QFT, S, T, ...): a small direct-mapped cache per host thread, keyed by
@@ -197,6 +197,16 @@ int nondiag_target(int code) {
 // between: each list is emitted just before the next non-diagonal op on its
 // position (or at the end of the pass).
 void merge_diagonals(std::vector<FusedOp>& ops, size_t begin) {
+  {
+    // nothing to merge: no phase factor and no two local-local factors in a row
+    bool any = false;
+    for (size_t i = begin; i < ops.size() && !any; ++i) {
+      DiagEnt es[2];
+      any = diag_entries(ops[i], es) > 0 ||
+            (ops[i].code == OPC_DLL && i + 1 < ops.size() && ops[i + 1].code == OPC_DLL);
+    }
+    if (!any) return;
+  }
   static thread_local std::vector<FusedOp> out;
   out.clear();
   DiagEnt open[5][8];
