@@ -531,6 +531,8 @@ def run_tqs(args):
     if not args.no_serving and rank == 0:
         from paper_2305_14398_gb300 import serve
         reqs = W.serving_requests(20000, 2000.0)
+        # warm-up (not reported): the server's pool, kernel attributes, cooperative launches
+        serve.replay(reqs[:2000], budget_bytes=120 * 10 ** 9, max_inflight=4, max_batch=256)
         r = serve.replay(reqs, budget_bytes=120 * 10 ** 9, max_inflight=4, max_batch=256)
         line["serving"] = {
             "workload": "20000 simulate requests, Poisson 2000 req/s (seeded), n ~ U{6..16}, "
@@ -539,7 +541,15 @@ def run_tqs(args):
             "p50_ms": r["p50_ms"], "p99_ms": r["p99_ms"], "mean_ms": r["mean_ms"],
             "max_ms": r["max_ms"], "completed_rps": r["throughput_rps"], "wall_s": r["wall_s"],
             "norm_max_err": float(np.max(np.abs(r["norms"] - 1.0))),
-            "peak_device_bytes": r["stats"]["peak_bytes"]}
+            "peak_device_bytes": r["stats"]["peak_bytes"], "busy_frac": r["busy_frac"]}
+        # offered load up to saturation (same mix, 20000 requests per rate)
+        sw = serve.sweep([5000, 20000, 50000, 100000, 200000, 400000])
+        kept = [x["offered_rps"] for x in sw if x["completed_rps"] >= 0.95 * x["offered_rps"]]
+        line["serving"]["sweep"] = sw
+        line["serving"]["max_sustained_rps"] = max(kept) if kept else None
+        line["serving"]["sweep_note"] = ("busy_frac: wall-time share with a batch in flight as the "
+                                         "polls see it; max_sustained_rps: the highest offered rate "
+                                         "completed at >= 95 %")
 
     # ---------------------------------------------------------- CPU oracle
     if not args.no_cpu_baseline and rank == 0:
@@ -666,6 +676,8 @@ def bench_batch(B, W, torch, peaks, flush, reps, fp32_peak):
              "4096 random mixed circuits, n = floor(exp(U[ln 4, ln 15))), depth U{5..40}"),
             ("random_4096_n14", W.batch_circuits_fixed_n(4096, 14, seed_tag=5),
              "4096 random mixed circuits, all n = 14, depth U{5..40}")]:
+        from paper_2305_14398_gb300 import autotune
+        tuned = autotune.tune_cta_threads(circs)
         b = B.tqs_batch_create_packed(*B.pack_ops(circs))
         count, total, _, steps_total, prog_bytes = B.tqs_batch_info(b, extra=True)
         states = torch.empty(total, dtype=torch.complex64, device="cuda")
@@ -696,6 +708,8 @@ def bench_batch(B, W, torch, peaks, flush, reps, fp32_peak):
                     "algorithmic_flops": flops,
                     "peak_source": "measured FP32 FMA microkernel (measured_peaks)"},
             "norm_max_err": float((norms.cpu() - 1.0).abs().max()),
+            "cta_threads": {"chosen": tuned["value"], "autotune_ms": tuned["timings_ms"],
+                            "source": tuned["source"]},
         }
         B.tqs_batch_destroy(b)
         del states, probs, norms
@@ -710,9 +724,12 @@ def bench_fsv(B, W, torch, hbm_peak, fp32_peak):
     bytes per pass; the ALU fraction counts the algorithmic FP32 flops of the
     per-gate update (eq. 12).  Also: the per-gate form (one pass per gate) at
     n = 24, and the fused kernel beside the tiled passes at n = 16."""
+    from paper_2305_14398_gb300 import autotune
     out = {"workload": "random layered: 10 x (U3 on every qubit + CNOTs on n/2 seeded pairs)"}
+    tiles = {}
     for n, reps in ((24, 5), (28, 3), (30, 2)):
         ops = W.random_layered(n, 10, (9, n))
+        tiles[n] = autotune.tune_fsv_tile(n, ops, reps=2 if n < 28 else 1)
         c = B.circuit_from_ops(n, ops)
         st = torch.zeros(1 << n, dtype=torch.complex64, device="cuda")
         st[0] = 1.0
@@ -728,7 +745,8 @@ def bench_fsv(B, W, torch, hbm_peak, fp32_peak):
         sec = s.elapsed_time(e) / 1e3 / reps
         alg = 16.0 * (1 << n) * passes
         flops = algorithmic_flops(n, ops)
-        out[f"n{n}"] = {"gates": len(ops), "passes": passes, "tile_bits": tile, "ms": 1e3 * sec,
+        out[f"n{n}"] = {"gates": len(ops), "passes": passes, "tile_bits": tile,
+                        "tile_autotune_ms": tiles[n]["timings_ms"], "ms": 1e3 * sec,
                         "gates_per_s": len(ops) / sec,
                         "hbm": {"achieved_gbs": alg / sec / 1e9, "peak": hbm_peak,
                                 "frac": alg / sec / 1e9 / hbm_peak, "algorithmic_bytes": alg},
@@ -738,6 +756,7 @@ def bench_fsv(B, W, torch, hbm_peak, fp32_peak):
         B.tqs_circuit_destroy(c)
         del st
         torch.cuda.empty_cache()
+    B.tqs_set_option(B.OPT_FSV_TILE_Q, 0, 0)  # the automatic choice for the legs below
     # The per-gate form of eq. 12 (one pass over the state per gate) at n = 24,
     # and the fused kernel on the same kind of circuit at n = 16 (its largest
     # size) beside the tiled passes.
@@ -816,10 +835,22 @@ def bench_chain(B, W, torch, peaks, mpeaks):
            "tf32_peak_tflops": tf32, "tf32_peak_source": "measured TF32 cuBLAS burst (measured_peaks)"}
     names = {B.PREC_TC_BF16X3: "tc_bf16x3", B.PREC_TC_TF32X3: "tc_tf32x3",
              B.PREC_FP32_SIMT: "fp32_simt"}
+    from paper_2305_14398_gb300 import autotune
+    group13 = None
     for n, prec, reps in [(12, B.PREC_TC_BF16X3, 3), (12, B.PREC_TC_TF32X3, 2),
                           (12, B.PREC_FP32_SIMT, 1), (13, B.PREC_TC_BF16X3, 2),
                           (14, B.PREC_TC_BF16X3, 1)]:
         ops = W.random_layered(n, 20, (2, n))
+        group = None
+        if prec != B.PREC_FP32_SIMT:
+            if n <= 13:
+                group = autotune.tune_chain_group(n, ops, prec)
+                if n == 13:
+                    group13 = group
+            else:  # one product at n = 14 takes about 50 ms: the n = 13 choice
+                B.tqs_set_option(B.OPT_CHAIN_GROUP, 0, group13["value"] if group13 else 16)
+                group = {"value": B.tqs_get_option(B.OPT_CHAIN_GROUP, 0), "timings_ms": {},
+                         "source": "the n = 13 choice"}
         c = B.circuit_from_ops(n, ops)
         U = torch.empty((1 << n, 1 << n), dtype=torch.complex64, device="cuda")
         B.tqs_circuit_unitary(c, prec, U)
@@ -836,6 +867,9 @@ def bench_chain(B, W, torch, peaks, mpeaks):
         key = f"n{n}_{names[prec]}"
         rec = {"ms": 1e3 * sec, "gemms": gemms,
                "useful_complex_gflops": 8.0 * N ** 3 * gemms / sec / 1e9}
+        if group is not None:
+            rec["raster_group"] = {"chosen": group["value"], "autotune_ms": group["timings_ms"],
+                                   "source": group["source"]}
         if prec != B.PREC_FP32_SIMT:
             issued = 18.0 * N ** 3 * gemms / sec / 1e12  # 3 real GEMMs x 3 split products
             rec["issued_tensor_tflops"] = issued

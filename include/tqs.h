@@ -562,6 +562,22 @@ tqs_status tqs_check_violations(uint32_t* count, int reset);
  * (double)x*x + (double)y*y).  The states and the FP64 norm do not depend on
  * it; tqs_probabilities always gives the exact form. */
 #define TQS_OPT_EXACT_PROBS 6
+/* Launch-shape options for the autotuner (results never depend on them
+ * beyond the order of floating-point reductions noted):
+ * TQS_OPT_CTA_THREADS, key = 0: threads of the one-CTA team that runs a
+ *   circuit of 12..14 qubits, 256 or 512 (default 512).  States and
+ *   probabilities are bitwise the same; the FP64 norm's reduction order
+ *   follows the team size.
+ * TQS_OPT_FSV_TILE_Q, key = 0: tile bits of tqs_simulate_fsv's passes, 0
+ *   (default: 13 from 24 qubits on, else 12) or 10..13.  Fewer tile bits mean
+ *   more passes over HBM but more tiles to spread over the SMs.
+ * TQS_OPT_CHAIN_GROUP, key = 0: output-tile rows per raster band of the
+ *   tensor-core chain's GEMM grid, 1..64 (default 16); consecutive CTAs walk
+ *   down a band, so CTAs resident at once share operand panels in L2.
+ *   Results are bitwise the same. */
+#define TQS_OPT_CTA_THREADS 7
+#define TQS_OPT_FSV_TILE_Q 8
+#define TQS_OPT_CHAIN_GROUP 9
 
 tqs_status tqs_set_option(int option, int key, int64_t value);
 tqs_status tqs_get_option(int option, int key, int64_t* value);

@@ -1,4 +1,6 @@
-"""Autotuner for the batched fused step kernel's launch shape.
+"""Autotuner for the launch shapes: the batched fused step kernel's warp
+class (below), the one-CTA team, the full-state-vector tiles and the
+tensor-core chain's raster (at the end of the file).
 
 The warp-class kernel (circuits of n <= 11, each state in a shared-memory slice
 of 2^q amplitudes) runs one or two warps per circuit and groups 1..16 warps per
@@ -105,3 +107,99 @@ def tune_warps_per_cta(circuits, sample: int = 16384, reps: int = 5, use_cache: 
     if use_cache:
         _save(cache)
     return {"q": q, "team_warps": tw, "warps": w, "timings_ms": timings, "source": "measured"}
+
+
+# ----------------------------------------------------------------------------
+# Further launch parameters, each timed on the workload it serves (CUDA
+# events, best of a few runs) and cached by GPU name, size and batch size:
+# * the one-CTA team's thread count for circuits of 12..14 qubits
+#   (TQS_OPT_CTA_THREADS: 256 or 512);
+# * the tile bits of the full-state-vector passes (TQS_OPT_FSV_TILE_Q);
+# * the raster band of the tensor-core chain's GEMM grid (TQS_OPT_CHAIN_GROUP).
+# None of them changes a state or a unitary (the CTA team's FP64 norm follows
+# the team size in its reduction order only).
+
+def _best_ms(fn, reps):
+    import torch
+    fn()
+    torch.cuda.synchronize()
+    best = float("inf")
+    for _ in range(reps):
+        s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        s.record()
+        fn()
+        e.record()
+        torch.cuda.synchronize()
+        best = min(best, s.elapsed_time(e))
+    return best
+
+
+def _tune(key, option, candidates, run, reps, use_cache):
+    """Time run() under each candidate value of `option`, set the fastest,
+    and cache it under `key`."""
+    cache = _load() if use_cache else {}
+    if key in cache:
+        v = int(cache[key]["value"])
+        B.tqs_set_option(option, 0, v)
+        return {"value": v, "timings_ms": cache[key]["timings_ms"], "source": "cache"}
+    old = B.tqs_get_option(option, 0)
+    timings = {}
+    try:
+        for v in candidates:
+            B.tqs_set_option(option, 0, v)
+            timings[str(v)] = _best_ms(run, reps)
+    except Exception:
+        B.tqs_set_option(option, 0, old)
+        raise
+    v = int(min(timings, key=timings.get))
+    B.tqs_set_option(option, 0, v)
+    if use_cache:
+        cache[key] = {"value": v, "timings_ms": timings}
+        _save(cache)
+    return {"value": v, "timings_ms": timings, "source": "measured"}
+
+
+def tune_cta_threads(circuits, reps: int = 3, use_cache: bool = True):
+    """Threads of the one-CTA team (circuits of 12..14 qubits) for this batch."""
+    import torch
+    ns = [n for n, _ in circuits if 12 <= max(n, 4) <= 14]
+    if not ns:
+        return {"value": None, "timings_ms": {}, "source": "no circuits of 12..14 qubits"}
+    key = f"v3|{torch.cuda.get_device_name()}|cta|n{max(ns)}|{len(circuits)}"
+    b = B.tqs_batch_create_packed(*B.pack_ops(list(circuits)))
+    try:
+        count, total, _ = B.tqs_batch_info(b)
+        st = torch.empty(total, dtype=torch.complex64, device="cuda")
+        nm = torch.empty(count, dtype=torch.float64, device="cuda")
+        return _tune(key, B.OPT_CTA_THREADS, (256, 512),
+                     lambda: B.tqs_batch_run(b, st, None, nm, use_graph=False), reps, use_cache)
+    finally:
+        B.tqs_batch_destroy(b)
+
+
+def tune_fsv_tile(n, ops, reps: int = 2, use_cache: bool = True):
+    """Tile bits of the full-state-vector passes for this circuit size."""
+    import torch
+    key = f"v3|{torch.cuda.get_device_name()}|fsv|n{n}|{len(ops)}"
+    c = B.circuit_from_ops(n, ops)
+    try:
+        st = torch.zeros(1 << n, dtype=torch.complex64, device="cuda")
+        st[0] = 1.0
+        cands = tuple(t for t in (11, 12, 13) if t <= n)
+        return _tune(key, B.OPT_FSV_TILE_Q, cands, lambda: B.tqs_simulate_fsv(c, st), reps, use_cache)
+    finally:
+        B.tqs_circuit_destroy(c)
+
+
+def tune_chain_group(n, ops, prec, reps: int = 2, use_cache: bool = True):
+    """Raster band of the tensor-core chain for this size and precision."""
+    import torch
+    key = f"v3|{torch.cuda.get_device_name()}|chain|n{n}|p{prec}|{len(ops)}"
+    c = B.circuit_from_ops(n, ops)
+    try:
+        U = torch.empty((1 << n, 1 << n), dtype=torch.complex64, device="cuda")
+        cands = tuple(g for g in (4, 8, 16, 32) if g <= (1 << n) // 128)
+        return _tune(key, B.OPT_CHAIN_GROUP, cands, lambda: B.tqs_circuit_unitary(c, prec, U), reps,
+                     use_cache)
+    finally:
+        B.tqs_circuit_destroy(c)

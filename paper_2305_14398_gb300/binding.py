@@ -513,6 +513,9 @@ OPT_FSV_MAX_GATES = 3
 OPT_MULTI_CTAS = 4
 OPT_HOST_WRITES = 5
 OPT_EXACT_PROBS = 6
+OPT_CTA_THREADS = 7
+OPT_FSV_TILE_Q = 8
+OPT_CHAIN_GROUP = 9
 
 
 def tqs_set_option(option: int, key: int, value: int) -> None:

@@ -130,8 +130,8 @@ tqs_status tqs_batch_create_packed(int count, const int32_t* h_nq, const int64_t
   // Circuits are independent: compile them on all host cores.  Worker w takes
   // the contiguous range [w C / W, (w + 1) C / W) and compiles into one reused
   // Program, appending the result to its own segment, reserved up front from
-  // the gate counts of its range (fusion only shrinks a program: at most one
-  // op per gate and one pass per gate plus one), so it never reallocates.
+  // the gate counts of its range (about one op and at most one pass per gate;
+  // a program rarely needs more, and then the segment grows).
   // Each worker records its first failure; the lowest failing circuit index
   // is reported.
   int width = static_cast<int>(std::max(1u, std::thread::hardware_concurrency()));
@@ -153,7 +153,7 @@ tqs_status tqs_batch_create_packed(int count, const int32_t* h_nq, const int64_t
     const int64_t span = h_gate_off[hi] - h_gate_off[lo];
     if (span >= 0) {
       sg.passes.reserve(static_cast<size_t>(span) + static_cast<size_t>(hi - lo));
-      sg.ops.reserve(static_cast<size_t>(span));
+      sg.ops.reserve(static_cast<size_t>(span) + 4 * static_cast<size_t>(hi - lo));
     }
     static thread_local std::vector<Gate> gates;
     static thread_local std::vector<int> last;
@@ -375,7 +375,7 @@ tqs_status tqs_batch_launch_info(const tqs_batch* b, int size_class, int* jobs, 
   if (jobs) *jobs = n_jobs;
   if (grid) *grid = n_jobs ? lp.grid : 0;
   const int nthreads = (lp.team == TEAM_WARP || lp.team == TEAM_PAIR) ? 32 * lp.warps
-                       : lp.team == TEAM_CTA ? kCtaThreads : kGlobalThreads;
+                       : lp.team == TEAM_CTA ? 32 * lp.warps : kGlobalThreads;
   if (threads) *threads = n_jobs ? nthreads : 0;
   if (teams) *teams = n_jobs ? lp.grid * per_cta : 0;
   return TQS_OK;
@@ -514,7 +514,7 @@ static tqs_status unitary_block(tqs_circuit* c, int prec, int col0, int ncols, t
   TQS_CUDA(c->d_err.ensure(sizeof(int)), "tqs_circuit_unitary: cudaMalloc");
   TQS_CUDA(cudaMemsetAsync(c->d_err.p, 0, sizeof(int), s), "tqs_circuit_unitary: memset");
   TQS_CUDA(chain_tc(c->d_factors.as<StepFactor>(), c->steps.data(), c->nsteps, c->n, prec, col0, ncols,
-                    U, ldu, c->d_chain.p, c->d_err.as<int>(), s),
+                    U, ldu, c->d_chain.p, c->d_err.as<int>(), g_chain_group.load(), s),
            "tqs_circuit_unitary: tensor-core chain");
   int err = 0;
   TQS_CUDA(cudaMemcpyAsync(&err, c->d_err.p, sizeof(int), cudaMemcpyDeviceToHost, s),

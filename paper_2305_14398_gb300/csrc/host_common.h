@@ -311,6 +311,7 @@ struct FsvPassInfo {
 struct FsvProgram {
   int T = 0;  // tile bits per pass
   int max_gates = 0;  // gates per pass at most (0: no limit) it was compiled with
+  int tile_opt = 0;   // TQS_OPT_FSV_TILE_Q it was compiled with
   std::vector<FsvPassInfo> passes;
   std::vector<Program> progs;  // one per pass
 };
@@ -763,6 +764,12 @@ inline std::atomic<int> g_warps_for_q[16] = {4, 4, 4, 4, 4, 4, 4, 4, 4, 4, 4, 4,
 // Gates per full-state-vector pass at most (0: as many as fit a tile).
 inline std::atomic<int> g_fsv_max_gates{0};
 inline std::atomic<int> g_team_warps_for_q[16] = {1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1};
+// TQS_OPT_CTA_THREADS: threads of the CTA team (circuits of 12..14 qubits).
+inline std::atomic<int> g_cta_threads{kCtaThreads};
+// TQS_OPT_FSV_TILE_Q: tile bits of the full-state-vector passes (0: automatic).
+inline std::atomic<int> g_fsv_tile_q{0};
+// TQS_OPT_CHAIN_GROUP: tile rows per raster band of the tensor-core chain.
+inline std::atomic<int> g_chain_group{16};
 
 inline LaunchPlan plan_for(int team, int max_nint, int jobs, int warps_hint) {
   LaunchPlan lp{team, 1, 4, 1};
@@ -787,7 +794,8 @@ inline LaunchPlan plan_for(int team, int max_nint, int jobs, int warps_hint) {
     lp.grid = std::max(1, std::min(want, per_sm * device_sms()));
   } else if (team == TEAM_CTA) {
     lp.slice_q = std::max(4, max_nint);
-    const int per_sm = std::max(1, fused_max_ctas_per_sm(TEAM_CTA, 1, lp.slice_q));
+    lp.warps = g_cta_threads.load() / 32;
+    const int per_sm = std::max(1, fused_max_ctas_per_sm(TEAM_CTA, lp.warps, lp.slice_q));
     lp.grid = std::max(1, std::min(jobs, per_sm * device_sms()));
   } else {
     lp.slice_q = kGlobalSlotQ;

@@ -99,12 +99,15 @@ tqs_status tqs_batch_sample(tqs_batch* b, const double* d_probs, int shots, cons
 // bits, a custom unitary's bits), at most T in all.  Controls and diagonal
 // factors may sit on any bit.  Unused tile slots take the lowest free bits.
 
-static tqs_status compile_fsv(int n, const std::vector<Gate>& gates, int max_gates, FsvProgram& P) {
+static tqs_status compile_fsv(int n, const std::vector<Gate>& gates, int max_gates, int tile_opt,
+                              FsvProgram& P) {
   P = FsvProgram();
   P.max_gates = max_gates;
-  // 2^13-amplitude tiles from 24 qubits on (fewer passes); below that 2^12,
-  // so that a state still spreads over enough tiles to fill the GPU
-  const int T = std::min(n, n >= 24 ? kFsvTileQ : kFsvTileQ - 1);
+  P.tile_opt = tile_opt;
+  // Automatic: 2^13-amplitude tiles from 24 qubits on (fewer passes); below
+  // that 2^12, so that a state still spreads over enough tiles to fill the
+  // GPU.  TQS_OPT_FSV_TILE_Q sets the tile bits instead.
+  const int T = std::min(n, tile_opt > 0 ? tile_opt : (n >= 24 ? kFsvTileQ : kFsvTileQ - 1));
   const int nlow = std::min(T, kFsvLowQ);
   P.T = T;
   const uint64_t low = (uint64_t(1) << nlow) - 1;
@@ -202,8 +205,9 @@ tqs_status tqs_simulate_fsv(tqs_circuit* c, tqs_c64* d_state, void* stream) {
     return tqs_simulate(c, c->d_collapse.as<tqs_c64>(), d_state, nullptr, nullptr, stream);
   }
   const int max_gates = g_fsv_max_gates.load();
-  if (!c->fsv_valid || c->fsv.max_gates != max_gates) {
-    tqs_status st = compile_fsv(c->n, c->gates, max_gates, c->fsv);
+  const int tile_opt = g_fsv_tile_q.load();
+  if (!c->fsv_valid || c->fsv.max_gates != max_gates || c->fsv.tile_opt != tile_opt) {
+    tqs_status st = compile_fsv(c->n, c->gates, max_gates, tile_opt, c->fsv);
     if (st != TQS_OK) return st;
     c->fsv_img = Image();
     for (const Program& tp : c->fsv.progs) c->fsv_img.add(tp, 0);
@@ -234,8 +238,9 @@ tqs_status tqs_fsv_passes(tqs_circuit* c, int* n_passes, int* tile_bits) {
   FsvProgram local;
   const FsvProgram* P = &c->fsv;
   const int max_gates = g_fsv_max_gates.load();
-  if (!c->fsv_valid || c->fsv.max_gates != max_gates) {
-    tqs_status st = compile_fsv(c->n, c->gates, max_gates, local);
+  const int tile_opt = g_fsv_tile_q.load();
+  if (!c->fsv_valid || c->fsv.max_gates != max_gates || c->fsv.tile_opt != tile_opt) {
+    tqs_status st = compile_fsv(c->n, c->gates, max_gates, tile_opt, local);
     if (st != TQS_OK) return st;
     P = &local;
   }

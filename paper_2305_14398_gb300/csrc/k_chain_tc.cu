@@ -40,7 +40,7 @@ constexpr int kStageBytes = 4 * kTileBytes;    // A hi, A lo, B hi, B lo
 constexpr int kGemmThreads = 192;
 constexpr uint32_t kTmemCols = 512;            // 3 accumulators x 128 columns
 constexpr size_t kGemmSmem = size_t(kStages) * kStageBytes + 1024 + 256;
-constexpr int kGroupM = 16;                    // tile rows per raster band
+constexpr int kMaxGroupM = 64;                 // tile rows per raster band at most
 
 // Operand precision: the element type of the planes, the MMA kind, and the
 // hi/lo split of an FP32 value.
@@ -83,6 +83,7 @@ struct GemmParams {
   E* planes;       // [6][M][N] output planes (final_step == 0)
   float2* u;       // final_step == 1: U block, entry (r, j) at u[r * ldu + j], r < N, j < M
   int64_t ldu;
+  int group;       // tile rows per raster band (1..kMaxGroupM)
   int* err;
 };
 
@@ -122,15 +123,15 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
   uint32_t* tmem_holder = reinterpret_cast<uint32_t*>(tmem_full + 1);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  // Grouped raster: consecutive CTAs walk down a band of kGroupM tile rows
+  // Grouped raster: consecutive CTAs walk down a band of P.group tile rows
   // before moving right, so the CTAs resident at one time share a few A and B
   // panels in L2 instead of streaming all of B once per tile row.
   const int num_m = P.M / BM, num_n = P.N / BN;
   const int pid = blockIdx.x;
-  const int band = pid / (kGroupM * num_n);
-  const int first_m = band * kGroupM;
-  const int gsize = min(num_m - first_m, kGroupM);
-  const int in_band = pid - band * kGroupM * num_n;
+  const int band = pid / (P.group * num_n);
+  const int first_m = band * P.group;
+  const int gsize = min(num_m - first_m, P.group);
+  const int in_band = pid - band * P.group * num_n;
   const int tile_m = (first_m + in_band % gsize) * BM;  // rows of V = rows of V'
   const int tile_n = (in_band / gsize) * BN;            // rows of S = columns of V'
   const int iters = (P.N / BK) * 3;                     // (k block, real GEMM j) pairs
@@ -368,7 +369,7 @@ cudaError_t launch_gen(const StepFactor* d_factors, const StepDesc& st, int n, i
 template <int PREC>
 cudaError_t chain_tc_impl(const StepFactor* d_factors, const StepDesc* steps, int nsteps, int n,
                           int col0, int ncols, float2* d_U, int64_t ldu, void* scratch, int* d_err,
-                          cudaStream_t s) {
+                          int group, cudaStream_t s) {
   using E = typename Prec<PREC>::E;
   const int N = 1 << n;
   const size_t MN = size_t(ncols) * N;  // the block's V planes: ncols rows of V
@@ -396,6 +397,7 @@ cudaError_t chain_tc_impl(const StepFactor* d_factors, const StepDesc* steps, in
     P.planes = cur0 ? V1 : V0;
     P.u = d_U;
     P.ldu = ldu;
+    P.group = group;
     P.err = d_err;
     const int grid = (N / BN) * (ncols / BM);
     chain_gemm_kernel<PREC><<<grid, kGemmThreads, kGemmSmem, s>>>(cur0 ? mV0 : mV1, mS, P);
@@ -444,16 +446,16 @@ size_t chain_tc_scratch_bytes(int n, int prec, int ncols) {
 // d_U[r * ldu + j].  n >= 7; col0 and ncols multiples of 128.
 cudaError_t chain_tc(const StepFactor* d_factors, const StepDesc* steps, int nsteps, int n,
                      int prec, int col0, int ncols, float2* d_U, int64_t ldu, void* scratch,
-                     int* d_err, cudaStream_t s) {
+                     int* d_err, int group, cudaStream_t s) {
   if (n < 7 || nsteps < 2 || col0 % BM || ncols % BM || ncols < BM || col0 + ncols > (1 << n) ||
-      ldu < ncols)
+      ldu < ncols || group < 1 || group > kMaxGroupM)
     return cudaErrorInvalidValue;
   if (prec == TQS_PREC_TC_BF16X3)
     return chain_tc_impl<TQS_PREC_TC_BF16X3>(d_factors, steps, nsteps, n, col0, ncols, d_U, ldu,
-                                             scratch, d_err, s);
+                                             scratch, d_err, group, s);
   if (prec == TQS_PREC_TC_TF32X3)
     return chain_tc_impl<TQS_PREC_TC_TF32X3>(d_factors, steps, nsteps, n, col0, ncols, d_U, ldu,
-                                             scratch, d_err, s);
+                                             scratch, d_err, group, s);
   return cudaErrorInvalidValue;
 }
 

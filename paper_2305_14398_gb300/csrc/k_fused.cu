@@ -933,7 +933,7 @@ size_t fused_smem_bytes(int team, int warps_per_cta, int slice_q) {
 
 int fused_threads(int team, int warps_per_cta) {
   if (team == TEAM_WARP || team == TEAM_PAIR) return 32 * warps_per_cta;
-  if (team == TEAM_CTA) return kCtaThreads;
+  if (team == TEAM_CTA) return warps_per_cta > 0 ? 32 * warps_per_cta : kCtaThreads;
   return kGlobalThreads;
 }
 

@@ -472,6 +472,24 @@ tqs_status tqs_set_option(int option, int key, int64_t value) {
     g_fsv_max_gates.store(static_cast<int>(value));
     return TQS_OK;
   }
+  if (option == TQS_OPT_CTA_THREADS) {
+    if (key != 0) return fail(TQS_ERR_ARG, "tqs_set_option: key %d of TQS_OPT_CTA_THREADS is not 0", key);
+    if (value != 256 && value != 512) return fail(TQS_ERR_ARG, "tqs_set_option: CTA threads %lld is not 256 or 512", static_cast<long long>(value));
+    g_cta_threads.store(static_cast<int>(value));
+    return TQS_OK;
+  }
+  if (option == TQS_OPT_FSV_TILE_Q) {
+    if (key != 0) return fail(TQS_ERR_ARG, "tqs_set_option: key %d of TQS_OPT_FSV_TILE_Q is not 0", key);
+    if (value != 0 && (value < 10 || value > kFsvTileQ)) return fail(TQS_ERR_ARG, "tqs_set_option: tile bits %lld not 0 or in [10, %d]", static_cast<long long>(value), kFsvTileQ);
+    g_fsv_tile_q.store(static_cast<int>(value));
+    return TQS_OK;
+  }
+  if (option == TQS_OPT_CHAIN_GROUP) {
+    if (key != 0) return fail(TQS_ERR_ARG, "tqs_set_option: key %d of TQS_OPT_CHAIN_GROUP is not 0", key);
+    if (value < 1 || value > 64) return fail(TQS_ERR_ARG, "tqs_set_option: raster band %lld outside [1, 64]", static_cast<long long>(value));
+    g_chain_group.store(static_cast<int>(value));
+    return TQS_OK;
+  }
   return fail(TQS_ERR_ARG, "tqs_set_option: unknown option %d", option);
 }
 
@@ -505,6 +523,12 @@ tqs_status tqs_get_option(int option, int key, int64_t* value) {
   if (option == TQS_OPT_FSV_MAX_GATES) {
     if (key != 0) return fail(TQS_ERR_ARG, "tqs_get_option: key %d of TQS_OPT_FSV_MAX_GATES is not 0", key);
     *value = g_fsv_max_gates.load();
+    return TQS_OK;
+  }
+  if (option == TQS_OPT_CTA_THREADS || option == TQS_OPT_FSV_TILE_Q || option == TQS_OPT_CHAIN_GROUP) {
+    if (key != 0) return fail(TQS_ERR_ARG, "tqs_get_option: key %d of option %d is not 0", key, option);
+    *value = option == TQS_OPT_CTA_THREADS ? g_cta_threads.load()
+             : option == TQS_OPT_FSV_TILE_Q ? g_fsv_tile_q.load() : g_chain_group.load();
     return TQS_OK;
   }
   return fail(TQS_ERR_ARG, "tqs_get_option: unknown option %d", option);

@@ -210,9 +210,10 @@ cudaError_t launch_matvec(const float2* d_S, const float2* d_x, float2* d_y, int
 // Both forms compute the columns [col0, col0 + ncols) of U = S_m ... S_1 into
 // d_U[r * ldu + j] = U[r][col0 + j] (the whole U: col0 = 0, ncols = ldu = 2^n).
 size_t chain_tc_scratch_bytes(int n, int prec, int ncols);
+// group: output-tile rows per raster band of the GEMM grid (L2 reuse).
 cudaError_t chain_tc(const StepFactor* d_factors, const StepDesc* steps, int nsteps, int n,
                      int prec, int col0, int ncols, float2* d_U, int64_t ldu, void* scratch,
-                     int* d_err, cudaStream_t s);
+                     int* d_err, int group, cudaStream_t s);
 size_t chain_simt_scratch_bytes(int n, int ncols);
 cudaError_t chain_simt(const StepFactor* d_factors, const StepDesc* steps, int nsteps, int n,
                        int col0, int ncols, float2* d_U, int64_t ldu, void* scratch, cudaStream_t s);

@@ -3,7 +3,13 @@
     python -m paper_2305_14398_gb300.prof COUNT KIND REPS [noprobs] [TWxW]
 
 chain: the 40-step random layered circuit-unitary chain at n = COUNT
-       (tensor-core BF16x3);
+       (tensor-core BF16x3); chain_tf32, chain_simt: the same in TF32x3 /
+       FP32 SIMT;
+probs: tqs_probabilities on a random 2^COUNT state;
+sample: 64 inverse-CDF shots per circuit of COUNT paper-shaped 11-qubit
+       circuits (tqs_batch_sample);
+multi: one random layered circuit of COUNT = 15 or 16 qubits on cooperating
+       CTAs (tqs_simulate);
 plain: the plain materialised form (tqs_simulate_plain) on one circuit of each
        paper kind at n = COUNT, REPS times;
 fsv:   the full-state-vector backend on a random layered circuit
@@ -80,6 +86,63 @@ def plain(n, reps):
         B.tqs_circuit_destroy(h)
 
 
+def chain_prec(n, reps, prec):
+    """The 40-step random layered chain at n in a given precision."""
+    ops = W.random_layered(n, 20, (2, n))
+    c = B.circuit_from_ops(n, ops)
+    U = torch.empty((1 << n, 1 << n), dtype=torch.complex64, device="cuda")
+    for _ in range(reps):
+        B.tqs_circuit_unitary(c, prec, U)
+    torch.cuda.synchronize()
+    print("chain", n, "prec", prec, "done")
+    B.tqs_circuit_destroy(c)
+
+
+def probs(n, reps):
+    """tqs_probabilities on a seeded random 2^n state."""
+    g = W.rng(31, n)
+    psi = torch.from_numpy((g.normal(size=1 << n) + 1j * g.normal(size=1 << n)).astype("complex64")).cuda()
+    p = torch.empty(1 << n, dtype=torch.float64, device="cuda")
+    tot = torch.empty(1, dtype=torch.float64, device="cuda")
+    for _ in range(reps):
+        B.tqs_probabilities(psi, n, p, tot)
+    torch.cuda.synchronize()
+    print("probs", n, "sum %.6f" % float(tot.cpu()[0]))
+
+
+def sample(count, reps, shots=64):
+    """tqs_batch_sample: `shots` draws per circuit from the probabilities of a
+    batch of `count` paper-shaped 11-qubit circuits."""
+    circs = [(11, ops) for _, ops in W.paper_mix(11, count)]
+    b = B.tqs_batch_create_packed(*B.pack_ops(circs))
+    c, total, _ = B.tqs_batch_info(b)
+    st = torch.empty(total, dtype=torch.complex64, device="cuda")
+    pr = torch.empty(total, dtype=torch.float64, device="cuda")
+    B.tqs_batch_run(b, st, pr, None, use_graph=False)
+    gen = torch.Generator(device="cuda")
+    gen.manual_seed(14398)
+    u = torch.rand(c * shots, dtype=torch.float64, device="cuda", generator=gen)
+    out = torch.empty(c * shots, dtype=torch.int64, device="cuda")
+    for _ in range(reps):
+        B.tqs_batch_sample(b, pr, shots, u, out)
+    torch.cuda.synchronize()
+    print("sample", count, "done")
+    B.tqs_batch_destroy(b)
+
+
+def multi(n, reps):
+    """One random layered circuit of n = 15 or 16 qubits on cooperating CTAs
+    (the fused kernel's TEAM_MULTI form)."""
+    ops = W.random_layered(n, 10, (9, n))
+    c = B.circuit_from_ops(n, ops)
+    out = torch.empty(1 << n, dtype=torch.complex64, device="cuda")
+    for _ in range(reps):
+        B.tqs_simulate(c, out)
+    torch.cuda.synchronize()
+    print("multi", n, "done")
+    B.tqs_circuit_destroy(c)
+
+
 def main(argv):
     count = int(argv[1]) if len(argv) > 1 else 2048
     kind = argv[2] if len(argv) > 2 else "mix"
@@ -92,6 +155,16 @@ def main(argv):
             B.tqs_set_option(B.OPT_WARPS_PER_CTA, 11, w)
     if kind == "chain":
         return chain(count, reps)
+    if kind == "chain_tf32":
+        return chain_prec(count, reps, B.PREC_TC_TF32X3)
+    if kind == "chain_simt":
+        return chain_prec(count, reps, B.PREC_FP32_SIMT)
+    if kind == "probs":
+        return probs(count, reps)
+    if kind == "sample":
+        return sample(count, reps)
+    if kind == "multi":
+        return multi(count, reps)
     if kind == "fsv":
         return fsv(count, reps)
     if kind == "plain":

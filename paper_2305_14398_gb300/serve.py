@@ -12,6 +12,7 @@ Requests are packed into host arrays before the clock starts (marshalling).
 from __future__ import annotations
 
 import argparse
+import gc
 import json
 import time
 
@@ -34,12 +35,21 @@ def replay(requests, budget_bytes: int, max_inflight: int = 4, max_batch: int = 
     norms = np.full(count, np.nan)
     states = {} if keep_states else None
     polls = 0
+    busy_s = 0.0  # wall time with at least one batch in flight (device busy)
+    # no cyclic garbage collection while the clock runs: a collection over a
+    # large caller heap pauses this polling loop for tens of milliseconds
+    gc_was_on = gc.isenabled()
+    gc.disable()
     try:
         t0 = time.perf_counter()
         nxt = 0
         done = 0
+        last = 0.0
         while done < count:
             now = time.perf_counter() - t0
+            if B.tqs_server_stats(sv)["inflight"] > 0:
+                busy_s += now - last
+            last = now
             if now > max_seconds:
                 raise RuntimeError(f"serving did not finish within {max_seconds} s")
             while nxt < count and arrivals[nxt] <= now:
@@ -60,6 +70,8 @@ def replay(requests, budget_bytes: int, max_inflight: int = 4, max_batch: int = 
         wall = time.perf_counter() - t0
         stats = B.tqs_server_stats(sv)
     finally:
+        if gc_was_on:
+            gc.enable()
         B.tqs_server_destroy(sv)
     lat = finish - arrivals
     return {
@@ -67,7 +79,24 @@ def replay(requests, budget_bytes: int, max_inflight: int = 4, max_batch: int = 
         "throughput_rps": count / wall, "p50_ms": 1e3 * float(np.percentile(lat, 50)),
         "p99_ms": 1e3 * float(np.percentile(lat, 99)), "mean_ms": 1e3 * float(np.mean(lat)),
         "max_ms": 1e3 * float(np.max(lat)), "polls": polls, "stats": stats,
+        "busy_frac": busy_s / wall,
     }
+
+
+def sweep(rates, requests_per_rate: int = 20000, budget_bytes: int = 120 * 10 ** 9,
+          max_inflight: int = 4, max_batch: int = 256, seed_tag: int = 4):
+    """Offered load against latency: one replay per Poisson rate (req/s) of the
+    same request mix; per rate p50 / p99 latency, completed req/s and the
+    busy fraction (wall time with a batch in flight)."""
+    out = []
+    for rate in rates:
+        reqs = W.serving_requests(requests_per_rate, float(rate), seed_tag=seed_tag)
+        r = replay(reqs, budget_bytes, max_inflight, max_batch)
+        out.append({"offered_rps": float(rate), "completed_rps": r["throughput_rps"],
+                    "p50_ms": r["p50_ms"], "p99_ms": r["p99_ms"], "max_ms": r["max_ms"],
+                    "busy_frac": r["busy_frac"],
+                    "norm_max_err": float(np.max(np.abs(r["norms"] - 1.0)))})
+    return out
 
 
 def main():

@@ -697,3 +697,22 @@ def test_server_cancel_host_side():
             assert e.value.name == status
     finally:
         B.tqs_server_destroy(sv)
+
+
+def test_launch_shape_options_validated():
+    """The autotuner's options take their documented ranges only (host check)."""
+    for opt, good, bad in [(B.OPT_CTA_THREADS, (256, 512), (128, 300, 1024)),
+                           (B.OPT_FSV_TILE_Q, (0, 10, 13), (9, 14, -1)),
+                           (B.OPT_CHAIN_GROUP, (1, 16, 64), (0, 65))]:
+        old = B.tqs_get_option(opt, 0)
+        try:
+            for v in good:
+                B.tqs_set_option(opt, 0, v)
+                assert B.tqs_get_option(opt, 0) == v
+            for v in bad:
+                with pytest.raises(B.TqsError):
+                    B.tqs_set_option(opt, 0, v)
+            with pytest.raises(B.TqsError):
+                B.tqs_set_option(opt, 1, good[0])
+        finally:
+            B.tqs_set_option(opt, 0, old)
