@@ -578,6 +578,18 @@ tqs_status tqs_check_violations(uint32_t* count, int reset);
 #define TQS_OPT_CTA_THREADS 7
 #define TQS_OPT_FSV_TILE_Q 8
 #define TQS_OPT_CHAIN_GROUP 9
+/* TQS_OPT_CHAIN_KCHUNK, key = 0: K (columns of S_k summed over) per
+ * accumulation chunk of the tensor-core chain's GEMMs, 0 or a multiple of 64
+ * up to 2^20.  The tensor cores accumulate in FP32 with truncation, which
+ * shrinks a sum of K products by a relative amount that grows with the number
+ * of accumulation steps; the GEMMs restart the TMEM accumulators every chunk
+ * and add the chunks' complex results in FP32 with rounding to nearest, which
+ * bounds that shrink by the chunk length.  0 (default): 512 for
+ * TQS_PREC_TC_BF16X3 and 256 for TQS_PREC_TC_TF32X3 (32 MMA accumulation
+ * steps either way); a value >= 2^n: all of K in one chunk (a shrink of about
+ * 2e-5 per product at K = 16384 in BF16x3).  Results depend on it only
+ * through rounding. */
+#define TQS_OPT_CHAIN_KCHUNK 10
 
 tqs_status tqs_set_option(int option, int key, int64_t value);
 tqs_status tqs_get_option(int option, int key, int64_t* value);

@@ -516,6 +516,7 @@ OPT_EXACT_PROBS = 6
 OPT_CTA_THREADS = 7
 OPT_FSV_TILE_Q = 8
 OPT_CHAIN_GROUP = 9
+OPT_CHAIN_KCHUNK = 10
 
 
 def tqs_set_option(option: int, key: int, value: int) -> None:

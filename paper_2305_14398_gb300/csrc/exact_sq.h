@@ -65,4 +65,15 @@ TQS_HD uint64_t sq_f32_as_f64_bits_general(uint32_t xbits) {
   return (static_cast<uint64_t>(E + 1023) << 52) | frac;
 }
 
+#if defined(__CUDACC__)
+// |x + iy|^2 correctly rounded to FP64 (bit-identical to (double)x * x +
+// (double)y * y): the two squares are exact FP64 values built with integer
+// operations, one FP64 add rounds their sum.
+__device__ __forceinline__ double sq_sum_f64(float x, float y) {
+  const double a = __longlong_as_double(static_cast<long long>(sq_f32_as_f64_bits(__float_as_uint(x))));
+  const double b = __longlong_as_double(static_cast<long long>(sq_f32_as_f64_bits(__float_as_uint(y))));
+  return __dadd_rn(a, b);
+}
+#endif
+
 }  // namespace tqs

@@ -770,6 +770,9 @@ inline std::atomic<int> g_cta_threads{kCtaThreads};
 inline std::atomic<int> g_fsv_tile_q{0};
 // TQS_OPT_CHAIN_GROUP: tile rows per raster band of the tensor-core chain.
 inline std::atomic<int> g_chain_group{16};
+// TQS_OPT_CHAIN_KCHUNK: K per accumulation chunk of the tensor-core chain
+// (0: the precision's default).
+inline std::atomic<int> g_chain_kchunk{0};
 
 inline LaunchPlan plan_for(int team, int max_nint, int jobs, int warps_hint) {
   LaunchPlan lp{team, 1, 4, 1};

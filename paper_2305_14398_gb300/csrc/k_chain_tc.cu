@@ -14,11 +14,14 @@
 //
 // GEMM tile: 128 x 128 output, K step one 128-byte swizzled row (64 BF16 or
 // 32 TF32), 3 stages of {A h, A l, B h, B l} (64 KiB each).  Warp 0 issues TMA, warp 1 issues the
-// MMAs (one thread), warps 2-5 read the three accumulators from TMEM and write
-// either the 6 planes of V' or, at the last step, U = V'^T as complex64.
+// MMAs (one thread), warps 2-9 read the three accumulators from TMEM once per
+// chunk of K (32 MMA accumulation steps by default), add the chunk's Re and Im into FP32 registers,
+// and at the end write either the 6 planes of V' or, at the last step,
+// U = V'^T as complex64.
 #include <cuda.h>
 #include <cuda_bf16.h>
 
+#include <algorithm>
 #include <mutex>
 
 #include "checked.h"
@@ -37,8 +40,10 @@ constexpr int kRowBytes = 128;                 // one swizzled row of K per tile
 constexpr int kStages = 3;
 constexpr int kTileBytes = BM * kRowBytes;     // 16 KiB, A and B tiles alike
 constexpr int kStageBytes = 4 * kTileBytes;    // A hi, A lo, B hi, B lo
-constexpr int kGemmThreads = 192;
-constexpr uint32_t kTmemCols = 512;            // 3 accumulators x 128 columns
+constexpr int kEpiWarps = 8;                   // 2 per TMEM lane quarter, half the columns each
+constexpr int kEpiCols = BN / 2;
+constexpr int kGemmThreads = 64 + 32 * kEpiWarps;  // TMA warp, MMA warp, epilogue
+constexpr uint32_t kTmemCols = 512;            // 4 slots of 128 columns for 3 accumulators
 constexpr size_t kGemmSmem = size_t(kStages) * kStageBytes + 1024 + 256;
 constexpr int kMaxGroupM = 64;                 // tile rows per raster band at most
 
@@ -51,6 +56,7 @@ template <>
 struct Prec<TQS_PREC_TC_BF16X3> {
   using E = __nv_bfloat16;
   static constexpr int BK = kRowBytes / 2;  // 64
+  static constexpr int kDefaultKChunk = 512;  // 32 MMAs of K = 16 per chunk
   static constexpr CUtensorMapDataType kTmaType = CU_TENSOR_MAP_DATA_TYPE_BFLOAT16;
   static __device__ __forceinline__ void mma(uint32_t d, uint64_t a, uint64_t b, uint32_t acc) {
     mma_bf16(d, a, b, idesc_bf16_f32(BM, BN), acc);
@@ -65,6 +71,7 @@ template <>
 struct Prec<TQS_PREC_TC_TF32X3> {
   using E = float;  // TF32 values (low 13 mantissa bits zero) in FP32 words
   static constexpr int BK = kRowBytes / 4;  // 32
+  static constexpr int kDefaultKChunk = 256;  // 32 MMAs of K = 8 per chunk
   static constexpr CUtensorMapDataType kTmaType = CU_TENSOR_MAP_DATA_TYPE_FLOAT32;
   static __device__ __forceinline__ void mma(uint32_t d, uint64_t a, uint64_t b, uint32_t acc) {
     mma_tf32(d, a, b, idesc_tf32_f32(BM, BN), acc);
@@ -84,6 +91,7 @@ struct GemmParams {
   float2* u;       // final_step == 1: U block, entry (r, j) at u[r * ldu + j], r < N, j < M
   int64_t ldu;
   int group;       // tile rows per raster band (1..kMaxGroupM)
+  int kchunk_blocks;  // k blocks per accumulation chunk (>= 1)
   int* err;
 };
 
@@ -119,8 +127,9 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
   uint8_t* stages = smem;
   uint64_t* full = reinterpret_cast<uint64_t*>(smem + kStages * kStageBytes);
   uint64_t* empty = full + kStages;
-  uint64_t* tmem_full = empty + kStages;
-  uint32_t* tmem_holder = reinterpret_cast<uint32_t*>(tmem_full + 1);
+  uint64_t* tmem_full = empty + kStages;   // a chunk's three accumulators are final
+  uint64_t* tmem_empty = tmem_full + 1;    // the epilogue has read a chunk's accumulators
+  uint32_t* tmem_holder = reinterpret_cast<uint32_t*>(tmem_empty + 1);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   // Grouped raster: consecutive CTAs walk down a band of P.group tile rows
@@ -134,7 +143,9 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
   const int in_band = pid - band * P.group * num_n;
   const int tile_m = (first_m + in_band % gsize) * BM;  // rows of V = rows of V'
   const int tile_n = (in_band / gsize) * BN;            // rows of S = columns of V'
-  const int iters = (P.N / BK) * 3;                     // (k block, real GEMM j) pairs
+  const int nkb = P.N / BK;                             // k blocks
+  const int kc = P.kchunk_blocks;                       // k blocks per accumulation chunk
+  const int nchunks = (nkb + kc - 1) / kc;
   (void)TQS_IX(tile_m, P.M - BM + 1);                   // whole tiles inside the M x N planes
   (void)TQS_IX(tile_n, P.N - BN + 1);
 
@@ -144,6 +155,7 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
       mbar_init(smem_u32(&empty[s]), 1);
     }
     mbar_init(smem_u32(tmem_full), 1);
+    mbar_init(smem_u32(tmem_empty), kEpiWarps);
     fence_barrier_init();
     fence_proxy_async();
   }
@@ -156,95 +168,155 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
   tc_fence_after();
   const uint32_t tmem_base = *tmem_holder;
 
+  // Order of the (k block, real GEMM j) pairs, the same for the producer and
+  // the MMA issuer: chunk by chunk, and inside a chunk all k blocks of GEMM 0,
+  // then of GEMM 1, then of GEMM 2.  Chunk c accumulates GEMM j in TMEM slot
+  // (3c + j) mod 4 (4 slots of 128 columns), so the next chunk's GEMM 0 runs
+  // in the slot its predecessor left free while the epilogue reads this one.
   if (warp == 0) {
     if (lane == 0) {
       prefetch_tmap(&tmA);
       prefetch_tmap(&tmB);
-      int issued = 0;
-      for (int it = 0; it < iters; ++it) {
-        const int s = it % kStages;
-        const uint32_t ph = (it / kStages) & 1;
-        if (it >= kStages && !mbar_wait(smem_u32(&empty[s]), ph ^ 1, P.err)) break;
-        const int kb = it / 3, j = it % 3;
-        const uint32_t st = smem_u32(stages + s * kStageBytes);
-        const uint32_t fb = smem_u32(&full[s]);
-        mbar_arrive_expect_tx(fb, kStageBytes);
-        tma_load_3d(st, &tmA, kb * BK, tile_m, 2 * j, fb);
-        tma_load_3d(st + kTileBytes, &tmA, kb * BK, tile_m, 2 * j + 1, fb);
-        tma_load_3d(st + 2 * kTileBytes, &tmB, kb * BK, tile_n, 2 * j, fb);
-        tma_load_3d(st + 3 * kTileBytes, &tmB, kb * BK, tile_n, 2 * j + 1, fb);
-        issued = it + 1;
+      int it = 0;
+      bool ok = true;
+      for (int c = 0; c < nchunks && ok; ++c) {
+        const int kb0 = c * kc, kb1 = min(nkb, kb0 + kc);
+        for (int j = 0; j < 3 && ok; ++j) {
+          for (int kb = kb0; kb < kb1; ++kb, ++it) {
+            const int s = it % kStages;
+            const uint32_t ph = (it / kStages) & 1;
+            if (it >= kStages && !mbar_wait(smem_u32(&empty[s]), ph ^ 1, P.err)) {
+              ok = false;
+              break;
+            }
+            const uint32_t st = smem_u32(stages + s * kStageBytes);
+            const uint32_t fb = smem_u32(&full[s]);
+            mbar_arrive_expect_tx(fb, kStageBytes);
+            tma_load_3d(st, &tmA, kb * BK, tile_m, 2 * j, fb);
+            tma_load_3d(st + kTileBytes, &tmA, kb * BK, tile_m, 2 * j + 1, fb);
+            tma_load_3d(st + 2 * kTileBytes, &tmB, kb * BK, tile_n, 2 * j, fb);
+            tma_load_3d(st + 3 * kTileBytes, &tmB, kb * BK, tile_n, 2 * j + 1, fb);
+          }
+        }
       }
       // Wait (bounded) for this thread's last copies so that none is in
       // flight when the CTA exits, whatever happened downstream.
-      for (int it = (issued > kStages ? issued - kStages : 0); it < issued; ++it)
-        mbar_wait(smem_u32(&full[it % kStages]), (it / kStages) & 1, P.err);
+      for (int i = (it > kStages ? it - kStages : 0); i < it; ++i)
+        mbar_wait(smem_u32(&full[i % kStages]), (i / kStages) & 1, P.err);
     }
   } else if (warp == 1) {
     if (lane == 0) {
-      for (int it = 0; it < iters; ++it) {
-        const int s = it % kStages;
-        const uint32_t ph = (it / kStages) & 1;
-        if (!mbar_wait(smem_u32(&full[s]), ph, P.err)) break;
-        tc_fence_after();
-        const int kb = it / 3, j = it % 3;
-        const uint32_t d = tmem_base + static_cast<uint32_t>(j * BN);
-        const uint32_t a_hi = smem_u32(stages + s * kStageBytes);
-        const uint32_t a_lo = a_hi + kTileBytes;
-        const uint32_t b_hi = a_hi + 2 * kTileBytes;
-        const uint32_t b_lo = a_hi + 3 * kTileBytes;
+      int it = 0, drained = 0;  // chunks the epilogue is known to have read
+      bool ok = true;
+      for (int c = 0; c < nchunks && ok; ++c) {
+        const int kb0 = c * kc, kb1 = min(nkb, kb0 + kc);
+        for (int j = 0; j < 3 && ok; ++j) {
+          // the slot's previous chunk (c - 2 for GEMM 0, c - 1 otherwise) must be read
+          const int need = j == 0 ? c - 1 : c;
+          while (drained < need) {
+            if (!mbar_wait(smem_u32(tmem_empty), drained & 1, P.err)) {
+              ok = false;
+              break;
+            }
+            ++drained;
+          }
+          if (!ok) break;
+          tc_fence_after();
+          const uint32_t d = tmem_base + static_cast<uint32_t>(((3 * c + j) & 3) * BN);
+          for (int kb = kb0; kb < kb1; ++kb, ++it) {
+            const int s = it % kStages;
+            const uint32_t ph = (it / kStages) & 1;
+            if (!mbar_wait(smem_u32(&full[s]), ph, P.err)) {
+              ok = false;
+              break;
+            }
+            tc_fence_after();
+            const uint32_t a_hi = smem_u32(stages + s * kStageBytes);
+            const uint32_t a_lo = a_hi + kTileBytes;
+            const uint32_t b_hi = a_hi + 2 * kTileBytes;
+            const uint32_t b_lo = a_hi + 3 * kTileBytes;
 #pragma unroll
-        for (int ks = 0; ks < kRowBytes / 32; ++ks) {
-          const uint32_t off = ks * 32;  // one MMA's K (32 bytes) inside the swizzled row
-          const uint32_t acc = (kb > 0 || ks > 0) ? 1u : 0u;
-          Prec<PREC>::mma(d, sw128_kmajor_desc(a_hi + off), sw128_kmajor_desc(b_hi + off), acc);
-          Prec<PREC>::mma(d, sw128_kmajor_desc(a_hi + off), sw128_kmajor_desc(b_lo + off), 1u);
-          Prec<PREC>::mma(d, sw128_kmajor_desc(a_lo + off), sw128_kmajor_desc(b_hi + off), 1u);
+            for (int ks = 0; ks < kRowBytes / 32; ++ks) {
+              const uint32_t off = ks * 32;  // one MMA's K (32 bytes) inside the swizzled row
+              const uint32_t acc = (kb > kb0 || ks > 0) ? 1u : 0u;
+              Prec<PREC>::mma(d, sw128_kmajor_desc(a_hi + off), sw128_kmajor_desc(b_hi + off), acc);
+              Prec<PREC>::mma(d, sw128_kmajor_desc(a_hi + off), sw128_kmajor_desc(b_lo + off), 1u);
+              Prec<PREC>::mma(d, sw128_kmajor_desc(a_lo + off), sw128_kmajor_desc(b_hi + off), 1u);
+            }
+            mma_commit(smem_u32(&empty[s]));  // the stage is free once these MMAs finish
+          }
         }
-        mma_commit(smem_u32(&empty[s]));  // the stage is free once these MMAs finish
+        if (ok) mma_commit(smem_u32(tmem_full));  // this chunk's accumulators are final
       }
-      mma_commit(smem_u32(tmem_full));  // all accumulators final
     }
   } else {
-    // Epilogue: warp w reads TMEM lanes 32 (w % 4) .. +31 = tile rows.
+    // Epilogue: 8 warps; warp w reads TMEM lanes 32 (w % 4) .. +31 (tile rows)
+    // and half h of the columns.  Each chunk's Re = T1 - T2 and Im = T3 - T1 -
+    // T2 are added into FP32 registers (round to nearest): the tensor cores
+    // accumulate in FP32 with truncation, so a sum over K has a systematic
+    // shrink proportional to the number of accumulation steps, which chunking
+    // bounds by the chunk length.
     const int q = warp & 3;
+    const int h = (warp - 2) >> 2;
     const int row = q * 32 + lane;
-    const bool ok = mbar_wait(smem_u32(tmem_full), 0, P.err);
-    tc_fence_after();
-    if (ok) {
-      const uint32_t tl = tmem_base + (static_cast<uint32_t>(q * 32) << 16);
-      const int gm = tile_m + row;
-      const size_t PS = static_cast<size_t>(P.M) * P.N;  // plane stride
-      const size_t ulen = static_cast<size_t>(P.N - 1) * static_cast<size_t>(P.ldu) + P.M;
-      for (int c0 = 0; c0 < BN; c0 += 32) {
-        float t1[32], t2[32], t3[32];
-        tmem_ld32(tl + 0 * BN + c0, t1);
-        tmem_ld32(tl + 1 * BN + c0, t2);
-        tmem_ld32(tl + 2 * BN + c0, t3);
+    const uint32_t tl = tmem_base + (static_cast<uint32_t>(q * 32) << 16) +
+                        static_cast<uint32_t>(h * kEpiCols);
+    float re[kEpiCols], im[kEpiCols];
+#pragma unroll
+    for (int i = 0; i < kEpiCols; ++i) re[i] = im[i] = 0.f;
+    bool ok = true;
+    for (int c = 0; c < nchunks; ++c) {
+      if (!mbar_wait(smem_u32(tmem_full), c & 1, P.err)) {
+        ok = false;
+        break;
+      }
+      tc_fence_after();
+      const uint32_t s1 = tl + static_cast<uint32_t>(((3 * c + 0) & 3) * BN);
+      const uint32_t s2 = tl + static_cast<uint32_t>(((3 * c + 1) & 3) * BN);
+      const uint32_t s3 = tl + static_cast<uint32_t>(((3 * c + 2) & 3) * BN);
+#pragma unroll
+      for (int g = 0; g < kEpiCols / 8; ++g) {
+        float t1[8], t2[8], t3[8];
+        tmem_ld8(s1 + g * 8, t1);
+        tmem_ld8(s2 + g * 8, t2);
+        tmem_ld8(s3 + g * 8, t3);
         tmem_wait_ld();
-        if (P.final_step) {
-          // U[n][m] = V'[m][n]: lanes hold consecutive m, so each store is coalesced.
 #pragma unroll
-          for (int i = 0; i < 32; ++i) {
-            const float re = t1[i] - t2[i];
-            const float im = t3[i] - t1[i] - t2[i];
-            P.u[TQS_IX(static_cast<size_t>(tile_n + c0 + i) * static_cast<size_t>(P.ldu) + gm, ulen)] =
-                make_float2(re, im);
-          }
-        } else {
-          // in place: t1 <- Re, t2 <- Im, t3 <- Re + Im
+        for (int i = 0; i < 8; ++i) {
+          re[g * 8 + i] += t1[i] - t2[i];
+          im[g * 8 + i] += t3[i] - t1[i] - t2[i];
+        }
+      }
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(smem_u32(tmem_empty));
+    }
+    if (ok) {
+      const int gm = tile_m + row;
+      const int col0 = tile_n + h * kEpiCols;
+      if (P.final_step) {
+        // U[n][m] = V'[m][n]: lanes hold consecutive m, so each store is coalesced.
+        const size_t ulen = static_cast<size_t>(P.N - 1) * static_cast<size_t>(P.ldu) + P.M;
 #pragma unroll
-          for (int i = 0; i < 32; ++i) {
-            const float a = t1[i], b = t2[i], c = t3[i];
-            t1[i] = a - b;
-            t2[i] = c - a - b;
-            t3[i] = t1[i] + t2[i];
+        for (int i = 0; i < kEpiCols; ++i)
+          P.u[TQS_IX(static_cast<size_t>(col0 + i) * static_cast<size_t>(P.ldu) + gm, ulen)] =
+              make_float2(re[i], im[i]);
+      } else {
+        const size_t PS = static_cast<size_t>(P.M) * P.N;  // plane stride
+        typename Prec<PREC>::E* rowp = P.planes + static_cast<size_t>(TQS_IX(gm, P.M)) * P.N +
+                                       TQS_IX(col0, P.N - kEpiCols + 1);
+#pragma unroll
+        for (int i0 = 0; i0 < kEpiCols; i0 += 16) {
+          float a[16], b[16], sm[16];
+#pragma unroll
+          for (int i = 0; i < 16; ++i) {
+            a[i] = re[i0 + i];
+            b[i] = im[i0 + i];
+            sm[i] = a[i] + b[i];
           }
-          typename Prec<PREC>::E* rowp = P.planes + static_cast<size_t>(TQS_IX(gm, P.M)) * P.N +
-                                         TQS_IX(tile_n + c0, P.N - 31);
-          store_split<PREC, 32>(t1, rowp, rowp + PS);
-          store_split<PREC, 32>(t2, rowp + 2 * PS, rowp + 3 * PS);
-          store_split<PREC, 32>(t3, rowp + 4 * PS, rowp + 5 * PS);
+          store_split<PREC, 16>(a, rowp + i0, rowp + PS + i0);
+          store_split<PREC, 16>(b, rowp + 2 * PS + i0, rowp + 3 * PS + i0);
+          store_split<PREC, 16>(sm, rowp + 4 * PS + i0, rowp + 5 * PS + i0);
         }
       }
     }
@@ -261,43 +333,77 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
 // split into hi + lo of the MMA input type.  transpose = 0: plane[r][c] =
 // S[r][c] (the B operand, rows = N, row0 = 0); transpose = 1: plane[j][r] =
 // S[r][row0 + j] for j < rows (rows row0.. of the initial V = S_1^T: the
-// columns row0.. of S_1).  Planes are rows x N, `rows * N` entries apart.  A
-// thread produces 32 consecutive entries of one output row.
+// columns row0.. of S_1).  Planes are rows x N, `rows * N` entries apart.
+//
+// A thread produces 32 consecutive entries of one output row: one index of
+// S (the fixed one) is the same for all of them and the other runs over 32
+// values that differ only in their low 5 bits.  An entry is the product of the
+// step's factor entries (Algorithm 2), so the factors that act on no qubit
+// below 5 contribute the same value to all 32 and are multiplied once; only
+// the (at most 5, the factors being disjoint) factors on the low qubits are
+// evaluated per entry.
 constexpr int kGenThreads = 256;
+constexpr int kGenChunksPerThread = 4;
 constexpr int kMaxFactors = 16;
 
+// At most 40 registers (6 CTAs' worth per SM): a generator CTA then fits
+// beside a GEMM CTA (320 threads x 168 registers) on one SM.
 template <int PREC>
-__global__ void __launch_bounds__(kGenThreads)
+__global__ void __launch_bounds__(kGenThreads, 6)
     gen_planes_kernel(const StepFactor* __restrict__ factors, int nf, uint32_t idle, int n,
                       int transpose, int row0, int rows, typename Prec<PREC>::E* __restrict__ planes) {
   __shared__ StepFactor fs[kMaxFactors];
+  __shared__ int s_lo[kMaxFactors], s_hi[kMaxFactors];
+  __shared__ int s_nlo, s_nhi;
   for (int i = threadIdx.x; i < nf * static_cast<int>(sizeof(StepFactor) / 8); i += blockDim.x)
     reinterpret_cast<float2*>(fs)[TQS_IX(i, int(sizeof(fs) / 8))] =
         reinterpret_cast<const float2*>(factors)[i];
   __syncthreads();
+  if (threadIdx.x == 0) {
+    int nlo = 0, nhi = 0;
+    for (int k = 0; k < nf; ++k) {
+      if (factor_qubits(fs[k]) & 31u) s_lo[TQS_IX(nlo++, kMaxFactors)] = k;
+      else s_hi[TQS_IX(nhi++, kMaxFactors)] = k;
+    }
+    s_nlo = nlo;
+    s_nhi = nhi;
+  }
+  __syncthreads();
+  const int nlo = s_nlo, nhi = s_nhi;
   const int64_t N = int64_t(1) << n;
   const size_t PS = static_cast<size_t>(rows) * N;  // plane stride
   const int64_t chunks = static_cast<int64_t>(PS) >> 5;
   const int64_t stride = int64_t(gridDim.x) * blockDim.x;
+  const uint32_t idle_lo = idle & 31u;
   for (int64_t e = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; e < chunks; e += stride) {
     const int64_t flat = e << 5;
-    const uint32_t orow = static_cast<uint32_t>(flat >> n);
-    const uint32_t ocol = static_cast<uint32_t>(flat & (N - 1));
+    const uint32_t fixed = static_cast<uint32_t>(flat >> n) + static_cast<uint32_t>(row0);
+    const uint32_t vary0 = static_cast<uint32_t>(flat & (N - 1));  // low 5 bits zero
+    const uint32_t r0 = transpose ? vary0 : fixed, c0 = transpose ? fixed : vary0;
+    // the factors on qubits >= 5 and the idle qubits >= 5: one value for all 32
+    float2 base = make_float2(0.f, 0.f);
+    if (((r0 ^ c0) & idle & ~31u) == 0) {
+      base = make_float2(1.f, 0.f);
+      for (int k = 0; k < nhi; ++k) base = step_cmul(base, factor_entry(fs[s_hi[k]], r0, c0));
+    }
+    const uint32_t fixed_lo = fixed & 31u;
     for (int i0 = 0; i0 < 32; i0 += 8) {
       float re[8], im[8], sm[8];
 #pragma unroll
       for (int i = 0; i < 8; ++i) {
-        const uint32_t r = transpose ? ocol + i0 + i : orow + row0;
-        const uint32_t c = transpose ? orow + row0 : ocol + i0 + i;
-        const float2 z = step_entry(fs, nf, idle, r, c);
+        const uint32_t v = static_cast<uint32_t>(i0 + i);
+        const uint32_t r = transpose ? vary0 | v : fixed;
+        const uint32_t c = transpose ? fixed : vary0 | v;
+        float2 z = ((v ^ fixed_lo) & idle_lo) ? make_float2(0.f, 0.f) : base;
+        for (int k = 0; k < nlo; ++k) z = step_cmul(z, factor_entry(fs[s_lo[k]], r, c));
         re[i] = z.x;
         im[i] = z.y;
         sm[i] = z.x + z.y;
       }
-      typename Prec<PREC>::E* base = planes + TQS_IX(static_cast<size_t>(flat + i0), PS - 7);
-      store_split<PREC, 8>(re, base, base + PS);
-      store_split<PREC, 8>(im, base + 2 * PS, base + 3 * PS);
-      store_split<PREC, 8>(sm, base + 4 * PS, base + 5 * PS);
+      typename Prec<PREC>::E* base_p = planes + TQS_IX(static_cast<size_t>(flat + i0), PS - 7);
+      store_split<PREC, 8>(re, base_p, base_p + PS);
+      store_split<PREC, 8>(im, base_p + 2 * PS, base_p + 3 * PS);
+      store_split<PREC, 8>(sm, base_p + 4 * PS, base_p + 5 * PS);
     }
   }
 }
@@ -340,25 +446,14 @@ bool make_planes_map(CUtensorMap* m, void* base, int N, int rows) {
             CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
-int sms() {
-  static int v = 0;
-  if (v == 0) {
-    int dev = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev);
-    if (v <= 0) v = 1;
-  }
-  return v;
-}
-
 template <int PREC>
 cudaError_t launch_gen(const StepFactor* d_factors, const StepDesc& st, int n, int transpose,
                        int row0, int rows, typename Prec<PREC>::E* planes, cudaStream_t s) {
   if (st.f_count > kMaxFactors) return cudaErrorInvalidValue;
   const int64_t N = int64_t(1) << n;
-  int64_t blocks = ((int64_t(rows) * N) / 32 + kGenThreads - 1) / kGenThreads;
-  const int64_t cap = int64_t(sms()) * 16;
-  if (blocks > cap) blocks = cap;
+  const int64_t per_block = int64_t(kGenThreads) * kGenChunksPerThread * 32;
+  int64_t blocks = (int64_t(rows) * N + per_block - 1) / per_block;
+  if (blocks > (int64_t(1) << 30)) blocks = int64_t(1) << 30;
   if (blocks < 1) blocks = 1;
   gen_planes_kernel<PREC><<<static_cast<int>(blocks), kGenThreads, 0, s>>>(
       d_factors + st.f_begin, st.f_count, st.idle, n, transpose, row0, rows, planes);
@@ -366,47 +461,138 @@ cudaError_t launch_gen(const StepFactor* d_factors, const StepDesc& st, int n, i
   return cudaGetLastError();
 }
 
+// The chain's two internal streams: the GEMMs on the device's highest stream
+// priority, the plane generators on its lowest, so that while the GEMM of step
+// k runs the generator of step k + 1 fills the room its CTAs leave (one GEMM
+// CTA per SM uses 198 KB of shared memory and 48 K registers) and the block
+// scheduler prefers the GEMM's CTAs whenever both wait.  Created once per
+// device; calls on the caller's stream are ordered against them with events.
+struct ChainStreams {
+  cudaStream_t gemm = nullptr, gen = nullptr;
+};
+
+cudaError_t chain_streams(ChainStreams* out) {
+  static std::mutex mu;
+  static ChainStreams per_dev[64];
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+  std::lock_guard<std::mutex> lock(mu);
+  ChainStreams& cs = per_dev[dev];
+  if (!cs.gemm) {
+    int least = 0, greatest = 0;
+    e = cudaDeviceGetStreamPriorityRange(&least, &greatest);
+    if (e != cudaSuccess) return e;
+    cudaStream_t a = nullptr, b = nullptr;
+    e = cudaStreamCreateWithPriority(&a, cudaStreamNonBlocking, greatest);
+    if (e != cudaSuccess) return e;
+    e = cudaStreamCreateWithPriority(&b, cudaStreamNonBlocking, least);
+    if (e != cudaSuccess) {
+      cudaStreamDestroy(a);
+      return e;
+    }
+    cs.gemm = a;
+    cs.gen = b;
+  }
+  *out = cs;
+  return cudaSuccess;
+}
+
+// Events of one chain call (destroyed on every return path).
+struct ChainEvents {
+  cudaEvent_t start = nullptr, gen_done[2] = {nullptr, nullptr}, gemm_done[2] = {nullptr, nullptr},
+              end = nullptr, end_gen = nullptr;
+  cudaError_t create() {
+    cudaEvent_t* all[] = {&start, &gen_done[0], &gen_done[1], &gemm_done[0], &gemm_done[1], &end,
+                          &end_gen};
+    for (cudaEvent_t* p : all) {
+      const cudaError_t e = cudaEventCreateWithFlags(p, cudaEventDisableTiming);
+      if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+  }
+  ~ChainEvents() {
+    cudaEvent_t all[] = {start, gen_done[0], gen_done[1], gemm_done[0], gemm_done[1], end, end_gen};
+    for (cudaEvent_t e : all)
+      if (e) cudaEventDestroy(e);
+  }
+};
+
 template <int PREC>
 cudaError_t chain_tc_impl(const StepFactor* d_factors, const StepDesc* steps, int nsteps, int n,
                           int col0, int ncols, float2* d_U, int64_t ldu, void* scratch, int* d_err,
-                          int group, cudaStream_t s) {
+                          int group, int kchunk, cudaStream_t s) {
   using E = typename Prec<PREC>::E;
   const int N = 1 << n;
   const size_t MN = size_t(ncols) * N;  // the block's V planes: ncols rows of V
+  const size_t NN = size_t(N) * N;
   E* V0 = static_cast<E*>(scratch);
   E* V1 = V0 + 6 * MN;
-  E* S = V1 + 6 * MN;
-  CUtensorMap mV0, mV1, mS;
+  E* S[2] = {V1 + 6 * MN, V1 + 6 * MN + 6 * NN};  // S_k in S[(k - 1) & 1]
+  CUtensorMap mV0, mV1, mS[2];
   if (!make_planes_map<PREC>(&mV0, V0, N, ncols) || !make_planes_map<PREC>(&mV1, V1, N, ncols) ||
-      !make_planes_map<PREC>(&mS, S, N, N))
+      !make_planes_map<PREC>(&mS[0], S[0], N, N) || !make_planes_map<PREC>(&mS[1], S[1], N, N))
     return cudaErrorNotSupported;
   cudaError_t e = cudaFuncSetAttribute(chain_gemm_kernel<PREC>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        static_cast<int>(kGemmSmem));
   if (e != cudaSuccess) return e;
-  e = launch_gen<PREC>(d_factors, steps[0], n, 1, col0, ncols, V0, s);  // V = rows of S_1^T
-  if (e != cudaSuccess) return e;
-  bool cur0 = true;
-  for (int k = 1; k < nsteps; ++k) {
-    e = launch_gen<PREC>(d_factors, steps[k], n, 0, 0, N, S, s);
-    if (e != cudaSuccess) return e;
-    GemmParams<E> P;
-    P.N = N;
-    P.M = ncols;
-    P.final_step = (k == nsteps - 1) ? 1 : 0;
-    P.planes = cur0 ? V1 : V0;
-    P.u = d_U;
-    P.ldu = ldu;
-    P.group = group;
-    P.err = d_err;
-    const int grid = (N / BN) * (ncols / BM);
-    chain_gemm_kernel<PREC><<<grid, kGemmThreads, kGemmSmem, s>>>(cur0 ? mV0 : mV1, mS, P);
-    count_launches(1);
-    e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
-    cur0 = !cur0;
-  }
-  return cudaSuccess;
+  ChainStreams cs;
+  if ((e = chain_streams(&cs)) != cudaSuccess) return e;
+  ChainEvents ev;
+  if ((e = ev.create()) != cudaSuccess) return e;
+  // fork: both internal streams start after the work already on the caller's stream
+  if ((e = cudaEventRecord(ev.start, s)) != cudaSuccess) return e;
+  if ((e = cudaStreamWaitEvent(cs.gemm, ev.start, 0)) != cudaSuccess) return e;
+  if ((e = cudaStreamWaitEvent(cs.gen, ev.start, 0)) != cudaSuccess) return e;
+  auto steps_loop = [&]() -> cudaError_t {
+    // V = rows col0.. of S_1^T
+    cudaError_t r = launch_gen<PREC>(d_factors, steps[0], n, 1, col0, ncols, V0, cs.gemm);
+    if (r != cudaSuccess) return r;
+    if ((r = launch_gen<PREC>(d_factors, steps[1], n, 0, 0, N, S[0], cs.gen)) != cudaSuccess) return r;
+    if ((r = cudaEventRecord(ev.gen_done[0], cs.gen)) != cudaSuccess) return r;
+    bool cur0 = true;
+    for (int k = 1; k < nsteps; ++k) {
+      const int b = (k - 1) & 1;  // S_k's buffer
+      // S_{k+1} into the other buffer, once the GEMM of step k - 1 (its last reader) is done
+      if (k + 1 < nsteps) {
+        if (k >= 2 && (r = cudaStreamWaitEvent(cs.gen, ev.gemm_done[b ^ 1], 0)) != cudaSuccess) return r;
+        if ((r = launch_gen<PREC>(d_factors, steps[k + 1], n, 0, 0, N, S[b ^ 1], cs.gen)) != cudaSuccess)
+          return r;
+        if ((r = cudaEventRecord(ev.gen_done[b ^ 1], cs.gen)) != cudaSuccess) return r;
+      }
+      if ((r = cudaStreamWaitEvent(cs.gemm, ev.gen_done[b], 0)) != cudaSuccess) return r;
+      GemmParams<E> P;
+      P.N = N;
+      P.M = ncols;
+      P.final_step = (k == nsteps - 1) ? 1 : 0;
+      P.planes = cur0 ? V1 : V0;
+      P.u = d_U;
+      P.ldu = ldu;
+      P.group = group;
+      // K per accumulation chunk in whole k blocks (0: the precision's default,
+      // the same number of MMA accumulation steps per chunk for both)
+      P.kchunk_blocks = std::max(1, (kchunk > 0 ? kchunk : Prec<PREC>::kDefaultKChunk) / Prec<PREC>::BK);
+      P.err = d_err;
+      const int grid = (N / BN) * (ncols / BM);
+      chain_gemm_kernel<PREC><<<grid, kGemmThreads, kGemmSmem, cs.gemm>>>(cur0 ? mV0 : mV1, mS[b], P);
+      count_launches(1);
+      if ((r = cudaGetLastError()) != cudaSuccess) return r;
+      if ((r = cudaEventRecord(ev.gemm_done[b], cs.gemm)) != cudaSuccess) return r;
+      cur0 = !cur0;
+    }
+    return cudaSuccess;
+  };
+  const cudaError_t le = steps_loop();
+  // join, on every path: the caller's stream continues after all work of both
+  // internal streams (normally every generator has finished before the GEMM
+  // that reads its planes, but not after an error in mid-chain)
+  if ((e = cudaEventRecord(ev.end, cs.gemm)) != cudaSuccess) return e;
+  if ((e = cudaEventRecord(ev.end_gen, cs.gen)) != cudaSuccess) return e;
+  if ((e = cudaStreamWaitEvent(s, ev.end, 0)) != cudaSuccess) return e;
+  if ((e = cudaStreamWaitEvent(s, ev.end_gen, 0)) != cudaSuccess) return e;
+  return le;
 }
 
 __global__ void wait_selftest_kernel(int* status, long long wait_cycles) {
@@ -437,7 +623,8 @@ cudaError_t launch_wait_selftest(int* status, long long wait_cycles, cudaStream_
 size_t chain_tc_scratch_bytes(int n, int prec, int ncols) {
   const size_t N = size_t(1) << n;
   const size_t es = prec == TQS_PREC_TC_TF32X3 ? 4 : 2;
-  return (12 * size_t(ncols) * N + 6 * N * N) * es;  // V and V' (ncols rows), S: 6 planes each
+  // V and V' (ncols rows) and two step unitaries S (double-buffered): 6 planes each
+  return (12 * size_t(ncols) * N + 12 * N * N) * es;
 }
 
 // Columns [col0, col0 + ncols) of U = S_m ... S_1 with the tensor-core chain
@@ -446,16 +633,16 @@ size_t chain_tc_scratch_bytes(int n, int prec, int ncols) {
 // d_U[r * ldu + j].  n >= 7; col0 and ncols multiples of 128.
 cudaError_t chain_tc(const StepFactor* d_factors, const StepDesc* steps, int nsteps, int n,
                      int prec, int col0, int ncols, float2* d_U, int64_t ldu, void* scratch,
-                     int* d_err, int group, cudaStream_t s) {
+                     int* d_err, int group, int kchunk, cudaStream_t s) {
   if (n < 7 || nsteps < 2 || col0 % BM || ncols % BM || ncols < BM || col0 + ncols > (1 << n) ||
-      ldu < ncols || group < 1 || group > kMaxGroupM)
+      ldu < ncols || group < 1 || group > kMaxGroupM || kchunk < 0 || kchunk % 64)
     return cudaErrorInvalidValue;
   if (prec == TQS_PREC_TC_BF16X3)
     return chain_tc_impl<TQS_PREC_TC_BF16X3>(d_factors, steps, nsteps, n, col0, ncols, d_U, ldu,
-                                             scratch, d_err, group, s);
+                                             scratch, d_err, group, kchunk, s);
   if (prec == TQS_PREC_TC_TF32X3)
     return chain_tc_impl<TQS_PREC_TC_TF32X3>(d_factors, steps, nsteps, n, col0, ncols, d_U, ldu,
-                                             scratch, d_err, group, s);
+                                             scratch, d_err, group, kchunk, s);
   return cudaErrorInvalidValue;
 }
 

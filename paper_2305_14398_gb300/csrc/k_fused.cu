@@ -414,15 +414,8 @@ __device__ __forceinline__ void run_ops(float2 (&a)[16], const FusedOp* __restri
   }
 }
 
-// |v|^2 correctly rounded to FP64: the two squares are exact FP64 values built
-// with integer operations; one FP64 add rounds their sum.
-__device__ __forceinline__ double prob_f64(float2 v) {
-  const double a = __longlong_as_double(
-      static_cast<long long>(sq_f32_as_f64_bits(__float_as_uint(v.x))));
-  const double b = __longlong_as_double(
-      static_cast<long long>(sq_f32_as_f64_bits(__float_as_uint(v.y))));
-  return __dadd_rn(a, b);
-}
+// |v|^2 correctly rounded to FP64 (exact_sq.h).
+__device__ __forceinline__ double prob_f64(float2 v) { return sq_sum_f64(v.x, v.y); }
 
 // The output map's linear part (FusedCirc::col): the XOR of col[q] over the
 // set bits q of v, v < 2^n.

@@ -1,7 +1,10 @@
 // Probabilities and their FP64 sum (sm_103a).
 //
-// p_i = |psi_i|^2 (Sec. 2.1, eq. 2) computed in FP64 from the FP32 parts (their
-// squares are exact in FP64), optionally written out, and summed over the
+// p_i = |psi_i|^2 (Sec. 2.1, eq. 2) correctly rounded to FP64 from the FP32
+// parts (their squares are exact FP64 values, built with integer operations:
+// GB300 runs FP64 arithmetic at about 1/64 of its FP32 rate, so each
+// probability costs one FP64 add instead of two widenings, a multiply and a
+// fused multiply-add), optionally written out, and summed over the
 // indices i with (i & zero_mask) == 0 (zero_mask = 0: the norm; otherwise the
 // marginal probability that the masked qubits read 0, as for the
 // Deutsch-Jozsa input register of Sec. 2.5).  The reduction runs in a fixed
@@ -11,6 +14,7 @@
 
 #include "../../include/tqs.h"
 #include "checked.h"
+#include "exact_sq.h"
 #include "tqs_internal.h"
 
 namespace tqs {
@@ -29,9 +33,8 @@ __global__ void __launch_bounds__(kProbThreads)
   double acc = 0.0;
   for (int64_t i = begin + 2 * threadIdx.x; i < end; i += 2 * kProbThreads) {
     const float4 v = __ldcs(reinterpret_cast<const float4*>(st) + TQS_IX(i >> 1, N >> 1));
-    const double x0 = v.x, y0 = v.y, x1 = v.z, y1 = v.w;
-    const double q0 = fma(x0, x0, y0 * y0);
-    const double q1 = fma(x1, x1, y1 * y1);
+    const double q0 = sq_sum_f64(v.x, v.y);
+    const double q1 = sq_sum_f64(v.z, v.w);
     if (probs) __stcs(reinterpret_cast<double2*>(probs) + TQS_IX(i >> 1, N >> 1), make_double2(q0, q1));
     if ((static_cast<uint64_t>(i) & zero_mask) == 0) acc += q0;
     if ((static_cast<uint64_t>(i + 1) & zero_mask) == 0) acc += q1;

@@ -490,6 +490,14 @@ tqs_status tqs_set_option(int option, int key, int64_t value) {
     g_chain_group.store(static_cast<int>(value));
     return TQS_OK;
   }
+  if (option == TQS_OPT_CHAIN_KCHUNK) {
+    if (key != 0) return fail(TQS_ERR_ARG, "tqs_set_option: key %d of TQS_OPT_CHAIN_KCHUNK is not 0", key);
+    if (value < 0 || value > (int64_t(1) << 20) || value % 64)
+      return fail(TQS_ERR_ARG, "tqs_set_option: K chunk %lld is not 0 or a multiple of 64 up to 2^20",
+                  static_cast<long long>(value));
+    g_chain_kchunk.store(static_cast<int>(value));
+    return TQS_OK;
+  }
   return fail(TQS_ERR_ARG, "tqs_set_option: unknown option %d", option);
 }
 
@@ -525,10 +533,13 @@ tqs_status tqs_get_option(int option, int key, int64_t* value) {
     *value = g_fsv_max_gates.load();
     return TQS_OK;
   }
-  if (option == TQS_OPT_CTA_THREADS || option == TQS_OPT_FSV_TILE_Q || option == TQS_OPT_CHAIN_GROUP) {
+  if (option == TQS_OPT_CTA_THREADS || option == TQS_OPT_FSV_TILE_Q || option == TQS_OPT_CHAIN_GROUP ||
+      option == TQS_OPT_CHAIN_KCHUNK) {
     if (key != 0) return fail(TQS_ERR_ARG, "tqs_get_option: key %d of option %d is not 0", key, option);
-    *value = option == TQS_OPT_CTA_THREADS ? g_cta_threads.load()
-             : option == TQS_OPT_FSV_TILE_Q ? g_fsv_tile_q.load() : g_chain_group.load();
+    *value = option == TQS_OPT_CTA_THREADS  ? g_cta_threads.load()
+             : option == TQS_OPT_FSV_TILE_Q ? g_fsv_tile_q.load()
+             : option == TQS_OPT_CHAIN_GROUP ? g_chain_group.load()
+                                             : g_chain_kchunk.load();
     return TQS_OK;
   }
   return fail(TQS_ERR_ARG, "tqs_get_option: unknown option %d", option);
