@@ -77,7 +77,11 @@ def build(force: bool = False, verbose: bool = False, extra_nvcc=None, checked: 
     for f in cpp:
         src, obj = os.path.join(CSRC, f), os.path.join(build_dir, f + ".o")
         if force or _stale(src, obj, hdr):
-            jobs.append(["g++", "-O2", "-std=c++17", "-fPIC", "-pthread", "-Wall", "-I", os.path.join(cuda, "include"),
+            # -fcx-fortran-rules: complex products without the C99 NaN
+            # re-check (finite values give the same results; the host compile
+            # multiplies many 2x2 complex matrices)
+            jobs.append(["g++", "-O3", "-fcx-fortran-rules", "-std=c++17", "-fPIC", "-pthread", "-Wall",
+                         "-I", os.path.join(cuda, "include"),
                          "-I", CSRC, "-I", INCLUDE, "-c", src, "-o", obj])
     objs = [os.path.join(build_dir, f + ".o") for f in cu + cpp]
 

@@ -36,12 +36,16 @@ float2 to_unit_f2(cd z) {
     float2 r;
     bool used = false;
   };
-  static thread_local Entry cache[256];
+  static thread_local Entry cache[1024];
   uint64_t kre, kim;
   const double zre = z.real(), zim = z.imag();
+  // parts FP32 holds exactly (1, -1, i, 0.5, ...): nothing to choose
+  if (static_cast<double>(static_cast<float>(zre)) == zre &&
+      static_cast<double>(static_cast<float>(zim)) == zim)
+    return make_float2(static_cast<float>(zre), static_cast<float>(zim));
   std::memcpy(&kre, &zre, 8);
   std::memcpy(&kim, &zim, 8);
-  Entry& ent = cache[((kre * 0x9E3779B97F4A7C15ull) ^ (kim * 0xC2B2AE3D27D4EB4Full)) >> 56];
+  Entry& ent = cache[((kre * 0x9E3779B97F4A7C15ull) ^ (kim * 0xC2B2AE3D27D4EB4Full)) >> 54];
   if (ent.used && ent.re == kre && ent.im == kim) return ent.r;
   const float2 rn = to_f2(z);
   const double zr = z.real(), zi = z.imag();

@@ -338,10 +338,13 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
 // A thread produces 32 consecutive entries of one output row: one index of
 // S (the fixed one) is the same for all of them and the other runs over 32
 // values that differ only in their low 5 bits.  An entry is the product of the
-// step's factor entries (Algorithm 2), so the factors that act on no qubit
-// below 5 contribute the same value to all 32 and are multiplied once; only
-// the (at most 5, the factors being disjoint) factors on the low qubits are
-// evaluated per entry.
+// step's factor entries (Algorithm 2), and the factors are disjoint, so:
+//   * factors on no qubit below 5 give one value for all 32 entries (once);
+//   * factors on qubits below 5 only give a 32-entry table over the low bits,
+//     the same for every thread of a row: when a warp's 32 threads share a row
+//     (rows of at least 1024 entries) lane v computes entry v of the table
+//     and the others read it by shuffle;
+//   * factors on qubits on both sides are evaluated per entry.
 constexpr int kGenThreads = 256;
 constexpr int kGenChunksPerThread = 4;
 constexpr int kMaxFactors = 16;
@@ -353,40 +356,51 @@ __global__ void __launch_bounds__(kGenThreads, 6)
     gen_planes_kernel(const StepFactor* __restrict__ factors, int nf, uint32_t idle, int n,
                       int transpose, int row0, int rows, typename Prec<PREC>::E* __restrict__ planes) {
   __shared__ StepFactor fs[kMaxFactors];
-  __shared__ int s_lo[kMaxFactors], s_hi[kMaxFactors];
-  __shared__ int s_nlo, s_nhi;
+  __shared__ int s_cls[3][kMaxFactors];  // factor indices: high, low-only, mixed
+  __shared__ int s_n[3];
   for (int i = threadIdx.x; i < nf * static_cast<int>(sizeof(StepFactor) / 8); i += blockDim.x)
     reinterpret_cast<float2*>(fs)[TQS_IX(i, int(sizeof(fs) / 8))] =
         reinterpret_cast<const float2*>(factors)[i];
   __syncthreads();
   if (threadIdx.x == 0) {
-    int nlo = 0, nhi = 0;
+    int cnt[3] = {0, 0, 0};
     for (int k = 0; k < nf; ++k) {
-      if (factor_qubits(fs[k]) & 31u) s_lo[TQS_IX(nlo++, kMaxFactors)] = k;
-      else s_hi[TQS_IX(nhi++, kMaxFactors)] = k;
+      const uint32_t qm = factor_qubits(fs[k]);
+      const int cls = (qm & 31u) == 0 ? 0 : (qm & ~31u) == 0 ? 1 : 2;
+      s_cls[cls][TQS_IX(cnt[cls]++, kMaxFactors)] = k;
     }
-    s_nlo = nlo;
-    s_nhi = nhi;
+    for (int c = 0; c < 3; ++c) s_n[c] = cnt[c];
   }
   __syncthreads();
-  const int nlo = s_nlo, nhi = s_nhi;
+  const int nhi = s_n[0], nlo = s_n[1], nmix = s_n[2];
+  const int lane = threadIdx.x & 31;
   const int64_t N = int64_t(1) << n;
   const size_t PS = static_cast<size_t>(rows) * N;  // plane stride
   const int64_t chunks = static_cast<int64_t>(PS) >> 5;
   const int64_t stride = int64_t(gridDim.x) * blockDim.x;
   const uint32_t idle_lo = idle & 31u;
+  // chunks is a multiple of 32 and a warp's threads take 32 consecutive
+  // chunks, so whole warps run every iteration (the shuffles below)
   for (int64_t e = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; e < chunks; e += stride) {
     const int64_t flat = e << 5;
     const uint32_t fixed = static_cast<uint32_t>(flat >> n) + static_cast<uint32_t>(row0);
     const uint32_t vary0 = static_cast<uint32_t>(flat & (N - 1));  // low 5 bits zero
     const uint32_t r0 = transpose ? vary0 : fixed, c0 = transpose ? fixed : vary0;
+    const uint32_t fixed_lo = fixed & 31u;
     // the factors on qubits >= 5 and the idle qubits >= 5: one value for all 32
     float2 base = make_float2(0.f, 0.f);
     if (((r0 ^ c0) & idle & ~31u) == 0) {
       base = make_float2(1.f, 0.f);
-      for (int k = 0; k < nhi; ++k) base = step_cmul(base, factor_entry(fs[s_hi[k]], r0, c0));
+      for (int k = 0; k < nhi; ++k) base = step_cmul(base, factor_entry(fs[s_cls[0][k]], r0, c0));
     }
-    const uint32_t fixed_lo = fixed & 31u;
+    // entry `lane` of the low-bit table of this thread's row
+    const uint32_t lv = static_cast<uint32_t>(lane);
+    float2 tab = ((lv ^ fixed_lo) & idle_lo) ? make_float2(0.f, 0.f) : make_float2(1.f, 0.f);
+    {
+      const uint32_t r = transpose ? vary0 | lv : fixed, c = transpose ? fixed : vary0 | lv;
+      for (int k = 0; k < nlo; ++k) tab = step_cmul(tab, factor_entry(fs[s_cls[1][k]], r, c));
+    }
+    const bool shared_row = __all_sync(0xffffffffu, fixed == __shfl_sync(0xffffffffu, fixed, 0));
     for (int i0 = 0; i0 < 32; i0 += 8) {
       float re[8], im[8], sm[8];
 #pragma unroll
@@ -394,8 +408,16 @@ __global__ void __launch_bounds__(kGenThreads, 6)
         const uint32_t v = static_cast<uint32_t>(i0 + i);
         const uint32_t r = transpose ? vary0 | v : fixed;
         const uint32_t c = transpose ? fixed : vary0 | v;
-        float2 z = ((v ^ fixed_lo) & idle_lo) ? make_float2(0.f, 0.f) : base;
-        for (int k = 0; k < nlo; ++k) z = step_cmul(z, factor_entry(fs[s_lo[k]], r, c));
+        float2 z;
+        if (shared_row) {
+          z = make_float2(__shfl_sync(0xffffffffu, tab.x, static_cast<int>(v)),
+                          __shfl_sync(0xffffffffu, tab.y, static_cast<int>(v)));
+          z = step_cmul(base, z);
+        } else {
+          z = ((v ^ fixed_lo) & idle_lo) ? make_float2(0.f, 0.f) : base;
+          for (int k = 0; k < nlo; ++k) z = step_cmul(z, factor_entry(fs[s_cls[1][k]], r, c));
+        }
+        for (int k = 0; k < nmix; ++k) z = step_cmul(z, factor_entry(fs[s_cls[2][k]], r, c));
         re[i] = z.x;
         im[i] = z.y;
         sm[i] = z.x + z.y;
