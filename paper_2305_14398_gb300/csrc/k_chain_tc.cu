@@ -108,8 +108,22 @@ __device__ __forceinline__ void store_split(const float (&v)[K], typename Prec<P
       E e[per16];
       uint4 u;
     } h, l;
+    if constexpr (PREC == TQS_PREC_TC_BF16X3) {
+      // two values per conversion instruction (round to nearest, as split())
 #pragma unroll
-    for (int i = 0; i < per16; ++i) Prec<PREC>::split(v[i0 + i], h.e[i], l.e[i]);
+      for (int i = 0; i < per16; i += 2) {
+        const __nv_bfloat162 h2 = __floats2bfloat162_rn(v[i0 + i], v[i0 + i + 1]);
+        const float2 hf = __bfloat1622float2(h2);
+        const __nv_bfloat162 l2 = __floats2bfloat162_rn(v[i0 + i] - hf.x, v[i0 + i + 1] - hf.y);
+        h.e[i] = h2.x;
+        h.e[i + 1] = h2.y;
+        l.e[i] = l2.x;
+        l.e[i + 1] = l2.y;
+      }
+    } else {
+#pragma unroll
+      for (int i = 0; i < per16; ++i) Prec<PREC>::split(v[i0 + i], h.e[i], l.e[i]);
+    }
     *reinterpret_cast<uint4*>(hp + i0) = h.u;
     *reinterpret_cast<uint4*>(lp + i0) = l.u;
   }
@@ -335,18 +349,20 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
 // S[r][row0 + j] for j < rows (rows row0.. of the initial V = S_1^T: the
 // columns row0.. of S_1).  Planes are rows x N, `rows * N` entries apart.
 //
-// A thread produces 32 consecutive entries of one output row: one index of
-// S (the fixed one) is the same for all of them and the other runs over 32
-// values that differ only in their low 5 bits.  An entry is the product of the
-// step's factor entries (Algorithm 2), and the factors are disjoint, so:
-//   * factors on no qubit below 5 give one value for all 32 entries (once);
+// A thread writes 8 consecutive entries of one output row (a warp 256, so
+// each store instruction of a warp covers 512 contiguous bytes of a BF16
+// plane).  One index of S (the fixed one) is the same for all of them; the
+// other runs over values whose low 5 bits take 8 of 32 values.  An entry is
+// the product of the step's factor entries (Algorithm 2), and the factors are
+// disjoint, so:
+//   * factors on no qubit below 5 give one value per group of 32 entries;
 //   * factors on qubits below 5 only give a 32-entry table over the low bits,
-//     the same for every thread of a row: when a warp's 32 threads share a row
-//     (rows of at least 1024 entries) lane v computes entry v of the table
+//     the same for every group of a row: when a warp's 256 entries lie in one
+//     row (rows of at least 256 entries) lane v computes entry v of the table
 //     and the others read it by shuffle;
 //   * factors on qubits on both sides are evaluated per entry.
 constexpr int kGenThreads = 256;
-constexpr int kGenChunksPerThread = 4;
+constexpr int kGenChunksPerThread = 8;
 constexpr int kMaxFactors = 16;
 
 // At most 40 registers (6 CTAs' worth per SM): a generator CTA then fits
@@ -376,57 +392,65 @@ __global__ void __launch_bounds__(kGenThreads, 6)
   const int lane = threadIdx.x & 31;
   const int64_t N = int64_t(1) << n;
   const size_t PS = static_cast<size_t>(rows) * N;  // plane stride
-  const int64_t chunks = static_cast<int64_t>(PS) >> 5;
+  const int64_t chunks = static_cast<int64_t>(PS) >> 3;
   const int64_t stride = int64_t(gridDim.x) * blockDim.x;
   const uint32_t idle_lo = idle & 31u;
   // chunks is a multiple of 32 and a warp's threads take 32 consecutive
   // chunks, so whole warps run every iteration (the shuffles below)
   for (int64_t e = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; e < chunks; e += stride) {
-    const int64_t flat = e << 5;
+    const int64_t flat = e << 3;
     const uint32_t fixed = static_cast<uint32_t>(flat >> n) + static_cast<uint32_t>(row0);
-    const uint32_t vary0 = static_cast<uint32_t>(flat & (N - 1));  // low 5 bits zero
-    const uint32_t r0 = transpose ? vary0 : fixed, c0 = transpose ? fixed : vary0;
+    const uint32_t col = static_cast<uint32_t>(flat & (N - 1));
     const uint32_t fixed_lo = fixed & 31u;
-    // the factors on qubits >= 5 and the idle qubits >= 5: one value for all 32
-    float2 base = make_float2(0.f, 0.f);
-    if (((r0 ^ c0) & idle & ~31u) == 0) {
-      base = make_float2(1.f, 0.f);
-      for (int k = 0; k < nhi; ++k) base = step_cmul(base, factor_entry(fs[s_cls[0][k]], r0, c0));
+    const bool shared_row = __all_sync(0xffffffffu, fixed == __shfl_sync(0xffffffffu, fixed, 0));
+    // group of 32 entries this thread writes into, and the one whose common
+    // value (the factors on qubits >= 5) this lane computes for the warp
+    const uint32_t vary0 = col & ~31u;
+    const uint32_t gvary = shared_row ? (__shfl_sync(0xffffffffu, col, 0) & ~31u) + 32u * (lane & 7) : vary0;
+    float2 gbase = make_float2(0.f, 0.f);
+    {
+      const uint32_t r0 = transpose ? gvary : fixed, c0 = transpose ? fixed : gvary;
+      if (((r0 ^ c0) & idle & ~31u) == 0) {
+        gbase = make_float2(1.f, 0.f);
+        for (int k = 0; k < nhi; ++k) gbase = step_cmul(gbase, factor_entry(fs[s_cls[0][k]], r0, c0));
+      }
     }
-    // entry `lane` of the low-bit table of this thread's row
+    // entry `lane` of the low-bit table of the warp's row
     const uint32_t lv = static_cast<uint32_t>(lane);
     float2 tab = ((lv ^ fixed_lo) & idle_lo) ? make_float2(0.f, 0.f) : make_float2(1.f, 0.f);
     {
       const uint32_t r = transpose ? vary0 | lv : fixed, c = transpose ? fixed : vary0 | lv;
       for (int k = 0; k < nlo; ++k) tab = step_cmul(tab, factor_entry(fs[s_cls[1][k]], r, c));
     }
-    const bool shared_row = __all_sync(0xffffffffu, fixed == __shfl_sync(0xffffffffu, fixed, 0));
-    for (int i0 = 0; i0 < 32; i0 += 8) {
-      float re[8], im[8], sm[8];
-#pragma unroll
-      for (int i = 0; i < 8; ++i) {
-        const uint32_t v = static_cast<uint32_t>(i0 + i);
-        const uint32_t r = transpose ? vary0 | v : fixed;
-        const uint32_t c = transpose ? fixed : vary0 | v;
-        float2 z;
-        if (shared_row) {
-          z = make_float2(__shfl_sync(0xffffffffu, tab.x, static_cast<int>(v)),
-                          __shfl_sync(0xffffffffu, tab.y, static_cast<int>(v)));
-          z = step_cmul(base, z);
-        } else {
-          z = ((v ^ fixed_lo) & idle_lo) ? make_float2(0.f, 0.f) : base;
-          for (int k = 0; k < nlo; ++k) z = step_cmul(z, factor_entry(fs[s_cls[1][k]], r, c));
-        }
-        for (int k = 0; k < nmix; ++k) z = step_cmul(z, factor_entry(fs[s_cls[2][k]], r, c));
-        re[i] = z.x;
-        im[i] = z.y;
-        sm[i] = z.x + z.y;
-      }
-      typename Prec<PREC>::E* base_p = planes + TQS_IX(static_cast<size_t>(flat + i0), PS - 7);
-      store_split<PREC, 8>(re, base_p, base_p + PS);
-      store_split<PREC, 8>(im, base_p + 2 * PS, base_p + 3 * PS);
-      store_split<PREC, 8>(sm, base_p + 4 * PS, base_p + 5 * PS);
+    float2 base = gbase;
+    if (shared_row) {
+      const int src = static_cast<int>((col - (__shfl_sync(0xffffffffu, col, 0) & ~31u)) >> 5);
+      base = make_float2(__shfl_sync(0xffffffffu, gbase.x, src), __shfl_sync(0xffffffffu, gbase.y, src));
     }
+    float re[8], im[8], sm[8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+      const uint32_t v = (col & 31u) + static_cast<uint32_t>(i);
+      const uint32_t r = transpose ? vary0 | v : fixed;
+      const uint32_t c = transpose ? fixed : vary0 | v;
+      float2 z;
+      if (shared_row) {
+        z = make_float2(__shfl_sync(0xffffffffu, tab.x, static_cast<int>(v)),
+                        __shfl_sync(0xffffffffu, tab.y, static_cast<int>(v)));
+        z = step_cmul(base, z);
+      } else {
+        z = ((v ^ fixed_lo) & idle_lo) ? make_float2(0.f, 0.f) : base;
+        for (int k = 0; k < nlo; ++k) z = step_cmul(z, factor_entry(fs[s_cls[1][k]], r, c));
+      }
+      for (int k = 0; k < nmix; ++k) z = step_cmul(z, factor_entry(fs[s_cls[2][k]], r, c));
+      re[i] = z.x;
+      im[i] = z.y;
+      sm[i] = z.x + z.y;
+    }
+    typename Prec<PREC>::E* base_p = planes + TQS_IX(static_cast<size_t>(flat), PS - 7);
+    store_split<PREC, 8>(re, base_p, base_p + PS);
+    store_split<PREC, 8>(im, base_p + 2 * PS, base_p + 3 * PS);
+    store_split<PREC, 8>(sm, base_p + 4 * PS, base_p + 5 * PS);
   }
 }
 
@@ -473,7 +497,7 @@ cudaError_t launch_gen(const StepFactor* d_factors, const StepDesc& st, int n, i
                        int row0, int rows, typename Prec<PREC>::E* planes, cudaStream_t s) {
   if (st.f_count > kMaxFactors) return cudaErrorInvalidValue;
   const int64_t N = int64_t(1) << n;
-  const int64_t per_block = int64_t(kGenThreads) * kGenChunksPerThread * 32;
+  const int64_t per_block = int64_t(kGenThreads) * kGenChunksPerThread * 8;
   int64_t blocks = (int64_t(rows) * N + per_block - 1) / per_block;
   if (blocks > (int64_t(1) << 30)) blocks = int64_t(1) << 30;
   if (blocks < 1) blocks = 1;
