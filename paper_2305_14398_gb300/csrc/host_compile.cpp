@@ -320,6 +320,72 @@ void merge_diagonals(std::vector<FusedOp>& ops, size_t begin) {
   }
 }
 
+// `act` of a factor with local control position c: the local indices with bit c set.
+constexpr uint16_t kLocalControlMask[4] = {0xAAAA, 0xCCCC, 0xF0F0, 0xFF00};
+
+// Local positions (bits 0..3) that an op reads or changes: its target, its
+// local control, the positions its phases depend on.
+unsigned touched_positions(const FusedOp& op) {
+  const int code = op.code;
+  if (code < OPC_XL) return 1u << (code & 3);                   // H, X, XF
+  if (code < OPC_HMASK) return (1u << ((code - OPC_XL) >> 2)) | (1u << ((code - OPC_XL) & 3));
+  if (code == OPC_HMASK) return op.t & 15u;
+  if (code < OPC_CDENSE) return 1u << (code & 3);               // DENSE
+  if (code < OPC_DLN) {                                         // CDENSE
+    unsigned m = 1u << (code & 3);
+    for (int c = 0; c < 4; ++c)
+      if (op.act == kLocalControlMask[c]) m |= 1u << c;
+    return m;
+  }
+  if (code < OPC_DFF) return 1u << (code & 3);                  // DLN, DLF, DFL
+  if (code == OPC_DFF) return 0u;
+  if (code == OPC_DLL) return (1u << op.t) | (1u << op.c);
+  if (code == OPC_DLIST) return op.t < 4 ? 1u << op.t : 0u;
+  return 15u;                                                   // DIAG16, NOP
+}
+
+// Uncontrolled Hadamards of a pass (ops [begin, end)) move later past ops on
+// other positions (they commute: different tensor factors) until an op on
+// their position or another Hadamard comes; Hadamards that meet run as one
+// OPC_HMASK op (one dispatch instead of several).
+void group_hadamards(std::vector<FusedOp>& ops, size_t begin) {
+  size_t nh = 0;
+  for (size_t i = begin; i < ops.size(); ++i) nh += ops[i].code < OPC_X;
+  if (nh < 2) return;
+  static thread_local std::vector<FusedOp> out;
+  out.clear();
+  unsigned pend = 0;  // positions with a Hadamard held back
+  auto flush = [&]() {
+    if (pend == 0) return;
+    FusedOp h{};
+    h.fbit = 0xFF;
+    h.tbit = 0xFF;
+    h.act = 0xFFFF;
+    if ((pend & (pend - 1)) == 0) {
+      h.code = static_cast<uint8_t>(OPC_H + __builtin_ctz(pend));
+    } else {
+      h.code = OPC_HMASK;
+      h.t = static_cast<uint8_t>(pend);
+    }
+    out.push_back(h);
+    pend = 0;
+  };
+  for (size_t i = begin; i < ops.size(); ++i) {
+    const FusedOp& op = ops[i];
+    if (op.code < OPC_X) {
+      const unsigned b = 1u << (op.code & 3);
+      if (pend & b) flush();  // two on one position: keep their order
+      pend |= b;
+      continue;
+    }
+    if (touched_positions(op) & pend) flush();
+    out.push_back(op);
+  }
+  flush();
+  ops.resize(begin);
+  ops.insert(ops.end(), out.begin(), out.end());
+}
+
 }  // namespace
 
 void compile_program(int n, const std::vector<const Gate*>& gs_in, Program& P,
@@ -496,7 +562,6 @@ void compile_program(int n, const std::vector<const Gate*>& gs_in, Program& P,
     ps.op_begin = static_cast<uint32_t>(P.ops.size());
     double pass_cost = 6.0;
     int h_count = 0;
-    static const uint16_t kBitMask[4] = {0xAAAA, 0xCCCC, 0xF0F0, 0xFF00};
     auto emit_raw = [&](const Raw& r) {
       // a factor that fused to the identity (H H, X X, ...) does nothing
       if (!r.is_h && is_identity2(r.u)) return;
@@ -511,7 +576,7 @@ void compile_program(int n, const std::vector<const Gate*>& gs_in, Program& P,
       if (far_c) op.fbit = static_cast<uint8_t>(r.c);
       if (r.cls != G_DIAG || r.is_h) {
         // non-diagonal: the target is local
-        if (cl >= 0) op.act = kBitMask[cl];
+        if (cl >= 0) op.act = kLocalControlMask[cl];
         if (r.is_h) {
           op.code = static_cast<uint8_t>(OPC_H + tl);
           ++h_count;
@@ -577,6 +642,7 @@ void compile_program(int n, const std::vector<const Gate*>& gs_in, Program& P,
       emit_raw(r);
     }
     merge_diagonals(P.ops, ps.op_begin);
+    group_hadamards(P.ops, ps.op_begin);
     ps.op_count = static_cast<uint32_t>(P.ops.size() - ps.op_begin);
     // exact power-of-two rescale for this pass's unscaled Hadamards
     const int tot = h_carry + h_count;

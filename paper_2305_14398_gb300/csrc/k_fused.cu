@@ -256,8 +256,8 @@ __device__ __forceinline__ void run_ops(float2 (&a)[16], const FusedOp* __restri
         t = (code - OPC_XL) >> 2;
         act = bit_mask((code - OPC_XL) & 3);
       }
-      pend_flush(a, pd, t);
       if (code < OPC_X) {
+        pend_flush(a, pd, t);
         switch (t) {
           case 0: h_t<0>(a); break;
           case 1: h_t<1>(a); break;
@@ -265,13 +265,22 @@ __device__ __forceinline__ void run_ops(float2 (&a)[16], const FusedOp* __restri
           default: h_t<3>(a); break;
         }
       } else if (code < OPC_ANTI) {
+        pend_flush(a, pd, t);
         switch (t) {
           case 0: swap_t<0>(a, act); break;
           case 1: swap_t<1>(a, act); break;
           case 2: swap_t<2>(a, act); break;
           default: swap_t<3>(a, act); break;
         }
+      } else if (code == OPC_HMASK) {
+        // Hadamards on several local positions, one dispatch
+        const int hm = (q0.x >> 8) & 15;
+        if (hm & 1) { pend_flush(a, pd, 0); h_t<0>(a); }
+        if (hm & 2) { pend_flush(a, pd, 1); h_t<1>(a); }
+        if (hm & 4) { pend_flush(a, pd, 2); h_t<2>(a); }
+        if (hm & 8) { pend_flush(a, pd, 3); h_t<3>(a); }
       } else {
+        pend_flush(a, pd, t);
         const uint4 q1 = __ldg(rec + 1);
         const uint4 q2 = __ldg(rec + 2);
         const uint4 q3 = __ldg(rec + 3);

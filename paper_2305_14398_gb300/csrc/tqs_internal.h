@@ -26,8 +26,10 @@ namespace tqs {
 //   OPC_X + t        uncontrolled exchange of the pair (X)
 //   OPC_XF + t       exchange where far control bit `fbit` of the group is 1 (CNOT)
 //   OPC_XL + 4t + c  exchange in the pairs whose local control bit c is 1 (CNOT)
-//   OPC_ANTI + t     (reserved; anti-diagonal factors other than X run as DENSE:
-//                    fewer kernel code paths, and their coefficients get hi + lo)
+//   OPC_HMASK        unscaled Hadamards on the local positions of the bit mask
+//                    in field t (two or more, in position order; they commute);
+//                    anti-diagonal factors other than X run as DENSE (fewer
+//                    kernel code paths, and their coefficients get hi + lo)
 //   OPC_DENSE + t    uncontrolled 2x2, coefficients as FP32 hi + lo
 //   OPC_CDENSE + t   controlled 2x2 (`act` mask for a local control, `fbit` far)
 //   OPC_DLN + t      diag(d0, d1), local target, uncontrolled
@@ -52,7 +54,8 @@ enum OpCode : uint8_t {
   OPC_X = 4,
   OPC_XF = 8,
   OPC_XL = 12,       // 16 codes (t, c), c != t used
-  OPC_ANTI = 28,
+  OPC_ANTI = 28,      // end of the exchange codes
+  OPC_HMASK = 28,
   OPC_DENSE = 32,
   OPC_CDENSE = 36,
   OPC_DLN = 40,

@@ -16,6 +16,7 @@ from paper_2305_14398_gb300 import binding as B
 from paper_2305_14398_gb300 import workloads as W
 
 OPC_H, OPC_X, OPC_XF, OPC_XL, OPC_ANTI, OPC_DENSE, OPC_CDENSE = 0, 4, 8, 12, 28, 32, 36
+OPC_HMASK = 28
 OPC_DLN, OPC_DLF, OPC_DFL, OPC_DFF, OPC_DLL, OPC_DLIST, OPC_DIAG16, OPC_NOP = 40, 44, 48, 52, 53, 54, 55, 56
 BIT_MASK = [0xAAAA, 0xCCCC, 0xF0F0, 0xFF00]
 
@@ -123,6 +124,23 @@ def replay(n, passes, ops, pos, out_scale=1.0, gen_index=0, uniforms=None, outco
                     for j in range(16):
                         if (j >> c) & 1:
                             a[:, j] *= d1 if (j >> t) & 1 else d0
+                continue
+            if code == OPC_HMASK:
+                # unscaled Hadamards on the positions of the mask in field t
+                hm = int(op["t"])
+                assert 2 <= bin(hm).count("1") and hm < 16 and fbit == 255
+                for t in range(4):
+                    if not (hm >> t) & 1:
+                        continue
+                    for j in range(16):
+                        if (j >> t) & 1:
+                            a[:, j] *= pend[:, t]
+                    pend[:, t] = 1.0
+                    for p in range(8):
+                        j0 = ((p >> t) << (t + 1)) | (p & ((1 << t) - 1))
+                        j1 = j0 | (1 << t)
+                        x0, x1 = a[:, j0].copy(), a[:, j1].copy()
+                        a[:, j0], a[:, j1] = x0 + x1, x0 - x1
                 continue
             act = int(op["act"])
             if code < OPC_X:
@@ -262,8 +280,33 @@ def test_permutation_tail_only_when_last():
     folded = compiled(n, [("h", (0,), ()), ("h", (2,), ()), ("cx", (0, 1), ()), ("x", (2,), ()),
                           ("swap", (1, 2), ())])
     assert any(OPC_XF <= int(o["code"]) < OPC_ANTI for o in kept[1])
-    assert all(int(o["code"]) < OPC_X for o in folded[1])
+    assert all(int(o["code"]) < OPC_X or int(o["code"]) == OPC_HMASK for o in folded[1])
     assert int(folded[2][16]) != 0  # the X on q2 is the map's offset
+
+
+def test_hadamards_grouped_into_one_op():
+    """Hadamards of a pass move later past ops on other local positions and
+    meet in one OPC_HMASK op; never past an op on their own position.  The
+    Deutsch-Jozsa (balanced) program at n = 11 shrinks to 10 ops; every
+    program's replay still matches the oracle (test_program_replay_matches_oracle)."""
+    ops = W.deutsch_jozsa(11, True, (1, 3, 2))
+    passes, pops, pos, osc, gen = compiled(11, ops)
+    codes = [int(o["code"]) for o in pops]
+    assert OPC_HMASK in codes
+    assert len(pops) <= 10
+    # H(0) S(0) H(1): the phase on position 0 is deferred to the end of the pass,
+    # so the Hadamards meet, and the phase stays after the Hadamard on its position
+    passes, pops, _, _, _ = compiled(2, [("h", (0,), ()), ("s", (0,), ()), ("h", (1,), ())])
+    seq = [(int(o["code"]), int(o["t"])) for o in pops]
+    assert seq[0] == (OPC_HMASK, 3) and len(seq) == 2 and seq[1][0] >= 40
+    # a phase on position 0 between H(0) and a second H(0): nothing is grouped
+    # across it (the two stay in order around it)
+    passes, pops, _, _, _ = compiled(2, [("h", (0,), ()), ("t", (0,), ()), ("h", (0,), ()),
+                                         ("h", (1,), ())])
+    assert all(int(o["code"]) != OPC_HMASK or not (int(o["t"]) & 1) for o in pops[:1])
+    # two Hadamards on different qubits with nothing between: one op
+    passes, pops, _, _, _ = compiled(3, [("h", (0,), ()), ("h", (1,), ()), ("h", (2,), ())])
+    assert len(pops) == 1 and int(pops[0]["code"]) == OPC_HMASK and int(pops[0]["t"]) == 7
 
 
 @pytest.mark.parametrize("bad,status", [
