@@ -330,6 +330,7 @@ unsigned touched_positions(const FusedOp& op) {
   if (code < OPC_XL) return 1u << (code & 3);                   // H, X, XF
   if (code < OPC_HMASK) return (1u << ((code - OPC_XL) >> 2)) | (1u << ((code - OPC_XL) & 3));
   if (code == OPC_HMASK) return op.t & 15u;
+  if (code == OPC_XP) return (1u << (op.t & 3)) | (op.c & 15u);
   if (code < OPC_CDENSE) return 1u << (code & 3);               // DENSE
   if (code < OPC_DLN) {                                         // CDENSE
     unsigned m = 1u << (code & 3);
@@ -348,6 +349,95 @@ unsigned touched_positions(const FusedOp& op) {
 // other positions (they commute: different tensor factors) until an op on
 // their position or another Hadamard comes; Hadamards that meet run as one
 // OPC_HMASK op (one dispatch instead of several).
+// An exchange op (X, CNOT) on one local position as (target, local control
+// positions, active local indices, far control mask); false for other ops.
+bool exchange_parts(const FusedOp& op, int& t, unsigned& cmask, unsigned& act, uint32_t& far) {
+  const int code = op.code;
+  if (code >= OPC_X && code < OPC_XF) {  // uncontrolled
+    t = code & 3, cmask = 0, act = 0xFFFF, far = 0;
+  } else if (code >= OPC_XF && code < OPC_XL) {  // far control
+    if (op.fbit >= 32) return false;  // the far mask covers bits 0..31
+    t = code & 3, cmask = 0, act = 0, far = 1u << op.fbit;  // on iff the far bit is 1
+  } else if (code >= OPC_XL && code < OPC_HMASK) {  // local control
+    const int c = (code - OPC_XL) & 3;
+    t = (code - OPC_XL) >> 2, cmask = 1u << c, act = kLocalControlMask[c], far = 0;
+  } else if (code == OPC_XP) {
+    uint32_t f;
+    std::memcpy(&f, &op.hc, 4);
+    t = op.t, cmask = op.c, act = op.act, far = f;
+  } else {
+    return false;
+  }
+  return true;
+}
+
+// Adjacent exchange ops on one local target (a fan of CNOTs into one qubit,
+// as in the Deutsch-Jozsa oracle) commute and compose: the pair swaps when an
+// odd number of them is active, so the run becomes one OPC_XP op whose active
+// set is the parity of the factors' (XOR of their masks) (one dispatch).
+void merge_exchanges(std::vector<FusedOp>& ops, size_t begin) {
+  {
+    // nothing to merge without two adjacent exchanges on one target
+    bool pair = false;
+    int t0 = -1;
+    for (size_t i = begin; i < ops.size() && !pair; ++i) {
+      int t;
+      unsigned cm, act;
+      uint32_t far;
+      const bool ex = exchange_parts(ops[i], t, cm, act, far);
+      pair = ex && t == t0;
+      t0 = ex ? t : -1;
+    }
+    if (!pair) return;
+  }
+  static thread_local std::vector<FusedOp> out;
+  out.clear();
+  bool any = false;
+  for (size_t i = begin; i < ops.size();) {
+    int t0;
+    unsigned cm0, act0;
+    uint32_t far0;
+    if (!exchange_parts(ops[i], t0, cm0, act0, far0)) {
+      out.push_back(ops[i++]);
+      continue;
+    }
+    size_t j = i + 1;
+    for (; j < ops.size(); ++j) {
+      int t;
+      unsigned cm, act;
+      uint32_t far;
+      if (!exchange_parts(ops[j], t, cm, act, far) || t != t0) break;
+      cm0 |= cm;
+      act0 ^= act;
+      far0 ^= far;
+    }
+    if (j == i + 1) {
+      out.push_back(ops[i++]);
+      continue;
+    }
+    any = true;
+    i = j;
+    if (act0 == 0 && far0 == 0) continue;  // an even number of every factor: the identity
+    FusedOp x{};
+    x.tbit = 0xFF;
+    x.fbit = 0xFF;
+    if (act0 == 0xFFFF && far0 == 0) {
+      x.code = static_cast<uint8_t>(OPC_X + t0);
+      x.act = 0xFFFF;
+    } else {
+      x.code = OPC_XP;
+      x.t = static_cast<uint8_t>(t0);
+      x.c = static_cast<uint8_t>(cm0);
+      x.act = static_cast<uint16_t>(act0);
+      std::memcpy(&x.hc, &far0, 4);
+    }
+    out.push_back(x);
+  }
+  if (!any) return;
+  ops.resize(begin);
+  ops.insert(ops.end(), out.begin(), out.end());
+}
+
 void group_hadamards(std::vector<FusedOp>& ops, size_t begin) {
   size_t nh = 0;
   for (size_t i = begin; i < ops.size(); ++i) nh += ops[i].code < OPC_X;
@@ -643,6 +733,7 @@ void compile_program(int n, const std::vector<const Gate*>& gs_in, Program& P,
     }
     merge_diagonals(P.ops, ps.op_begin);
     group_hadamards(P.ops, ps.op_begin);
+    merge_exchanges(P.ops, ps.op_begin);
     ps.op_count = static_cast<uint32_t>(P.ops.size() - ps.op_begin);
     // exact power-of-two rescale for this pass's unscaled Hadamards
     const int tot = h_carry + h_count;

@@ -279,6 +279,18 @@ __device__ __forceinline__ void run_ops(float2 (&a)[16], const FusedOp* __restri
         if (hm & 2) { pend_flush(a, pd, 1); h_t<1>(a); }
         if (hm & 4) { pend_flush(a, pd, 2); h_t<2>(a); }
         if (hm & 8) { pend_flush(a, pd, 3); h_t<3>(a); }
+      } else if (code == OPC_XP) {
+        // exchanges on one position under a parity of local and far bits
+        const int tt = (q0.x >> 8) & 3;
+        unsigned act2 = q0.y >> 16;
+        if (__popc(static_cast<unsigned>(base) & q0.z) & 1) act2 ^= 0xFFFFu;
+        pend_flush(a, pd, tt);
+        switch (tt) {
+          case 0: swap_t<0>(a, act2); break;
+          case 1: swap_t<1>(a, act2); break;
+          case 2: swap_t<2>(a, act2); break;
+          default: swap_t<3>(a, act2); break;
+        }
       } else {
         pend_flush(a, pd, t);
         const uint4 q1 = __ldg(rec + 1);

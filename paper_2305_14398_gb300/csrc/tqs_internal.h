@@ -30,6 +30,11 @@ namespace tqs {
 //                    in field t (two or more, in position order; they commute);
 //                    anti-diagonal factors other than X run as DENSE (fewer
 //                    kernel code paths, and their coefficients get hi + lo)
+//   OPC_XP           exchanges on local position t (field t) that commute and
+//                    compose: the pair (j, j ^ 2^t) swaps when bit j of `act`
+//                    XOR the parity of the group's physical bits in the far
+//                    mask (the first 4 bytes of hc) is 1; field c = the local
+//                    control positions (a run of X / CNOT factors on one target)
 //   OPC_DENSE + t    uncontrolled 2x2, coefficients as FP32 hi + lo
 //   OPC_CDENSE + t   controlled 2x2 (`act` mask for a local control, `fbit` far)
 //   OPC_DLN + t      diag(d0, d1), local target, uncontrolled
@@ -56,6 +61,7 @@ enum OpCode : uint8_t {
   OPC_XL = 12,       // 16 codes (t, c), c != t used
   OPC_ANTI = 28,      // end of the exchange codes
   OPC_HMASK = 28,
+  OPC_XP = 29,
   OPC_DENSE = 32,
   OPC_CDENSE = 36,
   OPC_DLN = 40,

@@ -16,7 +16,7 @@ from paper_2305_14398_gb300 import binding as B
 from paper_2305_14398_gb300 import workloads as W
 
 OPC_H, OPC_X, OPC_XF, OPC_XL, OPC_ANTI, OPC_DENSE, OPC_CDENSE = 0, 4, 8, 12, 28, 32, 36
-OPC_HMASK = 28
+OPC_HMASK, OPC_XP = 28, 29
 OPC_DLN, OPC_DLF, OPC_DFL, OPC_DFF, OPC_DLL, OPC_DLIST, OPC_DIAG16, OPC_NOP = 40, 44, 48, 52, 53, 54, 55, 56
 BIT_MASK = [0xAAAA, 0xCCCC, 0xF0F0, 0xFF00]
 
@@ -142,6 +142,23 @@ def replay(n, passes, ops, pos, out_scale=1.0, gen_index=0, uniforms=None, outco
                         x0, x1 = a[:, j0].copy(), a[:, j1].copy()
                         a[:, j0], a[:, j1] = x0 + x1, x0 - x1
                 continue
+            if code == OPC_XP:
+                # exchanges on position t where act's bit XOR the far parity is 1
+                t, act = int(op["t"]), int(op["act"])
+                far = int(np.frombuffer(op["hc"].tobytes()[:4], dtype=np.uint32)[0])
+                assert fbit == 255
+                par = np.array([bin(int(v) & far).count("1") & 1 for v in base])
+                for j in range(16):
+                    if (j >> t) & 1:
+                        a[:, j] *= pend[:, t]
+                pend[:, t] = 1.0
+                for p in range(8):
+                    j0 = ((p >> t) << (t + 1)) | (p & ((1 << t) - 1))
+                    j1 = j0 | (1 << t)
+                    on = (((act >> j0) & 1) ^ par) == 1
+                    x0, x1 = a[:, j0].copy(), a[:, j1].copy()
+                    a[on, j0], a[on, j1] = x1[on], x0[on]
+                continue
             act = int(op["act"])
             if code < OPC_X:
                 kind, t = "h", code & 3
@@ -212,6 +229,25 @@ CASES += [(f"dj{n}{b}", n, W.deutsch_jozsa(n, b, (5, n, int(b)))) for n in (3, 6
 CASES += [(f"rand{n}_{k}", n, W.random_small(n, 8 * n, (6, n, k))) for n in (1, 2, 3, 4, 5, 6, 8) for k in range(3)]
 CASES += [(f"mixed{n}", n, W.random_mixed(n, 12, (7, n))) for n in (4, 7, 9, 12)]
 CASES += [(f"layered{n}", n, W.random_layered(n, 3, (8, n))) for n in (5, 10, 12)]
+
+
+def cnot_fan(n, seed):
+    """H on every qubit, then CNOTs from a seeded subset of qubits into one target,
+    with X gates on the target among them, then H again: runs of exchanges on one
+    position with local and far controls (merged into one parity op)."""
+    g = W.rng(9, n, seed)
+    t = int(g.integers(0, n))
+    ops = [("h", (q,), ()) for q in range(n)]
+    for c in range(n):
+        if c != t and g.random() < 0.6:
+            ops.append(("cx", (c, t), ()))
+        if g.random() < 0.2:
+            ops.append(("x", (t,), ()))
+    ops += [("h", (q,), ()) for q in range(n) if q != t]
+    return ops
+
+
+CASES += [(f"fan{n}_{k}", n, cnot_fan(n, k)) for n in (5, 9, 12) for k in range(2)]
 
 
 @pytest.mark.parametrize("name,n,ops", CASES, ids=[c[0] for c in CASES])
@@ -287,7 +323,7 @@ def test_permutation_tail_only_when_last():
 def test_hadamards_grouped_into_one_op():
     """Hadamards of a pass move later past ops on other local positions and
     meet in one OPC_HMASK op; never past an op on their own position.  The
-    Deutsch-Jozsa (balanced) program at n = 11 shrinks to 10 ops; every
+    Deutsch-Jozsa (balanced) program at n = 11 shrinks to 10 ops or fewer; every
     program's replay still matches the oracle (test_program_replay_matches_oracle)."""
     ops = W.deutsch_jozsa(11, True, (1, 3, 2))
     passes, pops, pos, osc, gen = compiled(11, ops)
@@ -304,6 +340,10 @@ def test_hadamards_grouped_into_one_op():
     passes, pops, _, _, _ = compiled(2, [("h", (0,), ()), ("t", (0,), ()), ("h", (0,), ()),
                                          ("h", (1,), ())])
     assert all(int(o["code"]) != OPC_HMASK or not (int(o["t"]) & 1) for o in pops[:1])
+    # the oracle's CNOT fan into the ancilla: one exchange op under a parity
+    passes, pops, _, _, _ = compiled(11, ops)
+    assert sum(int(o["code"]) == OPC_XP for o in pops) == 1
+    assert not any(OPC_XF <= int(o["code"]) < OPC_ANTI for o in pops)
     # two Hadamards on different qubits with nothing between: one op
     passes, pops, _, _, _ = compiled(3, [("h", (0,), ()), ("h", (1,), ()), ("h", (2,), ())])
     assert len(pops) == 1 and int(pops[0]["code"]) == OPC_HMASK and int(pops[0]["t"]) == 7
