@@ -37,10 +37,10 @@ WORKLOAD = "paper-shaped 11-qubit circuits (GHZ / DJ-constant / DJ-balanced / QF
 
 # DRAM bytes (read + write) per launch of the fused kernel (two warps per
 # circuit, the autotuned shape) on this workload, from the ncu capture
-# summarised in profiles/: 36.70 MB read + 476.53 MB written for one launch
+# summarised in profiles/: 19.68 MB read + 475.97 MB written for one launch
 # over the 16384 circuits of a step.  Set back to None whenever the kernel
 # changes, until it is captured again.
-NCU_TRAFFIC_BYTES = 36_699_392 + 476_533_760
+NCU_TRAFFIC_BYTES = 19_684_352 + 475_965_184
 
 
 def parse_args():
@@ -439,9 +439,9 @@ def run_tqs(args):
                        "sequential_value": whole_job_rate(count * e2e_steps, world, te_seq),
                        "path": "tqs_batch_create_packed (host gate arrays) + tqs_batch_run_host "
                                "(page-locked host buffers, written by the kernel over C2C) + "
-                               "tqs_batch_destroy; value: creation of the next batch on a second "
-                               "host thread overlaps the current run; sequential_value: one batch "
-                               "after the other"}
+                               "tqs_batch_destroy; value: a second host thread creates the next "
+                               "batch (and destroys finished ones) while the current one runs; "
+                               "sequential_value: one batch after the other"}
 
     # ----------------------------------------------- measured peaks (rank 0)
     # (after the end-to-end leg: the sustained GEMM loop heats the GPU)
@@ -593,16 +593,22 @@ def step_stats(ms):
 
 def e2e_pipelined(B, arrays, bufs, steps):
     """End to end through the public API with two host threads: a producer
-    creates the batches (host compile from the gate arrays) while the caller
-    runs each with tqs_batch_run_host into alternating host buffers and
-    destroys it.  Returns the wall time of `steps` batches."""
+    creates the batches (host compile from the gate arrays) and destroys the
+    ones already run, while the caller runs each with tqs_batch_run_host into
+    alternating host buffers.  Returns the wall time of `steps` batches."""
     import queue
     q = queue.Queue(maxsize=2)
+    done = queue.Queue()
     errors = []
 
     def producer():
         try:
             for _ in range(steps):
+                while True:  # free what the caller has finished with
+                    try:
+                        B.tqs_batch_destroy(done.get_nowait())
+                    except queue.Empty:
+                        break
                 q.put(B.tqs_batch_create_packed(*arrays))
         except Exception as e:  # surfaced by the consumer
             errors.append(e)
@@ -616,8 +622,10 @@ def e2e_pipelined(B, arrays, bufs, steps):
         if bb is None:
             raise errors[0]
         B.tqs_batch_run_host(bb, *bufs[k % 2])
-        B.tqs_batch_destroy(bb)
+        done.put(bb)
     th.join()
+    while not done.empty():
+        B.tqs_batch_destroy(done.get_nowait())
     return time.perf_counter() - t0
 
 

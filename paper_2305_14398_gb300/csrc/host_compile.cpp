@@ -200,6 +200,8 @@ int nondiag_target(int code) {
 // one position between two non-diagonal ops on it commute with everything in
 // between: each list is emitted just before the next non-diagonal op on its
 // position (or at the end of the pass).
+constexpr size_t kMaxCachedRun = 12;  // longest run of local phases whose product is cached
+
 void merge_diagonals(std::vector<FusedOp>& ops, size_t begin) {
   {
     // nothing to merge: no phase factor and no two local-local factors in a row
@@ -292,6 +294,36 @@ void merge_diagonals(std::vector<FusedOp>& ops, size_t begin) {
       ++i;
       continue;
     }
+    // The same runs recur across the circuits of a batch (every QFT of one
+    // size has the same ones): a small direct-mapped cache per host thread,
+    // keyed by the run's factors (positions and FP32 values), holds the two
+    // records of the result.
+    struct RunEntry {
+      uint32_t key[kMaxCachedRun * 5];
+      size_t len = 0;
+      FusedOp a, b;
+    };
+    static thread_local RunEntry run_cache[64];
+    const size_t len = j - i;
+    uint32_t key[kMaxCachedRun * 5];
+    uint64_t h = 0x9E3779B97F4A7C15ull;
+    if (len <= kMaxCachedRun) {
+      for (size_t k = 0; k < len; ++k) {
+        const FusedOp& op = out[i + k];
+        uint32_t* w = key + 5 * k;
+        w[0] = static_cast<uint32_t>(op.t) | (static_cast<uint32_t>(op.c) << 8);
+        std::memcpy(w + 1, &op.m[0], 8);
+        std::memcpy(w + 3, &op.m[1], 8);
+        for (int x = 0; x < 5; ++x) h = (h ^ w[x]) * 0x100000001B3ull;
+      }
+      RunEntry& ce = run_cache[h >> 58];
+      if (ce.len == len && std::memcmp(ce.key, key, len * 5 * sizeof(uint32_t)) == 0) {
+        ops.push_back(ce.a);
+        ops.push_back(ce.b);
+        i = j;
+        continue;
+      }
+    }
     cd d[16];
     for (int e = 0; e < 16; ++e) d[e] = 1.0;
     for (size_t k = i; k < j; ++k) {
@@ -313,6 +345,13 @@ void merge_diagonals(std::vector<FusedOp>& ops, size_t begin) {
       a.lo[e] = to_unit_f2(d[4 + e]);
       b.m[e] = to_unit_f2(d[8 + e]);
       b.lo[e] = to_unit_f2(d[12 + e]);
+    }
+    if (len <= kMaxCachedRun) {
+      RunEntry& ce = run_cache[h >> 58];
+      std::memcpy(ce.key, key, len * 5 * sizeof(uint32_t));
+      ce.len = len;
+      ce.a = a;
+      ce.b = b;
     }
     ops.push_back(a);
     ops.push_back(b);
@@ -686,9 +725,14 @@ void compile_program(int n, const std::vector<const Gate*>& gs_in, Program& P,
           pass_cost += 3.0;
         }
       } else {
-        op.m[0] = to_unit_f2(u.m[0]);
-        op.m[1] = to_unit_f2(u.m[3]);
-        op.m[2] = to_unit_f2(u.m[3] / u.m[0]);
+        if (u.m[0] == cd(1.0)) {  // a phase gate: d1 and d1 / d0 are the same value
+          op.m[0] = make_float2(1.f, 0.f);
+          op.m[1] = op.m[2] = to_unit_f2(u.m[3]);
+        } else {
+          op.m[0] = to_unit_f2(u.m[0]);
+          op.m[1] = to_unit_f2(u.m[3]);
+          op.m[2] = to_unit_f2(u.m[3] / u.m[0]);
+        }
         op.d0one = (u.m[0] == cd(1.0)) ? 1 : 0;
         op.hc = (tl >= 0 && cl < 0) ? op.m[2] : op.m[1];
         pass_cost += 0.25;
