@@ -521,6 +521,10 @@ def run_tqs(args):
     if not args.no_chain and rank == 0:
         line["chain"] = bench_chain(B, W, torch, peaks, mpeaks)
         line["chain"]["cublas"] = bench_cublas_chain(B, W, torch)
+        # the library reference points also as top-level keys of the chain leg
+        for k, v in line["chain"]["cublas"].items():
+            if k.startswith("n1"):
+                line["chain"][k] = v
     # the column-sharded chain: every rank its own block of columns, no exchange
     if not args.no_chain:
         sh = bench_chain_sharded(B, W, torch, dist, rank, world, peaks)
@@ -884,6 +888,15 @@ def bench_chain(B, W, torch, peaks, mpeaks):
             own_peak = peak if prec == B.PREC_TC_BF16X3 else tf32
             rec["tensor_peak_tflops"] = own_peak
             rec["tensor_frac"] = issued / own_peak
+            # useful work (a complex GEMM, 8 N^3 per product) against the
+            # sustained peak of the precision (bf16 from MEASURED_PEAKS, TF32
+            # measured by this bench): the fraction a caller gets per flop asked
+            sus = (peaks.get("bf16_tflops_sustained") if prec == B.PREC_TC_BF16X3
+                   else mpeaks.get("tf32_tflops_sustained"))
+            if sus:
+                rec["useful_tflops"] = 8.0 * N ** 3 * gemms / sec / 1e12
+                rec["useful_frac_of_sustained"] = rec["useful_tflops"] / sus
+                rec["sustained_peak_tflops"] = sus
         if n == 12:
             cols = [0, 1, 777, 2048, 4095]
             got = U[:, cols].cpu().numpy().astype(np.complex128)
