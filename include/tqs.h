@@ -590,6 +590,13 @@ tqs_status tqs_check_violations(uint32_t* count, int reset);
  * 2e-5 per product at K = 16384 in BF16x3).  Results depend on it only
  * through rounding. */
 #define TQS_OPT_CHAIN_KCHUNK 10
+/* TQS_OPT_CHAIN_PAIR, key = 0: 1 runs the tensor-core chain's GEMMs as
+ * clusters of two CTAs on adjacent tile rows that load half of each shared B
+ * tile and multicast it to both (half the B traffic from L2), where the number
+ * of 128-row tiles is even; 0 (default): one CTA per tile (measured 1-2 %
+ * faster at n = 12..14: a stage is released only when both CTAs have consumed
+ * it).  Results are bitwise the same. */
+#define TQS_OPT_CHAIN_PAIR 11
 
 tqs_status tqs_set_option(int option, int key, int64_t value);
 tqs_status tqs_get_option(int option, int key, int64_t* value);

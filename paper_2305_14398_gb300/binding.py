@@ -517,6 +517,7 @@ OPT_CTA_THREADS = 7
 OPT_FSV_TILE_Q = 8
 OPT_CHAIN_GROUP = 9
 OPT_CHAIN_KCHUNK = 10
+OPT_CHAIN_PAIR = 11
 
 
 def tqs_set_option(option: int, key: int, value: int) -> None:

@@ -515,7 +515,7 @@ static tqs_status unitary_block(tqs_circuit* c, int prec, int col0, int ncols, t
   TQS_CUDA(cudaMemsetAsync(c->d_err.p, 0, sizeof(int), s), "tqs_circuit_unitary: memset");
   TQS_CUDA(chain_tc(c->d_factors.as<StepFactor>(), c->steps.data(), c->nsteps, c->n, prec, col0, ncols,
                     U, ldu, c->d_chain.p, c->d_err.as<int>(), g_chain_group.load(),
-                    g_chain_kchunk.load(), s),
+                    g_chain_kchunk.load(), g_chain_pair.load(), s),
            "tqs_circuit_unitary: tensor-core chain");
   int err = 0;
   TQS_CUDA(cudaMemcpyAsync(&err, c->d_err.p, sizeof(int), cudaMemcpyDeviceToHost, s),

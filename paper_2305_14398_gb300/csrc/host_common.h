@@ -773,6 +773,8 @@ inline std::atomic<int> g_chain_group{16};
 // TQS_OPT_CHAIN_KCHUNK: K per accumulation chunk of the tensor-core chain
 // (0: the precision's default).
 inline std::atomic<int> g_chain_kchunk{0};
+// TQS_OPT_CHAIN_PAIR: the chain's GEMMs as two-CTA clusters sharing B tiles (1) or not (0).
+inline std::atomic<int> g_chain_pair{0};
 
 inline LaunchPlan plan_for(int team, int max_nint, int jobs, int warps_hint) {
   LaunchPlan lp{team, 1, 4, 1};

@@ -129,7 +129,13 @@ __device__ __forceinline__ void store_split(const float (&v)[K], typename Prec<P
   }
 }
 
-template <int PREC>
+// PAIR: the grid runs as clusters of two CTAs on the tile rows 2i and 2i + 1 of
+// one tile column; they need the same B tiles, so each loads half of every B
+// tile (64 rows, hi and lo) and multicasts it into both CTAs' stage, halving the
+// B traffic from L2.  A stage is then released (empty barrier) only when the
+// MMAs of both CTAs have consumed it: each MMA issuer's commit arrives on the
+// empty barrier of both CTAs.
+template <int PREC, bool PAIR>
 __global__ void __launch_bounds__(kGemmThreads, 1)
     chain_gemm_kernel(const __grid_constant__ CUtensorMap tmA,
                       const __grid_constant__ CUtensorMap tmB,
@@ -149,14 +155,19 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
   // Grouped raster: consecutive CTAs walk down a band of P.group tile rows
   // before moving right, so the CTAs resident at one time share a few A and B
   // panels in L2 instead of streaming all of B once per tile row.
-  const int num_m = P.M / BM, num_n = P.N / BN;
-  const int pid = blockIdx.x;
-  const int band = pid / (P.group * num_n);
-  const int first_m = band * P.group;
-  const int gsize = min(num_m - first_m, P.group);
-  const int in_band = pid - band * P.group * num_n;
-  const int tile_m = (first_m + in_band % gsize) * BM;  // rows of V = rows of V'
+  // (PAIR: the raster runs over pairs of tile rows; the cluster's two CTAs take
+  // the two rows of a pair)
+  const int crank = PAIR ? static_cast<int>(cluster_ctarank()) : 0;
+  const int num_m = P.M / BM / (PAIR ? 2 : 1), num_n = P.N / BN;
+  const int grp = PAIR ? max(1, P.group / 2) : P.group;
+  const int pid = PAIR ? static_cast<int>(blockIdx.x >> 1) : static_cast<int>(blockIdx.x);
+  const int band = pid / (grp * num_n);
+  const int first_m = band * grp;
+  const int gsize = min(num_m - first_m, grp);
+  const int in_band = pid - band * grp * num_n;
+  const int tile_m = ((first_m + in_band % gsize) * (PAIR ? 2 : 1) + crank) * BM;  // rows of V
   const int tile_n = (in_band / gsize) * BN;            // rows of S = columns of V'
+  constexpr uint16_t kPairMask = 0x3;
   const int nkb = P.N / BK;                             // k blocks
   const int kc = P.kchunk_blocks;                       // k blocks per accumulation chunk
   const int nchunks = (nkb + kc - 1) / kc;
@@ -166,7 +177,7 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
   if (threadIdx.x == 0) {
     for (int s = 0; s < kStages; ++s) {
       mbar_init(smem_u32(&full[s]), 1);
-      mbar_init(smem_u32(&empty[s]), 1);
+      mbar_init(smem_u32(&empty[s]), PAIR ? 2 : 1);
     }
     mbar_init(smem_u32(tmem_full), 1);
     mbar_init(smem_u32(tmem_empty), kEpiWarps);
@@ -178,7 +189,8 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
     tmem_relinquish();
   }
   tc_fence_before();
-  __syncthreads();
+  if (PAIR) cluster_sync();  // the peer's barriers exist before any multicast or commit
+  else __syncthreads();
   tc_fence_after();
   const uint32_t tmem_base = *tmem_holder;
 
@@ -208,8 +220,16 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
             mbar_arrive_expect_tx(fb, kStageBytes);
             tma_load_3d(st, &tmA, kb * BK, tile_m, 2 * j, fb);
             tma_load_3d(st + kTileBytes, &tmA, kb * BK, tile_m, 2 * j + 1, fb);
-            tma_load_3d(st + 2 * kTileBytes, &tmB, kb * BK, tile_n, 2 * j, fb);
-            tma_load_3d(st + 3 * kTileBytes, &tmB, kb * BK, tile_n, 2 * j + 1, fb);
+            if (PAIR) {  // this CTA's half of the B tile (64 rows), into both CTAs
+              const uint32_t half = static_cast<uint32_t>(crank) * (kTileBytes / 2);
+              tma_load_3d_mc(st + 2 * kTileBytes + half, &tmB, kb * BK, tile_n + crank * (BN / 2), 2 * j,
+                             fb, kPairMask);
+              tma_load_3d_mc(st + 3 * kTileBytes + half, &tmB, kb * BK, tile_n + crank * (BN / 2),
+                             2 * j + 1, fb, kPairMask);
+            } else {
+              tma_load_3d(st + 2 * kTileBytes, &tmB, kb * BK, tile_n, 2 * j, fb);
+              tma_load_3d(st + 3 * kTileBytes, &tmB, kb * BK, tile_n, 2 * j + 1, fb);
+            }
           }
         }
       }
@@ -217,6 +237,11 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
       // flight when the CTA exits, whatever happened downstream.
       for (int i = (it > kStages ? it - kStages : 0); i < it; ++i)
         mbar_wait(smem_u32(&full[i % kStages]), (i / kStages) & 1, P.err);
+      // PAIR: and for both MMA issuers' last releases, the arrivals that the
+      // peer sends to this CTA's barriers (none may come after the exit)
+      if (PAIR)
+        for (int i = (it > kStages ? it - kStages : 0); i < it; ++i)
+          mbar_wait(smem_u32(&empty[i % kStages]), (i / kStages) & 1, P.err);
     }
   } else if (warp == 1) {
     if (lane == 0) {
@@ -257,7 +282,9 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
               Prec<PREC>::mma(d, sw128_kmajor_desc(a_hi + off), sw128_kmajor_desc(b_lo + off), 1u);
               Prec<PREC>::mma(d, sw128_kmajor_desc(a_lo + off), sw128_kmajor_desc(b_hi + off), 1u);
             }
-            mma_commit(smem_u32(&empty[s]));  // the stage is free once these MMAs finish
+            // the stage is free once these MMAs finish (PAIR: in both CTAs)
+            if (PAIR) mma_commit_mc(smem_u32(&empty[s]), kPairMask);
+            else mma_commit(smem_u32(&empty[s]));
           }
         }
         if (ok) mma_commit(smem_u32(tmem_full));  // this chunk's accumulators are final
@@ -336,7 +363,8 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
     }
   }
   tc_fence_before();
-  __syncthreads();
+  if (PAIR) cluster_sync();  // neither CTA exits while the other may still signal it
+  else __syncthreads();
   if (warp == 0) {
     tc_fence_after();
     tmem_dealloc(tmem_base, kTmemCols);
@@ -478,14 +506,14 @@ EncodeTiledFn encode_fn() {
 // [6][rows][N] planes as a 3-D tensor {k, row, plane}, box {one 128-byte row,
 // 128 rows, 1 plane}, 128-byte swizzle.
 template <int PREC>
-bool make_planes_map(CUtensorMap* m, void* base, int N, int rows) {
+bool make_planes_map(CUtensorMap* m, void* base, int N, int rows, int box_rows = BM) {
   EncodeTiledFn fn = encode_fn();
   if (!fn) return false;
   const cuuint64_t es = sizeof(typename Prec<PREC>::E);
   const cuuint64_t dims[3] = {static_cast<cuuint64_t>(N), static_cast<cuuint64_t>(rows), 6};
   const cuuint64_t strides[2] = {static_cast<cuuint64_t>(N) * es,
                                  static_cast<cuuint64_t>(rows) * N * es};
-  const cuuint32_t box[3] = {static_cast<cuuint32_t>(Prec<PREC>::BK), BM, 1};
+  const cuuint32_t box[3] = {static_cast<cuuint32_t>(Prec<PREC>::BK), static_cast<cuuint32_t>(box_rows), 1};
   const cuuint32_t estr[3] = {1, 1, 1};
   return fn(m, Prec<PREC>::kTmaType, 3, base, dims, strides, box, estr,
             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
@@ -565,10 +593,36 @@ struct ChainEvents {
   }
 };
 
+// One GEMM launch: plain, or (pair) as clusters of two CTAs sharing B tiles.
+template <int PREC>
+cudaError_t launch_gemm(bool pair, int grid, const CUtensorMap& mA, const CUtensorMap& mB,
+                        const GemmParams<typename Prec<PREC>::E>& P, cudaStream_t s) {
+  if (!pair) {
+    chain_gemm_kernel<PREC, false><<<grid, kGemmThreads, kGemmSmem, s>>>(mA, mB, P);
+    count_launches(1);
+    return cudaGetLastError();
+  }
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(static_cast<unsigned>(grid));
+  cfg.blockDim = dim3(kGemmThreads);
+  cfg.dynamicSmemBytes = kGemmSmem;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = 2;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  const cudaError_t e = cudaLaunchKernelEx(&cfg, chain_gemm_kernel<PREC, true>, mA, mB, P);
+  count_launches(1);
+  return e;
+}
+
 template <int PREC>
 cudaError_t chain_tc_impl(const StepFactor* d_factors, const StepDesc* steps, int nsteps, int n,
                           int col0, int ncols, float2* d_U, int64_t ldu, void* scratch, int* d_err,
-                          int group, int kchunk, cudaStream_t s) {
+                          int group, int kchunk, int pair_opt, cudaStream_t s) {
   using E = typename Prec<PREC>::E;
   const int N = 1 << n;
   const size_t MN = size_t(ncols) * N;  // the block's V planes: ncols rows of V
@@ -576,13 +630,19 @@ cudaError_t chain_tc_impl(const StepFactor* d_factors, const StepDesc* steps, in
   E* V0 = static_cast<E*>(scratch);
   E* V1 = V0 + 6 * MN;
   E* S[2] = {V1 + 6 * MN, V1 + 6 * MN + 6 * NN};  // S_k in S[(k - 1) & 1]
+  // cluster pairs need an even number of tile rows
+  const bool pair = pair_opt != 0 && (ncols / BM) % 2 == 0;
   CUtensorMap mV0, mV1, mS[2];
+  const int b_rows = pair ? BN / 2 : BN;  // B box: a CTA's half of the tile when paired
   if (!make_planes_map<PREC>(&mV0, V0, N, ncols) || !make_planes_map<PREC>(&mV1, V1, N, ncols) ||
-      !make_planes_map<PREC>(&mS[0], S[0], N, N) || !make_planes_map<PREC>(&mS[1], S[1], N, N))
+      !make_planes_map<PREC>(&mS[0], S[0], N, N, b_rows) || !make_planes_map<PREC>(&mS[1], S[1], N, N, b_rows))
     return cudaErrorNotSupported;
-  cudaError_t e = cudaFuncSetAttribute(chain_gemm_kernel<PREC>,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       static_cast<int>(kGemmSmem));
+  cudaError_t e = pair ? cudaFuncSetAttribute(chain_gemm_kernel<PREC, true>,
+                                              cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                              static_cast<int>(kGemmSmem))
+                       : cudaFuncSetAttribute(chain_gemm_kernel<PREC, false>,
+                                              cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                              static_cast<int>(kGemmSmem));
   if (e != cudaSuccess) return e;
   ChainStreams cs;
   if ((e = chain_streams(&cs)) != cudaSuccess) return e;
@@ -622,9 +682,7 @@ cudaError_t chain_tc_impl(const StepFactor* d_factors, const StepDesc* steps, in
       P.kchunk_blocks = std::max(1, (kchunk > 0 ? kchunk : Prec<PREC>::kDefaultKChunk) / Prec<PREC>::BK);
       P.err = d_err;
       const int grid = (N / BN) * (ncols / BM);
-      chain_gemm_kernel<PREC><<<grid, kGemmThreads, kGemmSmem, cs.gemm>>>(cur0 ? mV0 : mV1, mS[b], P);
-      count_launches(1);
-      if ((r = cudaGetLastError()) != cudaSuccess) return r;
+      if ((r = launch_gemm<PREC>(pair, grid, cur0 ? mV0 : mV1, mS[b], P, cs.gemm)) != cudaSuccess) return r;
       if ((r = cudaEventRecord(ev.gemm_done[b], cs.gemm)) != cudaSuccess) return r;
       cur0 = !cur0;
     }
@@ -679,16 +737,16 @@ size_t chain_tc_scratch_bytes(int n, int prec, int ncols) {
 // d_U[r * ldu + j].  n >= 7; col0 and ncols multiples of 128.
 cudaError_t chain_tc(const StepFactor* d_factors, const StepDesc* steps, int nsteps, int n,
                      int prec, int col0, int ncols, float2* d_U, int64_t ldu, void* scratch,
-                     int* d_err, int group, int kchunk, cudaStream_t s) {
+                     int* d_err, int group, int kchunk, int pair, cudaStream_t s) {
   if (n < 7 || nsteps < 2 || col0 % BM || ncols % BM || ncols < BM || col0 + ncols > (1 << n) ||
       ldu < ncols || group < 1 || group > kMaxGroupM || kchunk < 0 || kchunk % 64)
     return cudaErrorInvalidValue;
   if (prec == TQS_PREC_TC_BF16X3)
     return chain_tc_impl<TQS_PREC_TC_BF16X3>(d_factors, steps, nsteps, n, col0, ncols, d_U, ldu,
-                                             scratch, d_err, group, kchunk, s);
+                                             scratch, d_err, group, kchunk, pair, s);
   if (prec == TQS_PREC_TC_TF32X3)
     return chain_tc_impl<TQS_PREC_TC_TF32X3>(d_factors, steps, nsteps, n, col0, ncols, d_U, ldu,
-                                             scratch, d_err, group, kchunk, s);
+                                             scratch, d_err, group, kchunk, pair, s);
   return cudaErrorInvalidValue;
 }
 

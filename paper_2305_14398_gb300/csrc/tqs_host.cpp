@@ -498,6 +498,13 @@ tqs_status tqs_set_option(int option, int key, int64_t value) {
     g_chain_kchunk.store(static_cast<int>(value));
     return TQS_OK;
   }
+  if (option == TQS_OPT_CHAIN_PAIR) {
+    if (key != 0) return fail(TQS_ERR_ARG, "tqs_set_option: key %d of TQS_OPT_CHAIN_PAIR is not 0", key);
+    if (value != 0 && value != 1)
+      return fail(TQS_ERR_ARG, "tqs_set_option: TQS_OPT_CHAIN_PAIR %lld is not 0 or 1", static_cast<long long>(value));
+    g_chain_pair.store(static_cast<int>(value));
+    return TQS_OK;
+  }
   return fail(TQS_ERR_ARG, "tqs_set_option: unknown option %d", option);
 }
 
@@ -531,6 +538,11 @@ tqs_status tqs_get_option(int option, int key, int64_t* value) {
   if (option == TQS_OPT_FSV_MAX_GATES) {
     if (key != 0) return fail(TQS_ERR_ARG, "tqs_get_option: key %d of TQS_OPT_FSV_MAX_GATES is not 0", key);
     *value = g_fsv_max_gates.load();
+    return TQS_OK;
+  }
+  if (option == TQS_OPT_CHAIN_PAIR) {
+    if (key != 0) return fail(TQS_ERR_ARG, "tqs_get_option: key %d of option %d is not 0", key, option);
+    *value = g_chain_pair.load();
     return TQS_OK;
   }
   if (option == TQS_OPT_CTA_THREADS || option == TQS_OPT_FSV_TILE_Q || option == TQS_OPT_CHAIN_GROUP ||

@@ -222,7 +222,7 @@ size_t chain_tc_scratch_bytes(int n, int prec, int ncols);
 // group: output-tile rows per raster band of the GEMM grid (L2 reuse).
 cudaError_t chain_tc(const StepFactor* d_factors, const StepDesc* steps, int nsteps, int n,
                      int prec, int col0, int ncols, float2* d_U, int64_t ldu, void* scratch,
-                     int* d_err, int group, int kchunk, cudaStream_t s);
+                     int* d_err, int group, int kchunk, int pair, cudaStream_t s);
 size_t chain_simt_scratch_bytes(int n, int ncols);
 cudaError_t chain_simt(const StepFactor* d_factors, const StepDesc* steps, int nsteps, int n,
                        int col0, int ncols, float2* d_U, int64_t ldu, void* scratch, cudaStream_t s);

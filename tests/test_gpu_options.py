@@ -100,3 +100,34 @@ def test_chain_group_bitwise(prec):
         B.tqs_circuit_destroy(c)
     for g in (1, 3, 64):
         assert np.array_equal(out[g].view(np.uint32), out[16].view(np.uint32)), g
+
+
+@pytest.mark.parametrize("prec", [B.PREC_TC_BF16X3, B.PREC_TC_TF32X3])
+@pytest.mark.parametrize("n", [8, 11])
+def test_chain_pair_bitwise(prec, n):
+    """TQS_OPT_CHAIN_PAIR (two-CTA clusters sharing B tiles by multicast): the
+    circuit unitary is bitwise that of one CTA per tile, and a column block of
+    an odd number of tiles (no pairs) matches the whole unitary's columns."""
+    ops = W.random_layered(n, 4, (100, n))
+    c = B.circuit_from_ops(n, ops)
+    out = {}
+    try:
+        for pair in (0, 1):
+            B.tqs_set_option(B.OPT_CHAIN_PAIR, 0, pair)
+            U = torch.empty((1 << n, 1 << n), dtype=torch.complex64, device="cuda")
+            B.tqs_circuit_unitary(c, prec, U)
+            torch.cuda.synchronize()
+            out[pair] = U.cpu().numpy()
+        # an odd number of 128-column tiles: the pair option falls back to single CTAs
+        w = 384 if n >= 10 else 128
+        blk = torch.empty((1 << n, w), dtype=torch.complex64, device="cuda")
+        B.tqs_circuit_unitary_cols(c, prec, 128, w, blk)
+        torch.cuda.synchronize()
+        cols = blk.cpu().numpy()
+    finally:
+        B.tqs_set_option(B.OPT_CHAIN_PAIR, 0, 0)
+        B.tqs_circuit_destroy(c)
+    assert np.array_equal(out[1].view(np.uint32), out[0].view(np.uint32))
+    assert np.array_equal(cols.view(np.uint32), out[1][:, 128:128 + w].view(np.uint32))
+    want = fsv_route.unitary_columns(n, ops, [0, 200, (1 << n) - 1])
+    assert np.max(np.abs(out[1][:, [0, 200, (1 << n) - 1]] - want)) <= 1e-4

@@ -787,7 +787,8 @@ def test_launch_shape_options_validated():
     for opt, good, bad in [(B.OPT_CTA_THREADS, (256, 512), (128, 300, 1024)),
                            (B.OPT_FSV_TILE_Q, (0, 10, 13), (9, 14, -1)),
                            (B.OPT_CHAIN_GROUP, (1, 16, 64), (0, 65)),
-                           (B.OPT_CHAIN_KCHUNK, (0, 64, 512, 1 << 20), (-64, 32, 100, (1 << 20) + 64))]:
+                           (B.OPT_CHAIN_KCHUNK, (0, 64, 512, 1 << 20), (-64, 32, 100, (1 << 20) + 64)),
+                           (B.OPT_CHAIN_PAIR, (0, 1), (-1, 2))]:
         old = B.tqs_get_option(opt, 0)
         try:
             for v in good:
