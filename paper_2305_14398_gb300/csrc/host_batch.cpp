@@ -239,6 +239,7 @@ static tqs_status batch_upload(tqs_batch* b, cudaStream_t s) {
     TQS_CUDA(b->d_gscratch.ensure(size_t(b->plans[TEAM_GLOBAL].grid) *
                                   (size_t(1) << kGlobalSlotQ) * sizeof(float2)),
              "tqs_batch: cudaMalloc scratch");
+  TQS_CUDA(b->ensure_side(), "tqs_batch: side streams");
   b->uploaded = true;
   return TQS_OK;
 }
@@ -253,6 +254,13 @@ static tqs_status batch_enqueue_at(tqs_batch* b, char* base, size_t order_off, s
   TQS_CUDA(cudaMemsetAsync(counters, 0, 3 * sizeof(int32_t), s), "tqs_batch: memset counters");
   int k = 0;
   int first = 0;
+  int kinds = 0;
+  for (int t = 0; t < 3; ++t) kinds += b->n_team[t] > 0;
+  const bool fork = kinds > 1;  // (the side streams exist: ensure_side before any capture)
+  if (fork) {
+    if (!b->ev_fork) return fail(TQS_ERR_STATE, "tqs_batch: side streams missing");
+    TQS_CUDA(cudaEventRecord(b->ev_fork, s), "tqs_batch: fork");
+  }
   for (int t = 0; t < 3; ++t) {
     if (b->n_team[t] == 0) continue;
     FusedLaunch L{};
@@ -271,10 +279,19 @@ static tqs_status batch_enqueue_at(tqs_batch* b, char* base, size_t order_off, s
     L.warps_per_cta = b->plans[t].warps;
     L.slice_q = b->plans[t].slice_q;
     L.grid = b->plans[t].grid;
-    TQS_CUDA(launch_fused(L, s), "tqs_batch: launch");
+    if (fork) {
+      TQS_CUDA(cudaStreamWaitEvent(b->side[t], b->ev_fork, 0), "tqs_batch: fork");
+      TQS_CUDA(launch_fused(L, b->side[t]), "tqs_batch: launch");
+      TQS_CUDA(cudaEventRecord(b->ev_join[t], b->side[t]), "tqs_batch: join");
+    } else {
+      TQS_CUDA(launch_fused(L, s), "tqs_batch: launch");
+    }
     first += b->n_team[t];
     ++k;
   }
+  if (fork)
+    for (int t = 0; t < 3; ++t)
+      if (b->n_team[t] > 0) TQS_CUDA(cudaStreamWaitEvent(s, b->ev_join[t], 0), "tqs_batch: join");
   if (kernels) *kernels = k;
   return TQS_OK;
 }
@@ -431,6 +448,7 @@ tqs_status tqs_batch_run_host(tqs_batch* b, tqs_c64* h_states, double* h_probs, 
   double* dn = zn ? zn : reinterpret_cast<double*>(base + norms_off);
   const size_t gscr_at = (total + 255) & ~size_t(255);
   b->exact_probs = g_exact_probs.load();
+  TQS_CUDA(b->ensure_side(), "tqs_batch_run_host: side streams");
   tqs_status st = batch_enqueue_at(b, base, order_off, counter_off,
                                    reinterpret_cast<float2*>(base + gscr_at), ds, dp, dn, s);
   if (st != TQS_OK) return st;

@@ -1004,10 +1004,32 @@ struct tqs_batch {
   int g_exact = -1;
   int exact_probs = 0;             // TQS_OPT_EXACT_PROBS when the batch last ran
   int graph_kernels = 0;
+  // When the batch holds circuits of more than one team kind, their kernels run
+  // side by side: forked from the caller's stream onto these streams and
+  // joined back (inside a captured graph too), so the kinds share the GPU in
+  // each other's tails instead of running one after the other.
+  cudaStream_t side[3] = {nullptr, nullptr, nullptr};
+  cudaEvent_t ev_fork = nullptr;
+  cudaEvent_t ev_join[3] = {nullptr, nullptr, nullptr};
+  cudaError_t ensure_side() {
+    if (ev_fork) return cudaSuccess;
+    cudaError_t e = cudaSuccess;
+    for (int t = 0; t < 3 && e == cudaSuccess; ++t) {
+      if (!side[t]) e = cudaStreamCreateWithFlags(&side[t], cudaStreamNonBlocking);
+      if (e == cudaSuccess && !ev_join[t]) e = cudaEventCreateWithFlags(&ev_join[t], cudaEventDisableTiming);
+    }
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ev_fork, cudaEventDisableTiming);
+    return e;
+  }
   ~tqs_batch() {
     if (exec) cudaGraphExecDestroy(exec);
     if (graph) cudaGraphDestroy(graph);
     if (cap_stream) cudaStreamDestroy(cap_stream);
+    for (int t = 0; t < 3; ++t) {
+      if (side[t]) cudaStreamDestroy(side[t]);
+      if (ev_join[t]) cudaEventDestroy(ev_join[t]);
+    }
+    if (ev_fork) cudaEventDestroy(ev_fork);
   }
 };
 
