@@ -414,7 +414,7 @@ def run_tqs(args):
         bufs = [(torch.empty(total, dtype=torch.complex64).pin_memory(),
                  torch.empty(total, dtype=torch.float64).pin_memory(),
                  torch.empty(count, dtype=torch.float64).pin_memory()) for _ in range(2)]
-        e2e_steps = max(3, min(args.steps, 10))
+        e2e_steps = max(3, min(args.steps, 20))
         for k in range(2):  # warm: creation scratch, device pool, both buffer sets
             bb = B.tqs_batch_create_packed(*arrays)
             B.tqs_batch_run_host(bb, *bufs[k])
