@@ -280,6 +280,56 @@ void merge_diagonals(std::vector<FusedOp>& ops, size_t begin) {
     if (op.code < OPC_DLN) flush(nondiag_target(op.code));
     out.push_back(op);
   }
+  // At the end of the pass: lists of two or more targets over the same factor
+  // bits (the far-controlled phases of a QFT pass) run as one OPC_DLISTM op,
+  // which tests the bits once; the rest flush one by one.
+  {
+    bool done[5] = {false, false, false, false, false};
+    for (int t = 0; t < 5; ++t) {
+      if (done[t] || nopen[t] < 2) continue;
+      auto sorted_bits = [&](int u, uint8_t* fb, float2* v) {
+        // the list's entries in order of their bits (stable)
+        int idx[8];
+        for (int k = 0; k < nopen[u]; ++k) idx[k] = k;
+        std::stable_sort(idx, idx + nopen[u], [&](int x, int y) { return open[u][x].f < open[u][y].f; });
+        for (int k = 0; k < 8; ++k) {
+          fb[k] = k < nopen[u] ? open[u][idx[k]].f : 0xFF;
+          v[k] = k < nopen[u] ? open[u][idx[k]].v : make_float2(1.f, 0.f);
+        }
+      };
+      uint8_t fb_t[8];
+      float2 v_t[5][8];
+      sorted_bits(t, fb_t, v_t[t]);
+      unsigned mask = 1u << t;
+      for (int u = t + 1; u < 5; ++u) {
+        if (done[u] || nopen[u] != nopen[t]) continue;
+        uint8_t fb_u[8];
+        sorted_bits(u, fb_u, v_t[u]);
+        if (std::memcmp(fb_u, fb_t, 8) == 0) mask |= 1u << u;
+      }
+      if ((mask & (mask - 1)) == 0) continue;  // no other target with the same bits
+      bool first = true;
+      for (int u = 0; u < 5; ++u) {
+        if (!((mask >> u) & 1)) continue;
+        FusedOp op{};
+        op.code = first ? OPC_DLISTM : OPC_NOP;
+        op.t = static_cast<uint8_t>(first ? mask : 0);
+        op.c = static_cast<uint8_t>(first ? nopen[t] : 0);
+        op.tbit = 0xFF;
+        op.fbit = 0xFF;
+        op.act = 0xFFFF;
+        if (first) std::memcpy(&op.hc, fb_t, 8);
+        for (int k = 0; k < 4; ++k) {
+          op.m[k] = v_t[u][k];
+          op.lo[k] = v_t[u][4 + k];
+        }
+        out.push_back(op);
+        first = false;
+        done[u] = true;
+        nopen[u] = 0;
+      }
+    }
+  }
   for (int t = 0; t < 5; ++t) flush(t);
   // Runs of two or more local-local diagonal factors (OPC_DLL) become one
   // 16-entry diagonal: entry j is the product, in FP64 of the factors' FP32
@@ -381,6 +431,8 @@ unsigned touched_positions(const FusedOp& op) {
   if (code == OPC_DFF) return 0u;
   if (code == OPC_DLL) return (1u << op.t) | (1u << op.c);
   if (code == OPC_DLIST) return op.t < 4 ? 1u << op.t : 0u;
+  if (code == OPC_DLISTM) return op.t & 15u;
+  if (code == OPC_NOP) return 0u;  // a continuation record of the op before it
   return 15u;                                                   // DIAG16, NOP
 }
 

@@ -339,7 +339,48 @@ __device__ __forceinline__ void run_ops(float2 (&a)[16], const FusedOp* __restri
         ++k;
         if (k + 1 < count) next = __ldg(reinterpret_cast<const uint4*>(ops + k + 1));
       }
-      continue;  // OPC_NOP: the second record of an OPC_DIAG16
+      if (code == OPC_DLISTM) {
+        // phase lists of several targets over the same factor bits: the bits
+        // are tested once, then each target's product (8 factors, padded with
+        // (0xFF, 1)) goes into its pending factor or the group's scalar
+        const unsigned tmask = (q0.x >> 8) & 31;
+        const unsigned fb[2] = {q0.z, q0.w};
+        bool on[8];
+#pragma unroll
+        for (int e = 0; e < 8; ++e) {
+          const int f = (fb[e >> 2] >> (8 * (e & 3))) & 0xff;
+          on[e] = f == 0xff || ((base >> f) & 1);
+        }
+        const float2 one = make_float2(1.f, 0.f);
+        int rc = 0;
+#pragma unroll
+        for (int t = 0; t < 5; ++t) {
+          if (!((tmask >> t) & 1)) continue;
+          const uint4* rr = rec + 5 * rc;
+          const uint4 w[4] = {__ldg(rr + 1), __ldg(rr + 2), __ldg(rr + 3), __ldg(rr + 4)};
+          float2 acc = one;
+#pragma unroll
+          for (int e = 0; e < 8; ++e) {
+            const uint4 x = w[e >> 1];
+            const float2 v = (e & 1) ? f2(x.z, x.w) : f2(x.x, x.y);
+            acc = cmul(acc, on[e] ? v : one);
+          }
+          if (t < 4) {
+            pd.p[t] = cmul(pd.p[t], acc);
+            pd.dirty |= 1u << t;
+          } else {
+            sc = cmul(sc, acc);
+            sc_set = true;
+          }
+          ++rc;
+        }
+        // skip the continuation records (and fetch the header after them)
+        if (rc > 1) {
+          k += rc - 1;
+          if (k + 1 < count) next = __ldg(reinterpret_cast<const uint4*>(ops + k + 1));
+        }
+      }
+      continue;  // OPC_NOP: a continuation record, skipped by its op
     }
     if (code == OPC_DLIST) {
       // up to 8 phase factors, each on when its physical bit of the group is

@@ -52,6 +52,13 @@ namespace tqs {
 //                    that local bit set; 4: the whole group), field c = their
 //                    count; factor e (m[0..3], then lo[0..3]) applies when
 //                    the group's physical bit hc-byte e is 1 (0xFF: always)
+//   OPC_DLISTM       phase lists of several targets (field t: a mask of local
+//                    positions 0..3 and bit 4 for the group) over the same
+//                    factor bits (hc bytes, as for OPC_DLIST; field c = their
+//                    count, padded to 8 with 0xFF): one record per target in
+//                    increasing order (this one, then OPC_NOP records), each
+//                    with the target's 8 factors in m[0..3], lo[0..3]; the
+//                    bits are tested once for all targets
 // Diagonal ops carry d0, d1, d1/d0 and `d0one` = 1 when d0 is exactly 1; the
 // coefficient they use when d0 is 1 is repeated in the header (`hc`).
 enum OpCode : uint8_t {
@@ -72,7 +79,8 @@ enum OpCode : uint8_t {
   OPC_DLIST = 54,
   OPC_DIAG16 = 55,
   OPC_NOP = 56,
-  OPC_COUNT = 57
+  OPC_DLISTM = 57,
+  OPC_COUNT = 58
 };
 
 struct alignas(16) FusedOp {

@@ -17,6 +17,7 @@ from paper_2305_14398_gb300 import workloads as W
 
 OPC_H, OPC_X, OPC_XF, OPC_XL, OPC_ANTI, OPC_DENSE, OPC_CDENSE = 0, 4, 8, 12, 28, 32, 36
 OPC_HMASK, OPC_XP = 28, 29
+OPC_DLISTM = 57
 OPC_DLN, OPC_DLF, OPC_DFL, OPC_DFF, OPC_DLL, OPC_DLIST, OPC_DIAG16, OPC_NOP = 40, 44, 48, 52, 53, 54, 55, 56
 BIT_MASK = [0xAAAA, 0xCCCC, 0xF0F0, 0xFF00]
 
@@ -76,10 +77,32 @@ def replay(n, passes, ops, pos, out_scale=1.0, gen_index=0, uniforms=None, outco
         sc = np.ones(G, dtype=np.complex128)
         b0, cnt = int(ps["op_begin"]), int(ps["op_count"])
         prog = ops[b0:b0 + cnt]
+        skip = set()  # continuation records
         for k, op in enumerate(prog):
             code = int(op["code"])
-            if code == OPC_NOP:  # second record of a 16-entry diagonal
-                assert k > 0 and int(prog[k - 1]["code"]) == OPC_DIAG16
+            if code == OPC_NOP:  # second record of a 16-entry diagonal / a list
+                assert k > 0 and (int(prog[k - 1]["code"]) == OPC_DIAG16 or k in skip)
+                continue
+            if code == OPC_DLISTM:  # phase lists of several targets over the same bits
+                tmask, cnt = int(op["t"]), int(op["c"])
+                targets = [t for t in range(5) if (tmask >> t) & 1]
+                assert len(targets) >= 2 and 1 <= cnt <= 8 and int(op["fbit"]) == 255
+                fb = np.frombuffer(np.array([op["hc"]], dtype=np.complex64).tobytes(), dtype=np.uint8)
+                on = [np.ones(G, bool) if fb[e] == 255 else ((base >> int(fb[e])) & 1) == 1
+                      for e in range(8)]
+                for r, t in enumerate(targets):
+                    rec = prog[k + r]
+                    if r > 0:
+                        assert int(rec["code"]) == OPC_NOP
+                        skip.add(k + r)
+                    vs = np.concatenate([rec["m"], rec["lo"]]).astype(np.complex128)
+                    acc = np.ones(G, dtype=np.complex128)
+                    for e in range(8):
+                        acc[on[e]] *= vs[e]
+                    if t < 4:
+                        pend[:, t] *= acc
+                    else:
+                        sc *= acc
                 continue
             if code == OPC_DIAG16:  # entry j multiplies local amplitude j
                 assert int(prog[k + 1]["code"]) == OPC_NOP
