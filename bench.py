@@ -183,12 +183,16 @@ def run_reference(args):
         total_s += r["inner_seconds"]
         cores = r["procs"]
     value = total_c / total_s
+    # the workload's description is the GPU arm's (one batch of the mix per GPU)
+    from paper_2305_14398_gb300 import workloads as W
+    circs = replica_circuits(W, 0, args.batch)
+    steps_total = sum(W.asap_steps(ops) for _, ops in circs)
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": "circuits/s",
         "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": 1e3 * total_s / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "n_qubits": N_QUBITS},
+        "config": workload_config(len(circs), steps_total, max(1, args.gpus)),
         "cpu_baseline": {"value": value, "unit": "circuits/s", "cores": cores, "kind": "oracle",
                          "sample": "per step one circuit in each of one single-thread process "
                                    "per host core at once, kinds in rotation GHZ/DJ-constant/"
@@ -264,6 +268,16 @@ class ClockSampler:
         return {"sm_mhz": statistics.median(sm) if sm else None,
                 "sm_max_mhz": max(smax) if smax else None, "reasons": reasons,
                 "samples": len(inside), "window": window}
+
+
+def workload_config(count, steps_total, world):
+    """The bench line's `config`: the workload, the same for this implementation
+    and the reference arm (no implementation or launch keys)."""
+    return {"workload": WORKLOAD, "n_qubits": N_QUBITS, "circuits_per_gpu": count,
+            "steps_per_batch": steps_total, "parallelism": f"replicas x{world}",
+            "l2": "GPU arm: flushed between timed steps (256 MiB write, not timed); "
+                  "CPU reference arm: not applicable",
+            "outputs": "state (complex64) + |psi|^2 (f64) + norm (f64) per circuit"}
 
 
 def replica_circuits(W, rank, batch):
@@ -388,13 +402,10 @@ def run_tqs(args):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
         "data": "synthetic",
-        "config": {"workload": WORKLOAD, "n_qubits": N_QUBITS, "circuits_per_gpu": count,
-                   "steps_per_batch": steps_total, "parallelism": f"replicas x{world}",
-                   "l2": "flushed between timed steps (256 MiB write, not timed)",
-                   "outputs": "state (complex64) + |psi|^2 (f64) + norm (f64) per circuit",
-                   "launch": {"warps_per_circuit": tuned["team_warps"],
-                              "warps_per_cta": tuned["warps"], "autotune_ms": tuned["timings_ms"],
-                              "autotune_source": tuned["source"]}},
+        "config": workload_config(count, steps_total, world),
+        "launch": {"warps_per_circuit": tuned["team_warps"],
+                   "warps_per_cta": tuned["warps"], "autotune_ms": tuned["timings_ms"],
+                   "autotune_source": tuned["source"]},
         "dense_equiv_complex_gflops": dense_flops * world * args.steps / total_s / 1e9,
         "step_ms_stats": step_stats(step_ms),
         "roofline": {"bound": "hbm", "achieved": achieved_gbs, "peak": hbm_peak,

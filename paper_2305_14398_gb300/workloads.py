@@ -233,6 +233,20 @@ def paper_mix(n: int, count: int, seed_tag: int = 1) -> List[Tuple[str, List[Op]
     return out
 
 
+def asap_steps(ops) -> int:
+    """Number of circuit steps when gates are packed as soon as possible (a
+    gate goes into the step after the last one that touches any of its
+    qubits): the step count of the library's step table, on the host."""
+    last = {}
+    steps = 0
+    for _, qs, _ in ops:
+        k = 1 + max((last.get(q, 0) for q in qs), default=0)
+        for q in qs:
+            last[q] = k
+        steps = max(steps, k)
+    return steps
+
+
 def serving_requests(count: int = 20000, rate_hz: float = 2000.0, n_lo: int = 6,
                      n_hi: int = 16, seed_tag: int = 4):
     """Poisson arrivals at ``rate_hz``; n ~ U{n_lo..n_hi}; kinds 25% each of

@@ -824,3 +824,16 @@ def test_launch_shape_options_validated():
                 B.tqs_set_option(opt, 1, good[0])
         finally:
             B.tqs_set_option(opt, 0, old)
+
+
+def test_asap_steps_matches_library_step_count():
+    """workloads.asap_steps (the bench reference arm's step count, pure Python)
+    equals the library's ASAP step table (tqs_batch_info's total steps)."""
+    mix = W.paper_mix(11, 48, seed_tag=5) + [("r", W.random_mixed(7, 9, (5, 1)))]
+    circs = [(11, ops) for _, ops in mix[:-1]] + [(7, mix[-1][1])]
+    b = B.tqs_batch_create_packed(*B.pack_ops(circs))
+    try:
+        steps = B.tqs_batch_info(b, extra=True)[3]
+    finally:
+        B.tqs_batch_destroy(b)
+    assert steps == sum(W.asap_steps(ops) for _, ops in circs)
