@@ -204,9 +204,11 @@ def test_simulate_and_collapse(kind):
 
 
 def test_shared_memory_path_equals_global_path():
-    """Batch sampling stages circuits of n <= 13 in shared memory; tqs_sample
-    always takes the global path.  Same cumulative sums, so the indices must
-    be identical, boundary draws included."""
+    """Batch sampling stages circuits of n <= 13 in shared memory (exact
+    fixed-point cumulative sums); tqs_sample always takes the global path (FP64
+    sums in the same order).  Away from the boundaries the indices must be
+    identical; for uniforms placed on boundaries C_j / T both paths must give
+    an index the oracle accepts within 1e-12 of that boundary."""
     circs = W.batch_circuits(96, seed_tag=21)
     b = B.tqs_batch_create_packed(*B.pack_ops(circs))
     try:
@@ -230,6 +232,11 @@ def test_shared_memory_path_equals_global_path():
         one = torch.empty(shots, dtype=torch.int64, device="cuda")
         for i, (n, _) in enumerate(circs):
             B.tqs_sample(dp[offs[i]:offs[i + 1]], n, shots, du[i * shots:(i + 1) * shots], one)
-            assert np.array_equal(one.cpu().numpy(), got[i * shots:(i + 1) * shots]), (i, n)
+            g1 = one.cpu().numpy()
+            g0 = got[i * shots:(i + 1) * shots]
+            assert np.array_equal(g1[:shots - 10], g0[:shots - 10]), (i, n)
+            pi, ui = probs[offs[i]:offs[i + 1]], u[i * shots:(i + 1) * shots]
+            check_indices(pi, ui[shots - 10:], g0[shots - 10:], 1e-12)
+            check_indices(pi, ui[shots - 10:], g1[shots - 10:], 1e-12)
     finally:
         B.tqs_batch_destroy(b)
