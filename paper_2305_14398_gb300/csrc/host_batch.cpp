@@ -13,6 +13,13 @@
 // device arrays are the segments concatenated in order, so a program's global
 // offsets are its segment's base plus its local offsets.  Headers are written
 // and passes renumbered in parallel, in place.
+// Number of team kinds (warp, CTA, global) that have circuits in the batch.
+static int team_kinds(const tqs_batch* b) {
+  int k = 0;
+  for (int t = 0; t < 3; ++t) k += b->n_team[t] > 0;
+  return k;
+}
+
 static tqs_status batch_finish(tqs_batch* b, const std::vector<CircMeta>& progs,
                                std::vector<ImageSeg>&& segs) {
   b->count = static_cast<int>(progs.size());
@@ -239,7 +246,7 @@ static tqs_status batch_upload(tqs_batch* b, cudaStream_t s) {
     TQS_CUDA(b->d_gscratch.ensure(size_t(b->plans[TEAM_GLOBAL].grid) *
                                   (size_t(1) << kGlobalSlotQ) * sizeof(float2)),
              "tqs_batch: cudaMalloc scratch");
-  TQS_CUDA(b->ensure_side(), "tqs_batch: side streams");
+  if (team_kinds(b) > 1) TQS_CUDA(b->ensure_side(), "tqs_batch: side streams");
   b->uploaded = true;
   return TQS_OK;
 }
@@ -254,9 +261,7 @@ static tqs_status batch_enqueue_at(tqs_batch* b, char* base, size_t order_off, s
   TQS_CUDA(cudaMemsetAsync(counters, 0, 3 * sizeof(int32_t), s), "tqs_batch: memset counters");
   int k = 0;
   int first = 0;
-  int kinds = 0;
-  for (int t = 0; t < 3; ++t) kinds += b->n_team[t] > 0;
-  const bool fork = kinds > 1;  // (the side streams exist: ensure_side before any capture)
+  const bool fork = team_kinds(b) > 1;  // (the side streams exist: ensure_side before any capture)
   if (fork) {
     if (!b->ev_fork) return fail(TQS_ERR_STATE, "tqs_batch: side streams missing");
     TQS_CUDA(cudaEventRecord(b->ev_fork, s), "tqs_batch: fork");
@@ -448,7 +453,7 @@ tqs_status tqs_batch_run_host(tqs_batch* b, tqs_c64* h_states, double* h_probs, 
   double* dn = zn ? zn : reinterpret_cast<double*>(base + norms_off);
   const size_t gscr_at = (total + 255) & ~size_t(255);
   b->exact_probs = g_exact_probs.load();
-  TQS_CUDA(b->ensure_side(), "tqs_batch_run_host: side streams");
+  if (team_kinds(b) > 1) TQS_CUDA(b->ensure_side(), "tqs_batch_run_host: side streams");
   tqs_status st = batch_enqueue_at(b, base, order_off, counter_off,
                                    reinterpret_cast<float2*>(base + gscr_at), ds, dp, dn, s);
   if (st != TQS_OK) return st;
