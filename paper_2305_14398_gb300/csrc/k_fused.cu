@@ -120,10 +120,10 @@ __device__ __forceinline__ void h_t(float2 (&a)[16]) {
   for (int p = 0; p < 8; ++p) {
     const int j0 = ((p >> T) << (T + 1)) | (p & ((1 << T) - 1));
     const int j1 = j0 | (1 << T);
-    a[j0].x += a[j1].x;
-    a[j0].y += a[j1].y;
-    a[j1].x = fmaf(-2.f, a[j1].x, a[j0].x);
-    a[j1].y = fmaf(-2.f, a[j1].y, a[j0].y);
+    // packed FP32x2 (both parts in one instruction; each rounded as the
+    // scalar operation would be)
+    a[j0] = __fadd2_rn(a[j0], a[j1]);
+    a[j1] = __ffma2_rn(make_float2(-2.f, -2.f), a[j1], a[j0]);
   }
 }
 
@@ -471,8 +471,9 @@ __device__ __forceinline__ void run_ops(float2 (&a)[16], const FusedOp* __restri
 #pragma unroll
     for (int j = 0; j < 16; ++j) a[j] = cmul(a[j], sc);
   } else if (scale != 1.0f) {
+    const float2 s2 = make_float2(scale, scale);
 #pragma unroll
-    for (int j = 0; j < 16; ++j) a[j] = make_float2(a[j].x * scale, a[j].y * scale);
+    for (int j = 0; j < 16; ++j) a[j] = __fmul2_rn(a[j], s2);
   }
 }
 
