@@ -37,10 +37,10 @@ WORKLOAD = "paper-shaped 11-qubit circuits (GHZ / DJ-constant / DJ-balanced / QF
 
 # DRAM bytes (read + write) per launch of the fused kernel (two warps per
 # circuit, the autotuned shape) on this workload, from the ncu capture
-# summarised in profiles/: 19.68 MB read + 475.97 MB written for one launch
+# summarised in profiles/: 19.63 MB read + 475.75 MB written for one launch
 # over the 16384 circuits of a step.  Set back to None whenever the kernel
 # changes, until it is captured again.
-NCU_TRAFFIC_BYTES = 19_684_352 + 475_965_184
+NCU_TRAFFIC_BYTES = None
 
 
 def parse_args():

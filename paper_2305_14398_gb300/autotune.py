@@ -159,20 +159,36 @@ def _tune(key, option, candidates, run, reps, use_cache):
     return {"value": v, "timings_ms": timings, "source": "measured"}
 
 
+def cta_subset(circuits):
+    """The circuits of a batch that run on one-CTA teams (12..14 qubits) and
+    the cache-key part that tells such subsets apart."""
+    sub = [(n, ops) for n, ops in circuits if 12 <= max(n, 4) <= 14]
+    amps = sum(1 << n for n, _ in sub)
+    gates = sum(len(ops) for _, ops in sub)
+    return sub, f"cta|{len(sub)}|a{amps}|g{gates}"
+
+
 def tune_cta_threads(circuits, reps: int = 3, use_cache: bool = True):
-    """Threads of the one-CTA team (circuits of 12..14 qubits) for this batch."""
+    """Threads of the one-CTA team (circuits of 12..14 qubits) for this batch.
+
+    Timed on those circuits alone, with the probabilities written as in a real
+    run, so that the rest of the batch neither hides nor blurs the difference.
+    The cache key carries the count, total amplitudes and total gates of that
+    subset: two batches of the same size and largest n but another mix of
+    circuits are tuned apart."""
     import torch
-    ns = [n for n, _ in circuits if 12 <= max(n, 4) <= 14]
-    if not ns:
+    sub, tail = cta_subset(circuits)
+    if not sub:
         return {"value": None, "timings_ms": {}, "source": "no circuits of 12..14 qubits"}
-    key = f"v3|{torch.cuda.get_device_name()}|cta|n{max(ns)}|{len(circuits)}"
-    b = B.tqs_batch_create_packed(*B.pack_ops(list(circuits)))
+    key = f"v4|{torch.cuda.get_device_name()}|{tail}"
+    b = B.tqs_batch_create_packed(*B.pack_ops(sub))
     try:
         count, total, _ = B.tqs_batch_info(b)
         st = torch.empty(total, dtype=torch.complex64, device="cuda")
+        pr = torch.empty(total, dtype=torch.float64, device="cuda")
         nm = torch.empty(count, dtype=torch.float64, device="cuda")
         return _tune(key, B.OPT_CTA_THREADS, (256, 512),
-                     lambda: B.tqs_batch_run(b, st, None, nm, use_graph=False), reps, use_cache)
+                     lambda: B.tqs_batch_run(b, st, pr, nm, use_graph=False), reps, use_cache)
     finally:
         B.tqs_batch_destroy(b)
 

@@ -38,6 +38,19 @@ __device__ __forceinline__ int ins0(int x, int b) {
   return ((x >> b) << (b + 1)) | (x & ((1 << b) - 1));
 }
 
+// The low bits of x spread over the set bits of mask, lowest first (a bit
+// deposit: bit k of x lands on the k-th set bit of mask).
+__device__ __forceinline__ int deposit_bits(int x, int mask) {
+  int r = 0;
+  while (mask != 0) {
+    const int b = mask & -mask;
+    if (x & 1) r |= b;
+    x >>= 1;
+    mask ^= b;
+  }
+  return r;
+}
+
 // (ah + al) * x + (bh + bl) * y for coefficients split into FP32 hi + lo
 // parts: the small lo products first, then the hi products, so that the
 // coefficient rounding of a single FP32 matrix adds no bias to the norm.
@@ -676,15 +689,29 @@ __device__ void run_circuit(const FusedLaunch& L, int ci, float2* st, int rank, 
       st[TQS_IX(swz(i), NI)] = (i < N) ? init[i] : make_float2(0.f, 0.f);
     if (TEAM == TEAM_MULTI) grid_sync(*bar); else team_sync<TEAM>();
   }
+  // Support of a state started from the basis state |gen_index>: a register
+  // pass mixes amplitudes only within its groups (indices that differ in its
+  // local positions), so once the passes so far have had the positions T as
+  // local ones, every amplitude whose index differs from gen_index in a bit
+  // outside T is still exactly zero.  `touched` holds T (all ones: no such
+  // knowledge, after an initial state, a measurement or a custom unitary).
+  // A pass's groups whose far bits differ from gen_index outside T are zero
+  // and stay zero under its ops, so the team works only the others: the
+  // group counter is deposited into the far bits inside T, the far bits
+  // outside T are those of gen_index.  The generation pass first writes
+  // zeros over the whole state; later passes leave the zero groups as they are.
+  int touched = init == nullptr ? 0 : -1;
   for (int p = 0; p < cd.pass_count; ++p) {
     const uint4 pr = __ldg(reinterpret_cast<const uint4*>(L.passes + cd.pass_begin + p));
     const int l0 = pr.x & 0xff, l1 = (pr.x >> 8) & 0xff, l2 = (pr.x >> 16) & 0xff, l3 = pr.x >> 24;
     if (l0 == kInstrPass) {
       instr_pass<TEAM>(L, nint, l1, (l2 & 1) != 0, pr.y, st, rank, size, s_red);
+      touched = -1;
       continue;
     }
     if (l0 == kWidePass) {
       wide_pass<TEAM>(L, nint, l1, pr.y, pr.z, pr.w, st, rank, size);
+      touched = -1;
       continue;
     }
     const FusedOp* ops = L.ops + pr.y;
@@ -693,8 +720,21 @@ __device__ void run_circuit(const FusedLaunch& L, int ci, float2* st, int rank, 
     const bool gen = (p == 0) && (init == nullptr);
     const int w0 = swz(1 << l0), w1 = swz(1 << l1), w2 = swz(1 << l2), w3 = swz(1 << l3);
     const int b0 = 1 << l0, b1 = 1 << l1, b2 = 1 << l2, b3 = 1 << l3;
-    for (int g = rank; g < G; g += size) {
-      const int base = ins0(ins0(ins0(ins0(g, l0), l1), l2), l3);
+    const int far = ((1 << nint) - 1) & ~(b0 | b1 | b2 | b3);
+    const int free_far = far & touched;
+    const bool sparse = free_far != far;
+    const int fixed = cd.gen_index & far & ~touched;
+    const int Gs = sparse ? (1 << __popc(free_far)) : G;
+    if (sparse && gen) {
+      float4* const st4 = reinterpret_cast<float4*>(st);
+      const int NH = 1 << (nint - 1);
+      for (int i = rank; i < NH; i += size) st4[TQS_IX(i, NH)] = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (TEAM == TEAM_MULTI) grid_sync(*bar); else team_sync<TEAM>();
+    }
+    touched |= b0 | b1 | b2 | b3;
+    for (int g = rank; g < Gs; g += size) {
+      const int base = sparse ? (fixed | deposit_bits(g, free_far))
+                              : ins0(ins0(ins0(ins0(g, l0), l1), l2), l3);
       const int sb = swz(base);
       float2 a[16];
 #pragma unroll

@@ -837,3 +837,19 @@ def test_asap_steps_matches_library_step_count():
     finally:
         B.tqs_batch_destroy(b)
     assert steps == sum(W.asap_steps(ops) for _, ops in circs)
+
+
+def test_cta_threads_tuning_keys_tell_batches_apart():
+    """The one-CTA team's thread count is tuned per subset of 12..14-qubit
+    circuits: the mixed random batch and the all-14-qubit batch (same size,
+    same largest n) must not share a cached choice."""
+    from paper_2305_14398_gb300 import autotune
+    mixed = W.batch_circuits(4096, seed_tag=3)
+    n14 = W.batch_circuits_fixed_n(4096, 14, seed_tag=5)
+    sub_m, key_m = autotune.cta_subset(mixed)
+    sub_14, key_14 = autotune.cta_subset(n14)
+    assert len(sub_14) == 4096
+    assert 0 < len(sub_m) < 4096
+    assert all(12 <= n <= 14 for n, _ in sub_m)
+    assert key_m != key_14
+    assert autotune.cta_subset([(8, [("h", [0], [])])]) == ([], "cta|0|a0|g0")
