@@ -35,12 +35,13 @@ BATCH = 16384
 METRIC = "circuits/s"
 WORKLOAD = "paper-shaped 11-qubit circuits (GHZ / DJ-constant / DJ-balanced / QFT, 25% each)"
 
-# DRAM bytes (read + write) per launch of the fused kernel (two warps per
-# circuit, the autotuned shape) on this workload, from the ncu capture
-# summarised in profiles/: 19.63 MB read + 475.75 MB written for one launch
-# over the 16384 circuits of a step.  Set back to None whenever the kernel
+# DRAM bytes (read + write) per launch of the fused kernel on this workload,
+# from the ncu capture summarised in profiles/: 19.64 MB read + 476.63 MB
+# written for one launch over the 16384 circuits of a step, at the launch
+# shape given here (one warp per circuit, one warp per CTA).  Reported only
+# when the autotuner picked that shape; set back to None whenever the kernel
 # changes, until it is captured again.
-NCU_TRAFFIC_BYTES = None
+NCU_TRAFFIC = {"team_warps": 1, "warps_per_cta": 1, "bytes": 19_641_600 + 476_631_296}
 
 
 def parse_args():
@@ -410,7 +411,10 @@ def run_tqs(args):
         "step_ms_stats": step_stats(step_ms),
         "roofline": {"bound": "hbm", "achieved": achieved_gbs, "peak": hbm_peak,
                      "unit": "GB/s", "frac": achieved_gbs / hbm_peak,
-                     "traffic": NCU_TRAFFIC_BYTES if tuned["team_warps"] == 2 else None,
+                     "traffic": (NCU_TRAFFIC["bytes"] if NCU_TRAFFIC is not None and
+                                 (tuned["team_warps"], tuned["warps"]) ==
+                                 (NCU_TRAFFIC["team_warps"], NCU_TRAFFIC["warps_per_cta"])
+                                 else None),
                      "peak_source": peak_src,
                      "kernel": ("fused_kernel<TEAM_PAIR>" if tuned["team_warps"] == 2
                                 else "fused_kernel<TEAM_WARP>"),
