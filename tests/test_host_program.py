@@ -27,7 +27,10 @@ def ins0(x, b):
 
 
 def replay(n, passes, ops, pos, out_scale=1.0, gen_index=0, uniforms=None, outcomes=None,
-           customs=()):
+           customs=(), on_pass=None):
+    """The compiled program in FP64 on the CPU.  on_pass(pi, L, st), if given,
+    sees the physical state before pass pi (pi = len(passes), L = None: after
+    the last pass, before the output map)."""
     nint = max(n, 4)
     st = np.zeros(1 << nint, dtype=np.complex128)
     st[gen_index] = 1.0
@@ -35,6 +38,8 @@ def replay(n, passes, ops, pos, out_scale=1.0, gen_index=0, uniforms=None, outco
     customs = list(customs)
     for pi, ps in enumerate(passes):
         L = [int(v) for v in ps["L"]]
+        if on_pass is not None:
+            on_pass(pi, L, st)
         if L[0] == 254:  # custom k-qubit unitary: the next custom matrix, on the
             k = L[1]     # physical bits packed 5 bits each in op_count
             assert pi > 0 and 2 <= k <= 5
@@ -228,6 +233,8 @@ def replay(n, passes, ops, pos, out_scale=1.0, gen_index=0, uniforms=None, outco
                     a[:, j] *= pend[:, b]
         a *= sc[:, None] * float(ps["scale"])
         st[idx] = a
+    if on_pass is not None:
+        on_pass(len(passes), None, st)
     # output map: physical index of logical y = map[16] ^ XOR of map[q] over y's set bits
     i = np.arange(1 << n, dtype=np.int64)
     phys = np.full_like(i, int(pos[16]))
@@ -280,6 +287,57 @@ def test_program_replay_matches_oracle(name, n, ops):
     want = fsv_route.simulate(n, ops)
     # the program stores matrices in FP32; the replay computes in FP64
     assert np.max(np.abs(got - want)) < 2e-6
+
+
+def support_tracker(nint, gen):
+    """The fused kernel's zero-group rule, checked on the replay: before each
+    pass, every amplitude whose physical index differs from the start index
+    gen in a bit outside T (the union of the local positions of the register
+    passes so far; all bits after a measure / reset or a custom unitary) is
+    exactly zero.  Returns the hook and a list of (pass, live amplitudes)."""
+    allb = (1 << nint) - 1
+    idx = np.arange(1 << nint)
+    touched = [0]
+    seen = []
+
+    def on_pass(pi, L, st):
+        if touched[0] != -1:
+            outside = ((idx ^ gen) & allb & ~touched[0]) != 0
+            assert np.all(st[outside] == 0), (pi, int(np.count_nonzero(st[outside])))
+            seen.append((pi, int(np.count_nonzero(~outside))))
+        if L is None:
+            return
+        if L[0] in (254, 255):
+            touched[0] = -1
+        elif touched[0] != -1:
+            touched[0] |= sum(1 << b for b in L)
+
+    return on_pass, seen
+
+
+@pytest.mark.parametrize("name,n,ops", CASES, ids=[c[0] for c in CASES])
+def test_zero_groups_of_a_basis_start(name, n, ops):
+    """What the fused kernel skips is zero: checked pass by pass on the replay
+    of the compiled program (the kernel works only the groups that can hold a
+    nonzero amplitude, and the generation pass starts from zeros)."""
+    passes, prog_ops, pos, osc, gen = compiled(n, ops)
+    on_pass, seen = support_tracker(max(n, 4), gen)
+    got = replay(n, passes, prog_ops, pos, osc, gen, on_pass=on_pass)
+    assert np.max(np.abs(got - fsv_route.simulate(n, ops))) < 2e-6
+    assert seen[0] == (0, 1)  # the generation pass works the start state's group only
+
+
+@pytest.mark.parametrize("n,seed", [(3, 0), (5, 1), (8, 2), (11, 0)])
+def test_zero_groups_stop_at_an_instruction(n, seed):
+    """After a measure / reset the rule no longer applies (the kernel works
+    every group from there on); before it, it holds as above."""
+    ops = with_instructions(n, 100 * n + seed)
+    u = safe_uniforms(n, ops, seed)
+    passes, prog_ops, pos, osc, gen = compiled(n, ops)
+    on_pass, seen = support_tracker(max(n, 4), gen)
+    replay(n, passes, prog_ops, pos, osc, gen, uniforms=u, outcomes=[], on_pass=on_pass)
+    first_instr = next(i for i, p in enumerate(passes) if int(p["L"][0]) == 255)
+    assert [pi for pi, _ in seen] == list(range(first_instr + 1))
 
 
 def test_steps_are_asap():
