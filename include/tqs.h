@@ -567,7 +567,8 @@ tqs_status tqs_check_violations(uint32_t* count, int reset);
  * TQS_OPT_CTA_THREADS, key = 0: threads of the one-CTA team that runs a
  *   circuit of 12..14 qubits, 256 or 512 (default 512).  States and
  *   probabilities are bitwise the same; the FP64 norm's reduction order
- *   follows the team size.
+ *   follows the team size.  A batch reads it (with the warp-class options)
+ *   when it is first run on the device, and keeps that launch plan.
  * TQS_OPT_FSV_TILE_Q, key = 0: tile bits of tqs_simulate_fsv's passes, 0
  *   (default: 13 from 24 qubits on, else 12) or 10..13.  Fewer tile bits mean
  *   more passes over HBM but more tiles to spread over the SMs.
