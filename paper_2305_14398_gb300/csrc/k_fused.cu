@@ -9,7 +9,9 @@
 // circuit's state in shared memory (or, above 2^14 amplitudes, in L2-resident
 // global scratch) and runs the passes, then writes the state in logical
 // order, |psi_i|^2 (FP32 arithmetic, or exact in FP64) stored as FP64, and
-// the FP64 norm.
+// the FP64 norm.  A circuit that starts from a basis state works, in each
+// pass, only the groups of 16 amplitudes that can be nonzero by then (the
+// support rule in run_circuit); the rest of its state is zero.
 //
 // Teams: one warp or a pair of warps per circuit (n <= 11), one 512-thread CTA
 // per circuit (n <= 14), one CTA on global scratch (n <= 16), or several
