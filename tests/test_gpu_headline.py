@@ -1,8 +1,9 @@
 """GPU parity of the exact configuration the benchmark times: 16384 paper-shaped
 11-qubit circuits (GHZ chain, Deutsch-Jozsa constant and balanced, QFT on a
 seeded basis state, 25 % each; seed tag 1) in one CUDA-graph launch of the
-persistent fused kernel, with two warps per circuit and 16 warps per CTA (the
-autotuned shape) and with one warp per circuit and 8 warps per CTA.
+persistent fused kernel, at three launch shapes: one warp per circuit and one
+warp per CTA (the shape the autotuner picks), one warp per circuit and 8 warps
+per CTA, and two warps per circuit and 16 warps per CTA.
 
 Every circuit's state is compared element by element with the oracle's
 per-gate route (eq. 12) at 1e-5; every probability with the oracle's
@@ -76,9 +77,10 @@ def check_against_oracle(want, st, pr, nm):
     assert np.all(np.abs(nm - 1.0) <= NORM_TOL)
 
 
-# (warps per circuit, warps per CTA): the autotuned pair shape, and one warp per
-# circuit with the most warps whose 16 KiB slices fit a CTA's shared memory
-SHAPES = [(2, 16), (1, 8)]
+# (warps per circuit, warps per CTA): the autotuned shape (one team per CTA,
+# 13 CTAs per SM), one warp per circuit with the most warps whose 16 KiB slices
+# fit a CTA's shared memory, and the pair shape
+SHAPES = [(1, 1), (1, 8), (2, 16)]
 
 
 @pytest.mark.parametrize("team_warps,warps", SHAPES)
@@ -97,6 +99,7 @@ def test_headline_shapes_bitwise_equal(headline):
     """States and probabilities do not depend on the launch shape."""
     circs, _ = headline
     a = run_shape(circs, *SHAPES[0])
-    b = run_shape(circs, *SHAPES[1])
-    assert np.array_equal(a[0].view(np.uint32), b[0].view(np.uint32))
-    assert np.array_equal(a[1].view(np.uint64), b[1].view(np.uint64))
+    for shape in SHAPES[1:]:
+        b = run_shape(circs, *shape)
+        assert np.array_equal(a[0].view(np.uint32), b[0].view(np.uint32)), shape
+        assert np.array_equal(a[1].view(np.uint64), b[1].view(np.uint64)), shape
