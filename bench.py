@@ -44,6 +44,16 @@ WORKLOAD = "paper-shaped 11-qubit circuits (GHZ / DJ-constant / DJ-balanced / QF
 NCU_TRAFFIC = {"team_warps": 1, "warps_per_cta": 1, "bytes": 19_641_600 + 476_631_296}
 
 
+def roofline_traffic(team_warps, warps_per_cta, capture=NCU_TRAFFIC):
+    """The captured DRAM bytes per launch when the timed launch shape is the
+    captured one, else None (another shape's traffic was not measured)."""
+    if capture is None:
+        return None
+    if (team_warps, warps_per_cta) != (capture["team_warps"], capture["warps_per_cta"]):
+        return None
+    return capture["bytes"]
+
+
 def parse_args():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -411,10 +421,7 @@ def run_tqs(args):
         "step_ms_stats": step_stats(step_ms),
         "roofline": {"bound": "hbm", "achieved": achieved_gbs, "peak": hbm_peak,
                      "unit": "GB/s", "frac": achieved_gbs / hbm_peak,
-                     "traffic": (NCU_TRAFFIC["bytes"] if NCU_TRAFFIC is not None and
-                                 (tuned["team_warps"], tuned["warps"]) ==
-                                 (NCU_TRAFFIC["team_warps"], NCU_TRAFFIC["warps_per_cta"])
-                                 else None),
+                     "traffic": roofline_traffic(tuned["team_warps"], tuned["warps"]),
                      "peak_source": peak_src,
                      "kernel": ("fused_kernel<TEAM_PAIR>" if tuned["team_warps"] == 2
                                 else "fused_kernel<TEAM_WARP>"),

@@ -911,3 +911,17 @@ def test_cta_threads_tuning_keys_tell_batches_apart():
     assert all(12 <= n <= 14 for n, _ in sub_m)
     assert key_m != key_14
     assert autotune.cta_subset([(8, [("h", [0], [])])]) == ([], "cta|0|a0|g0")
+
+
+def test_bench_reports_traffic_only_for_the_captured_shape():
+    """roofline.traffic is the ncu capture's DRAM bytes, and only when the bench
+    times the launch shape that capture was taken at."""
+    import bench
+    cap = {"team_warps": 1, "warps_per_cta": 1, "bytes": 123}
+    assert bench.roofline_traffic(1, 1, cap) == 123
+    assert bench.roofline_traffic(2, 8, cap) is None
+    assert bench.roofline_traffic(1, 8, cap) is None
+    assert bench.roofline_traffic(1, 1, None) is None
+    c = bench.NCU_TRAFFIC
+    if c is not None:  # the committed capture: DRAM bytes of one launch, within the outputs
+        assert 0 < c["bytes"] <= 16384 * (16 << 11) + 64 << 20
