@@ -924,4 +924,4 @@ def test_bench_reports_traffic_only_for_the_captured_shape():
     assert bench.roofline_traffic(1, 1, None) is None
     c = bench.NCU_TRAFFIC
     if c is not None:  # the committed capture: DRAM bytes of one launch, within the outputs
-        assert 0 < c["bytes"] <= 16384 * (16 << 11) + 64 << 20
+        assert 0 < c["bytes"] <= 16384 * (16 << 11) + (64 << 20)
