@@ -596,17 +596,21 @@ void compile_program(int n, const std::vector<const Gate*>& gs_in, Program& P,
   if (absorb) {
     static thread_local std::vector<char> take_tls;
     std::vector<char>& take = take_tls;
-    take.assign(gs.size(), 0);
+    // scan from the end; once every qubit has a later gate that stays, no
+    // earlier gate can join the tail, so the scan stops there (at `from`)
+    const uint32_t all_q = n >= 32 ? 0xffffffffu : ((1u << n) - 1u);
     uint32_t blocked = 0;  // qubits with a later gate that stays in the program
-    for (size_t i = gs.size(); i-- > 0;) {
-      const Gate& g = *gs[i];
+    size_t from = gs.size();
+    take.assign(gs.size(), 0);
+    while (from > 0 && blocked != all_q) {
+      const Gate& g = *gs[--from];
       const uint32_t qm = qubit_mask(g);
       const bool perm = g.kind == TQS_X || g.kind == TQS_CNOT || g.kind == TQS_SWAP;
-      if (perm && !(qm & blocked)) take[i] = 1;
+      if (perm && !(qm & blocked)) take[from] = 1;
       else blocked |= qm;
     }
-    size_t k = 0;
-    for (size_t i = 0; i < gs.size(); ++i) {
+    size_t k = from;
+    for (size_t i = from; i < gs.size(); ++i) {
       if (take[i]) tail.push_back(gs[i]);
       else gs[k++] = gs[i];
     }
@@ -971,8 +975,7 @@ void compile_program(int n, const std::vector<const Gate*>& gs_in, Program& P,
   }
   auto relabel = [&](uint32_t v) {
     uint32_t r = 0;
-    for (int q = 0; q < n && q < 32; ++q)
-      if ((v >> q) & 1) r |= 1u << phys[q];
+    for (; v != 0; v &= v - 1) r |= 1u << phys[__builtin_ctz(v)];
     return r;
   };
   for (int q = 0; q < 16; ++q)
